@@ -1,0 +1,150 @@
+"""Pins of the whole oracle scheme against closed forms of Sec. 2.1 and Secs. 3-4.
+
+* Chapman-Enskog (Sec. 2.1): nu = (1/omega - 1/2) theta and
+  kappa = (d+2)/2 nu rho.  With c_p = (d+2)/2 the thermal diffusivity equals nu,
+  and the sound attenuation (longitudinal viscosity 2 nu (d-1)/d plus
+  (gamma-1) times the diffusivity) also equals nu: shear, entropy and sound modes
+  all decay as exp(-nu k^2 t).  Sound travels at sqrt(gamma theta),
+  gamma = (d+2)/d.  Checked on the linearised one-step operator (the
+  deviation must shrink like k^2) and by simulating a shear wave.
+* A shear wave riding on a uniform flow is carried downstream at that flow
+  speed (pins the direction of streaming).
+* Stability: the literal omega = 1.8 at theta = 1 on {0,+-1,+-3}^2 is
+  linearly unstable; omega = 1.3 is stable.
+* Positivity ranges of Sec. 3.1: |u|/sqrt(theta0) <= sqrt(3) for zeta = 4 and
+  sqrt(2) for zeta = 3 (D1Q3); u = 0 window a^2/3 < theta < b^2/3 for the
+  symmetric five-velocity set {0, +-a, +-b} (from Eq. eq:1d5v at u = 0).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import stability as S
+from paper_1402_5487_gb300 import inputs as I
+
+from conftest import read_printed_values
+
+V5 = (0, 1, -1, 3, -3)
+
+
+def _mode_table(lat, k, theta):
+    lam = S.hydro_modes(lat, k)
+    nu = (1.0 / lat.omega - 0.5) * theta
+    hydro = lam[: lat.dim + 2]
+    decay = -np.log(np.abs(hydro)) / (k * k) / nu - 1.0
+    speed = np.angle(hydro) / k
+    return decay, speed
+
+
+@pytest.mark.parametrize("dim,theta,omega", [(2, 1.0, 1.3), (1, 0.5, 1.5), (2, 0.6, 1.7)])
+def test_linear_modes_decay_at_nu_k2(dim, theta, omega):
+    d64, s64 = _mode_table(O.Lattice(dim, V5, omega, 4, 4, theta0=theta), 2 * np.pi / 64, theta)
+    d128, s128 = _mode_table(O.Lattice(dim, V5, omega, 4, 4, theta0=theta), 2 * np.pi / 128, theta)
+    # all d+2 hydrodynamic modes decay at nu k^2 up to an O(k^2) correction
+    assert np.max(np.abs(d128)) < 3e-3
+    ratio = np.abs(d64) / np.maximum(np.abs(d128), 1e-30)
+    assert np.all((ratio > 3.5) & (ratio < 4.5))
+    richardson = (4 * d128 - d64) / 3
+    assert np.max(np.abs(richardson)) < 2e-5
+    # two sound modes at +- sqrt(gamma theta), gamma = (d+2)/d; the others do not propagate
+    cs = math.sqrt((dim + 2) / dim * theta)
+    srt = np.sort(s128)
+    assert abs(srt[-1] - cs) / cs < 2e-4 and abs(srt[0] + cs) / cs < 2e-4
+    assert np.all(np.abs(srt[1:-1]) < 1e-8)
+
+
+def test_kappa_matches_nu_in_entropy_mode():
+    # kappa = (d+2)/2 nu rho  <=>  thermal diffusivity kappa/(rho c_p) = nu; an initial
+    # temperature wave at constant pressure decays as exp(-nu k^2 t).
+    L, theta0, omega = 64, 1.0, 1.3
+    lat = O.Lattice(2, V5, omega, L, 4, theta0=theta0)
+    x = np.arange(L)[None, :] * np.ones((4, 1))
+    eps = 1e-4
+    th = theta0 * (1 + eps * np.cos(2 * np.pi * x / L))
+    rho = 1.0 / (1 + eps * np.cos(2 * np.pi * x / L))  # p = rho theta uniform
+    f = lat.init(rho, 0 * x, 0 * x, th)
+    k = 2 * np.pi / L
+    amps = []
+    for _ in range(2):
+        f = lat.run(f, 150)
+        rr, _, _, tt = lat.moments(f)
+        # entropy variable d(theta)/theta0 - (gamma-1) d(rho)/rho0 removes the sound modes
+        ent = (tt[0] - theta0) / theta0 - (2.0 - 1.0) * (rr[0] - 1.0)
+        amps.append(np.sum(ent * np.cos(k * np.arange(L))) * 2 / L)
+    nu = (1 / omega - 0.5) * theta0
+    rate = -math.log(amps[1] / amps[0]) / (k * k * 150)
+    assert abs(rate / nu - 1) < 0.01
+
+
+def test_shear_wave_decay_simulation():
+    L, theta0, omega = 64, 1.0, 1.3
+    lat = O.Lattice(2, V5, omega, 4, L, theta0=theta0)
+    f = lat.init(*I.shear_wave_fields(4, theta0, amp=1e-3, ny=L))
+    y = np.arange(L)
+    k = 2 * np.pi / L
+    nu = (1 / omega - 0.5) * theta0
+    amps = []
+    for _ in range(3):
+        f = lat.run(f, 100)
+        _, ux, _, _ = lat.moments(f)
+        amps.append(np.sum(ux[:, 0] * np.sin(k * y)) * 2 / L)
+    rate = -math.log(amps[2] / amps[0]) / (k * k * 200)
+    assert abs(rate / nu - 1) < 0.01
+
+
+def test_shear_wave_advected_downstream():
+    # u_x(y) shear wave on a uniform flow U along y would need u_y; use the transposed
+    # case: u_y = A sin(k x) on a uniform u_x = U; its phase moves by +U t.
+    L, theta0, omega, U = 64, 1.0, 1.3, 0.05
+    lat = O.Lattice(2, V5, omega, L, 4, theta0=theta0)
+    x = np.arange(L)
+    k = 2 * np.pi / L
+    ux = np.full((4, L), U)
+    uy = 1e-3 * np.sin(k * x)[None, :] * np.ones((4, 1))
+    f = lat.init(np.ones((4, L)), ux, uy, np.full((4, L), theta0))
+    t = 160
+    f = lat.run(f, t)
+    _, _, uyt, _ = lat.moments(f)
+    c = np.sum(uyt[0] * np.cos(k * x))
+    s = np.sum(uyt[0] * np.sin(k * x))
+    shift = -math.atan2(c, s) / k  # u_y ~ sin(k (x - shift))
+    assert abs(shift - U * t) < 0.02 * U * t
+
+
+def test_literal_kh_omega_is_linearly_unstable():
+    unstable = O.Lattice(2, V5, 1.8, 4, 4, theta0=1.0)
+    stable = O.Lattice(2, V5, 1.3, 4, 4, theta0=1.0)
+    assert S.spectral_radius(unstable, n=16) > 1.1
+    assert S.spectral_radius(stable, n=16) <= 1.0 + 1e-9
+    assert S.spectral_radius(stable, n=16, ux=0.1) <= 1.0 + 1e-9
+
+
+@pytest.mark.parametrize("zeta,printed", [(4, "positivity_zeta4"), (3, "positivity_zeta3")])
+def test_d1q3_positivity_range(zeta, printed):
+    vals = read_printed_values()
+    theta0 = 1.0 / zeta  # lattice velocities {0, +-1} = {0, +-sqrt(zeta theta0)}
+    lo, hi = S.positivity_interval((0, 1, -1), theta0)
+    assert abs(hi / math.sqrt(theta0) - vals[printed]) < 1e-9
+    assert abs(lo / math.sqrt(theta0) + vals[printed]) < 1e-9
+
+
+@pytest.mark.parametrize("v", [(0, 1, -1, 3, -3), (0, 1, -1, 2, -2), (0, 2, -2, 3, -3)])
+def test_d1q5_zero_velocity_theta_window(v):
+    a, b = abs(v[1]), abs(v[3])
+    lo, hi = S.positivity_theta_window(v)
+    assert abs(lo - a * a / 3) < 1e-9 and abs(hi - b * b / 3) < 1e-9
+
+
+def test_matched_relaxation_constant():
+    # Sec. 3.2: nu = (1/omega - 1/2) sqrt(theta0) dx / sqrt(zeta); LBGK (zeta 3, omega 1)
+    # and zeta = 4 share viscosity at omega = 4 sqrt(3) - 6.
+    vals = read_printed_values()
+    om4 = vals["omega_zeta4_matched"]
+    assert abs(om4 - (4 * math.sqrt(3) - 6)) < 1e-15
+    nu3 = (1 / 1.0 - 0.5) / math.sqrt(3)
+    nu4 = (1 / om4 - 0.5) / math.sqrt(4)
+    assert abs(nu3 - nu4) < 1e-15
+    # footnote: 362 LBGK iterations are 362 * 2/sqrt(3) ~ 418 zeta=4 iterations
+    assert abs(vals["shock6_iterations_lbgk"] * 2 / math.sqrt(3) - vals["shock6_iterations_param"]) < 0.01
