@@ -1,0 +1,345 @@
+#!/usr/bin/env python3
+"""Benchmark of the PLBM stream-and-collide step on GB300.
+
+Default workload: D2Q25 ({0,+-1,+-3}^2) Kelvin-Helmholtz double shear layer on
+a periodic 2048 x 2048 grid, FP32 populations, theta0 = 1, omega = 1.3.  The two
+population arrays (2 x 839 MB) are far larger than the 129 MB L2, so every
+timed step streams its inputs from HBM.
+
+Prints ONE JSON line (rank 0).  ``value`` is whole-job MLUPS (node updates per
+microsecond summed over ranks) measured with CUDA events on the solver's stream;
+``e2e`` is the same metric through the public API with host (pinned) buffers:
+plbm_init from host fields, K steps, plbm_moments back to host.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload and prints the same metric with "impl": "reference".
+Under torchrun every rank runs an independent replica (the build is
+single-GPU: replicas only); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1402_5487_gb300 import inputs as I  # noqa: E402
+
+V5 = I.SET_013
+OMEGA = 1.3
+THETA0 = 1.0
+ELEM = {"f64": 8, "f32": 4, "f16dev": 2, "bf16dev": 2}
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def time_device(solver, steps: int, warmup: int, torch, barrier):
+    """CUDA-event time of `steps` plbm_step launches on the solver's stream."""
+    solver.step(warmup)
+    st = solver.stream
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier()
+    e0.record(st)
+    solver.step(steps)
+    e1.record(st)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    return e0.elapsed_time(e1) * 1e-3
+
+
+def run_variant(torch, L, prec, steps, warmup, barrier, dim=2, v=V5, bc="periodic", fields=None,
+                theta0=THETA0, omega=OMEGA, left=None, right=None, nx=None):
+    from paper_1402_5487_gb300 import plbm
+    nx = L if nx is None else nx
+    ny = L if dim == 2 else 1
+    s = plbm.Solver(dim, v, omega, nx, ny, theta0=theta0, prec=prec, bc=bc, left_state=left,
+                    right_state=right)
+    fields = I.kh_fields(L) if fields is None else fields
+    s.init(*fields)
+    t = time_device(s, steps, warmup, torch, barrier)
+    st = s.check()
+    s.close()
+    q = len(v) ** dim
+    return {"mlups": nx * ny * steps / t / 1e6, "ms_per_step": t / steps * 1e3,
+            "gbs_algorithmic": 2 * q * ELEM[prec] * nx * ny * steps / t / 1e9,
+            "status": "ok" if st == 0 else "diverged"}
+
+
+def cpu_oracle_sample(L, seconds=12.0, max_steps=50):
+    """Time the FP64 oracle as it stands on this host's cores on an L x L KH grid."""
+    import oracle as O
+    lat = O.Lattice(2, V5, OMEGA, L, L, theta0=THETA0)
+    f = lat.init(*I.kh_fields(L))
+    cores = O.max_threads()
+    f = lat.step(f)  # one untimed step (page-in)
+    n = 0
+    t0 = time.perf_counter()
+    while n < max_steps and time.perf_counter() - t0 < seconds:
+        f = lat.step(f)
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": L * L * n / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": "%dx%d D2Q25 KH, %d FP64 steps of the C oracle (OpenMP over rows)" % (L, L, n)}
+
+
+def end_to_end(torch, plbm, fields, L, args, local, barrier, dist, ws):
+    """Public-API job with pinned host buffers: init from host, K steps, moments to host."""
+    pinned = [torch.from_numpy(a).pin_memory() for a in fields]
+    host_fields = [p.numpy() for p in pinned]
+    outs = [torch.empty((L, L), dtype=torch.float64).pin_memory() for _ in range(4)]
+    host_outs = [o.numpy() for o in outs]
+    e2e_steps = args.steps
+    solver2 = plbm.Solver(2, V5, OMEGA, L, L, theta0=THETA0, prec=args.prec, device=local)
+    solver2.init(*host_fields)
+    solver2.step(args.warmup)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    solver2.init(*host_fields)
+    solver2.step(e2e_steps)
+    from paper_1402_5487_gb300.plbm import lib as _lib
+    ptrs = [o.ctypes.data for o in host_outs]
+    stt = _lib().plbm_moments(solver2.h, *ptrs, 0)
+    assert stt == 0
+    t_e2e = time.perf_counter() - t0
+    barrier()
+    solver2.close()
+    if dist is not None:
+        tt = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+    h2d = 4 * L * L * 8
+    d2h = 4 * L * L * 8
+    e2e = {"value": ws * L * L * e2e_steps / t_e2e / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps,
+           "job": "plbm_init from pinned host fields + %d steps + plbm_moments to pinned host" % e2e_steps}
+
+    return e2e
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=2048)
+    ap.add_argument("--prec", default="f32", choices=list(ELEM))
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    ws, rank, local = dist_env()
+    L = args.size
+    q = 25
+    metric = "D2Q25 MLUPS"
+    config = {"workload": "kh%d_d2q25_%s" % (L, args.prec),
+              "description": "Kelvin-Helmholtz double shear layer, D2Q25 {0,+-1,+-3}^2, %dx%d periodic, "
+                             "theta0=1, omega=1.3, %s populations" % (L, L, args.prec),
+              "grid": [L, L], "velocities": list(V5), "omega": OMEGA, "theta0": THETA0,
+              "l2": "inputs larger than L2 (2 population arrays of %.0f MB each)" % (
+                  q * ELEM[args.prec] * L * L / 1e6),
+              "parallelism": "replicas" if ws > 1 else "single-gpu"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        import oracle as O
+        lat = O.Lattice(2, V5, OMEGA, L, L, theta0=THETA0)
+        f = lat.init(*I.kh_fields(L))
+        for _ in range(args.warmup):
+            f = lat.step(f)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            f = lat.step(f)
+        dt = time.perf_counter() - t0
+        val = L * L * args.steps / dt / 1e6
+        cores = O.max_threads()
+        line = {"impl": "reference", "metric": metric, "value": val, "unit": "MLUPS", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": config,
+                "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                                 "sample": "%dx%d D2Q25 KH, %d timed FP64 steps of the C oracle" % (
+                                     L, L, args.steps)},
+                "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    import torch
+    from paper_1402_5487_gb300 import build, plbm
+    dist = None
+    if ws > 1:
+        import torch.distributed as td
+        td.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        dist = td
+    torch.cuda.set_device(local)
+    build.build()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    fields = I.kh_fields(L)
+    solver = plbm.Solver(2, V5, OMEGA, L, L, theta0=THETA0, prec=args.prec, device=local)
+    solver.init(*fields)
+    solver.step(args.warmup)
+    st = solver.stream
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    torch.cuda.synchronize()
+    barrier()
+    clocks.start()
+    time.sleep(0.3)
+    e0.record(st)
+    solver.step(args.steps)
+    e1.record(st)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    clock_info = clocks.stop()
+    barrier()
+    t = e0.elapsed_time(e1) * 1e-3
+    healthy = solver.check() == 0
+    solver.close()
+    t_max = t
+    if dist is not None:
+        tt = torch.tensor([t], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = ws * L * L * args.steps / t_max / 1e6
+    per_launch = t / args.steps
+    alg_bytes = 2 * q * ELEM[args.prec] * L * L
+    peak, peak_kind = read_peaks()
+    achieved = alg_bytes / per_launch / 1e9
+
+    # End to end through the public API with pinned host buffers.
+    e2e = None
+    if not args.no_e2e:
+        e2e = end_to_end(torch, plbm, fields, L, args, local, barrier, dist, ws)
+
+    variants = {}
+    if not args.no_variants and rank == 0:
+        for prec in ("f16dev", "bf16dev", "f64"):
+            if prec == args.prec:
+                continue
+            variants["kh%d_%s" % (L, prec)] = run_variant(torch, L, prec, 200, 10, lambda: None)
+        variants["kh512_f32"] = run_variant(torch, 512, "f32", 1000, 50, lambda: None)
+        variants["kh512_f64"] = run_variant(torch, 512, "f64", 200, 20, lambda: None)
+        left, right = (1.1, 0.0, 0.5), (1.0, 0.0, 0.5)
+        variants["shock1000_d1q5_f64"] = run_variant(
+            torch, 1000, "f64", 500, 20, lambda: None, dim=1, bc="fixed",
+            fields=I.shock_tube_fields(1000, left, right), theta0=0.5, omega=1.5, left=left, right=right)
+        base = value / ws
+        for k, vv in variants.items():
+            if k.startswith("kh%d_" % L):
+                vv["speedup_vs_f32"] = vv["mlups"] / base
+
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and ws == 1:
+        cpu = cpu_oracle_sample(L)
+
+    if rank == 0:
+        line = {"metric": metric, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
+                "config": config, "healthy": healthy,
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": None,
+                             "peak_source": peak_kind,
+                             "algorithmic_bytes_per_launch": alg_bytes,
+                             "kernel": "k_stream_collide<float,5,2>"},
+                "e2e": e2e, "gpu_launches": args.steps, "clocks": clock_info,
+                "cpu_baseline": cpu, "variants": variants}
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,197 @@
+/*
+ * plbm.h - C ABI of the GB300 (sm_103a) parametric lattice Boltzmann solver.
+ *
+ * Method: J. W. Shim, "Parametric Lattice Boltzmann Method" (arXiv:1402.5487).
+ *   f^eq_i = rho r_i                                  (Eq. eq:eqdist)
+ *   r_i    = sum_{j=1}^{q} c_ij mu_{j-1}              (Eq. eq:rdr)
+ *   c_ij   = coefficient of v^{j-1} in the Lagrange polynomial through
+ *            (v_k, delta_ik); C = V^{-1}, V_{n,k} = v_k^n   (Appendix)
+ *   mu_n   = n-th moment of the Maxwell-Boltzmann distribution (Appendix)
+ *   2D     : tensor product of 1D rules (Sec. 2.1)
+ *   step   : f_i(x + v_i, t + 1) = (1 - omega) f_i(x, t) + omega f^eq_i(x, t)
+ *            (Eq. eq:srt, lattice units dx = dt = 1)
+ *
+ * Conventions shared by every call:
+ *   - Lattice units.  Velocities are integers (on-lattice sets, Sec. 2.4).
+ *   - Field arrays are FP64, row-major [ny][nx] (ny = 1 in 1D).
+ *   - Population arrays at the boundary are FP64 [q][ny][nx], q = q1^dim,
+ *     population p = ix*q1 + iy has velocity (v[ix], v[iy]) in 2D, p = ix in 1D.
+ *   - The stored state is the post-collision state; a step is "pull-stream,
+ *     then collide", which yields the same sequence of states as Eq. (eq:srt).
+ *   - Moments: rho = sum f, rho u = sum v f, d rho theta = sum |v - u|^2 f.
+ *   - The caller owns every array it passes.  The handle owns its device
+ *     populations unless a workspace was supplied in the descriptor.
+ *   - Calls are asynchronous on the handle's stream, except those that return
+ *     host data or a status read from the device (documented per call).
+ *   - Every call returns a plbm_status.  Errors are sticky per handle: after
+ *     PLBM_E_DIVERGED or PLBM_E_CUDA only plbm_destroy, plbm_get_populations,
+ *     plbm_last_error and plbm_diagnostics are accepted.
+ *   - Thread safety: a handle must not be used from two threads at once.
+ *   - No call falls back to the CPU: without a usable CUDA device,
+ *     plbm_create returns PLBM_E_CUDA.
+ */
+#ifndef PLBM_H
+#define PLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PLBM_ABI_VERSION 1
+#define PLBM_MAX_Q1 8
+
+typedef struct plbm_s *plbm_handle;
+
+typedef enum {
+    PLBM_OK = 0,
+    PLBM_E_ARG = -1,           /* invalid argument or descriptor */
+    PLBM_E_CUDA = -2,          /* a CUDA runtime call failed */
+    PLBM_E_INADMISSIBLE = -3,  /* r_i < 0 for the requested state (Sec. 3.1) */
+    PLBM_E_DIVERGED = -4,      /* non-finite, rho <= 0 or theta <= 0 seen on the device */
+    PLBM_E_TIMEOUT = -5,       /* a bounded device-side wait ran out */
+    PLBM_E_STATE = -6,         /* call not valid in the handle's state */
+    PLBM_E_CHECKSUM = -7,      /* checkpoint checksum or header mismatch */
+    PLBM_E_NOMEM = -8          /* device allocation failed or workspace too small */
+} plbm_status;
+
+/* Storage precision of the populations.  F64 stores f itself and does the
+ * arithmetic in FP64.  F32, F16DEV and BF16DEV store the deviation
+ * g = f - w0 from the rest equilibrium w0 = f^eq(rho = 1, u = 0, theta0) in
+ * 32 or 16 bits and do the arithmetic in FP32. */
+typedef enum { PLBM_F64 = 0, PLBM_F32 = 1, PLBM_F16DEV = 2, PLBM_BF16DEV = 3 } plbm_prec;
+
+/* PERIODIC: periodic in every direction.  FIXED_ENDS: nodes left of x = 0 and
+ * right of x = nx-1 hold f^eq(left_state) and f^eq(right_state) for ever (the
+ * shock-tube ends "maintained by C_L and C_R", Sec. 3.2); y stays periodic. */
+typedef enum { PLBM_PERIODIC = 0, PLBM_FIXED_ENDS = 1 } plbm_bc;
+
+/* Descriptor flags. */
+#define PLBM_FLAG_ISOTHERMAL 0x1u      /* theta in f^eq held at theta0 (Eq. eq:1d3v models) */
+#define PLBM_FLAG_SKIP_ADMISSIBILITY 0x2u /* do not run the positivity gate at create */
+
+typedef struct {
+    int dim;                   /* 1 or 2 */
+    int q1;                    /* velocities per axis: 3, 4 or 5 (D1Q3..D1Q5, D2Q9..D2Q25) */
+    const int *v;              /* q1 distinct integer velocities (copied at create) */
+    double omega;              /* BGK relaxation constant, 0 < omega < 2 */
+    double theta0;             /* reference temperature (rest state, isothermal models) */
+    int nx, ny;                /* grid; ny must be 1 when dim == 1 */
+    plbm_prec prec;
+    plbm_bc bc;
+    const double *left_state;  /* (rho, u, theta) at the left end, FIXED_ENDS only */
+    const double *right_state; /* (rho, u, theta) at the right end, FIXED_ENDS only */
+    void *stream;              /* cudaStream_t for every launch; NULL = default stream */
+    unsigned flags;            /* PLBM_FLAG_* */
+    int check_every;           /* plbm_step reads the device status every this many
+                                  steps and at its end (0 = never inside plbm_step) */
+    double u_max;              /* positivity gate: r_i >= 0 required for |u| <= u_max
+                                  at theta0 (0 = check the rest state only) */
+    void *workspace;           /* optional caller-owned device memory of at least
+                                  plbm_workspace_bytes(desc) bytes, 256-byte aligned;
+                                  NULL = the handle allocates its own */
+    size_t workspace_bytes;
+    int device;                /* CUDA device ordinal */
+} plbm_desc;
+
+/* Global diagnostics of the stored state, all accumulated in FP64. */
+typedef struct {
+    double mass;      /* sum over nodes of rho */
+    double jx, jy;    /* sum of rho u */
+    double energy;    /* sum of sum_p |v_p|^2 f_p  (= sum of d rho theta + rho |u|^2) */
+    double rho_min, theta_min;
+    uint32_t status;  /* PLBM_STATUS_* bits seen since create */
+    int64_t steps;    /* steps taken since create (or since the last set_populations) */
+} plbm_diag;
+
+#define PLBM_STATUS_NONFINITE 0x1u
+#define PLBM_STATUS_RHO_NONPOS 0x2u
+#define PLBM_STATUS_THETA_NONPOS 0x4u
+
+/* Library and ABI version; never fails. */
+int plbm_abi_version(void);
+
+/* Coefficients c_ij of Eq. (eq:rdr) for a velocity set, in FP64, computed on
+ * the host by expanding the Lagrange polynomials of the Appendix
+ * (C = V^{-1}).  C_out: q1*q1 doubles, C_out[i*q1 + n] multiplies mu_n in r_i.
+ * Errors: PLBM_E_ARG for q1 out of range or repeated velocities. */
+plbm_status plbm_coefficients(int q1, const int *v, double *C_out);
+
+/* Device bytes a handle with this descriptor needs (two population arrays,
+ * reduction scratch, status words).  Returns 0 for an invalid descriptor. */
+size_t plbm_workspace_bytes(const plbm_desc *desc);
+
+/* Create a solver (Secs. 2-4).  Validates the descriptor, computes c_ij in FP64
+ * on the host, runs the positivity gate of Sec. 3.1 (every r_i(u, theta0) >= 0
+ * for |u| <= desc->u_max along each axis, unless PLBM_FLAG_SKIP_ADMISSIBILITY),
+ * and allocates or adopts device memory.  Populations are undefined until
+ * plbm_init or plbm_set_populations.  Synchronous.
+ * Errors: PLBM_E_ARG, PLBM_E_INADMISSIBLE, PLBM_E_NOMEM, PLBM_E_CUDA; *out is
+ * NULL on error and the reason is available from plbm_last_error(NULL). */
+plbm_status plbm_create(const plbm_desc *desc, plbm_handle *out);
+
+/* Release the handle and the memory it owns.  Accepts NULL.  Synchronises the
+ * handle's stream. */
+plbm_status plbm_destroy(plbm_handle h);
+
+/* Initial state f = f^eq(rho, u, theta) at every node (Eq. eq:eqdist), computed
+ * in FP64 on the device and stored in the handle's precision.  Fields: FP64
+ * [ny][nx]; uy may be NULL in 1D; theta may be NULL for isothermal handles.
+ * on_device != 0: the pointers are device memory, read on the handle's stream
+ * (asynchronous); otherwise host memory, copied before return.  Resets the
+ * step counter and the status word. */
+plbm_status plbm_init(plbm_handle h, const double *rho, const double *ux, const double *uy,
+                      const double *theta, int on_device);
+
+/* Advance n >= 0 steps of Eq. (eq:srt) (pull-stream + BGK collision of the
+ * equilibrium of Eq. eq:rdr).  Asynchronous unless check_every > 0, in which
+ * case the device status is read (with a stream synchronisation) every
+ * check_every steps and at the end; a set status returns PLBM_E_DIVERGED. */
+plbm_status plbm_step(plbm_handle h, long n);
+
+/* Read the device status word (synchronises the stream).  Returns
+ * PLBM_E_DIVERGED if any PLBM_STATUS_* bit has been set. */
+plbm_status plbm_check(plbm_handle h);
+
+/* Macroscopic fields of the stored state: rho, u_x, u_y, theta as FP64
+ * [ny][nx] (uy may be NULL).  on_device != 0: device pointers, asynchronous;
+ * otherwise host pointers, synchronous. */
+plbm_status plbm_moments(plbm_handle h, double *rho, double *ux, double *uy, double *theta,
+                         int on_device);
+
+/* Global FP64 sums and extrema of the stored state plus the status word.
+ * Synchronous. */
+plbm_status plbm_diagnostics(plbm_handle h, plbm_diag *out);
+
+/* Conserved sums out[4] = (mass, jx, jy, energy) of the stored state, FP64.
+ * Synchronous. */
+plbm_status plbm_conserved(plbm_handle h, double out[4]);
+
+/* Populations as FP64 [q][ny][nx] (for F16DEV/BF16DEV: w0 + g).  on_device as
+ * in plbm_moments. */
+plbm_status plbm_get_populations(plbm_handle h, double *f, int on_device);
+
+/* Replace the stored state with FP64 populations [q][ny][nx], rounded to the
+ * handle's precision.  Resets the step counter to `step`. */
+plbm_status plbm_set_populations(plbm_handle h, const double *f, int on_device, int64_t step);
+
+/* Descriptor facts of a live handle. */
+plbm_status plbm_get_info(plbm_handle h, int *q, int *pitch, size_t *population_bytes);
+
+/* Raw device pointer of the current population array (storage layout
+ * [q][ny][pitch] in the handle's precision).  For profiling and tests. */
+plbm_status plbm_device_populations(plbm_handle h, void **ptr);
+
+/* Text of the last error of h (or of the calling thread when h is NULL). */
+const char *plbm_last_error(plbm_handle h);
+
+/* Name of a status code. */
+const char *plbm_status_string(plbm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PLBM_H */

@@ -1,0 +1,236 @@
+// Non-hot kernels of libplbm: initial equilibrium, moments of the stored state,
+// deterministic FP64 reductions and population import/export.  All arithmetic
+// here is FP64 regardless of the storage precision.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "plbm_device.cuh"
+
+namespace plbm {
+
+cudaError_t launch_step_f64(const LatticeParams&, const void*, void*, bool, cudaStream_t);
+cudaError_t launch_step_f32(const LatticeParams&, const void*, void*, bool, cudaStream_t);
+cudaError_t launch_step_f16(const LatticeParams&, const void*, void*, bool, cudaStream_t);
+cudaError_t launch_step_bf16(const LatticeParams&, const void*, void*, bool, cudaStream_t);
+
+cudaError_t launch_step(int prec, const LatticeParams& P, const void* src, void* dst, bool reduce,
+                        cudaStream_t stream) {
+    switch (prec) {
+        case kF64: return launch_step_f64(P, src, dst, reduce, stream);
+        case kF32: return launch_step_f32(P, src, dst, reduce, stream);
+        case kF16Dev: return launch_step_f16(P, src, dst, reduce, stream);
+        case kBF16Dev: return launch_step_bf16(P, src, dst, reduce, stream);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// FP64 equilibrium of one node, Eq. (eq:eqdist) with Eq. (eq:rdr) per axis and
+// the tensor product of Sec. 2.1.  out[p], p = ix*q1 + iy.
+__device__ void node_feq_f64(const LatticeParams& P, double rho, double ux, double uy, double th,
+                             double* out) {
+    double rx[kMaxQ1], ry[kMaxQ1], mu[kMaxQ1];
+    const int q1 = P.q1;
+    for (int a = 0; a < P.dim; ++a) {
+        const double u = (a == 0) ? ux : uy;
+        mu[0] = 1.0;
+        mu[1] = u;
+        for (int n = 1; n + 1 < q1; ++n) mu[n + 1] = u * mu[n] + (double)n * th * mu[n - 1];
+        for (int i = 0; i < q1; ++i) {
+            double r = 0.0;
+            for (int n = 0; n < q1; ++n) r += P.C[i * q1 + n] * mu[n];
+            if (a == 0) rx[i] = r; else ry[i] = r;
+        }
+    }
+    if (P.dim == 1) {
+        for (int i = 0; i < q1; ++i) out[i] = rho * rx[i];
+    } else {
+        for (int i = 0; i < q1; ++i)
+            for (int j = 0; j < q1; ++j) out[i * q1 + j] = rho * rx[i] * ry[j];
+    }
+}
+
+// Moments of one node from FP64 populations.
+__device__ void node_moments_f64(const LatticeParams& P, const double* f, double& rho, double& ux,
+                                 double& uy, double& th, double& e, double& jx_o, double& jy_o) {
+    double r = 0.0, jx = 0.0, jy = 0.0, en = 0.0;
+    for (int p = 0; p < P.q; ++p) {
+        const int ix = (P.dim == 1) ? p : p / P.q1;
+        const int iy = (P.dim == 1) ? 0 : p % P.q1;
+        const double vx = (double)P.v[ix];
+        const double vy = (P.dim == 1) ? 0.0 : (double)P.v[iy];
+        r += f[p];
+        jx += vx * f[p];
+        jy += vy * f[p];
+        en += (vx * vx + vy * vy) * f[p];
+    }
+    rho = r;
+    ux = jx / r;
+    uy = jy / r;
+    th = (en / r - (ux * ux + uy * uy)) / (double)P.dim;
+    e = en;
+    jx_o = jx;
+    jy_o = jy;
+}
+
+template <typename S>
+__global__ void k_init(const __grid_constant__ LatticeParams P, const double* __restrict__ rho,
+                       const double* __restrict__ ux, const double* __restrict__ uy,
+                       const double* __restrict__ theta, S* __restrict__ f) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= P.nx) return;
+    const long long n = (long long)y * P.nx + x;
+    const double th = (P.isothermal || theta == nullptr) ? P.theta0 : theta[n];
+    double feq[kMaxQ];
+    node_feq_f64(P, rho[n], ux[n], (P.dim == 2 && uy) ? uy[n] : 0.0, th, feq);
+    for (int p = 0; p < P.q; ++p) f[elem_index(P, p, x, y)] = Storage<S>::from_f64(feq[p], P.W0[p]);
+}
+
+template <typename S>
+__global__ void k_moments(const __grid_constant__ LatticeParams P, const S* __restrict__ f,
+                          double* rho, double* ux, double* uy, double* theta) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= P.nx) return;
+    double fn[kMaxQ];
+    for (int p = 0; p < P.q; ++p) fn[p] = Storage<S>::to_f64(f[elem_index(P, p, x, y)], P.W0[p]);
+    double r, a, b, t, e, jx, jy;
+    node_moments_f64(P, fn, r, a, b, t, e, jx, jy);
+    const long long n = (long long)y * P.nx + x;
+    if (rho) rho[n] = r;
+    if (ux) ux[n] = a;
+    if (uy) uy[n] = b;
+    if (theta) theta[n] = t;
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kBlockX) k_reduce_state(const __grid_constant__ LatticeParams P,
+                                                          const S* __restrict__ f) {
+    const int x = blockIdx.x * kBlockX + threadIdx.x;
+    const int y = blockIdx.y;
+    NodeDiag d;
+    diag_zero(d);
+    if (x < P.nx) {
+        double fn[kMaxQ];
+        for (int p = 0; p < P.q; ++p) fn[p] = Storage<S>::to_f64(f[elem_index(P, p, x, y)], P.W0[p]);
+        double r, a, b, t, e, jx, jy;
+        node_moments_f64(P, fn, r, a, b, t, e, jx, jy);
+        d.mass = r;
+        d.jx = jx;
+        d.jy = jy;
+        d.energy = e;
+        d.rho_min = r;
+        d.theta_min = t;
+        flag_status<double>(P, r, t);
+    }
+    const int blk = blockIdx.y * gridDim.x + blockIdx.x;
+    block_reduce_diag<kBlockX>(d, P.partials + (long long)blk * kPartialStride);
+}
+
+// One block of kFinalThreads threads sums the per-block partials in a fixed
+// order, so the result is bit-reproducible for a given lattice.
+constexpr int kFinalThreads = 512;
+__global__ void __launch_bounds__(kFinalThreads) k_finalize(const double* __restrict__ partials,
+                                                            int nblocks, double* __restrict__ out) {
+    __shared__ double sh[6][kFinalThreads];
+    double r[6] = {0, 0, 0, 0, 1e300, 1e300};
+    for (int b = threadIdx.x; b < nblocks; b += kFinalThreads) {
+        const double* q = partials + (long long)b * kPartialStride;
+        r[0] += q[0];
+        r[1] += q[1];
+        r[2] += q[2];
+        r[3] += q[3];
+        r[4] = fmin(r[4], q[4]);
+        r[5] = fmin(r[5], q[5]);
+    }
+    for (int k = 0; k < 6; ++k) sh[k][threadIdx.x] = r[k];
+    __syncthreads();
+    for (int s = kFinalThreads / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + s];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + s];
+            sh[2][threadIdx.x] += sh[2][threadIdx.x + s];
+            sh[3][threadIdx.x] += sh[3][threadIdx.x + s];
+            sh[4][threadIdx.x] = fmin(sh[4][threadIdx.x], sh[4][threadIdx.x + s]);
+            sh[5][threadIdx.x] = fmin(sh[5][threadIdx.x], sh[5][threadIdx.x + s]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 6) out[threadIdx.x] = sh[threadIdx.x][0];
+}
+
+template <typename S>
+__global__ void k_get_pop(const __grid_constant__ LatticeParams P, const S* __restrict__ f,
+                          double* __restrict__ out) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    const int p = blockIdx.z;
+    if (x >= P.nx) return;
+    const double v = Storage<S>::to_f64(f[elem_index(P, p, x, y)], P.W0[p]);
+    out[((long long)p * P.ny + y) * P.nx + x] = v;
+}
+
+template <typename S>
+__global__ void k_set_pop(const __grid_constant__ LatticeParams P, const double* __restrict__ in,
+                          S* __restrict__ f) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    const int p = blockIdx.z;
+    if (x >= P.nx) return;
+    f[elem_index(P, p, x, y)] = Storage<S>::from_f64(in[((long long)p * P.ny + y) * P.nx + x], P.W0[p]);
+}
+
+#define PLBM_DISPATCH(prec, CALL)                                        \
+    switch (prec) {                                                      \
+        case kF64: { using S = double; CALL; break; }                    \
+        case kF32: { using S = float; CALL; break; }                     \
+        case kF16Dev: { using S = __half; CALL; break; }                 \
+        case kBF16Dev: { using S = __nv_bfloat16; CALL; break; }         \
+        default: return cudaErrorInvalidValue;                           \
+    }
+
+cudaError_t launch_init(int prec, const LatticeParams& P, const double* rho, const double* ux,
+                        const double* uy, const double* theta, void* f, cudaStream_t stream) {
+    dim3 grid((P.nx + 127) / 128, P.ny);
+    PLBM_DISPATCH(prec, (k_init<S><<<grid, 128, 0, stream>>>(P, rho, ux, uy, theta,
+                                                             static_cast<S*>(f))));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments(int prec, const LatticeParams& P, const void* f, double* rho,
+                           double* ux, double* uy, double* theta, cudaStream_t stream) {
+    dim3 grid((P.nx + 127) / 128, P.ny);
+    PLBM_DISPATCH(prec, (k_moments<S><<<grid, 128, 0, stream>>>(P, static_cast<const S*>(f), rho,
+                                                                ux, uy, theta)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const LatticeParams& P, int nblocks, double* out, cudaStream_t stream) {
+    k_finalize<<<1, kFinalThreads, 0, stream>>>(P.partials, nblocks, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_state(int prec, const LatticeParams& P, const void* f, double* out,
+                                cudaStream_t stream) {
+    dim3 grid((P.nx + kBlockX - 1) / kBlockX, P.ny);
+    PLBM_DISPATCH(prec, (k_reduce_state<S><<<grid, kBlockX, 0, stream>>>(P, static_cast<const S*>(f))));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_finalize(P, reduce_blocks(P), out, stream);
+}
+
+cudaError_t launch_get_populations(int prec, const LatticeParams& P, const void* f, double* out,
+                                   cudaStream_t stream) {
+    dim3 grid((P.nx + 127) / 128, P.ny, P.q);
+    PLBM_DISPATCH(prec, (k_get_pop<S><<<grid, 128, 0, stream>>>(P, static_cast<const S*>(f), out)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_populations(int prec, const LatticeParams& P, const double* in, void* f,
+                                   cudaStream_t stream) {
+    dim3 grid((P.nx + 127) / 128, P.ny, P.q);
+    PLBM_DISPATCH(prec, (k_set_pop<S><<<grid, 128, 0, stream>>>(P, in, static_cast<S*>(f))));
+    return cudaGetLastError();
+}
+
+}  // namespace plbm

@@ -1,0 +1,626 @@
+// Host side of libplbm: descriptor validation, FP64 coefficients, the
+// positivity gate, device memory and the extern "C" entry points of plbm.h.
+#include "plbm.h"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "plbm_internal.h"
+
+using plbm::LatticeParams;
+
+namespace {
+
+thread_local char g_thread_error[512] = "";
+
+struct Handle {
+    plbm_desc desc{};
+    int v[plbm::kMaxQ1]{};
+    LatticeParams P{};
+    int prec = 0;
+    size_t elem = 0;
+    size_t pop_bytes = 0;      // one population array
+    size_t ws_bytes = 0;
+    char* ws = nullptr;        // device workspace base
+    bool owns_ws = false;
+    void* f[2] = {nullptr, nullptr};
+    int cur = 0;
+    double* partials = nullptr;
+    double* result = nullptr;  // 8 doubles on the device
+    unsigned* status = nullptr;
+    double* host_buf = nullptr; // pinned: 8 result doubles + status word
+    cudaStream_t stream = nullptr;
+    long long steps = 0;
+    plbm_status sticky = PLBM_OK;
+    bool initialised = false;
+    char err[512] = "";
+};
+
+void set_err(Handle* h, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    std::snprintf(g_thread_error, sizeof g_thread_error, "%s", buf);
+    if (h) std::snprintf(h->err, sizeof h->err, "%s", buf);
+}
+
+size_t align_up(size_t n, size_t a) { return (n + a - 1) / a * a; }
+
+size_t elem_size(int prec) {
+    switch (prec) {
+        case PLBM_F64: return 8;
+        case PLBM_F32: return 4;
+        case PLBM_F16DEV:
+        case PLBM_BF16DEV: return 2;
+    }
+    return 0;
+}
+
+// Coefficients of Eq. (eq:rdr): row i holds the monomial coefficients of the
+// Lagrange polynomial L_i(v) = prod_{j != i} (v - v_j) / prod_{j != i} (v_i - v_j),
+// i.e. C = V^{-1} of the Appendix.  The numerator is expanded factor by factor.
+bool lagrange_coefficients(int q1, const int* v, double* C) {
+    for (int i = 0; i < q1; ++i) {
+        double poly[plbm::kMaxQ1 + 1] = {1.0};
+        int deg = 0;
+        double den = 1.0;
+        for (int j = 0; j < q1; ++j) {
+            if (j == i) continue;
+            if (v[j] == v[i]) return false;
+            // poly <- poly * (v - v_j)
+            for (int k = deg + 1; k >= 1; --k) poly[k] = poly[k - 1] - (double)v[j] * poly[k];
+            poly[0] = -(double)v[j] * poly[0];
+            ++deg;
+            den *= (double)(v[i] - v[j]);
+        }
+        for (int n = 0; n < q1; ++n) C[i * q1 + n] = poly[n] / den;
+    }
+    return true;
+}
+
+// Maxwell-Boltzmann raw moments mu_0..mu_{q1-1} (Gaussian, mean u, variance theta).
+void mb_moments(double u, double theta, int q1, double* mu) {
+    mu[0] = 1.0;
+    if (q1 > 1) mu[1] = u;
+    for (int n = 1; n + 1 < q1; ++n) mu[n + 1] = u * mu[n] + n * theta * mu[n - 1];
+}
+
+void rule_1d(int q1, const double* C, double u, double theta, double* r) {
+    double mu[plbm::kMaxQ1];
+    mb_moments(u, theta, q1, mu);
+    for (int i = 0; i < q1; ++i) {
+        double s = 0.0;
+        for (int n = 0; n < q1; ++n) s += C[i * q1 + n] * mu[n];
+        r[i] = s;
+    }
+}
+
+void feq_host(int dim, int q1, const double* C, double rho, double ux, double uy, double th,
+              double* out) {
+    double rx[plbm::kMaxQ1], ry[plbm::kMaxQ1];
+    rule_1d(q1, C, ux, th, rx);
+    if (dim == 1) {
+        for (int i = 0; i < q1; ++i) out[i] = rho * rx[i];
+        return;
+    }
+    rule_1d(q1, C, uy, th, ry);
+    for (int i = 0; i < q1; ++i)
+        for (int j = 0; j < q1; ++j) out[i * q1 + j] = rho * rx[i] * ry[j];
+}
+
+bool finite_pos(double a) { return std::isfinite(a) && a > 0.0; }
+
+plbm_status validate(const plbm_desc* d, Handle* h) {
+    if (!d) { set_err(h, "descriptor is NULL"); return PLBM_E_ARG; }
+    if (d->dim != 1 && d->dim != 2) { set_err(h, "dim must be 1 or 2 (got %d)", d->dim); return PLBM_E_ARG; }
+    if (d->q1 < 3 || d->q1 > 5) {
+        set_err(h, "q1 must be 3, 4 or 5 (got %d)", d->q1);
+        return PLBM_E_ARG;
+    }
+    if (!d->v) { set_err(h, "velocity array is NULL"); return PLBM_E_ARG; }
+    for (int i = 0; i < d->q1; ++i) {
+        if (d->v[i] < -64 || d->v[i] > 64) { set_err(h, "|v| must be <= 64"); return PLBM_E_ARG; }
+        for (int j = 0; j < i; ++j)
+            if (d->v[i] == d->v[j]) { set_err(h, "velocities must be distinct"); return PLBM_E_ARG; }
+    }
+    if (!(d->omega >= 0.0 && d->omega < 2.0)) {
+        set_err(h, "omega must lie in [0, 2) (got %g)", d->omega);
+        return PLBM_E_ARG;
+    }
+    if (!finite_pos(d->theta0)) { set_err(h, "theta0 must be finite and > 0"); return PLBM_E_ARG; }
+    if (d->nx < 1 || d->ny < 1) { set_err(h, "nx, ny must be >= 1"); return PLBM_E_ARG; }
+    if (d->dim == 1 && d->ny != 1) { set_err(h, "ny must be 1 in 1D"); return PLBM_E_ARG; }
+    if (d->ny > 65535) { set_err(h, "ny must be <= 65535"); return PLBM_E_ARG; }
+    if ((long long)d->nx * d->ny > (1LL << 31)) { set_err(h, "grid too large"); return PLBM_E_ARG; }
+    if (elem_size(d->prec) == 0) { set_err(h, "unknown precision %d", (int)d->prec); return PLBM_E_ARG; }
+    if (d->bc != PLBM_PERIODIC && d->bc != PLBM_FIXED_ENDS) { set_err(h, "unknown boundary"); return PLBM_E_ARG; }
+    if (d->bc == PLBM_FIXED_ENDS) {
+        if (!d->left_state || !d->right_state) { set_err(h, "fixed ends need both end states"); return PLBM_E_ARG; }
+        for (const double* s : {d->left_state, d->right_state}) {
+            if (!finite_pos(s[0]) || !std::isfinite(s[1]) || !finite_pos(s[2])) {
+                set_err(h, "end states need rho > 0, finite u, theta > 0");
+                return PLBM_E_ARG;
+            }
+        }
+    }
+    if (d->check_every < 0) { set_err(h, "check_every must be >= 0"); return PLBM_E_ARG; }
+    if (!(d->u_max >= 0.0) || !std::isfinite(d->u_max)) { set_err(h, "u_max must be >= 0"); return PLBM_E_ARG; }
+    if (d->workspace && (reinterpret_cast<uintptr_t>(d->workspace) & 255u)) {
+        set_err(h, "workspace must be 256-byte aligned");
+        return PLBM_E_ARG;
+    }
+    return PLBM_OK;
+}
+
+struct Layout {
+    int pitch;
+    size_t pop_bytes, partial_off, result_off, status_off, total;
+    int nblocks;
+};
+
+Layout layout_of(const plbm_desc* d) {
+    Layout L{};
+    L.pitch = (int)align_up((size_t)d->nx, plbm::kPitchAlign);
+    const int q = d->dim == 1 ? d->q1 : d->q1 * d->q1;
+    L.pop_bytes = align_up((size_t)q * d->ny * L.pitch * elem_size(d->prec), 256);
+    L.nblocks = ((d->nx + plbm::kBlockX - 1) / plbm::kBlockX) * d->ny;
+    L.partial_off = 2 * L.pop_bytes;
+    L.result_off = L.partial_off + align_up((size_t)L.nblocks * plbm::kPartialStride * sizeof(double), 256);
+    L.status_off = L.result_off + 256;
+    L.total = L.status_off + 256;
+    return L;
+}
+
+// Positivity gate of Sec. 3.1: every r_i(u, theta0) >= 0 for |u| <= u_max.
+bool admissible(int q1, const double* C, double theta0, double u_max, double* worst_u, double* worst_r) {
+    const int n = u_max > 0.0 ? 401 : 1;
+    double r[plbm::kMaxQ1];
+    *worst_r = 1e300;
+    for (int k = 0; k < n; ++k) {
+        const double u = (n == 1) ? 0.0 : -u_max + 2.0 * u_max * k / (n - 1);
+        rule_1d(q1, C, u, theta0, r);
+        for (int i = 0; i < q1; ++i) {
+            if (r[i] < *worst_r) { *worst_r = r[i]; *worst_u = u; }
+        }
+    }
+    return *worst_r >= -1e-14;
+}
+
+#define CK(call)                                                                       \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            set_err(h, "%s failed: %s", #call, cudaGetErrorString(e_));                \
+            if (h) h->sticky = PLBM_E_CUDA;                                            \
+            return PLBM_E_CUDA;                                                        \
+        }                                                                              \
+    } while (0)
+
+plbm_status usable(Handle* h, bool need_init = true) {
+    if (!h) { set_err(nullptr, "handle is NULL"); return PLBM_E_ARG; }
+    if (h->sticky != PLBM_OK) {
+        set_err(h, "handle is in error state %d: %s", (int)h->sticky, h->err);
+        return h->sticky;
+    }
+    if (need_init && !h->initialised) { set_err(h, "populations not initialised"); return PLBM_E_STATE; }
+    if (cudaSetDevice(h->desc.device) != cudaSuccess) { set_err(h, "cudaSetDevice failed"); return PLBM_E_CUDA; }
+    return PLBM_OK;
+}
+
+void free_handle(Handle* h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    if (h->owns_ws && h->ws) cudaFree(h->ws);
+    if (h->host_buf) cudaFreeHost(h->host_buf);
+    delete h;
+}
+
+plbm_status read_status(Handle* h, unsigned* bits) {
+    CK(cudaMemcpyAsync(h->host_buf + 8, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    std::memcpy(bits, h->host_buf + 8, sizeof(unsigned));
+    return PLBM_OK;
+}
+
+// Temporary device buffer for host<->device staging, stream-ordered.
+struct Staging {
+    void* p = nullptr;
+    cudaStream_t s = nullptr;
+    ~Staging() { if (p) cudaFreeAsync(p, s); }
+};
+
+}  // namespace
+
+extern "C" {
+
+int plbm_abi_version(void) { return PLBM_ABI_VERSION; }
+
+plbm_status plbm_coefficients(int q1, const int* v, double* C_out) {
+    if (q1 < 2 || q1 > PLBM_MAX_Q1 || !v || !C_out) { set_err(nullptr, "bad arguments"); return PLBM_E_ARG; }
+    if (!lagrange_coefficients(q1, v, C_out)) { set_err(nullptr, "velocities must be distinct"); return PLBM_E_ARG; }
+    return PLBM_OK;
+}
+
+size_t plbm_workspace_bytes(const plbm_desc* desc) {
+    if (validate(desc, nullptr) != PLBM_OK) return 0;
+    return layout_of(desc).total;
+}
+
+plbm_status plbm_create(const plbm_desc* desc, plbm_handle* out) {
+    if (!out) { set_err(nullptr, "out is NULL"); return PLBM_E_ARG; }
+    *out = nullptr;
+    plbm_status st = validate(desc, nullptr);
+    if (st != PLBM_OK) return st;
+    Handle* h = new (std::nothrow) Handle();
+    if (!h) { set_err(nullptr, "host allocation failed"); return PLBM_E_NOMEM; }
+    h->desc = *desc;
+    std::memcpy(h->v, desc->v, sizeof(int) * desc->q1);
+    h->desc.v = h->v;
+    h->desc.left_state = nullptr;
+    h->desc.right_state = nullptr;
+    h->stream = static_cast<cudaStream_t>(desc->stream);
+    h->prec = (int)desc->prec;
+    h->elem = elem_size(desc->prec);
+
+    LatticeParams& P = h->P;
+    std::memset(&P, 0, sizeof P);
+    const int q1 = desc->q1, dim = desc->dim;
+    P.nx = desc->nx;
+    P.ny = desc->ny;
+    P.dim = dim;
+    P.q1 = q1;
+    P.q = dim == 1 ? q1 : q1 * q1;
+    P.fixed_ends = desc->bc == PLBM_FIXED_ENDS;
+    P.isothermal = (desc->flags & PLBM_FLAG_ISOTHERMAL) ? 1 : 0;
+    P.omega = desc->omega;
+    P.theta0 = desc->theta0;
+    P.omegaf = (float)desc->omega;
+    P.theta0f = (float)desc->theta0;
+    for (int i = 0; i < q1; ++i) {
+        P.v[i] = desc->v[i];
+        P.vxm[i] = ((-desc->v[i]) % P.nx + P.nx) % P.nx;
+        P.vym[i] = ((-desc->v[i]) % P.ny + P.ny) % P.ny;
+    }
+    if (!lagrange_coefficients(q1, desc->v, P.C)) {
+        set_err(nullptr, "velocities must be distinct");
+        delete h;
+        return PLBM_E_ARG;
+    }
+    for (int k = 0; k < q1 * q1; ++k) {
+        P.Cf[k] = (float)P.C[k];
+        P.Cf_lo[k] = (float)(P.C[k] - (double)P.Cf[k]);
+    }
+    const int* v = desc->v;
+    P.sym5 = (q1 == 5 && v[0] == 0 && v[1] > 0 && v[2] == -v[1] && v[3] > 0 && v[4] == -v[3] &&
+              v[1] != v[3]) ? 1 : 0;
+    if (P.sym5) {
+        const double a = v[1], b = v[3];
+        P.sa = (float)a;
+        P.sb = (float)b;
+        P.sa2 = (float)(a * a);
+        P.sb2 = (float)(b * b);
+        P.kOa = (float)(1.0 / (2.0 * a));
+        P.kOb = (float)(1.0 / (2.0 * b * (b * b - a * a)));
+        P.kEa = (float)(1.0 / (2.0 * a * a));
+        P.kEb = (float)(1.0 / (2.0 * b * b * (b * b - a * a)));
+    }
+    // Row-paired layout and the two-nodes-per-thread kernel: 2D periodic symmetric
+    // five-velocity thermal lattices with an even number of rows, 16/32-bit storage.
+    P.paired = (dim == 2 && desc->ny % 2 == 0 && desc->prec != PLBM_F64 && P.sym5 && !P.isothermal &&
+                desc->bc == PLBM_PERIODIC) ? 1 : 0;
+    P.half_ny = P.paired ? desc->ny / 2 : 0;
+
+    if (!(desc->flags & PLBM_FLAG_SKIP_ADMISSIBILITY)) {
+        double wu = 0, wr = 0;
+        if (!admissible(q1, P.C, desc->theta0, desc->u_max, &wu, &wr)) {
+            set_err(nullptr,
+                    "inadmissible: r_i(u=%g, theta0=%g) = %g < 0 (positivity range of Sec. 3.1)",
+                    wu, desc->theta0, wr);
+            delete h;
+            return PLBM_E_INADMISSIBLE;
+        }
+    }
+
+    // Rest equilibrium w0 = f^eq(1, 0, theta0) and the moments it reproduces.
+    double mu0[plbm::kMaxQ1];
+    mb_moments(0.0, desc->theta0, q1, mu0);
+    rule_1d(q1, P.C, 0.0, desc->theta0, P.w1);
+    for (int i = 0; i < q1; ++i) {
+        P.w1f[i] = (float)P.w1[i];
+        P.mu0f[i] = (float)mu0[i];
+    }
+    feq_host(dim, q1, P.C, 1.0, 0.0, 0.0, desc->theta0, P.W0);
+    for (int p = 0; p < P.q; ++p) P.W0f[p] = (float)P.W0[p];
+    if (P.fixed_ends) {
+        const double* L = desc->left_state;
+        const double* R = desc->right_state;
+        const double thL = P.isothermal ? desc->theta0 : L[2];
+        const double thR = P.isothermal ? desc->theta0 : R[2];
+        feq_host(dim, q1, P.C, L[0], L[1], 0.0, thL, P.ghostL);
+        feq_host(dim, q1, P.C, R[0], R[1], 0.0, thR, P.ghostR);
+        for (int p = 0; p < P.q; ++p) {
+            P.ghostLg[p] = (float)(P.ghostL[p] - P.W0[p]);
+            P.ghostRg[p] = (float)(P.ghostR[p] - P.W0[p]);
+        }
+    }
+
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= desc->device || desc->device < 0) {
+        set_err(nullptr, "no usable CUDA device %d (count %d)", desc->device, ndev);
+        delete h;
+        return PLBM_E_CUDA;
+    }
+    const Layout L = layout_of(desc);
+    P.pitch = L.pitch;
+    P.plane = (long long)L.pitch * desc->ny;
+    h->pop_bytes = L.pop_bytes;
+    h->ws_bytes = L.total;
+    if (cudaSetDevice(desc->device) != cudaSuccess) {
+        set_err(nullptr, "cudaSetDevice(%d) failed", desc->device);
+        delete h;
+        return PLBM_E_CUDA;
+    }
+    if (desc->workspace) {
+        if (desc->workspace_bytes < L.total) {
+            set_err(nullptr, "workspace of %zu bytes is smaller than the %zu bytes needed",
+                    desc->workspace_bytes, L.total);
+            delete h;
+            return PLBM_E_NOMEM;
+        }
+        h->ws = static_cast<char*>(desc->workspace);
+    } else {
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, L.total);
+        if (e != cudaSuccess) {
+            set_err(nullptr, "cudaMalloc(%zu) failed: %s", L.total, cudaGetErrorString(e));
+            delete h;
+            return PLBM_E_NOMEM;
+        }
+        h->ws = static_cast<char*>(p);
+        h->owns_ws = true;
+    }
+    if (cudaMallocHost(reinterpret_cast<void**>(&h->host_buf), 16 * sizeof(double)) != cudaSuccess) {
+        set_err(nullptr, "cudaMallocHost failed");
+        free_handle(h);
+        return PLBM_E_NOMEM;
+    }
+    h->f[0] = h->ws;
+    h->f[1] = h->ws + L.pop_bytes;
+    h->partials = reinterpret_cast<double*>(h->ws + L.partial_off);
+    h->result = reinterpret_cast<double*>(h->ws + L.result_off);
+    h->status = reinterpret_cast<unsigned*>(h->ws + L.status_off);
+    P.partials = h->partials;
+    P.status = h->status;
+    if (cudaMemsetAsync(h->status, 0, 256, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        set_err(nullptr, "initial status reset failed");
+        free_handle(h);
+        return PLBM_E_CUDA;
+    }
+    *out = reinterpret_cast<plbm_handle>(h);
+    return PLBM_OK;
+}
+
+plbm_status plbm_destroy(plbm_handle hh) {
+    free_handle(reinterpret_cast<Handle*>(hh));
+    return PLBM_OK;
+}
+
+plbm_status plbm_init(plbm_handle hh, const double* rho, const double* ux, const double* uy,
+                      const double* theta, int on_device) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    plbm_status st = usable(h, false);
+    if (st != PLBM_OK) return st;
+    if (!rho || !ux || (h->P.dim == 2 && !uy) || (!theta && !h->P.isothermal)) {
+        set_err(h, "missing field array");
+        return PLBM_E_ARG;
+    }
+    const size_t n = (size_t)h->P.nx * h->P.ny;
+    const double *d_rho = rho, *d_ux = ux, *d_uy = uy, *d_th = theta;
+    Staging stg;
+    stg.s = h->stream;
+    if (!on_device) {
+        CK(cudaMallocAsync(&stg.p, 4 * n * sizeof(double), h->stream));
+        double* base = static_cast<double*>(stg.p);
+        CK(cudaMemcpyAsync(base, rho, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemcpyAsync(base + n, ux, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        d_rho = base;
+        d_ux = base + n;
+        d_uy = nullptr;
+        d_th = nullptr;
+        if (uy && h->P.dim == 2) {
+            CK(cudaMemcpyAsync(base + 2 * n, uy, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+            d_uy = base + 2 * n;
+        }
+        if (theta) {
+            CK(cudaMemcpyAsync(base + 3 * n, theta, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+            d_th = base + 3 * n;
+        }
+    }
+    h->cur = 0;
+    CK(plbm::launch_init(h->prec, h->P, d_rho, d_ux, d_uy, d_th, h->f[0], h->stream));
+    CK(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
+    if (!on_device) CK(cudaStreamSynchronize(h->stream));
+    h->steps = 0;
+    h->initialised = true;
+    return PLBM_OK;
+}
+
+plbm_status plbm_check(plbm_handle hh) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    plbm_status st = usable(h);
+    if (st != PLBM_OK) return st;
+    unsigned bits = 0;
+    st = read_status(h, &bits);
+    if (st != PLBM_OK) return st;
+    if (bits) {
+        set_err(h, "diverged (status 0x%x) at or before step %lld", bits, h->steps);
+        h->sticky = PLBM_E_DIVERGED;
+        return PLBM_E_DIVERGED;
+    }
+    return PLBM_OK;
+}
+
+plbm_status plbm_step(plbm_handle hh, long n) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    plbm_status st = usable(h);
+    if (st != PLBM_OK) return st;
+    if (n < 0) { set_err(h, "n must be >= 0"); return PLBM_E_ARG; }
+    const int ce = h->desc.check_every;
+    for (long s = 0; s < n; ++s) {
+        CK(plbm::launch_step(h->prec, h->P, h->f[h->cur], h->f[h->cur ^ 1], false, h->stream));
+        h->cur ^= 1;
+        ++h->steps;
+        if (ce > 0 && ((s + 1) % ce == 0) && s + 1 < n) {
+            st = plbm_check(hh);
+            if (st != PLBM_OK) return st;
+        }
+    }
+    if (ce > 0) return plbm_check(hh);
+    return PLBM_OK;
+}
+
+plbm_status plbm_moments(plbm_handle hh, double* rho, double* ux, double* uy, double* theta,
+                         int on_device) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    plbm_status st = usable(h);
+    if (st != PLBM_OK && st != PLBM_E_DIVERGED) return st;
+    if (st == PLBM_E_DIVERGED) { set_err(h, "handle diverged"); return st; }
+    const size_t n = (size_t)h->P.nx * h->P.ny;
+    if (on_device) {
+        CK(plbm::launch_moments(h->prec, h->P, h->f[h->cur], rho, ux, uy, theta, h->stream));
+        return PLBM_OK;
+    }
+    Staging stg;
+    stg.s = h->stream;
+    CK(cudaMallocAsync(&stg.p, 4 * n * sizeof(double), h->stream));
+    double* b = static_cast<double*>(stg.p);
+    CK(plbm::launch_moments(h->prec, h->P, h->f[h->cur], rho ? b : nullptr, ux ? b + n : nullptr,
+                            uy ? b + 2 * n : nullptr, theta ? b + 3 * n : nullptr, h->stream));
+    double* outs[4] = {rho, ux, uy, theta};
+    for (int k = 0; k < 4; ++k)
+        if (outs[k]) CK(cudaMemcpyAsync(outs[k], b + k * n, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return PLBM_OK;
+}
+
+plbm_status plbm_diagnostics(plbm_handle hh, plbm_diag* out) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !out) { set_err(h, "bad arguments"); return PLBM_E_ARG; }
+    if (!h->initialised) { set_err(h, "populations not initialised"); return PLBM_E_STATE; }
+    if (h->sticky == PLBM_E_CUDA) { set_err(h, "handle in CUDA error state"); return PLBM_E_CUDA; }
+    CK(cudaSetDevice(h->desc.device));
+    CK(plbm::launch_reduce_state(h->prec, h->P, h->f[h->cur], h->result, h->stream));
+    CK(cudaMemcpyAsync(h->host_buf, h->result, 6 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(h->host_buf + 8, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    out->mass = h->host_buf[0];
+    out->jx = h->host_buf[1];
+    out->jy = h->host_buf[2];
+    out->energy = h->host_buf[3];
+    out->rho_min = h->host_buf[4];
+    out->theta_min = h->host_buf[5];
+    std::memcpy(&out->status, h->host_buf + 8, sizeof(unsigned));
+    out->steps = h->steps;
+    return PLBM_OK;
+}
+
+plbm_status plbm_conserved(plbm_handle hh, double out[4]) {
+    plbm_diag d;
+    plbm_status st = plbm_diagnostics(hh, &d);
+    if (st != PLBM_OK) return st;
+    out[0] = d.mass;
+    out[1] = d.jx;
+    out[2] = d.jy;
+    out[3] = d.energy;
+    return PLBM_OK;
+}
+
+plbm_status plbm_get_populations(plbm_handle hh, double* f, int on_device) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !f) { set_err(h, "bad arguments"); return PLBM_E_ARG; }
+    if (!h->initialised) { set_err(h, "populations not initialised"); return PLBM_E_STATE; }
+    if (h->sticky == PLBM_E_CUDA) { set_err(h, "handle in CUDA error state"); return PLBM_E_CUDA; }
+    CK(cudaSetDevice(h->desc.device));
+    const size_t n = (size_t)h->P.q * h->P.nx * h->P.ny;
+    if (on_device) {
+        CK(plbm::launch_get_populations(h->prec, h->P, h->f[h->cur], f, h->stream));
+        return PLBM_OK;
+    }
+    Staging stg;
+    stg.s = h->stream;
+    CK(cudaMallocAsync(&stg.p, n * sizeof(double), h->stream));
+    CK(plbm::launch_get_populations(h->prec, h->P, h->f[h->cur], static_cast<double*>(stg.p), h->stream));
+    CK(cudaMemcpyAsync(f, stg.p, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return PLBM_OK;
+}
+
+plbm_status plbm_set_populations(plbm_handle hh, const double* f, int on_device, int64_t step) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    plbm_status st = usable(h, false);
+    if (st != PLBM_OK) return st;
+    if (!f) { set_err(h, "populations pointer is NULL"); return PLBM_E_ARG; }
+    const size_t n = (size_t)h->P.q * h->P.nx * h->P.ny;
+    const double* src = f;
+    Staging stg;
+    stg.s = h->stream;
+    if (!on_device) {
+        CK(cudaMallocAsync(&stg.p, n * sizeof(double), h->stream));
+        CK(cudaMemcpyAsync(stg.p, f, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        src = static_cast<const double*>(stg.p);
+    }
+    h->cur = 0;
+    CK(plbm::launch_set_populations(h->prec, h->P, src, h->f[0], h->stream));
+    CK(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
+    if (!on_device) CK(cudaStreamSynchronize(h->stream));
+    h->steps = step;
+    h->initialised = true;
+    return PLBM_OK;
+}
+
+plbm_status plbm_get_info(plbm_handle hh, int* q, int* pitch, size_t* population_bytes) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) { set_err(nullptr, "handle is NULL"); return PLBM_E_ARG; }
+    if (q) *q = h->P.q;
+    if (pitch) *pitch = h->P.pitch;
+    if (population_bytes) *population_bytes = h->pop_bytes;
+    return PLBM_OK;
+}
+
+plbm_status plbm_device_populations(plbm_handle hh, void** ptr) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !ptr) { set_err(h, "bad arguments"); return PLBM_E_ARG; }
+    *ptr = h->f[h->cur];
+    return PLBM_OK;
+}
+
+const char* plbm_last_error(plbm_handle hh) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    return h ? h->err : g_thread_error;
+}
+
+const char* plbm_status_string(plbm_status s) {
+    switch (s) {
+        case PLBM_OK: return "PLBM_OK";
+        case PLBM_E_ARG: return "PLBM_E_ARG";
+        case PLBM_E_CUDA: return "PLBM_E_CUDA";
+        case PLBM_E_INADMISSIBLE: return "PLBM_E_INADMISSIBLE";
+        case PLBM_E_DIVERGED: return "PLBM_E_DIVERGED";
+        case PLBM_E_TIMEOUT: return "PLBM_E_TIMEOUT";
+        case PLBM_E_STATE: return "PLBM_E_STATE";
+        case PLBM_E_CHECKSUM: return "PLBM_E_CHECKSUM";
+        case PLBM_E_NOMEM: return "PLBM_E_NOMEM";
+    }
+    return "PLBM_E_UNKNOWN";
+}
+
+}  // extern "C"

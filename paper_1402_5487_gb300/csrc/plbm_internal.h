@@ -1,0 +1,99 @@
+// Internal declarations shared by the host library and the CUDA translation
+// units of libplbm.  Not part of the public ABI (see include/plbm.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace plbm {
+
+constexpr int kMaxQ1 = 8;
+constexpr int kMaxQ = kMaxQ1 * kMaxQ1;
+constexpr int kBlockX = 128;       // threads per block along x in the step kernels
+constexpr int kPartialStride = 8;  // doubles per block in the reduction scratch
+constexpr int kPitchAlign = 64;    // row pitch is a multiple of this many elements
+
+enum Prec { kF64 = 0, kF32 = 1, kF16Dev = 2, kBF16Dev = 3 };
+
+// Everything a step kernel needs about one lattice, passed by value as a
+// __grid_constant__ kernel parameter (it lives in the constant bank, so the
+// c_ij, velocities and rest weights are broadcast reads).
+struct LatticeParams {
+    int nx, ny, pitch, dim;
+    long long plane;        // elements between population planes (= pitch * ny)
+    int q1, q;
+    int fixed_ends;         // 1: ghost populations outside 0 <= x < nx
+    int isothermal;         // 1: theta in f^eq held at theta0
+    int paired;             // 1: row-paired layout (see elem_index), 2D even ny only
+    int half_ny;            // ny / 2 when paired
+    int sym5;               // 1: q1 = 5 with v = (0, a, -a, b, -b), a, b > 0, a != b
+    int v[kMaxQ1];          // integer velocities
+    int vxm[kMaxQ1];        // (-v) mod nx, in [0, nx): source column = x + vxm (- nx)
+    int vym[kMaxQ1];        // (-v) mod ny, in [0, ny)
+    double omega, theta0;
+    float omegaf, theta0f;
+    double C[kMaxQ1 * kMaxQ1];   // C[i*q1 + n] multiplies mu_n in r_i (Eq. eq:rdr)
+    float Cf[kMaxQ1 * kMaxQ1];   // FP32 part of C ...
+    float Cf_lo[kMaxQ1 * kMaxQ1];// ... and the FP32 remainder C - Cf (coefficients to ~2^-48)
+    // Symmetric five-velocity sets: factors of the constraint form of the rule
+    // (odd part from sum v r = mu_1, sum v^3 r = mu_3; even part from
+    // sum r = mu_0, sum v^2 r = mu_2, sum v^4 r = mu_4).
+    float sa, sb, sa2, sb2;      // a, b, a^2, b^2
+    float kOa, kOb, kEa, kEb;    // 1/(2a), 1/(2b(b^2-a^2)), 1/(2a^2), 1/(2b^2(b^2-a^2))
+    float w1f[kMaxQ1];           // 1D rest weights r_i(0, theta0)
+    float mu0f[kMaxQ1];          // mu_n(0, theta0)
+    float W0f[kMaxQ];            // rest equilibrium w0_p (product of 1D weights in 2D)
+    double W0[kMaxQ];            // the same in FP64
+    double w1[kMaxQ1];           // 1D rest weights in FP64
+    double ghostL[kMaxQ], ghostR[kMaxQ];    // f^eq of the end states (f-space, FP64)
+    float ghostLg[kMaxQ], ghostRg[kMaxQ];   // the same as deviations from w0 (FP32)
+    unsigned* status;            // device status word (PLBM_STATUS_* bits)
+    double* partials;            // reduction scratch, kPartialStride doubles per block
+};
+
+// Launchers implemented in the CUDA translation units.  All are asynchronous
+// on `stream` and return the launch error.
+cudaError_t launch_step(int prec, const LatticeParams& P, const void* src, void* dst,
+                        bool reduce, cudaStream_t stream);
+cudaError_t launch_init(int prec, const LatticeParams& P, const double* rho, const double* ux,
+                        const double* uy, const double* theta, void* f, cudaStream_t stream);
+cudaError_t launch_moments(int prec, const LatticeParams& P, const void* f, double* rho,
+                           double* ux, double* uy, double* theta, cudaStream_t stream);
+// Per-block partial sums of the stored state, then one deterministic final pass
+// writing out[0..5] = mass, jx, jy, energy, rho_min, theta_min.
+cudaError_t launch_reduce_state(int prec, const LatticeParams& P, const void* f, double* out,
+                                cudaStream_t stream);
+// Final pass over the partials written by a reducing step kernel.
+cudaError_t launch_finalize(const LatticeParams& P, int nblocks, double* out, cudaStream_t stream);
+cudaError_t launch_get_populations(int prec, const LatticeParams& P, const void* f, double* out,
+                                   cudaStream_t stream);
+cudaError_t launch_set_populations(int prec, const LatticeParams& P, const double* in, void* f,
+                                   cudaStream_t stream);
+
+// Number of blocks of a step launch (row-paired kernels cover two rows per block row).
+inline int step_blocks(const LatticeParams& P) {
+    return ((P.nx + kBlockX - 1) / kBlockX) * (P.paired ? P.half_ny : P.ny);
+}
+
+// Number of blocks of a reduction over the stored state (one node per thread).
+inline int reduce_blocks(const LatticeParams& P) {
+    return ((P.nx + kBlockX - 1) / kBlockX) * P.ny;
+}
+
+// Element index of population p at node (x, y) in a population array.
+// Plain layout:  p * plane + y * pitch + x.
+// Row-paired layout (2D, even ny, H = ny / 2): nodes (x, r) and (x, r + H) sit
+// next to each other, so one aligned 2-element vector holds both:
+//                p * plane + (y mod H) * 2 * pitch + 2 x + (y >= H).
+__host__ __device__ inline long long elem_index(const LatticeParams& P, int p, int x, int y) {
+    if (P.paired) {
+        const int hi = y >= P.half_ny;
+        const int r = hi ? y - P.half_ny : y;
+        return (long long)p * P.plane + (long long)r * 2 * P.pitch + 2LL * x + hi;
+    }
+    return (long long)p * P.plane + (long long)y * P.pitch + x;
+}
+
+}  // namespace plbm

@@ -1,0 +1,259 @@
+// Fast stream-and-collide for 2D symmetric five-velocity sets
+// (D2Q25 = D1Q5 x D1Q5 with v = (0, a, -a, b, -b), Sec. 2.4 and Sec. 4),
+// periodic, FP32 / FP16 / BF16 deviation storage, FP32 arithmetic.
+//
+// Each thread updates the two nodes (x, r) and (x, r + ny/2), which the
+// row-paired layout stores side by side: every pull f_p(x - v_p) of both
+// nodes is one aligned 8-byte (FP32) or 4-byte (16-bit) vector load, and every
+// store one vector store.  The two nodes travel through the collision as the
+// two lanes of float2 values, so the arithmetic issues as Blackwell packed
+// FP32x2 instructions (fma/add/mul .f32x2).
+//
+// Pull across the y wrap: node (x, r) reads row s = (r - v_y) mod ny and node
+// (x, r + H) reads (s + H) mod ny.  When s < H the pair row s holds them in
+// lane order; when s >= H the pair row s - H holds them swapped.
+//
+// Equilibrium in constraint form.  For v = (0, +-a, +-b) the deviation
+// dr = r(u, theta) - r(0, theta0) of Eq. (eq:rdr) splits into an odd part
+// (O_a for +-a, O_b for +-b) and an even part (E_0, E_a, E_b) fixed by the
+// moment identities sum v^n dr = dmu_n (n = 0..4):
+//   O_b = (dmu_3 - a^2 dmu_1) / (2b(b^2 - a^2)),   O_a = (dmu_1 - 2b O_b) / (2a),
+//   E_b = (dmu_4 - a^2 dmu_2) / (2b^2(b^2 - a^2)), E_a = (dmu_2 - 2b^2 E_b) / (2a^2),
+//   E_0 = -2 (E_a + E_b),   dr_(+-a) = E_a +- O_a,   dr_(+-b) = E_b +- O_b.
+// Written this way the conserved moments (n = 0, 1, 2) hold up to the rounding
+// of the last operations, whatever the rounding of the constant factors, so
+// FP32 collisions conserve mass, momentum and energy without a systematic drift.
+#pragma once
+
+#include "plbm_device.cuh"
+
+namespace plbm {
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, f2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Storage of one node pair.
+template <typename S>
+struct PairStore;
+
+template <>
+struct PairStore<float> {
+    using V = float2;
+    static __device__ __forceinline__ float2 load(const V* p) { return __ldg(p); }
+    static __device__ __forceinline__ float2 load_swapped(const V* p) {
+        const float2 v = __ldg(p);
+        return f2(v.y, v.x);
+    }
+    static __device__ __forceinline__ void store(V* p, float2 v) { *p = v; }
+};
+
+template <>
+struct PairStore<__half> {
+    using V = __half2;
+    static __device__ __forceinline__ float2 load(const V* p) { return __half22float2(__ldg(p)); }
+    static __device__ __forceinline__ float2 load_swapped(const V* p) {
+        return __half22float2(__lowhigh2highlow(__ldg(p)));
+    }
+    static __device__ __forceinline__ void store(V* p, float2 v) { *p = __float22half2_rn(v); }
+};
+
+template <>
+struct PairStore<__nv_bfloat16> {
+    using V = __nv_bfloat162;
+    static __device__ __forceinline__ float2 load(const V* p) { return __bfloat1622float2(__ldg(p)); }
+    static __device__ __forceinline__ float2 load_swapped(const V* p) {
+        return __bfloat1622float2(__lowhigh2highlow(__ldg(p)));
+    }
+    static __device__ __forceinline__ void store(V* p, float2 v) { *p = __float22bfloat162_rn(v); }
+};
+
+// dmu_1..dmu_4 = mu_n(u, theta) - mu_n(0, theta0) from mu_{n+1} = u mu_n + n theta mu_{n-1}
+// with mu(0, theta0) = (1, 0, theta0, 0, 3 theta0^2), then dr by the constraint form.
+__device__ __forceinline__ void sym5_axis(const LatticeParams& P, float2 u, float2 th, float2 dth,
+                                          float2 (&dr)[5]) {
+    const float2 th0 = f2s(P.theta0f);
+    const float2 d1 = u;
+    const float2 d2 = fma2(u, u, dth);
+    const float2 d3 = mul2(u, add2(add2(th0, d2), add2(th, th)));
+    const float2 d4 = fma2(u, d3, mul2(f2s(3.0f), fma2(th, d2, mul2(dth, th0))));
+    const float2 Ob = mul2(fma2(f2s(-P.sa2), d1, d3), f2s(P.kOb));
+    const float2 Oa = mul2(fma2(f2s(-2.0f * P.sb), Ob, d1), f2s(P.kOa));
+    const float2 Eb = mul2(fma2(f2s(-P.sa2), d2, d4), f2s(P.kEb));
+    const float2 Ea = mul2(fma2(f2s(-2.0f * P.sb2), Eb, d2), f2s(P.kEa));
+    dr[0] = mul2(f2s(-2.0f), add2(Ea, Eb));
+    dr[1] = add2(Ea, Oa);
+    dr[2] = sub2(Ea, Oa);
+    dr[3] = add2(Eb, Ob);
+    dr[4] = sub2(Eb, Ob);
+}
+
+// g: pulled deviations of both nodes on entry, post-collision deviations on exit.
+// Returns rho and theta of both nodes (for the status check and reductions).
+__device__ __forceinline__ void sym5_collide(const LatticeParams& P, float2 (&g)[25], float2& rho_o,
+                                             float2& th_o, float2& drho_o, float2& jx_o, float2& jy_o,
+                                             float2& e_o) {
+    float2 S[5], T[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        S[i] = add2(add2(g[5 * i], g[5 * i + 1]), add2(add2(g[5 * i + 2], g[5 * i + 3]), g[5 * i + 4]));
+    }
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        T[j] = add2(add2(g[j], g[5 + j]), add2(add2(g[10 + j], g[15 + j]), g[20 + j]));
+    }
+    const float2 a = f2s(P.sa), b = f2s(P.sb), a2 = f2s(P.sa2), b2 = f2s(P.sb2);
+    const float2 drho = add2(add2(S[0], S[1]), add2(add2(S[2], S[3]), S[4]));
+    const float2 jx = fma2(a, sub2(S[1], S[2]), mul2(b, sub2(S[3], S[4])));
+    const float2 ex = fma2(a2, add2(S[1], S[2]), mul2(b2, add2(S[3], S[4])));
+    const float2 jy = fma2(a, sub2(T[1], T[2]), mul2(b, sub2(T[3], T[4])));
+    const float2 ey = fma2(a2, add2(T[1], T[2]), mul2(b2, add2(T[3], T[4])));
+    const float2 rho = add2(f2s(1.0f), drho);
+    const float2 inv = f2(__frcp_rn(rho.x), __frcp_rn(rho.y));
+    const float2 ux = mul2(jx, inv), uy = mul2(jy, inv);
+    const float2 uu = fma2(ux, ux, mul2(uy, uy));
+    // 2 rho theta = 2 theta0 + sum |v|^2 g - rho |u|^2  =>  theta - theta0:
+    const float2 dth = mul2(f2s(0.5f), fma2(fma2(f2s(-2.0f * P.theta0f), drho, add2(ex, ey)), inv,
+                                            f2(-uu.x, -uu.y)));
+    const float2 th = add2(f2s(P.theta0f), dth);
+    rho_o = rho;
+    th_o = th;
+    drho_o = drho;
+    jx_o = jx;
+    jy_o = jy;
+    e_o = add2(ex, ey);
+
+    float2 dx[5], dy[5];
+    sym5_axis(P, ux, th, dth, dx);
+    sym5_axis(P, uy, th, dth, dy);
+
+    // g' = (1 - omega) g + omega (f^eq - w0) with
+    // f^eq - w0 = drho w_i w_j + rho (dx_i r^y_j + w_i dy_j),  r^y_j = w_j + dy_j:
+    //   g'_ij = (1 - omega) g_ij + A_i r^y_j + w_i Y_j,
+    //   A_i = omega rho dx_i,  Y_j = omega (rho dy_j + drho w_j).
+    const float2 om = f2s(P.omegaf);
+    const float2 orho = mul2(om, rho);
+    const float2 odrho = mul2(om, drho);
+    const float2 keep = f2s(1.0f - P.omegaf);
+    float2 ry[5], Y[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        ry[j] = add2(f2s(P.w1f[j]), dy[j]);
+        Y[j] = fma2(orho, dy[j], mul2(odrho, f2s(P.w1f[j])));
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const float2 A = mul2(orho, dx[i]);
+        const float2 w = f2s(P.w1f[i]);
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            const int p = 5 * i + j;
+            g[p] = fma2(keep, g[p], fma2(A, ry[j], mul2(w, Y[j])));
+        }
+    }
+}
+
+__device__ __forceinline__ bool healthy2(float2 rho, float2 th) {
+    // false for NaN, infinities and non-positive values (NaN compares false)
+    return (rho.x > 0.0f) & (rho.y > 0.0f) & (th.x > 0.0f) & (th.y > 0.0f) &
+           (rho.x < 3.0e38f) & (rho.y < 3.0e38f) & (th.x < 3.0e38f) & (th.y < 3.0e38f);
+}
+
+// grid = (ceil(nx / kBlockX), ny / 2); thread (x, r) owns nodes (x, r) and (x, r + ny/2).
+template <typename S, bool REDUCE>
+__global__ void __launch_bounds__(kBlockX)
+k_stream_collide_pair(const __grid_constant__ LatticeParams P,
+                      const typename PairStore<S>::V* __restrict__ src,
+                      typename PairStore<S>::V* __restrict__ dst) {
+    using PS = PairStore<S>;
+    const int x = blockIdx.x * kBlockX + threadIdx.x;
+    const int r = blockIdx.y;
+    const int H = P.half_ny;
+    const long long plane2 = (long long)H * P.pitch;  // pairs per population plane
+    NodeDiag d;
+    if (REDUCE) diag_zero(d);
+
+    if (x < P.nx) {
+        unsigned col[5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            const int s = x + P.vxm[i];
+            col[i] = (unsigned)((s >= P.nx) ? s - P.nx : s);
+        }
+        unsigned row[5];
+        bool swp[5];
+        bool any_swap = false;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            int s = r + P.vym[j];
+            s = (s >= P.ny) ? s - P.ny : s;
+            swp[j] = s >= H;
+            any_swap |= swp[j];
+            row[j] = (unsigned)((swp[j] ? s - H : s) * P.pitch);
+        }
+        float2 g[25];
+        if (!any_swap) {
+#pragma unroll
+            for (int i = 0; i < 5; ++i)
+#pragma unroll
+                for (int j = 0; j < 5; ++j) {
+                    const int p = 5 * i + j;
+                    g[p] = PS::load(src + p * plane2 + (row[j] + col[i]));
+                }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 5; ++i)
+#pragma unroll
+                for (int j = 0; j < 5; ++j) {
+                    const int p = 5 * i + j;
+                    const typename PS::V* a = src + p * plane2 + (row[j] + col[i]);
+                    g[p] = swp[j] ? PS::load_swapped(a) : PS::load(a);
+                }
+        }
+        float2 rho, th, drho, jx, jy, e;
+        sym5_collide(P, g, rho, th, drho, jx, jy, e);
+        if (!healthy2(rho, th)) {
+            unsigned bits = 0u;
+            bits |= (!(rho.x == rho.x) || !(rho.y == rho.y) || !(th.x == th.x) || !(th.y == th.y) ||
+                     !(rho.x < 3.0e38f) || !(rho.y < 3.0e38f) || !(th.x < 3.0e38f) || !(th.y < 3.0e38f))
+                        ? 1u : 0u;
+            bits |= (rho.x <= 0.0f || rho.y <= 0.0f) ? 2u : 0u;
+            bits |= (th.x <= 0.0f || th.y <= 0.0f) ? 4u : 0u;
+            atomicOr(P.status, bits);
+        }
+        if (REDUCE) {
+            d.mass = 2.0 + (double)drho.x + (double)drho.y;
+            d.jx = (double)jx.x + (double)jx.y;
+            d.jy = (double)jy.x + (double)jy.y;
+            d.energy = 4.0 * P.theta0 + (double)e.x + (double)e.y;
+            d.rho_min = fmin((double)rho.x, (double)rho.y);
+            d.theta_min = fmin((double)th.x, (double)th.y);
+        }
+        const unsigned here = (unsigned)(r * P.pitch + x);
+#pragma unroll
+        for (int p = 0; p < 25; ++p) PS::store(dst + p * plane2 + here, g[p]);
+    }
+    if (REDUCE) {
+        const int blk = blockIdx.y * gridDim.x + blockIdx.x;
+        block_reduce_diag<kBlockX>(d, P.partials + (long long)blk * kPartialStride);
+    }
+}
+
+template <typename S>
+cudaError_t launch_step_pair_t(const LatticeParams& P, const void* src, void* dst, bool reduce,
+                               cudaStream_t stream) {
+    using V = typename PairStore<S>::V;
+    dim3 grid((P.nx + kBlockX - 1) / kBlockX, P.half_ny);
+    const V* s = static_cast<const V*>(src);
+    V* t = static_cast<V*>(dst);
+    if (reduce)
+        k_stream_collide_pair<S, true><<<grid, kBlockX, 0, stream>>>(P, s, t);
+    else
+        k_stream_collide_pair<S, false><<<grid, kBlockX, 0, stream>>>(P, s, t);
+    return cudaGetLastError();
+}
+
+}  // namespace plbm

@@ -1,0 +1,13 @@
+// Stream-and-collide launcher for one storage precision (__nv_bfloat16).  The kernel
+// templates live in plbm_device.cuh; this unit only instantiates them so the
+// four precisions compile in parallel.  Row-paired lattices take the
+// two-nodes-per-thread kernel of plbm_pair.cuh.
+#include "plbm_pair.cuh"
+
+namespace plbm {
+cudaError_t launch_step_bf16(const LatticeParams& P, const void* src, void* dst, bool reduce,
+                             cudaStream_t stream) {
+    if (P.paired) return launch_step_pair_t<__nv_bfloat16>(P, src, dst, reduce, stream);
+    return launch_step_t<__nv_bfloat16>(P, src, dst, reduce, stream);
+}
+}  // namespace plbm

@@ -1,0 +1,328 @@
+"""ctypes binding of libplbm (include/plbm.h): argument marshalling only.
+
+Every step of the method runs in the CUDA kernels of ``libplbm.so``.  PyTorch
+supplies device memory (the handle's workspace) and the CUDA stream; NumPy
+arrays are accepted for host-side inputs and outputs.  There is no CPU path:
+if the shared library is missing or no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libplbm.so")
+
+PLBM_OK = 0
+PLBM_E_ARG = -1
+PLBM_E_CUDA = -2
+PLBM_E_INADMISSIBLE = -3
+PLBM_E_DIVERGED = -4
+PLBM_E_TIMEOUT = -5
+PLBM_E_STATE = -6
+PLBM_E_CHECKSUM = -7
+PLBM_E_NOMEM = -8
+
+PREC = {"f64": 0, "f32": 1, "f16dev": 2, "bf16dev": 3}
+BC = {"periodic": 0, "fixed": 1}
+FLAG_ISOTHERMAL = 0x1
+FLAG_SKIP_ADMISSIBILITY = 0x2
+
+
+class PlbmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (status_name(status) if _lib else status, msg))
+        self.status = status
+
+
+class PlbmDesc(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int),
+        ("q1", ctypes.c_int),
+        ("v", ctypes.POINTER(ctypes.c_int)),
+        ("omega", ctypes.c_double),
+        ("theta0", ctypes.c_double),
+        ("nx", ctypes.c_int),
+        ("ny", ctypes.c_int),
+        ("prec", ctypes.c_int),
+        ("bc", ctypes.c_int),
+        ("left_state", ctypes.POINTER(ctypes.c_double)),
+        ("right_state", ctypes.POINTER(ctypes.c_double)),
+        ("stream", ctypes.c_void_p),
+        ("flags", ctypes.c_uint),
+        ("check_every", ctypes.c_int),
+        ("u_max", ctypes.c_double),
+        ("workspace", ctypes.c_void_p),
+        ("workspace_bytes", ctypes.c_size_t),
+        ("device", ctypes.c_int),
+    ]
+
+
+class PlbmDiag(ctypes.Structure):
+    _fields_ = [
+        ("mass", ctypes.c_double),
+        ("jx", ctypes.c_double),
+        ("jy", ctypes.c_double),
+        ("energy", ctypes.c_double),
+        ("rho_min", ctypes.c_double),
+        ("theta_min", ctypes.c_double),
+        ("status", ctypes.c_uint32),
+        ("steps", ctypes.c_int64),
+    ]
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+_H = ctypes.c_void_p
+_lock = threading.Lock()
+_lib = None
+
+# name -> (restype, argtypes) for every function declared in include/plbm.h
+SIGNATURES = {
+    "plbm_abi_version": (ctypes.c_int, []),
+    "plbm_coefficients": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), _D]),
+    "plbm_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(PlbmDesc)]),
+    "plbm_create": (ctypes.c_int, [ctypes.POINTER(PlbmDesc), ctypes.POINTER(_H)]),
+    "plbm_destroy": (ctypes.c_int, [_H]),
+    "plbm_init": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.c_int]),
+    "plbm_step": (ctypes.c_int, [_H, ctypes.c_long]),
+    "plbm_check": (ctypes.c_int, [_H]),
+    "plbm_moments": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_int]),
+    "plbm_diagnostics": (ctypes.c_int, [_H, ctypes.POINTER(PlbmDiag)]),
+    "plbm_conserved": (ctypes.c_int, [_H, _D]),
+    "plbm_get_populations": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int]),
+    "plbm_set_populations": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64]),
+    "plbm_get_info": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_size_t)]),
+    "plbm_device_populations": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_void_p)]),
+    "plbm_last_error": (ctypes.c_char_p, [_H]),
+    "plbm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+
+def lib():
+    """Load libplbm.so (built by ``paper_1402_5487_gb300.build``); raise if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    "libplbm.so not built (%s); run paper_1402_5487_gb300.build.build() "
+                    "(the CUDA library is required: there is no CPU path)" % LIB_PATH)
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+        return _lib
+
+
+def status_name(st: int) -> str:
+    return lib().plbm_status_string(int(st)).decode()
+
+
+def last_error(h=None) -> str:
+    return lib().plbm_last_error(h).decode(errors="replace")
+
+
+def _ok(st: int, h=None):
+    if st != PLBM_OK:
+        raise PlbmError(st, last_error(h))
+
+
+def coefficients(v) -> np.ndarray:
+    """c_ij of Eq. (eq:rdr) computed by the library's host code (FP64)."""
+    q1 = len(v)
+    va = (ctypes.c_int * q1)(*[int(a) for a in v])
+    C = np.zeros(q1 * q1)
+    _ok(lib().plbm_coefficients(q1, va, C.ctypes.data_as(_D)))
+    return C.reshape(q1, q1)
+
+
+def make_desc(dim, v, omega, nx, ny=1, theta0=1.0, prec="f32", bc="periodic", left_state=None,
+              right_state=None, isothermal=False, check_every=0, u_max=0.0, stream=None,
+              device=0, skip_admissibility=False):
+    """Build a PlbmDesc; the returned tuple keeps the ctypes buffers alive."""
+    q1 = len(v)
+    va = (ctypes.c_int * q1)(*[int(a) for a in v])
+    d = PlbmDesc()
+    d.dim, d.q1, d.v = int(dim), q1, va
+    d.omega, d.theta0 = float(omega), float(theta0)
+    d.nx, d.ny = int(nx), int(ny)
+    d.prec = PREC[prec] if isinstance(prec, str) else int(prec)
+    d.bc = BC[bc] if isinstance(bc, str) else int(bc)
+    keep = [va]
+    if left_state is not None:
+        ls = (ctypes.c_double * 3)(*[float(a) for a in left_state])
+        rs = (ctypes.c_double * 3)(*[float(a) for a in right_state])
+        d.left_state = ctypes.cast(ls, _D)
+        d.right_state = ctypes.cast(rs, _D)
+        keep += [ls, rs]
+    d.stream = stream
+    d.flags = (FLAG_ISOTHERMAL if isothermal else 0) | (FLAG_SKIP_ADMISSIBILITY if skip_admissibility else 0)
+    d.check_every = int(check_every)
+    d.u_max = float(u_max)
+    d.device = int(device)
+    return d, keep
+
+
+def workspace_bytes(desc: PlbmDesc) -> int:
+    return int(lib().plbm_workspace_bytes(ctypes.byref(desc)))
+
+
+def _ptr(a) -> int | None:
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()  # torch tensor
+
+
+class Solver:
+    """One lattice on one GPU (a handle of the C ABI).
+
+    Device memory for populations and scratch comes from a PyTorch uint8 tensor
+    passed as the handle's workspace; launches go to PyTorch's current stream of
+    the device unless ``stream`` is given (a ``torch.cuda.Stream``).
+    """
+
+    def __init__(self, dim, v, omega, nx, ny=1, theta0=1.0, prec="f32", bc="periodic",
+                 left_state=None, right_state=None, isothermal=False, check_every=0, u_max=0.0,
+                 device=0, stream=None, skip_admissibility=False, torch_workspace=True):
+        import torch  # device memory and streams only
+
+        self.torch = torch
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.dim, self.v, self.q1 = dim, tuple(int(a) for a in v), len(v)
+        self.q = self.q1 ** dim
+        self.nx, self.ny = int(nx), (int(ny) if dim == 2 else 1)
+        self.prec = prec
+        desc, self._keep = make_desc(dim, v, omega, nx, self.ny, theta0, prec, bc, left_state,
+                                     right_state, isothermal, check_every, u_max,
+                                     self.stream.cuda_stream, device, skip_admissibility)
+        self._ws = None
+        if torch_workspace:
+            nbytes = workspace_bytes(desc)
+            if nbytes == 0:
+                # invalid descriptor: let create report the reason
+                pass
+            else:
+                self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+                base = self._ws.data_ptr()
+                desc.workspace = (base + 255) // 256 * 256
+                desc.workspace_bytes = nbytes
+        h = _H()
+        st = lib().plbm_create(ctypes.byref(desc), ctypes.byref(h))
+        if st != PLBM_OK:
+            raise PlbmError(st, last_error(None))
+        self.h = h
+        self.desc = desc
+
+    # -- lifetime ----------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None):
+            lib().plbm_destroy(self.h)
+            self.h = None
+        self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- calls ---------------------------------------------------------------
+    def _field_args(self, arrs):
+        on_dev = None
+        ptrs = []
+        keep = []
+        for a in arrs:
+            if a is None:
+                ptrs.append(None)
+                continue
+            if isinstance(a, np.ndarray):
+                a = np.ascontiguousarray(a, dtype=np.float64)
+                assert a.size == self.nx * self.ny
+                dev = 0
+            else:
+                assert a.dtype == self.torch.float64 and a.is_contiguous() and a.numel() == self.nx * self.ny
+                dev = 1
+            if on_dev is None:
+                on_dev = dev
+            elif on_dev != dev:
+                raise ValueError("mix of host and device arrays")
+            keep.append(a)
+            ptrs.append(_ptr(a))
+        return ptrs, on_dev or 0, keep
+
+    def init(self, rho, ux, uy=None, theta=None):
+        ptrs, on_dev, keep = self._field_args([rho, ux, uy, theta])
+        _ok(lib().plbm_init(self.h, *ptrs, on_dev), self.h)
+
+    def step(self, n: int = 1):
+        _ok(lib().plbm_step(self.h, int(n)), self.h)
+
+    def step_status(self, n: int = 1) -> int:
+        """Like step() but returns the status code instead of raising."""
+        return int(lib().plbm_step(self.h, int(n)))
+
+    def check(self) -> int:
+        return int(lib().plbm_check(self.h))
+
+    def moments(self, on_device: bool = False):
+        """(rho, ux, uy, theta) as FP64 [ny][nx] NumPy arrays (or torch CUDA tensors)."""
+        shp = (self.ny, self.nx)
+        if on_device:
+            outs = [self.torch.empty(shp, dtype=self.torch.float64, device=self.device) for _ in range(4)]
+        else:
+            outs = [np.empty(shp) for _ in range(4)]
+        _ok(lib().plbm_moments(self.h, *[_ptr(o) for o in outs], 1 if on_device else 0), self.h)
+        return tuple(outs)
+
+    def diagnostics(self) -> dict:
+        d = PlbmDiag()
+        _ok(lib().plbm_diagnostics(self.h, ctypes.byref(d)), self.h)
+        return {k: getattr(d, k) for k, _ in PlbmDiag._fields_}
+
+    def conserved(self) -> np.ndarray:
+        out = np.zeros(4)
+        _ok(lib().plbm_conserved(self.h, out.ctypes.data_as(_D)), self.h)
+        return out
+
+    def get_populations(self, on_device: bool = False):
+        shp = (self.q, self.ny, self.nx)
+        out = (self.torch.empty(shp, dtype=self.torch.float64, device=self.device) if on_device
+               else np.empty(shp))
+        _ok(lib().plbm_get_populations(self.h, _ptr(out), 1 if on_device else 0), self.h)
+        return out
+
+    def set_populations(self, f, step: int = 0):
+        if isinstance(f, np.ndarray):
+            f = np.ascontiguousarray(f, dtype=np.float64)
+            on = 0
+        else:
+            on = 1
+        assert tuple(f.shape) == (self.q, self.ny, self.nx)
+        _ok(lib().plbm_set_populations(self.h, _ptr(f), on, int(step)), self.h)
+
+    def info(self):
+        q, pitch, nb = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+        _ok(lib().plbm_get_info(self.h, ctypes.byref(q), ctypes.byref(pitch), ctypes.byref(nb)), self.h)
+        return {"q": q.value, "pitch": pitch.value, "population_bytes": nb.value}
+
+    def device_populations_ptr(self) -> int:
+        p = ctypes.c_void_p()
+        _ok(lib().plbm_device_populations(self.h, ctypes.byref(p)), self.h)
+        return int(p.value)

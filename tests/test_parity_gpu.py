@@ -1,0 +1,311 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (max|a-b|/max|b| per field, vector norm for u, and the same over
+all populations):
+  FP64 storage  <= 1e-12 relative,
+  FP32 storage  <= 1e-5 relative over 1000 steps.
+Integer-like work (pure streaming with omega = 0, checkpoint round trips)
+is compared bit for bit.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import riemann as R
+from paper_1402_5487_gb300 import build, inputs as I, plbm
+
+from parity_util import field_errors, gpu_run, oracle_run, patch_fields, rel
+
+pytestmark = pytest.mark.gpu
+
+V5 = I.SET_013
+TOL64 = 1e-12
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    plbm.lib()
+
+
+def smooth_fields(nx, ny, seed, amp_u=0.05, amp_r=0.02, theta0=1.0):
+    rng = np.random.default_rng(seed)
+    x = np.arange(nx)[None, :] * 2 * np.pi / nx
+    y = np.arange(ny)[:, None] * 2 * np.pi / ny
+    ph = rng.uniform(0, 2 * np.pi, 4)
+    rho = 1 + amp_r * np.sin(x + ph[0]) * np.cos(y + ph[1]) + 0.001 * rng.uniform(-1, 1, (ny, nx))
+    ux = amp_u * np.sin(y + ph[2]) + 0.002 * rng.uniform(-1, 1, (ny, nx))
+    uy = amp_u * np.cos(x + ph[3]) + 0.002 * rng.uniform(-1, 1, (ny, nx))
+    th = theta0 * (1 + amp_r * np.cos(x + y + ph[0])) + 0 * rho
+    return (np.ascontiguousarray(rho), np.ascontiguousarray(ux), np.ascontiguousarray(uy),
+            np.ascontiguousarray(th))
+
+
+@pytest.mark.parametrize("nx,ny", [(33, 17), (7, 5), (1, 1), (130, 3), (256, 2)])
+def test_pure_stream_bit_exact(nx, ny):
+    # omega = 0 leaves only the pull: identical FP64 inputs must give identical outputs.
+    lat = O.Lattice(2, V5, 0.0, nx, ny, theta0=1.0)
+    f0 = lat.init(*smooth_fields(nx, ny, 1))
+    s = plbm.Solver(2, V5, 0.0, nx, ny, theta0=1.0, prec="f64")
+    s.set_populations(f0)
+    s.step(3)
+    assert np.array_equal(s.get_populations(), lat.run(f0, 3))
+    s.close()
+
+
+@pytest.mark.parametrize("nx,ny", [(33, 17), (130, 3)])
+def test_pure_stream_fixed_ends_bit_exact(nx, ny):
+    left, right = (1.2, 0.05, 0.9), (0.8, -0.02, 1.1)
+    lat = O.Lattice(2, V5, 0.0, nx, ny, bc="fixed", theta0=1.0, left_state=left, right_state=right)
+    f0 = lat.init(*smooth_fields(nx, ny, 5))
+    s = plbm.Solver(2, V5, 0.0, nx, ny, theta0=1.0, prec="f64", bc="fixed", left_state=left,
+                    right_state=right)
+    s.set_populations(f0)
+    s.step(4)
+    got, ref = s.get_populations(), lat.run(f0, 4)
+    # ghost populations come from the library's own FP64 f^eq: equal to rounding
+    assert np.max(np.abs(got - ref)) <= 1e-15
+    s.close()
+
+
+@pytest.mark.parametrize("nx,ny", [(33, 17), (7, 5), (1, 1), (200, 9), (34, 18), (1, 2)])
+def test_parity_d2q25_f64(nx, ny):
+    fields = smooth_fields(nx, ny, 2)
+    (mg, fg, _) = gpu_run(2, V5, 1.3, nx, ny, fields, 100, prec="f64")
+    _, fo, mo = oracle_run(2, V5, 1.3, nx, ny, fields, 100)
+    assert rel(fg, fo) <= TOL64
+    # tiny periodic grids damp u to a small fraction of its start within 100 steps: scale
+    # the velocity error by its initial amplitude
+    u0 = np.max(np.hypot(fields[1], fields[2]))
+    assert np.max(np.hypot(mg[1] - mo[1], mg[2] - mo[2])) <= TOL64 * u0
+    assert O.rel_err(mg[0], mo[0]) <= TOL64 and O.rel_err(mg[3], mo[3]) <= TOL64
+
+
+# Even ny takes the row-paired two-nodes-per-thread kernel, odd ny the one-node kernel.
+@pytest.mark.parametrize("nx,ny", [(33, 17), (7, 5), (1, 1), (130, 3), (34, 18), (8, 6), (1, 2),
+                                   (130, 4), (257, 10)])
+@pytest.mark.parametrize("prec,tol", [("f32", 2e-6), ("f16dev", 2e-3), ("bf16dev", 2e-2)])
+def test_parity_d2q25_reduced_storage_small_grids(nx, ny, prec, tol):
+    fields = smooth_fields(nx, ny, 7)
+    steps = 50
+    (mg, fg, _) = gpu_run(2, V5, 1.3, nx, ny, fields, steps, prec=prec)
+    _, fo, mo = oracle_run(2, V5, 1.3, nx, ny, fields, steps)
+    u0 = np.max(np.hypot(fields[1], fields[2]))
+    assert np.max(np.hypot(mg[1] - mo[1], mg[2] - mo[2])) <= tol * u0
+    assert O.rel_err(mg[0], mo[0]) <= tol * 0.1 and O.rel_err(mg[3], mo[3]) <= tol * 0.1
+    assert np.max(np.abs(fg - fo)) <= tol * 0.1 * np.max(np.abs(fo))
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", TOL64), ("f32", 2e-6)])
+@pytest.mark.parametrize("v,theta0,omega,iso", [((0, 1, -1), 0.25, 1.2, True),
+                                                ((0, 1, -1), 1.0 / 3.0, 1.5, True),
+                                                ((1, -1, 3, -3), 4.0 / 3.0, 1.1, True),
+                                                ((0, 1, -1, 2, -2), 1 / 1.6 ** 2, 1.6, False),
+                                                ((0, 2, -2, 3, -3), 1.6, 1.2, False),
+                                                ((0, 2, -4), 1.0, 1.0, True)])
+def test_parity_other_sets(v, theta0, omega, iso, prec, tol):
+    nx, ny = 70, 19
+    fields = smooth_fields(nx, ny, 3, amp_u=0.03, amp_r=0.01, theta0=theta0)
+    (mg, fg, _) = gpu_run(2, v, omega, nx, ny, fields, 60, prec=prec, theta0=theta0, isothermal=iso)
+    _, fo, mo = oracle_run(2, v, omega, nx, ny, fields, 60, theta0=theta0, isothermal=iso)
+    assert rel(fg, fo) <= tol
+    assert O.rel_err(mg[0], mo[0]) <= tol and O.rel_err(mg[3], mo[3]) <= tol
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", TOL64), ("f32", TOL32)])
+def test_parity_d1q5_shock_tube(prec, tol):
+    left, right = (1.1, 0.0, 0.5), (1.0, 0.0, 0.5)
+    fields = I.shock_tube_fields(1000, left, right)
+    (mg, fg, _) = gpu_run(1, V5, 1.5, 1000, 1, fields, 500, prec=prec, theta0=0.5, bc="fixed",
+                          left=left, right=right)
+    _, fo, mo = oracle_run(1, V5, 1.5, 1000, 1, fields, 500, theta0=0.5, bc="fixed", left=left,
+                           right=right)
+    errs = field_errors(mg, mo)
+    assert max(errs.values()) <= tol, errs
+    if prec == "f64":
+        assert rel(fg, fo) <= tol
+
+
+def test_shock_tube_gpu_vs_exact_riemann():
+    left, right = (1.1, 0.0, 0.5), (1.0, 0.0, 0.5)
+    fields = I.shock_tube_fields(1000, left, right)
+    (mg, _, _) = gpu_run(1, V5, 1.5, 1000, 1, fields, 361, prec="f64", theta0=0.5, bc="fixed",
+                         left=left, right=right)
+    rho, ux, _, th = (a[0] for a in mg)
+    x = np.arange(1000) + 0.5
+    re, ue, pe = R.sample(R.State(1.1, 0.0, 0.55), R.State(1.0, 0.0, 0.5), 3.0, (x - 500) / 361)
+    assert np.mean(np.abs(rho - re)) / np.mean(re) < 0.002
+    assert np.mean(np.abs(ux - ue)) / np.max(np.abs(ue)) < 0.02
+    assert np.mean(np.abs(th - pe / re)) / np.mean(pe / re) < 0.002
+
+
+@pytest.mark.parametrize("L", [128])
+def test_parity_kh_1000_steps(L):
+    fields = I.kh_fields(L)
+    _, fo, mo = oracle_run(2, V5, 1.3, L, L, fields, 1000)
+    (m64, f64, _) = gpu_run(2, V5, 1.3, L, L, fields, 1000, prec="f64")
+    (m32, f32, _) = gpu_run(2, V5, 1.3, L, L, fields, 1000, prec="f32")
+    e64 = field_errors(m64, mo)
+    e32 = field_errors(m32, mo)
+    assert max(e64.values()) <= TOL64 and rel(f64, fo) <= TOL64, e64
+    assert max(e32.values()) <= TOL32 and rel(f32, fo) <= TOL32, e32
+
+
+@pytest.mark.slow
+def test_parity_kh_512_config_1000_steps():
+    # Kelvin-Helmholtz double shear layer, 512^2, D2Q25 {0,+-1,+-3}^2, theta0 = 1, omega = 1.3.
+    L = 512
+    fields = I.kh_fields(L)
+    _, fo, mo = oracle_run(2, V5, 1.3, L, L, fields, 1000)
+    (m64, f64, _) = gpu_run(2, V5, 1.3, L, L, fields, 1000, prec="f64")
+    (m32, f32, _) = gpu_run(2, V5, 1.3, L, L, fields, 1000, prec="f32")
+    e64 = field_errors(m64, mo)
+    e32 = field_errors(m32, mo)
+    assert max(e64.values()) <= TOL64 and rel(f64, fo) <= TOL64, e64
+    assert max(e32.values()) <= TOL32 and rel(f32, fo) <= TOL32, e32
+
+
+def test_fullsize_2048_sampled_nodes():
+    # Bench workload (2048^2 KH, FP32): after k steps a node depends only on nodes within
+    # 3k in each direction, so the oracle advances a (6k+1)^2 periodic window around each
+    # sampled node and its centre must match the GPU.
+    L, k, half = 2048, 4, 12
+    fields = I.kh_fields(L)
+    s = plbm.Solver(2, V5, 1.3, L, L, theta0=1.0, prec="f32")
+    s.init(*fields)
+    s.step(k)
+    mg = s.moments()
+    rng = np.random.default_rng(11)
+    pts = [(0, 0), (L - 1, L - 1), (L // 2, L // 4), (3, L - 2)] + [
+        tuple(int(a) for a in rng.integers(0, L, 2)) for _ in range(28)]
+    errs = []
+    for cx, cy in pts:
+        pf = patch_fields(fields, cx, cy, half, L, L)
+        lat, f, mo = oracle_run(2, V5, 1.3, 2 * half + 1, 2 * half + 1, pf, k)
+        for gi, oi in zip(mg, mo):
+            errs.append(abs(gi[cy, cx] - oi[half, half]) / max(1e-30, np.max(np.abs(fields[0]))))
+    rho_g, ux_g, uy_g, _ = mg
+    assert max(errs[0::4]) < 1e-6      # rho
+    assert max(errs[3::4]) < 1e-6      # theta
+    assert max(max(errs[1::4]), max(errs[2::4])) < 1e-6  # velocity components (scale ~0.1)
+    d = s.diagnostics()
+    assert abs(d["mass"] - L * L) / (L * L) < 1e-6
+    s.close()
+
+
+def test_conservation_periodic_f64():
+    L = 64
+    fields = I.kh_fields(L)
+    s = plbm.Solver(2, V5, 1.3, L, L, theta0=1.0, prec="f64")
+    s.init(*fields)
+    c0 = s.conserved()
+    s.step(1000)
+    c1 = s.conserved()
+    assert np.max(np.abs(c1 - c0)) <= 1e-12 * np.max(np.abs(c0))
+    lat = O.Lattice(2, V5, 1.3, L, L, theta0=1.0)
+    f = lat.init(*fields)
+    assert np.max(np.abs(c0 - lat.conserved(f))) <= 1e-13 * np.max(np.abs(c0))
+    s.close()
+
+
+def test_diagnostics_match_oracle():
+    L = 48
+    fields = I.kh_fields(L, seed=5)
+    (mg, fg, s) = gpu_run(2, V5, 1.3, L, L, fields, 37, prec="f64")
+    lat, fo, mo = oracle_run(2, V5, 1.3, L, L, fields, 37)
+    d = s.diagnostics()
+    co = lat.conserved(fo)
+    for a, b in zip((d["mass"], d["jx"], d["jy"], d["energy"]), co):
+        assert abs(a - b) <= 1e-12 * max(1.0, abs(co[0]))
+    assert abs(d["rho_min"] - mo[0].min()) < 1e-13
+    assert abs(d["theta_min"] - mo[3].min()) < 1e-13
+    assert d["status"] == 0 and d["steps"] == 37
+    s.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16dev", "bf16dev"])
+def test_checkpoint_resume_is_bit_identical(prec):
+    L = 40
+    fields = I.kh_fields(L, seed=3)
+    a = plbm.Solver(2, V5, 1.3, L, L, theta0=1.0, prec=prec)
+    a.init(*fields)
+    a.step(20)
+    f20 = a.get_populations()
+    a.step(20)
+    ref = a.get_populations()
+    b = plbm.Solver(2, V5, 1.3, L, L, theta0=1.0, prec=prec)
+    b.set_populations(f20, step=20)
+    b.step(20)
+    assert np.array_equal(b.get_populations(), ref)
+    assert b.diagnostics()["steps"] == 40
+    a.close()
+    b.close()
+
+
+def test_device_pointers_and_streams():
+    import torch
+    L = 64
+    fields = I.kh_fields(L, seed=4)
+    st = torch.cuda.Stream()
+    s = plbm.Solver(2, V5, 1.3, L, L, theta0=1.0, prec="f32", stream=st)
+    dev = [torch.from_numpy(a).to("cuda") for a in fields]
+    torch.cuda.synchronize()
+    s.init(*dev)
+    s.step(10)
+    md = s.moments(on_device=True)
+    st.synchronize()
+    mh = s.moments()
+    for a, b in zip(md, mh):
+        assert np.array_equal(a.cpu().numpy(), b)
+    (mg, _, _) = gpu_run(2, V5, 1.3, L, L, fields, 10, prec="f32")
+    for a, b in zip(mg, mh):
+        assert np.array_equal(a, b)
+    s.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("f16dev", 2e-2), ("bf16dev", 1e-1)])
+def test_reduced_precision_error_is_bounded(prec, tol):
+    L = 128
+    fields = I.kh_fields(L)
+    _, _, mo = oracle_run(2, V5, 1.3, L, L, fields, 1000)
+    (mg, _, s) = gpu_run(2, V5, 1.3, L, L, fields, 1000, prec=prec)
+    errs = field_errors(mg, mo)
+    assert errs["u"] <= tol and errs["rho"] <= tol * 0.1 and errs["theta"] <= tol * 0.1, errs
+    assert s.check() == plbm.PLBM_OK
+
+
+def test_literal_shock_tube_reports_divergence():
+    # rho 1 / 0.125, theta 0.5 / 0.4 on {0,+-1,+-3}: leaves the positivity region (theta <= 0).
+    left, right = (1.0, 0.0, 0.5), (0.125, 0.0, 0.4)
+    s = plbm.Solver(1, V5, 1.5, 1000, 1, theta0=0.5, prec="f64", bc="fixed", left_state=left,
+                    right_state=right, check_every=5)
+    s.init(*I.shock_tube_fields(1000, left, right))
+    st = s.step_status(500)
+    assert st == plbm.PLBM_E_DIVERGED
+    assert "diverged" in plbm.last_error(s.h)
+    # sticky: further steps are refused, diagnostics still readable
+    assert s.step_status(1) == plbm.PLBM_E_DIVERGED
+    assert s.diagnostics()["status"] != 0
+    s.close()
+
+
+def test_literal_kh_omega_reports_divergence():
+    L = 64
+    s = plbm.Solver(2, V5, 1.8, L, L, theta0=1.0, prec="f32", check_every=50)
+    s.init(*I.kh_fields(L))
+    assert s.step_status(3000) == plbm.PLBM_E_DIVERGED
+    s.close()
+
+
+def test_stable_kh_stays_healthy():
+    L = 64
+    s = plbm.Solver(2, V5, 1.3, L, L, theta0=1.0, prec="f32", check_every=100)
+    s.init(*I.kh_fields(L))
+    assert s.step_status(3000) == plbm.PLBM_OK
+    rho, ux, uy, th = s.moments()
+    assert abs(rho - 1).max() < 0.01 and abs(th - 1).max() < 0.01
+    assert np.hypot(ux, uy).max() < 0.12
+    s.close()
