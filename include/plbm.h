@@ -184,6 +184,32 @@ plbm_status plbm_get_info(plbm_handle h, int *q, int *pitch, size_t *population_
  * [q][ny][pitch] in the handle's precision).  For profiling and tests. */
 plbm_status plbm_device_populations(plbm_handle h, void **ptr);
 
+/* Largest lattice (nx * ny nodes) plbm_diagnostics_noalloc accepts: its
+ * static scratch array holds one 64-byte record per 256 nodes (1 MiB). */
+#define PLBM_NOALLOC_MAX_NODES (1 << 22)
+
+/* Diagnostics for callers that cannot allocate device memory.  The paper has
+ * no counterpart; this is a service of the library.  Some callers cannot call
+ * cudaMalloc: code recording a CUDA graph, plug-ins whose host application owns
+ * every allocation, or embedded set-ups that forbid allocation after start-up.
+ * This call needs no handle, allocates nothing (no cudaMalloc or cudaFree, no
+ * allocating library routine) and keeps its only scratch in a static device
+ * array of PLBM_NOALLOC_MAX_NODES / 256 records (1 MiB) that every GPU loading
+ * the library holds until the process exits.
+ *   f:   device pointer, FP64 populations [q][ny][nx] (q = q1^dim, the layout of
+ *        plbm_get_populations), velocities v (q1 integers, host memory).
+ *   out: device pointer to 6 doubles: mass, jx, jy, energy (sum |v|^2 f),
+ *        rho_min, theta_min, with the moment definitions of this header.
+ * Runs on `stream` (cudaStream_t, NULL = default) of the current device and
+ * returns without synchronising.  The first call on a device looks up the
+ * scratch array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture starts.  All calls share the one array: calls that
+ * overlap on the GPU race and may return wrong sums, so serialise them.
+ * Errors: PLBM_E_ARG for bad arguments or nx * ny > PLBM_NOALLOC_MAX_NODES,
+ * PLBM_E_CUDA for a failed lookup or launch (text in plbm_last_error(NULL)). */
+plbm_status plbm_diagnostics_noalloc(int dim, int q1, const int *v, int nx, int ny, const double *f,
+                                     double *out, void *stream);
+
 /* Text of the last error of h (or of the calling thread when h is NULL). */
 const char *plbm_last_error(plbm_handle h);
 

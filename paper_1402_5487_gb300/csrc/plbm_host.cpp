@@ -239,6 +239,10 @@ struct Staging {
 
 }  // namespace
 
+namespace plbm {
+void set_thread_error(const char* msg) { std::snprintf(g_thread_error, sizeof g_thread_error, "%s", msg); }
+}  // namespace plbm
+
 extern "C" {
 
 int plbm_abi_version(void) { return PLBM_ABI_VERSION; }

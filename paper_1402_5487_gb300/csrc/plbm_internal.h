@@ -53,6 +53,9 @@ struct LatticeParams {
     double* partials;            // reduction scratch, kPartialStride doubles per block
 };
 
+// Records the error text returned by plbm_last_error(NULL) for this thread.
+void set_thread_error(const char* msg);
+
 // Launchers implemented in the CUDA translation units.  All are asynchronous
 // on `stream` and return the launch error.
 cudaError_t launch_step(int prec, const LatticeParams& P, const void* src, void* dst,

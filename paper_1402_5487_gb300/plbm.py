@@ -99,6 +99,9 @@ SIGNATURES = {
     "plbm_get_info": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_size_t)]),
     "plbm_device_populations": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_void_p)]),
+    "plbm_diagnostics_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                                 ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                                 ctypes.c_void_p, ctypes.c_void_p]),
     "plbm_last_error": (ctypes.c_char_p, [_H]),
     "plbm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
