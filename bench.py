@@ -40,6 +40,28 @@ THETA0 = 1.0
 ELEM = {"f64": 8, "f32": 4, "f16dev": 2, "bf16dev": 2}
 
 
+KERNEL_NAME = {"f32": "k_stream_collide_pair<float>", "f16dev": "k_stream_collide_pair<__half>",
+               "bf16dev": "k_stream_collide_pair<__nv_bfloat16>", "f64": "k_stream_collide<double,5,2>"}
+
+
+def read_traffic(prec):
+    """DRAM bytes per launch from the committed ncu capture, or None when absent or
+    when the kernel sources changed since the counters were taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            d = json.load(fh)[KERNEL_NAME[prec]]
+        h = hashlib.sha256()
+        for f in d["kernel_sources"]:
+            with open(os.path.join(ROOT, f), "rb") as fh:
+                h.update(fh.read())
+        if h.hexdigest() != d["kernel_sources_sha256"]:
+            return None
+        return float(d["bytes_per_launch"])
+    except Exception:
+        return None
+
+
 def read_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -329,10 +351,10 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
                 "config": config, "healthy": healthy,
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "traffic": None,
-                             "peak_source": peak_kind,
+                             "frac": achieved / peak, "traffic": read_traffic(args.prec),
+                             "peak_source": peak_kind + " (copy bandwidth, MEASURED_PEAKS.json hbm_gbs)",
                              "algorithmic_bytes_per_launch": alg_bytes,
-                             "kernel": "k_stream_collide<float,5,2>"},
+                             "kernel": KERNEL_NAME[args.prec]},
                 "e2e": e2e, "gpu_launches": args.steps, "clocks": clock_info,
                 "cpu_baseline": cpu, "variants": variants}
         print(json.dumps(line))
