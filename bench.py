@@ -169,6 +169,42 @@ def run_variant(torch, L, prec, steps, warmup, barrier, dim=2, v=V5, bc="periodi
             "status": "ok" if st == 0 else "diverged"}
 
 
+def run_batched(torch, steps=100, warmup=4, n=256):
+    """Batched sweep of n admissible instances (FP32): persistent graph vs per-instance launches."""
+    from paper_1402_5487_gb300 import batch as B
+    t0 = time.perf_counter()
+    inst, stats = B.draw_instances(n)
+    t_draw = time.perf_counter() - t0
+    b = B.Batch(inst, prec="f32")
+    b.init()
+    cache = os.path.join(ROOT, "paper_1402_5487_gb300", "_build", "autotune.json")
+    tuned = b.autotune(steps_per_trial=6, cache_path=cache)
+    b.init()
+    nodes = b.nodes
+    out = {"instances": n, "nodes": nodes, "draw_seconds": t_draw, "acceptance": stats["acceptance"],
+           "autotune": tuned, "launch": b.info()}
+    st = b.stream
+    for mode in ("persistent_graph", "persistent", "per_instance", "per_instance_graph"):
+        b.step(warmup, mode)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        b.step(steps, mode)
+        e1.record(st)
+        e1.synchronize()
+        t = e0.elapsed_time(e1) * 1e-3
+        out[mode] = {"mlups": nodes * steps / t / 1e6, "ms_per_step": t / steps * 1e3,
+                     "gbs_algorithmic": 200.0 * nodes * steps / t / 1e9}
+    out["speedup_persistent_graph_vs_per_instance"] = (out["persistent_graph"]["mlups"] /
+                                                      out["per_instance"]["mlups"])
+    out["speedup_persistent_graph_vs_per_instance_graph"] = (out["persistent_graph"]["mlups"] /
+                                                            out["per_instance_graph"]["mlups"])
+    out["status"] = "ok" if b.check()[0] == 0 else "diverged"
+    b.close()
+    return out
+
+
 def cpu_oracle_sample(L, seconds=12.0, max_steps=50):
     """Time the FP64 oracle as it stands on this host's cores on an L x L KH grid."""
     import oracle as O
@@ -232,6 +268,8 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-instances", type=int, default=256)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -336,6 +374,8 @@ def main():
         variants["shock1000_d1q5_f64"] = run_variant(
             torch, 1000, "f64", 500, 20, lambda: None, dim=1, bc="fixed",
             fields=I.shock_tube_fields(1000, left, right), theta0=0.5, omega=1.5, left=left, right=right)
+        if not args.no_batch:
+            variants["batched_%d_f32" % args.batch_instances] = run_batched(torch, n=args.batch_instances)
         base = value / ws
         for k, vv in variants.items():
             if k.startswith("kh%d_" % L):

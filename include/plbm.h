@@ -119,6 +119,30 @@ int plbm_abi_version(void);
  * Errors: PLBM_E_ARG for q1 out of range or repeated velocities. */
 plbm_status plbm_coefficients(int q1, const int *v, double *C_out);
 
+/* Positivity range of Sec. 3.1 for the lattice described by desc: *min_r =
+ * min over i and over |u| <= u_max (401 samples along one axis) of r_i(u, theta0)
+ * (Eq. eq:rdr).  The rule is admissible there when *min_r >= 0; plbm_create runs
+ * the same test with desc->u_max.  Host computation (no GPU). */
+plbm_status plbm_positivity(const plbm_desc *desc, double u_max, double *min_r);
+
+/* Linear (von Neumann) stability of the lattice described by desc around the
+ * uniform state f^eq(rho = 1, u = (ux, 0), theta0): the largest |lambda| of the
+ * one-step operator A(k) = J S(k) over the wave vectors k = 2 pi (a, b) / nk,
+ * where S(k) = diag(exp(-i k.v_p)) is the pull of Eq. (eq:srt) and J the
+ * Jacobian of its BGK collision with the equilibrium of Eq. (eq:rdr) (exact to
+ * rounding, complex-step).  The lattice is linearly stable there when the
+ * result is <= 1 (up to rounding: conserved modes sit at exactly 1).  Both
+ * k axes are also scanned at 8 nk points (narrow unstable bands of tensor-
+ * product lattices lie there).  For symmetric velocity sets only
+ * 0 <= k_y <= pi is scanned (mirror symmetry).
+ * stop_above > 0 lets the scan stop at the first |lambda| above that value (the
+ * result is then a lower bound above it); 0 scans every k.  Host computation
+ * (no GPU), multithreaded over k.  Used to screen parameter draws of batched
+ * sweeps.  Errors: PLBM_E_ARG for an invalid descriptor, nk outside 1..256 or
+ * a non-finite ux. */
+plbm_status plbm_linear_stability(const plbm_desc *desc, double ux, int nk, double stop_above,
+                                  double *max_abs_lambda);
+
 /* Device bytes a handle with this descriptor needs (two population arrays,
  * reduction scratch, status words).  Returns 0 for an invalid descriptor. */
 size_t plbm_workspace_bytes(const plbm_desc *desc);
@@ -183,6 +207,68 @@ plbm_status plbm_get_info(plbm_handle h, int *q, int *pitch, size_t *population_
 /* Raw device pointer of the current population array (storage layout
  * [q][ny][pitch] in the handle's precision).  For profiling and tests. */
 plbm_status plbm_device_populations(plbm_handle h, void **ptr);
+
+/* ------------------------------------------------------------------------
+ * Batched runner: many independent lattices advanced together.
+ * The paper runs one lattice at a time; batching is a throughput service for
+ * parameter sweeps over its models.  Each instance is an ordinary handle
+ * (plbm_batch_instance) for init, moments, diagnostics and checkpoints; the
+ * batch advances all of them with one of four launch schemes:
+ *   PLBM_BATCH_PERSISTENT           one persistent launch per step for all
+ *                                   instances (CTAs walk contiguous ranges of a
+ *                                   global tile list; per-instance parameters in
+ *                                   a device table);
+ *   PLBM_BATCH_PERSISTENT_GRAPH     the same, two steps per CUDA graph replay;
+ *   PLBM_BATCH_PER_INSTANCE         one launch per instance per step;
+ *   PLBM_BATCH_PER_INSTANCE_GRAPH   the same, captured in a CUDA graph.
+ * All four give bit-identical populations.
+ * ------------------------------------------------------------------------ */
+typedef struct plbm_batch_s *plbm_batch;
+
+#define PLBM_BATCH_PERSISTENT 0
+#define PLBM_BATCH_PERSISTENT_GRAPH 1
+#define PLBM_BATCH_PER_INSTANCE 2
+#define PLBM_BATCH_PER_INSTANCE_GRAPH 3
+
+/* Create n instances from n descriptors (same precision and device; each 2D,
+ * periodic, thermal, v = (0, a, -a, b, -b) with 0 < a != b, even ny, FP32/FP16/BF16
+ * storage; each passes plbm_create's checks).  One device allocation holds all
+ * instances; descs[i].workspace and .stream are ignored.  stream: cudaStream_t
+ * for every launch (NULL: the batch creates its own non-blocking stream, as graph
+ * capture cannot use the legacy default stream).  Synchronous. */
+plbm_status plbm_batch_create(const plbm_desc *descs, int n, void *stream, plbm_batch *out);
+
+/* Release the batch, its instances and its memory.  Accepts NULL. */
+plbm_status plbm_batch_destroy(plbm_batch b);
+
+/* Handle of instance i (owned by the batch; plbm_destroy refuses it). */
+plbm_status plbm_batch_instance(plbm_batch b, int i, plbm_handle *h);
+
+/* Advance every instance n steps (Eq. eq:srt) with launch scheme `mode`.  All
+ * instances must be initialised and at the same step parity.  Asynchronous. */
+plbm_status plbm_batch_step(plbm_batch b, long n, int mode);
+
+/* Read every instance's status word (synchronous).  PLBM_E_DIVERGED names the
+ * first bad instance in *first_bad (else -1). */
+plbm_status plbm_batch_check(plbm_batch b, int *first_bad);
+
+/* Launch shape of the persistent kernel: block_x in {64, 128, 256} threads (one
+ * tile = block_x node pairs of one pair row), ctas_per_sm persistent CTAs per SM
+ * (0 = as many as fit). */
+plbm_status plbm_batch_set_config(plbm_batch b, int block_x, int ctas_per_sm);
+
+/* Current launch shape and the occupancy limit for it. */
+plbm_status plbm_batch_info(plbm_batch b, int *ninst, int *total_tiles, int *block_x, int *ctas,
+                            int *max_ctas_per_sm);
+
+/* Autotuner: times steps_per_trial persistent steps for every block_x and every
+ * ctas_per_sm up to the occupancy limit and keeps the fastest.  It advances the
+ * instances (initialise them again afterwards if the state matters). */
+plbm_status plbm_batch_tune(plbm_batch b, int steps_per_trial, int *best_block_x, int *best_ctas_per_sm,
+                            double *best_ms_per_step);
+
+/* Text of the last error of the batch (or of the calling thread when NULL). */
+const char *plbm_batch_last_error(plbm_batch b);
 
 /* Largest lattice (nx * ny nodes) plbm_diagnostics_noalloc accepts: its
  * static scratch array holds one 64-byte record per 256 nodes (1 MiB). */

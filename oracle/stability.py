@@ -49,14 +49,21 @@ def hydro_modes(lat: Lattice, k: float, rho=1.0, ux=0.0, uy=0.0, theta=None, J=N
     return lam[np.argsort(-np.abs(lam))]
 
 
-def spectral_radius(lat: Lattice, n=32, rho=1.0, ux=0.0, uy=0.0, theta=None) -> float:
+def spectral_radius(lat: Lattice, n=32, rho=1.0, ux=0.0, uy=0.0, theta=None, axis_refine=1) -> float:
+    """max |lambda| over the k-grid 2 pi (a, b) / n; with axis_refine > 1 the two k
+    axes are also sampled at n * axis_refine points."""
     J = collision_jacobian(lat, rho, ux, uy, theta)
     ks = 2.0 * np.pi * np.arange(n) / n
+    pts = [(kx, ky) for kx in ks for ky in (ks if lat.dim == 2 else [0.0])]
+    if axis_refine > 1:
+        fine = 2.0 * np.pi * np.arange(n * axis_refine) / (n * axis_refine)
+        pts += [(k, 0.0) for k in fine]
+        if lat.dim == 2:
+            pts += [(0.0, k) for k in fine]
     best = 0.0
-    for kx in ks:
-        for ky in (ks if lat.dim == 2 else [0.0]):
-            lam = np.linalg.eigvals(step_operator(lat, J, kx, ky))
-            best = max(best, float(np.max(np.abs(lam))))
+    for kx, ky in pts:
+        lam = np.linalg.eigvals(step_operator(lat, J, kx, ky))
+        best = max(best, float(np.max(np.abs(lam))))
     return best
 
 

@@ -21,6 +21,7 @@ LIB = os.path.join(BUILD, "libplbm.so")
 
 SOURCES = [
     "plbm_host.cpp",
+    "plbm_stability.cpp",
     "plbm_aux.cu",
     "plbm_step_f64.cu",
     "plbm_step_f32.cu",

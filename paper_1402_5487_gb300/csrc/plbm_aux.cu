@@ -13,6 +13,32 @@ cudaError_t launch_step_f32(const LatticeParams&, const void*, void*, bool, cuda
 cudaError_t launch_step_f16(const LatticeParams&, const void*, void*, bool, cudaStream_t);
 cudaError_t launch_step_bf16(const LatticeParams&, const void*, void*, bool, cudaStream_t);
 
+cudaError_t launch_batch_f32(const PairParams*, int, int, int, int, int, cudaStream_t);
+cudaError_t launch_batch_f16(const PairParams*, int, int, int, int, int, cudaStream_t);
+cudaError_t launch_batch_bf16(const PairParams*, int, int, int, int, int, cudaStream_t);
+cudaError_t batch_occupancy_f32(int, int*);
+cudaError_t batch_occupancy_f16(int, int*);
+cudaError_t batch_occupancy_bf16(int, int*);
+
+cudaError_t launch_batch(int prec, const PairParams* inst, int ninst, int total_tiles, int block_x,
+                         int ctas, int parity, cudaStream_t stream) {
+    switch (prec) {
+        case kF32: return launch_batch_f32(inst, ninst, total_tiles, block_x, ctas, parity, stream);
+        case kF16Dev: return launch_batch_f16(inst, ninst, total_tiles, block_x, ctas, parity, stream);
+        case kBF16Dev: return launch_batch_bf16(inst, ninst, total_tiles, block_x, ctas, parity, stream);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t batch_occupancy(int prec, int block_x, int* blocks_per_sm) {
+    switch (prec) {
+        case kF32: return batch_occupancy_f32(block_x, blocks_per_sm);
+        case kF16Dev: return batch_occupancy_f16(block_x, blocks_per_sm);
+        case kBF16Dev: return batch_occupancy_bf16(block_x, blocks_per_sm);
+    }
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_step(int prec, const LatticeParams& P, const void* src, void* dst, bool reduce,
                         cudaStream_t stream) {
     switch (prec) {

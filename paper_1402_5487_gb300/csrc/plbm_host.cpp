@@ -39,6 +39,7 @@ struct Handle {
     long long steps = 0;
     plbm_status sticky = PLBM_OK;
     bool initialised = false;
+    bool in_batch = false;     // owned by a plbm_batch: not destroyable on its own
     char err[512] = "";
 };
 
@@ -253,6 +254,41 @@ plbm_status plbm_coefficients(int q1, const int* v, double* C_out) {
     return PLBM_OK;
 }
 
+plbm_status plbm_positivity(const plbm_desc* desc, double u_max, double* min_r) {
+    if (!min_r || !(u_max >= 0.0) || !std::isfinite(u_max)) {
+        set_err(nullptr, "bad arguments");
+        return PLBM_E_ARG;
+    }
+    plbm_status st = validate(desc, nullptr);
+    if (st != PLBM_OK) return st;
+    double C[plbm::kMaxQ1 * plbm::kMaxQ1];
+    if (!lagrange_coefficients(desc->q1, desc->v, C)) {
+        set_err(nullptr, "velocities must be distinct");
+        return PLBM_E_ARG;
+    }
+    double wu = 0.0;
+    admissible(desc->q1, C, desc->theta0, u_max, &wu, min_r);
+    return PLBM_OK;
+}
+
+plbm_status plbm_linear_stability(const plbm_desc* desc, double ux, int nk, double stop_above,
+                                  double* max_abs_lambda) {
+    if (!max_abs_lambda || nk < 1 || nk > 256 || !std::isfinite(ux)) {
+        set_err(nullptr, "bad arguments");
+        return PLBM_E_ARG;
+    }
+    plbm_status st = validate(desc, nullptr);
+    if (st != PLBM_OK) return st;
+    double C[plbm::kMaxQ1 * plbm::kMaxQ1];
+    if (!lagrange_coefficients(desc->q1, desc->v, C)) {
+        set_err(nullptr, "velocities must be distinct");
+        return PLBM_E_ARG;
+    }
+    *max_abs_lambda = plbm::spectral_radius(desc->dim, desc->q1, desc->v, C, desc->omega, desc->theta0,
+                                            (desc->flags & PLBM_FLAG_ISOTHERMAL) != 0, ux, nk, stop_above);
+    return PLBM_OK;
+}
+
 size_t plbm_workspace_bytes(const plbm_desc* desc) {
     if (validate(desc, nullptr) != PLBM_OK) return 0;
     return layout_of(desc).total;
@@ -414,7 +450,12 @@ plbm_status plbm_create(const plbm_desc* desc, plbm_handle* out) {
 }
 
 plbm_status plbm_destroy(plbm_handle hh) {
-    free_handle(reinterpret_cast<Handle*>(hh));
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (h && h->in_batch) {
+        set_err(h, "instance handles of a batch are released by plbm_batch_destroy");
+        return PLBM_E_STATE;
+    }
+    free_handle(h);
     return PLBM_OK;
 }
 
@@ -625,6 +666,369 @@ const char* plbm_status_string(plbm_status s) {
         case PLBM_E_NOMEM: return "PLBM_E_NOMEM";
     }
     return "PLBM_E_UNKNOWN";
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched runner.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Batch {
+    std::vector<Handle*> inst;
+    int prec = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool owns_stream = false;
+    char* ws = nullptr;
+    plbm::PairParams* d_table = nullptr;
+    std::vector<plbm::PairParams> table;
+    int block_x = 128, ctas_per_sm = 0, sms = 0, total_tiles = 0;
+    cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [kind][start parity]
+    long long steps = 0;
+    char err[512] = "";
+};
+
+void batch_err(Batch* b, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    std::snprintf(g_thread_error, sizeof g_thread_error, "%s", buf);
+    if (b) std::snprintf(b->err, sizeof b->err, "%s", buf);
+}
+
+#define BCK(call)                                                                  \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            batch_err(b, "%s failed: %s", #call, cudaGetErrorString(e_));          \
+            return PLBM_E_CUDA;                                                    \
+        }                                                                          \
+    } while (0)
+
+void drop_graphs(Batch* b) {
+    for (auto& row : b->graph)
+        for (auto& g : row)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+}
+
+int batch_ctas(Batch* b, int* occ_out = nullptr) {
+    int occ = 0;
+    if (plbm::batch_occupancy(b->prec, b->block_x, &occ) != cudaSuccess || occ < 1) occ = 1;
+    if (occ_out) *occ_out = occ;
+    const int per_sm = b->ctas_per_sm > 0 ? std::min(b->ctas_per_sm, occ) : occ;
+    return b->sms * per_sm;
+}
+
+plbm_status batch_table(Batch* b) {
+    int tile = 0;
+    for (size_t i = 0; i < b->inst.size(); ++i) {
+        plbm::PairParams& Q = b->table[i];
+        Q.tiles_x = (Q.nx + b->block_x - 1) / b->block_x;
+        Q.tile_begin = tile;
+        tile += Q.tiles_x * Q.half_ny;
+    }
+    b->total_tiles = tile;
+    BCK(cudaMemcpyAsync(b->d_table, b->table.data(), sizeof(plbm::PairParams) * b->table.size(),
+                        cudaMemcpyHostToDevice, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    drop_graphs(b);
+    return PLBM_OK;
+}
+
+void free_batch(Batch* b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    drop_graphs(b);
+    for (Handle* h : b->inst) {
+        if (!h) continue;
+        h->in_batch = false;
+        free_handle(h);
+    }
+    if (b->ws) cudaFree(b->ws);
+    if (b->owns_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+// One step of every instance with the chosen launch scheme (no graph).
+plbm_status batch_launch(Batch* b, int scheme, int parity, int ctas) {
+    if (scheme == 0) {
+        BCK(plbm::launch_batch(b->prec, b->d_table, (int)b->inst.size(), b->total_tiles, b->block_x,
+                               ctas, parity, b->stream));
+    } else {
+        for (Handle* h : b->inst)
+            BCK(plbm::launch_step(b->prec, h->P, h->f[parity], h->f[parity ^ 1], false, b->stream));
+    }
+    return PLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+plbm_status plbm_batch_create(const plbm_desc* descs, int n, void* stream, plbm_batch* out) {
+    if (!out || !descs || n < 1) {
+        batch_err(nullptr, "bad arguments");
+        return PLBM_E_ARG;
+    }
+    *out = nullptr;
+    Batch* b = new (std::nothrow) Batch();
+    if (!b) return PLBM_E_NOMEM;
+    b->prec = (int)descs[0].prec;
+    b->device = descs[0].device;
+    std::vector<size_t> off(n);
+    size_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        const plbm_desc& d = descs[i];
+        if ((int)d.prec != b->prec || d.device != b->device) {
+            batch_err(b, "instance %d: all instances need the same precision and device", i);
+            delete b;
+            return PLBM_E_ARG;
+        }
+        const size_t need = plbm_workspace_bytes(&d);
+        if (need == 0) {
+            batch_err(b, "instance %d: %s", i, g_thread_error);
+            delete b;
+            return PLBM_E_ARG;
+        }
+        off[i] = total;
+        total += align_up(need, 256);
+    }
+    const size_t table_off = total;
+    total += align_up(sizeof(plbm::PairParams) * n, 256);
+    if (cudaSetDevice(b->device) != cudaSuccess) {
+        batch_err(b, "cudaSetDevice(%d) failed", b->device);
+        delete b;
+        return PLBM_E_CUDA;
+    }
+    if (stream) {
+        b->stream = static_cast<cudaStream_t>(stream);
+    } else {
+        // graph capture needs a stream other than the legacy default stream
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            batch_err(b, "cudaStreamCreate failed");
+            delete b;
+            return PLBM_E_CUDA;
+        }
+        b->owns_stream = true;
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, total);
+    if (e != cudaSuccess) {
+        batch_err(b, "cudaMalloc(%zu) failed: %s", total, cudaGetErrorString(e));
+        free_batch(b);
+        return PLBM_E_NOMEM;
+    }
+    b->ws = static_cast<char*>(p);
+    b->d_table = reinterpret_cast<plbm::PairParams*>(b->ws + table_off);
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
+    b->inst.assign(n, nullptr);
+    b->table.resize(n);
+    for (int i = 0; i < n; ++i) {
+        plbm_desc d = descs[i];
+        d.workspace = b->ws + off[i];
+        d.workspace_bytes = align_up(plbm_workspace_bytes(&descs[i]), 256);
+        d.stream = b->stream;
+        plbm_handle hh = nullptr;
+        plbm_status st = plbm_create(&d, &hh);
+        if (st != PLBM_OK) {
+            batch_err(b, "instance %d: %s", i, g_thread_error);
+            free_batch(b);
+            return st;
+        }
+        Handle* h = reinterpret_cast<Handle*>(hh);
+        h->in_batch = true;
+        b->inst[i] = h;
+        if (!h->P.paired) {
+            batch_err(b, "instance %d: the batched runner needs 2D periodic thermal lattices with "
+                         "v = (0, a, -a, b, -b), an even row count and FP32/FP16/BF16 storage", i);
+            free_batch(b);
+            return PLBM_E_ARG;
+        }
+        plbm::PairParams Q = plbm::pair_params(h->P);
+        Q.f[0] = h->f[0];
+        Q.f[1] = h->f[1];
+        b->table[i] = Q;
+    }
+    plbm_status st = batch_table(b);
+    if (st != PLBM_OK) {
+        free_batch(b);
+        return st;
+    }
+    *out = reinterpret_cast<plbm_batch>(b);
+    return PLBM_OK;
+}
+
+plbm_status plbm_batch_destroy(plbm_batch bb) {
+    free_batch(reinterpret_cast<Batch*>(bb));
+    return PLBM_OK;
+}
+
+plbm_status plbm_batch_instance(plbm_batch bb, int i, plbm_handle* out) {
+    Batch* b = reinterpret_cast<Batch*>(bb);
+    if (!b || !out || i < 0 || i >= (int)b->inst.size()) {
+        batch_err(b, "bad arguments");
+        return PLBM_E_ARG;
+    }
+    *out = reinterpret_cast<plbm_handle>(b->inst[i]);
+    return PLBM_OK;
+}
+
+plbm_status plbm_batch_step(plbm_batch bb, long n, int mode) {
+    Batch* b = reinterpret_cast<Batch*>(bb);
+    if (!b || n < 0 || mode < 0 || mode > 3) {
+        batch_err(b, "bad arguments");
+        return PLBM_E_ARG;
+    }
+    const int parity0 = b->inst[0]->cur;
+    for (size_t i = 0; i < b->inst.size(); ++i) {
+        Handle* h = b->inst[i];
+        if (h->sticky != PLBM_OK || !h->initialised) {
+            batch_err(b, "instance %zu is not initialised or in an error state", i);
+            return PLBM_E_STATE;
+        }
+        if (h->cur != parity0) {
+            batch_err(b, "instance %zu was stepped on its own; all instances must be in step", i);
+            return PLBM_E_STATE;
+        }
+    }
+    BCK(cudaSetDevice(b->device));
+    const int scheme = (mode == PLBM_BATCH_PERSISTENT || mode == PLBM_BATCH_PERSISTENT_GRAPH) ? 0 : 1;
+    const bool use_graph = (mode == PLBM_BATCH_PERSISTENT_GRAPH || mode == PLBM_BATCH_PER_INSTANCE_GRAPH);
+    int parity = parity0;
+    long done = 0;
+    const int ctas = batch_ctas(b);  // occupancy query outside any stream capture
+    if (use_graph) {
+        for (; done + 2 <= n; done += 2) {
+            cudaGraphExec_t& g = b->graph[scheme][parity];
+            if (!g) {
+                cudaGraph_t graph = nullptr;
+                BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+                plbm_status st = batch_launch(b, scheme, parity, ctas);
+                if (st == PLBM_OK) st = batch_launch(b, scheme, parity ^ 1, ctas);
+                cudaError_t ec = cudaStreamEndCapture(b->stream, &graph);
+                if (st != PLBM_OK) return st;
+                BCK(ec);
+                cudaError_t ei = cudaGraphInstantiate(&g, graph, 0);
+                cudaGraphDestroy(graph);
+                BCK(ei);
+            }
+            BCK(cudaGraphLaunch(g, b->stream));
+        }
+    }
+    for (; done < n; ++done) {
+        plbm_status st = batch_launch(b, scheme, parity, ctas);
+        if (st != PLBM_OK) return st;
+        parity ^= 1;
+    }
+    if (n % 2) parity = parity0 ^ 1; else parity = parity0;
+    for (Handle* h : b->inst) {
+        h->cur = parity;
+        h->steps += n;
+    }
+    b->steps += n;
+    return PLBM_OK;
+}
+
+plbm_status plbm_batch_check(plbm_batch bb, int* first_bad) {
+    Batch* b = reinterpret_cast<Batch*>(bb);
+    if (!b) return PLBM_E_ARG;
+    if (first_bad) *first_bad = -1;
+    std::vector<unsigned> bits(b->inst.size(), 0u);
+    for (size_t i = 0; i < b->inst.size(); ++i)
+        BCK(cudaMemcpyAsync(&bits[i], b->inst[i]->status, sizeof(unsigned), cudaMemcpyDeviceToHost, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    for (size_t i = 0; i < bits.size(); ++i)
+        if (bits[i]) {
+            if (first_bad) *first_bad = (int)i;
+            batch_err(b, "instance %zu diverged (status 0x%x)", i, bits[i]);
+            return PLBM_E_DIVERGED;
+        }
+    return PLBM_OK;
+}
+
+plbm_status plbm_batch_set_config(plbm_batch bb, int block_x, int ctas_per_sm) {
+    Batch* b = reinterpret_cast<Batch*>(bb);
+    if (!b || (block_x != 64 && block_x != 128 && block_x != 256) || ctas_per_sm < 0 || ctas_per_sm > 64) {
+        batch_err(b, "block_x must be 64, 128 or 256 and 0 <= ctas_per_sm <= 64");
+        return PLBM_E_ARG;
+    }
+    b->block_x = block_x;
+    b->ctas_per_sm = ctas_per_sm;
+    return batch_table(b);
+}
+
+plbm_status plbm_batch_info(plbm_batch bb, int* ninst, int* total_tiles, int* block_x, int* ctas,
+                            int* max_ctas_per_sm) {
+    Batch* b = reinterpret_cast<Batch*>(bb);
+    if (!b) return PLBM_E_ARG;
+    int occ = 0;
+    const int c = batch_ctas(b, &occ);
+    if (ninst) *ninst = (int)b->inst.size();
+    if (total_tiles) *total_tiles = b->total_tiles;
+    if (block_x) *block_x = b->block_x;
+    if (ctas) *ctas = c;
+    if (max_ctas_per_sm) *max_ctas_per_sm = occ;
+    return PLBM_OK;
+}
+
+plbm_status plbm_batch_tune(plbm_batch bb, int steps_per_trial, int* best_block_x, int* best_ctas_per_sm,
+                            double* best_ms_per_step) {
+    Batch* b = reinterpret_cast<Batch*>(bb);
+    if (!b || steps_per_trial < 1) return PLBM_E_ARG;
+    for (Handle* h : b->inst)
+        if (!h->initialised) {
+            batch_err(b, "initialise every instance before tuning");
+            return PLBM_E_STATE;
+        }
+    cudaEvent_t e0, e1;
+    BCK(cudaEventCreate(&e0));
+    BCK(cudaEventCreate(&e1));
+    double best = 1e300;
+    int bx_best = 128, cps_best = 0;
+    const int bxs[3] = {64, 128, 256};
+    for (int bx : bxs) {
+        int occ = 0;
+        if (plbm::batch_occupancy(b->prec, bx, &occ) != cudaSuccess || occ < 1) continue;
+        for (int cps = 1; cps <= occ; ++cps) {
+            plbm_status st = plbm_batch_set_config(bb, bx, cps);
+            if (st != PLBM_OK) return st;
+            st = plbm_batch_step(bb, 2, PLBM_BATCH_PERSISTENT);
+            if (st != PLBM_OK) return st;
+            BCK(cudaEventRecord(e0, b->stream));
+            st = plbm_batch_step(bb, steps_per_trial, PLBM_BATCH_PERSISTENT);
+            if (st != PLBM_OK) return st;
+            BCK(cudaEventRecord(e1, b->stream));
+            BCK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            BCK(cudaEventElapsedTime(&ms, e0, e1));
+            const double per = ms / steps_per_trial;
+            if (per < best) {
+                best = per;
+                bx_best = bx;
+                cps_best = cps;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    plbm_status st = plbm_batch_set_config(bb, bx_best, cps_best);
+    if (st != PLBM_OK) return st;
+    if (best_block_x) *best_block_x = bx_best;
+    if (best_ctas_per_sm) *best_ctas_per_sm = cps_best;
+    if (best_ms_per_step) *best_ms_per_step = best;
+    return PLBM_OK;
+}
+
+const char* plbm_batch_last_error(plbm_batch bb) {
+    Batch* b = reinterpret_cast<Batch*>(bb);
+    return b ? b->err : g_thread_error;
 }
 
 }  // extern "C"

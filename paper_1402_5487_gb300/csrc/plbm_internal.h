@@ -53,6 +53,57 @@ struct LatticeParams {
     double* partials;            // reduction scratch, kPartialStride doubles per block
 };
 
+// Compact parameters of the row-paired kernel (one lattice).  The batched
+// runner keeps one per instance in device memory and caches it in shared memory.
+struct PairParams {
+    int nx, ny, half_ny, pitch;   // pitch in elements of one row (pairs per pair row)
+    long long plane2;             // pairs per population plane (= half_ny * pitch)
+    int vxm[5], vym[5];
+    float sa, sb, sa2, sb2, kOa, kOb, kEa, kEb;
+    float w1f[5];
+    float omegaf, theta0f;
+    double theta0;
+    unsigned* status;
+    double* partials;
+    void* f[2];                   // population arrays (batched runner; unused by single launches)
+    int tile_begin, tiles_x;      // batched runner: first global tile, tiles per pair row
+};
+
+inline PairParams pair_params(const LatticeParams& P) {
+    PairParams Q{};
+    Q.nx = P.nx;
+    Q.ny = P.ny;
+    Q.half_ny = P.half_ny;
+    Q.pitch = P.pitch;
+    Q.plane2 = (long long)P.half_ny * P.pitch;
+    for (int i = 0; i < 5; ++i) {
+        Q.vxm[i] = P.vxm[i];
+        Q.vym[i] = P.vym[i];
+        Q.w1f[i] = P.w1f[i];
+    }
+    Q.sa = P.sa;
+    Q.sb = P.sb;
+    Q.sa2 = P.sa2;
+    Q.sb2 = P.sb2;
+    Q.kOa = P.kOa;
+    Q.kOb = P.kOb;
+    Q.kEa = P.kEa;
+    Q.kEb = P.kEb;
+    Q.omegaf = P.omegaf;
+    Q.theta0f = P.theta0f;
+    Q.theta0 = P.theta0;
+    Q.status = P.status;
+    Q.partials = P.partials;
+    return Q;
+}
+
+// max |lambda| of the one-step operator linearised at f^eq(1, (ux, 0), theta0),
+// over an nk x nk grid of wave vectors (plbm_stability.cpp).  With stop_above > 0
+// the search may stop at the first |lambda| above it (the result is then a lower
+// bound that exceeds stop_above).
+double spectral_radius(int dim, int q1, const int* v, const double* C, double omega, double theta0,
+                       bool isothermal, double ux, int nk, double stop_above);
+
 // Records the error text returned by plbm_last_error(NULL) for this thread.
 void set_thread_error(const char* msg);
 
@@ -74,6 +125,12 @@ cudaError_t launch_get_populations(int prec, const LatticeParams& P, const void*
                                    cudaStream_t stream);
 cudaError_t launch_set_populations(int prec, const LatticeParams& P, const double* in, void* f,
                                    cudaStream_t stream);
+
+// Batched persistent step over the instances of `inst` (device array, tile_begin
+// ascending); block_x in {64, 128, 256}; ctas persistent CTAs.
+cudaError_t launch_batch(int prec, const PairParams* inst, int ninst, int total_tiles, int block_x,
+                         int ctas, int parity, cudaStream_t stream);
+cudaError_t batch_occupancy(int prec, int block_x, int* blocks_per_sm);
 
 // Number of blocks of a step launch (row-paired kernels cover two rows per block row).
 inline int step_blocks(const LatticeParams& P) {

@@ -26,6 +26,7 @@
 #pragma once
 
 #include "plbm_device.cuh"
+#include "plbm_internal.h"
 
 namespace plbm {
 
@@ -73,7 +74,7 @@ struct PairStore<__nv_bfloat16> {
 
 // dmu_1..dmu_4 = mu_n(u, theta) - mu_n(0, theta0) from mu_{n+1} = u mu_n + n theta mu_{n-1}
 // with mu(0, theta0) = (1, 0, theta0, 0, 3 theta0^2), then dr by the constraint form.
-__device__ __forceinline__ void sym5_axis(const LatticeParams& P, float2 u, float2 th, float2 dth,
+__device__ __forceinline__ void sym5_axis(const PairParams& P, float2 u, float2 th, float2 dth,
                                           float2 (&dr)[5]) {
     const float2 th0 = f2s(P.theta0f);
     const float2 d1 = u;
@@ -93,7 +94,7 @@ __device__ __forceinline__ void sym5_axis(const LatticeParams& P, float2 u, floa
 
 // g: pulled deviations of both nodes on entry, post-collision deviations on exit.
 // Returns rho and theta of both nodes (for the status check and reductions).
-__device__ __forceinline__ void sym5_collide(const LatticeParams& P, float2 (&g)[25], float2& rho_o,
+__device__ __forceinline__ void sym5_collide(const PairParams& P, float2 (&g)[25], float2& rho_o,
                                              float2& th_o, float2& drho_o, float2& jx_o, float2& jy_o,
                                              float2& e_o) {
     float2 S[5], T[5];
@@ -162,80 +163,84 @@ __device__ __forceinline__ bool healthy2(float2 rho, float2 th) {
            (rho.x < 3.0e38f) & (rho.y < 3.0e38f) & (th.x < 3.0e38f) & (th.y < 3.0e38f);
 }
 
+// One thread's work: nodes (x, r) and (x, r + ny/2) of one lattice, x < nx.
+template <typename S, bool REDUCE>
+__device__ __forceinline__ void pair_node(const PairParams& P, const typename PairStore<S>::V* __restrict__ src,
+                                          typename PairStore<S>::V* __restrict__ dst, int x, int r,
+                                          NodeDiag& d) {
+    using PS = PairStore<S>;
+    const int H = P.half_ny;
+    const long long plane2 = P.plane2;
+    unsigned col[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const int s = x + P.vxm[i];
+        col[i] = (unsigned)((s >= P.nx) ? s - P.nx : s);
+    }
+    unsigned row[5];
+    bool swp[5];
+    bool any_swap = false;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        int s = r + P.vym[j];
+        s = (s >= P.ny) ? s - P.ny : s;
+        swp[j] = s >= H;
+        any_swap |= swp[j];
+        row[j] = (unsigned)((swp[j] ? s - H : s) * P.pitch);
+    }
+    float2 g[25];
+    if (!any_swap) {
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+#pragma unroll
+            for (int j = 0; j < 5; ++j) {
+                const int p = 5 * i + j;
+                g[p] = PS::load(src + p * plane2 + (row[j] + col[i]));
+            }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+#pragma unroll
+            for (int j = 0; j < 5; ++j) {
+                const int p = 5 * i + j;
+                const typename PS::V* a = src + p * plane2 + (row[j] + col[i]);
+                g[p] = swp[j] ? PS::load_swapped(a) : PS::load(a);
+            }
+    }
+    float2 rho, th, drho, jx, jy, e;
+    sym5_collide(P, g, rho, th, drho, jx, jy, e);
+    if (!healthy2(rho, th)) {
+        unsigned bits = 0u;
+        bits |= (!(rho.x == rho.x) || !(rho.y == rho.y) || !(th.x == th.x) || !(th.y == th.y) ||
+                 !(rho.x < 3.0e38f) || !(rho.y < 3.0e38f) || !(th.x < 3.0e38f) || !(th.y < 3.0e38f))
+                    ? 1u : 0u;
+        bits |= (rho.x <= 0.0f || rho.y <= 0.0f) ? 2u : 0u;
+        bits |= (th.x <= 0.0f || th.y <= 0.0f) ? 4u : 0u;
+        atomicOr(P.status, bits);
+    }
+    if (REDUCE) {
+        d.mass = 2.0 + (double)drho.x + (double)drho.y;
+        d.jx = (double)jx.x + (double)jx.y;
+        d.jy = (double)jy.x + (double)jy.y;
+        d.energy = 4.0 * P.theta0 + (double)e.x + (double)e.y;
+        d.rho_min = fmin((double)rho.x, (double)rho.y);
+        d.theta_min = fmin((double)th.x, (double)th.y);
+    }
+    const unsigned here = (unsigned)(r * P.pitch + x);
+#pragma unroll
+    for (int p = 0; p < 25; ++p) PS::store(dst + p * plane2 + here, g[p]);
+}
+
 // grid = (ceil(nx / kBlockX), ny / 2); thread (x, r) owns nodes (x, r) and (x, r + ny/2).
 template <typename S, bool REDUCE>
 __global__ void __launch_bounds__(kBlockX)
-k_stream_collide_pair(const __grid_constant__ LatticeParams P,
+k_stream_collide_pair(const __grid_constant__ PairParams P,
                       const typename PairStore<S>::V* __restrict__ src,
                       typename PairStore<S>::V* __restrict__ dst) {
-    using PS = PairStore<S>;
     const int x = blockIdx.x * kBlockX + threadIdx.x;
-    const int r = blockIdx.y;
-    const int H = P.half_ny;
-    const long long plane2 = (long long)H * P.pitch;  // pairs per population plane
     NodeDiag d;
     if (REDUCE) diag_zero(d);
-
-    if (x < P.nx) {
-        unsigned col[5];
-#pragma unroll
-        for (int i = 0; i < 5; ++i) {
-            const int s = x + P.vxm[i];
-            col[i] = (unsigned)((s >= P.nx) ? s - P.nx : s);
-        }
-        unsigned row[5];
-        bool swp[5];
-        bool any_swap = false;
-#pragma unroll
-        for (int j = 0; j < 5; ++j) {
-            int s = r + P.vym[j];
-            s = (s >= P.ny) ? s - P.ny : s;
-            swp[j] = s >= H;
-            any_swap |= swp[j];
-            row[j] = (unsigned)((swp[j] ? s - H : s) * P.pitch);
-        }
-        float2 g[25];
-        if (!any_swap) {
-#pragma unroll
-            for (int i = 0; i < 5; ++i)
-#pragma unroll
-                for (int j = 0; j < 5; ++j) {
-                    const int p = 5 * i + j;
-                    g[p] = PS::load(src + p * plane2 + (row[j] + col[i]));
-                }
-        } else {
-#pragma unroll
-            for (int i = 0; i < 5; ++i)
-#pragma unroll
-                for (int j = 0; j < 5; ++j) {
-                    const int p = 5 * i + j;
-                    const typename PS::V* a = src + p * plane2 + (row[j] + col[i]);
-                    g[p] = swp[j] ? PS::load_swapped(a) : PS::load(a);
-                }
-        }
-        float2 rho, th, drho, jx, jy, e;
-        sym5_collide(P, g, rho, th, drho, jx, jy, e);
-        if (!healthy2(rho, th)) {
-            unsigned bits = 0u;
-            bits |= (!(rho.x == rho.x) || !(rho.y == rho.y) || !(th.x == th.x) || !(th.y == th.y) ||
-                     !(rho.x < 3.0e38f) || !(rho.y < 3.0e38f) || !(th.x < 3.0e38f) || !(th.y < 3.0e38f))
-                        ? 1u : 0u;
-            bits |= (rho.x <= 0.0f || rho.y <= 0.0f) ? 2u : 0u;
-            bits |= (th.x <= 0.0f || th.y <= 0.0f) ? 4u : 0u;
-            atomicOr(P.status, bits);
-        }
-        if (REDUCE) {
-            d.mass = 2.0 + (double)drho.x + (double)drho.y;
-            d.jx = (double)jx.x + (double)jx.y;
-            d.jy = (double)jy.x + (double)jy.y;
-            d.energy = 4.0 * P.theta0 + (double)e.x + (double)e.y;
-            d.rho_min = fmin((double)rho.x, (double)rho.y);
-            d.theta_min = fmin((double)th.x, (double)th.y);
-        }
-        const unsigned here = (unsigned)(r * P.pitch + x);
-#pragma unroll
-        for (int p = 0; p < 25; ++p) PS::store(dst + p * plane2 + here, g[p]);
-    }
+    if (x < P.nx) pair_node<S, REDUCE>(P, src, dst, x, blockIdx.y, d);
     if (REDUCE) {
         const int blk = blockIdx.y * gridDim.x + blockIdx.x;
         block_reduce_diag<kBlockX>(d, P.partials + (long long)blk * kPartialStride);
@@ -243,9 +248,10 @@ k_stream_collide_pair(const __grid_constant__ LatticeParams P,
 }
 
 template <typename S>
-cudaError_t launch_step_pair_t(const LatticeParams& P, const void* src, void* dst, bool reduce,
+cudaError_t launch_step_pair_t(const LatticeParams& L, const void* src, void* dst, bool reduce,
                                cudaStream_t stream) {
     using V = typename PairStore<S>::V;
+    const PairParams P = pair_params(L);
     dim3 grid((P.nx + kBlockX - 1) / kBlockX, P.half_ny);
     const V* s = static_cast<const V*>(src);
     V* t = static_cast<V*>(dst);
@@ -254,6 +260,85 @@ cudaError_t launch_step_pair_t(const LatticeParams& P, const void* src, void* ds
     else
         k_stream_collide_pair<S, false><<<grid, kBlockX, 0, stream>>>(P, s, t);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Batched persistent step: every instance of a batch advances one step in one
+// launch.  The instances' tiles (BX threads x one pair row) form one global
+// list; CTA c walks the contiguous range [c * per_cta, (c + 1) * per_cta), so it
+// meets few instance boundaries and keeps the current instance's PairParams in
+// shared memory.  `parity` selects which of each instance's two arrays is read.
+// ---------------------------------------------------------------------------
+template <typename S, int BX>
+__global__ void __launch_bounds__(BX)
+k_batch_pair(const PairParams* __restrict__ inst, int ninst, int total_tiles, int per_cta, int parity) {
+    using V = typename PairStore<S>::V;
+    __shared__ PairParams sp;
+    __shared__ int s_inst;
+    const int t0 = blockIdx.x * per_cta;
+    const int t1 = min(t0 + per_cta, total_tiles);
+    if (t0 >= t1) return;
+    // first instance containing t0 (binary search over tile_begin)
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = ninst - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (inst[mid].tile_begin <= t0) lo = mid; else hi = mid - 1;
+        }
+        s_inst = lo;
+    }
+    __syncthreads();
+    int i = s_inst;
+    int next_begin = (i + 1 < ninst) ? inst[i + 1].tile_begin : total_tiles;
+    constexpr int kWords = (int)(sizeof(PairParams) / sizeof(int));
+    static_assert(sizeof(PairParams) % sizeof(int) == 0, "PairParams copy granularity");
+    for (int k = threadIdx.x; k < kWords; k += BX)
+        reinterpret_cast<int*>(&sp)[k] = reinterpret_cast<const int*>(&inst[i])[k];
+    __syncthreads();
+    NodeDiag d;
+    for (int t = t0; t < t1; ++t) {
+        if (t >= next_begin) {  // block-uniform: move to the instance holding tile t
+            while (t >= next_begin) {
+                ++i;
+                next_begin = (i + 1 < ninst) ? inst[i + 1].tile_begin : total_tiles;
+            }
+            __syncthreads();
+            for (int k = threadIdx.x; k < kWords; k += BX)
+                reinterpret_cast<int*>(&sp)[k] = reinterpret_cast<const int*>(&inst[i])[k];
+            __syncthreads();
+        }
+        const int local = t - sp.tile_begin;
+        const int r = local / sp.tiles_x;
+        const int x = (local - r * sp.tiles_x) * BX + threadIdx.x;
+        if (x < sp.nx) {
+            const V* src = static_cast<const V*>(sp.f[parity]);
+            V* dst = static_cast<V*>(sp.f[parity ^ 1]);
+            pair_node<S, false>(sp, src, dst, x, r, d);
+        }
+    }
+}
+
+template <typename S>
+cudaError_t launch_batch_pair_t(const PairParams* inst, int ninst, int total_tiles, int block_x, int ctas,
+                                int parity, cudaStream_t stream) {
+    const int per_cta = (total_tiles + ctas - 1) / ctas;
+    switch (block_x) {
+        case 64: k_batch_pair<S, 64><<<ctas, 64, 0, stream>>>(inst, ninst, total_tiles, per_cta, parity); break;
+        case 128: k_batch_pair<S, 128><<<ctas, 128, 0, stream>>>(inst, ninst, total_tiles, per_cta, parity); break;
+        case 256: k_batch_pair<S, 256><<<ctas, 256, 0, stream>>>(inst, ninst, total_tiles, per_cta, parity); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t batch_occupancy_t(int block_x, int* blocks_per_sm) {
+    switch (block_x) {
+        case 64: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batch_pair<S, 64>, 64, 0);
+        case 128: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batch_pair<S, 128>, 128, 0);
+        case 256: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batch_pair<S, 256>, 256, 0);
+    }
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace plbm

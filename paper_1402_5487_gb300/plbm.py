@@ -84,6 +84,20 @@ SIGNATURES = {
     "plbm_abi_version": (ctypes.c_int, []),
     "plbm_coefficients": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), _D]),
     "plbm_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(PlbmDesc)]),
+    "plbm_linear_stability": (ctypes.c_int, [ctypes.POINTER(PlbmDesc), ctypes.c_double, ctypes.c_int,
+                                             ctypes.c_double, _D]),
+    "plbm_positivity": (ctypes.c_int, [ctypes.POINTER(PlbmDesc), ctypes.c_double, _D]),
+    "plbm_batch_create": (ctypes.c_int, [ctypes.POINTER(PlbmDesc), ctypes.c_int, ctypes.c_void_p,
+                                         ctypes.POINTER(ctypes.c_void_p)]),
+    "plbm_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "plbm_batch_instance": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(_H)]),
+    "plbm_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_long, ctypes.c_int]),
+    "plbm_batch_check": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    "plbm_batch_set_config": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "plbm_batch_info": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int)] * 5),
+    "plbm_batch_tune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int), _D]),
+    "plbm_batch_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "plbm_create": (ctypes.c_int, [ctypes.POINTER(PlbmDesc), ctypes.POINTER(_H)]),
     "plbm_destroy": (ctypes.c_int, [_H]),
     "plbm_init": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -174,6 +188,24 @@ def make_desc(dim, v, omega, nx, ny=1, theta0=1.0, prec="f32", bc="periodic", le
     return d, keep
 
 
+def linear_stability(dim, v, omega, theta0=1.0, ux=0.0, nk=48, isothermal=False, stop_above=0.0) -> float:
+    """max |lambda| of the library's linearised one-step operator (host computation)."""
+    desc, keep = make_desc(dim, v, omega, 4, 4 if dim == 2 else 1, theta0=theta0, isothermal=isothermal,
+                           skip_admissibility=True)
+    out = ctypes.c_double()
+    _ok(lib().plbm_linear_stability(ctypes.byref(desc), float(ux), int(nk), float(stop_above),
+                                    ctypes.byref(out)))
+    return out.value
+
+
+def positivity(dim, v, theta0=1.0, u_max=0.0) -> float:
+    """min_i min_{|u| <= u_max} r_i(u, theta0) from the library's host code."""
+    desc, keep = make_desc(dim, v, 1.0, 4, 4 if dim == 2 else 1, theta0=theta0, skip_admissibility=True)
+    out = ctypes.c_double()
+    _ok(lib().plbm_positivity(ctypes.byref(desc), float(u_max), ctypes.byref(out)))
+    return out.value
+
+
 def workspace_bytes(desc: PlbmDesc) -> int:
     return int(lib().plbm_workspace_bytes(ctypes.byref(desc)))
 
@@ -229,6 +261,9 @@ class Solver:
 
     # -- lifetime ----------------------------------------------------------
     def close(self):
+        if getattr(self, "_borrowed", False):
+            self.h = None
+            return
         if getattr(self, "h", None):
             lib().plbm_destroy(self.h)
             self.h = None
@@ -324,6 +359,19 @@ class Solver:
         q, pitch, nb = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
         _ok(lib().plbm_get_info(self.h, ctypes.byref(q), ctypes.byref(pitch), ctypes.byref(nb)), self.h)
         return {"q": q.value, "pitch": pitch.value, "population_bytes": nb.value}
+
+    @classmethod
+    def _wrap(cls, h, dim, v, nx, ny, prec, stream, torch):
+        """A Solver view of a handle owned by a batch (not closed by this object)."""
+        s = cls.__new__(cls)
+        s.torch, s.h, s._ws, s._keep = torch, h, None, []
+        s.device = torch.device("cuda", torch.cuda.current_device())
+        s.stream = stream
+        s.dim, s.v, s.q1 = dim, tuple(int(a) for a in v), len(v)
+        s.q = s.q1 ** dim
+        s.nx, s.ny, s.prec = nx, ny, prec
+        s._borrowed = True
+        return s
 
     def device_populations_ptr(self) -> int:
         p = ctypes.c_void_p()

@@ -1,0 +1,109 @@
+"""Batched runner on the GPU: the four launch schemes agree bit for bit, agree
+with single-lattice handles, and match the FP64 oracle per instance."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1402_5487_gb300 import batch as B, build, inputs as I, plbm
+
+from parity_util import field_errors, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    plbm.lib()
+
+
+@pytest.fixture(scope="module")
+def small_instances():
+    inst, _ = B.draw_instances(10, seed=4242, size_lo=16, size_hi=150)
+    return inst
+
+
+def _run(instances, mode, steps, prec="f32", config=None):
+    b = B.Batch(instances, prec=prec)
+    if config:
+        b.set_config(*config)
+    b.init()
+    b.step(steps, mode)
+    pops = [s.get_populations() for s in b.solvers]
+    st = b.check()
+    b.close()
+    return pops, st
+
+
+def test_launch_schemes_bit_identical(small_instances):
+    ref, st = _run(small_instances, "persistent", 7)
+    assert st[0] == plbm.PLBM_OK
+    for mode in ("persistent_graph", "per_instance", "per_instance_graph"):
+        got, _ = _run(small_instances, mode, 7)
+        for a, b in zip(got, ref):
+            assert np.array_equal(a, b), mode
+    for cfg in ((64, 1), (256, 2), (128, 0)):
+        got, _ = _run(small_instances, "persistent_graph", 7, config=cfg)
+        for a, b in zip(got, ref):
+            assert np.array_equal(a, b), cfg
+
+
+def test_batch_equals_single_handles(small_instances):
+    got, _ = _run(small_instances, "persistent_graph", 12)
+    for inst, g in zip(small_instances, got):
+        s = plbm.Solver(2, inst.v, inst.omega, inst.L, inst.L, theta0=inst.theta0, prec="f32")
+        s.init(*I.instance_fields(inst))
+        s.step(12)
+        assert np.array_equal(s.get_populations(), g)
+        s.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("f32", 1e-5), ("f16dev", 5e-3)])
+def test_batch_instances_vs_oracle_100_steps(small_instances, prec, tol):
+    b = B.Batch(small_instances, prec=prec)
+    b.init()
+    b.step(100, "persistent_graph")
+    for inst, s in zip(small_instances, b.solvers):
+        _, _, mo = oracle_run(2, inst.v, inst.omega, inst.L, inst.L, I.instance_fields(inst), 100,
+                              theta0=inst.theta0)
+        mg = s.moments()
+        e = field_errors(mg, mo)
+        # velocity error on the scale of the sweep's largest flow (0.1): 16-bit storage
+        # resolves a 1e-3 shear wave only to about 1 % of its own amplitude
+        du = np.max(np.hypot(mg[1] - mo[1], mg[2] - mo[2])) / 0.1
+        assert e["rho"] <= tol and e["theta"] <= tol and du <= tol, (inst, e, du)
+    assert b.check()[0] == plbm.PLBM_OK
+    b.close()
+
+
+def test_autotune_and_cache(tmp_path, small_instances):
+    b = B.Batch(small_instances)
+    b.init()
+    cache = str(tmp_path / "tune.json")
+    c1 = b.autotune(steps_per_trial=2, cache_path=cache)
+    assert c1["block_x"] in (64, 128, 256) and c1["ctas_per_sm"] >= 1 and not c1["cached"]
+    info = b.info()
+    assert info["block_x"] == c1["block_x"] and info["ctas"] >= 1
+    c2 = b.autotune(cache_path=cache)
+    assert c2["cached"] and c2["block_x"] == c1["block_x"]
+    with pytest.raises(plbm.PlbmError):
+        b.set_config(96, 1)
+    b.close()
+
+
+def test_unstable_instance_is_reported():
+    inst, _ = B.draw_instances(3, seed=99, size_lo=32, size_hi=64)
+    bad = I.Instance(index=3, L=48, v=I.SET_013, omega=1.8, theta0=1.0, kind="kh", seed=5)
+    b = B.Batch(inst + [bad])
+    b.init()
+    b.step(400, "persistent_graph")
+    st, first = b.check()
+    assert st == plbm.PLBM_E_DIVERGED and first == 3
+    b.close()
+
+
+def test_instance_handles_are_owned_by_the_batch(small_instances):
+    b = B.Batch(small_instances[:2])
+    h = b.solvers[0].h
+    assert plbm.lib().plbm_destroy(h) == plbm.PLBM_E_STATE
+    b.close()
