@@ -205,6 +205,122 @@ def run_batched(torch, steps=100, warmup=4, n=256):
     return out
 
 
+def _field_err(mg, mr):
+    rho = float(np.max(np.abs(mg[0] - mr[0])) / np.max(np.abs(mr[0])))
+    u = float(np.max(np.hypot(mg[1] - mr[1], mg[2] - mr[2])) / np.max(np.hypot(mr[1], mr[2])))
+    th = float(np.max(np.abs(mg[3] - mr[3])) / np.max(np.abs(mr[3])))
+    return {"rho": rho, "u": u, "theta": th}
+
+
+def run_surrogate(torch, n_train=2000, n_test=100, train_steps=2000, batch=16, K=32, L=256):
+    """Learned surrogate: data from the batched solver, training, held-out errors, speed."""
+    import oracle as O
+    from paper_1402_5487_gb300 import plbm, surrogate as SG
+    from paper_1402_5487_gb300.batch import Batch
+    out = {"grid": [L, L], "K": K, "train_trajectories": n_train, "test_trajectories": n_test}
+    t0 = time.perf_counter()
+    stack = SG.generate(range(n_train), L=L, K=K, snaps=9)
+    out["generate_seconds"] = time.perf_counter() - t0
+    pairs = SG.pairs_of(n_train, 9)
+    norm = SG.fit_norm(stack, pairs)
+    net = SG.Surrogate(64, L, L, seed=0)
+    net.set_norm(*norm)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = net.train(stack, pairs, train_steps, batch=batch, lr=1e-3, lr_end=1e-4, log_every=train_steps // 4)
+    t_train = time.perf_counter() - t0
+    flops_sample = 3 * 2.0 * L * L * (9 * 4 * 64 + 4 * 9 * 64 * 64 + 9 * 64 * 4)
+    out["training"] = {"steps": train_steps, "batch": batch, "seconds": t_train,
+                       "samples_per_s": train_steps * batch / t_train,
+                       "tflops": train_steps * batch * flops_sample / t_train / 1e12,
+                       "loss": losses}
+    del stack
+    torch.cuda.empty_cache()
+    snaps = 17
+    test_seeds = list(range(10000, 10000 + n_test))
+    tstack = SG.generate(test_seeds, L=L, K=K, snaps=snaps)
+    mse_net, mse_p = net.evaluate(tstack, SG.pairs_of(n_test, snaps))
+    out["test_mse_normalised"] = {"network": mse_net, "persistence": mse_p}
+    # rollouts: the LBM trajectory (FP32, parity-checked against the FP64 oracle) is the judge
+    nroll = min(n_test, 64)
+    solvers = [plbm.Solver(2, SG.V5, SG.OMEGA, L, L, theta0=SG.THETA0, prec="f32") for _ in range(nroll)]
+    for s, seed in zip(solvers, test_seeds):
+        s.init(*SG.trajectory_fields(seed, L))
+        s.step(64)
+    errs = {}
+    fell = 0
+    calls = 0
+    for k in range(1, 17):
+        flags = net.advance(solvers, K=K, tol=1e-4)
+        fell += sum(flags)
+        calls += len(flags)
+        if k in (1, 4, 16):
+            e_net, e_pers = [], []
+            for j, s in enumerate(solvers):
+                ref = tstack[j * snaps + k].cpu().numpy().astype(np.float64)
+                ref = [ref[:, c].reshape(L, L) for c in range(4)]
+                ini = tstack[j * snaps].cpu().numpy().astype(np.float64)
+                ini = [ini[:, c].reshape(L, L) for c in range(4)]
+                e_net.append(_field_err(s.moments(), ref))
+                e_pers.append(_field_err(ini, ref))
+            errs[str(k)] = {"surrogate_vs_lbm": {f: float(np.mean([e[f] for e in e_net])) for f in ("rho", "u", "theta")},
+                            "persistence_vs_lbm": {f: float(np.mean([e[f] for e in e_pers])) for f in ("rho", "u", "theta")}}
+    out["rollout_errors_mean_over_%d_seeds" % nroll] = errs
+    out["fallback_rate"] = fell / calls
+    for s in solvers:
+        s.close()
+    # FP64 oracle check on two held-out seeds after one advance
+    orc = []
+    for seed in test_seeds[:2]:
+        lat = O.Lattice(2, SG.V5, SG.OMEGA, L, L, theta0=SG.THETA0)
+        mo = lat.moments(lat.run(lat.init(*SG.trajectory_fields(seed, L)), 64 + K))
+        s = plbm.Solver(2, SG.V5, SG.OMEGA, L, L, theta0=SG.THETA0, prec="f32")
+        s.init(*SG.trajectory_fields(seed, L))
+        s.step(64)
+        net.advance([s], K=K, tol=1.0)
+        e_sur = _field_err(s.moments(), mo)
+        s.init(*SG.trajectory_fields(seed, L))
+        s.step(64 + K)
+        e_lbm = _field_err(s.moments(), mo)
+        s.close()
+        orc.append({"seed": seed, "surrogate_vs_fp64_oracle": e_sur, "lbm_f32_vs_fp64_oracle": e_lbm})
+    out["one_advance_vs_fp64_oracle"] = orc
+    # speed: one surrogate advance of B lattices vs K LBM steps of the same lattices
+    speed = {}
+    for B in (1, 16, 64):
+        sols = [plbm.Solver(2, SG.V5, SG.OMEGA, L, L, theta0=SG.THETA0, prec="f32") for _ in range(B)]
+        for s, seed in zip(sols, test_seeds):
+            s.init(*SG.trajectory_fields(seed, L))
+        net.advance(sols, K=K, tol=1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        net.advance(sols, K=K, tol=1.0)
+        torch.cuda.synchronize()
+        t_sur = time.perf_counter() - t0
+        for s in sols:
+            s.close()
+        insts = [SG.trajectory_instance(sd, L)[0] for sd in test_seeds[:B]]
+        bt = Batch(insts, prec="f32")
+        bt.init()
+        bt.step(2, "persistent_graph")
+        bt.stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(bt.stream)
+        bt.step(K, "persistent_graph")
+        e1.record(bt.stream)
+        e1.synchronize()
+        t_lbm = e0.elapsed_time(e1) * 1e-3
+        bt.close()
+        speed[str(B)] = {"surrogate_advance_ms": t_sur * 1e3, "lbm_K_steps_ms": t_lbm * 1e3,
+                         "speedup_vs_lbm": t_lbm / t_sur}
+    out["speed_one_advance"] = speed
+    net.close()
+    del tstack
+    torch.cuda.empty_cache()
+    return out
+
+
 def cpu_oracle_sample(L, seconds=12.0, max_steps=50):
     """Time the FP64 oracle as it stands on this host's cores on an L x L KH grid."""
     import oracle as O
@@ -270,6 +386,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-instances", type=int, default=256)
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--surrogate-train", type=int, default=2000, help="training trajectories")
+    ap.add_argument("--surrogate-steps", type=int, default=2000, help="Adam steps")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -376,6 +495,9 @@ def main():
             fields=I.shock_tube_fields(1000, left, right), theta0=0.5, omega=1.5, left=left, right=right)
         if not args.no_batch:
             variants["batched_%d_f32" % args.batch_instances] = run_batched(torch, n=args.batch_instances)
+        if not args.no_surrogate:
+            variants["surrogate_kh256"] = run_surrogate(torch, n_train=args.surrogate_train,
+                                                        train_steps=args.surrogate_steps)
         base = value / ws
         for k, vv in variants.items():
             if k.startswith("kh%d_" % L):

@@ -270,6 +270,80 @@ plbm_status plbm_batch_tune(plbm_batch b, int steps_per_trial, int *best_block_x
 /* Text of the last error of the batch (or of the calling thread when NULL). */
 const char *plbm_batch_last_error(plbm_batch b);
 
+/* ------------------------------------------------------------------------
+ * Learned surrogate (not in the paper; a throughput service around its solver,
+ * which generates the training data and stays the fallback and the judge).
+ * A 6-layer 3x3 CNN with circular padding, channels 4 -> 64 -> 64 -> 64 -> 64
+ * -> 64 -> 4, ReLU after the first five layers, BF16 weights and activations
+ * with FP32 accumulation, maps the normalised fields (rho, u_x, u_y, theta)
+ * of a periodic H x W lattice to the normalised change of those fields over K
+ * lattice steps.  FP32 master weights, Adam, mean squared error.
+ * Tensors are NHWC on the device: network input bf16 [B][H][W][4], targets and
+ * outputs fp32 [B][H][W][4].  W must be a multiple of 128.
+ * ------------------------------------------------------------------------ */
+typedef struct plbm_surrogate_s *plbm_surrogate;
+
+/* Number of FP32 parameters; flat layout per layer W[3][3][cin][cout], b[cout]. */
+int plbm_sur_num_params(void);
+
+/* Network for batches of up to max_batch lattices of H x W nodes, He-initialised
+ * from `seed` (last layer scaled by 0.1).  stream: cudaStream_t (NULL: own). */
+plbm_status plbm_sur_create(int max_batch, int H, int W, unsigned long long seed, void *stream,
+                            plbm_surrogate *out);
+plbm_status plbm_sur_destroy(plbm_surrogate s);
+
+/* Replace (host FP32, resets Adam) or read the parameters and the last gradients. */
+plbm_status plbm_sur_set_params(plbm_surrogate s, const float *params);
+plbm_status plbm_sur_get_params(plbm_surrogate s, float *params, float *grads);
+
+/* Per-field normalisation: input (x - mean_in) / std_in, target
+ * (x_{t+K} - x_t - mean_d) / std_d.  Four values each, host memory. */
+plbm_status plbm_sur_set_norm(plbm_surrogate s, const float *mean_in, const float *std_in, const float *mean_d,
+                              const float *std_d);
+
+/* Forward pass of B samples; out (device fp32, may be NULL) receives the output. */
+plbm_status plbm_sur_forward(plbm_surrogate s, int B, const void *x, float *out);
+
+/* Forward and backward pass for the upstream gradient dout (device fp32) of the
+ * output; the gradients are then read with plbm_sur_get_params. */
+plbm_status plbm_sur_backward(plbm_surrogate s, int B, const void *x, const float *dout);
+
+/* Copy a stored tensor of the last pass for B samples to dst (device):
+ * kind 0: output of layer 1..5 (bf16 [B][H][W][64], after ReLU) or 6 (fp32
+ * [B][H][W][4]); kind 1 (after a backward pass): gradient of the loss with
+ * respect to the convolution output of layer 1..5 (bf16 [B][H][W][64]).
+ * Synchronous. */
+plbm_status plbm_sur_copy(plbm_surrogate s, int kind, int layer, int B, void *dst);
+
+/* One Adam step on the mean squared error against target.  loss (host, may be
+ * NULL) receives the loss, which synchronises the stream. */
+plbm_status plbm_sur_train_step(plbm_surrogate s, int B, const void *x, const float *target, float lr,
+                                float *loss);
+
+/* FP32 NHWC fields [n][4] from four FP64 planes (device). */
+plbm_status plbm_sur_pack_fields(const double *rho, const double *ux, const double *uy, const double *theta,
+                                 long long n, float *out, void *stream);
+
+/* Training batch from a stack of field snapshots (device fp32 [S][npix][4]):
+ * for b < B with pairs[2b] = s0, pairs[2b+1] = s1 (device int32), x[b] is the
+ * normalised snapshot s0 (bf16) and y[b] the normalised change s1 - s0 (fp32). */
+plbm_status plbm_sur_assemble(plbm_surrogate s, const float *snaps, long long npix, const int *pairs, int B,
+                              void *x, float *y);
+
+/* Advance n lattices (handles of H x W periodic 2D lattices, 16/32/64-bit
+ * storage) by K steps with the network: fields from the populations, predicted
+ * change, and the FP64 global drift of mass, energy (relative) and momentum
+ * (relative to 0.1 x mass) between the old and the predicted fields.  Drift <=
+ * tol: the populations are rebuilt by Chapman-Enskog reconstruction (f^eq plus
+ * -((1 - omega) / omega) D f^eq with Euler time derivatives, projected so the
+ * conserved moments equal the predicted fields) and the step counter advances
+ * by K.  Otherwise (or for a non-finite prediction) the lattice runs K ordinary
+ * steps (Eq. eq:srt).  fell_back[b] (host, may be NULL) reports which. */
+plbm_status plbm_sur_advance(plbm_surrogate s, plbm_handle *hs, int n, int K, double tol, int *fell_back);
+
+/* Text of the last error of s (or of the calling thread when NULL). */
+const char *plbm_sur_last_error(plbm_surrogate s);
+
 /* Largest lattice (nx * ny nodes) plbm_diagnostics_noalloc accepts: its
  * static scratch array holds one 64-byte record per 256 nodes (1 MiB). */
 #define PLBM_NOALLOC_MAX_NODES (1 << 22)

@@ -28,6 +28,9 @@ SOURCES = [
     "plbm_step_f16.cu",
     "plbm_step_bf16.cu",
     "plbm_noalloc.cu",
+    "plbm_cnn.cu",
+    "plbm_ce.cu",
+    "plbm_surrogate.cpp",
 ]
 HEADERS = ["plbm_internal.h", "plbm_device.cuh", "plbm_pair.cuh"]
 

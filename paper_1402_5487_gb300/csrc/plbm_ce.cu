@@ -1,0 +1,292 @@
+// Field-level kernels of the surrogate path: packing moments into FP32 NHWC
+// fields, building normalised training pairs, applying a predicted change,
+// FP64 conserved sums of field arrays, and the Chapman-Enskog reconstruction
+// of populations from fields.
+//
+// Reconstruction.  For the stored (post-collision) state the first-order
+// Chapman-Enskog population is
+//     f_p = f^eq_p - ((1 - omega) / omega) D_p f^eq_p,   D_p = d_t + v_p . grad,
+// (pre-collision non-equilibrium -(1/omega) D_p f^eq_p, relaxed once by the
+// BGK step of Eq. eq:srt).  f^eq_p = rho r^x_i r^y_j (Eq. eq:rdr, Sec. 2.1), so
+//     D_p f^eq_p = r^x r^y D rho + rho r^x' r^y D u_x + rho r^x r^y' D u_y
+//                  + rho (r^x_th r^y + r^x r^y_th) D theta,
+// with r' = C dmu/du, dmu_n/du = n mu_{n-1}, and r_th = C dmu/dtheta,
+// dmu_n/dtheta = n (n - 1) mu_{n-2} / 2 (Gaussian moments).  Time derivatives
+// come from the Euler equations of the ideal gas p = rho theta in d = 2
+// (d_t rho = -div(rho u), d_t u = -u.grad u - grad p / rho,
+// d_t theta = -u.grad theta - (2/d) theta div u); spatial derivatives are
+// second-order central differences on the periodic grid.  Finally the
+// non-equilibrium part is projected off span{w0, w0 v_x, w0 v_y, w0 |v|^2} so
+// that mass, momentum and energy of the populations equal the fields exactly
+// (to rounding).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "plbm_device.cuh"
+#include "plbm_internal.h"
+
+namespace plbm {
+
+// fields_out[n][4] = (rho, ux, uy, theta) as FP32 from FP64 planes [n].
+__global__ void k_pack_fields(const double* __restrict__ rho, const double* __restrict__ ux,
+                              const double* __restrict__ uy, const double* __restrict__ th, long long n,
+                              float4* __restrict__ out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = make_float4((float)rho[i], (float)ux[i], (float)uy[i], (float)th[i]);
+}
+
+// Training pair b: x[b] = (F[s0] - mean_in) / std_in (bf16), y[b] = (F[s1] - F[s0] - mean_d) / std_d (fp32),
+// F a stack of snapshots of `npix` nodes x 4 fields, pairs[b] = (s0, s1).
+__global__ void k_assemble(const float4* __restrict__ snaps, long long npix, const int* __restrict__ pairs,
+                           int B, float4 mean_in, float4 istd_in, float4 mean_d, float4 istd_d,
+                           __nv_bfloat16* __restrict__ x, float4* __restrict__ y) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npix * B) return;
+    const int b = (int)(i / npix);
+    const long long k = i - (long long)b * npix;
+    const float4 a = snaps[(long long)pairs[2 * b] * npix + k];
+    const float4 c = snaps[(long long)pairs[2 * b + 1] * npix + k];
+    __nv_bfloat16* xo = x + i * 4;
+    xo[0] = __float2bfloat16_rn((a.x - mean_in.x) * istd_in.x);
+    xo[1] = __float2bfloat16_rn((a.y - mean_in.y) * istd_in.y);
+    xo[2] = __float2bfloat16_rn((a.z - mean_in.z) * istd_in.z);
+    xo[3] = __float2bfloat16_rn((a.w - mean_in.w) * istd_in.w);
+    y[i] = make_float4((c.x - a.x - mean_d.x) * istd_d.x, (c.y - a.y - mean_d.y) * istd_d.y,
+                       (c.z - a.z - mean_d.z) * istd_d.z, (c.w - a.w - mean_d.w) * istd_d.w);
+}
+
+// Network input from current fields: x = (F - mean_in) / std_in (bf16).
+__global__ void k_normalise(const float4* __restrict__ F, long long n, float4 mean_in, float4 istd_in,
+                            __nv_bfloat16* __restrict__ x) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 a = F[i];
+    __nv_bfloat16* xo = x + i * 4;
+    xo[0] = __float2bfloat16_rn((a.x - mean_in.x) * istd_in.x);
+    xo[1] = __float2bfloat16_rn((a.y - mean_in.y) * istd_in.y);
+    xo[2] = __float2bfloat16_rn((a.z - mean_in.z) * istd_in.z);
+    xo[3] = __float2bfloat16_rn((a.w - mean_in.w) * istd_in.w);
+}
+
+// F_new = F + delta * std_d + mean_d.
+__global__ void k_apply_delta(const float4* __restrict__ F, const float4* __restrict__ d, long long n, float4 mean_d,
+                              float4 std_d, float4* __restrict__ out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 a = F[i], e = d[i];
+    out[i] = make_float4(a.x + fmaf(e.x, std_d.x, mean_d.x), a.y + fmaf(e.y, std_d.y, mean_d.y),
+                         a.z + fmaf(e.z, std_d.z, mean_d.z), a.w + fmaf(e.w, std_d.w, mean_d.w));
+}
+
+// Per-block FP64 sums over the fields of one lattice: mass, rho u_x, rho u_y,
+// energy d rho theta + rho |u|^2 (d = 2); out[blk * 4 + k].
+__global__ void k_field_sums(const float4* __restrict__ F, long long n, double* __restrict__ out) {
+    __shared__ double sh[4][256];
+    double s[4] = {0, 0, 0, 0};
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float4 a = F[i];
+        const double r = a.x, u = a.y, v = a.z, t = a.w;
+        s[0] += r;
+        s[1] += r * u;
+        s[2] += r * v;
+        s[3] += r * (2.0 * t + u * u + v * v);
+    }
+    for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] = s[k];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) out[blockIdx.x * 4 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+struct CEConsts {
+    float Ginv[16];   // inverse of G_jk = sum_p w0_p m_j(p) m_k(p), m = (1, v_x, v_y, |v|^2)
+    float coef;       // (1 - omega) / omega
+};
+
+template <typename S>
+__global__ void k_ce_reconstruct(const __grid_constant__ LatticeParams P, const __grid_constant__ CEConsts K,
+                                 const float4* __restrict__ F, S* __restrict__ f) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= P.nx) return;
+    const int nx = P.nx, ny = P.ny;
+    const int xp = x + 1 == nx ? 0 : x + 1, xm = x == 0 ? nx - 1 : x - 1;
+    const int yp = y + 1 == ny ? 0 : y + 1, ym = y == 0 ? ny - 1 : y - 1;
+    const float4 c = F[(long long)y * nx + x];
+    const float4 e = F[(long long)y * nx + xp], w = F[(long long)y * nx + xm];
+    const float4 n = F[(long long)yp * nx + x], s = F[(long long)ym * nx + x];
+    const float rho = c.x, ux = c.y, uy = c.z, th = c.w;
+    // central differences
+    const float drx = 0.5f * (e.x - w.x), dry = 0.5f * (n.x - s.x);
+    const float dux_x = 0.5f * (e.y - w.y), dux_y = 0.5f * (n.y - s.y);
+    const float duy_x = 0.5f * (e.z - w.z), duy_y = 0.5f * (n.z - s.z);
+    const float dth_x = 0.5f * (e.w - w.w), dth_y = 0.5f * (n.w - s.w);
+    const float dp_x = 0.5f * (e.x * e.w - w.x * w.w), dp_y = 0.5f * (n.x * n.w - s.x * s.w);
+    const float divu = dux_x + duy_y;
+    const float inv_rho = 1.0f / rho;
+    // Euler time derivatives (d = 2)
+    const float dt_rho = -(ux * drx + uy * dry) - rho * divu;
+    const float dt_ux = -(ux * dux_x + uy * dux_y) - dp_x * inv_rho;
+    const float dt_uy = -(ux * duy_x + uy * duy_y) - dp_y * inv_rho;
+    const float dt_th = -(ux * dth_x + uy * dth_y) - th * divu;
+    // per-axis rule, its u- and theta-derivatives
+    const int q1 = P.q1;
+    float r[2][kMaxQ1], ru[2][kMaxQ1], rt[2][kMaxQ1];
+    for (int a = 0; a < 2; ++a) {
+        const float u = a == 0 ? ux : uy;
+        float mu[kMaxQ1 + 1];
+        mu[0] = 1.0f;
+        mu[1] = u;
+        for (int k = 1; k + 1 < q1; ++k) mu[k + 1] = u * mu[k] + (float)k * th * mu[k - 1];
+        for (int i = 0; i < q1; ++i) {
+            float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
+            for (int k = 0; k < q1; ++k) {
+                const float cik = P.Cf[i * q1 + k] + P.Cf_lo[i * q1 + k];
+                s0 += cik * mu[k];
+                if (k >= 1) s1 += cik * (float)k * mu[k - 1];
+                if (k >= 2) s2 += cik * 0.5f * (float)(k * (k - 1)) * mu[k - 2];
+            }
+            r[a][i] = s0;
+            ru[a][i] = s1;
+            rt[a][i] = s2;
+        }
+    }
+    float fneq[kMaxQ], feq[kMaxQ];
+    float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
+    for (int i = 0; i < q1; ++i) {
+        const float vx = (float)P.v[i];
+        for (int j = 0; j < q1; ++j) {
+            const float vy = (float)P.v[j];
+            const int p = i * q1 + j;
+            const float Drho = dt_rho + vx * drx + vy * dry;
+            const float Dux = dt_ux + vx * dux_x + vy * dux_y;
+            const float Duy = dt_uy + vx * duy_x + vy * duy_y;
+            const float Dth = dt_th + vx * dth_x + vy * dth_y;
+            const float D = r[0][i] * r[1][j] * Drho + rho * ru[0][i] * r[1][j] * Dux + rho * r[0][i] * ru[1][j] * Duy +
+                            rho * (rt[0][i] * r[1][j] + r[0][i] * rt[1][j]) * Dth;
+            const float fn = -K.coef * D;
+            fneq[p] = fn;
+            feq[p] = rho * r[0][i] * r[1][j];
+            m0 += fn;
+            m1 += vx * fn;
+            m2 += vy * fn;
+            m3 += (vx * vx + vy * vy) * fn;
+        }
+    }
+    float cc[4];
+    for (int k = 0; k < 4; ++k) cc[k] = K.Ginv[4 * k] * m0 + K.Ginv[4 * k + 1] * m1 + K.Ginv[4 * k + 2] * m2 + K.Ginv[4 * k + 3] * m3;
+    for (int i = 0; i < q1; ++i) {
+        const float vx = (float)P.v[i];
+        for (int j = 0; j < q1; ++j) {
+            const float vy = (float)P.v[j];
+            const int p = i * q1 + j;
+            const float proj = P.W0f[p] * (cc[0] + cc[1] * vx + cc[2] * vy + cc[3] * (vx * vx + vy * vy));
+            const double fp = (double)feq[p] + (double)(fneq[p] - proj);
+            f[elem_index(P, p, x, y)] = Storage<S>::from_f64(fp, P.W0[p]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+cudaError_t ce_pack_fields(const double* rho, const double* ux, const double* uy, const double* th, long long n,
+                           float* out, cudaStream_t s) {
+    k_pack_fields<<<(int)((n + 255) / 256), 256, 0, s>>>(rho, ux, uy, th, n, reinterpret_cast<float4*>(out));
+    return cudaGetLastError();
+}
+
+cudaError_t ce_assemble(const float* snaps, long long npix, const int* pairs, int B, const float* mean_in,
+                        const float* std_in, const float* mean_d, const float* std_d, void* x, float* y,
+                        cudaStream_t s) {
+    const float4 mi = make_float4(mean_in[0], mean_in[1], mean_in[2], mean_in[3]);
+    const float4 si = make_float4(1.f / std_in[0], 1.f / std_in[1], 1.f / std_in[2], 1.f / std_in[3]);
+    const float4 md = make_float4(mean_d[0], mean_d[1], mean_d[2], mean_d[3]);
+    const float4 sd = make_float4(1.f / std_d[0], 1.f / std_d[1], 1.f / std_d[2], 1.f / std_d[3]);
+    const long long n = npix * B;
+    k_assemble<<<(int)((n + 255) / 256), 256, 0, s>>>(reinterpret_cast<const float4*>(snaps), npix, pairs, B, mi, si,
+                                                       md, sd, static_cast<__nv_bfloat16*>(x),
+                                                       reinterpret_cast<float4*>(y));
+    return cudaGetLastError();
+}
+
+cudaError_t ce_normalise(const float* F, long long n, const float* mean_in, const float* std_in, void* x,
+                         cudaStream_t s) {
+    const float4 mi = make_float4(mean_in[0], mean_in[1], mean_in[2], mean_in[3]);
+    const float4 si = make_float4(1.f / std_in[0], 1.f / std_in[1], 1.f / std_in[2], 1.f / std_in[3]);
+    k_normalise<<<(int)((n + 255) / 256), 256, 0, s>>>(reinterpret_cast<const float4*>(F), n, mi, si,
+                                                        static_cast<__nv_bfloat16*>(x));
+    return cudaGetLastError();
+}
+
+cudaError_t ce_apply_delta(const float* F, const float* d, long long n, const float* mean_d, const float* std_d,
+                           float* out, cudaStream_t s) {
+    const float4 md = make_float4(mean_d[0], mean_d[1], mean_d[2], mean_d[3]);
+    const float4 sd = make_float4(std_d[0], std_d[1], std_d[2], std_d[3]);
+    k_apply_delta<<<(int)((n + 255) / 256), 256, 0, s>>>(reinterpret_cast<const float4*>(F),
+                                                          reinterpret_cast<const float4*>(d), n, md, sd,
+                                                          reinterpret_cast<float4*>(out));
+    return cudaGetLastError();
+}
+
+int ce_sum_blocks() { return 64; }
+
+cudaError_t ce_field_sums(const float* F, long long n, double* partial, cudaStream_t s) {
+    k_field_sums<<<ce_sum_blocks(), 256, 0, s>>>(reinterpret_cast<const float4*>(F), n, partial);
+    return cudaGetLastError();
+}
+
+cudaError_t ce_reconstruct(int prec, const LatticeParams& P, const float* F, void* f, cudaStream_t s) {
+    if (P.dim != 2) return cudaErrorInvalidValue;
+    // G_jk = sum_p w0_p m_j m_k, m = (1, vx, vy, |v|^2), inverted in FP64 on the host.
+    double G[4][4] = {{0}};
+    for (int i = 0; i < P.q1; ++i)
+        for (int j = 0; j < P.q1; ++j) {
+            const double vx = P.v[i], vy = P.v[j];
+            const double m[4] = {1.0, vx, vy, vx * vx + vy * vy};
+            const double w = P.W0[i * P.q1 + j];
+            for (int a = 0; a < 4; ++a)
+                for (int b = 0; b < 4; ++b) G[a][b] += w * m[a] * m[b];
+        }
+    double A[4][8];
+    for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 8; ++b) A[a][b] = b < 4 ? G[a][b] : (b - 4 == a ? 1.0 : 0.0);
+    for (int col = 0; col < 4; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < 4; ++r)
+            if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
+        for (int b = 0; b < 8; ++b) {
+            const double t = A[col][b];
+            A[col][b] = A[piv][b];
+            A[piv][b] = t;
+        }
+        const double d = A[col][col];
+        if (d == 0.0) return cudaErrorInvalidValue;
+        for (int b = 0; b < 8; ++b) A[col][b] /= d;
+        for (int r = 0; r < 4; ++r)
+            if (r != col) {
+                const double m = A[r][col];
+                for (int b = 0; b < 8; ++b) A[r][b] -= m * A[col][b];
+            }
+    }
+    CEConsts K;
+    for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) K.Ginv[4 * a + b] = (float)A[a][4 + b];
+    K.coef = (float)((1.0 - P.omega) / P.omega);
+    dim3 grid((P.nx + 127) / 128, P.ny);
+    const float4* Fv = reinterpret_cast<const float4*>(F);
+    switch (prec) {
+        case kF32: k_ce_reconstruct<float><<<grid, 128, 0, s>>>(P, K, Fv, static_cast<float*>(f)); break;
+        case kF16Dev: k_ce_reconstruct<__half><<<grid, 128, 0, s>>>(P, K, Fv, static_cast<__half*>(f)); break;
+        case kBF16Dev:
+            k_ce_reconstruct<__nv_bfloat16><<<grid, 128, 0, s>>>(P, K, Fv, static_cast<__nv_bfloat16*>(f));
+            break;
+        case kF64: k_ce_reconstruct<double><<<grid, 128, 0, s>>>(P, K, Fv, static_cast<double*>(f)); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace plbm

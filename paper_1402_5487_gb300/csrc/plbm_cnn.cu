@@ -1,0 +1,774 @@
+// Kernels of the learned surrogate: 3x3 convolutions with circular padding on
+// NHWC activations, their gradients, loss and optimiser.
+//
+// The surrogate is a 6-layer CNN (4 -> 64, 4 x (64 -> 64), 64 -> 4 channels)
+// mapping (rho, u_x, u_y, theta) of a periodic lattice to the change of those
+// fields K lattice steps later.  It is not in the paper; it is a throughput
+// service built around the paper's solver, which generates its training data
+// and stays the fallback.
+//
+//  * 64 -> 64 layers: implicit GEMM on the tensor cores with mma.sync
+//    m16n8k16 BF16 x BF16 -> FP32 (M = output pixels, N = 64 output channels,
+//    K = 9 taps x 64 input channels).  Weights (72 KB) stay in shared memory for
+//    the life of a persistent CTA; the three input rows of each 128-pixel tile
+//    are staged with cp.async into a double buffer while the previous tile runs.
+//    Shared rows of 128 bytes are XOR-swizzled in 16-byte chunks so that the
+//    eight row addresses of every ldmatrix hit distinct banks.
+//  * Backward data of a 64 -> 64 layer is the same forward kernel with the
+//    taps flipped and the channel axes of the weights swapped, epilogue
+//    multiplying by the ReLU mask of the layer input.
+//  * Weight gradients of 64 -> 64 layers: one warp per tap accumulates the
+//    64 x 64 block X_shift^T dY over the CTA's pixels with mma.sync; per-CTA
+//    partial sums are reduced in a fixed order.
+//  * The thin 4 -> 64 and 64 -> 4 layers (and their gradients) run on the CUDA
+//    cores in FP32.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "plbm_internal.h"
+
+namespace plbm {
+namespace cnn {
+
+constexpr int kC = 64;            // hidden channels
+constexpr int kTile = 128;        // output pixels per tile (one row segment)
+constexpr int kRowPix = kTile + 2;
+constexpr int kThreadsMid = 256;  // 8 warps: 4 pixel slabs x 2 channel halves
+constexpr int kWBytes = 9 * kC * kC * 2;             // 73728
+constexpr int kInBytes = 3 * kRowPix * kC * 2;       // 49920
+constexpr int kMidSmem = kWBytes + 2 * kInBytes;     // 173568
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem)), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+__device__ __forceinline__ void ldsm_x4(unsigned addr, unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x4_t(unsigned addr, unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+__device__ __forceinline__ void mma_bf16(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                         unsigned b0, unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// Byte offset of 16-byte chunk c (0..7) of 128-byte row `row` with the XOR swizzle.
+__device__ __forceinline__ int swz(int row, int c) { return (row * 8 + (c ^ (row & 7))) * 16; }
+
+struct ConvShape {
+    int B, H, W;
+};
+
+// ---------------------------------------------------------------------------
+// 64 -> 64 convolution, forward (mode 0: + bias, ReLU if relu; mode 1: no bias,
+// output multiplied by (mask > 0)).  X, Y, mask: NHWC bf16; Wt: [tap][ci][co] bf16;
+// bias: fp32[64].
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreadsMid, 1)
+k_conv64_fwd(ConvShape S, const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ Wt,
+             const float* __restrict__ bias, const __nv_bfloat16* __restrict__ mask, __nv_bfloat16* __restrict__ Y,
+             int mode, int relu) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char* sW = smem;
+    unsigned char* sIn = smem + kWBytes;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp & 3, wn = warp >> 2;
+    const int tiles_x = S.W / kTile;
+    const int ntiles = S.B * S.H * tiles_x;
+
+    // weights: 9*64 rows of 128 bytes
+    for (int i = tid; i < 9 * kC * 8; i += kThreadsMid) {
+        const int row = i >> 3, c = i & 7;
+        cp_async16(sW + swz(row, c), Wt + (size_t)row * kC + c * 8);
+    }
+    auto load_tile = [&](int t, int buf) {
+        const int b = t / (S.H * tiles_x);
+        const int rem = t - b * S.H * tiles_x;
+        const int y = rem / tiles_x;
+        const int x0 = (rem - y * tiles_x) * kTile;
+        unsigned char* dst = sIn + buf * kInBytes;
+        for (int i = tid; i < 3 * kRowPix * 8; i += kThreadsMid) {
+            const int c = i & 7;
+            const int pr = i >> 3;              // r * kRowPix + p
+            const int r = pr / kRowPix, p = pr - r * kRowPix;
+            int yy = y + r - 1;
+            yy += (yy < 0) ? S.H : 0;
+            yy -= (yy >= S.H) ? S.H : 0;
+            int xx = x0 + p - 1;
+            xx += (xx < 0) ? S.W : 0;
+            xx -= (xx >= S.W) ? S.W : 0;
+            const __nv_bfloat16* src = X + (((size_t)b * S.H + yy) * S.W + xx) * kC + c * 8;
+            cp_async16(dst + r * kRowPix * 128 + swz(p, c), src);
+        }
+    };
+    int t = blockIdx.x;
+    if (t < ntiles) load_tile(t, 0);
+    cp_async_commit();
+    int buf = 0;
+    for (; t < ntiles; t += gridDim.x) {
+        const int tn = t + gridDim.x;
+        if (tn < ntiles) load_tile(tn, buf ^ 1);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+
+        float acc[2][4][4];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.0f;
+
+        const unsigned char* in = sIn + buf * kInBytes;
+#pragma unroll 1
+        for (int tap = 0; tap < 9; ++tap) {
+            const int ky = tap / 3, kx = tap - ky * 3;
+            const unsigned char* rowp = in + ky * kRowPix * 128;
+#pragma unroll
+            for (int kc = 0; kc < 4; ++kc) {  // 16 input channels per step
+                unsigned a[2][4];
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    const int j = lane >> 3;
+                    const int p = wm * 32 + mt * 16 + (lane & 7) + 8 * (j & 1) + kx;
+                    const int c = kc * 2 + (j >> 1);
+                    ldsm_x4(smem_u32(rowp + swz(p, c)), a[mt][0], a[mt][1], a[mt][2], a[mt][3]);
+                }
+                unsigned bf[4][2];
+#pragma unroll
+                for (int np = 0; np < 2; ++np) {  // two n8 tiles per ldmatrix
+                    const int krow = tap * kC + kc * 16 + (lane & 7) + 8 * ((lane >> 3) & 1);
+                    const int c = wn * 4 + np * 2 + (lane >> 4);
+                    ldsm_x4_t(smem_u32(sW + swz(krow, c)), bf[np * 2][0], bf[np * 2][1], bf[np * 2 + 1][0],
+                              bf[np * 2 + 1][1]);
+                }
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                    for (int nt = 0; nt < 4; ++nt)
+                        mma_bf16(acc[mt][nt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], bf[nt][0], bf[nt][1]);
+            }
+        }
+        // epilogue
+        const int b = t / (S.H * tiles_x);
+        const int rem = t - b * S.H * tiles_x;
+        const int y = rem / tiles_x;
+        const int x0 = (rem - y * tiles_x) * kTile;
+        const int g = lane >> 2, q = lane & 3;
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int x = x0 + wm * 32 + mt * 16 + g + 8 * h;
+                const size_t pix = ((size_t)b * S.H + y) * S.W + x;
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt) {
+                    const int co = wn * 32 + nt * 8 + 2 * q;
+                    float v0 = acc[mt][nt][2 * h], v1 = acc[mt][nt][2 * h + 1];
+                    if (mode == 0) {
+                        v0 += bias[co];
+                        v1 += bias[co + 1];
+                        if (relu) {
+                            v0 = fmaxf(v0, 0.0f);
+                            v1 = fmaxf(v1, 0.0f);
+                        }
+                    } else {
+                        const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162*>(mask + pix * kC + co);
+                        v0 = __bfloat162float(mk.x) > 0.0f ? v0 : 0.0f;
+                        v1 = __bfloat162float(mk.y) > 0.0f ? v1 : 0.0f;
+                    }
+                    *reinterpret_cast<__nv_bfloat162*>(Y + pix * kC + co) = __floats2bfloat162_rn(v0, v1);
+                }
+            }
+        __syncthreads();  // the buffer is refilled by the next iteration's prefetch
+        buf ^= 1;
+    }
+    cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------
+// 64 -> 64 weight gradient.  Warp w (w < 9) owns tap w and accumulates
+// dW[tap][ci][co] = sum_pixels X[pix + shift][ci] dY[pix][co] for the CTA's
+// tiles; warp 9 also sums dY per channel for the bias.  Partials per CTA:
+// partial[cta][tap][ci][co] (fp32), partial_b[cta][co].
+// ---------------------------------------------------------------------------
+constexpr int kThreadsWg = 320;  // 10 warps
+constexpr int kDyBytes = kTile * kC * 2;  // 16384
+constexpr int kWgSmem = 2 * (kInBytes + kDyBytes);
+
+__global__ void __launch_bounds__(kThreadsWg, 1)
+k_conv64_wgrad(ConvShape S, const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ dY,
+               float* __restrict__ partial, float* __restrict__ partial_b) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tiles_x = S.W / kTile;
+    const int ntiles = S.B * S.H * tiles_x;
+    auto load_tile = [&](int t, int buf) {
+        const int b = t / (S.H * tiles_x);
+        const int rem = t - b * S.H * tiles_x;
+        const int y = rem / tiles_x;
+        const int x0 = (rem - y * tiles_x) * kTile;
+        unsigned char* dIn = smem + buf * (kInBytes + kDyBytes);
+        unsigned char* dG = dIn + kInBytes;
+        for (int i = tid; i < 3 * kRowPix * 8; i += kThreadsWg) {
+            const int c = i & 7;
+            const int pr = i >> 3;
+            const int r = pr / kRowPix, p = pr - r * kRowPix;
+            int yy = y + r - 1;
+            yy += (yy < 0) ? S.H : 0;
+            yy -= (yy >= S.H) ? S.H : 0;
+            int xx = x0 + p - 1;
+            xx += (xx < 0) ? S.W : 0;
+            xx -= (xx >= S.W) ? S.W : 0;
+            cp_async16(dIn + r * kRowPix * 128 + swz(p, c), X + (((size_t)b * S.H + yy) * S.W + xx) * kC + c * 8);
+        }
+        for (int i = tid; i < kTile * 8; i += kThreadsWg) {
+            const int c = i & 7, p = i >> 3;
+            cp_async16(dG + swz(p, c), dY + (((size_t)b * S.H + y) * S.W + x0 + p) * kC + c * 8);
+        }
+    };
+    float acc[4][8][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.0f;
+    float bsum = 0.0f;  // warp 9, lanes 0..31: channels lane and lane + 32
+
+    float bsum2 = 0.0f;
+    int t = blockIdx.x;
+    if (t < ntiles) load_tile(t, 0);
+    cp_async_commit();
+    int buf = 0;
+    for (; t < ntiles; t += gridDim.x) {
+        const int tn = t + gridDim.x;
+        if (tn < ntiles) load_tile(tn, buf ^ 1);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        const unsigned char* in = smem + buf * (kInBytes + kDyBytes);
+        const unsigned char* gy = in + kInBytes;
+        if (warp < 9) {
+            const int ky = warp / 3, kx = warp - ky * 3;
+            const unsigned char* rowp = in + ky * kRowPix * 128;
+#pragma unroll 1
+            for (int ks = 0; ks < kTile / 16; ++ks) {  // 16 pixels per k step
+                unsigned a[4][4];
+#pragma unroll
+                for (int mt = 0; mt < 4; ++mt) {  // 16 input channels per m tile
+                    const int j = lane >> 3;
+                    const int p = ks * 16 + (lane & 7) + 8 * (j >> 1) + kx;
+                    const int c = mt * 2 + (j & 1);
+                    ldsm_x4_t(smem_u32(rowp + swz(p, c)), a[mt][0], a[mt][1], a[mt][2], a[mt][3]);
+                }
+#pragma unroll
+                for (int np = 0; np < 4; ++np) {
+                    unsigned b0, b1, b2, b3;
+                    const int p = ks * 16 + (lane & 7) + 8 * ((lane >> 3) & 1);
+                    const int c = np * 2 + (lane >> 4);
+                    ldsm_x4_t(smem_u32(gy + swz(p, c)), b0, b1, b2, b3);
+#pragma unroll
+                    for (int mt = 0; mt < 4; ++mt) {
+                        mma_bf16(acc[mt][np * 2], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b0, b1);
+                        mma_bf16(acc[mt][np * 2 + 1], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b2, b3);
+                    }
+                }
+            }
+        } else {
+            // bias gradient: lane owns channels lane and lane + 32
+            for (int p = 0; p < kTile; ++p) {
+                const __nv_bfloat16* row = reinterpret_cast<const __nv_bfloat16*>(gy + swz(p, lane >> 3));
+                const __nv_bfloat16* row2 = reinterpret_cast<const __nv_bfloat16*>(gy + swz(p, (lane + 32) >> 3));
+                bsum += __bfloat162float(row[lane & 7]);
+                bsum2 += __bfloat162float(row2[lane & 7]);
+            }
+        }
+        __syncthreads();
+        buf ^= 1;
+    }
+    cp_async_wait<0>();
+    if (warp < 9) {
+        float* out = partial + ((size_t)blockIdx.x * 9 + warp) * kC * kC;
+        const int g = lane >> 2, q = lane & 3;
+#pragma unroll
+        for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int ci = mt * 16 + g + 8 * h;
+                    const int co = nt * 8 + 2 * q;
+                    out[ci * kC + co] = acc[mt][nt][2 * h];
+                    out[ci * kC + co + 1] = acc[mt][nt][2 * h + 1];
+                }
+    } else {
+        partial_b[(size_t)blockIdx.x * kC + lane] = bsum;
+        partial_b[(size_t)blockIdx.x * kC + lane + 32] = bsum2;
+    }
+}
+
+// out[j] = sum_c partial[c * n + j] in a fixed order.
+__global__ void k_sum_partials(const float* __restrict__ partial, int nparts, int n, float* __restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    float s = 0.0f;
+    for (int c = 0; c < nparts; ++c) s += partial[(size_t)c * n + j];
+    out[j] = s;
+}
+
+// ---------------------------------------------------------------------------
+// Thin layers on the CUDA cores (FP32 arithmetic, weights fp32 [tap][ci][co]).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ float to_f(T v);
+template <>
+__device__ __forceinline__ float to_f<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+__device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// 4 -> 64: tile = 128 pixels of one row, thread = pixel.  The 36 inputs of a
+// pixel sit in registers, the weights are read as broadcast float4 from shared
+// memory, and the 64 outputs per pixel leave through a swizzled shared tile so
+// that the global stores are 16-byte and coalesced.
+// mode 0: + bias, ReLU if relu; mode 1: no bias, times (mask > 0).
+constexpr int kInFwdSmem = 9 * 4 * 64 * 4 + kTile * 64 * 2;
+
+template <typename TI>
+__global__ void __launch_bounds__(128)
+k_thin_in_fwd(ConvShape S, const TI* __restrict__ X, const float* __restrict__ Wf, const float* __restrict__ bias,
+              const __nv_bfloat16* __restrict__ mask, __nv_bfloat16* __restrict__ Y, int mode, int relu) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    float* sW = reinterpret_cast<float*>(dsm);
+    unsigned char* sOut = dsm + 9 * 4 * 64 * 4;
+    const int tiles_x = S.W / kTile;
+    const int t = blockIdx.x;
+    const int b = t / (S.H * tiles_x);
+    const int rem = t - b * S.H * tiles_x;
+    const int y = rem / tiles_x;
+    const int x0 = (rem - y * tiles_x) * kTile;
+    for (int i = threadIdx.x; i < 9 * 4 * 64; i += 128) sW[i] = Wf[i];
+    const int px = threadIdx.x, x = x0 + px;
+    float in[36];
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+        const int yy = wrap(y + tap / 3 - 1, S.H), xx = wrap(x + tap % 3 - 1, S.W);
+        const TI* xp = X + (((size_t)b * S.H + yy) * S.W + xx) * 4;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) in[tap * 4 + i] = to_f<TI>(xp[i]);
+    }
+    __syncthreads();
+    float acc[64];
+#pragma unroll
+    for (int o = 0; o < 64; ++o) acc[o] = (mode == 0) ? bias[o] : 0.0f;
+#pragma unroll
+    for (int k = 0; k < 36; ++k) {
+        const float xv = in[k];
+        const float4* w = reinterpret_cast<const float4*>(sW + k * 64);
+#pragma unroll
+        for (int o4 = 0; o4 < 16; ++o4) {
+            const float4 ww = w[o4];
+            acc[4 * o4 + 0] = fmaf(xv, ww.x, acc[4 * o4 + 0]);
+            acc[4 * o4 + 1] = fmaf(xv, ww.y, acc[4 * o4 + 1]);
+            acc[4 * o4 + 2] = fmaf(xv, ww.z, acc[4 * o4 + 2]);
+            acc[4 * o4 + 3] = fmaf(xv, ww.w, acc[4 * o4 + 3]);
+        }
+    }
+    const size_t pix = ((size_t)b * S.H + y) * S.W + x;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        float v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = acc[8 * c + k];
+        if (mode == 0) {
+            if (relu)
+#pragma unroll
+                for (int k = 0; k < 8; ++k) v[k] = fmaxf(v[k], 0.0f);
+        } else {
+            const uint4 mk = *reinterpret_cast<const uint4*>(mask + pix * 64 + 8 * c);
+            const __nv_bfloat16* m = reinterpret_cast<const __nv_bfloat16*>(&mk);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = __bfloat162float(m[k]) > 0.0f ? v[k] : 0.0f;
+        }
+        uint4 o;
+        __nv_bfloat162* ob = reinterpret_cast<__nv_bfloat162*>(&o);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) ob[k] = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+        *reinterpret_cast<uint4*>(sOut + swz(px, c)) = o;
+    }
+    __syncthreads();
+    // coalesced copy-out: the tile's 128 pixels x 128 bytes are contiguous in global memory
+    uint4* dst = reinterpret_cast<uint4*>(Y + (((size_t)b * S.H + y) * S.W + x0) * 64);
+    for (int i = threadIdx.x; i < kTile * 8; i += 128) {
+        const int p = i >> 3, c = i & 7;
+        dst[i] = *reinterpret_cast<const uint4*>(sOut + swz(p, c));
+    }
+}
+
+// 64 -> 4 (+ bias, fp32 output): tile = 128 pixels of one row; the three input rows
+// are staged in shared memory (16-byte chunks XOR-swizzled by pixel), thread =
+// pixel, one 16-byte store per thread.
+constexpr int kOutSmem = 9 * 64 * 4 * 4 + 3 * kRowPix * 64 * 2;
+
+__global__ void __launch_bounds__(128)
+k_thin_out_fwd(ConvShape S, const __nv_bfloat16* __restrict__ X, const float* __restrict__ Wf,
+               const float* __restrict__ bias, float* __restrict__ Y) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    float* sW = reinterpret_cast<float*>(dsm);
+    unsigned char* sX = dsm + 9 * 64 * 4 * 4;
+    const int tiles_x = S.W / kTile;
+    const int t = blockIdx.x;
+    const int b = t / (S.H * tiles_x);
+    const int rem = t - b * S.H * tiles_x;
+    const int y = rem / tiles_x;
+    const int x0 = (rem - y * tiles_x) * kTile;
+    for (int i = threadIdx.x; i < 9 * 64 * 4; i += 128) sW[i] = Wf[i];
+    for (int i = threadIdx.x; i < 3 * kRowPix * 8; i += 128) {
+        const int c = i & 7, pr = i >> 3, r = pr / kRowPix, p = pr - r * kRowPix;
+        const int yy = wrap(y + r - 1, S.H), xx = wrap(x0 + p - 1, S.W);
+        *reinterpret_cast<uint4*>(sX + r * kRowPix * 128 + swz(p, c)) =
+            *reinterpret_cast<const uint4*>(X + (((size_t)b * S.H + yy) * S.W + xx) * 64 + 8 * c);
+    }
+    __syncthreads();
+    const int px = threadIdx.x;
+    float4 acc = make_float4(bias[0], bias[1], bias[2], bias[3]);
+#pragma unroll 1
+    for (int tap = 0; tap < 9; ++tap) {
+        const int ky = tap / 3, kx = tap % 3;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const uint4 raw = *reinterpret_cast<const uint4*>(sX + ky * kRowPix * 128 + swz(px + kx, c));
+            const __nv_bfloat16* xv = reinterpret_cast<const __nv_bfloat16*>(&raw);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const float a = __bfloat162float(xv[k]);
+                const float4 w = *reinterpret_cast<const float4*>(sW + (tap * 64 + 8 * c + k) * 4);
+                acc.x = fmaf(a, w.x, acc.x);
+                acc.y = fmaf(a, w.y, acc.y);
+                acc.z = fmaf(a, w.z, acc.z);
+                acc.w = fmaf(a, w.w, acc.w);
+            }
+        }
+    }
+    reinterpret_cast<float4*>(Y)[((size_t)b * S.H + y) * S.W + x0 + px] = acc;
+}
+
+// Weight gradient of a thin layer, X with CX channels (bf16), dY with CG channels
+// (TG), one of CX, CG equal to 64 and the other to 4.  Thread (tap, a), a < 64,
+// accumulates the 4 entries of dW[tap][.][.] along the narrow axis over the CTA's
+// 128-pixel tiles staged in shared memory; threads with tap 0 also sum dY for the
+// bias.  partial[cta][tap][ci][co], partial_b[cta][co].
+template <int CX, int CG, typename TG>
+constexpr int thin_wgrad_smem() { return 3 * kRowPix * CX * 2 + kTile * CG * (int)sizeof(TG); }
+
+template <int CX, int CG, typename TG>
+__global__ void __launch_bounds__(576)
+k_thin_wgrad(ConvShape S, const __nv_bfloat16* __restrict__ X, const TG* __restrict__ dY, float* __restrict__ partial,
+             float* __restrict__ partial_b) {
+    static_assert((CX == 64 && CG == 4) || (CX == 4 && CG == 64), "thin layer shapes");
+    extern __shared__ __align__(16) unsigned char dsm[];
+    auto sX = reinterpret_cast<__nv_bfloat16 (*)[kRowPix][CX]>(dsm);
+    auto sG = reinterpret_cast<TG (*)[CG]>(dsm + 3 * kRowPix * CX * 2);
+    const int tap = threadIdx.x / 64, a = threadIdx.x % 64;
+    const int ky = tap / 3, kx = tap % 3;
+    const int tiles_x = S.W / kTile;
+    const int ntiles = S.B * S.H * tiles_x;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    float bacc = 0.0f;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int b = t / (S.H * tiles_x);
+        const int rem = t - b * S.H * tiles_x;
+        const int y = rem / tiles_x;
+        const int x0 = (rem - y * tiles_x) * kTile;
+        __syncthreads();
+        // staging in 8-byte pieces (4 bf16 of X, or 4 values of dY)
+        for (int i = threadIdx.x; i < 3 * kRowPix * (CX / 4); i += blockDim.x) {
+            const int q = i % (CX / 4), pr = i / (CX / 4), r = pr / kRowPix, p = pr - r * kRowPix;
+            const __nv_bfloat16* src =
+                X + (((size_t)b * S.H + wrap(y + r - 1, S.H)) * S.W + wrap(x0 + p - 1, S.W)) * CX + 4 * q;
+            *reinterpret_cast<uint2*>(&sX[r][p][4 * q]) = *reinterpret_cast<const uint2*>(src);
+        }
+        constexpr int GV = 8 / (int)sizeof(TG);  // dY values per 8-byte piece
+        for (int i = threadIdx.x; i < kTile * (CG / GV); i += blockDim.x) {
+            const int q = i % (CG / GV), p = i / (CG / GV);
+            *reinterpret_cast<uint2*>(&sG[p][GV * q]) =
+                *reinterpret_cast<const uint2*>(dY + (((size_t)b * S.H + y) * S.W + x0 + p) * CG + GV * q);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int p = 0; p < kTile; ++p) {
+            if (CX == 64) {  // a = ci, narrow axis = co (dY fp32, 4 values)
+                const float xv = __bfloat162float(sX[ky][p + kx][a]);
+                float g[4];
+#pragma unroll
+                for (int o = 0; o < 4; ++o) g[o] = to_f<TG>(sG[p][o]);
+#pragma unroll
+                for (int o = 0; o < 4; ++o) acc[o] = fmaf(xv, g[o], acc[o]);
+                if (tap == 0 && a < 4) bacc += g[a & 3];
+            } else {  // a = co, narrow axis = ci
+                const float g = to_f<TG>(sG[p][a]);
+                const uint2 raw = *reinterpret_cast<const uint2*>(&sX[ky][p + kx][0]);
+                const __nv_bfloat16* xv = reinterpret_cast<const __nv_bfloat16*>(&raw);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc[i] = fmaf(__bfloat162float(xv[i]), g, acc[i]);
+                if (tap == 0) bacc += g;
+            }
+        }
+    }
+    float* out = partial + (size_t)blockIdx.x * 9 * CX * CG + (size_t)tap * CX * CG;
+    if (CX == 64) {
+#pragma unroll
+        for (int o = 0; o < 4; ++o) out[a * CG + o] = acc[o];
+        if (tap == 0 && a < 4) partial_b[(size_t)blockIdx.x * CG + a] = bacc;
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) out[i * CG + a] = acc[i];
+        if (tap == 0) partial_b[(size_t)blockIdx.x * CG + a] = bacc;
+    }
+}
+
+// Backward-data weights of a 64 -> 64 layer: Wb[tap'][co][ci] = W[8 - tap'][ci][co] (bf16).
+__global__ void k_flip64(const __nv_bfloat16* __restrict__ W, __nv_bfloat16* __restrict__ Wb) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 9 * kC * kC) return;
+    const int ci = i % kC, co = (i / kC) % kC, tap = i / (kC * kC);
+    Wb[i] = W[((8 - tap) * kC + ci) * kC + co];
+}
+
+// Backward-data weights of a thin layer (fp32): Wb[tap'][co][ci] = W[8 - tap'][ci][co].
+__global__ void k_flip_thin(const float* __restrict__ W, int CI, int CO, float* __restrict__ Wb) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 9 * CI * CO) return;
+    const int ci = i % CI, co = (i / CI) % CO, tap = i / (CI * CO);
+    Wb[i] = W[((8 - tap) * CI + ci) * CO + co];
+}
+
+// Mean squared error of pred against target (fp32, n values) and its gradient
+// 2 (pred - target) / n; per-block partial sums of squares.
+__global__ void k_mse(const float* __restrict__ pred, const float* __restrict__ target, long long n,
+                      float* __restrict__ grad, float* __restrict__ partial) {
+    __shared__ float sh[256];
+    float s = 0.0f;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float d = pred[i] - target[i];
+        grad[i] = 2.0f * d / (float)n;
+        s += d * d;
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if (threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+// Adam (Kingma & Ba): m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+// p -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       long long n, float lr, float b1, float b2, float eps, float c1, float c2) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+__global__ void k_f32_to_bf16(const float* __restrict__ a, long long n, __nv_bfloat16* __restrict__ b) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = __float2bfloat16_rn(a[i]);
+}
+
+__global__ void k_bf16_round_f32(const float* __restrict__ a, long long n, float* __restrict__ b) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = __bfloat162float(__float2bfloat16_rn(a[i]));
+}
+
+}  // namespace cnn
+
+// ---------------------------------------------------------------------------
+// Launchers (plbm_internal.h).
+// ---------------------------------------------------------------------------
+static int g_sms = 0;
+
+static int sm_count() {
+    if (!g_sms) {
+        int d = 0;
+        cudaGetDevice(&d);
+        cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, d);
+        if (g_sms <= 0) g_sms = 1;
+    }
+    return g_sms;
+}
+
+cudaError_t cnn_conv64_fwd(int B, int H, int W, const void* X, const void* Wt, const float* bias, const void* mask,
+                           void* Y, int mode, int relu, cudaStream_t s) {
+    if (W % cnn::kTile) return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(cnn::k_conv64_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             cnn::kMidSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int ntiles = B * H * (W / cnn::kTile);
+    const int grid = ntiles < sm_count() ? ntiles : sm_count();
+    cnn::k_conv64_fwd<<<grid, cnn::kThreadsMid, cnn::kMidSmem, s>>>(
+        cnn::ConvShape{B, H, W}, static_cast<const __nv_bfloat16*>(X), static_cast<const __nv_bfloat16*>(Wt), bias,
+        static_cast<const __nv_bfloat16*>(mask), static_cast<__nv_bfloat16*>(Y), mode, relu);
+    return cudaGetLastError();
+}
+
+int cnn_wgrad64_parts(int B, int H, int W) {
+    const int ntiles = B * H * (W / cnn::kTile);
+    return ntiles < sm_count() ? ntiles : sm_count();
+}
+
+cudaError_t cnn_conv64_wgrad(int B, int H, int W, const void* X, const void* dY, float* partial, float* partial_b,
+                             float* dW, float* db, cudaStream_t s) {
+    if (W % cnn::kTile) return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(cnn::k_conv64_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             cnn::kWgSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int grid = cnn_wgrad64_parts(B, H, W);
+    cnn::k_conv64_wgrad<<<grid, cnn::kThreadsWg, cnn::kWgSmem, s>>>(
+        cnn::ConvShape{B, H, W}, static_cast<const __nv_bfloat16*>(X), static_cast<const __nv_bfloat16*>(dY), partial,
+        partial_b);
+    const int n = 9 * cnn::kC * cnn::kC;
+    cnn::k_sum_partials<<<(n + 255) / 256, 256, 0, s>>>(partial, grid, n, dW);
+    cnn::k_sum_partials<<<1, 64, 0, s>>>(partial_b, grid, cnn::kC, db);
+    return cudaGetLastError();
+}
+
+// Thin layer dispatch: (ci, co, ti, to) with ti/to 0 = bf16, 1 = fp32.
+cudaError_t cnn_conv_thin_fwd(int ci, int co, int ti, int to, int B, int H, int W, const void* X, const float* Wf,
+                              const float* bias, const void* mask, void* Y, int mode, int relu, cudaStream_t s) {
+    cnn::ConvShape S{B, H, W};
+    const __nv_bfloat16* mk = static_cast<const __nv_bfloat16*>(mask);
+    if (ci == 4 && co == 64 && to == 0) {
+        if (W % cnn::kTile) return cudaErrorInvalidValue;
+        const int grid = B * H * (W / cnn::kTile);
+        if (ti == 0)
+            cnn::k_thin_in_fwd<__nv_bfloat16><<<grid, 128, cnn::kInFwdSmem, s>>>(
+                S, static_cast<const __nv_bfloat16*>(X), Wf, bias, mk, static_cast<__nv_bfloat16*>(Y), mode, relu);
+        else
+            cnn::k_thin_in_fwd<float><<<grid, 128, cnn::kInFwdSmem, s>>>(
+                S, static_cast<const float*>(X), Wf, bias, mk, static_cast<__nv_bfloat16*>(Y), mode, relu);
+    } else if (ci == 64 && co == 4 && ti == 0 && to == 1 && mode == 0 && !relu) {
+        if (W % cnn::kTile) return cudaErrorInvalidValue;
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(cnn::k_thin_out_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 cnn::kOutSmem);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        const int grid = B * H * (W / cnn::kTile);
+        cnn::k_thin_out_fwd<<<grid, 128, cnn::kOutSmem, s>>>(S, static_cast<const __nv_bfloat16*>(X), Wf, bias,
+                                                             static_cast<float*>(Y));
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+int cnn_thin_parts(int B, int H, int W, int* pix_per_block) {
+    const int ntiles = B * H * (W / cnn::kTile);
+    const int parts = ntiles < 2 * sm_count() ? ntiles : 2 * sm_count();
+    if (pix_per_block) *pix_per_block = cnn::kTile;
+    return parts;
+}
+
+cudaError_t cnn_conv_thin_wgrad(int ci, int co, int tx, int tg, int B, int H, int W, const void* X, const void* dY,
+                                float* partial, float* partial_b, float* dW, float* db, cudaStream_t s) {
+    if (W % cnn::kTile || tx != 0) return cudaErrorInvalidValue;
+    const int parts = cnn_thin_parts(B, H, W, nullptr);
+    cnn::ConvShape S{B, H, W};
+    const __nv_bfloat16* Xb = static_cast<const __nv_bfloat16*>(X);
+    if (ci == 4 && co == 64 && tg == 0) {
+        constexpr int sm = cnn::thin_wgrad_smem<4, 64, __nv_bfloat16>();
+        cnn::k_thin_wgrad<4, 64, __nv_bfloat16><<<parts, 576, sm, s>>>(S, Xb, static_cast<const __nv_bfloat16*>(dY),
+                                                                      partial, partial_b);
+    } else if (ci == 64 && co == 4 && tg == 1) {
+        constexpr int sm = cnn::thin_wgrad_smem<64, 4, float>();
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(cnn::k_thin_wgrad<64, 4, float>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        cnn::k_thin_wgrad<64, 4, float><<<parts, 576, sm, s>>>(S, Xb, static_cast<const float*>(dY), partial,
+                                                               partial_b);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    const int n = 9 * ci * co;
+    cnn::k_sum_partials<<<(n + 255) / 256, 256, 0, s>>>(partial, parts, n, dW);
+    cnn::k_sum_partials<<<1, 64, 0, s>>>(partial_b, parts, co, db);
+    return cudaGetLastError();
+}
+
+cudaError_t cnn_flip64(const void* W, void* Wb, cudaStream_t s) {
+    cnn::k_flip64<<<(9 * 64 * 64 + 255) / 256, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(W),
+                                                            static_cast<__nv_bfloat16*>(Wb));
+    return cudaGetLastError();
+}
+
+cudaError_t cnn_flip_thin(const float* W, int ci, int co, float* Wb, cudaStream_t s) {
+    cnn::k_flip_thin<<<(9 * ci * co + 255) / 256, 256, 0, s>>>(W, ci, co, Wb);
+    return cudaGetLastError();
+}
+
+cudaError_t cnn_mse(const float* pred, const float* target, long long n, float* grad, float* partial, int parts,
+                    cudaStream_t s) {
+    cnn::k_mse<<<parts, 256, 0, s>>>(pred, target, n, grad, partial);
+    return cudaGetLastError();
+}
+
+cudaError_t cnn_adam(float* p, const float* g, float* m, float* v, long long n, float lr, float b1, float b2, float eps,
+                     int t, cudaStream_t s) {
+    const float c1 = 1.0f - powf(b1, (float)t), c2 = 1.0f - powf(b2, (float)t);
+    cnn::k_adam<<<(int)((n + 255) / 256), 256, 0, s>>>(p, g, m, v, n, lr, b1, b2, eps, c1, c2);
+    return cudaGetLastError();
+}
+
+cudaError_t cnn_to_bf16(const float* a, long long n, void* b, cudaStream_t s) {
+    cnn::k_f32_to_bf16<<<(int)((n + 255) / 256), 256, 0, s>>>(a, n, static_cast<__nv_bfloat16*>(b));
+    return cudaGetLastError();
+}
+
+cudaError_t cnn_bf16_round(const float* a, long long n, float* b, cudaStream_t s) {
+    cnn::k_bf16_round_f32<<<(int)((n + 255) / 256), 256, 0, s>>>(a, n, b);
+    return cudaGetLastError();
+}
+
+}  // namespace plbm

@@ -242,6 +242,17 @@ struct Staging {
 
 namespace plbm {
 void set_thread_error(const char* msg) { std::snprintf(g_thread_error, sizeof g_thread_error, "%s", msg); }
+
+bool handle_view(void* hh, HandleView* out) {
+    Handle* h = static_cast<Handle*>(hh);
+    if (!h || !out || !h->initialised || h->sticky != PLBM_OK) return false;
+    out->P = &h->P;
+    out->f_cur = h->f[h->cur];
+    out->prec = h->prec;
+    out->stream = h->stream;
+    out->steps = &h->steps;
+    return true;
+}
 }  // namespace plbm
 
 extern "C" {

@@ -104,6 +104,48 @@ inline PairParams pair_params(const LatticeParams& P) {
 double spectral_radius(int dim, int q1, const int* v, const double* C, double omega, double theta0,
                        bool isothermal, double ux, int nk, double stop_above);
 
+// Surrogate kernels (plbm_cnn.cu, plbm_ce.cu).
+cudaError_t cnn_conv64_fwd(int B, int H, int W, const void* X, const void* Wt, const float* bias, const void* mask,
+                           void* Y, int mode, int relu, cudaStream_t s);
+int cnn_wgrad64_parts(int B, int H, int W);
+cudaError_t cnn_conv64_wgrad(int B, int H, int W, const void* X, const void* dY, float* partial, float* partial_b,
+                             float* dW, float* db, cudaStream_t s);
+cudaError_t cnn_conv_thin_fwd(int ci, int co, int ti, int to, int B, int H, int W, const void* X, const float* Wf,
+                              const float* bias, const void* mask, void* Y, int mode, int relu, cudaStream_t s);
+int cnn_thin_parts(int B, int H, int W, int* pix_per_block);
+cudaError_t cnn_conv_thin_wgrad(int ci, int co, int tx, int tg, int B, int H, int W, const void* X, const void* dY,
+                                float* partial, float* partial_b, float* dW, float* db, cudaStream_t s);
+cudaError_t cnn_flip64(const void* W, void* Wb, cudaStream_t s);
+cudaError_t cnn_flip_thin(const float* W, int ci, int co, float* Wb, cudaStream_t s);
+cudaError_t cnn_mse(const float* pred, const float* target, long long n, float* grad, float* partial, int parts,
+                    cudaStream_t s);
+cudaError_t cnn_adam(float* p, const float* g, float* m, float* v, long long n, float lr, float b1, float b2, float eps,
+                     int t, cudaStream_t s);
+cudaError_t cnn_to_bf16(const float* a, long long n, void* b, cudaStream_t s);
+cudaError_t cnn_bf16_round(const float* a, long long n, float* b, cudaStream_t s);
+cudaError_t ce_pack_fields(const double* rho, const double* ux, const double* uy, const double* th, long long n,
+                           float* out, cudaStream_t s);
+cudaError_t ce_assemble(const float* snaps, long long npix, const int* pairs, int B, const float* mean_in,
+                        const float* std_in, const float* mean_d, const float* std_d, void* x, float* y,
+                        cudaStream_t s);
+cudaError_t ce_normalise(const float* F, long long n, const float* mean_in, const float* std_in, void* x,
+                         cudaStream_t s);
+cudaError_t ce_apply_delta(const float* F, const float* d, long long n, const float* mean_d, const float* std_d,
+                           float* out, cudaStream_t s);
+int ce_sum_blocks();
+cudaError_t ce_field_sums(const float* F, long long n, double* partial, cudaStream_t s);
+cudaError_t ce_reconstruct(int prec, const LatticeParams& P, const float* F, void* f, cudaStream_t s);
+
+// Internals of a live handle for the surrogate path (plbm_host.cpp).
+struct HandleView {
+    const LatticeParams* P;
+    void* f_cur;
+    int prec;
+    cudaStream_t stream;
+    long long* steps;
+};
+bool handle_view(void* h, HandleView* out);
+
 // Records the error text returned by plbm_last_error(NULL) for this thread.
 void set_thread_error(const char* msg);
 

@@ -1,0 +1,448 @@
+// Learned surrogate: network state, training step, inference and the advance
+// of lattices by K steps with Chapman-Enskog reconstruction and LBM fallback.
+//
+// Network: 6 convolutions 3x3 with circular padding, channels 4 -> 64 -> 64 ->
+// 64 -> 64 -> 64 -> 4, ReLU after the first five, BF16 activations and
+// weights with FP32 accumulation, FP32 master weights and Adam state.  Input:
+// normalised (rho, u_x, u_y, theta) of a periodic lattice; output: the
+// normalised change of those fields over K lattice steps.
+//
+// Flat parameter layout (FP32): for each layer, W[3][3][cin][cout] then b[cout].
+#include "plbm.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "plbm_internal.h"
+
+namespace {
+
+constexpr int kLayers = 6;
+constexpr int kCin[kLayers] = {4, 64, 64, 64, 64, 64};
+constexpr int kCout[kLayers] = {64, 64, 64, 64, 64, 4};
+
+struct Sur {
+    int Bm = 0, H = 0, W = 0;
+    cudaStream_t stream = nullptr;
+    bool owns_stream = false;
+    long long woff[kLayers], boff[kLayers], nparams = 0;
+    float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
+    float* pr = nullptr;            // parameters rounded to bf16 precision (fp32 storage)
+    void* wbf = nullptr;            // bf16 weights of layers 1..4 (64 -> 64), 4 x 9*64*64
+    void* wflip = nullptr;          // their backward-data form
+    float* w6flip = nullptr;        // backward-data weights of the last layer (4 -> 64)
+    void* act[kLayers] = {nullptr}; // act[0..4] bf16 [B][H][W][64]; act[5] fp32 [B][H][W][4]
+    void* dz[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // dL/d(pre-activation) of layers 1..5
+    float* dout = nullptr;
+    float *part = nullptr, *part_b = nullptr;
+    float* loss_part = nullptr;
+    float* host_loss = nullptr;
+    int adam_t = 0;
+    float norm[16] = {0, 0, 0, 0, 1, 1, 1, 1, 0, 0, 0, 0, 1, 1, 1, 1};  // mean_in, std_in, mean_d, std_d
+    // advance scratch
+    float *Fold = nullptr, *Fnew = nullptr;
+    void* xin = nullptr;
+    double* planes = nullptr;
+    double* sums = nullptr;
+    double* host_sums = nullptr;
+    char err[512] = "";
+};
+
+void serr(Sur* s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    plbm::set_thread_error(buf);
+    if (s) std::snprintf(s->err, sizeof s->err, "%s", buf);
+}
+
+#define SCK(call)                                                              \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess) {                                               \
+            serr(s, "%s failed: %s", #call, cudaGetErrorString(e_));           \
+            return PLBM_E_CUDA;                                                \
+        }                                                                      \
+    } while (0)
+
+// splitmix64 and Box-Muller: a fully specified generator, so the initial
+// weights are the same on every host.
+uint64_t splitmix(uint64_t& x) {
+    uint64_t z = (x += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+double uniform01(uint64_t& st) { return ((splitmix(st) >> 11) + 0.5) * (1.0 / 9007199254740992.0); }
+double normal(uint64_t& st) {
+    const double u1 = uniform01(st), u2 = uniform01(st);
+    return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+}
+
+void free_sur(Sur* s) {
+    if (!s) return;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    void* bufs[] = {s->p, s->g, s->m, s->v, s->pr, s->wbf, s->wflip, s->w6flip, s->dz[0], s->dz[1], s->dz[2],
+                    s->dz[3], s->dz[4], s->dout, s->part, s->part_b, s->loss_part, s->Fold, s->Fnew, s->xin,
+                    s->planes, s->sums};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    for (void* a : s->act)
+        if (a) cudaFree(a);
+    if (s->host_loss) cudaFreeHost(s->host_loss);
+    if (s->host_sums) cudaFreeHost(s->host_sums);
+    if (s->owns_stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+// Rounded copies, bf16 weights and backward-data weights from the FP32 master weights.
+plbm_status refresh_weights(Sur* s) {
+    SCK(plbm::cnn_bf16_round(s->p, s->nparams, s->pr, s->stream));
+    for (int l = 1; l <= 4; ++l) {
+        char* wb = static_cast<char*>(s->wbf) + (size_t)(l - 1) * 9 * 64 * 64 * 2;
+        char* wf = static_cast<char*>(s->wflip) + (size_t)(l - 1) * 9 * 64 * 64 * 2;
+        SCK(plbm::cnn_to_bf16(s->p + s->woff[l], 9LL * 64 * 64, wb, s->stream));
+        SCK(plbm::cnn_flip64(wb, wf, s->stream));
+    }
+    SCK(plbm::cnn_flip_thin(s->pr + s->woff[5], 64, 4, s->w6flip, s->stream));
+    return PLBM_OK;
+}
+
+plbm_status forward(Sur* s, int B, const void* x) {
+    const int H = s->H, W = s->W;
+    SCK(plbm::cnn_conv_thin_fwd(4, 64, 0, 0, B, H, W, x, s->pr + s->woff[0], s->p + s->boff[0], nullptr, s->act[0],
+                                0, 1, s->stream));
+    for (int l = 1; l <= 4; ++l) {
+        const char* wb = static_cast<const char*>(s->wbf) + (size_t)(l - 1) * 9 * 64 * 64 * 2;
+        SCK(plbm::cnn_conv64_fwd(B, H, W, s->act[l - 1], wb, s->p + s->boff[l], nullptr, s->act[l], 0, 1,
+                                 s->stream));
+    }
+    SCK(plbm::cnn_conv_thin_fwd(64, 4, 0, 1, B, H, W, s->act[4], s->pr + s->woff[5], s->p + s->boff[5], nullptr,
+                                s->act[5], 0, 0, s->stream));
+    return PLBM_OK;
+}
+
+// Gradients of every parameter into s->g for the upstream gradient dout of the
+// output.  dz[k] keeps dL/dZ of layer k + 1 (Z = convolution output before ReLU).
+plbm_status backward(Sur* s, int B, const void* x, const float* dout) {
+    const int H = s->H, W = s->W;
+    // last layer (64 -> 4): weights, then dZ_5 = (conv^T dout) * (A_5 > 0)
+    SCK(plbm::cnn_conv_thin_wgrad(64, 4, 0, 1, B, H, W, s->act[4], dout, s->part, s->part_b, s->g + s->woff[5],
+                                  s->g + s->boff[5], s->stream));
+    SCK(plbm::cnn_conv_thin_fwd(4, 64, 1, 0, B, H, W, dout, s->w6flip, nullptr, s->act[4], s->dz[4], 1, 0,
+                                s->stream));
+    for (int l = 4; l >= 1; --l) {
+        SCK(plbm::cnn_conv64_wgrad(B, H, W, s->act[l - 1], s->dz[l], s->part, s->part_b, s->g + s->woff[l],
+                                   s->g + s->boff[l], s->stream));
+        const char* wf = static_cast<const char*>(s->wflip) + (size_t)(l - 1) * 9 * 64 * 64 * 2;
+        SCK(plbm::cnn_conv64_fwd(B, H, W, s->dz[l], wf, nullptr, s->act[l - 1], s->dz[l - 1], 1, 0, s->stream));
+    }
+    SCK(plbm::cnn_conv_thin_wgrad(4, 64, 0, 0, B, H, W, x, s->dz[0], s->part, s->part_b, s->g + s->woff[0],
+                                  s->g + s->boff[0], s->stream));
+    return PLBM_OK;
+}
+
+Sur* as_sur(plbm_surrogate h) { return reinterpret_cast<Sur*>(h); }
+
+}  // namespace
+
+extern "C" {
+
+int plbm_sur_num_params(void) {
+    long long n = 0;
+    for (int l = 0; l < kLayers; ++l) n += 9LL * kCin[l] * kCout[l] + kCout[l];
+    return (int)n;
+}
+
+plbm_status plbm_sur_create(int max_batch, int H, int W, unsigned long long seed, void* stream, plbm_surrogate* out) {
+    if (!out || max_batch < 1 || H < 3 || W < 128 || W % 128) {
+        serr(nullptr, "plbm_sur_create: need max_batch >= 1, H >= 3 and W a multiple of 128");
+        return PLBM_E_ARG;
+    }
+    *out = nullptr;
+    Sur* s = new (std::nothrow) Sur();
+    if (!s) return PLBM_E_NOMEM;
+    s->Bm = max_batch;
+    s->H = H;
+    s->W = W;
+    if (stream) {
+        s->stream = static_cast<cudaStream_t>(stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            serr(s, "cudaStreamCreate failed");
+            delete s;
+            return PLBM_E_CUDA;
+        }
+        s->owns_stream = true;
+    }
+    long long off = 0;
+    for (int l = 0; l < kLayers; ++l) {
+        s->woff[l] = off;
+        off += 9LL * kCin[l] * kCout[l];
+        s->boff[l] = off;
+        off += kCout[l];
+    }
+    s->nparams = off;
+    const size_t np = (size_t)off * sizeof(float);
+    const size_t pix = (size_t)max_batch * H * W;
+    int pb = 0;
+    const int thin_parts = plbm::cnn_thin_parts(max_batch, H, W, &pb);
+    const int mid_parts = plbm::cnn_wgrad64_parts(max_batch, H, W);
+    const size_t part_n = std::max((size_t)mid_parts * 9 * 64 * 64, (size_t)thin_parts * 9 * 64 * 4);
+    const size_t partb_n = (size_t)std::max(mid_parts, thin_parts) * 64;
+    struct A {
+        void** p;
+        size_t n;
+    } allocs[] = {
+        {(void**)&s->p, np}, {(void**)&s->g, np}, {(void**)&s->m, np}, {(void**)&s->v, np}, {(void**)&s->pr, np},
+        {&s->wbf, 4 * 9 * 64 * 64 * 2}, {&s->wflip, 4 * 9 * 64 * 64 * 2}, {(void**)&s->w6flip, 9 * 4 * 64 * 4},
+        {&s->dz[0], pix * 64 * 2}, {&s->dz[1], pix * 64 * 2}, {&s->dz[2], pix * 64 * 2},
+        {&s->dz[3], pix * 64 * 2}, {&s->dz[4], pix * 64 * 2}, {(void**)&s->dout, pix * 4 * 4},
+        {(void**)&s->part, part_n * 4}, {(void**)&s->part_b, partb_n * 4}, {(void**)&s->loss_part, 1024 * 4},
+        {(void**)&s->Fold, pix * 4 * 4}, {(void**)&s->Fnew, pix * 4 * 4}, {&s->xin, pix * 4 * 2},
+        {(void**)&s->planes, (size_t)H * W * 4 * 8}, {(void**)&s->sums, (size_t)max_batch * 2 * 64 * 4 * 8},
+    };
+    for (auto& a : allocs) {
+        if (cudaMalloc(a.p, a.n) != cudaSuccess) {
+            serr(s, "cudaMalloc of %zu bytes failed", a.n);
+            free_sur(s);
+            return PLBM_E_NOMEM;
+        }
+    }
+    for (int l = 0; l < 5; ++l) {
+        if (cudaMalloc(&s->act[l], pix * 64 * 2) != cudaSuccess) {
+            serr(s, "cudaMalloc of activations failed");
+            free_sur(s);
+            return PLBM_E_NOMEM;
+        }
+    }
+    if (cudaMalloc(&s->act[5], pix * 4 * 4) != cudaSuccess ||
+        cudaMallocHost((void**)&s->host_loss, 1024 * 4) != cudaSuccess ||
+        cudaMallocHost((void**)&s->host_sums, (size_t)max_batch * 2 * 64 * 4 * 8) != cudaSuccess) {
+        serr(s, "allocation failed");
+        free_sur(s);
+        return PLBM_E_NOMEM;
+    }
+    // He initialisation (normal, std sqrt(2 / fan_in)); the last layer scaled by 0.1 so
+    // that an untrained network predicts almost no change.  Biases zero.
+    std::vector<float> h(off, 0.0f);
+    uint64_t st = seed * 0x2545F4914F6CDD1DULL + 12345;
+    for (int l = 0; l < kLayers; ++l) {
+        const double sd = std::sqrt(2.0 / (9.0 * kCin[l])) * (l == kLayers - 1 ? 0.1 : 1.0);
+        for (long long k = 0; k < 9LL * kCin[l] * kCout[l]; ++k) h[s->woff[l] + k] = (float)(sd * normal(st));
+    }
+    plbm_surrogate out_h = reinterpret_cast<plbm_surrogate>(s);
+    plbm_status r = plbm_sur_set_params(out_h, h.data());
+    if (r != PLBM_OK) {
+        free_sur(s);
+        return r;
+    }
+    *out = out_h;
+    return PLBM_OK;
+}
+
+plbm_status plbm_sur_destroy(plbm_surrogate h) {
+    free_sur(as_sur(h));
+    return PLBM_OK;
+}
+
+plbm_status plbm_sur_set_params(plbm_surrogate h, const float* params) {
+    Sur* s = as_sur(h);
+    if (!s || !params) return PLBM_E_ARG;
+    SCK(cudaMemcpyAsync(s->p, params, s->nparams * 4, cudaMemcpyHostToDevice, s->stream));
+    SCK(cudaMemsetAsync(s->m, 0, s->nparams * 4, s->stream));
+    SCK(cudaMemsetAsync(s->v, 0, s->nparams * 4, s->stream));
+    s->adam_t = 0;
+    plbm_status r = refresh_weights(s);
+    if (r != PLBM_OK) return r;
+    SCK(cudaStreamSynchronize(s->stream));
+    return PLBM_OK;
+}
+
+plbm_status plbm_sur_get_params(plbm_surrogate h, float* params, float* grads) {
+    Sur* s = as_sur(h);
+    if (!s) return PLBM_E_ARG;
+    if (params) SCK(cudaMemcpyAsync(params, s->p, s->nparams * 4, cudaMemcpyDeviceToHost, s->stream));
+    if (grads) SCK(cudaMemcpyAsync(grads, s->g, s->nparams * 4, cudaMemcpyDeviceToHost, s->stream));
+    SCK(cudaStreamSynchronize(s->stream));
+    return PLBM_OK;
+}
+
+plbm_status plbm_sur_set_norm(plbm_surrogate h, const float* mean_in, const float* std_in, const float* mean_d,
+                              const float* std_d) {
+    Sur* s = as_sur(h);
+    if (!s || !mean_in || !std_in || !mean_d || !std_d) return PLBM_E_ARG;
+    for (int k = 0; k < 4; ++k) {
+        if (!(std_in[k] > 0.0f) || !(std_d[k] > 0.0f)) {
+            serr(s, "standard deviations must be > 0");
+            return PLBM_E_ARG;
+        }
+        s->norm[k] = mean_in[k];
+        s->norm[4 + k] = std_in[k];
+        s->norm[8 + k] = mean_d[k];
+        s->norm[12 + k] = std_d[k];
+    }
+    return PLBM_OK;
+}
+
+plbm_status plbm_sur_forward(plbm_surrogate h, int B, const void* x, float* out) {
+    Sur* s = as_sur(h);
+    if (!s || !x || B < 1 || B > s->Bm) return PLBM_E_ARG;
+    plbm_status r = forward(s, B, x);
+    if (r != PLBM_OK) return r;
+    if (out) SCK(cudaMemcpyAsync(out, s->act[5], (size_t)B * s->H * s->W * 16, cudaMemcpyDeviceToDevice, s->stream));
+    return PLBM_OK;
+}
+
+plbm_status plbm_sur_backward(plbm_surrogate h, int B, const void* x, const float* dout) {
+    Sur* s = as_sur(h);
+    if (!s || !x || !dout || B < 1 || B > s->Bm) return PLBM_E_ARG;
+    plbm_status r = forward(s, B, x);
+    if (r != PLBM_OK) return r;
+    return backward(s, B, x, dout);
+}
+
+plbm_status plbm_sur_copy(plbm_surrogate h, int kind, int layer, int B, void* dst) {
+    Sur* s = as_sur(h);
+    if (!s || !dst || B < 1 || B > s->Bm) return PLBM_E_ARG;
+    const size_t pix = (size_t)B * s->H * s->W;
+    const void* src = nullptr;
+    size_t bytes = 0;
+    if (kind == 0 && layer >= 1 && layer <= 5) {
+        src = s->act[layer - 1];
+        bytes = pix * 64 * 2;
+    } else if (kind == 0 && layer == 6) {
+        src = s->act[5];
+        bytes = pix * 4 * 4;
+    } else if (kind == 1 && layer >= 1 && layer <= 5) {
+        src = s->dz[layer - 1];
+        bytes = pix * 64 * 2;
+    } else {
+        serr(s, "plbm_sur_copy: kind 0 takes layers 1..6, kind 1 layers 1..5");
+        return PLBM_E_ARG;
+    }
+    SCK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s->stream));
+    SCK(cudaStreamSynchronize(s->stream));
+    return PLBM_OK;
+}
+
+plbm_status plbm_sur_train_step(plbm_surrogate h, int B, const void* x, const float* target, float lr, float* loss) {
+    Sur* s = as_sur(h);
+    if (!s || !x || !target || B < 1 || B > s->Bm || !(lr > 0.0f)) return PLBM_E_ARG;
+    plbm_status r = forward(s, B, x);
+    if (r != PLBM_OK) return r;
+    const long long n = (long long)B * s->H * s->W * 4;
+    const int parts = 256;
+    SCK(plbm::cnn_mse(static_cast<const float*>(s->act[5]), target, n, s->dout, s->loss_part, parts, s->stream));
+    r = backward(s, B, x, s->dout);
+    if (r != PLBM_OK) return r;
+    ++s->adam_t;
+    SCK(plbm::cnn_adam(s->p, s->g, s->m, s->v, s->nparams, lr, 0.9f, 0.999f, 1e-8f, s->adam_t, s->stream));
+    r = refresh_weights(s);
+    if (r != PLBM_OK) return r;
+    if (loss) {
+        SCK(cudaMemcpyAsync(s->host_loss, s->loss_part, parts * 4, cudaMemcpyDeviceToHost, s->stream));
+        SCK(cudaStreamSynchronize(s->stream));
+        double t = 0.0;
+        for (int k = 0; k < parts; ++k) t += s->host_loss[k];
+        *loss = (float)(t / (double)n);
+    }
+    return PLBM_OK;
+}
+
+plbm_status plbm_sur_pack_fields(const double* rho, const double* ux, const double* uy, const double* theta,
+                                 long long n, float* out, void* stream) {
+    if (!rho || !ux || !uy || !theta || !out || n < 1) return PLBM_E_ARG;
+    cudaError_t e = plbm::ce_pack_fields(rho, ux, uy, theta, n, out, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? PLBM_OK : PLBM_E_CUDA;
+}
+
+plbm_status plbm_sur_assemble(plbm_surrogate h, const float* snaps, long long npix, const int* pairs, int B, void* x,
+                              float* y) {
+    Sur* s = as_sur(h);
+    if (!s || !snaps || !pairs || !x || !y || B < 1) return PLBM_E_ARG;
+    SCK(plbm::ce_assemble(snaps, npix, pairs, B, s->norm, s->norm + 4, s->norm + 8, s->norm + 12, x, y, s->stream));
+    return PLBM_OK;
+}
+
+plbm_status plbm_sur_advance(plbm_surrogate h, plbm_handle* hs, int n, int K, double tol, int* fell_back) {
+    Sur* s = as_sur(h);
+    if (!s || !hs || n < 1 || n > s->Bm || K < 1) return PLBM_E_ARG;
+    const long long npix = (long long)s->H * s->W;
+    std::vector<plbm::HandleView> views(n);
+    for (int b = 0; b < n; ++b) {
+        if (!plbm::handle_view(hs[b], &views[b])) {
+            serr(s, "handle %d is not initialised or in an error state", b);
+            return PLBM_E_STATE;
+        }
+        const plbm::LatticeParams& P = *views[b].P;
+        if (P.dim != 2 || P.nx != s->W || P.ny != s->H || P.fixed_ends) {
+            serr(s, "handle %d: the surrogate takes periodic %d x %d lattices", b, s->W, s->H);
+            return PLBM_E_ARG;
+        }
+    }
+    SCK(cudaStreamSynchronize(s->stream));
+    double* pl = s->planes;
+    for (int b = 0; b < n; ++b) {
+        // moments on the handle's stream, then pack on it as well
+        plbm_status r = plbm_moments(hs[b], pl, pl + npix, pl + 2 * npix, pl + 3 * npix, 1);
+        if (r != PLBM_OK) return r;
+        SCK(plbm::ce_pack_fields(pl, pl + npix, pl + 2 * npix, pl + 3 * npix, npix, s->Fold + (size_t)b * npix * 4,
+                                 views[b].stream));
+        SCK(cudaStreamSynchronize(views[b].stream));
+    }
+    SCK(plbm::ce_normalise(s->Fold, npix * n, s->norm, s->norm + 4, s->xin, s->stream));
+    plbm_status r = forward(s, n, s->xin);
+    if (r != PLBM_OK) return r;
+    SCK(plbm::ce_apply_delta(s->Fold, static_cast<const float*>(s->act[5]), npix * n, s->norm + 8, s->norm + 12, s->Fnew, s->stream));
+    const int nb = plbm::ce_sum_blocks();
+    for (int b = 0; b < n; ++b) {
+        SCK(plbm::ce_field_sums(s->Fold + (size_t)b * npix * 4, npix, s->sums + (size_t)(2 * b) * nb * 4, s->stream));
+        SCK(plbm::ce_field_sums(s->Fnew + (size_t)b * npix * 4, npix, s->sums + (size_t)(2 * b + 1) * nb * 4,
+                                s->stream));
+    }
+    SCK(cudaMemcpyAsync(s->host_sums, s->sums, (size_t)n * 2 * nb * 4 * 8, cudaMemcpyDeviceToHost, s->stream));
+    SCK(cudaStreamSynchronize(s->stream));
+    for (int b = 0; b < n; ++b) {
+        double so[4] = {0, 0, 0, 0}, sn[4] = {0, 0, 0, 0};
+        for (int k = 0; k < nb; ++k)
+            for (int j = 0; j < 4; ++j) {
+                so[j] += s->host_sums[((size_t)(2 * b) * nb + k) * 4 + j];
+                sn[j] += s->host_sums[((size_t)(2 * b + 1) * nb + k) * 4 + j];
+            }
+        // relative drift: mass and energy against themselves, momentum against 0.1 M
+        const double dm = std::fabs(sn[0] - so[0]) / std::fabs(so[0]);
+        const double de = std::fabs(sn[3] - so[3]) / std::fabs(so[3]);
+        const double dj = std::hypot(sn[1] - so[1], sn[2] - so[2]) / (0.1 * std::fabs(so[0]));
+        const double drift = std::fmax(dm, std::fmax(de, dj));
+        const bool fall = !(drift <= tol);
+        if (fell_back) fell_back[b] = fall ? 1 : 0;
+        if (fall) {
+            r = plbm_step(hs[b], K);
+            if (r != PLBM_OK) return r;
+        } else {
+            SCK(cudaStreamSynchronize(s->stream));
+            SCK(plbm::ce_reconstruct(views[b].prec, *views[b].P, s->Fnew + (size_t)b * npix * 4, views[b].f_cur,
+                                     views[b].stream));
+            *views[b].steps += K;
+        }
+    }
+    return PLBM_OK;
+}
+
+const char* plbm_sur_last_error(plbm_surrogate h) {
+    Sur* s = as_sur(h);
+    return s ? s->err : plbm_last_error(nullptr);
+}
+
+}  // extern "C"

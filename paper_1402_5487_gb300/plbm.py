@@ -116,6 +116,25 @@ SIGNATURES = {
     "plbm_diagnostics_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                                  ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                                  ctypes.c_void_p, ctypes.c_void_p]),
+    "plbm_sur_num_params": (ctypes.c_int, []),
+    "plbm_sur_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong,
+                                       ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "plbm_sur_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "plbm_sur_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "plbm_sur_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "plbm_sur_set_norm": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_float)] * 4),
+    "plbm_sur_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "plbm_sur_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "plbm_sur_copy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    "plbm_sur_train_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_float, ctypes.POINTER(ctypes.c_float)]),
+    "plbm_sur_pack_fields": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.c_longlong, ctypes.c_void_p,
+                                                                     ctypes.c_void_p]),
+    "plbm_sur_assemble": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p,
+                                         ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "plbm_sur_advance": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_int)]),
+    "plbm_sur_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "plbm_last_error": (ctypes.c_char_p, [_H]),
     "plbm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
