@@ -292,6 +292,15 @@ plbm_status plbm_sur_create(int max_batch, int H, int W, unsigned long long seed
                             plbm_surrogate *out);
 plbm_status plbm_sur_destroy(plbm_surrogate s);
 
+/* Options: PLBM_SUR_OPT_TENSOR_PATH selects the kernel of the 64 -> 64
+ * convolutions and their backward-data passes: 1 (default) tcgen05.mma with
+ * tensor-memory accumulators, 0 mma.sync (kept as a cross-check). */
+#define PLBM_SUR_OPT_TENSOR_PATH 1
+plbm_status plbm_sur_set_option(plbm_surrogate s, int option, int value);
+
+/* PLBM_E_TIMEOUT if a bounded wait of a tensor-core kernel ran out (synchronous). */
+plbm_status plbm_sur_check(plbm_surrogate s);
+
 /* Replace (host FP32, resets Adam) or read the parameters and the last gradients. */
 plbm_status plbm_sur_set_params(plbm_surrogate s, const float *params);
 plbm_status plbm_sur_get_params(plbm_surrogate s, float *params, float *grads);

@@ -29,6 +29,7 @@ SOURCES = [
     "plbm_step_bf16.cu",
     "plbm_noalloc.cu",
     "plbm_cnn.cu",
+    "plbm_cnn_tc.cu",
     "plbm_ce.cu",
     "plbm_surrogate.cpp",
 ]

@@ -117,6 +117,9 @@ cudaError_t cnn_conv_thin_wgrad(int ci, int co, int tx, int tg, int B, int H, in
                                 float* partial, float* partial_b, float* dW, float* db, cudaStream_t s);
 cudaError_t cnn_flip64(const void* W, void* Wb, cudaStream_t s);
 cudaError_t cnn_flip_thin(const float* W, int ci, int co, float* Wb, cudaStream_t s);
+cudaError_t cnn_conv64_tc(int B, int H, int W, const void* X, const void* Wk, const float* bias, const void* mask,
+                          void* Y, int mode, int relu, unsigned* err, cudaStream_t s);
+cudaError_t cnn_weights_kmajor(const void* W, void* Wf, void* Wb, cudaStream_t s);
 cudaError_t cnn_mse(const float* pred, const float* target, long long n, float* grad, float* partial, int parts,
                     cudaStream_t s);
 cudaError_t cnn_adam(float* p, const float* g, float* m, float* v, long long n, float lr, float b1, float b2, float eps,

@@ -39,6 +39,9 @@ struct Sur {
     void* wbf = nullptr;            // bf16 weights of layers 1..4 (64 -> 64), 4 x 9*64*64
     void* wflip = nullptr;          // their backward-data form
     float* w6flip = nullptr;        // backward-data weights of the last layer (4 -> 64)
+    void* wtc = nullptr;            // K-major bf16 weights for tcgen05: 4 layers x (forward, backward data)
+    unsigned* derr = nullptr;       // device flag: a bounded wait in a tensor-core kernel ran out
+    int use_tc = 1;                 // 64 -> 64 forward and backward data: 1 tcgen05, 0 mma.sync
     void* act[kLayers] = {nullptr}; // act[0..4] bf16 [B][H][W][64]; act[5] fp32 [B][H][W][4]
     void* dz[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // dL/d(pre-activation) of layers 1..5
     float* dout = nullptr;
@@ -94,7 +97,7 @@ void free_sur(Sur* s) {
     if (s->stream) cudaStreamSynchronize(s->stream);
     void* bufs[] = {s->p, s->g, s->m, s->v, s->pr, s->wbf, s->wflip, s->w6flip, s->dz[0], s->dz[1], s->dz[2],
                     s->dz[3], s->dz[4], s->dout, s->part, s->part_b, s->loss_part, s->Fold, s->Fnew, s->xin,
-                    s->planes, s->sums};
+                    s->planes, s->sums, s->wtc, s->derr};
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (void* a : s->act)
@@ -105,6 +108,9 @@ void free_sur(Sur* s) {
     delete s;
 }
 
+void* wtc_fwd(Sur* s, int l) { return static_cast<char*>(s->wtc) + (size_t)(2 * (l - 1)) * 9 * 64 * 64 * 2; }
+void* wtc_bwd(Sur* s, int l) { return static_cast<char*>(s->wtc) + (size_t)(2 * (l - 1) + 1) * 9 * 64 * 64 * 2; }
+
 // Rounded copies, bf16 weights and backward-data weights from the FP32 master weights.
 plbm_status refresh_weights(Sur* s) {
     SCK(plbm::cnn_bf16_round(s->p, s->nparams, s->pr, s->stream));
@@ -113,6 +119,7 @@ plbm_status refresh_weights(Sur* s) {
         char* wf = static_cast<char*>(s->wflip) + (size_t)(l - 1) * 9 * 64 * 64 * 2;
         SCK(plbm::cnn_to_bf16(s->p + s->woff[l], 9LL * 64 * 64, wb, s->stream));
         SCK(plbm::cnn_flip64(wb, wf, s->stream));
+        SCK(plbm::cnn_weights_kmajor(wb, wtc_fwd(s, l), wtc_bwd(s, l), s->stream));
     }
     SCK(plbm::cnn_flip_thin(s->pr + s->woff[5], 64, 4, s->w6flip, s->stream));
     return PLBM_OK;
@@ -123,9 +130,14 @@ plbm_status forward(Sur* s, int B, const void* x) {
     SCK(plbm::cnn_conv_thin_fwd(4, 64, 0, 0, B, H, W, x, s->pr + s->woff[0], s->p + s->boff[0], nullptr, s->act[0],
                                 0, 1, s->stream));
     for (int l = 1; l <= 4; ++l) {
-        const char* wb = static_cast<const char*>(s->wbf) + (size_t)(l - 1) * 9 * 64 * 64 * 2;
-        SCK(plbm::cnn_conv64_fwd(B, H, W, s->act[l - 1], wb, s->p + s->boff[l], nullptr, s->act[l], 0, 1,
-                                 s->stream));
+        if (s->use_tc) {
+            SCK(plbm::cnn_conv64_tc(B, H, W, s->act[l - 1], wtc_fwd(s, l), s->p + s->boff[l], nullptr, s->act[l], 0, 1,
+                                    s->derr, s->stream));
+        } else {
+            const char* wb = static_cast<const char*>(s->wbf) + (size_t)(l - 1) * 9 * 64 * 64 * 2;
+            SCK(plbm::cnn_conv64_fwd(B, H, W, s->act[l - 1], wb, s->p + s->boff[l], nullptr, s->act[l], 0, 1,
+                                     s->stream));
+        }
     }
     SCK(plbm::cnn_conv_thin_fwd(64, 4, 0, 1, B, H, W, s->act[4], s->pr + s->woff[5], s->p + s->boff[5], nullptr,
                                 s->act[5], 0, 0, s->stream));
@@ -144,8 +156,13 @@ plbm_status backward(Sur* s, int B, const void* x, const float* dout) {
     for (int l = 4; l >= 1; --l) {
         SCK(plbm::cnn_conv64_wgrad(B, H, W, s->act[l - 1], s->dz[l], s->part, s->part_b, s->g + s->woff[l],
                                    s->g + s->boff[l], s->stream));
-        const char* wf = static_cast<const char*>(s->wflip) + (size_t)(l - 1) * 9 * 64 * 64 * 2;
-        SCK(plbm::cnn_conv64_fwd(B, H, W, s->dz[l], wf, nullptr, s->act[l - 1], s->dz[l - 1], 1, 0, s->stream));
+        if (s->use_tc) {
+            SCK(plbm::cnn_conv64_tc(B, H, W, s->dz[l], wtc_bwd(s, l), nullptr, s->act[l - 1], s->dz[l - 1], 1, 0,
+                                    s->derr, s->stream));
+        } else {
+            const char* wf = static_cast<const char*>(s->wflip) + (size_t)(l - 1) * 9 * 64 * 64 * 2;
+            SCK(plbm::cnn_conv64_fwd(B, H, W, s->dz[l], wf, nullptr, s->act[l - 1], s->dz[l - 1], 1, 0, s->stream));
+        }
     }
     SCK(plbm::cnn_conv_thin_wgrad(4, 64, 0, 0, B, H, W, x, s->dz[0], s->part, s->part_b, s->g + s->woff[0],
                                   s->g + s->boff[0], s->stream));
@@ -211,6 +228,7 @@ plbm_status plbm_sur_create(int max_batch, int H, int W, unsigned long long seed
         {(void**)&s->part, part_n * 4}, {(void**)&s->part_b, partb_n * 4}, {(void**)&s->loss_part, 1024 * 4},
         {(void**)&s->Fold, pix * 4 * 4}, {(void**)&s->Fnew, pix * 4 * 4}, {&s->xin, pix * 4 * 2},
         {(void**)&s->planes, (size_t)H * W * 4 * 8}, {(void**)&s->sums, (size_t)max_batch * 2 * 64 * 4 * 8},
+        {&s->wtc, 8 * 9 * 64 * 64 * 2}, {(void**)&s->derr, 256},
     };
     for (auto& a : allocs) {
         if (cudaMalloc(a.p, a.n) != cudaSuccess) {
@@ -232,6 +250,11 @@ plbm_status plbm_sur_create(int max_batch, int H, int W, unsigned long long seed
         serr(s, "allocation failed");
         free_sur(s);
         return PLBM_E_NOMEM;
+    }
+    if (cudaMemsetAsync(s->derr, 0, 256, s->stream) != cudaSuccess) {
+        serr(s, "cudaMemset failed");
+        free_sur(s);
+        return PLBM_E_CUDA;
     }
     // He initialisation (normal, std sqrt(2 / fan_in)); the last layer scaled by 0.1 so
     // that an untrained network predicts almost no change.  Biases zero.
@@ -275,6 +298,30 @@ plbm_status plbm_sur_get_params(plbm_surrogate h, float* params, float* grads) {
     if (params) SCK(cudaMemcpyAsync(params, s->p, s->nparams * 4, cudaMemcpyDeviceToHost, s->stream));
     if (grads) SCK(cudaMemcpyAsync(grads, s->g, s->nparams * 4, cudaMemcpyDeviceToHost, s->stream));
     SCK(cudaStreamSynchronize(s->stream));
+    return PLBM_OK;
+}
+
+plbm_status plbm_sur_set_option(plbm_surrogate h, int option, int value) {
+    Sur* s = as_sur(h);
+    if (!s) return PLBM_E_ARG;
+    if (option == PLBM_SUR_OPT_TENSOR_PATH && (value == 0 || value == 1)) {
+        s->use_tc = value;
+        return PLBM_OK;
+    }
+    serr(s, "unknown option %d or value %d", option, value);
+    return PLBM_E_ARG;
+}
+
+plbm_status plbm_sur_check(plbm_surrogate h) {
+    Sur* s = as_sur(h);
+    if (!s) return PLBM_E_ARG;
+    unsigned e = 0;
+    SCK(cudaMemcpyAsync(&e, s->derr, sizeof e, cudaMemcpyDeviceToHost, s->stream));
+    SCK(cudaStreamSynchronize(s->stream));
+    if (e) {
+        serr(s, "a tensor-core kernel gave up waiting for its MMAs");
+        return PLBM_E_TIMEOUT;
+    }
     return PLBM_OK;
 }
 

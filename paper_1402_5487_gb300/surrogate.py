@@ -133,6 +133,13 @@ class Surrogate:
         except Exception:
             pass
 
+    def set_tensor_path(self, tcgen05: bool):
+        """tcgen05.mma (True, default) or mma.sync (False) for the 64 -> 64 convolutions."""
+        self._ok(plbm.lib().plbm_sur_set_option(self.h, 1, 1 if tcgen05 else 0))
+
+    def check(self):
+        return int(plbm.lib().plbm_sur_check(self.h))
+
     def set_norm(self, mean_in, std_in, mean_d, std_d):
         self.norm = tuple(np.asarray(a, dtype=np.float64) for a in (mean_in, std_in, mean_d, std_d))
         arrs = [(ctypes.c_float * 4)(*[float(v) for v in a]) for a in self.norm]

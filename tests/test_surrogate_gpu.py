@@ -55,10 +55,11 @@ def rel(a, b):
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-30))
 
 
-@pytest.fixture(scope="module")
-def net_and_pass():
+@pytest.fixture(scope="module", params=["tcgen05", "mma_sync"])
+def net_and_pass(request):
     import torch
     net = SG.Surrogate(2, H=5, W=128, seed=7)
+    net.set_tensor_path(request.param == "tcgen05")
     g = torch.Generator().manual_seed(3)
     x = torch.randn((2, 5, 128, 4), generator=g).to(torch.bfloat16).cuda()
     dout = (0.01 * torch.randn((2, 5, 128, 4), generator=g)).cuda()
@@ -70,6 +71,7 @@ def net_and_pass():
     grads = net.backward(x, dout, 2)
     dZ = [net.tensor(1, l, 2).float().cpu().numpy().astype(np.float64) for l in range(1, 6)]
     p, _ = net.params()
+    assert net.check() == plbm.PLBM_OK
     yield net, A, dZ, dout.cpu().numpy().astype(np.float64), split(p), split(grads)
     net.close()
 
