@@ -1,21 +1,38 @@
-// 64 -> 64 circular 3x3 convolution on the 5th-generation tensor cores
-// (tcgen05.mma, accumulators in tensor memory), sm_103a.
+// Circular 3x3 convolutions of the surrogate on the 5th-generation tensor
+// cores (tcgen05.mma, accumulators in tensor memory), sm_103a.
 //
-// Implicit GEMM per tile of 128 output pixels of one row: D[128 x 64] =
-// sum over 9 taps and 4 K-steps of A_tap[128 x 16] B_tap[16 x 64], with
-// A_tap the input pixels shifted by the tap (K-major: 64 channels = one
-// 128-byte row per pixel) and B_tap the tap's weights (K-major: one 128-byte
-// row per output channel).  Every operand tile starts on a 1024-byte boundary
-// and is stored with the 128-byte swizzle (16-byte chunk index XOR row % 8), the
-// layout the shared-memory matrix descriptors name; the three horizontal taps
-// of a row get their own shifted copy of the input so that no tile starts
-// inside a swizzle period.
+// Implicit GEMM per tile of 128 output pixels of one row segment:
+// D[128 x N] = sum over 9 taps (ky, kx) and 4 K-steps of A[128 x 16] B[16 x N],
+// A = input pixels shifted by the tap, B = the tap's weights.
 //
-// One elected thread issues the 36 MMAs of a tile and commits them to an
-// mbarrier; all 256 threads then read the 128 x 64 FP32 accumulator from
-// tensor memory (warp w: lanes 32 (w % 4).., columns 32 (w / 4)..) and run the
-// epilogue.  Waits are bounded: on a timeout the kernel records it in *err,
-// stops issuing work, frees its tensor memory and returns.
+// k_conv_ring<N, MODE> (64 input channels: the 64 -> 64 layers and the 64 -> 4
+// output layer with N = 16, four columns used) is warp-specialised and
+// pipelined:
+//   * warps 0..2 stream input row segments (pixels x0 - 1 .. x0 + 128,
+//     wrapped) into a ring of shared-memory slots with cp.async, each warp one
+//     row in flight.  A CTA owns a run of consecutive output rows of one column
+//     of tiles, so each input row is loaded once and serves the three taps ky
+//     of three output rows;
+//   * one thread each of warps 3 and 4 issues the 36 MMAs of alternate tiles
+//     into eight TMEM accumulators (a single issuing thread that waits on
+//     barriers between tiles leaves the tensor pipe idle; two keep it fed) and
+//     commits them to mbarriers that hand the accumulator to the epilogue and
+//     the rows no later tile needs back to the loaders;
+//   * warps 5..8 read the accumulator (warp w owns TMEM lanes 32 (w % 4)..),
+//     hand it back, and run the epilogue while later tiles' MMAs run.
+// The row slots use the no-swizzle K-major layout with one plane per 16-byte
+// channel chunk (pixel p, chunk c at c * plane + 16 p): 8-row core matrices are
+// contiguous 128-byte blocks, so the tap shift kx is a 16 * kx byte offset of
+// the descriptor start.  The weights use the 128-byte swizzle (1024-byte
+// aligned 8-row atoms).
+//
+// k_conv_in_tc is the 4 -> 64 input layer: the 36 products of a pixel (9 taps
+// x 4 channels) are gathered into one K = 48 row (zero padded) and three MMAs
+// make the tile.
+//
+// Every wait is bounded by the global timer: on a timeout a kernel records it
+// in *err, stops issuing work, waits (bounded) for the MMAs it issued, frees
+// its tensor memory and returns.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -28,192 +45,597 @@ namespace tc {
 
 constexpr int kC = 64;
 constexpr int kTile = 128;
-constexpr int kThreads = 256;
-constexpr int kATile = kTile * 128;       // 16 KB per tap
-constexpr int kBTile = kC * 128;          // 8 KB per tap
-constexpr int kSmemA = 9 * kATile;        // 147456
-constexpr int kSmemB = 9 * kBTile;        // 73728
-constexpr int kSmem = kSmemA + kSmemB + 1024 + 64;  // + alignment slack + barrier/tmem slot
-constexpr unsigned kTmemCols = 64;
-constexpr long long kSpinLimit = 1LL << 26;
+constexpr unsigned long long kTimeoutNs = 2000000000ull;  // 2 s per wait
 
 __device__ __forceinline__ uint32_t s2u(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 __device__ __forceinline__ int swz(int row, int c) { return (row * 8 + (c ^ (row & 7))) * 16; }
+__device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
+__device__ __forceinline__ uint64_t gtime() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
 __device__ __forceinline__ void cp_async16(uint32_t smem, const void* gmem) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem), "l"(gmem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+
+__device__ __forceinline__ void bar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(uint32_t bar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}\n" ::"r"(bar) : "memory");
+}
+// One potentially blocking test of the phase: the thread may be suspended (up
+// to the hint, 10 ms) until the phase completes, so waiting warps do not take
+// issue slots from the warps that work.
+__device__ __forceinline__ bool bar_try(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity), "r"(10000000u)
+        : "memory");
+    return done != 0;
+}
+// Wait for the phase of parity `parity` of `bar`; false on a timeout (which sets
+// *abort) or when another role has already set *abort.
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+    if (bar_try(bar, parity)) return true;
+    const uint64_t t0 = gtime();
+    for (;;) {
+        if (bar_try(bar, parity)) return true;
+        if (*abort) return false;
+        if (gtime() - t0 > kTimeoutNs) {
+            *abort = 1;
+            return false;
+        }
+    }
+}
+// Non-blocking test of the phase, for the MMA issuer: it must not be suspended
+// while the tensor pipe could take more work.  Its shared-memory reads queue
+// behind the tensor cores' operand reads, so the issuer tests several phases
+// at once (test_many) instead of one per tile.
+__device__ __forceinline__ bool bar_test(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+__device__ __forceinline__ bool bar_spin(uint32_t bar, uint32_t parity, volatile int* abort) {
+    if (bar_test(bar, parity)) return true;
+    const uint64_t t0 = gtime();
+    for (uint32_t i = 1;; ++i) {
+        if (bar_test(bar, parity)) return true;
+        if ((i & 255) == 0) {
+            if (*abort) return false;
+            if (gtime() - t0 > kTimeoutNs) {
+                *abort = 1;
+                return false;
+            }
+        }
+    }
+}
+// Tests of up to 4 barrier phases issued together; returns how many of them, in
+// order, have completed.  Each queried phase must be at most one ahead of a
+// phase known to be complete on the same barrier (a parity test cannot tell a
+// phase from the one two before it).
+__device__ __forceinline__ int test_many(const uint32_t (&bars)[4], const uint32_t (&par)[4], int n) {
+    uint32_t d[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) d[k] = k < n ? (bar_test(bars[k], par[k]) ? 1u : 0u) : 0u;
+    int c = 0;
+    while (c < n && d[c]) ++c;
+    return c;
+}
+// The same without looking at *abort (used to drain issued MMAs before freeing TMEM).
+__device__ __forceinline__ bool bar_wait_drain(uint32_t bar, uint32_t parity) {
+    const uint64_t t0 = gtime();
+    for (;;) {
+        if (bar_try(bar, parity)) return true;
+        if (gtime() - t0 > kTimeoutNs) return false;
+    }
 }
 
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((addr & 0x3FFFF) >> 4);          // start address
-    d |= (uint64_t)1 << 16;                          // leading byte offset (unused with swizzle)
-    d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset
-    d |= (uint64_t)1 << 46;                          // descriptor version
-    d |= (uint64_t)2 << 61;                          // 128-byte swizzle
-    return d;
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t slot_addr, uint32_t cols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(slot_addr), "r"(cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void tmem_free(uint32_t tmem, uint32_t cols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(cols) : "memory");
 }
 
-// Instruction descriptor of kind::f16: D fp32, A and B bf16, both K-major, N = 64, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kC >> 3) << 17) |
-                            ((uint32_t)(kTile >> 4) << 24);
+// Shared-memory matrix descriptors (K-major).
+// 128-byte swizzle: 8-row atoms of 1024 bytes (stride byte offset 1024).
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t addr) {
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// No swizzle: 8 rows x 16 bytes core matrices; `kstride` bytes between the two
+// core matrices of a K = 16 step (leading byte offset), 128 bytes between
+// 8-row groups (stride byte offset).
+__device__ __forceinline__ uint64_t desc_plain(uint32_t addr, uint32_t kstride) {
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(kstride >> 4) << 16) | ((uint64_t)(128 >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
 
-__device__ __forceinline__ void mma_issue(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+// Instruction descriptor of kind::f16: D fp32, A and B bf16, both K-major, M = 128.
+template <int N>
+struct Idesc {
+    static constexpr uint32_t value = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+                                      ((uint32_t)(kTile >> 4) << 24);
+};
+
+template <int N>
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.u32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate));
+        "l"(a), "l"(b), "r"(Idesc<N>::value), "r"(accumulate)
+        : "memory");
 }
 
-__device__ __forceinline__ bool wait_parity(uint32_t bar, uint32_t parity) {
-    for (long long i = 0; i < kSpinLimit; ++i) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(done)
-            : "r"(bar), "r"(parity));
-        if (done) return true;
+#define PLBM_TMEM_LD32(v, base, addr)                                                                               \
+    asm volatile(                                                                                                   \
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"            \
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"                                \
+        : "=r"(v[base + 0]), "=r"(v[base + 1]), "=r"(v[base + 2]), "=r"(v[base + 3]), "=r"(v[base + 4]),           \
+          "=r"(v[base + 5]), "=r"(v[base + 6]), "=r"(v[base + 7]), "=r"(v[base + 8]), "=r"(v[base + 9]),           \
+          "=r"(v[base + 10]), "=r"(v[base + 11]), "=r"(v[base + 12]), "=r"(v[base + 13]), "=r"(v[base + 14]),      \
+          "=r"(v[base + 15]), "=r"(v[base + 16]), "=r"(v[base + 17]), "=r"(v[base + 18]), "=r"(v[base + 19]),      \
+          "=r"(v[base + 20]), "=r"(v[base + 21]), "=r"(v[base + 22]), "=r"(v[base + 23]), "=r"(v[base + 24]),      \
+          "=r"(v[base + 25]), "=r"(v[base + 26]), "=r"(v[base + 27]), "=r"(v[base + 28]), "=r"(v[base + 29]),      \
+          "=r"(v[base + 30]), "=r"(v[base + 31])                                                                    \
+        : "r"(addr)                                                                                                 \
+        : "memory")
+
+// 64 accumulator columns of this thread's TMEM lane -> bias/ReLU or mask -> 64 bf16 at dst.
+__device__ __forceinline__ void store64(const uint32_t (&v)[64], int mode, int relu, const float* __restrict__ bias,
+                                        const __nv_bfloat16* __restrict__ mask, __nv_bfloat16* __restrict__ dst) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {  // 8 channels per 16-byte store
+        float f[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) f[k] = __uint_as_float(v[8 * q + k]);
+        if (mode == 0) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                f[k] += bias[8 * q + k];
+                if (relu) f[k] = fmaxf(f[k], 0.0f);
+            }
+        } else {
+            const uint4 mk = *reinterpret_cast<const uint4*>(mask + 8 * q);
+            const __nv_bfloat16* m = reinterpret_cast<const __nv_bfloat16*>(&mk);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) f[k] = __bfloat162float(m[k]) > 0.0f ? f[k] : 0.0f;
+        }
+        uint4 o;
+        __nv_bfloat162* ob = reinterpret_cast<__nv_bfloat162*>(&o);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) ob[k] = __floats2bfloat162_rn(f[2 * k], f[2 * k + 1]);
+        *reinterpret_cast<uint4*>(dst + 8 * q) = o;
     }
-    return false;
 }
 
-// mode 0: Y = relu?(conv(X) + bias); mode 1: Y = conv(X) * (mask > 0).  Wk: K-major
-// weights [tap][n][k] bf16 (n = output channel, k = input channel).
-__global__ void __launch_bounds__(kThreads, 1)
-k_conv64_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ Wk,
-            const float* __restrict__ bias, const __nv_bfloat16* __restrict__ mask, __nv_bfloat16* __restrict__ Y,
-            int mode, int relu, unsigned* __restrict__ err) {
+// ---------------------------------------------------------------------------
+// Ring-staged convolution with 64 input channels.
+// MODE 0: Y bf16 [.][64] = relu?(conv + bias)    (N = 64)
+// MODE 1: Y bf16 [.][64] = conv * (mask > 0)     (N = 64, backward data)
+// MODE 2: Y fp32 [.][4]  = conv + bias           (N = 16, output columns 0..3)
+// Wk: bf16 [9 taps][N][64], K-major.
+// ---------------------------------------------------------------------------
+constexpr int kLoaders = 3;            // warps 0..2 load input rows
+constexpr int kIssuers = 2;            // warps 3, 4 issue the MMAs of alternate tiles
+constexpr int kRingThreads = 32 * (kLoaders + kIssuers + 4);  // warps 5..8 run the epilogue
+constexpr int kSegPix = kTile + 2;     // staged pixels per input row: x0 - 1 .. x0 + 128
+// One 16-byte channel chunk of every staged pixel, padded so that planes start
+// 64 bytes apart modulo 128: the loaders' 16-pixel x 2-chunk warp stores are
+// then free of bank conflicts.
+constexpr int kPlane = kSegPix * 16 + 32;  // 2112 bytes
+constexpr int kSeg = 8 * kPlane;       // 16896 bytes per staged row
+constexpr int kRing = 8;               // row slots
+static_assert(kRing >= 3 + kLoaders, "three rows feed the MMAs while every loader has one in flight");
+constexpr int kRingBytes = kRing * kSeg;
+constexpr int kRingWOff = ((kRingBytes + 1023) / 1024) * 1024;  // weights after the ring, 1024-aligned
+constexpr int kRingBarBytes = 512 + 256;  // barriers, TMEM slot, abort flag, then 64 fp32 biases
+template <int N>
+constexpr int ring_smem() { return 1024 + kRingWOff + 9 * N * 128 + kRingBarBytes; }
+constexpr int kAcc = 8;                  // TMEM accumulators (all 512 columns); issuer q uses acc = q mod 2
+constexpr uint32_t kRingTmemCols = 64 * kAcc;
+
+// barrier slots (8 bytes each) after the weights; row slot s has one release
+// barrier per issuer (kBarEmpty + q * kRing + s)
+constexpr int kBarFull = 0, kBarEmpty = kRing, kBarTFull = (1 + kIssuers) * kRing, kBarTEmpty = kBarTFull + kAcc,
+              kBarDrain = kBarTEmpty + kAcc, kBarCount = kBarDrain + kIssuers;
+static_assert(kBarCount * 8 + 16 <= 512, "barrier area below the biases");
+
+// Tiles t = ((b * tiles_x + xt) * H + y); a CTA takes a contiguous range, which
+// splits into strips of consecutive rows y of one column (b, xt).
+struct Strip {
+    int b, x0, y0, n;
+};
+__device__ __forceinline__ Strip strip_at(int t, int t1, int H, int tiles_x) {
+    const int col = t / H, y0 = t - col * H;
+    Strip s;
+    s.b = col / tiles_x;
+    s.x0 = (col - s.b * tiles_x) * kTile;
+    s.y0 = y0;
+    s.n = min(t1 - t, H - y0);
+    return s;
+}
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(kRingThreads, 1)
+k_conv_ring(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ Wk,
+            const float* __restrict__ bias, const __nv_bfloat16* __restrict__ mask, void* __restrict__ Yv, int relu,
+            unsigned* __restrict__ err) {
+    static_assert((N == 64 && MODE < 2) || (N == 16 && MODE == 2), "ring conv shapes");
     extern __shared__ unsigned char dsm_raw[];
-    // 1024-byte aligned operand area
     const uint32_t raw = s2u(dsm_raw);
     const uint32_t pad = (1024 - (raw & 1023)) & 1023;
     unsigned char* base = dsm_raw + pad;
-    const uint32_t sA = raw + pad;
-    const uint32_t sB = sA + kSmemA;
-    unsigned char* slot = base + kSmemA + kSmemB;
-    const uint32_t bar = s2u(slot);
-    volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(slot + 16);
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(slot + 32);
+    const uint32_t sRing = raw + pad;
+    const uint32_t sW = sRing + kRingWOff;
+    unsigned char* bars_p = base + kRingWOff + 9 * N * 128;
+    const uint32_t bars = s2u(bars_p);
+    volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(bars_p + kBarCount * 8);
+    volatile int* abortp = reinterpret_cast<volatile int*>(bars_p + kBarCount * 8 + 8);
+    float* sbias = reinterpret_cast<float*>(bars_p + 512);
+    auto bar = [&](int i) { return bars + 8u * (uint32_t)i; };
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tiles_x = W / kTile;
     const int ntiles = B * H * tiles_x;
+    const int per = (ntiles + gridDim.x - 1) / gridDim.x;
+    const int t_begin = min(ntiles, (int)blockIdx.x * per);
+    const int t_end = min(ntiles, t_begin + per);
 
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar));
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
-        *abort_flag = 0;
+        for (int i = 0; i < kRing; ++i) bar_init(bar(kBarFull + i), 32);
+        for (int i = 0; i < kIssuers * kRing; ++i) bar_init(bar(kBarEmpty + i), 1);
+        for (int i = 0; i < kAcc; ++i) {
+            bar_init(bar(kBarTFull + i), 1);
+            bar_init(bar(kBarTEmpty + i), 128);
+        }
+        for (int i = 0; i < kIssuers; ++i) bar_init(bar(kBarDrain + i), 1);
+        *abortp = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(s2u(slot + 16)),
-                     "r"(kTmemCols));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+    if (warp == kLoaders) tmem_alloc(s2u(bars_p + kBarCount * 8), kRingTmemCols);
+    for (int i = tid; i < 9 * N * 8; i += kRingThreads) {  // weights: 9 N rows of 8 chunks, swizzled
+        const int c = i & 7, row = i >> 3;
+        cp_async16(sW + swz(row, c), Wk + (size_t)row * kC + c * 8);
     }
-    // weights: 9 taps x 64 rows x 8 chunks
-    for (int i = tid; i < 9 * kC * 8; i += kThreads) {
-        const int c = i & 7, row = i >> 3;  // row = tap * 64 + n
-        cp_async16(sB + swz(row, c), Wk + (size_t)row * kC + c * 8);
-    }
-    asm volatile("cp.async.wait_all;\n" ::);
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+    if (MODE != 1 && tid < (MODE == 2 ? 4 : 64)) sbias[tid] = bias[tid];
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    fence_async_smem();
+    tc_before_sync();
     __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+    tc_after_sync();
     const uint32_t tmem = *tmem_slot;
 
+    if (warp < kLoaders) {
+        // ---- loaders: rows y0 - 1 .. y0 + n of every strip; loader warp w takes
+        // the rows e = w mod kLoaders, one in flight, and publishes each (full
+        // barrier) as soon as its copies have landed ----
+        uint32_t e = 0;
+        bool ok = true;
+        for (int t = t_begin; t < t_end && ok;) {
+            const Strip s = strip_at(t, t_end, H, tiles_x);
+            for (int j = 0; j < s.n + 2; ++j, ++e) {
+                if ((int)(e % kLoaders) != warp) continue;
+                const int slot = (int)(e % kRing);
+                const uint32_t par = ((e / kRing) & 1) ^ 1;
+                if (!bar_wait(bar(kBarEmpty + slot), par, abortp) ||
+                    !bar_wait(bar(kBarEmpty + kRing + slot), par, abortp)) {
+                    ok = false;
+                    break;
+                }
+                const int yy = wrapi(s.y0 - 1 + j, H);
+                const __nv_bfloat16* row = X + ((size_t)s.b * H + yy) * (size_t)W * kC;
+                const uint32_t seg = sRing + (uint32_t)slot * kSeg;
+                // lane pairs move one 32-byte sector (two chunks) of one pixel;
+                // a warp covers 16 consecutive pixels
+                for (int i = lane; i < kSegPix * 8; i += 32) {
+                    const int u = i >> 1, p = u % kSegPix, c = 2 * (u / kSegPix) + (i & 1);
+                    const int xx = wrapi(s.x0 - 1 + p, W);
+                    cp_async16(seg + c * kPlane + p * 16, row + (size_t)xx * kC + c * 8);
+                }
+                asm volatile("cp.async.wait_all;\n" ::: "memory");
+                fence_async_smem();
+                bar_arrive(bar(kBarFull + slot));
+            }
+            t += s.n;
+        }
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+    } else if (warp < kLoaders + kIssuers) {
+        if (lane == 0) {
+            // ---- MMA issuers: issuer q computes the tiles with local index = q
+            // mod 2.  Both walk every tile: after tile i of a strip each releases
+            // (on its own barrier of the row slot) the rows that no later tile
+            // uses, so a release arrives once all of its earlier MMAs, including
+            // every use of that row, have completed ----
+            const int q = warp - kLoaders;
+            const uint64_t a0 = desc_plain(sRing, kPlane);
+            const uint64_t b0 = desc_sw128(sW);
+            const uint32_t empty0 = kBarEmpty + q * kRing;
+            // entries below `ready` have been seen full; tiles below `freed` (of
+            // this issuer's accumulators) have been released by the epilogue
+            uint32_t e0 = 0, tcount = 0, ready = 0, freed = (uint32_t)q, nent = 0;
+            for (int t = t_begin; t < t_end;) {
+                const Strip s = strip_at(t, t_end, H, tiles_x);
+                nent += s.n + 2;
+                t += s.n;
+            }
+            const uint32_t ntile = (uint32_t)(t_end - t_begin);
+            bool ok = true, issued = false;
+            for (int t = t_begin; t < t_end && ok;) {
+                const Strip s = strip_at(t, t_end, H, tiles_x);
+                for (int i = 0; i < s.n; ++i, ++tcount) {
+                    if ((int)(tcount & 1) == q) {
+                        const uint32_t need = e0 + i + 2;
+                        while (ok && ready <= need) {
+                            uint32_t b[4], par[4];
+                            const int n = (int)min(4u, nent - ready);
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                b[k] = bar(kBarFull + (ready + k) % kRing);
+                                par[k] = ((ready + k) / kRing) & 1;
+                            }
+                            const int c = test_many(b, par, n);
+                            if (c) ready += c;
+                            else ok = bar_spin(b[0], par[0], abortp) && (++ready, true);
+                        }
+                        if (tcount >= (uint32_t)kAcc) {
+                            // this issuer's tiles are tcount = q, q + 2, ...; tile u frees
+                            // accumulator u mod kAcc for tile u + kAcc
+                            const uint32_t want = tcount - kAcc;
+                            while (ok && freed <= want) {
+                                uint32_t b[4], par[4];
+                                uint32_t u = freed;
+                                int n = 0;
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) {
+                                    const uint32_t uk = u + 2 * k;
+                                    b[k] = bar(kBarTEmpty + uk % kAcc);
+                                    par[k] = (uk / kAcc) & 1;
+                                    if (uk + kAcc < ntile) ++n;
+                                }
+                                const int c = test_many(b, par, n);
+                                if (c) freed += 2 * c;
+                                else ok = bar_spin(b[0], par[0], abortp) && (freed += 2, true);
+                            }
+                        }
+                        if (!ok) break;
+                        const uint32_t slot[3] = {(e0 + i) % kRing, (e0 + i + 1) % kRing, (e0 + i + 2) % kRing};
+                        const uint32_t acc = tcount % kAcc;
+                        tc_after_sync();
+                        const uint32_t d = tmem + acc * 64;
+#pragma unroll
+                        for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+                            for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+                                for (int ks = 0; ks < 4; ++ks) {
+                                    const uint32_t aoff = slot[ky] * kSeg + kx * 16 + ks * 2 * kPlane;
+                                    const uint32_t boff = (ky * 3 + kx) * N * 128 + ks * 32;
+                                    mma<N>(d, a0 + (aoff >> 4), b0 + (boff >> 4), (ky | kx | ks) != 0);
+                                }
+                        tc_commit(bar(kBarTFull + acc));
+                        issued = true;
+                    }
+                    // rows no later tile of the strip uses
+                    tc_commit(bar(empty0 + (e0 + i) % kRing));
+                    if (i == s.n - 1) {
+                        tc_commit(bar(empty0 + (e0 + s.n) % kRing));
+                        tc_commit(bar(empty0 + (e0 + s.n + 1) % kRing));
+                    }
+                }
+                if (!ok) break;
+                e0 += s.n + 2;
+                t += s.n;
+            }
+            // every MMA issued has completed before the accumulators are released
+            if (issued) {
+                tc_commit(bar(kBarDrain + q));
+                if (!bar_wait_drain(bar(kBarDrain + q), 0)) *abortp = 1;
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue: warps 5..8, TMEM lanes 32 (warp % 4) .. + 31 ----
+        const int quad = warp & 3;
+        const int px = 32 * quad + lane;
+        uint32_t tcount = 0;
+        bool ok = true;
+        for (int t = t_begin; t < t_end && ok;) {
+            const Strip s = strip_at(t, t_end, H, tiles_x);
+            for (int i = 0; i < s.n; ++i) {
+                const uint32_t acc = tcount % kAcc;
+                if (!bar_wait(bar(kBarTFull + acc), (tcount / kAcc) & 1, abortp)) {
+                    ok = false;
+                    break;
+                }
+                tc_after_sync();
+                const uint32_t taddr = tmem + ((uint32_t)(32 * quad) << 16) + acc * 64;
+                const size_t pix = ((size_t)s.b * H + s.y0 + i) * W + s.x0 + px;
+                if (MODE == 2) {
+                    uint32_t v[4];
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n"
+                                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+                                 : "r"(taddr)
+                                 : "memory");
+                    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                    tc_before_sync();
+                    bar_arrive(bar(kBarTEmpty + acc));
+                    float4 o;
+                    o.x = __uint_as_float(v[0]) + sbias[0];
+                    o.y = __uint_as_float(v[1]) + sbias[1];
+                    o.z = __uint_as_float(v[2]) + sbias[2];
+                    o.w = __uint_as_float(v[3]) + sbias[3];
+                    reinterpret_cast<float4*>(Yv)[pix] = o;
+                } else {
+                    uint32_t v[64];
+                    PLBM_TMEM_LD32(v, 0, taddr);
+                    PLBM_TMEM_LD32(v, 32, taddr + 32);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                    tc_before_sync();
+                    bar_arrive(bar(kBarTEmpty + acc));
+                    store64(v, MODE, relu, sbias, MODE == 1 ? mask + pix * kC : nullptr,
+                            static_cast<__nv_bfloat16*>(Yv) + pix * kC);
+                }
+                ++tcount;
+            }
+            t += s.n;
+        }
+    }
+    __syncthreads();
+    if (tid == 0 && *abortp) atomicOr(err, 1u);
+    if (warp == kLoaders) {
+        tc_after_sync();
+        tmem_free(tmem, kRingTmemCols);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 4 -> 64 input layer: Y bf16 [.][64] = relu?(conv(X) + bias), X bf16 [.][4].
+// A row of a pixel: K = tap * 4 + ci for the 36 products, zero to K = 48, in the
+// no-swizzle chunk-planar layout (6 planes of 128 pixels x 16 bytes).
+// Win: bf16 [6 chunks][64 n][8], the same layout for B (plane = 64 x 16 bytes).
+// One tile at a time per CTA; several CTAs per SM overlap.
+// ---------------------------------------------------------------------------
+constexpr int kInThreads = 128;
+constexpr int kInPlanes = 6;
+constexpr int kInA = kInPlanes * kTile * 16;  // 12288
+constexpr int kInB = kInPlanes * kC * 16;     // 6144
+constexpr int kInBar = 64 + 256;  // barriers, TMEM slot, abort flag, 64 fp32 biases
+constexpr int kInSmem = 26 * 1024;  // A, B, barriers and padding that caps residency at 8 CTAs per SM
+static_assert(128 + kInA + kInB + kInBar <= kInSmem, "input-layer shared memory");
+constexpr uint32_t kInTmemCols = 64;
+
+__global__ void __launch_bounds__(kInThreads)
+k_conv_in_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ Win,
+             const float* __restrict__ bias, __nv_bfloat16* __restrict__ Y, int relu, unsigned* __restrict__ err) {
+    extern __shared__ unsigned char dsm_raw[];
+    const uint32_t raw = s2u(dsm_raw);
+    const uint32_t pad = (128 - (raw & 127)) & 127;
+    unsigned char* base = dsm_raw + pad;
+    const uint32_t sA = raw + pad;
+    const uint32_t sB = sA + kInA;
+    unsigned char* bars_p = base + kInA + kInB;
+    const uint32_t bar_mma = s2u(bars_p), bar_drain = bar_mma + 8;
+    volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(bars_p + 16);
+    volatile int* abortp = reinterpret_cast<volatile int*>(bars_p + 24);
+    float* sbias = reinterpret_cast<float*>(bars_p + 64);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tiles_x = W / kTile;
+    const int ntiles = B * H * tiles_x;
+    if (tid < 64) sbias[tid] = bias[tid];
+    if (tid == 0) {
+        bar_init(bar_mma, 1);
+        bar_init(bar_drain, 1);
+        *abortp = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(s2u(bars_p + 16), kInTmemCols);
+    for (int i = tid; i < kInB / 16; i += kInThreads)
+        *reinterpret_cast<uint4*>(base + kInA + 16 * i) = reinterpret_cast<const uint4*>(Win)[i];
+    fence_async_smem();
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    const uint64_t adesc = desc_plain(sA, kTile * 16);
+    const uint64_t bdesc = desc_plain(sB, kC * 16);
+
+    // the gathered inputs of the next tile are loaded while the current tile's MMAs run
+    auto gather = [&](int t, uint2 (&g)[9]) {
+        const int b = t / (H * tiles_x);
+        const int rem = t - b * H * tiles_x;
+        const int y = rem / tiles_x;
+        const int x = (rem - y * tiles_x) * kTile + tid;
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+            const int yy = wrapi(y + tap / 3 - 1, H), xx = wrapi(x + tap % 3 - 1, W);
+            g[tap] = *reinterpret_cast<const uint2*>(X + (((size_t)b * H + yy) * W + xx) * 4);
+        }
+    };
+    *reinterpret_cast<uint4*>(base + 5 * kTile * 16 + tid * 16) = make_uint4(0u, 0u, 0u, 0u);
+    uint2 g[9];
+    if ((int)blockIdx.x < ntiles) gather(blockIdx.x, g);
     uint32_t phase = 0;
+    bool issued = false;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int b = t / (H * tiles_x);
         const int rem = t - b * H * tiles_x;
         const int y = rem / tiles_x;
-        const int x0 = (rem - y * tiles_x) * kTile;
-        // A tiles: tap (ky, kx) row r holds input pixel (y + ky - 1, x0 + r + kx - 1)
-        for (int i = tid; i < 9 * kTile * 8; i += kThreads) {
-            const int c = i & 7, rr = i >> 3, tap = rr >> 7, r = rr & (kTile - 1);
-            const int ky = tap / 3, kx = tap - 3 * ky;
-            int yy = y + ky - 1;
-            yy += (yy < 0) ? H : 0;
-            yy -= (yy >= H) ? H : 0;
-            int xx = x0 + r + kx - 1;
-            xx += (xx < 0) ? W : 0;
-            xx -= (xx >= W) ? W : 0;
-            cp_async16(sA + tap * kATile + swz(r, c), X + (((size_t)b * H + yy) * W + xx) * kC + c * 8);
-        }
-        asm volatile("cp.async.wait_all;\n" ::);
-        asm volatile("fence.proxy.async.shared::cta;\n" ::);
+        const int x = (rem - y * tiles_x) * kTile + tid;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            *reinterpret_cast<uint4*>(base + c * kTile * 16 + tid * 16) =
+                make_uint4(g[2 * c].x, g[2 * c].y, g[2 * c + 1].x, g[2 * c + 1].y);
+        *reinterpret_cast<uint4*>(base + 4 * kTile * 16 + tid * 16) = make_uint4(g[8].x, g[8].y, 0u, 0u);
+        fence_async_smem();
         __syncthreads();
         if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-            uint32_t acc = 0;
-            for (int tap = 0; tap < 9; ++tap)
-                for (int k = 0; k < 4; ++k) {
-                    mma_issue(tmem, smem_desc(sA + tap * kATile + k * 32), smem_desc(sB + tap * kBTile + k * 32), acc);
-                    acc = 1;
-                }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar));
+            tc_after_sync();
+#pragma unroll
+            for (int ks = 0; ks < 3; ++ks)
+                mma<64>(tmem, adesc + ((ks * 2 * kTile * 16) >> 4), bdesc + ((ks * 2 * kC * 16) >> 4), ks != 0);
+            tc_commit(bar_mma);
+            issued = true;
         }
-        const bool ok = wait_parity(bar, phase);
+        if (t + (int)gridDim.x < ntiles) gather(t + gridDim.x, g);
+        if (!bar_wait(bar_mma, phase, abortp)) *abortp = 1;
         phase ^= 1;
-        if (!ok) *abort_flag = 1;
         __syncthreads();
-        if (*abort_flag) break;
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-        // accumulator rows 32 (warp % 4) + lane, columns 32 (warp / 4) .. + 31
-        uint32_t v[32];
-        const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(32 * (warp >> 2));
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-              "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-            : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
-        const int px = 32 * (warp & 3) + lane;
-        const int cb = 32 * (warp >> 2);
-        const size_t pix = ((size_t)b * H + y) * W + x0 + px;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {  // 8 channels per 16-byte store
-            float f[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) f[k] = __uint_as_float(v[8 * q + k]);
-            if (mode == 0) {
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    f[k] += bias[cb + 8 * q + k];
-                    if (relu) f[k] = fmaxf(f[k], 0.0f);
-                }
-            } else {
-                const uint4 mk = *reinterpret_cast<const uint4*>(mask + pix * kC + cb + 8 * q);
-                const __nv_bfloat16* m = reinterpret_cast<const __nv_bfloat16*>(&mk);
-#pragma unroll
-                for (int k = 0; k < 8; ++k) f[k] = __bfloat162float(m[k]) > 0.0f ? f[k] : 0.0f;
-            }
-            uint4 o;
-            __nv_bfloat162* ob = reinterpret_cast<__nv_bfloat162*>(&o);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) ob[k] = __floats2bfloat162_rn(f[2 * k], f[2 * k + 1]);
-            *reinterpret_cast<uint4*>(Y + pix * kC + cb + 8 * q) = o;
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+        if (*abortp) break;
+        tc_after_sync();
+        uint32_t v[64];
+        const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
+        PLBM_TMEM_LD32(v, 0, taddr);
+        PLBM_TMEM_LD32(v, 32, taddr + 32);
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        tc_before_sync();
+        store64(v, 0, relu, sbias, nullptr, Y + (((size_t)b * H + y) * W + x) * kC);
         __syncthreads();
     }
-    if (*abort_flag && tid == 0) atomicOr(err, 1u);
+    if (tid == 0 && issued) {  // drain before the accumulator is released
+        tc_commit(bar_drain);
+        if (!bar_wait_drain(bar_drain, 0)) *abortp = 1;
+    }
     __syncthreads();
+    if (tid == 0 && *abortp) atomicOr(err, 1u);
     if (warp == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
+        tc_after_sync();
+        tmem_free(tmem, kInTmemCols);
     }
+    (void)lane;
 }
 
-// K-major weight layouts from W[tap][ci][co] (bf16):
-// forward: Wk[tap][co][ci] = W[tap][ci][co]; backward data: Wk[tap][ci][co] = W[8 - tap][ci][co].
+// ---------------------------------------------------------------------------
+// Weight layouts for the kernels above, from W[tap][ci][co].
+// ---------------------------------------------------------------------------
+// 64 -> 64: forward Wf[tap][co][ci] = W[tap][ci][co]; backward data Wb[tap][ci][co] = W[8 - tap][ci][co].
 __global__ void k_weights_kmajor(const __nv_bfloat16* __restrict__ W, __nv_bfloat16* __restrict__ Wf,
                                  __nv_bfloat16* __restrict__ Wb) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -222,6 +644,23 @@ __global__ void k_weights_kmajor(const __nv_bfloat16* __restrict__ W, __nv_bfloa
     const __nv_bfloat16 w = W[i];
     Wf[(tap * kC + co) * kC + ci] = w;
     Wb[((8 - tap) * kC + ci) * kC + co] = w;
+}
+
+// 64 -> 4 output layer (fp32 W[9][64][4]): Wo[tap][n][ci], n < 16, zero for n >= 4.
+__global__ void k_weights_out16(const float* __restrict__ W, __nv_bfloat16* __restrict__ Wo) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 9 * 16 * kC) return;
+    const int ci = i % kC, n = (i / kC) % 16, tap = i / (16 * kC);
+    Wo[i] = __float2bfloat16_rn(n < 4 ? W[(tap * kC + ci) * 4 + n] : 0.0f);
+}
+
+// 4 -> 64 input layer (fp32 W[9][4][64]): Win[c][n][j] = W[tap][ci][n] for k = 8c + j = 4 tap + ci < 36.
+__global__ void k_weights_in(const float* __restrict__ W, __nv_bfloat16* __restrict__ Win) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kInPlanes * kC * 8) return;
+    const int j = i % 8, n = (i / 8) % kC, c = i / (8 * kC);
+    const int k = 8 * c + j;
+    Win[i] = __float2bfloat16_rn(k < 36 ? W[((k >> 2) * 4 + (k & 3)) * kC + n] : 0.0f);
 }
 
 }  // namespace tc
@@ -237,26 +676,66 @@ static int tc_sms() {
     return n;
 }
 
-cudaError_t cnn_conv64_tc(int B, int H, int W, const void* X, const void* Wk, const float* bias, const void* mask,
-                          void* Y, int mode, int relu, unsigned* err, cudaStream_t s) {
-    if (W % tc::kTile) return cudaErrorInvalidValue;
+template <int N, int MODE>
+static cudaError_t launch_ring(int B, int H, int W, const void* X, const void* Wk, const float* bias,
+                               const void* mask, void* Y, int relu, unsigned* err, cudaStream_t s) {
+    if (W % tc::kTile || H < 1 || B < 1) return cudaErrorInvalidValue;
+    constexpr int smem = tc::ring_smem<N>();
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(tc::k_conv64_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmem);
+        cudaError_t e = cudaFuncSetAttribute(tc::k_conv_ring<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     const int ntiles = B * H * (W / tc::kTile);
     const int grid = ntiles < tc_sms() ? ntiles : tc_sms();
-    tc::k_conv64_tc<<<grid, tc::kThreads, tc::kSmem, s>>>(
+    tc::k_conv_ring<N, MODE><<<grid, tc::kRingThreads, smem, s>>>(
         B, H, W, static_cast<const __nv_bfloat16*>(X), static_cast<const __nv_bfloat16*>(Wk), bias,
-        static_cast<const __nv_bfloat16*>(mask), static_cast<__nv_bfloat16*>(Y), mode, relu, err);
+        static_cast<const __nv_bfloat16*>(mask), Y, relu, err);
+    return cudaGetLastError();
+}
+
+cudaError_t cnn_conv64_tc(int B, int H, int W, const void* X, const void* Wk, const float* bias, const void* mask,
+                          void* Y, int mode, int relu, unsigned* err, cudaStream_t s) {
+    if (mode == 0) return launch_ring<64, 0>(B, H, W, X, Wk, bias, mask, Y, relu, err, s);
+    return launch_ring<64, 1>(B, H, W, X, Wk, bias, mask, Y, relu, err, s);
+}
+
+cudaError_t cnn_conv_out_tc(int B, int H, int W, const void* X, const void* Wo, const float* bias, float* Y,
+                            unsigned* err, cudaStream_t s) {
+    return launch_ring<16, 2>(B, H, W, X, Wo, bias, nullptr, Y, 0, err, s);
+}
+
+cudaError_t cnn_conv_in_tc(int B, int H, int W, const void* X, const void* Win, const float* bias, void* Y, int relu,
+                           unsigned* err, cudaStream_t s) {
+    if (W % tc::kTile || H < 1 || B < 1) return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(tc::k_conv_in_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kInSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int ntiles = B * H * (W / tc::kTile);
+    const int grid = ntiles < 8 * tc_sms() ? ntiles : 8 * tc_sms();
+    tc::k_conv_in_tc<<<grid, tc::kInThreads, tc::kInSmem, s>>>(B, H, W, static_cast<const __nv_bfloat16*>(X),
+                                                               static_cast<const __nv_bfloat16*>(Win), bias,
+                                                               static_cast<__nv_bfloat16*>(Y), relu, err);
     return cudaGetLastError();
 }
 
 cudaError_t cnn_weights_kmajor(const void* W, void* Wf, void* Wb, cudaStream_t s) {
     tc::k_weights_kmajor<<<(9 * 64 * 64 + 255) / 256, 256, 0, s>>>(
         static_cast<const __nv_bfloat16*>(W), static_cast<__nv_bfloat16*>(Wf), static_cast<__nv_bfloat16*>(Wb));
+    return cudaGetLastError();
+}
+
+cudaError_t cnn_weights_out16(const float* W, void* Wo, cudaStream_t s) {
+    tc::k_weights_out16<<<(9 * 16 * 64 + 255) / 256, 256, 0, s>>>(W, static_cast<__nv_bfloat16*>(Wo));
+    return cudaGetLastError();
+}
+
+cudaError_t cnn_weights_in(const float* W, void* Win, cudaStream_t s) {
+    tc::k_weights_in<<<(tc::kInPlanes * 64 * 8 + 255) / 256, 256, 0, s>>>(W, static_cast<__nv_bfloat16*>(Win));
     return cudaGetLastError();
 }
 

@@ -120,6 +120,12 @@ cudaError_t cnn_flip_thin(const float* W, int ci, int co, float* Wb, cudaStream_
 cudaError_t cnn_conv64_tc(int B, int H, int W, const void* X, const void* Wk, const float* bias, const void* mask,
                           void* Y, int mode, int relu, unsigned* err, cudaStream_t s);
 cudaError_t cnn_weights_kmajor(const void* W, void* Wf, void* Wb, cudaStream_t s);
+cudaError_t cnn_conv_out_tc(int B, int H, int W, const void* X, const void* Wo, const float* bias, float* Y,
+                            unsigned* err, cudaStream_t s);
+cudaError_t cnn_conv_in_tc(int B, int H, int W, const void* X, const void* Win, const float* bias, void* Y, int relu,
+                           unsigned* err, cudaStream_t s);
+cudaError_t cnn_weights_out16(const float* W, void* Wo, cudaStream_t s);
+cudaError_t cnn_weights_in(const float* W, void* Win, cudaStream_t s);
 cudaError_t cnn_mse(const float* pred, const float* target, long long n, float* grad, float* partial, int parts,
                     cudaStream_t s);
 cudaError_t cnn_adam(float* p, const float* g, float* m, float* v, long long n, float lr, float b1, float b2, float eps,

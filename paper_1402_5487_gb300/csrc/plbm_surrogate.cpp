@@ -40,8 +40,10 @@ struct Sur {
     void* wflip = nullptr;          // their backward-data form
     float* w6flip = nullptr;        // backward-data weights of the last layer (4 -> 64)
     void* wtc = nullptr;            // K-major bf16 weights for tcgen05: 4 layers x (forward, backward data)
+    void* win = nullptr;            // first layer (4 -> 64) for tcgen05: bf16 [6][64][8]
+    void* wout = nullptr;           // last layer (64 -> 4) for tcgen05: bf16 [9][16][64]
     unsigned* derr = nullptr;       // device flag: a bounded wait in a tensor-core kernel ran out
-    int use_tc = 1;                 // 64 -> 64 forward and backward data: 1 tcgen05, 0 mma.sync
+    int use_tc = 1;                 // forward convolutions and 64 -> 64 backward data: 1 tcgen05, 0 mma.sync / CUDA cores
     void* act[kLayers] = {nullptr}; // act[0..4] bf16 [B][H][W][64]; act[5] fp32 [B][H][W][4]
     void* dz[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // dL/d(pre-activation) of layers 1..5
     float* dout = nullptr;
@@ -97,7 +99,7 @@ void free_sur(Sur* s) {
     if (s->stream) cudaStreamSynchronize(s->stream);
     void* bufs[] = {s->p, s->g, s->m, s->v, s->pr, s->wbf, s->wflip, s->w6flip, s->dz[0], s->dz[1], s->dz[2],
                     s->dz[3], s->dz[4], s->dout, s->part, s->part_b, s->loss_part, s->Fold, s->Fnew, s->xin,
-                    s->planes, s->sums, s->wtc, s->derr};
+                    s->planes, s->sums, s->wtc, s->derr, s->win, s->wout};
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (void* a : s->act)
@@ -122,13 +124,19 @@ plbm_status refresh_weights(Sur* s) {
         SCK(plbm::cnn_weights_kmajor(wb, wtc_fwd(s, l), wtc_bwd(s, l), s->stream));
     }
     SCK(plbm::cnn_flip_thin(s->pr + s->woff[5], 64, 4, s->w6flip, s->stream));
+    SCK(plbm::cnn_weights_in(s->pr + s->woff[0], s->win, s->stream));
+    SCK(plbm::cnn_weights_out16(s->pr + s->woff[5], s->wout, s->stream));
     return PLBM_OK;
 }
 
 plbm_status forward(Sur* s, int B, const void* x) {
     const int H = s->H, W = s->W;
-    SCK(plbm::cnn_conv_thin_fwd(4, 64, 0, 0, B, H, W, x, s->pr + s->woff[0], s->p + s->boff[0], nullptr, s->act[0],
-                                0, 1, s->stream));
+    if (s->use_tc) {
+        SCK(plbm::cnn_conv_in_tc(B, H, W, x, s->win, s->p + s->boff[0], s->act[0], 1, s->derr, s->stream));
+    } else {
+        SCK(plbm::cnn_conv_thin_fwd(4, 64, 0, 0, B, H, W, x, s->pr + s->woff[0], s->p + s->boff[0], nullptr,
+                                    s->act[0], 0, 1, s->stream));
+    }
     for (int l = 1; l <= 4; ++l) {
         if (s->use_tc) {
             SCK(plbm::cnn_conv64_tc(B, H, W, s->act[l - 1], wtc_fwd(s, l), s->p + s->boff[l], nullptr, s->act[l], 0, 1,
@@ -139,8 +147,13 @@ plbm_status forward(Sur* s, int B, const void* x) {
                                      s->stream));
         }
     }
-    SCK(plbm::cnn_conv_thin_fwd(64, 4, 0, 1, B, H, W, s->act[4], s->pr + s->woff[5], s->p + s->boff[5], nullptr,
-                                s->act[5], 0, 0, s->stream));
+    if (s->use_tc) {
+        SCK(plbm::cnn_conv_out_tc(B, H, W, s->act[4], s->wout, s->p + s->boff[5], static_cast<float*>(s->act[5]),
+                                  s->derr, s->stream));
+    } else {
+        SCK(plbm::cnn_conv_thin_fwd(64, 4, 0, 1, B, H, W, s->act[4], s->pr + s->woff[5], s->p + s->boff[5], nullptr,
+                                    s->act[5], 0, 0, s->stream));
+    }
     return PLBM_OK;
 }
 
@@ -228,7 +241,8 @@ plbm_status plbm_sur_create(int max_batch, int H, int W, unsigned long long seed
         {(void**)&s->part, part_n * 4}, {(void**)&s->part_b, partb_n * 4}, {(void**)&s->loss_part, 1024 * 4},
         {(void**)&s->Fold, pix * 4 * 4}, {(void**)&s->Fnew, pix * 4 * 4}, {&s->xin, pix * 4 * 2},
         {(void**)&s->planes, (size_t)H * W * 4 * 8}, {(void**)&s->sums, (size_t)max_batch * 2 * 64 * 4 * 8},
-        {&s->wtc, 8 * 9 * 64 * 64 * 2}, {(void**)&s->derr, 256},
+        {&s->wtc, 8 * 9 * 64 * 64 * 2}, {(void**)&s->derr, 256}, {&s->win, 6 * 64 * 8 * 2},
+        {&s->wout, 9 * 16 * 64 * 2},
     };
     for (auto& a : allocs) {
         if (cudaMalloc(a.p, a.n) != cudaSuccess) {
