@@ -350,6 +350,11 @@ plbm_status plbm_sur_assemble(plbm_surrogate s, const float *snaps, long long np
  * steps (Eq. eq:srt).  fell_back[b] (host, may be NULL) reports which. */
 plbm_status plbm_sur_advance(plbm_surrogate s, plbm_handle *hs, int n, int K, double tol, int *fell_back);
 
+/* Drift values (as defined for plbm_sur_advance) of the first n lattices of the
+ * last advance, into out[n] (host).  PLBM_E_ARG if n exceeds that advance's
+ * lattice count. */
+plbm_status plbm_sur_last_drift(plbm_surrogate s, double *out, int n);
+
 /* Text of the last error of s (or of the calling thread when NULL). */
 const char *plbm_sur_last_error(plbm_surrogate s);
 

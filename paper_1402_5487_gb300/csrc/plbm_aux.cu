@@ -129,6 +129,73 @@ __global__ void k_moments(const __grid_constant__ LatticeParams P, const S* __re
     if (theta) theta[n] = t;
 }
 
+// Moments of the stored state packed for the surrogate: F[n] = (rho, u_x, u_y,
+// theta) in FP32 and the network input x[n] = bf16((F - mean_in) * istd_in).
+// FP32 arithmetic on the deviations g = f - w0 (the network's input is bf16 and
+// its fields FP32): rho = rho0 + sum g, j = sum v g, E = E0 + sum |v|^2 g, with
+// the row and column sums of g factorising the velocity weights.
+template <typename S>
+__device__ __forceinline__ float dev_f32(const S* f, long long i, double w0) {
+    return Storage<S>::load(f + i);
+}
+template <>
+__device__ __forceinline__ float dev_f32<double>(const double* f, long long i, double w0) {
+    return (float)(__ldg(f + i) - w0);
+}
+
+template <typename S, int Q1>
+__global__ void k_moments_pack(const __grid_constant__ LatticeParams P, const S* __restrict__ f,
+                               float4* __restrict__ F, __nv_bfloat16* __restrict__ x, float4 mean_in,
+                               float4 istd_in) {
+    const int xx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (xx >= P.nx) return;
+    constexpr int kQ1 = Q1 ? Q1 : kMaxQ1;
+    const int q1 = Q1 ? Q1 : P.q1;
+    float sx[kQ1], ty[kQ1];
+#pragma unroll
+    for (int i = 0; i < kQ1; ++i) sx[i] = ty[i] = 0.0f;
+#pragma unroll
+    for (int i = 0; i < kQ1; ++i) {
+        if (i >= q1) break;
+#pragma unroll
+        for (int j = 0; j < kQ1; ++j) {
+            if (j >= q1) break;
+            const int p = i * q1 + j;
+            const float g = dev_f32<S>(f, elem_index(P, p, xx, y), P.W0[p]);
+            sx[i] += g;
+            ty[j] += g;
+        }
+    }
+    float w = 0.0f, wv = 0.0f, wv2 = 0.0f, dr = 0.0f, jx = 0.0f, jy = 0.0f, de = 0.0f;
+#pragma unroll
+    for (int i = 0; i < kQ1; ++i) {
+        if (i >= q1) break;
+        const float v = (float)P.v[i];
+        w += P.w1f[i];
+        wv += v * P.w1f[i];
+        wv2 += v * v * P.w1f[i];
+        dr += sx[i];
+        jx += v * sx[i];
+        jy += v * ty[i];
+        de += v * v * (sx[i] + ty[i]);
+    }
+    const float rho = w * w + dr;
+    const float en = 2.0f * wv2 * w + de;
+    const float ir = 1.0f / rho;
+    const float ux = (jx + wv * w) * ir, uy = (jy + wv * w) * ir;
+    const float th = 0.5f * (en * ir - (ux * ux + uy * uy));
+    const long long n = (long long)y * P.nx + xx;
+    const float4 v = make_float4(rho, ux, uy, th);
+    F[n] = v;
+    __nv_bfloat162 lo = __floats2bfloat162_rn((v.x - mean_in.x) * istd_in.x, (v.y - mean_in.y) * istd_in.y);
+    __nv_bfloat162 hi = __floats2bfloat162_rn((v.z - mean_in.z) * istd_in.z, (v.w - mean_in.w) * istd_in.w);
+    uint2 o;
+    o.x = *reinterpret_cast<uint32_t*>(&lo);
+    o.y = *reinterpret_cast<uint32_t*>(&hi);
+    reinterpret_cast<uint2*>(x)[n] = o;
+}
+
 template <typename S>
 __global__ void __launch_bounds__(kBlockX) k_reduce_state(const __grid_constant__ LatticeParams P,
                                                           const S* __restrict__ f) {
@@ -228,6 +295,24 @@ cudaError_t launch_moments(int prec, const LatticeParams& P, const void* f, doub
     dim3 grid((P.nx + 127) / 128, P.ny);
     PLBM_DISPATCH(prec, (k_moments<S><<<grid, 128, 0, stream>>>(P, static_cast<const S*>(f), rho,
                                                                 ux, uy, theta)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments_pack(int prec, const LatticeParams& P, const void* f, float* F, void* x,
+                                const float* mean_in, const float* std_in, cudaStream_t stream) {
+    if (P.dim != 2) return cudaErrorInvalidValue;
+    const float4 mi = make_float4(mean_in[0], mean_in[1], mean_in[2], mean_in[3]);
+    const float4 si = make_float4(1.f / std_in[0], 1.f / std_in[1], 1.f / std_in[2], 1.f / std_in[3]);
+    dim3 grid((P.nx + 127) / 128, P.ny);
+    if (P.q1 == 5) {
+        PLBM_DISPATCH(prec, (k_moments_pack<S, 5><<<grid, 128, 0, stream>>>(
+                                P, static_cast<const S*>(f), reinterpret_cast<float4*>(F),
+                                static_cast<__nv_bfloat16*>(x), mi, si)));
+    } else {
+        PLBM_DISPATCH(prec, (k_moments_pack<S, 0><<<grid, 128, 0, stream>>>(
+                                P, static_cast<const S*>(f), reinterpret_cast<float4*>(F),
+                                static_cast<__nv_bfloat16*>(x), mi, si)));
+    }
     return cudaGetLastError();
 }
 

@@ -102,14 +102,77 @@ __global__ void k_field_sums(const float4* __restrict__ F, long long n, double* 
     if (threadIdx.x < 4) out[blockIdx.x * 4 + threadIdx.x] = sh[threadIdx.x][0];
 }
 
+// The same for `nlat` lattices of n nodes each stored one after another:
+// out[(lat * gridDim.x + blk) * 4 + k].  Each thread adds its nodes in FP32
+// (a few per thread), then FP64 warp and block sums in a fixed order.
+__global__ void __launch_bounds__(256) k_field_sums_batch(const float4* __restrict__ F, long long n,
+                                                          double* __restrict__ out) {
+    __shared__ double sh[8][4];
+    const float4* Fl = F + (long long)blockIdx.y * n;
+    float s[4] = {0.f, 0.f, 0.f, 0.f};
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float4 a = Fl[i];
+        s[0] += a.x;
+        s[1] += a.x * a.y;
+        s[2] += a.x * a.z;
+        s[3] += a.x * (2.0f * a.w + a.y * a.y + a.z * a.z);
+    }
+    double d[4] = {s[0], s[1], s[2], s[3]};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) d[k] += __shfl_xor_sync(0xffffffffu, d[k], o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+        for (int k = 0; k < 4; ++k) sh[warp][k] = d[k];
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += sh[w][threadIdx.x];
+        out[((long long)blockIdx.y * gridDim.x + blockIdx.x) * 4 + threadIdx.x] = t;
+    }
+}
+
+// Relative drift of lattice b between the old and the predicted fields (FP64,
+// partial sums added in a fixed order): max(|dM| / M, |dE| / E, |dJ| / (0.1 M)).
+// One warp per lattice.
+__global__ void k_field_drift(const double* __restrict__ so, const double* __restrict__ sn, int nblk, int nlat,
+                              double* __restrict__ drift) {
+    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (b >= nlat) return;
+    double a[4] = {0, 0, 0, 0}, c[4] = {0, 0, 0, 0};
+    for (int k = lane; k < nblk; k += 32)
+        for (int j = 0; j < 4; ++j) {
+            a[j] += so[((long long)b * nblk + k) * 4 + j];
+            c[j] += sn[((long long)b * nblk + k) * 4 + j];
+        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            a[j] += __shfl_xor_sync(0xffffffffu, a[j], o);
+            c[j] += __shfl_xor_sync(0xffffffffu, c[j], o);
+        }
+    if (lane == 0) {
+        const double dm = fabs(c[0] - a[0]) / fabs(a[0]);
+        const double de = fabs(c[3] - a[3]) / fabs(a[3]);
+        const double dj = hypot(c[1] - a[1], c[2] - a[2]) / (0.1 * fabs(a[0]));
+        drift[b] = fmax(dm, fmax(de, dj));
+    }
+}
+
 struct CEConsts {
     float Ginv[16];   // inverse of G_jk = sum_p w0_p m_j(p) m_k(p), m = (1, v_x, v_y, |v|^2)
     float coef;       // (1 - omega) / omega
 };
 
-template <typename S>
+// Q1: the 1D velocity count when known at compile time (arrays then stay in
+// registers), 0 for any q1 <= kMaxQ1.
+template <typename S, int Q1>
 __global__ void k_ce_reconstruct(const __grid_constant__ LatticeParams P, const __grid_constant__ CEConsts K,
                                  const float4* __restrict__ F, S* __restrict__ f) {
+    constexpr int kQ1 = Q1 ? Q1 : kMaxQ1;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= P.nx) return;
@@ -134,17 +197,24 @@ __global__ void k_ce_reconstruct(const __grid_constant__ LatticeParams P, const 
     const float dt_uy = -(ux * duy_x + uy * duy_y) - dp_y * inv_rho;
     const float dt_th = -(ux * dth_x + uy * dth_y) - th * divu;
     // per-axis rule, its u- and theta-derivatives
-    const int q1 = P.q1;
-    float r[2][kMaxQ1], ru[2][kMaxQ1], rt[2][kMaxQ1];
+    const int q1 = Q1 ? Q1 : P.q1;
+    float r[2][kQ1], ru[2][kQ1], rt[2][kQ1];
+#pragma unroll
     for (int a = 0; a < 2; ++a) {
         const float u = a == 0 ? ux : uy;
-        float mu[kMaxQ1 + 1];
+        float mu[kQ1 + 1];
         mu[0] = 1.0f;
         mu[1] = u;
-        for (int k = 1; k + 1 < q1; ++k) mu[k + 1] = u * mu[k] + (float)k * th * mu[k - 1];
-        for (int i = 0; i < q1; ++i) {
+#pragma unroll
+        for (int k = 1; k + 1 < kQ1; ++k)
+            if (k + 1 < q1) mu[k + 1] = u * mu[k] + (float)k * th * mu[k - 1];
+#pragma unroll
+        for (int i = 0; i < kQ1; ++i) {
+            if (i >= q1) break;
             float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
-            for (int k = 0; k < q1; ++k) {
+#pragma unroll
+            for (int k = 0; k < kQ1; ++k) {
+                if (k >= q1) break;
                 const float cik = P.Cf[i * q1 + k] + P.Cf_lo[i * q1 + k];
                 s0 += cik * mu[k];
                 if (k >= 1) s1 += cik * (float)k * mu[k - 1];
@@ -155,11 +225,15 @@ __global__ void k_ce_reconstruct(const __grid_constant__ LatticeParams P, const 
             rt[a][i] = s2;
         }
     }
-    float fneq[kMaxQ], feq[kMaxQ];
+    float fneq[kQ1 * kQ1], feq[kQ1 * kQ1];
     float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
-    for (int i = 0; i < q1; ++i) {
+#pragma unroll
+    for (int i = 0; i < kQ1; ++i) {
+        if (i >= q1) break;
         const float vx = (float)P.v[i];
-        for (int j = 0; j < q1; ++j) {
+#pragma unroll
+        for (int j = 0; j < kQ1; ++j) {
+            if (j >= q1) break;
             const float vy = (float)P.v[j];
             const int p = i * q1 + j;
             const float Drho = dt_rho + vx * drx + vy * dry;
@@ -179,14 +253,21 @@ __global__ void k_ce_reconstruct(const __grid_constant__ LatticeParams P, const 
     }
     float cc[4];
     for (int k = 0; k < 4; ++k) cc[k] = K.Ginv[4 * k] * m0 + K.Ginv[4 * k + 1] * m1 + K.Ginv[4 * k + 2] * m2 + K.Ginv[4 * k + 3] * m3;
-    for (int i = 0; i < q1; ++i) {
+#pragma unroll
+    for (int i = 0; i < kQ1; ++i) {
+        if (i >= q1) break;
         const float vx = (float)P.v[i];
-        for (int j = 0; j < q1; ++j) {
+#pragma unroll
+        for (int j = 0; j < kQ1; ++j) {
+            if (j >= q1) break;
             const float vy = (float)P.v[j];
             const int p = i * q1 + j;
             const float proj = P.W0f[p] * (cc[0] + cc[1] * vx + cc[2] * vy + cc[3] * (vx * vx + vy * vy));
-            const double fp = (double)feq[p] + (double)(fneq[p] - proj);
-            f[elem_index(P, p, x, y)] = Storage<S>::from_f64(fp, P.W0[p]);
+            if constexpr (Storage<S>::kDeviation) {
+                Storage<S>::store(f + elem_index(P, p, x, y), (feq[p] - P.W0f[p]) + (fneq[p] - proj));
+            } else {
+                f[elem_index(P, p, x, y)] = (double)feq[p] + (double)(fneq[p] - proj);
+            }
         }
     }
 }
@@ -233,6 +314,15 @@ cudaError_t ce_apply_delta(const float* F, const float* d, long long n, const fl
 
 int ce_sum_blocks() { return 64; }
 
+cudaError_t ce_field_drift(const float* Fold, const float* Fnew, long long n, int nlat, double* partial_old,
+                           double* partial_new, double* drift, cudaStream_t s) {
+    const dim3 grid(ce_sum_blocks(), nlat);
+    k_field_sums_batch<<<grid, 256, 0, s>>>(reinterpret_cast<const float4*>(Fold), n, partial_old);
+    k_field_sums_batch<<<grid, 256, 0, s>>>(reinterpret_cast<const float4*>(Fnew), n, partial_new);
+    k_field_drift<<<(nlat + 3) / 4, 128, 0, s>>>(partial_old, partial_new, ce_sum_blocks(), nlat, drift);
+    return cudaGetLastError();
+}
+
 cudaError_t ce_field_sums(const float* F, long long n, double* partial, cudaStream_t s) {
     k_field_sums<<<ce_sum_blocks(), 256, 0, s>>>(reinterpret_cast<const float4*>(F), n, partial);
     return cudaGetLastError();
@@ -278,13 +368,26 @@ cudaError_t ce_reconstruct(int prec, const LatticeParams& P, const float* F, voi
     dim3 grid((P.nx + 127) / 128, P.ny);
     const float4* Fv = reinterpret_cast<const float4*>(F);
     switch (prec) {
-        case kF32: k_ce_reconstruct<float><<<grid, 128, 0, s>>>(P, K, Fv, static_cast<float*>(f)); break;
-        case kF16Dev: k_ce_reconstruct<__half><<<grid, 128, 0, s>>>(P, K, Fv, static_cast<__half*>(f)); break;
-        case kBF16Dev:
-            k_ce_reconstruct<__nv_bfloat16><<<grid, 128, 0, s>>>(P, K, Fv, static_cast<__nv_bfloat16*>(f));
+        case kF32:
+            if (P.q1 == 5) k_ce_reconstruct<float, 5><<<grid, 128, 0, s>>>(P, K, Fv, static_cast<float*>(f));
+            else k_ce_reconstruct<float, 0><<<grid, 128, 0, s>>>(P, K, Fv, static_cast<float*>(f));
             break;
-        case kF64: k_ce_reconstruct<double><<<grid, 128, 0, s>>>(P, K, Fv, static_cast<double*>(f)); break;
-        default: return cudaErrorInvalidValue;
+        case kF16Dev:
+            if (P.q1 == 5) k_ce_reconstruct<__half, 5><<<grid, 128, 0, s>>>(P, K, Fv, static_cast<__half*>(f));
+            else k_ce_reconstruct<__half, 0><<<grid, 128, 0, s>>>(P, K, Fv, static_cast<__half*>(f));
+            break;
+        case kBF16Dev:
+            if (P.q1 == 5)
+                k_ce_reconstruct<__nv_bfloat16, 5><<<grid, 128, 0, s>>>(P, K, Fv, static_cast<__nv_bfloat16*>(f));
+            else
+                k_ce_reconstruct<__nv_bfloat16, 0><<<grid, 128, 0, s>>>(P, K, Fv, static_cast<__nv_bfloat16*>(f));
+            break;
+        case kF64:
+            if (P.q1 == 5) k_ce_reconstruct<double, 5><<<grid, 128, 0, s>>>(P, K, Fv, static_cast<double*>(f));
+            else k_ce_reconstruct<double, 0><<<grid, 128, 0, s>>>(P, K, Fv, static_cast<double*>(f));
+            break;
+        default:
+            return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }

@@ -144,6 +144,8 @@ cudaError_t ce_apply_delta(const float* F, const float* d, long long n, const fl
 int ce_sum_blocks();
 cudaError_t ce_field_sums(const float* F, long long n, double* partial, cudaStream_t s);
 cudaError_t ce_reconstruct(int prec, const LatticeParams& P, const float* F, void* f, cudaStream_t s);
+cudaError_t ce_field_drift(const float* Fold, const float* Fnew, long long n, int nlat, double* partial_old,
+                           double* partial_new, double* drift, cudaStream_t s);
 
 // Internals of a live handle for the surrogate path (plbm_host.cpp).
 struct HandleView {
@@ -166,6 +168,8 @@ cudaError_t launch_init(int prec, const LatticeParams& P, const double* rho, con
                         const double* uy, const double* theta, void* f, cudaStream_t stream);
 cudaError_t launch_moments(int prec, const LatticeParams& P, const void* f, double* rho,
                            double* ux, double* uy, double* theta, cudaStream_t stream);
+cudaError_t launch_moments_pack(int prec, const LatticeParams& P, const void* f, float* F, void* x,
+                                const float* mean_in, const float* std_in, cudaStream_t stream);
 // Per-block partial sums of the stored state, then one deterministic final pass
 // writing out[0..5] = mass, jx, jy, energy, rho_min, theta_min.
 cudaError_t launch_reduce_state(int prec, const LatticeParams& P, const void* f, double* out,

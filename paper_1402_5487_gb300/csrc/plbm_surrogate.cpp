@@ -56,8 +56,11 @@ struct Sur {
     float *Fold = nullptr, *Fnew = nullptr;
     void* xin = nullptr;
     double* planes = nullptr;
-    double* sums = nullptr;
+    double* sums = nullptr;         // per-block FP64 field sums: old fields, then predicted fields
     double* host_sums = nullptr;
+    double* drift = nullptr;        // device: drift of every lattice of the last advance
+    std::vector<double> last_drift;
+    cudaEvent_t ev = nullptr;
     char err[512] = "";
 };
 
@@ -99,13 +102,14 @@ void free_sur(Sur* s) {
     if (s->stream) cudaStreamSynchronize(s->stream);
     void* bufs[] = {s->p, s->g, s->m, s->v, s->pr, s->wbf, s->wflip, s->w6flip, s->dz[0], s->dz[1], s->dz[2],
                     s->dz[3], s->dz[4], s->dout, s->part, s->part_b, s->loss_part, s->Fold, s->Fnew, s->xin,
-                    s->planes, s->sums, s->wtc, s->derr, s->win, s->wout};
+                    s->planes, s->sums, s->wtc, s->derr, s->win, s->wout, s->drift};
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (void* a : s->act)
         if (a) cudaFree(a);
     if (s->host_loss) cudaFreeHost(s->host_loss);
     if (s->host_sums) cudaFreeHost(s->host_sums);
+    if (s->ev) cudaEventDestroy(s->ev);
     if (s->owns_stream) cudaStreamDestroy(s->stream);
     delete s;
 }
@@ -242,7 +246,7 @@ plbm_status plbm_sur_create(int max_batch, int H, int W, unsigned long long seed
         {(void**)&s->Fold, pix * 4 * 4}, {(void**)&s->Fnew, pix * 4 * 4}, {&s->xin, pix * 4 * 2},
         {(void**)&s->planes, (size_t)H * W * 4 * 8}, {(void**)&s->sums, (size_t)max_batch * 2 * 64 * 4 * 8},
         {&s->wtc, 8 * 9 * 64 * 64 * 2}, {(void**)&s->derr, 256}, {&s->win, 6 * 64 * 8 * 2},
-        {&s->wout, 9 * 16 * 64 * 2},
+        {&s->wout, 9 * 16 * 64 * 2}, {(void**)&s->drift, (size_t)max_batch * 8},
     };
     for (auto& a : allocs) {
         if (cudaMalloc(a.p, a.n) != cudaSuccess) {
@@ -264,6 +268,11 @@ plbm_status plbm_sur_create(int max_batch, int H, int W, unsigned long long seed
         serr(s, "allocation failed");
         free_sur(s);
         return PLBM_E_NOMEM;
+    }
+    if (cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming) != cudaSuccess) {
+        serr(s, "cudaEventCreate failed");
+        free_sur(s);
+        return PLBM_E_CUDA;
     }
     if (cudaMemsetAsync(s->derr, 0, 256, s->stream) != cudaSuccess) {
         serr(s, "cudaMemset failed");
@@ -452,52 +461,53 @@ plbm_status plbm_sur_advance(plbm_surrogate h, plbm_handle* hs, int n, int K, do
             return PLBM_E_ARG;
         }
     }
-    SCK(cudaStreamSynchronize(s->stream));
-    double* pl = s->planes;
+    // 1. fields and network input of every lattice, on the surrogate's stream
+    //    once the lattice's own stream has reached this point
     for (int b = 0; b < n; ++b) {
-        // moments on the handle's stream, then pack on it as well
-        plbm_status r = plbm_moments(hs[b], pl, pl + npix, pl + 2 * npix, pl + 3 * npix, 1);
-        if (r != PLBM_OK) return r;
-        SCK(plbm::ce_pack_fields(pl, pl + npix, pl + 2 * npix, pl + 3 * npix, npix, s->Fold + (size_t)b * npix * 4,
-                                 views[b].stream));
-        SCK(cudaStreamSynchronize(views[b].stream));
+        SCK(cudaEventRecord(s->ev, views[b].stream));
+        SCK(cudaStreamWaitEvent(s->stream, s->ev, 0));
+        SCK(plbm::launch_moments_pack(views[b].prec, *views[b].P, views[b].f_cur, s->Fold + (size_t)b * npix * 4,
+                                      static_cast<char*>(s->xin) + (size_t)b * npix * 4 * 2, s->norm, s->norm + 4,
+                                      s->stream));
     }
-    SCK(plbm::ce_normalise(s->Fold, npix * n, s->norm, s->norm + 4, s->xin, s->stream));
+    // 2. network, predicted fields, drift of the conserved sums
     plbm_status r = forward(s, n, s->xin);
     if (r != PLBM_OK) return r;
-    SCK(plbm::ce_apply_delta(s->Fold, static_cast<const float*>(s->act[5]), npix * n, s->norm + 8, s->norm + 12, s->Fnew, s->stream));
-    const int nb = plbm::ce_sum_blocks();
-    for (int b = 0; b < n; ++b) {
-        SCK(plbm::ce_field_sums(s->Fold + (size_t)b * npix * 4, npix, s->sums + (size_t)(2 * b) * nb * 4, s->stream));
-        SCK(plbm::ce_field_sums(s->Fnew + (size_t)b * npix * 4, npix, s->sums + (size_t)(2 * b + 1) * nb * 4,
-                                s->stream));
-    }
-    SCK(cudaMemcpyAsync(s->host_sums, s->sums, (size_t)n * 2 * nb * 4 * 8, cudaMemcpyDeviceToHost, s->stream));
+    SCK(plbm::ce_apply_delta(s->Fold, static_cast<const float*>(s->act[5]), npix * n, s->norm + 8, s->norm + 12,
+                             s->Fnew, s->stream));
+    const size_t half = (size_t)s->Bm * plbm::ce_sum_blocks() * 4;
+    SCK(plbm::ce_field_drift(s->Fold, s->Fnew, npix, n, s->sums, s->sums + half, s->drift, s->stream));
+    SCK(cudaMemcpyAsync(s->host_sums, s->drift, (size_t)n * 8, cudaMemcpyDeviceToHost, s->stream));
     SCK(cudaStreamSynchronize(s->stream));
+    s->last_drift.assign(s->host_sums, s->host_sums + n);
+    // 3. accepted lattices: Chapman-Enskog populations on the surrogate's stream,
+    //    which the lattice's stream then waits for; the others run K LBM steps
+    bool any = false;
     for (int b = 0; b < n; ++b) {
-        double so[4] = {0, 0, 0, 0}, sn[4] = {0, 0, 0, 0};
-        for (int k = 0; k < nb; ++k)
-            for (int j = 0; j < 4; ++j) {
-                so[j] += s->host_sums[((size_t)(2 * b) * nb + k) * 4 + j];
-                sn[j] += s->host_sums[((size_t)(2 * b + 1) * nb + k) * 4 + j];
-            }
-        // relative drift: mass and energy against themselves, momentum against 0.1 M
-        const double dm = std::fabs(sn[0] - so[0]) / std::fabs(so[0]);
-        const double de = std::fabs(sn[3] - so[3]) / std::fabs(so[3]);
-        const double dj = std::hypot(sn[1] - so[1], sn[2] - so[2]) / (0.1 * std::fabs(so[0]));
-        const double drift = std::fmax(dm, std::fmax(de, dj));
-        const bool fall = !(drift <= tol);
+        const bool fall = !(s->last_drift[b] <= tol);
         if (fell_back) fell_back[b] = fall ? 1 : 0;
-        if (fall) {
+        if (fall) continue;
+        SCK(plbm::ce_reconstruct(views[b].prec, *views[b].P, s->Fnew + (size_t)b * npix * 4, views[b].f_cur,
+                                 s->stream));
+        *views[b].steps += K;
+        any = true;
+    }
+    if (any) SCK(cudaEventRecord(s->ev, s->stream));
+    for (int b = 0; b < n; ++b) {
+        if (!(s->last_drift[b] <= tol)) {
             r = plbm_step(hs[b], K);
             if (r != PLBM_OK) return r;
         } else {
-            SCK(cudaStreamSynchronize(s->stream));
-            SCK(plbm::ce_reconstruct(views[b].prec, *views[b].P, s->Fnew + (size_t)b * npix * 4, views[b].f_cur,
-                                     views[b].stream));
-            *views[b].steps += K;
+            SCK(cudaStreamWaitEvent(views[b].stream, s->ev, 0));
         }
     }
+    return PLBM_OK;
+}
+
+plbm_status plbm_sur_last_drift(plbm_surrogate h, double* out, int n) {
+    Sur* s = as_sur(h);
+    if (!s || !out || n < 0 || (size_t)n > s->last_drift.size()) return PLBM_E_ARG;
+    for (int b = 0; b < n; ++b) out[b] = s->last_drift[b];
     return PLBM_OK;
 }
 

@@ -136,6 +136,7 @@ SIGNATURES = {
                                          ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "plbm_sur_advance": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
                                         ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_int)]),
+    "plbm_sur_last_drift": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "plbm_sur_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "plbm_last_error": (ctypes.c_char_p, [_H]),
     "plbm_status_string": (ctypes.c_char_p, [ctypes.c_int]),

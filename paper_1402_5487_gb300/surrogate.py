@@ -237,4 +237,11 @@ class Surrogate:
         hs = (ctypes.c_void_p * n)(*[s.h.value if hasattr(s.h, "value") else s.h for s in solvers])
         flags = (ctypes.c_int * n)()
         self._ok(plbm.lib().plbm_sur_advance(self.h, hs, n, int(K), float(tol), flags))
+        self.n_last = n
         return list(flags)
+
+    def last_drift(self):
+        """Drift of every lattice of the last advance (the quantity compared with tol)."""
+        out = np.empty(self.n_last, dtype=np.float64)
+        self._ok(plbm.lib().plbm_sur_last_drift(self.h, out.ctypes.data, self.n_last))
+        return out

@@ -166,3 +166,28 @@ def test_reconstruction_matches_oracle_and_fallback_matches_lbm(trained):
     assert np.array_equal(b.get_populations(), c.get_populations())
     for s in (a, b, c):
         s.close()
+
+
+def test_reported_drift_matches_fields_before_and_after(trained):
+    # After an accepted advance the populations carry the predicted fields
+    # exactly (projection), so the drift the library reports must equal the
+    # drift of the FP64 sums of the moments before and after.
+    net = trained[0]
+    L = 128
+    sol = plbm.Solver(2, SG.V5, SG.OMEGA, L, L, theta0=SG.THETA0, prec="f32")
+    sol.init(*SG.trajectory_fields(2001, L))
+    sol.step(64)
+
+    def sums(m):
+        rho, ux, uy, th = m
+        return np.array([rho.sum(), (rho * ux).sum(), (rho * uy).sum(),
+                         (rho * (2 * th + ux * ux + uy * uy)).sum()])
+
+    a = sums(sol.moments())
+    assert net.advance([sol], K=32, tol=1.0) == [0]
+    b = sums(sol.moments())
+    ref = max(abs(b[0] - a[0]) / abs(a[0]), abs(b[3] - a[3]) / abs(a[3]),
+              np.hypot(b[1] - a[1], b[2] - a[2]) / (0.1 * abs(a[0])))
+    got = net.last_drift()[0]
+    assert abs(got - ref) <= 1e-6 + 1e-3 * ref, (got, ref)
+    sol.close()
