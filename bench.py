@@ -243,32 +243,67 @@ def run_surrogate(torch, n_train=2000, n_test=100, train_steps=2000, batch=16, K
     out["test_mse_normalised"] = {"network": mse_net, "persistence": mse_p}
     # rollouts: the LBM trajectory (FP32, parity-checked against the FP64 oracle) is the judge
     nroll = min(n_test, 64)
-    solvers = [plbm.Solver(2, SG.V5, SG.OMEGA, L, L, theta0=SG.THETA0, prec="f32") for _ in range(nroll)]
-    for s, seed in zip(solvers, test_seeds):
-        s.init(*SG.trajectory_fields(seed, L))
-        s.step(64)
-    errs = {}
-    fell = 0
-    calls = 0
-    for k in range(1, 17):
-        flags = net.advance(solvers, K=K, tol=1e-4)
-        fell += sum(flags)
-        calls += len(flags)
-        if k in (1, 4, 16):
-            e_net, e_pers = [], []
-            for j, s in enumerate(solvers):
-                ref = tstack[j * snaps + k].cpu().numpy().astype(np.float64)
-                ref = [ref[:, c].reshape(L, L) for c in range(4)]
-                ini = tstack[j * snaps].cpu().numpy().astype(np.float64)
-                ini = [ini[:, c].reshape(L, L) for c in range(4)]
-                e_net.append(_field_err(s.moments(), ref))
-                e_pers.append(_field_err(ini, ref))
-            errs[str(k)] = {"surrogate_vs_lbm": {f: float(np.mean([e[f] for e in e_net])) for f in ("rho", "u", "theta")},
-                            "persistence_vs_lbm": {f: float(np.mean([e[f] for e in e_pers])) for f in ("rho", "u", "theta")}}
+
+    def rollout(tol, checkpoints=(1, 4, 16)):
+        solvers = [plbm.Solver(2, SG.V5, SG.OMEGA, L, L, theta0=SG.THETA0, prec="f32") for _ in range(nroll)]
+        for s, seed in zip(solvers, test_seeds):
+            s.init(*SG.trajectory_fields(seed, L))
+            s.step(64)
+        errs, drifts = {}, []
+        fell = calls = 0
+        t_roll = 0.0
+        for k in range(1, 17):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            flags = net.advance(solvers, K=K, tol=tol)
+            torch.cuda.synchronize()
+            t_roll += time.perf_counter() - t0
+            drifts.append(net.last_drift())
+            fell += sum(flags)
+            calls += len(flags)
+            if k in checkpoints:
+                e_net, e_pers = [], []
+                for j, s in enumerate(solvers):
+                    ref = tstack[j * snaps + k].cpu().numpy().astype(np.float64)
+                    ref = [ref[:, c].reshape(L, L) for c in range(4)]
+                    ini = tstack[j * snaps].cpu().numpy().astype(np.float64)
+                    ini = [ini[:, c].reshape(L, L) for c in range(4)]
+                    e_net.append(_field_err(s.moments(), ref))
+                    e_pers.append(_field_err(ini, ref))
+                errs[str(k)] = {"surrogate_vs_lbm": {f: float(np.mean([e[f] for e in e_net])) for f in ("rho", "u", "theta")},
+                                "persistence_vs_lbm": {f: float(np.mean([e[f] for e in e_pers])) for f in ("rho", "u", "theta")}}
+        for s in solvers:
+            s.close()
+        return t_roll, fell / calls, np.concatenate(drifts), errs
+
+    t_roll, rate, d, errs = rollout(1e-4)
     out["rollout_errors_mean_over_%d_seeds" % nroll] = errs
-    out["fallback_rate"] = fell / calls
-    for s in solvers:
-        s.close()
+    out["fallback_rate"] = rate
+    out["drift"] = {"tol": 1e-4, "median": float(np.median(d)), "p10": float(np.percentile(d, 10)),
+                    "p90": float(np.percentile(d, 90)), "fraction_within_tol": float(np.mean(d <= 1e-4))}
+    sweep = {"1e-4": (t_roll, rate, errs["16"]["surrogate_vs_lbm"]["u"])}
+    for tol in (3e-4, 1e-3):
+        t_r, r_r, _, e_r = rollout(tol, checkpoints=(16,))
+        sweep["%g" % tol] = (t_r, r_r, e_r["16"]["surrogate_vs_lbm"]["u"])
+    # gain test: the same lattices and horizon (16 x K steps) with plain batched LBM
+    insts = [SG.trajectory_instance(sd, L)[0] for sd in test_seeds[:nroll]]
+    bt = Batch(insts, prec="f32")
+    for sol, sd in zip(bt.solvers, test_seeds[:nroll]):
+        sol.init(*SG.trajectory_fields(sd, L))
+    bt.step(64, "persistent_graph")
+    bt.stream.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(bt.stream)
+    bt.step(16 * K, "persistent_graph")
+    e1.record(bt.stream)
+    e1.synchronize()
+    t_lbm_roll = e0.elapsed_time(e1) * 1e-3
+    bt.close()
+    out["gain_test"] = {"lattices": nroll, "horizon_steps": 16 * K, "lbm_s": t_lbm_roll,
+                        "by_tol": {k: {"surrogate_with_fallback_s": v[0], "speedup": t_lbm_roll / v[0],
+                                       "fallback_rate": v[1], "u_error_at_horizon_vs_lbm": v[2]}
+                                   for k, v in sweep.items()}}
     # FP64 oracle check on two held-out seeds after one advance
     orc = []
     for seed in test_seeds[:2]:
@@ -388,7 +423,7 @@ def main():
     ap.add_argument("--batch-instances", type=int, default=256)
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--surrogate-train", type=int, default=2000, help="training trajectories")
-    ap.add_argument("--surrogate-steps", type=int, default=2000, help="Adam steps")
+    ap.add_argument("--surrogate-steps", type=int, default=6000, help="Adam steps")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

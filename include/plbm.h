@@ -347,7 +347,11 @@ plbm_status plbm_sur_assemble(plbm_surrogate s, const float *snaps, long long np
  * -((1 - omega) / omega) D f^eq with Euler time derivatives, projected so the
  * conserved moments equal the predicted fields) and the step counter advances
  * by K.  Otherwise (or for a non-finite prediction) the lattice runs K ordinary
- * steps (Eq. eq:srt).  fell_back[b] (host, may be NULL) reports which. */
+ * steps (Eq. eq:srt); fallback lattices in the row-paired layout of one
+ * precision take them together, one persistent launch per step, without the
+ * check_every status reads of plbm_step (plbm_check reads the status).
+ * fell_back[b] (host, may be NULL) reports which.  Synchronous up to the drift
+ * read; the lattices' streams are ordered after the work it queues. */
 plbm_status plbm_sur_advance(plbm_surrogate s, plbm_handle *hs, int n, int K, double tol, int *fell_back);
 
 /* Drift values (as defined for plbm_sur_advance) of the first n lattices of the

@@ -248,6 +248,8 @@ bool handle_view(void* hh, HandleView* out) {
     if (!h || !out || !h->initialised || h->sticky != PLBM_OK) return false;
     out->P = &h->P;
     out->f_cur = h->f[h->cur];
+    out->f_next = h->f[h->cur ^ 1];
+    out->cur = &h->cur;
     out->prec = h->prec;
     out->stream = h->stream;
     out->steps = &h->steps;

@@ -151,6 +151,8 @@ cudaError_t ce_field_drift(const float* Fold, const float* Fnew, long long n, in
 struct HandleView {
     const LatticeParams* P;
     void* f_cur;
+    void* f_next;      // the other population array
+    int* cur;          // index of the current array (0/1)
     int prec;
     cudaStream_t stream;
     long long* steps;

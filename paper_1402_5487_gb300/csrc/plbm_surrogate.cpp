@@ -59,6 +59,8 @@ struct Sur {
     double* sums = nullptr;         // per-block FP64 field sums: old fields, then predicted fields
     double* host_sums = nullptr;
     double* drift = nullptr;        // device: drift of every lattice of the last advance
+    plbm::PairParams* fb_table = nullptr;  // device: batched fallback of row-paired lattices
+    int sms = 0;
     std::vector<double> last_drift;
     cudaEvent_t ev = nullptr;
     char err[512] = "";
@@ -102,7 +104,7 @@ void free_sur(Sur* s) {
     if (s->stream) cudaStreamSynchronize(s->stream);
     void* bufs[] = {s->p, s->g, s->m, s->v, s->pr, s->wbf, s->wflip, s->w6flip, s->dz[0], s->dz[1], s->dz[2],
                     s->dz[3], s->dz[4], s->dout, s->part, s->part_b, s->loss_part, s->Fold, s->Fnew, s->xin,
-                    s->planes, s->sums, s->wtc, s->derr, s->win, s->wout, s->drift};
+                    s->planes, s->sums, s->wtc, s->derr, s->win, s->wout, s->drift, s->fb_table};
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (void* a : s->act)
@@ -247,6 +249,7 @@ plbm_status plbm_sur_create(int max_batch, int H, int W, unsigned long long seed
         {(void**)&s->planes, (size_t)H * W * 4 * 8}, {(void**)&s->sums, (size_t)max_batch * 2 * 64 * 4 * 8},
         {&s->wtc, 8 * 9 * 64 * 64 * 2}, {(void**)&s->derr, 256}, {&s->win, 6 * 64 * 8 * 2},
         {&s->wout, 9 * 16 * 64 * 2}, {(void**)&s->drift, (size_t)max_batch * 8},
+        {(void**)&s->fb_table, (size_t)max_batch * sizeof(plbm::PairParams)},
     };
     for (auto& a : allocs) {
         if (cudaMalloc(a.p, a.n) != cudaSuccess) {
@@ -268,6 +271,12 @@ plbm_status plbm_sur_create(int max_batch, int H, int W, unsigned long long seed
         serr(s, "allocation failed");
         free_sur(s);
         return PLBM_E_NOMEM;
+    }
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev);
+        if (s->sms < 1) s->sms = 1;
     }
     if (cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming) != cudaSuccess) {
         serr(s, "cudaEventCreate failed");
@@ -492,14 +501,59 @@ plbm_status plbm_sur_advance(plbm_surrogate h, plbm_handle* hs, int n, int K, do
         *views[b].steps += K;
         any = true;
     }
-    if (any) SCK(cudaEventRecord(s->ev, s->stream));
+    // Fallback lattices in the row-paired layout (one precision) take K steps
+    // together, one persistent launch per step over all of them (the batched
+    // runner's kernel); any other fallback lattice steps on its own.
+    std::vector<int> batched, single;
+    int bprec = -1;
     for (int b = 0; b < n; ++b) {
-        if (!(s->last_drift[b] <= tol)) {
-            r = plbm_step(hs[b], K);
-            if (r != PLBM_OK) return r;
+        if (s->last_drift[b] <= tol) continue;
+        const plbm::LatticeParams& P = *views[b].P;
+        if (P.paired && (bprec < 0 || views[b].prec == bprec)) {
+            bprec = views[b].prec;
+            batched.push_back(b);
         } else {
-            SCK(cudaStreamWaitEvent(views[b].stream, s->ev, 0));
+            single.push_back(b);
         }
+    }
+    if (batched.size() < 2) {
+        single.insert(single.end(), batched.begin(), batched.end());
+        batched.clear();
+    }
+    if (!batched.empty()) {
+        constexpr int kBX = 128;
+        std::vector<plbm::PairParams> table(batched.size());
+        int tiles = 0;
+        for (size_t k = 0; k < batched.size(); ++k) {
+            const plbm::HandleView& v = views[batched[k]];
+            plbm::PairParams Q = plbm::pair_params(*v.P);
+            Q.f[0] = v.f_cur;
+            Q.f[1] = v.f_next;
+            Q.tiles_x = (Q.nx + kBX - 1) / kBX;
+            Q.tile_begin = tiles;
+            tiles += Q.tiles_x * Q.half_ny;
+            table[k] = Q;
+        }
+        SCK(cudaMemcpyAsync(s->fb_table, table.data(), sizeof(plbm::PairParams) * table.size(),
+                            cudaMemcpyHostToDevice, s->stream));
+        int occ = 1;
+        if (plbm::batch_occupancy(bprec, kBX, &occ) != cudaSuccess || occ < 1) occ = 1;
+        for (int k = 0; k < K; ++k)
+            SCK(plbm::launch_batch(bprec, s->fb_table, (int)table.size(), tiles, kBX, s->sms * occ, k & 1,
+                                   s->stream));
+        for (int b : batched) {
+            if (K & 1) *views[b].cur ^= 1;
+            *views[b].steps += K;
+        }
+        any = true;
+    }
+    if (any) SCK(cudaEventRecord(s->ev, s->stream));
+    for (int b = 0; b < n; ++b)
+        if (s->last_drift[b] <= tol || std::find(batched.begin(), batched.end(), b) != batched.end())
+            SCK(cudaStreamWaitEvent(views[b].stream, s->ev, 0));
+    for (int b : single) {
+        r = plbm_step(hs[b], K);
+        if (r != PLBM_OK) return r;
     }
     return PLBM_OK;
 }

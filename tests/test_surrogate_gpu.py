@@ -191,3 +191,31 @@ def test_reported_drift_matches_fields_before_and_after(trained):
     got = net.last_drift()[0]
     assert abs(got - ref) <= 1e-6 + 1e-3 * ref, (got, ref)
     sol.close()
+
+
+@pytest.mark.parametrize("K", [32, 5])
+def test_batched_fallback_equals_plain_stepping(trained, K):
+    # Several fallback lattices in the row-paired layout step together in one
+    # persistent launch per step; the populations must equal plain stepping bit
+    # for bit, for even and odd K (the current array flips when K is odd).
+    net = trained[0]
+    L = 128
+    mk = lambda: plbm.Solver(2, SG.V5, SG.OMEGA, L, L, theta0=SG.THETA0, prec="f32")
+    a = [mk() for _ in range(3)]
+    b = [mk() for _ in range(3)]
+    for j, (x, y) in enumerate(zip(a, b)):
+        f = SG.trajectory_fields(3000 + j, L)
+        x.init(*f)
+        y.init(*f)
+        x.step(64)
+        y.step(64)
+    assert net.advance(a, K=K, tol=0.0) == [1, 1, 1]
+    for x, y in zip(a, b):
+        y.step(K)
+        assert np.array_equal(x.get_populations(), y.get_populations())
+        assert x.diagnostics()["steps"] == 64 + K
+        x.step(3)
+        y.step(3)
+        assert np.array_equal(x.get_populations(), y.get_populations())
+    for s in a + b:
+        s.close()
