@@ -219,9 +219,9 @@ def run_surrogate(torch, n_train=2000, n_test=100, train_steps=2000, batch=16, K
     from paper_1402_5487_gb300.batch import Batch
     out = {"grid": [L, L], "K": K, "train_trajectories": n_train, "test_trajectories": n_test}
     t0 = time.perf_counter()
-    stack = SG.generate(range(n_train), L=L, K=K, snaps=9)
+    stack = SG.generate(range(n_train), L=L, K=K, snaps=17)
     out["generate_seconds"] = time.perf_counter() - t0
-    pairs = SG.pairs_of(n_train, 9)
+    pairs = SG.pairs_of(n_train, 17)
     norm = SG.fit_norm(stack, pairs)
     net = SG.Surrogate(64, L, L, seed=0)
     net.set_norm(*norm)
@@ -356,6 +356,42 @@ def run_surrogate(torch, n_train=2000, n_test=100, train_steps=2000, batch=16, K
     return out
 
 
+def run_case(torch, args):
+    """One secondary workload alone: the surrogate network on a batch of 256 x 256
+    lattices (forward passes and Adam steps on seeded random tensors), or the
+    batched 256-instance sweep."""
+    if args.case == "batched":
+        return {"case": "batched", **run_batched(torch, steps=args.steps, warmup=args.warmup,
+                                                 n=args.batch_instances)}
+    import ctypes
+    from paper_1402_5487_gb300 import plbm, surrogate as SG
+    B, L = args.batch, 256
+    net = SG.Surrogate(B, L, L, seed=0)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn((B, L, L, 4), generator=g, device="cuda").to(torch.bfloat16)
+    y = torch.randn((B, L, L, 4), generator=g, device="cuda")
+    out = {"case": "surrogate", "batch": B, "grid": [L, L]}
+    fwd_flops = 2.0 * L * L * (9 * 4 * 64 + 4 * 9 * 64 * 64 + 9 * 64 * 4)
+    for name, call, flops in (
+            ("forward", lambda: plbm.lib().plbm_sur_forward(net.h, B, x.data_ptr(), None), fwd_flops),
+            ("train_step", lambda: plbm.lib().plbm_sur_train_step(net.h, B, x.data_ptr(), y.data_ptr(),
+                                                                  ctypes.c_float(1e-4), None), 3 * fwd_flops)):
+        for _ in range(args.warmup):
+            call()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(net.stream)
+        for _ in range(args.steps):
+            call()
+        e1.record(net.stream)
+        e1.synchronize()
+        t = e0.elapsed_time(e1) * 1e-3 / args.steps
+        out[name] = {"ms": t * 1e3, "tflops": B * flops / t / 1e12}
+    out["status"] = "ok" if net.check() == 0 else "timeout"
+    net.close()
+    return out
+
+
 def cpu_oracle_sample(L, seconds=12.0, max_steps=50):
     """Time the FP64 oracle as it stands on this host's cores on an L x L KH grid."""
     import oracle as O
@@ -424,6 +460,10 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--surrogate-train", type=int, default=2000, help="training trajectories")
     ap.add_argument("--surrogate-steps", type=int, default=6000, help="Adam steps")
+    ap.add_argument("--case", default="main", choices=["main", "surrogate", "batched"],
+                    help="main: the bench line; surrogate / batched: one of the secondary workloads "
+                         "alone (a JSON line of its own, for profiling)")
+    ap.add_argument("--batch", type=int, default=16, help="lattices per surrogate call (--case surrogate)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -473,6 +513,10 @@ def main():
         dist = td
     torch.cuda.set_device(local)
     build.build()
+    if args.case != "main":
+        if rank == 0:
+            print(json.dumps(run_case(torch, args)))
+        return 0
 
     def barrier():
         if dist is not None:
