@@ -68,9 +68,27 @@ class OrcLattice(ctypes.Structure):
     ]
 
 
+MAXQ1_3D = 5
+
+
+class OrcLattice3(ctypes.Structure):
+    _fields_ = [
+        ("q1", ctypes.c_int),
+        ("nx", ctypes.c_int),
+        ("ny", ctypes.c_int),
+        ("nz", ctypes.c_int),
+        ("isothermal", ctypes.c_int),
+        ("v", ctypes.c_int * MAXQ1_3D),
+        ("omega", ctypes.c_double),
+        ("theta0", ctypes.c_double),
+        ("C", ctypes.c_double * (MAXQ1_3D * MAXQ1_3D)),
+    ]
+
+
 _D = ctypes.POINTER(ctypes.c_double)
 _I = ctypes.POINTER(ctypes.c_int)
 _LP = ctypes.POINTER(OrcLattice)
+_LP3 = ctypes.POINTER(OrcLattice3)
 
 
 def _load(path: str):
@@ -93,6 +111,19 @@ def _load(path: str):
     L.orc_max_threads.restype = ctypes.c_int
     if L.orc_sizeof_lattice() != ctypes.sizeof(OrcLattice):
         raise RuntimeError("oracle lattice struct size mismatch")
+    if hasattr(L, "orc3_sizeof_lattice"):
+        L.orc3_sizeof_lattice.restype = ctypes.c_int
+        L.orc3_feq.argtypes = [ctypes.c_int, _D, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                               ctypes.c_double, ctypes.c_double, _D]
+        L.orc3_node_moments.argtypes = [_LP3, _D, _D]
+        L.orc3_collide_node.argtypes = [_LP3, _D, _D]
+        L.orc3_step.argtypes = [_LP3, _D, _D]
+        L.orc3_run.argtypes = [_LP3, _D, _D, ctypes.c_long]
+        L.orc3_init.argtypes = [_LP3, _D, _D, _D, _D, _D, _D]
+        L.orc3_moments.argtypes = [_LP3, _D, _D]
+        L.orc3_conserved.argtypes = [_LP3, _D, _D]
+        if L.orc3_sizeof_lattice() != ctypes.sizeof(OrcLattice3):
+            raise RuntimeError("oracle 3D lattice struct size mismatch")
     return L
 
 
@@ -311,6 +342,99 @@ class Lattice:
         lib().orc_node_moments(self.ref(), _dp(fin), ctypes.byref(r), ctypes.byref(a),
                                ctypes.byref(b), ctypes.byref(t))
         return r.value, a.value, b.value, t.value
+
+
+class Lattice3:
+    """A periodic three-dimensional lattice for the oracle (FP64), Sec. 2.1's
+    tensor product of three 1D rules.  Population p = (ix*q1 + iy)*q1 + iz;
+    arrays f[p][z][y][x]; fields [z][y][x]."""
+
+    def __init__(self, v, omega, nx, ny, nz, theta0=1.0, isothermal=False):
+        v = [int(a) for a in v]
+        if not 1 <= len(v) <= MAXQ1_3D:
+            raise ValueError("1 <= q1 <= 5 in 3D")
+        self.dim, self.v, self.q1 = 3, v, len(v)
+        self.q = self.q1 ** 3
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.omega, self.theta0 = float(omega), float(theta0)
+        self.isothermal = bool(isothermal)
+        self.C = vandermonde_inverse(v)
+        s = OrcLattice3()
+        s.q1, s.nx, s.ny, s.nz = self.q1, self.nx, self.ny, self.nz
+        s.isothermal = 1 if isothermal else 0
+        for i, a in enumerate(v):
+            s.v[i] = a
+        s.omega, s.theta0 = self.omega, self.theta0
+        for i, c in enumerate(self.C.ravel()):
+            s.C[i] = c
+        self.struct = s
+
+    @property
+    def shape(self):
+        return (self.q, self.nz, self.ny, self.nx)
+
+    def velocities(self) -> np.ndarray:
+        return np.array([(a, b, c) for a in self.v for b in self.v for c in self.v], dtype=np.int64)
+
+    def ref(self):
+        return ctypes.byref(self.struct)
+
+    def _field(self, a, default):
+        shp = (self.nz, self.ny, self.nx)
+        if a is None:
+            return np.full(shp, float(default))
+        return np.ascontiguousarray(np.broadcast_to(a, shp), dtype=np.float64)
+
+    def feq(self, rho, ux, uy, uz, theta) -> np.ndarray:
+        C = np.ascontiguousarray(self.C)
+        out = np.zeros(self.q)
+        lib().orc3_feq(self.q1, _dp(C), float(rho), float(ux), float(uy), float(uz), float(theta), _dp(out))
+        return out
+
+    def init(self, rho, ux=None, uy=None, uz=None, theta=None) -> np.ndarray:
+        f = np.zeros(self.shape)
+        lib().orc3_init(self.ref(), _dp(self._field(rho, 1.0)), _dp(self._field(ux, 0.0)),
+                        _dp(self._field(uy, 0.0)), _dp(self._field(uz, 0.0)),
+                        _dp(self._field(theta, self.theta0)), _dp(f))
+        return f
+
+    def step(self, f: np.ndarray) -> np.ndarray:
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        out = np.empty_like(f)
+        lib().orc3_step(self.ref(), _dp(f), _dp(out))
+        return out
+
+    def run(self, f: np.ndarray, nsteps: int) -> np.ndarray:
+        a = np.array(f, dtype=np.float64, order="C", copy=True)
+        b = np.empty_like(a)
+        lib().orc3_run(self.ref(), _dp(a), _dp(b), int(nsteps))
+        return a
+
+    def moments(self, f: np.ndarray):
+        """(rho, ux, uy, uz, theta), each [z][y][x]."""
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        out = np.zeros((5, self.nz, self.ny, self.nx))
+        lib().orc3_moments(self.ref(), _dp(f), _dp(out))
+        return tuple(out)
+
+    def conserved(self, f: np.ndarray) -> np.ndarray:
+        """(sum f, sum v_x f, sum v_y f, sum v_z f, sum |v|^2 f), compensated FP64."""
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        out = np.zeros(5)
+        lib().orc3_conserved(self.ref(), _dp(f), _dp(out))
+        return out
+
+    def collide_node(self, fin) -> np.ndarray:
+        fin = np.ascontiguousarray(fin, dtype=np.float64)
+        out = np.zeros(self.q)
+        lib().orc3_collide_node(self.ref(), _dp(fin), _dp(out))
+        return out
+
+    def node_moments(self, fin):
+        fin = np.ascontiguousarray(fin, dtype=np.float64)
+        m = np.zeros(5)
+        lib().orc3_node_moments(self.ref(), _dp(fin), _dp(m))
+        return tuple(m)
 
 
 def rel_err(a, b) -> float:

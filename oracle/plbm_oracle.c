@@ -327,3 +327,168 @@ void orc_conserved(const orc_lattice *L, const double *f, double *out)
     }
     for (int k = 0; k < 4; ++k) out[k] = s[k] + c[k];
 }
+
+/* ======================================================================
+ * Three dimensions (Sec. 2.1: the D3 models are the tensor product of three
+ * 1D rules with one scalar theta).  A separate description and separate
+ * functions keep the 1D/2D code above unchanged.
+ *
+ * Population index: p = (ix * q1 + iy) * q1 + iz, velocity (v[ix], v[iy], v[iz]).
+ * Array layout: f[p][z][y][x], x fastest, no padding.  Periodic in x, y and z.
+ * theta = (sum |v|^2 f / rho - |u|^2) / 3.
+ * ====================================================================== */
+#define ORC3_MAXQ1 5
+#define ORC3_MAXQ (ORC3_MAXQ1 * ORC3_MAXQ1 * ORC3_MAXQ1)
+
+typedef struct {
+    int q1;
+    int nx, ny, nz;
+    int isothermal;
+    int v[ORC3_MAXQ1];
+    double omega;
+    double theta0;
+    double C[ORC3_MAXQ1 * ORC3_MAXQ1];
+} orc_lattice3;
+
+int orc3_sizeof_lattice(void) { return (int)sizeof(orc_lattice3); }
+
+/* f^eq_{(ix,iy,iz)} = rho r_ix(u_x) r_iy(u_y) r_iz(u_z), one theta for the three factors. */
+void orc3_feq(int q1, const double *C, double rho, double ux, double uy, double uz,
+              double theta, double *feq)
+{
+    double ra[ORC3_MAXQ1], rb[ORC3_MAXQ1], rc[ORC3_MAXQ1];
+    orc_r1d(q1, C, ux, theta, ra);
+    orc_r1d(q1, C, uy, theta, rb);
+    orc_r1d(q1, C, uz, theta, rc);
+    for (int a = 0; a < q1; ++a)
+        for (int b = 0; b < q1; ++b)
+            for (int c = 0; c < q1; ++c) feq[(a * q1 + b) * q1 + c] = rho * ra[a] * rb[b] * rc[c];
+}
+
+/* rho = sum f; rho u = sum v f; 3 rho theta = sum |v|^2 f - rho |u|^2. */
+void orc3_node_moments(const orc_lattice3 *L, const double *f, double *m_out)
+{
+    const int q1 = L->q1;
+    double m0 = 0.0, mx = 0.0, my = 0.0, mz = 0.0, en = 0.0;
+    for (int a = 0; a < q1; ++a)
+        for (int b = 0; b < q1; ++b)
+            for (int c = 0; c < q1; ++c) {
+                const double fv = f[(a * q1 + b) * q1 + c];
+                const double cx = L->v[a], cy = L->v[b], cz = L->v[c];
+                m0 = m0 + fv;
+                mx = mx + cx * fv;
+                my = my + cy * fv;
+                mz = mz + cz * fv;
+                en = en + (cx * cx + cy * cy + cz * cz) * fv;
+            }
+    const double wx = mx / m0, wy = my / m0, wz = mz / m0;
+    m_out[0] = m0;
+    m_out[1] = wx;
+    m_out[2] = wy;
+    m_out[3] = wz;
+    m_out[4] = (en / m0 - (wx * wx + wy * wy + wz * wz)) / 3.0;
+}
+
+/* BGK collision of one node: fo = (1 - omega) fi + omega f^eq(moments of fi). */
+void orc3_collide_node(const orc_lattice3 *L, const double *fi, double *fo)
+{
+    const int q = L->q1 * L->q1 * L->q1;
+    double m[5], fe[ORC3_MAXQ];
+    orc3_node_moments(L, fi, m);
+    const double th = L->isothermal ? L->theta0 : m[4];
+    orc3_feq(L->q1, L->C, m[0], m[1], m[2], m[3], th, fe);
+    for (int p = 0; p < q; ++p) fo[p] = (1.0 - L->omega) * fi[p] + L->omega * fe[p];
+}
+
+static int orc3_wrap(int i, int n) { return ((i % n) + n) % n; }
+
+/* One step: pull f_p(x - v_p) with periodic wrap in x, y, z, then collide. */
+void orc3_step(const orc_lattice3 *L, const double *fsrc, double *fdst)
+{
+    const int nx = L->nx, ny = L->ny, nz = L->nz, q1 = L->q1;
+    const long vol = (long)nx * ny * nz;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) collapse(2)
+#endif
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y) {
+            double fi[ORC3_MAXQ], fo[ORC3_MAXQ];
+            for (int x = 0; x < nx; ++x) {
+                for (int a = 0; a < q1; ++a)
+                    for (int b = 0; b < q1; ++b)
+                        for (int c = 0; c < q1; ++c) {
+                            const int p = (a * q1 + b) * q1 + c;
+                            const int px = orc3_wrap(x - L->v[a], nx);
+                            const int py = orc3_wrap(y - L->v[b], ny);
+                            const int pz = orc3_wrap(z - L->v[c], nz);
+                            fi[p] = fsrc[p * vol + ((long)pz * ny + py) * nx + px];
+                        }
+                orc3_collide_node(L, fi, fo);
+                const int q = q1 * q1 * q1;
+                for (int p = 0; p < q; ++p) fdst[p * vol + ((long)z * ny + y) * nx + x] = fo[p];
+            }
+        }
+}
+
+void orc3_run(const orc_lattice3 *L, double *a, double *b, long nsteps)
+{
+    const long total = (long)L->q1 * L->q1 * L->q1 * L->nx * L->ny * L->nz;
+    double *src = a, *dst = b;
+    for (long s = 0; s < nsteps; ++s) {
+        orc3_step(L, src, dst);
+        double *t = src;
+        src = dst;
+        dst = t;
+    }
+    if (src != a) memcpy(a, src, sizeof(double) * (size_t)total);
+}
+
+/* f = f^eq(rho, u, theta) at every node; fields are [z][y][x]. */
+void orc3_init(const orc_lattice3 *L, const double *rho, const double *ux, const double *uy,
+               const double *uz, const double *theta, double *f)
+{
+    const int q = L->q1 * L->q1 * L->q1;
+    const long vol = (long)L->nx * L->ny * L->nz;
+    for (long n = 0; n < vol; ++n) {
+        double fe[ORC3_MAXQ];
+        const double th = L->isothermal ? L->theta0 : theta[n];
+        orc3_feq(L->q1, L->C, rho[n], ux[n], uy[n], uz[n], th, fe);
+        for (int p = 0; p < q; ++p) f[p * vol + n] = fe[p];
+    }
+}
+
+/* Fields of every node: out[k * vol + n], k = rho, u_x, u_y, u_z, theta. */
+void orc3_moments(const orc_lattice3 *L, const double *f, double *out)
+{
+    const int q = L->q1 * L->q1 * L->q1;
+    const long vol = (long)L->nx * L->ny * L->nz;
+    for (long n = 0; n < vol; ++n) {
+        double fn[ORC3_MAXQ], m[5];
+        for (int p = 0; p < q; ++p) fn[p] = f[p * vol + n];
+        orc3_node_moments(L, fn, m);
+        for (int k = 0; k < 5; ++k) out[k * vol + n] = m[k];
+    }
+}
+
+/* Global sums (compensated): mass, momentum x, y, z, energy sum |v|^2 f. */
+void orc3_conserved(const orc_lattice3 *L, const double *f, double *out)
+{
+    const int q1 = L->q1;
+    const long vol = (long)L->nx * L->ny * L->nz;
+    double s[5] = {0, 0, 0, 0, 0}, c[5] = {0, 0, 0, 0, 0};
+    for (int a = 0; a < q1; ++a)
+        for (int b = 0; b < q1; ++b)
+            for (int k = 0; k < q1; ++k) {
+                const int p = (a * q1 + b) * q1 + k;
+                const double cx = L->v[a], cy = L->v[b], cz = L->v[k];
+                for (long n = 0; n < vol; ++n) {
+                    const double fv = f[p * vol + n];
+                    neu_add(&s[0], &c[0], fv);
+                    neu_add(&s[1], &c[1], cx * fv);
+                    neu_add(&s[2], &c[2], cy * fv);
+                    neu_add(&s[3], &c[3], cz * fv);
+                    neu_add(&s[4], &c[4], (cx * cx + cy * cy + cz * cz) * fv);
+                }
+            }
+    for (int k = 0; k < 5; ++k) out[k] = s[k] + c[k];
+}
