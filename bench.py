@@ -169,6 +169,23 @@ def run_variant(torch, L, prec, steps, warmup, barrier, dim=2, v=V5, bc="periodi
             "status": "ok" if st == 0 else "diverged"}
 
 
+def run_variant3(torch, n, prec, steps, warmup):
+    """D3Q125 {0,+-1,+-3}^3 double shear layer on an n^3 periodic grid."""
+    from paper_1402_5487_gb300 import plbm
+    s = plbm.Solver(3, V5, OMEGA, n, n, nz=n, theta0=THETA0, prec=prec)
+    rho, ux, uy, uz, th = I.kh3_fields(n, n, n)
+    s.init(rho, ux, uy, th, uz=uz)
+    t = time_device(s, steps, warmup, torch, lambda: None)
+    st = s.check()
+    s.close()
+    nodes = n ** 3
+    gbs = 2 * 125 * ELEM[prec] * nodes * steps / t / 1e9
+    peak, _ = read_peaks()
+    return {"grid": [n, n, n], "mlups": nodes * steps / t / 1e6, "ms_per_step": t / steps * 1e3,
+            "gbs_algorithmic": gbs, "frac_of_measured_hbm": gbs / peak,
+            "status": "ok" if st == 0 else "diverged"}
+
+
 def run_batched(torch, steps=100, warmup=4, n=256):
     """Batched sweep of n admissible instances (FP32): persistent graph vs per-instance launches."""
     from paper_1402_5487_gb300 import batch as B
@@ -568,6 +585,9 @@ def main():
             variants["kh%d_%s" % (L, prec)] = run_variant(torch, L, prec, 200, 10, lambda: None)
         variants["kh512_f32"] = run_variant(torch, 512, "f32", 1000, 50, lambda: None)
         variants["kh512_f64"] = run_variant(torch, 512, "f64", 200, 20, lambda: None)
+        for prec in ("f32", "f16dev", "bf16dev"):
+            variants["kh3d256_d3q125_%s" % prec] = run_variant3(torch, 256, prec, 40, 4)
+        variants["kh3d64_d3q125_f64"] = run_variant3(torch, 64, "f64", 20, 3)
         left, right = (1.1, 0.0, 0.5), (1.0, 0.0, 0.5)
         variants["shock1000_d1q5_f64"] = run_variant(
             torch, 1000, "f64", 500, 20, lambda: None, dim=1, bc="fixed",

@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define PLBM_ABI_VERSION 1
+#define PLBM_ABI_VERSION 2
 #define PLBM_MAX_Q1 8
 
 typedef struct plbm_s *plbm_handle;
@@ -73,8 +73,9 @@ typedef enum { PLBM_PERIODIC = 0, PLBM_FIXED_ENDS = 1 } plbm_bc;
 #define PLBM_FLAG_SKIP_ADMISSIBILITY 0x2u /* do not run the positivity gate at create */
 
 typedef struct {
-    int dim;                   /* 1 or 2 */
-    int q1;                    /* velocities per axis: 3, 4 or 5 (D1Q3..D1Q5, D2Q9..D2Q25) */
+    int dim;                   /* 1, 2 or 3 */
+    int q1;                    /* velocities per axis: 3, 4 or 5 (D1Q3..D1Q5, D2Q9..D2Q25,
+                                  D3Q27..D3Q125) */
     const int *v;              /* q1 distinct integer velocities (copied at create) */
     double omega;              /* BGK relaxation constant, 0 < omega < 2 */
     double theta0;             /* reference temperature (rest state, isothermal models) */
@@ -94,6 +95,10 @@ typedef struct {
                                   NULL = the handle allocates its own */
     size_t workspace_bytes;
     int device;                /* CUDA device ordinal */
+    int nz;                    /* nodes along z when dim == 3 (Sec. 2.1's tensor product
+                                  in three dimensions: periodic only; 16/32-bit storage
+                                  needs a thermal set v = (0, a, -a, b, -b), FP64 takes
+                                  any); ignored for dim 1 and 2 */
 } plbm_desc;
 
 /* Global diagnostics of the stored state, all accumulated in FP64. */
@@ -190,11 +195,24 @@ plbm_status plbm_moments(plbm_handle h, double *rho, double *ux, double *uy, dou
 plbm_status plbm_diagnostics(plbm_handle h, plbm_diag *out);
 
 /* Conserved sums out[4] = (mass, jx, jy, energy) of the stored state, FP64.
- * Synchronous. */
+ * Synchronous.  (3D handles: plbm_conserved3.) */
 plbm_status plbm_conserved(plbm_handle h, double out[4]);
 
-/* Populations as FP64 [q][ny][nx] (for F16DEV/BF16DEV: w0 + g).  on_device as
- * in plbm_moments. */
+/* Three-dimensional handles (dim == 3, Sec. 2.1: f^eq = rho r^x r^y r^z with one
+ * theta; theta = (sum |v|^2 f / rho - |u|^2) / 3).  Fields are FP64
+ * [nz][ny][nx]; populations [q][nz][ny][nx] with q = q1^3 and p = (a q1 + b) q1 + c
+ * for the velocity (v[a], v[b], v[c]).  plbm_init, plbm_moments and
+ * plbm_conserved return PLBM_E_ARG for 3D handles; these take their place.
+ * on_device as in plbm_init / plbm_moments. */
+plbm_status plbm_init3(plbm_handle h, const double *rho, const double *ux, const double *uy, const double *uz,
+                       const double *theta, int on_device);
+plbm_status plbm_moments3(plbm_handle h, double *rho, double *ux, double *uy, double *uz, double *theta,
+                          int on_device);
+/* out[5] = (mass, jx, jy, jz, energy) of the stored state, FP64.  Synchronous. */
+plbm_status plbm_conserved3(plbm_handle h, double out[5]);
+
+/* Populations as FP64 [q][ny][nx] ([q][nz][ny][nx] in 3D; for F16DEV/BF16DEV:
+ * w0 + g).  on_device as in plbm_moments. */
 plbm_status plbm_get_populations(plbm_handle h, double *f, int on_device);
 
 /* Replace the stored state with FP64 populations [q][ny][nx], rounded to the

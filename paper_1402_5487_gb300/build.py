@@ -26,6 +26,7 @@ SOURCES = [
     "plbm_step_f64.cu",
     "plbm_step_f32.cu",
     "plbm_step_f16.cu",
+    "plbm_step3.cu",
     "plbm_step_bf16.cu",
     "plbm_noalloc.cu",
     "plbm_cnn.cu",

@@ -132,8 +132,9 @@ __global__ void k_moments(const __grid_constant__ LatticeParams P, const S* __re
 // Moments of the stored state packed for the surrogate: F[n] = (rho, u_x, u_y,
 // theta) in FP32 and the network input x[n] = bf16((F - mean_in) * istd_in).
 // FP32 arithmetic on the deviations g = f - w0 (the network's input is bf16 and
-// its fields FP32): rho = rho0 + sum g, j = sum v g, E = E0 + sum |v|^2 g, with
-// the row and column sums of g factorising the velocity weights.
+// its fields FP32): rho = 1 + sum g, j = sum v g, E = 2 theta0 + sum |v|^2 g
+// (the rest sums the 1D rule reproduces), with the row and column sums of g
+// factorising the velocity weights.
 template <typename S>
 __device__ __forceinline__ float dev_f32(const S* f, long long i, double w0) {
     return Storage<S>::load(f + i);
@@ -167,24 +168,21 @@ __global__ void k_moments_pack(const __grid_constant__ LatticeParams P, const S*
             ty[j] += g;
         }
     }
-    float w = 0.0f, wv = 0.0f, wv2 = 0.0f, dr = 0.0f, jx = 0.0f, jy = 0.0f, de = 0.0f;
+    // rest sums: sum w0 = 1, sum v w0 = 0, sum |v|^2 w0 = 2 theta0
+    float dr = 0.0f, jx = 0.0f, jy = 0.0f, de = 0.0f;
 #pragma unroll
     for (int i = 0; i < kQ1; ++i) {
         if (i >= q1) break;
         const float v = (float)P.v[i];
-        w += P.w1f[i];
-        wv += v * P.w1f[i];
-        wv2 += v * v * P.w1f[i];
         dr += sx[i];
         jx += v * sx[i];
         jy += v * ty[i];
         de += v * v * (sx[i] + ty[i]);
     }
-    const float rho = w * w + dr;
-    const float en = 2.0f * wv2 * w + de;
+    const float rho = 1.0f + dr;
     const float ir = 1.0f / rho;
-    const float ux = (jx + wv * w) * ir, uy = (jy + wv * w) * ir;
-    const float th = 0.5f * (en * ir - (ux * ux + uy * uy));
+    const float ux = jx * ir, uy = jy * ir;
+    const float th = P.theta0f + 0.5f * ((de - 2.0f * P.theta0f * dr) * ir - (ux * ux + uy * uy));
     const long long n = (long long)y * P.nx + xx;
     const float4 v = make_float4(rho, ux, uy, th);
     F[n] = v;

@@ -121,7 +121,7 @@ bool finite_pos(double a) { return std::isfinite(a) && a > 0.0; }
 
 plbm_status validate(const plbm_desc* d, Handle* h) {
     if (!d) { set_err(h, "descriptor is NULL"); return PLBM_E_ARG; }
-    if (d->dim != 1 && d->dim != 2) { set_err(h, "dim must be 1 or 2 (got %d)", d->dim); return PLBM_E_ARG; }
+    if (d->dim < 1 || d->dim > 3) { set_err(h, "dim must be 1, 2 or 3 (got %d)", d->dim); return PLBM_E_ARG; }
     if (d->q1 < 3 || d->q1 > 5) {
         set_err(h, "q1 must be 3, 4 or 5 (got %d)", d->q1);
         return PLBM_E_ARG;
@@ -140,7 +140,19 @@ plbm_status validate(const plbm_desc* d, Handle* h) {
     if (d->nx < 1 || d->ny < 1) { set_err(h, "nx, ny must be >= 1"); return PLBM_E_ARG; }
     if (d->dim == 1 && d->ny != 1) { set_err(h, "ny must be 1 in 1D"); return PLBM_E_ARG; }
     if (d->ny > 65535) { set_err(h, "ny must be <= 65535"); return PLBM_E_ARG; }
-    if ((long long)d->nx * d->ny > (1LL << 31)) { set_err(h, "grid too large"); return PLBM_E_ARG; }
+    const long long nz = d->dim == 3 ? d->nz : 1;
+    if (d->dim == 3) {
+        if (d->nz < 1 || d->nz > 65535) { set_err(h, "nz must lie in [1, 65535] in 3D"); return PLBM_E_ARG; }
+        if (d->bc != PLBM_PERIODIC) { set_err(h, "3D lattices are periodic"); return PLBM_E_ARG; }
+        const int* v = d->v;
+        const bool sym5 = d->q1 == 5 && v && v[0] == 0 && v[1] > 0 && v[2] == -v[1] && v[3] > 0 && v[4] == -v[3] &&
+                          v[1] != v[3];
+        if (d->prec != PLBM_F64 && (!sym5 || (d->flags & PLBM_FLAG_ISOTHERMAL))) {
+            set_err(h, "3D with 16/32-bit storage needs a thermal set v = (0, a, -a, b, -b)");
+            return PLBM_E_ARG;
+        }
+    }
+    if ((long long)d->nx * d->ny * nz > (1LL << 31)) { set_err(h, "grid too large"); return PLBM_E_ARG; }
     if (elem_size(d->prec) == 0) { set_err(h, "unknown precision %d", (int)d->prec); return PLBM_E_ARG; }
     if (d->bc != PLBM_PERIODIC && d->bc != PLBM_FIXED_ENDS) { set_err(h, "unknown boundary"); return PLBM_E_ARG; }
     if (d->bc == PLBM_FIXED_ENDS) {
@@ -170,9 +182,10 @@ struct Layout {
 Layout layout_of(const plbm_desc* d) {
     Layout L{};
     L.pitch = (int)align_up((size_t)d->nx, plbm::kPitchAlign);
-    const int q = d->dim == 1 ? d->q1 : d->q1 * d->q1;
-    L.pop_bytes = align_up((size_t)q * d->ny * L.pitch * elem_size(d->prec), 256);
-    L.nblocks = ((d->nx + plbm::kBlockX - 1) / plbm::kBlockX) * d->ny;
+    const int q = d->dim == 1 ? d->q1 : (d->dim == 2 ? d->q1 * d->q1 : d->q1 * d->q1 * d->q1);
+    const size_t rows = (size_t)d->ny * (d->dim == 3 ? d->nz : 1);
+    L.pop_bytes = align_up((size_t)q * rows * L.pitch * elem_size(d->prec), 256);
+    L.nblocks = (int)(((d->nx + plbm::kBlockX - 1) / plbm::kBlockX) * rows);
     L.partial_off = 2 * L.pop_bytes;
     L.result_off = L.partial_off + align_up((size_t)L.nblocks * plbm::kPartialStride * sizeof(double), 256);
     L.status_off = L.result_off + 256;
@@ -292,6 +305,10 @@ plbm_status plbm_linear_stability(const plbm_desc* desc, double ux, int nk, doub
     }
     plbm_status st = validate(desc, nullptr);
     if (st != PLBM_OK) return st;
+    if (desc->dim == 3) {
+        set_err(nullptr, "the linear stability scan covers 1D and 2D lattices");
+        return PLBM_E_ARG;
+    }
     double C[plbm::kMaxQ1 * plbm::kMaxQ1];
     if (!lagrange_coefficients(desc->q1, desc->v, C)) {
         set_err(nullptr, "velocities must be distinct");
@@ -330,7 +347,8 @@ plbm_status plbm_create(const plbm_desc* desc, plbm_handle* out) {
     P.ny = desc->ny;
     P.dim = dim;
     P.q1 = q1;
-    P.q = dim == 1 ? q1 : q1 * q1;
+    P.q = dim == 1 ? q1 : (dim == 2 ? q1 * q1 : q1 * q1 * q1);
+    P.nz = dim == 3 ? desc->nz : 1;
     P.fixed_ends = desc->bc == PLBM_FIXED_ENDS;
     P.isothermal = (desc->flags & PLBM_FLAG_ISOTHERMAL) ? 1 : 0;
     P.omega = desc->omega;
@@ -341,6 +359,7 @@ plbm_status plbm_create(const plbm_desc* desc, plbm_handle* out) {
         P.v[i] = desc->v[i];
         P.vxm[i] = ((-desc->v[i]) % P.nx + P.nx) % P.nx;
         P.vym[i] = ((-desc->v[i]) % P.ny + P.ny) % P.ny;
+        P.vzm[i] = ((-desc->v[i]) % P.nz + P.nz) % P.nz;
     }
     if (!lagrange_coefficients(q1, desc->v, P.C)) {
         set_err(nullptr, "velocities must be distinct");
@@ -390,8 +409,10 @@ plbm_status plbm_create(const plbm_desc* desc, plbm_handle* out) {
         P.w1f[i] = (float)P.w1[i];
         P.mu0f[i] = (float)mu0[i];
     }
-    feq_host(dim, q1, P.C, 1.0, 0.0, 0.0, desc->theta0, P.W0);
-    for (int p = 0; p < P.q; ++p) P.W0f[p] = (float)P.W0[p];
+    if (dim <= 2) {  // 3D kernels form w0 from the 1D weights (q1^3 exceeds the table)
+        feq_host(dim, q1, P.C, 1.0, 0.0, 0.0, desc->theta0, P.W0);
+        for (int p = 0; p < P.q; ++p) P.W0f[p] = (float)P.W0[p];
+    }
     if (P.fixed_ends) {
         const double* L = desc->left_state;
         const double* R = desc->right_state;
@@ -413,7 +434,7 @@ plbm_status plbm_create(const plbm_desc* desc, plbm_handle* out) {
     }
     const Layout L = layout_of(desc);
     P.pitch = L.pitch;
-    P.plane = (long long)L.pitch * desc->ny;
+    P.plane = (long long)L.pitch * desc->ny * P.nz;
     h->pop_bytes = L.pop_bytes;
     h->ws_bytes = L.total;
     if (cudaSetDevice(desc->device) != cudaSuccess) {
@@ -477,6 +498,7 @@ plbm_status plbm_init(plbm_handle hh, const double* rho, const double* ux, const
     Handle* h = reinterpret_cast<Handle*>(hh);
     plbm_status st = usable(h, false);
     if (st != PLBM_OK) return st;
+    if (h->P.dim == 3) { set_err(h, "3D handle: use plbm_init3"); return PLBM_E_ARG; }
     if (!rho || !ux || (h->P.dim == 2 && !uy) || (!theta && !h->P.isothermal)) {
         set_err(h, "missing field array");
         return PLBM_E_ARG;
@@ -534,7 +556,10 @@ plbm_status plbm_step(plbm_handle hh, long n) {
     if (n < 0) { set_err(h, "n must be >= 0"); return PLBM_E_ARG; }
     const int ce = h->desc.check_every;
     for (long s = 0; s < n; ++s) {
-        CK(plbm::launch_step(h->prec, h->P, h->f[h->cur], h->f[h->cur ^ 1], false, h->stream));
+        if (h->P.dim == 3)
+            CK(plbm::launch_step3(h->prec, h->P, h->f[h->cur], h->f[h->cur ^ 1], h->stream));
+        else
+            CK(plbm::launch_step(h->prec, h->P, h->f[h->cur], h->f[h->cur ^ 1], false, h->stream));
         h->cur ^= 1;
         ++h->steps;
         if (ce > 0 && ((s + 1) % ce == 0) && s + 1 < n) {
@@ -552,6 +577,7 @@ plbm_status plbm_moments(plbm_handle hh, double* rho, double* ux, double* uy, do
     plbm_status st = usable(h);
     if (st != PLBM_OK && st != PLBM_E_DIVERGED) return st;
     if (st == PLBM_E_DIVERGED) { set_err(h, "handle diverged"); return st; }
+    if (h->P.dim == 3) { set_err(h, "3D handle: use plbm_moments3"); return PLBM_E_ARG; }
     const size_t n = (size_t)h->P.nx * h->P.ny;
     if (on_device) {
         CK(plbm::launch_moments(h->prec, h->P, h->f[h->cur], rho, ux, uy, theta, h->stream));
@@ -576,8 +602,11 @@ plbm_status plbm_diagnostics(plbm_handle hh, plbm_diag* out) {
     if (!h->initialised) { set_err(h, "populations not initialised"); return PLBM_E_STATE; }
     if (h->sticky == PLBM_E_CUDA) { set_err(h, "handle in CUDA error state"); return PLBM_E_CUDA; }
     CK(cudaSetDevice(h->desc.device));
-    CK(plbm::launch_reduce_state(h->prec, h->P, h->f[h->cur], h->result, h->stream));
-    CK(cudaMemcpyAsync(h->host_buf, h->result, 6 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (h->P.dim == 3)
+        CK(plbm::launch_reduce3(h->prec, h->P, h->f[h->cur], h->result, h->stream));
+    else
+        CK(plbm::launch_reduce_state(h->prec, h->P, h->f[h->cur], h->result, h->stream));
+    CK(cudaMemcpyAsync(h->host_buf, h->result, 7 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaMemcpyAsync(h->host_buf + 8, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     out->mass = h->host_buf[0];
@@ -592,6 +621,8 @@ plbm_status plbm_diagnostics(plbm_handle hh, plbm_diag* out) {
 }
 
 plbm_status plbm_conserved(plbm_handle hh, double out[4]) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (h && h->P.dim == 3) { set_err(h, "3D handle: use plbm_conserved3"); return PLBM_E_ARG; }
     plbm_diag d;
     plbm_status st = plbm_diagnostics(hh, &d);
     if (st != PLBM_OK) return st;
@@ -602,21 +633,98 @@ plbm_status plbm_conserved(plbm_handle hh, double out[4]) {
     return PLBM_OK;
 }
 
+plbm_status plbm_init3(plbm_handle hh, const double* rho, const double* ux, const double* uy, const double* uz,
+                       const double* theta, int on_device) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    plbm_status st = usable(h, false);
+    if (st != PLBM_OK) return st;
+    if (h->P.dim != 3) { set_err(h, "plbm_init3 takes 3D handles"); return PLBM_E_ARG; }
+    if (!rho || !ux || !uy || !uz || (!theta && !h->P.isothermal)) {
+        set_err(h, "missing field array");
+        return PLBM_E_ARG;
+    }
+    const size_t n = (size_t)h->P.nx * h->P.ny * h->P.nz;
+    const double* d[5] = {rho, ux, uy, uz, theta};
+    Staging stg;
+    stg.s = h->stream;
+    if (!on_device) {
+        CK(cudaMallocAsync(&stg.p, 5 * n * sizeof(double), h->stream));
+        double* base = static_cast<double*>(stg.p);
+        for (int k = 0; k < 5; ++k) {
+            if (!d[k]) continue;
+            CK(cudaMemcpyAsync(base + k * n, d[k], n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+            d[k] = base + k * n;
+        }
+    }
+    h->cur = 0;
+    CK(plbm::launch_init3(h->prec, h->P, d[0], d[1], d[2], d[3], d[4], h->f[0], h->stream));
+    CK(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
+    if (!on_device) CK(cudaStreamSynchronize(h->stream));
+    h->steps = 0;
+    h->initialised = true;
+    return PLBM_OK;
+}
+
+plbm_status plbm_moments3(plbm_handle hh, double* rho, double* ux, double* uy, double* uz, double* theta,
+                          int on_device) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    plbm_status st = usable(h);
+    if (st != PLBM_OK && st != PLBM_E_DIVERGED) return st;
+    if (st == PLBM_E_DIVERGED) { set_err(h, "handle diverged"); return st; }
+    if (h->P.dim != 3) { set_err(h, "plbm_moments3 takes 3D handles"); return PLBM_E_ARG; }
+    const size_t n = (size_t)h->P.nx * h->P.ny * h->P.nz;
+    if (on_device) {
+        CK(plbm::launch_moments3(h->prec, h->P, h->f[h->cur], rho, ux, uy, uz, theta, h->stream));
+        return PLBM_OK;
+    }
+    Staging stg;
+    stg.s = h->stream;
+    CK(cudaMallocAsync(&stg.p, 5 * n * sizeof(double), h->stream));
+    double* b = static_cast<double*>(stg.p);
+    double* outs[5] = {rho, ux, uy, uz, theta};
+    CK(plbm::launch_moments3(h->prec, h->P, h->f[h->cur], rho ? b : nullptr, ux ? b + n : nullptr,
+                             uy ? b + 2 * n : nullptr, uz ? b + 3 * n : nullptr, theta ? b + 4 * n : nullptr,
+                             h->stream));
+    for (int k = 0; k < 5; ++k)
+        if (outs[k]) CK(cudaMemcpyAsync(outs[k], b + k * n, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return PLBM_OK;
+}
+
+plbm_status plbm_conserved3(plbm_handle hh, double out[5]) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !out) { set_err(h, "bad arguments"); return PLBM_E_ARG; }
+    if (h->P.dim != 3) { set_err(h, "plbm_conserved3 takes 3D handles"); return PLBM_E_ARG; }
+    plbm_diag d;
+    plbm_status st = plbm_diagnostics(hh, &d);
+    if (st != PLBM_OK) return st;
+    out[0] = d.mass;
+    out[1] = d.jx;
+    out[2] = d.jy;
+    out[3] = h->host_buf[6];  // j_z, the seventh entry of the 3D reduction
+    out[4] = d.energy;
+    return PLBM_OK;
+}
+
 plbm_status plbm_get_populations(plbm_handle hh, double* f, int on_device) {
     Handle* h = reinterpret_cast<Handle*>(hh);
     if (!h || !f) { set_err(h, "bad arguments"); return PLBM_E_ARG; }
     if (!h->initialised) { set_err(h, "populations not initialised"); return PLBM_E_STATE; }
     if (h->sticky == PLBM_E_CUDA) { set_err(h, "handle in CUDA error state"); return PLBM_E_CUDA; }
     CK(cudaSetDevice(h->desc.device));
-    const size_t n = (size_t)h->P.q * h->P.nx * h->P.ny;
+    const size_t n = (size_t)h->P.q * h->P.nx * h->P.ny * h->P.nz;
+    auto get = [&](double* dst) {
+        return h->P.dim == 3 ? plbm::launch_get_pop3(h->prec, h->P, h->f[h->cur], dst, h->stream)
+                             : plbm::launch_get_populations(h->prec, h->P, h->f[h->cur], dst, h->stream);
+    };
     if (on_device) {
-        CK(plbm::launch_get_populations(h->prec, h->P, h->f[h->cur], f, h->stream));
+        CK(get(f));
         return PLBM_OK;
     }
     Staging stg;
     stg.s = h->stream;
     CK(cudaMallocAsync(&stg.p, n * sizeof(double), h->stream));
-    CK(plbm::launch_get_populations(h->prec, h->P, h->f[h->cur], static_cast<double*>(stg.p), h->stream));
+    CK(get(static_cast<double*>(stg.p)));
     CK(cudaMemcpyAsync(f, stg.p, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return PLBM_OK;
@@ -627,7 +735,7 @@ plbm_status plbm_set_populations(plbm_handle hh, const double* f, int on_device,
     plbm_status st = usable(h, false);
     if (st != PLBM_OK) return st;
     if (!f) { set_err(h, "populations pointer is NULL"); return PLBM_E_ARG; }
-    const size_t n = (size_t)h->P.q * h->P.nx * h->P.ny;
+    const size_t n = (size_t)h->P.q * h->P.nx * h->P.ny * h->P.nz;
     const double* src = f;
     Staging stg;
     stg.s = h->stream;
@@ -637,7 +745,10 @@ plbm_status plbm_set_populations(plbm_handle hh, const double* f, int on_device,
         src = static_cast<const double*>(stg.p);
     }
     h->cur = 0;
-    CK(plbm::launch_set_populations(h->prec, h->P, src, h->f[0], h->stream));
+    if (h->P.dim == 3)
+        CK(plbm::launch_set_pop3(h->prec, h->P, src, h->f[0], h->stream));
+    else
+        CK(plbm::launch_set_populations(h->prec, h->P, src, h->f[0], h->stream));
     CK(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
     if (!on_device) CK(cudaStreamSynchronize(h->stream));
     h->steps = step;

@@ -32,6 +32,8 @@ struct LatticeParams {
     int v[kMaxQ1];          // integer velocities
     int vxm[kMaxQ1];        // (-v) mod nx, in [0, nx): source column = x + vxm (- nx)
     int vym[kMaxQ1];        // (-v) mod ny, in [0, ny)
+    int nz;                 // 3D: nodes along z (1 otherwise); rows of elem_index are z * ny + y
+    int vzm[kMaxQ1];        // (-v) mod nz, in [0, nz)
     double omega, theta0;
     float omegaf, theta0f;
     double C[kMaxQ1 * kMaxQ1];   // C[i*q1 + n] multiplies mu_n in r_i (Eq. eq:rdr)
@@ -170,6 +172,16 @@ cudaError_t launch_init(int prec, const LatticeParams& P, const double* rho, con
                         const double* uy, const double* theta, void* f, cudaStream_t stream);
 cudaError_t launch_moments(int prec, const LatticeParams& P, const void* f, double* rho,
                            double* ux, double* uy, double* theta, cudaStream_t stream);
+// Three-dimensional lattices (plbm_step3.cu): storage [q][nz][ny][pitch].
+long long reduce3_blocks(const LatticeParams& P);
+cudaError_t launch_step3(int prec, const LatticeParams& P, const void* src, void* dst, cudaStream_t s);
+cudaError_t launch_init3(int prec, const LatticeParams& P, const double* rho, const double* ux, const double* uy,
+                         const double* uz, const double* theta, void* f, cudaStream_t s);
+cudaError_t launch_moments3(int prec, const LatticeParams& P, const void* f, double* rho, double* ux, double* uy,
+                            double* uz, double* theta, cudaStream_t s);
+cudaError_t launch_reduce3(int prec, const LatticeParams& P, const void* f, double* out, cudaStream_t s);
+cudaError_t launch_get_pop3(int prec, const LatticeParams& P, const void* f, double* out, cudaStream_t s);
+cudaError_t launch_set_pop3(int prec, const LatticeParams& P, const double* in, void* f, cudaStream_t s);
 cudaError_t launch_moments_pack(int prec, const LatticeParams& P, const void* f, float* F, void* x,
                                 const float* mean_in, const float* std_in, cudaStream_t stream);
 // Per-block partial sums of the stored state, then one deterministic final pass

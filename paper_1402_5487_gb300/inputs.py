@@ -48,6 +48,22 @@ def kh_fields(L: int, theta0: float = 1.0, seed: int = 0, u0: float = 0.1,
     return rho, np.ascontiguousarray(ux), np.ascontiguousarray(uy), theta
 
 
+def kh3_fields(nx: int, ny: int, nz: int, u0: float = 0.1, theta0: float = 1.0, seed: int = 0):
+    """Three-dimensional double shear layer (the 2D KH workload extended along y),
+    fields [nz][ny][nx] in the order (rho, u_x, u_y, u_z, theta):
+    u_x = u0 tanh((|z - nz/2| - nz/4) / delta), delta = nz / 16,
+    u_z = 0.005 sin(2 pi x / nx), uniform noise in [-1e-4, 1e-4] on u_x then u_z
+    (numpy default_rng(seed), C order), rho = 1, theta = theta0, u_y = 0."""
+    rng = np.random.default_rng(seed)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    ux = u0 * np.tanh((np.abs(z - nz / 2) - nz / 4) / (nz / 16))
+    uz = 0.005 * np.sin(2 * np.pi * x / nx)
+    ux = ux + rng.uniform(-1e-4, 1e-4, ux.shape)
+    uz = uz + rng.uniform(-1e-4, 1e-4, uz.shape)
+    one = np.ones_like(ux)
+    return tuple(np.ascontiguousarray(a) for a in (one, ux, 0.0 * one, uz, theta0 * one))
+
+
 def shear_wave_fields(L: int, theta0: float, amp: float = 1e-3, ny: int | None = None,
                       ux0: float = 0.0):
     """u_x = ux0 + amp sin(2 pi y / ny), rho = 1, u_y = 0, theta = theta0."""

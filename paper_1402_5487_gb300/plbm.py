@@ -58,6 +58,7 @@ class PlbmDesc(ctypes.Structure):
         ("workspace", ctypes.c_void_p),
         ("workspace_bytes", ctypes.c_size_t),
         ("device", ctypes.c_int),
+        ("nz", ctypes.c_int),
     ]
 
 
@@ -108,6 +109,11 @@ SIGNATURES = {
                                     ctypes.c_void_p, ctypes.c_int]),
     "plbm_diagnostics": (ctypes.c_int, [_H, ctypes.POINTER(PlbmDiag)]),
     "plbm_conserved": (ctypes.c_int, [_H, _D]),
+    "plbm_init3": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_void_p, ctypes.c_int]),
+    "plbm_moments3": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_int]),
+    "plbm_conserved3": (ctypes.c_int, [_H, _D]),
     "plbm_get_populations": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int]),
     "plbm_set_populations": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64]),
     "plbm_get_info": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -185,7 +191,7 @@ def coefficients(v) -> np.ndarray:
 
 def make_desc(dim, v, omega, nx, ny=1, theta0=1.0, prec="f32", bc="periodic", left_state=None,
               right_state=None, isothermal=False, check_every=0, u_max=0.0, stream=None,
-              device=0, skip_admissibility=False):
+              device=0, skip_admissibility=False, nz=1):
     """Build a PlbmDesc; the returned tuple keeps the ctypes buffers alive."""
     q1 = len(v)
     va = (ctypes.c_int * q1)(*[int(a) for a in v])
@@ -207,6 +213,7 @@ def make_desc(dim, v, omega, nx, ny=1, theta0=1.0, prec="f32", bc="periodic", le
     d.check_every = int(check_every)
     d.u_max = float(u_max)
     d.device = int(device)
+    d.nz = int(nz) if int(dim) == 3 else 1
     return d, keep
 
 
@@ -250,7 +257,7 @@ class Solver:
 
     def __init__(self, dim, v, omega, nx, ny=1, theta0=1.0, prec="f32", bc="periodic",
                  left_state=None, right_state=None, isothermal=False, check_every=0, u_max=0.0,
-                 device=0, stream=None, skip_admissibility=False, torch_workspace=True):
+                 device=0, stream=None, skip_admissibility=False, torch_workspace=True, nz=1):
         import torch  # device memory and streams only
 
         self.torch = torch
@@ -258,11 +265,12 @@ class Solver:
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.dim, self.v, self.q1 = dim, tuple(int(a) for a in v), len(v)
         self.q = self.q1 ** dim
-        self.nx, self.ny = int(nx), (int(ny) if dim == 2 else 1)
+        self.nx, self.ny = int(nx), (int(ny) if dim >= 2 else 1)
+        self.nz = int(nz) if dim == 3 else 1
         self.prec = prec
         desc, self._keep = make_desc(dim, v, omega, nx, self.ny, theta0, prec, bc, left_state,
                                      right_state, isothermal, check_every, u_max,
-                                     self.stream.cuda_stream, device, skip_admissibility)
+                                     self.stream.cuda_stream, device, skip_admissibility, self.nz)
         self._ws = None
         if torch_workspace:
             nbytes = workspace_bytes(desc)
@@ -314,10 +322,10 @@ class Solver:
                 continue
             if isinstance(a, np.ndarray):
                 a = np.ascontiguousarray(a, dtype=np.float64)
-                assert a.size == self.nx * self.ny
+                assert a.size == self.nx * self.ny * self.nz
                 dev = 0
             else:
-                assert a.dtype == self.torch.float64 and a.is_contiguous() and a.numel() == self.nx * self.ny
+                assert a.dtype == self.torch.float64 and a.is_contiguous() and a.numel() == self.nx * self.ny * self.nz
                 dev = 1
             if on_dev is None:
                 on_dev = dev
@@ -327,7 +335,12 @@ class Solver:
             ptrs.append(_ptr(a))
         return ptrs, on_dev or 0, keep
 
-    def init(self, rho, ux, uy=None, theta=None):
+    def init(self, rho, ux, uy=None, theta=None, uz=None):
+        """Equilibrium initial state; 3D handles take uz as well (fields [nz][ny][nx])."""
+        if self.dim == 3:
+            ptrs, on_dev, keep = self._field_args([rho, ux, uy, uz, theta])
+            _ok(lib().plbm_init3(self.h, *ptrs, on_dev), self.h)
+            return
         ptrs, on_dev, keep = self._field_args([rho, ux, uy, theta])
         _ok(lib().plbm_init(self.h, *ptrs, on_dev), self.h)
 
@@ -342,13 +355,16 @@ class Solver:
         return int(lib().plbm_check(self.h))
 
     def moments(self, on_device: bool = False):
-        """(rho, ux, uy, theta) as FP64 [ny][nx] NumPy arrays (or torch CUDA tensors)."""
-        shp = (self.ny, self.nx)
+        """(rho, ux, uy, theta) as FP64 [ny][nx] NumPy arrays (or torch CUDA tensors);
+        3D handles: (rho, ux, uy, uz, theta), each [nz][ny][nx]."""
+        shp = (self.ny, self.nx) if self.dim < 3 else (self.nz, self.ny, self.nx)
+        k = 5 if self.dim == 3 else 4
         if on_device:
-            outs = [self.torch.empty(shp, dtype=self.torch.float64, device=self.device) for _ in range(4)]
+            outs = [self.torch.empty(shp, dtype=self.torch.float64, device=self.device) for _ in range(k)]
         else:
-            outs = [np.empty(shp) for _ in range(4)]
-        _ok(lib().plbm_moments(self.h, *[_ptr(o) for o in outs], 1 if on_device else 0), self.h)
+            outs = [np.empty(shp) for _ in range(k)]
+        call = lib().plbm_moments3 if self.dim == 3 else lib().plbm_moments
+        _ok(call(self.h, *[_ptr(o) for o in outs], 1 if on_device else 0), self.h)
         return tuple(outs)
 
     def diagnostics(self) -> dict:
@@ -357,12 +373,17 @@ class Solver:
         return {k: getattr(d, k) for k, _ in PlbmDiag._fields_}
 
     def conserved(self) -> np.ndarray:
-        out = np.zeros(4)
-        _ok(lib().plbm_conserved(self.h, out.ctypes.data_as(_D)), self.h)
+        """(mass, jx, jy, energy); 3D handles: (mass, jx, jy, jz, energy)."""
+        out = np.zeros(5 if self.dim == 3 else 4)
+        call = lib().plbm_conserved3 if self.dim == 3 else lib().plbm_conserved
+        _ok(call(self.h, out.ctypes.data_as(_D)), self.h)
         return out
 
+    def _pop_shape(self):
+        return (self.q, self.ny, self.nx) if self.dim < 3 else (self.q, self.nz, self.ny, self.nx)
+
     def get_populations(self, on_device: bool = False):
-        shp = (self.q, self.ny, self.nx)
+        shp = self._pop_shape()
         out = (self.torch.empty(shp, dtype=self.torch.float64, device=self.device) if on_device
                else np.empty(shp))
         _ok(lib().plbm_get_populations(self.h, _ptr(out), 1 if on_device else 0), self.h)
@@ -374,7 +395,7 @@ class Solver:
             on = 0
         else:
             on = 1
-        assert tuple(f.shape) == (self.q, self.ny, self.nx)
+        assert tuple(f.shape) == self._pop_shape()
         _ok(lib().plbm_set_populations(self.h, _ptr(f), on, int(step)), self.h)
 
     def info(self):
@@ -391,7 +412,7 @@ class Solver:
         s.stream = stream
         s.dim, s.v, s.q1 = dim, tuple(int(a) for a in v), len(v)
         s.q = s.q1 ** dim
-        s.nx, s.ny, s.prec = nx, ny, prec
+        s.nx, s.ny, s.nz, s.prec = nx, ny, 1, prec
         s._borrowed = True
         return s
 

@@ -43,7 +43,7 @@ def test_every_declared_symbol_is_exported(L):
 
 
 def test_abi_version(L):
-    assert L.plbm_abi_version() == 1
+    assert L.plbm_abi_version() == 2
 
 
 @pytest.mark.parametrize("v", [(0, 1, -1, 3, -3), (0, 1, -1, 2, -2), (0, 2, -4), (1, -1, 3, -3),
@@ -66,7 +66,7 @@ def _create(desc):
 
 
 @pytest.mark.parametrize("field,value", [("omega", 2.0), ("omega", -0.1), ("omega", float("nan")),
-                                         ("theta0", 0.0), ("nx", 0), ("dim", 3), ("q1", 6),
+                                         ("theta0", 0.0), ("nx", 0), ("dim", 4), ("q1", 6),
                                          ("prec", 7), ("bc", 5), ("check_every", -1)])
 def test_descriptor_validation(L, field, value):
     desc, keep = plbm.make_desc(2, (0, 1, -1, 3, -3), 1.3, 16, 16)
@@ -75,6 +75,29 @@ def test_descriptor_validation(L, field, value):
     assert st == plbm.PLBM_E_ARG and not h.value
     assert plbm.last_error(None)
     assert plbm.workspace_bytes(desc) == 0
+
+
+@pytest.mark.parametrize("kw", [dict(v=(0, 1, -1, 3, -3), bc="fixed", left_state=(1, 0, 1), right_state=(1, 0, 1)),
+                                dict(v=(0, 1, -1, 2, -3)),            # not a symmetric pair set
+                                dict(v=(0, 1, -1)),                   # q1 = 3 needs FP64 in 3D
+                                dict(v=(0, 1, -1, 3, -3), isothermal=True),
+                                dict(v=(0, 1, -1, 3, -3), nz=0)],
+                         ids=["fixed-ends", "asymmetric", "q1-3", "isothermal", "nz-0"])
+def test_3d_descriptor_validation(L, kw):
+    kw = dict(kw)
+    v = kw.pop("v")
+    nz = kw.pop("nz", 8)
+    desc, keep = plbm.make_desc(3, v, 1.3, 16, 8, prec="f32", nz=nz, skip_admissibility=True, **kw)
+    st, h = _create(desc)
+    assert st == plbm.PLBM_E_ARG and not h.value, plbm.last_error(None)
+
+
+def test_3d_workspace_counts_q1_cubed(L):
+    desc, keep = plbm.make_desc(3, (0, 1, -1, 3, -3), 1.3, 64, 8, prec="f32", nz=4)
+    # two population arrays of 125 x 4 x 8 rows x 64 floats, plus scratch
+    assert plbm.workspace_bytes(desc) >= 2 * 125 * 4 * 8 * 64 * 4
+    desc, keep = plbm.make_desc(3, (0, 1, -1), 1.2, 64, 8, prec="f64", nz=4, isothermal=True, theta0=1 / 3)
+    assert plbm.workspace_bytes(desc) >= 2 * 27 * 4 * 8 * 64 * 8
 
 
 def test_repeated_velocity_rejected(L):

@@ -1,0 +1,146 @@
+"""GPU parity of three-dimensional lattices (D3Q125, D3Q27) against the 3D oracle.
+
+The CUDA path runs through the C ABI (plbm_init3 / plbm_step / plbm_moments3 /
+plbm_get_populations / plbm_conserved3) on the same seeded host fields as the
+FP64 oracle (oracle.Lattice3).  Grids are ragged (nx not a multiple of the
+128-thread block, odd ny and nz) and span several blocks.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+V5 = (0, 1, -1, 3, -3)
+TOL64 = 1e-12
+
+
+def fields3(nx, ny, nz, seed, amp_u=0.03, amp_r=0.01, theta0=1.0):
+    """Smooth periodic seeded fields [nz][ny][nx]."""
+    rng = np.random.default_rng(seed)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+
+    def wave():
+        kx, ky, kz = rng.integers(1, 3, 3)
+        ph = rng.uniform(0, 2 * np.pi)
+        return np.cos(2 * np.pi * (kx * x / nx + ky * y / ny + kz * z / nz) + ph)
+
+    rho = 1.0 + amp_r * wave()
+    ux, uy, uz = (amp_u * wave() for _ in range(3))
+    th = theta0 * (1.0 + amp_r * wave())
+    return tuple(np.ascontiguousarray(a) for a in (rho, ux, uy, uz, th))
+
+
+def run_pair(v, omega, shape, steps, prec, theta0=1.0, isothermal=False, seed=3, amp_u=0.03):
+    from paper_1402_5487_gb300 import plbm
+    nx, ny, nz = shape
+    f = fields3(nx, ny, nz, seed, amp_u=amp_u, theta0=theta0)
+    lat = O.Lattice3(v, omega, nx, ny, nz, theta0=theta0, isothermal=isothermal)
+    fo = lat.run(lat.init(*f), steps)
+    s = plbm.Solver(3, v, omega, nx, ny, nz=nz, theta0=theta0, prec=prec, isothermal=isothermal)
+    s.init(f[0], f[1], f[2], None if isothermal else f[4], uz=f[3])
+    s.step(steps)
+    out = s.moments(), s.get_populations(), s.conserved()
+    s.close()
+    return lat, fo, out, f
+
+
+@pytest.mark.parametrize("shape", [(130, 7, 5), (16, 9, 11)])
+def test_d3q125_f64_matches_oracle(shape):
+    lat, fo, (mg, fg, cg), _ = run_pair(V5, 1.3, shape, 30, "f64")
+    assert O.rel_err(fg, fo) <= TOL64
+    mo = lat.moments(fo)
+    for a, b in zip(mg, mo):
+        assert np.max(np.abs(a - b)) <= TOL64 * max(np.max(np.abs(b)), 0.03)
+    assert np.max(np.abs(cg - lat.conserved(fo)) / np.maximum(1.0, np.abs(lat.conserved(fo)))) <= TOL64
+
+
+def test_d3q27_isothermal_f64_matches_oracle():
+    lat, fo, (mg, fg, cg), _ = run_pair((0, 1, -1), 1.2, (20, 6, 7), 40, "f64", theta0=1.0 / 3.0,
+                                        isothermal=True)
+    assert O.rel_err(fg, fo) <= TOL64
+
+
+@pytest.mark.parametrize("prec,tol", [("f32", 2e-6), ("f16dev", 2e-3), ("bf16dev", 2e-2)])
+def test_d3q125_reduced_storage_matches_oracle(prec, tol):
+    lat, fo, (mg, fg, cg), f = run_pair(V5, 1.3, (130, 7, 5), 30, prec)
+    mo = lat.moments(fo)
+    u0 = np.max(np.sqrt(f[1] ** 2 + f[2] ** 2 + f[3] ** 2))
+    du = np.sqrt((mg[1] - mo[1]) ** 2 + (mg[2] - mo[2]) ** 2 + (mg[3] - mo[3]) ** 2)
+    assert np.max(du) <= tol * u0
+    assert O.rel_err(mg[0], mo[0]) <= tol * 0.1 and O.rel_err(mg[4], mo[4]) <= tol * 0.1
+    assert np.max(np.abs(fg - fo)) <= tol * 0.1 * np.max(np.abs(fo))
+
+
+def kh3(nx, ny, nz):
+    from paper_1402_5487_gb300 import inputs as I
+    return I.kh3_fields(nx, ny, nz)
+
+
+def _f32_run_1000(fields, shape):
+    from paper_1402_5487_gb300 import plbm
+    nx, ny, nz = shape
+    rho, ux, uy, uz, th = fields
+    lat = O.Lattice3(V5, 1.3, nx, ny, nz)
+    mo = lat.moments(lat.run(lat.init(rho, ux, uy, uz, th), 1000))
+    s = plbm.Solver(3, V5, 1.3, nx, ny, nz=nz, prec="f32")
+    s.init(rho, ux, uy, th, uz=uz)
+    s.step(1000)
+    mg = s.moments()
+    s.close()
+    den = np.max(np.sqrt(mo[1] ** 2 + mo[2] ** 2 + mo[3] ** 2))
+    du = np.sqrt((mg[1] - mo[1]) ** 2 + (mg[2] - mo[2]) ** 2 + (mg[3] - mo[3]) ** 2)
+    return np.max(du) / den, O.rel_err(mg[0], mo[0]), O.rel_err(mg[4], mo[4]), den
+
+
+def test_d3q125_f32_1000_steps_shear_layer_within_1e5():
+    # The FP32 bar of the parity contract (relative error <= 1e-5 after 1000
+    # steps) on the 3D double shear layer.  The box is long across the layers
+    # (nz = 256, so nu k^2 t ~ 0.16 and the flow persists for 1000 steps) and
+    # short in x and y to keep the oracle fast.
+    eu, er, et, den = _f32_run_1000(kh3(8, 4, 256), (8, 4, 256))
+    assert den > 0.05
+    assert eu <= 1e-5 and er <= 1e-5 and et <= 1e-5, (eu, er, et)
+
+
+def test_d3q125_f32_1000_steps_uniform_flow_bound():
+    # Worst case for FP32 storage: a uniform flow (which viscosity cannot damp)
+    # carrying small perturbations; every node holds nearly the same values, so
+    # the rounding of the stored deviations is the same everywhere and the mean
+    # velocity drifts by ~1e-9 per step.  A regression bound, not the contract.
+    rho, ux, uy, uz, th = fields3(32, 16, 12, 21, amp_u=0.02)
+    eu, er, et, den = _f32_run_1000((rho, ux + 0.04, uy - 0.03, uz + 0.02, th), (32, 16, 12))
+    assert den > 0.04
+    assert eu <= 5e-5 and er <= 1e-5 and et <= 1e-5, (eu, er, et)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_d3q125_pure_streaming_is_exact(prec):
+    from paper_1402_5487_gb300 import plbm
+    nx, ny, nz = 131, 6, 5
+    lat = O.Lattice3(V5, 0.0, nx, ny, nz)
+    f0 = lat.init(*fields3(nx, ny, nz, 9))
+    s = plbm.Solver(3, V5, 0.0, nx, ny, nz=nz, prec=prec, skip_admissibility=True)
+    s.set_populations(f0)
+    start = s.get_populations()        # the stored (rounded) state
+    s.step(1)
+    g = s.get_populations()
+    s.close()
+    for p, (cx, cy, cz) in enumerate(lat.velocities()):
+        expect = np.roll(np.roll(np.roll(start[p], cz, axis=0), cy, axis=1), cx, axis=2)
+        assert np.array_equal(g[p], expect), p
+
+
+def test_d3q125_conserves_to_rounding():
+    from paper_1402_5487_gb300 import plbm
+    nx, ny, nz = 40, 12, 9
+    f = fields3(nx, ny, nz, 4)
+    s = plbm.Solver(3, V5, 1.3, nx, ny, nz=nz, prec="f32")
+    s.init(f[0], f[1], f[2], f[4], uz=f[3])
+    c0 = s.conserved()
+    s.step(200)
+    c1 = s.conserved()
+    s.close()
+    scale = np.array([c0[0], c0[0], c0[0], c0[0], c0[4]])
+    assert np.max(np.abs(c1 - c0) / scale) < 2e-6
