@@ -375,11 +375,14 @@ def run_surrogate(torch, n_train=2000, n_test=100, train_steps=2000, batch=16, K
 
 def run_case(torch, args):
     """One secondary workload alone: the surrogate network on a batch of 256 x 256
-    lattices (forward passes and Adam steps on seeded random tensors), or the
-    batched 256-instance sweep."""
+    lattices (forward passes and Adam steps on seeded random tensors), the
+    batched 256-instance sweep, or the D3Q125 shear layer on a size^3 grid."""
     if args.case == "batched":
         return {"case": "batched", **run_batched(torch, steps=args.steps, warmup=args.warmup,
                                                  n=args.batch_instances)}
+    if args.case == "d3q125":
+        return {"case": "d3q125", "prec": args.prec,
+                **run_variant3(torch, args.size, args.prec, args.steps, args.warmup)}
     import ctypes
     from paper_1402_5487_gb300 import plbm, surrogate as SG
     B, L = args.batch, 256
@@ -477,7 +480,7 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--surrogate-train", type=int, default=2000, help="training trajectories")
     ap.add_argument("--surrogate-steps", type=int, default=6000, help="Adam steps")
-    ap.add_argument("--case", default="main", choices=["main", "surrogate", "batched"],
+    ap.add_argument("--case", default="main", choices=["main", "surrogate", "batched", "d3q125"],
                     help="main: the bench line; surrogate / batched: one of the secondary workloads "
                          "alone (a JSON line of its own, for profiling)")
     ap.add_argument("--batch", type=int, default=16, help="lattices per surrogate call (--case surrogate)")
