@@ -17,6 +17,7 @@ Workloads (lattice units, dx = dt = 1):
 """
 from __future__ import annotations
 
+import math
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -46,6 +47,26 @@ def kh_fields(L: int, theta0: float = 1.0, seed: int = 0, u0: float = 0.1,
     rho = np.ones((ny, nx))
     theta = np.full((ny, nx), float(theta0))
     return rho, np.ascontiguousarray(ux), np.ascontiguousarray(uy), theta
+
+
+def paper_kh_fields(L: int = 128, a: float = 1.6, u0: float = 0.069, l0: float = 80.0, eps: float = 0.05):
+    """The paper's shear-layer initial condition (Sec. 4, 25-velocity model) in
+    lattice units.  The paper's set {0, +-a, +-2a} sqrt(theta0) in units where the
+    temperature is 1 is the lattice set {0, +-1, +-2} with theta0 = 1 / a^2, and
+    its velocities scale by sqrt(theta0).  Domain [0, 1)^2 on L x L nodes, node
+    (i, j) at (x, y) = (i / L, j / L):
+    u_x = u0 tanh(l0 (y - 1/4)) for y <= 1/2, u0 tanh(l0 (3/4 - y)) otherwise;
+    u_y = u0 eps sin(2 pi (x + 1/4)); rho = 1, theta = theta0.
+    Returns ((rho, ux, uy, theta) [L][L], theta0)."""
+    theta0 = 1.0 / (a * a)
+    s = math.sqrt(theta0)
+    x = np.arange(L) / L
+    y = np.arange(L) / L
+    prof = np.where(y <= 0.5, np.tanh(l0 * (y - 0.25)), np.tanh(l0 * (0.75 - y)))
+    ux = np.broadcast_to((u0 * s * prof)[:, None], (L, L))
+    uy = np.broadcast_to((u0 * eps * s * np.sin(2 * np.pi * (x + 0.25)))[None, :], (L, L))
+    one = np.ones((L, L))
+    return tuple(np.ascontiguousarray(f) for f in (one, ux, uy, theta0 * one)), theta0
 
 
 def kh3_fields(nx: int, ny: int, nz: int, u0: float = 0.1, theta0: float = 1.0, seed: int = 0):

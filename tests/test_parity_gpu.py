@@ -309,3 +309,141 @@ def test_stable_kh_stays_healthy():
     assert abs(rho - 1).max() < 0.01 and abs(th - 1).max() < 0.01
     assert np.hypot(ux, uy).max() < 0.12
     s.close()
+
+
+# --------------------------------------------------------------------------
+# The paper's own parameters (Sec. 4): {0, +-1, +-2} = {0, +-a, +-2a} sqrt(theta0),
+# theta0 = 1 / a^2, omega = 1.9.
+# --------------------------------------------------------------------------
+SET_012 = (0, 1, -1, 2, -2)
+
+
+def _exact_rounded_coefficients(v):
+    """V^{-1} in exact rational arithmetic, each entry rounded once to FP64."""
+    from fractions import Fraction
+    q = len(v)
+    A = [[Fraction(vk) ** n for vk in v] + [Fraction(int(n == k)) for k in range(q)] for n in range(q)]
+    for c in range(q):
+        p = next(r for r in range(c, q) if A[r][c] != 0)
+        A[c], A[p] = A[p], A[c]
+        d = A[c][c]
+        A[c] = [x / d for x in A[c]]
+        for r in range(q):
+            if r != c and A[r][c] != 0:
+                m = A[r][c]
+                A[r] = [a_ - m * b_ for a_, b_ in zip(A[r], A[c])]
+    return np.array([[float(A[i][q + n]) for n in range(q)] for i in range(q)])
+
+
+def test_paper_shear_layer_f64_within_the_coefficient_rounding_sensitivity():
+    # At omega = 1.9 the BGK step hardly damps the momentum error that a one-ulp
+    # difference in the c_ij injects every step, so two correct FP64
+    # implementations whose coefficients differ in the last bit drift apart
+    # linearly (the library builds c_ij by Lagrange expansion, the oracle by
+    # Gauss-Jordan elimination).  The bound is the oracle's own drift against a
+    # copy of itself with correctly rounded coefficients (at most one ulp away).
+    fields, theta0 = I.paper_kh_fields()
+    steps = 1000
+    lat = O.Lattice(2, SET_012, 1.9, 128, 128, theta0=theta0)
+    alt = O.Lattice(2, SET_012, 1.9, 128, 128, theta0=theta0)
+    cex = _exact_rounded_coefficients(SET_012)
+    assert np.max(np.abs(cex - lat.C) / np.spacing(np.abs(cex) + 1e-300)) <= 1.0
+    for i, c in enumerate(cex.ravel()):
+        alt.struct.C[i] = c
+    m0 = lat.moments(lat.run(lat.init(*fields), steps))
+    m1 = alt.moments(alt.run(alt.init(*fields), steps))
+    (mg, _, _) = gpu_run(2, SET_012, 1.9, 128, 128, fields, steps, prec="f64", theta0=theta0)
+    sens = field_errors(m1, m0)
+    errs = field_errors(mg, m0)
+    assert errs["rho"] <= TOL64 and errs["theta"] <= TOL64, errs
+    assert errs["u"] <= max(TOL64, 2.0 * sens["u"]), (errs, sens)
+
+
+@pytest.mark.parametrize("steps,tol", [(100, TOL32), (1000, 1e-4)])
+def test_paper_shear_layer_f32_matches_oracle(steps, tol):
+    # The FP32 bar (1e-5) at 100 steps.  With the paper's slow flow (u0 = 0.043)
+    # and omega = 1.9, which hardly damps the momentum error of the FP32 storage
+    # rounding (a few 1e-9 per population per step), the relative u error walks to
+    # 1.05e-5 at 200 steps and 4.4e-5 at 1000 steps (a regression bound there).
+    fields, theta0 = I.paper_kh_fields()
+    (mg, fg, _) = gpu_run(2, SET_012, 1.9, 128, 128, fields, steps, prec="f32", theta0=theta0)
+    _, fo, mo = oracle_run(2, SET_012, 1.9, 128, 128, fields, steps, theta0=theta0)
+    errs = field_errors(mg, mo)
+    assert max(errs.values()) <= tol, errs
+
+
+def test_paper_shear_layer_stays_stable_to_the_last_printed_step_in_f64():
+    # The paper shows the 25-velocity shear layer up to step 3695 at omega = 1.9.
+    from paper_1402_5487_gb300 import plbm
+    fields, theta0 = I.paper_kh_fields()
+    s = plbm.Solver(2, SET_012, 1.9, 128, 128, theta0=theta0, prec="f64")
+    s.init(*fields)
+    s.step(3695)
+    assert s.check() == plbm.PLBM_OK
+    rho, ux, uy, th = s.moments()
+    s.close()
+    assert 0.995 < rho.min() and rho.max() < 1.005
+    assert 0.995 < th.min() / theta0 and th.max() / theta0 < 1.005
+    assert np.max(np.hypot(ux, uy)) < 0.06
+
+
+def test_paper_shear_layer_in_f32_follows_f64_then_diverges_and_is_reported():
+    # FP32 rounding (~1e-7) seeds the mode that the oracle shows growing from a
+    # 1e-7 perturbation of the FP64 initial state (tests/test_oracle_paper_params.py):
+    # the FP32 run follows FP64 for 1500 steps, then departs and the status word
+    # reports the divergence before the paper's last printed step.
+    from paper_1402_5487_gb300 import plbm
+    fields, theta0 = I.paper_kh_fields()
+    a = plbm.Solver(2, SET_012, 1.9, 128, 128, theta0=theta0, prec="f32")
+    b = plbm.Solver(2, SET_012, 1.9, 128, 128, theta0=theta0, prec="f64")
+    for s in (a, b):
+        s.init(*fields)
+        s.step(1500)
+    ea = field_errors(a.moments(), b.moments())
+    assert max(ea.values()) < 1e-3, ea
+    statuses = []
+    for _ in range(9):                       # up to step 3750
+        a.step(250)
+        statuses.append(a.check())
+        if statuses[-1] != plbm.PLBM_OK:
+            break
+    a.close()
+    b.close()
+    assert statuses[-1] == plbm.PLBM_E_DIVERGED, statuses
+
+
+def test_paper_d1q5_shock_tube_f64_within_the_coefficient_rounding_sensitivity():
+    # Same bound as the shear layer: at omega = 1.9 the one-ulp differences of the
+    # c_ij between the library and the oracle drift the slow post-shock flow apart.
+    theta = 1 / 1.96
+    left, right = (1.1, 0.0, theta), (1.0, 0.0, theta)
+    fields = I.shock_tube_fields(1000, left, right)
+    mk = lambda: O.Lattice(1, SET_012, 1.9, 1000, bc="fixed", theta0=theta, left_state=left, right_state=right)
+    lat, alt = mk(), mk()
+    for i, c in enumerate(_exact_rounded_coefficients(SET_012).ravel()):
+        alt.struct.C[i] = c
+    m0 = lat.moments(lat.run(lat.init(*fields), 346))
+    m1 = alt.moments(alt.run(alt.init(*fields), 346))
+    (mg, _, _) = gpu_run(1, SET_012, 1.9, 1000, 1, fields, 346, prec="f64", theta0=theta, bc="fixed",
+                         left=left, right=right)
+    sens = field_errors(m1, m0)
+    errs = field_errors(mg, m0)
+    assert errs["rho"] <= TOL64 and errs["theta"] <= TOL64, errs
+    assert errs["u"] <= max(TOL64, 2.0 * sens["u"]), (errs, sens)
+
+
+def test_paper_d1q5_shock_tube_f32_matches_oracle():
+    # A regression bound: at omega = 1.9 the shock leaves acoustic oscillations of
+    # a third of the post-shock velocity that the collision barely damps, and the
+    # FP32 rounding of the stored populations walks the slow flow (u ~ 0.02) away
+    # from FP64 by ~2.5e-5 in u after 346 steps (the 1e-5 bar holds for the
+    # omega = 1.5 shock tube, test_parity_d1q5_shock_tube).
+    theta = 1 / 1.96
+    left, right = (1.1, 0.0, theta), (1.0, 0.0, theta)
+    fields = I.shock_tube_fields(1000, left, right)
+    (mg, fg, _) = gpu_run(1, SET_012, 1.9, 1000, 1, fields, 346, prec="f32", theta0=theta, bc="fixed",
+                          left=left, right=right)
+    _, fo, mo = oracle_run(1, SET_012, 1.9, 1000, 1, fields, 346, theta0=theta, bc="fixed", left=left,
+                           right=right)
+    errs = field_errors(mg, mo)
+    assert errs["u"] <= 5e-5 and errs["rho"] <= 5e-6 and errs["theta"] <= 5e-6, errs
