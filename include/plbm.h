@@ -74,8 +74,9 @@ typedef enum { PLBM_PERIODIC = 0, PLBM_FIXED_ENDS = 1 } plbm_bc;
 
 typedef struct {
     int dim;                   /* 1, 2 or 3 */
-    int q1;                    /* velocities per axis: 3, 4 or 5 (D1Q3..D1Q5, D2Q9..D2Q25,
-                                  D3Q27..D3Q125) */
+    int q1;                    /* velocities per axis: 3..8 in 1D and 2D (D1Q3..D1Q8,
+                                  D2Q9..D2Q64; n* = q1 - 1 moments reproduced), 3..5 in 3D
+                                  (D3Q27..D3Q125) */
     const int *v;              /* q1 distinct integer velocities (copied at create) */
     double omega;              /* BGK relaxation constant, 0 < omega < 2 */
     double theta0;             /* reference temperature (rest state, isothermal models) */

@@ -504,9 +504,15 @@ cudaError_t launch_step_t(const LatticeParams& P, const void* src, void* dst, bo
     PLBM_LAUNCH(3, 1)
     PLBM_LAUNCH(4, 1)
     PLBM_LAUNCH(5, 1)
+    PLBM_LAUNCH(6, 1)
+    PLBM_LAUNCH(7, 1)
+    PLBM_LAUNCH(8, 1)
     PLBM_LAUNCH(3, 2)
     PLBM_LAUNCH(4, 2)
     PLBM_LAUNCH(5, 2)
+    PLBM_LAUNCH(6, 2)
+    PLBM_LAUNCH(7, 2)
+    PLBM_LAUNCH(8, 2)
 #undef PLBM_LAUNCH
     return cudaErrorInvalidValue;
 }

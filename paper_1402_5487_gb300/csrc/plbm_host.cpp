@@ -122,8 +122,8 @@ bool finite_pos(double a) { return std::isfinite(a) && a > 0.0; }
 plbm_status validate(const plbm_desc* d, Handle* h) {
     if (!d) { set_err(h, "descriptor is NULL"); return PLBM_E_ARG; }
     if (d->dim < 1 || d->dim > 3) { set_err(h, "dim must be 1, 2 or 3 (got %d)", d->dim); return PLBM_E_ARG; }
-    if (d->q1 < 3 || d->q1 > 5) {
-        set_err(h, "q1 must be 3, 4 or 5 (got %d)", d->q1);
+    if (d->q1 < 3 || d->q1 > PLBM_MAX_Q1 || (d->dim == 3 && d->q1 > 5)) {
+        set_err(h, "q1 must lie in [3, %d] (3D: [3, 5]) (got %d)", PLBM_MAX_Q1, d->q1);
         return PLBM_E_ARG;
     }
     if (!d->v) { set_err(h, "velocity array is NULL"); return PLBM_E_ARG; }

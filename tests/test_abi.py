@@ -66,7 +66,7 @@ def _create(desc):
 
 
 @pytest.mark.parametrize("field,value", [("omega", 2.0), ("omega", -0.1), ("omega", float("nan")),
-                                         ("theta0", 0.0), ("nx", 0), ("dim", 4), ("q1", 6),
+                                         ("theta0", 0.0), ("nx", 0), ("dim", 4), ("q1", 9),
                                          ("prec", 7), ("bc", 5), ("check_every", -1)])
 def test_descriptor_validation(L, field, value):
     desc, keep = plbm.make_desc(2, (0, 1, -1, 3, -3), 1.3, 16, 16)
