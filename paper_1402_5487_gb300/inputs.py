@@ -49,7 +49,8 @@ def kh_fields(L: int, theta0: float = 1.0, seed: int = 0, u0: float = 0.1,
     return rho, np.ascontiguousarray(ux), np.ascontiguousarray(uy), theta
 
 
-def paper_kh_fields(L: int = 128, a: float = 1.6, u0: float = 0.069, l0: float = 80.0, eps: float = 0.05):
+def paper_kh_fields(L: int = 128, a: float = 1.6, u0: float = 0.069, l0: float = 80.0, eps: float = 0.05,
+                    theta0: float | None = None):
     """The paper's shear-layer initial condition (Sec. 4, 25-velocity model) in
     lattice units.  The paper's set {0, +-a, +-2a} sqrt(theta0) in units where the
     temperature is 1 is the lattice set {0, +-1, +-2} with theta0 = 1 / a^2, and
@@ -57,8 +58,10 @@ def paper_kh_fields(L: int = 128, a: float = 1.6, u0: float = 0.069, l0: float =
     (i, j) at (x, y) = (i / L, j / L):
     u_x = u0 tanh(l0 (y - 1/4)) for y <= 1/2, u0 tanh(l0 (3/4 - y)) otherwise;
     u_y = u0 eps sin(2 pi (x + 1/4)); rho = 1, theta = theta0.
+    theta0 (optional) replaces 1 / a^2: the three-velocity models of Sec. 4 use
+    {0, +-1} = {0, +-sqrt(zeta theta0)}, theta0 = 1 / zeta.
     Returns ((rho, ux, uy, theta) [L][L], theta0)."""
-    theta0 = 1.0 / (a * a)
+    theta0 = 1.0 / (a * a) if theta0 is None else float(theta0)
     s = math.sqrt(theta0)
     x = np.arange(L) / L
     y = np.arange(L) / L
@@ -67,6 +70,20 @@ def paper_kh_fields(L: int = 128, a: float = 1.6, u0: float = 0.069, l0: float =
     uy = np.broadcast_to((u0 * eps * s * np.sin(2 * np.pi * (x + 0.25)))[None, :], (L, L))
     one = np.ones((L, L))
     return tuple(np.ascontiguousarray(f) for f in (one, ux, uy, theta0 * one)), theta0
+
+
+def taylor_green_fields(N: int, U: float, theta0: float):
+    """Decaying Taylor-Green vortex on [0, 1)^2, node (i, j) at (i / N, j / N):
+    u_x = U sin(2 pi x) cos(2 pi y), u_y = -U cos(2 pi x) sin(2 pi y),
+    rho = 1 - U^2 / (4 theta0) (cos 4 pi x + cos 4 pi y) (the pressure of the
+    incompressible solution over rho theta0), theta = theta0; fields [N][N]."""
+    x = np.arange(N) / N
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    k = 2 * np.pi
+    ux = U * np.sin(k * X) * np.cos(k * Y)
+    uy = -U * np.cos(k * X) * np.sin(k * Y)
+    rho = 1 - (U * U / (4 * theta0)) * (np.cos(2 * k * X) + np.cos(2 * k * Y))
+    return tuple(np.ascontiguousarray(f) for f in (rho, ux, uy, theta0 * np.ones((N, N))))
 
 
 def kh3_fields(nx: int, ny: int, nz: int, u0: float = 0.1, theta0: float = 1.0, seed: int = 0):

@@ -9,6 +9,13 @@ with theta0 = 1 / a^2 (a = 1.6 and 1.4), omega = 1.9.
 * The shear layer at omega = 1.9 is stable in FP64 to the paper's last printed
   step (3695) but carries a mode that grows from a perturbation of relative size
   1e-7 (FP32 rounding level) and ruins the flow before step 3695.
+* The three-velocity shear layer (Sec. 4, D2Q9 tensor products): the LBGK model
+  (zeta = 3, omega = 1.99880) is ruined by grid-scale noise by its step 1500 and
+  diverges before 1800, while the parametric zeta = 4 model (omega = 1.99862)
+  is only slightly noisy at the equivalent step 1732 and still finite at 2078.
+* Second-order convergence (Sec. 4, Fig. "errors with respect to the 128 x 128
+  grids"): on a smooth decaying Taylor-Green vortex in diffusive scaling, the
+  velocity error against the finest grid falls as the square of the spacing.
 * The shock tube rho_L / rho_R = 1.1 at a = 1.4: the post-shock plateau values of
   u, rho and theta (the quantities the paper compares with the exact Riemann
   solution) agree with the exact gamma = 3 solution.
@@ -51,6 +58,76 @@ def test_paper_shear_layer_grows_a_seeded_mode():
         th_min[name] = float(lat.moments(f)[3].min() / theta0)
     assert th_min["plain"] > 0.995, th_min
     assert th_min["seeded"] < 0.95, th_min
+
+
+def _high_k_vorticity_fraction(ux, uy):
+    """Share of the vorticity energy at |k| > N/4 (grid-scale noise)."""
+    n = ux.shape[0]
+    w = (np.roll(uy, -1, 1) - np.roll(uy, 1, 1)) / 2 - (np.roll(ux, -1, 0) - np.roll(ux, 1, 0)) / 2
+    W = np.abs(np.fft.fft2(w)) ** 2
+    k = np.fft.fftfreq(n) * n
+    K = np.hypot(k[:, None], k[None, :])
+    return float(W[K > n / 4].sum() / W.sum())
+
+
+def run_zeta_shear_layer(zeta, marks):
+    theta0 = 1.0 / zeta
+    omega = {3: 1.99880, 4: 1.99862}[zeta]
+    fields, _ = I.paper_kh_fields(theta0=theta0)
+    lat = O.Lattice(2, (0, 1, -1), omega, 128, 128, theta0=theta0, isothermal=True)
+    f = lat.init(*fields)
+    out, t = {}, 0
+    for m in marks:
+        f = lat.run(f, m - t)
+        t = m
+        rho, ux, uy, _ = lat.moments(f)
+        ok = bool(np.all(np.isfinite(rho)) and rho.min() > 0)
+        out[m] = (ok, _high_k_vorticity_fraction(ux, uy) if ok else float("inf"))
+    return out
+
+
+@pytest.mark.slow
+def test_zeta4_shear_layer_outlasts_lbgk():
+    lbgk = run_zeta_shear_layer(3, (500, 1500, 1800))
+    z4 = run_zeta_shear_layer(4, (577, 1732, 2078))
+    assert lbgk[500][1] < 0.01 and z4[577][1] < 0.01          # both smooth early
+    assert lbgk[1500][0] and lbgk[1500][1] > 0.2              # LBGK "highly unstable" at 1500
+    assert not lbgk[1800][0]                                  # and gone by 1800
+    assert z4[1732][0] and z4[1732][1] < 0.5 * lbgk[1500][1]  # zeta = 4 "slightly unstable"
+    assert z4[2078][0]                                        # and still finite at 2078
+
+
+def taylor_green_errors(v, theta0, isothermal, omega, sizes=(16, 32, 64, 128), runner=None):
+    """RMS normalised velocity error against the finest grid (its nodes at the
+    coarse nodes) in diffusive scaling: u = 0.04 * 16 / N, 40 (N / 16)^2 steps."""
+    res = {}
+    for N in sizes:
+        U = 0.04 * 16 / N
+        steps = int(40 * (N / 16) ** 2)
+        fields = I.taylor_green_fields(N, U, theta0)
+        if runner is None:
+            lat = O.Lattice(2, v, omega, N, N, theta0=theta0, isothermal=isothermal)
+            m = lat.moments(lat.run(lat.init(*fields), steps))
+        else:
+            m = runner(v, theta0, isothermal, omega, N, fields, steps)
+        res[N] = (m[1] / U, m[2] / U)
+    fine = sizes[-1]
+    errs = []
+    for N in sizes[:-1]:
+        s = fine // N
+        ex, ey = res[fine][0][::s, ::s], res[fine][1][::s, ::s]
+        errs.append(float(np.sqrt(np.mean((res[N][0] - ex) ** 2 + (res[N][1] - ey) ** 2))))
+    return errs
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("v,theta0,iso,omega", [((0, 1, -1), 0.25, True, 1.2),
+                                                ((0, 1, -1, 3, -3), 1.0, False, 1.3)],
+                         ids=["zeta4", "d2q25"])
+def test_taylor_green_converges_at_second_order(v, theta0, iso, omega):
+    errs = taylor_green_errors(v, theta0, iso, omega)
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert all(o > 1.8 for o in orders), (errs, orders)
 
 
 def test_paper_d1q5_shock_tube_plateau_values():

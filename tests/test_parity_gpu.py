@@ -483,3 +483,43 @@ def test_paper_d1q5_shock_tube_f32_matches_oracle():
                            right=right)
     errs = field_errors(mg, mo)
     assert errs["u"] <= 5e-5 and errs["rho"] <= 5e-6 and errs["theta"] <= 5e-6, errs
+
+
+# --------------------------------------------------------------------------
+# The three-velocity models of Sec. 4 (isothermal, D2Q9 tensor products):
+# LBGK (zeta = 3) and the parametric zeta = 4 model on the paper's shear layer,
+# and second-order convergence on the GPU path.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("zeta", [3, 4])
+def test_zeta_shear_layer_matches_oracle_and_the_papers_stability_pattern(zeta):
+    from paper_1402_5487_gb300 import plbm
+    theta0 = 1.0 / zeta
+    omega = {3: 1.99880, 4: 1.99862}[zeta]
+    fields, _ = I.paper_kh_fields(theta0=theta0)
+    early, late = {3: (500, 1800), 4: (577, 2078)}[zeta]
+    (mg, fg, s) = gpu_run(2, (0, 1, -1), omega, 128, 128, fields, early, prec="f64", theta0=theta0,
+                          isothermal=True)
+    _, fo, mo = oracle_run(2, (0, 1, -1), omega, 128, 128, fields, early, theta0=theta0, isothermal=True)
+    assert max(field_errors(mg, mo).values()) <= TOL64
+    s.step(late - early)
+    status = s.check()
+    s.close()
+    # LBGK is gone before its step 1800; zeta = 4 is still running at 2078
+    assert status == (plbm.PLBM_E_DIVERGED if zeta == 3 else plbm.PLBM_OK), status
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("v,theta0,iso,omega", [((0, 1, -1), 0.25, True, 1.2),
+                                                ((0, 1, -1, 3, -3), 1.0, False, 1.3)],
+                         ids=["zeta4", "d2q25"])
+def test_taylor_green_converges_at_second_order_on_gpu(v, theta0, iso, omega, prec):
+    from test_oracle_paper_params import taylor_green_errors
+
+    def runner(v, theta0, iso, omega, N, fields, steps):
+        (m, _, s) = gpu_run(2, v, omega, N, N, fields, steps, prec=prec, theta0=theta0, isothermal=iso)
+        s.close()
+        return m
+
+    errs = taylor_green_errors(v, theta0, iso, omega, runner=runner)
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert all(o > 1.8 for o in orders), (errs, orders)
