@@ -112,6 +112,86 @@ __global__ void k_init(const __grid_constant__ LatticeParams P, const double* __
     for (int p = 0; p < P.q; ++p) f[elem_index(P, p, x, y)] = Storage<S>::from_f64(feq[p], P.W0[p]);
 }
 
+// Compile-time q1 versions of the two kernels above (arrays in registers, no
+// integer division per population); the same FP64 formulas, the moments from
+// the row and column sums S_i = sum_j f_ij, T_j = sum_i f_ij.
+template <typename S, int Q1, int DIM>
+__global__ void k_init_q(const __grid_constant__ LatticeParams P, const double* __restrict__ rho,
+                         const double* __restrict__ ux, const double* __restrict__ uy,
+                         const double* __restrict__ theta, S* __restrict__ f) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= P.nx) return;
+    const long long n = (long long)y * P.nx + x;
+    const double th = (P.isothermal || theta == nullptr) ? P.theta0 : theta[n];
+    double r[DIM][Q1];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        const double u = a == 0 ? ux[n] : (uy ? uy[n] : 0.0);
+        double mu[Q1];
+        mu[0] = 1.0;
+        if (Q1 > 1) mu[1] = u;
+#pragma unroll
+        for (int k = 1; k + 1 < Q1; ++k) mu[k + 1] = u * mu[k] + (double)k * th * mu[k - 1];
+#pragma unroll
+        for (int i = 0; i < Q1; ++i) {
+            double s = 0.0;
+#pragma unroll
+            for (int k = 0; k < Q1; ++k) s += P.C[i * Q1 + k] * mu[k];
+            r[a][i] = s;
+        }
+    }
+    const double rh = rho[n];
+#pragma unroll
+    for (int i = 0; i < Q1; ++i) {
+        const double ri = rh * r[0][i];
+#pragma unroll
+        for (int j = 0; j < (DIM == 2 ? Q1 : 1); ++j) {
+            const int p = DIM == 2 ? i * Q1 + j : i;
+            const double fe = DIM == 2 ? ri * r[DIM - 1][j] : ri;
+            f[elem_index(P, p, x, y)] = Storage<S>::from_f64(fe, P.W0[p]);
+        }
+    }
+}
+
+template <typename S, int Q1, int DIM>
+__global__ void k_moments_q(const __grid_constant__ LatticeParams P, const S* __restrict__ f, double* rho,
+                            double* ux, double* uy, double* theta) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= P.nx) return;
+    double Sx[Q1], Ty[Q1];
+#pragma unroll
+    for (int i = 0; i < Q1; ++i) Sx[i] = Ty[i] = 0.0;
+#pragma unroll
+    for (int i = 0; i < Q1; ++i)
+#pragma unroll
+        for (int j = 0; j < (DIM == 2 ? Q1 : 1); ++j) {
+            const int p = DIM == 2 ? i * Q1 + j : i;
+            const double v = Storage<S>::to_f64(f[elem_index(P, p, x, y)], P.W0[p]);
+            Sx[i] += v;
+            Ty[j] += v;
+        }
+    double m0 = 0.0, jx = 0.0, jy = 0.0, en = 0.0;
+#pragma unroll
+    for (int i = 0; i < Q1; ++i) {
+        const double vi = (double)P.v[i];
+        m0 += Sx[i];
+        jx += vi * Sx[i];
+        en += vi * vi * Sx[i];
+        if (DIM == 2) {
+            jy += vi * Ty[i];
+            en += vi * vi * Ty[i];
+        }
+    }
+    const double a = jx / m0, b = jy / m0;
+    const long long n = (long long)y * P.nx + x;
+    if (rho) rho[n] = m0;
+    if (ux) ux[n] = a;
+    if (uy) uy[n] = b;
+    if (theta) theta[n] = (en / m0 - (a * a + b * b)) / (double)DIM;
+}
+
 template <typename S>
 __global__ void k_moments(const __grid_constant__ LatticeParams P, const S* __restrict__ f,
                           double* rho, double* ux, double* uy, double* theta) {
@@ -283,6 +363,17 @@ __global__ void k_set_pop(const __grid_constant__ LatticeParams P, const double*
 cudaError_t launch_init(int prec, const LatticeParams& P, const double* rho, const double* ux,
                         const double* uy, const double* theta, void* f, cudaStream_t stream) {
     dim3 grid((P.nx + 127) / 128, P.ny);
+#define PLBM_INIT_Q(Q1v, DIMv)                                                                          \
+    if (P.q1 == Q1v && P.dim == DIMv) {                                                                 \
+        PLBM_DISPATCH(prec, (k_init_q<S, Q1v, DIMv><<<grid, 128, 0, stream>>>(P, rho, ux, uy, theta,     \
+                                                                              static_cast<S*>(f))));     \
+        return cudaGetLastError();                                                                      \
+    }
+    PLBM_INIT_Q(3, 2)
+    PLBM_INIT_Q(4, 2)
+    PLBM_INIT_Q(5, 2)
+    PLBM_INIT_Q(5, 1)
+#undef PLBM_INIT_Q
     PLBM_DISPATCH(prec, (k_init<S><<<grid, 128, 0, stream>>>(P, rho, ux, uy, theta,
                                                              static_cast<S*>(f))));
     return cudaGetLastError();
@@ -291,6 +382,17 @@ cudaError_t launch_init(int prec, const LatticeParams& P, const double* rho, con
 cudaError_t launch_moments(int prec, const LatticeParams& P, const void* f, double* rho,
                            double* ux, double* uy, double* theta, cudaStream_t stream) {
     dim3 grid((P.nx + 127) / 128, P.ny);
+#define PLBM_MOM_Q(Q1v, DIMv)                                                                           \
+    if (P.q1 == Q1v && P.dim == DIMv) {                                                                 \
+        PLBM_DISPATCH(prec, (k_moments_q<S, Q1v, DIMv><<<grid, 128, 0, stream>>>(                       \
+                                P, static_cast<const S*>(f), rho, ux, uy, theta)));                     \
+        return cudaGetLastError();                                                                      \
+    }
+    PLBM_MOM_Q(3, 2)
+    PLBM_MOM_Q(4, 2)
+    PLBM_MOM_Q(5, 2)
+    PLBM_MOM_Q(5, 1)
+#undef PLBM_MOM_Q
     PLBM_DISPATCH(prec, (k_moments<S><<<grid, 128, 0, stream>>>(P, static_cast<const S*>(f), rho,
                                                                 ux, uy, theta)));
     return cudaGetLastError();
