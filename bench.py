@@ -373,6 +373,61 @@ def run_surrogate(torch, n_train=2000, n_test=100, train_steps=2000, batch=16, K
     return out
 
 
+def _long_errors(mg, mr):
+    """Per-field errors of a run against stored FP64 oracle fields: relative
+    maximum (velocity as a vector), relative L2 and absolute maximum."""
+    out = _field_err(mg, mr)
+    du = np.hypot(mg[1] - mr[1], mg[2] - mr[2])
+    out["rho_l2"] = float(np.sqrt(np.mean((mg[0] - mr[0]) ** 2) / np.mean(mr[0] ** 2)))
+    out["u_l2"] = float(np.sqrt(np.mean(du ** 2) / np.mean(mr[1] ** 2 + mr[2] ** 2)))
+    out["theta_l2"] = float(np.sqrt(np.mean((mg[3] - mr[3]) ** 2) / np.mean(mr[3] ** 2)))
+    out["rho_abs"] = float(np.max(np.abs(mg[0] - mr[0])))
+    out["u_abs"] = float(np.max(du))
+    out["theta_abs"] = float(np.max(np.abs(mg[3] - mr[3])))
+    return out
+
+
+def run_longrun(torch, paths, precs=("f64", "f32", "f16dev", "bf16dev")):
+    """Errors of each storage precision against FP64 oracle snapshots of the double
+    shear layer (files written by the oracle's long-run script), with the
+    plausibility bounds of the flow (rho, theta within 1 +- 0.01, |u| <= 0.12)."""
+    from paper_1402_5487_gb300 import plbm
+    res = []
+    for path in paths:
+        d = np.load(path)
+        L, stride = int(d["size"]), int(d["stride"])
+        omega, theta0, seed = float(d["omega"]), float(d["theta0"]), int(d["seed"])
+        steps = [int(n) for n in d["steps"]]
+        fields = I.kh_fields(L, theta0=theta0, seed=seed)
+        entry = {"grid": [L, L], "omega": omega, "theta0": theta0, "seed": seed,
+                 "sampled": "every %d-th node in x and y" % stride if stride > 1 else "all nodes",
+                 "precisions": {}}
+        for prec in precs:
+            s = plbm.Solver(2, V5, omega, L, L, theta0=theta0, prec=prec)
+            s.init(*fields)
+            done, per = 0, {}
+            t0 = time.perf_counter()
+            for n in steps:
+                s.step(n - done)
+                done = n
+                st = s.check()
+                if st != 0:
+                    per[str(n)] = {"status": "diverged"}
+                    break
+                mg = [a[::stride, ::stride] for a in s.moments()]
+                mr = [d["%s_%d" % (k, n)] for k in ("rho", "ux", "uy", "theta")]
+                e = _long_errors(mg, mr)
+                e["plausible"] = bool(np.all(np.abs(mg[0] - 1) <= 0.01) and np.all(np.abs(mg[3] - 1) <= 0.01)
+                                      and np.max(np.hypot(mg[1], mg[2])) <= 0.12)
+                e["status"] = "ok"
+                per[str(n)] = e
+            per["seconds"] = time.perf_counter() - t0
+            s.close()
+            entry["precisions"][prec] = per
+        res.append(entry)
+    return res
+
+
 def run_case(torch, args):
     """One secondary workload alone: the surrogate network on a batch of 256 x 256
     lattices (forward passes and Adam steps on seeded random tensors), the
@@ -380,6 +435,8 @@ def run_case(torch, args):
     if args.case == "batched":
         return {"case": "batched", **run_batched(torch, steps=args.steps, warmup=args.warmup,
                                                  n=args.batch_instances)}
+    if args.case == "longrun":
+        return {"case": "longrun", "runs": run_longrun(torch, args.snapshots)}
     if args.case == "d3q125":
         return {"case": "d3q125", "prec": args.prec,
                 **run_variant3(torch, args.size, args.prec, args.steps, args.warmup)}
@@ -480,10 +537,12 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--surrogate-train", type=int, default=2000, help="training trajectories")
     ap.add_argument("--surrogate-steps", type=int, default=6000, help="Adam steps")
-    ap.add_argument("--case", default="main", choices=["main", "surrogate", "batched", "d3q125"],
-                    help="main: the bench line; surrogate / batched: one of the secondary workloads "
-                         "alone (a JSON line of its own, for profiling)")
+    ap.add_argument("--case", default="main", choices=["main", "surrogate", "batched", "d3q125", "longrun"],
+                    help="main: the bench line; any other: one secondary workload alone (a JSON "
+                         "line of its own); longrun: errors against FP64 oracle snapshots")
     ap.add_argument("--batch", type=int, default=16, help="lattices per surrogate call (--case surrogate)")
+    ap.add_argument("--snapshots", nargs="+", default=[],
+                    help="FP64 oracle snapshot files (.npz) for --case longrun")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

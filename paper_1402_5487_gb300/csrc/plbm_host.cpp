@@ -2,7 +2,9 @@
 // positivity gate, device memory and the extern "C" entry points of plbm.h.
 #include "plbm.h"
 
+#include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -389,6 +391,16 @@ plbm_status plbm_create(const plbm_desc* desc, plbm_handle* out) {
     P.paired = (dim == 2 && desc->ny % 2 == 0 && desc->prec != PLBM_F64 && P.sym5 && !P.isothermal &&
                 desc->bc == PLBM_PERIODIC) ? 1 : 0;
     P.half_ny = P.paired ? desc->ny / 2 : 0;
+    // z-paired layout and the two-nodes-per-thread 3D kernel: 16-bit storage, even nz,
+    // every |v| <= nz / 2 (one wrap of the pair row per pull).
+    int vmax = 0;
+    for (int i = 0; i < q1; ++i) vmax = std::max(vmax, std::abs(desc->v[i]));
+    // The kernel indexes a population array in 32-bit pair offsets.
+    const double pairs = (double)q1 * q1 * q1 * (double)align_up((size_t)desc->nx, plbm::kPitchAlign) *
+                         desc->ny * (dim == 3 ? desc->nz : 1) / 2.0;
+    P.zpaired = (dim == 3 && desc->nz % 2 == 0 && vmax <= desc->nz / 2 && P.sym5 && !P.isothermal &&
+                 (desc->prec == PLBM_F16DEV || desc->prec == PLBM_BF16DEV) && pairs < 4294967296.0) ? 1 : 0;
+    P.half_nz = P.zpaired ? desc->nz / 2 : 0;
 
     if (!(desc->flags & PLBM_FLAG_SKIP_ADMISSIBILITY)) {
         double wu = 0, wr = 0;

@@ -33,6 +33,9 @@ struct LatticeParams {
     int vxm[kMaxQ1];        // (-v) mod nx, in [0, nx): source column = x + vxm (- nx)
     int vym[kMaxQ1];        // (-v) mod ny, in [0, ny)
     int nz;                 // 3D: nodes along z (1 otherwise); rows of elem_index are z * ny + y
+    int zpaired;            // 3D z-paired layout (16-bit storage, even nz): nodes (x, y, z) and
+                            // (x, y, z + nz/2) side by side, row (z mod nz/2) * ny + y
+    int half_nz;            // nz / 2 when zpaired
     int vzm[kMaxQ1];        // (-v) mod nz, in [0, nz)
     double omega, theta0;
     float omegaf, theta0f;

@@ -25,12 +25,21 @@
 //   * f^eq - w0 = rho r^x r^y r^z - w^x w^y w^z
 //               = d_a (r^y_b r^z_c) + w_a (dr^y_b r^z_c + w_b dr^z_c),  d_a = rho r^x_a - w_a;
 //   * BGK: g' = g + omega (f^eq - w0 - g).
+// k_stream_collide3_zpair<S> (FP16 or BF16 storage, even nz): the same update
+// on the z-paired layout, where nodes (x, y, z) and (x, y, z + nz/2) sit side by
+// side.  One thread updates both: each of the 125 pulls is one aligned 4-byte
+// load of the two 16-bit deviations (kept packed in one register until the
+// collision), each store one 4-byte store, and the arithmetic runs on the two
+// nodes as the lanes of packed FP32x2 instructions.  Pull across the z wrap:
+// node z = r reads z - v_z; when r - v_z leaves [0, nz/2) the source pair row is
+// r - v_z -+ nz/2 and holds the two nodes in swapped lane order.
 // k_stream_collide3_f64: FP64 storage of f, any q1 <= 5, thermal or isothermal,
 // the plain formulas (an ALU-bound path).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include "plbm_device.cuh"
+#include "plbm_pair.cuh"
 
 namespace plbm {
 
@@ -43,6 +52,16 @@ constexpr int kQ3 = kQ1 * kQ1 * kQ1;
 __device__ __forceinline__ int wrap_add(int i, int d, int n) {
     const int s = i + d;
     return s >= n ? s - n : s;
+}
+
+// Element offset of node (x, y, z) within a population plane (plain or z-paired layout).
+__device__ __forceinline__ long long node3(const LatticeParams& P, int x, int y, int z) {
+    if (P.zpaired) {
+        const int hi = z >= P.half_nz;
+        const int r = hi ? z - P.half_nz : z;
+        return ((long long)r * P.ny + y) * 2 * P.pitch + 2LL * x + hi;
+    }
+    return ((long long)z * P.ny + y) * P.pitch + x;
 }
 
 // Per-axis rule deviations dr_i = r_i(u, theta) - w_i for (0, a, -a, b, -b),
@@ -144,6 +163,185 @@ __global__ void __launch_bounds__(kB3, 2) k_stream_collide3(const __grid_constan
         }
 }
 
+// Two packed 16-bit deviations <-> float2 (lane x = the node in the lower half).
+template <typename S>
+struct Pack2;
+
+// unpack_again converts a second time in the collision (an asm statement, so the
+// compiler keeps the 125 packed registers instead of 250 converted ones).
+template <>
+struct Pack2<__half> {
+    static __device__ __forceinline__ float2 unpack(unsigned r) {
+        __half2 h;
+        memcpy(&h, &r, 4);
+        return __half22float2(h);
+    }
+    static __device__ __forceinline__ float2 unpack_again(unsigned r) {
+        float2 v;
+        asm volatile("{\n\t.reg .f16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\tcvt.f32.f16 %0, lo;\n\tcvt.f32.f16 %1, hi;\n\t}"
+                     : "=f"(v.x), "=f"(v.y) : "r"(r));
+        return v;
+    }
+    static __device__ __forceinline__ unsigned pack(float2 v) {
+        const __half2 h = __float22half2_rn(v);
+        unsigned r;
+        memcpy(&r, &h, 4);
+        return r;
+    }
+};
+
+template <>
+struct Pack2<__nv_bfloat16> {
+    static __device__ __forceinline__ float2 unpack(unsigned r) {
+        return make_float2(__uint_as_float(r << 16), __uint_as_float(r & 0xffff0000u));
+    }
+    static __device__ __forceinline__ float2 unpack_again(unsigned r) {
+        unsigned lo, hi;
+        asm volatile("shl.b32 %0, %2, 16;\n\tand.b32 %1, %2, 0xffff0000;" : "=r"(lo), "=r"(hi) : "r"(r));
+        return make_float2(__uint_as_float(lo), __uint_as_float(hi));
+    }
+    static __device__ __forceinline__ unsigned pack(float2 v) {
+        const __nv_bfloat162 h = __float22bfloat162_rn(v);
+        unsigned r;
+        memcpy(&r, &h, 4);
+        return r;
+    }
+};
+
+// axis_dev on both nodes of a pair.
+__device__ __forceinline__ void axis_dev2(const LatticeParams& P, float2 u, float2 dth, float2 (&dr)[kQ1]) {
+    const float2 th0 = f2s(P.theta0f);
+    const float2 u2 = mul2(u, u);
+    const float2 th = add2(th0, dth);
+    const float2 dm1 = u;
+    const float2 dm2 = add2(u2, dth);
+    const float2 dm3 = mul2(u, fma2(f2s(3.0f), th, u2));
+    const float2 dm4 = fma2(u2, fma2(f2s(6.0f), th, u2), mul2(mul2(f2s(3.0f), dth), add2(th, th0)));
+    const float2 Ob = mul2(fma2(f2s(-P.sa2), dm1, dm3), f2s(P.kOb));
+    const float2 Oa = mul2(fma2(f2s(-2.0f * P.sb), Ob, dm1), f2s(P.kOa));
+    const float2 Eb = mul2(fma2(f2s(-P.sa2), dm2, dm4), f2s(P.kEb));
+    const float2 Ea = mul2(fma2(f2s(-2.0f * P.sb2), Eb, dm2), f2s(P.kEa));
+    dr[0] = mul2(f2s(-2.0f), add2(Ea, Eb));
+    dr[1] = add2(Ea, Oa);
+    dr[2] = sub2(Ea, Oa);
+    dr[3] = add2(Eb, Ob);
+    dr[4] = sub2(Eb, Ob);
+}
+
+// Both nodes of pair row r at column x.  WRAP: some pull of z crosses the wrap
+// (r < max|v| or r >= nz/2 - max|v|), so the lanes of those loads are swapped;
+// pair rows away from the wrap (all but 2 max|v| of them) take the WRAP = false
+// copy without the per-load lane test.
+template <typename S, bool WRAP>
+__device__ __forceinline__ void zpair_update(const LatticeParams& P, const unsigned* __restrict__ s32,
+                                             unsigned* __restrict__ d32, int x, int y, int r) {
+    const int H = P.half_nz;
+    int xs[kQ1], ys[kQ1], zr[kQ1];
+    bool sw[kQ1];
+#pragma unroll
+    for (int i = 0; i < kQ1; ++i) {
+        xs[i] = wrap_add(x, P.vxm[i], P.nx);
+        ys[i] = wrap_add(y, P.vym[i], P.ny);
+        const int zs = r - P.v[i];             // |v| <= nz/2 (checked on the host)
+        sw[i] = zs < 0 || zs >= H;
+        zr[i] = zs < 0 ? zs + H : (zs >= H ? zs - H : zs);
+    }
+    // Offsets in pairs fit 32 bits (the host sends larger lattices to the plain kernel).
+    const unsigned plane = (unsigned)(P.plane >> 1);   // pairs per population plane
+    unsigned g[kQ3];
+#pragma unroll
+    for (int b = 0; b < kQ1; ++b)
+#pragma unroll
+        for (int c = 0; c < kQ1; ++c) {
+            const unsigned row = ((unsigned)zr[c] * P.ny + ys[b]) * P.pitch;   // in pairs
+#pragma unroll
+            for (int a = 0; a < kQ1; ++a) {
+                const int p = (a * kQ1 + b) * kQ1 + c;
+                const unsigned v = __ldg(s32 + (p * plane + row + xs[a]));
+                g[p] = (WRAP && sw[c]) ? __byte_perm(v, 0u, 0x1032) : v;
+            }
+        }
+    // Row sums: R_ab = sum_c g, S_a = sum_b R_ab, T_b = sum_a R_ab, U_c = sum_ab g.
+    float2 Sa[kQ1], Tb[kQ1], Uc[kQ1];
+#pragma unroll
+    for (int i = 0; i < kQ1; ++i) Sa[i] = Tb[i] = Uc[i] = f2s(0.0f);
+#pragma unroll
+    for (int a = 0; a < kQ1; ++a)
+#pragma unroll
+        for (int b = 0; b < kQ1; ++b) {
+            float2 R = f2s(0.0f);
+#pragma unroll
+            for (int c = 0; c < kQ1; ++c) {
+                const float2 v = Pack2<S>::unpack(g[(a * kQ1 + b) * kQ1 + c]);
+                R = add2(R, v);
+                Uc[c] = add2(Uc[c], v);
+            }
+            Sa[a] = add2(Sa[a], R);
+            Tb[b] = add2(Tb[b], R);
+        }
+    float2 drho = f2s(0.0f), jx = drho, jy = drho, jz = drho, de = drho;
+#pragma unroll
+    for (int i = 0; i < kQ1; ++i) {
+        const float2 vi = f2s((float)P.v[i]);
+        drho = add2(drho, Sa[i]);
+        jx = fma2(vi, Sa[i], jx);
+        jy = fma2(vi, Tb[i], jy);
+        jz = fma2(vi, Uc[i], jz);
+        de = fma2(mul2(vi, vi), add2(add2(Sa[i], Tb[i]), Uc[i]), de);
+    }
+    const float2 rho = add2(f2s(1.0f), drho);
+    const float2 ir = f2(1.0f / rho.x, 1.0f / rho.y);
+    const float2 ux = mul2(jx, ir), uy = mul2(jy, ir), uz = mul2(jz, ir);
+    const float2 uu = fma2(ux, ux, fma2(uy, uy, mul2(uz, uz)));
+    const float2 dth = mul2(sub2(mul2(fma2(f2s(-3.0f * P.theta0f), drho, de), ir), uu), f2s(1.0f / 3.0f));
+    flag_status<float>(P, rho.x, P.theta0f + dth.x);
+    flag_status<float>(P, rho.y, P.theta0f + dth.y);
+    float2 drx[kQ1], dry[kQ1], drz[kQ1];
+    axis_dev2(P, ux, dth, drx);
+    axis_dev2(P, uy, dth, dry);
+    axis_dev2(P, uz, dth, drz);
+    // g' = (1 - omega) g + omega (f^eq - w0), with omega folded into the x factors:
+    // omega (f^eq - w0) = X_a P_bc + W_a Q_bc, X_a = omega (rho r^x_a - w_a), W_a = omega w_a.
+    const float2 om = f2s(P.omegaf);
+    float2 X[kQ1];
+#pragma unroll
+    for (int a = 0; a < kQ1; ++a) X[a] = mul2(om, fma2(drho, f2s(P.w1f[a]), mul2(rho, drx[a])));
+    const float2 keep = f2s(1.0f - P.omegaf);
+    const unsigned here = ((unsigned)r * P.ny + y) * P.pitch + x;   // in pairs
+#pragma unroll
+    for (int b = 0; b < kQ1; ++b)
+#pragma unroll
+        for (int c = 0; c < kQ1; ++c) {
+            const float2 rzc = add2(f2s(P.w1f[c]), drz[c]);
+            const float2 Pbc = mul2(add2(f2s(P.w1f[b]), dry[b]), rzc);
+            const float2 Qbc = fma2(dry[b], rzc, mul2(f2s(P.w1f[b]), drz[c]));
+#pragma unroll
+            for (int a = 0; a < kQ1; ++a) {
+                const int p = (a * kQ1 + b) * kQ1 + c;
+                const float2 gp = Pack2<S>::unpack_again(g[p]);
+                const float2 d = fma2(X[a], Pbc, mul2(f2s(P.omegaf * P.w1f[a]), Qbc));
+                d32[p * plane + here] = Pack2<S>::pack(fma2(keep, gp, d));   // 32-bit index
+            }
+        }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kB3, 2) k_stream_collide3_zpair(const __grid_constant__ LatticeParams P,
+                                                                 const S* __restrict__ src, S* __restrict__ dst) {
+    const int x = blockIdx.x * kB3 + threadIdx.x;
+    const int y = blockIdx.y, r = blockIdx.z;   // pair row r: nodes z = r and z = r + nz/2
+    if (x >= P.nx) return;
+    bool wrap = false;
+#pragma unroll
+    for (int i = 0; i < kQ1; ++i) wrap |= (r - P.v[i] < 0) || (r - P.v[i] >= P.half_nz);
+    const unsigned* s32 = reinterpret_cast<const unsigned*>(src);
+    unsigned* d32 = reinterpret_cast<unsigned*>(dst);
+    if (wrap)
+        zpair_update<S, true>(P, s32, d32, x, y, r);
+    else
+        zpair_update<S, false>(P, s32, d32, x, y, r);
+}
+
 // FP64: any q1 <= 5; fin[p] pulled, moments, f^eq from C and the Gaussian moments.
 __device__ void rule_f64(const LatticeParams& P, double u, double th, double* r) {
     double mu[kMaxQ1];
@@ -236,7 +434,7 @@ __global__ void k_init3(const __grid_constant__ LatticeParams P, const double* _
     const double th = (P.isothermal || theta == nullptr) ? P.theta0 : theta[n];
     double fe[kQ3];
     feq3_f64(P, rho[n], ux ? ux[n] : 0.0, uy ? uy[n] : 0.0, uz ? uz[n] : 0.0, th, fe);
-    const long long here = ((long long)z * P.ny + y) * P.pitch + x;
+    const long long here = node3(P, x, y, z);
     for (int p = 0; p < P.q; ++p) f[(long long)p * P.plane + here] = Storage<S>::from_f64(fe[p], w0_3(P, p));
 }
 
@@ -246,7 +444,7 @@ __global__ void k_moments3(const __grid_constant__ LatticeParams P, const S* __r
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     if (x >= P.nx) return;
-    const long long here = ((long long)z * P.ny + y) * P.pitch + x;
+    const long long here = node3(P, x, y, z);
     double fn[kQ3], m[9];
     for (int p = 0; p < P.q; ++p) fn[p] = Storage<S>::to_f64(f[(long long)p * P.plane + here], w0_3(P, p));
     moments3_f64(P, fn, m);
@@ -266,7 +464,7 @@ __global__ void __launch_bounds__(kB3) k_reduce3(const __grid_constant__ Lattice
     const int y = blockIdx.y, z = blockIdx.z;
     double r[7] = {0, 0, 0, 0, 1e300, 1e300, 0};
     if (x < P.nx) {
-        const long long here = ((long long)z * P.ny + y) * P.pitch + x;
+        const long long here = node3(P, x, y, z);
         double fn[kQ3], m[9];
         for (int p = 0; p < P.q; ++p) fn[p] = Storage<S>::to_f64(f[(long long)p * P.plane + here], w0_3(P, p));
         moments3_f64(P, fn, m);
@@ -321,7 +519,7 @@ __global__ void k_get_pop3(const __grid_constant__ LatticeParams P, const S* __r
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     if (x >= P.nx) return;
-    const long long here = ((long long)z * P.ny + y) * P.pitch + x;
+    const long long here = node3(P, x, y, z);
     const long long vol = (long long)P.nx * P.ny * P.nz;
     const long long n = ((long long)z * P.ny + y) * P.nx + x;
     for (int p = 0; p < P.q; ++p) out[p * vol + n] = Storage<S>::to_f64(f[(long long)p * P.plane + here], w0_3(P, p));
@@ -332,7 +530,7 @@ __global__ void k_set_pop3(const __grid_constant__ LatticeParams P, const double
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     if (x >= P.nx) return;
-    const long long here = ((long long)z * P.ny + y) * P.pitch + x;
+    const long long here = node3(P, x, y, z);
     const long long vol = (long long)P.nx * P.ny * P.nz;
     const long long n = ((long long)z * P.ny + y) * P.nx + x;
     for (int p = 0; p < P.q; ++p) f[(long long)p * P.plane + here] = Storage<S>::from_f64(in[p * vol + n], w0_3(P, p));
@@ -361,6 +559,18 @@ cudaError_t launch_step3(int prec, const LatticeParams& P, const void* src, void
         return cudaGetLastError();
     }
     if (!P.sym5 || P.q1 != kQ1 || P.isothermal) return cudaErrorInvalidValue;
+    if (P.zpaired) {
+        const dim3 g((P.nx + kB3 - 1) / kB3, P.ny, P.half_nz);
+        if (prec == kF16Dev)
+            k_stream_collide3_zpair<__half><<<g, kB3, 0, s>>>(P, static_cast<const __half*>(src),
+                                                               static_cast<__half*>(dst));
+        else if (prec == kBF16Dev)
+            k_stream_collide3_zpair<__nv_bfloat16><<<g, kB3, 0, s>>>(
+                P, static_cast<const __nv_bfloat16*>(src), static_cast<__nv_bfloat16*>(dst));
+        else
+            return cudaErrorInvalidValue;
+        return cudaGetLastError();
+    }
     switch (prec) {
         case kF32:
             k_stream_collide3<float><<<grid3(P), kB3, 0, s>>>(P, static_cast<const float*>(src), static_cast<float*>(dst));

@@ -62,9 +62,14 @@ def test_d3q27_isothermal_f64_matches_oracle():
     assert O.rel_err(fg, fo) <= TOL64
 
 
-@pytest.mark.parametrize("prec,tol", [("f32", 2e-6), ("f16dev", 2e-3), ("bf16dev", 2e-2)])
-def test_d3q125_reduced_storage_matches_oracle(prec, tol):
-    lat, fo, (mg, fg, cg), f = run_pair(V5, 1.3, (130, 7, 5), 30, prec)
+# Odd nz: one node per thread.  Even nz with 16-bit storage: the z-paired layout
+# and the two-nodes-per-thread kernel (nz = 6 puts every pair row within
+# max|v| = 3 of the wrap, so each pull of z crosses it in one lane or the other).
+@pytest.mark.parametrize("prec,tol,shape", [("f32", 2e-6, (130, 7, 5)), ("f16dev", 2e-3, (130, 7, 5)),
+                                            ("bf16dev", 2e-2, (130, 7, 5)), ("f16dev", 2e-3, (130, 7, 6)),
+                                            ("bf16dev", 2e-2, (130, 7, 6)), ("f16dev", 2e-3, (20, 5, 14))])
+def test_d3q125_reduced_storage_matches_oracle(prec, tol, shape):
+    lat, fo, (mg, fg, cg), f = run_pair(V5, 1.3, shape, 30, prec)
     mo = lat.moments(fo)
     u0 = np.max(np.sqrt(f[1] ** 2 + f[2] ** 2 + f[3] ** 2))
     du = np.sqrt((mg[1] - mo[1]) ** 2 + (mg[2] - mo[2]) ** 2 + (mg[3] - mo[3]) ** 2)
@@ -115,10 +120,10 @@ def test_d3q125_f32_1000_steps_uniform_flow_bound():
     assert eu <= 5e-5 and er <= 1e-5 and et <= 1e-5, (eu, er, et)
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
-def test_d3q125_pure_streaming_is_exact(prec):
+@pytest.mark.parametrize("prec,nz", [("f64", 5), ("f32", 5), ("f16dev", 6), ("bf16dev", 6), ("f16dev", 10)])
+def test_d3q125_pure_streaming_is_exact(prec, nz):
     from paper_1402_5487_gb300 import plbm
-    nx, ny, nz = 131, 6, 5
+    nx, ny = 131, 6
     lat = O.Lattice3(V5, 0.0, nx, ny, nz)
     f0 = lat.init(*fields3(nx, ny, nz, 9))
     s = plbm.Solver(3, V5, 0.0, nx, ny, nz=nz, prec=prec, skip_admissibility=True)
