@@ -115,14 +115,17 @@ __global__ void __launch_bounds__(kB3, 2) k_stream_collide3(const __grid_constan
 #pragma unroll
     for (int a = 0; a < kQ1; ++a)
 #pragma unroll
-        for (int b = 0; b < kQ1; ++b)
+        for (int b = 0; b < kQ1; ++b) {
+            float R = 0.0f;   // R_ab = sum_c g; S_a = sum_b R_ab, T_b = sum_a R_ab
 #pragma unroll
             for (int c = 0; c < kQ1; ++c) {
                 const float v = g[(a * kQ1 + b) * kQ1 + c];
-                Sa[a] += v;
-                Tb[b] += v;
+                R += v;
                 Uc[c] += v;
             }
+            Sa[a] += R;
+            Tb[b] += R;
+        }
     float drho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f, de = 0.0f;
 #pragma unroll
     for (int i = 0; i < kQ1; ++i) {
@@ -142,10 +145,13 @@ __global__ void __launch_bounds__(kB3, 2) k_stream_collide3(const __grid_constan
     axis_dev(P, ux, dth, drx);
     axis_dev(P, uy, dth, dry);
     axis_dev(P, uz, dth, drz);
-    float da[kQ1];  // rho r^x_a - w_a = (rho - 1) w_a + rho dr^x_a
-#pragma unroll
-    for (int a = 0; a < kQ1; ++a) da[a] = fmaf(drho, P.w1f[a], rho * drx[a]);
+    // g' = (1 - omega) g + omega (f^eq - w0), omega (f^eq - w0) = X_a P_bc + W_a Q_bc with
+    // X_a = omega (rho r^x_a - w_a) = omega ((rho - 1) w_a + rho dr^x_a), W_a = omega w_a.
     const float om = P.omegaf;
+    float X[kQ1];
+#pragma unroll
+    for (int a = 0; a < kQ1; ++a) X[a] = om * fmaf(drho, P.w1f[a], rho * drx[a]);
+    const float keep = 1.0f - om;
     const long long here = ((long long)z * P.ny + y) * P.pitch + x;
 #pragma unroll
     for (int b = 0; b < kQ1; ++b)
@@ -157,8 +163,8 @@ __global__ void __launch_bounds__(kB3, 2) k_stream_collide3(const __grid_constan
 #pragma unroll
             for (int a = 0; a < kQ1; ++a) {
                 const int p = (a * kQ1 + b) * kQ1 + c;
-                const float d = fmaf(da[a], Pbc, P.w1f[a] * Qbc);
-                Storage<S>::store(dst + (long long)p * P.plane + here, fmaf(om, d - g[p], g[p]));
+                const float d = fmaf(X[a], Pbc, (om * P.w1f[a]) * Qbc);
+                Storage<S>::store(dst + (long long)p * P.plane + here, fmaf(keep, g[p], d));
             }
         }
 }
