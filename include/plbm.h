@@ -167,11 +167,16 @@ plbm_status plbm_create(const plbm_desc *desc, plbm_handle *out);
 plbm_status plbm_destroy(plbm_handle h);
 
 /* Initial state f = f^eq(rho, u, theta) at every node (Eq. eq:eqdist), computed
- * in FP64 on the device and stored in the handle's precision.  Fields: FP64
- * [ny][nx]; uy may be NULL in 1D; theta may be NULL for isothermal handles.
+ * on the device and stored in the handle's precision: in FP64, except for
+ * FP32/FP16/BF16 handles with a symmetric five-velocity set (0, +-a, +-b), which
+ * evaluate f^eq - w0 in the FP32 deviation arithmetic of their own collision
+ * from rho - 1, u and theta - theta0 (formed in FP64).  Fields: FP64 [ny][nx];
+ * uy may be NULL in 1D; theta may be NULL for isothermal handles.
  * on_device != 0: the pointers are device memory, read on the handle's stream
- * (asynchronous); otherwise host memory, copied before return.  Resets the
- * step counter and the status word. */
+ * (asynchronous); otherwise host memory, copied before return (through a
+ * staging buffer of 4 nx ny doubles that the handle keeps after first use, in
+ * row bands whose copies overlap the kernel).  Resets the step counter and
+ * the status word. */
 plbm_status plbm_init(plbm_handle h, const double *rho, const double *ux, const double *uy,
                       const double *theta, int on_device);
 
@@ -186,8 +191,10 @@ plbm_status plbm_step(plbm_handle h, long n);
 plbm_status plbm_check(plbm_handle h);
 
 /* Macroscopic fields of the stored state: rho, u_x, u_y, theta as FP64
- * [ny][nx] (uy may be NULL).  on_device != 0: device pointers, asynchronous;
- * otherwise host pointers, synchronous. */
+ * [ny][nx] (uy may be NULL).  FP32/FP16/BF16 handles sum their stored
+ * deviations in float-float arithmetic (~2^-48 relative), then form the fields
+ * in FP64.  on_device != 0: device pointers, asynchronous; otherwise host
+ * pointers, synchronous (the staging buffer of plbm_init). */
 plbm_status plbm_moments(plbm_handle h, double *rho, double *ux, double *uy, double *theta,
                          int on_device);
 

@@ -101,9 +101,9 @@ __device__ void node_moments_f64(const LatticeParams& P, const double* f, double
 template <typename S>
 __global__ void k_init(const __grid_constant__ LatticeParams P, const double* __restrict__ rho,
                        const double* __restrict__ ux, const double* __restrict__ uy,
-                       const double* __restrict__ theta, S* __restrict__ f) {
+                       const double* __restrict__ theta, S* __restrict__ f, int y0) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
+    const int y = y0 + blockIdx.y;
     if (x >= P.nx) return;
     const long long n = (long long)y * P.nx + x;
     const double th = (P.isothermal || theta == nullptr) ? P.theta0 : theta[n];
@@ -118,9 +118,9 @@ __global__ void k_init(const __grid_constant__ LatticeParams P, const double* __
 template <typename S, int Q1, int DIM>
 __global__ void k_init_q(const __grid_constant__ LatticeParams P, const double* __restrict__ rho,
                          const double* __restrict__ ux, const double* __restrict__ uy,
-                         const double* __restrict__ theta, S* __restrict__ f) {
+                         const double* __restrict__ theta, S* __restrict__ f, int y0) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
+    const int y = y0 + blockIdx.y;
     if (x >= P.nx) return;
     const long long n = (long long)y * P.nx + x;
     const double th = (P.isothermal || theta == nullptr) ? P.theta0 : theta[n];
@@ -156,9 +156,9 @@ __global__ void k_init_q(const __grid_constant__ LatticeParams P, const double* 
 
 template <typename S, int Q1, int DIM>
 __global__ void k_moments_q(const __grid_constant__ LatticeParams P, const S* __restrict__ f, double* rho,
-                            double* ux, double* uy, double* theta) {
+                            double* ux, double* uy, double* theta, int y0) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
+    const int y = y0 + blockIdx.y;
     if (x >= P.nx) return;
     double Sx[Q1], Ty[Q1];
 #pragma unroll
@@ -192,11 +192,133 @@ __global__ void k_moments_q(const __grid_constant__ LatticeParams P, const S* __
     if (theta) theta[n] = (en / m0 - (a * a + b * b)) / (double)DIM;
 }
 
+// Initial state of a 16/32-bit handle with a symmetric five-velocity set, in the
+// FP32 deviation arithmetic of its own collision: per axis the constraint form
+// of the rule (dmu_n = mu_n(u, theta) - mu_n(0, theta0), n = 1..4;
+// O_b = (dmu3 - a^2 dmu1) / (2b(b^2 - a^2)), O_a = (dmu1 - 2b O_b) / (2a),
+// E_b = (dmu4 - a^2 dmu2) / (2b^2(b^2 - a^2)), E_a = (dmu2 - 2b^2 E_b) / (2a^2),
+// dr = (-2(E_a + E_b), E_a +- O_a, E_b +- O_b)), then
+// f^eq - w0 = X_i (w_j + dr^y_j) + w_i dr^y_j with X_i = (rho - 1) w_i + rho dr^x_i
+// (in 1D: X_i).  The inputs enter as the small quantities rho - 1, u and
+// theta - theta0, formed in FP64.
+__device__ __forceinline__ void sym5_dev(const LatticeParams& P, float u, float dth, float (&dr)[5]) {
+    const float u2 = u * u;
+    const float th = P.theta0f + dth;
+    const float dm1 = u;
+    const float dm2 = u2 + dth;
+    const float dm3 = u * (u2 + 3.0f * th);
+    const float dm4 = u2 * (u2 + 6.0f * th) + 3.0f * dth * (th + P.theta0f);
+    const float Ob = (dm3 - P.sa2 * dm1) * P.kOb;
+    const float Oa = (dm1 - 2.0f * P.sb * Ob) * P.kOa;
+    const float Eb = (dm4 - P.sa2 * dm2) * P.kEb;
+    const float Ea = (dm2 - 2.0f * P.sb2 * Eb) * P.kEa;
+    dr[0] = -2.0f * (Ea + Eb);
+    dr[1] = Ea + Oa;
+    dr[2] = Ea - Oa;
+    dr[3] = Eb + Ob;
+    dr[4] = Eb - Ob;
+}
+
+template <typename S, int DIM>
+__global__ void k_init_sym5_dev(const __grid_constant__ LatticeParams P, const double* __restrict__ rho,
+                                const double* __restrict__ ux, const double* __restrict__ uy,
+                                const double* __restrict__ theta, S* __restrict__ f, int y0) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = y0 + blockIdx.y;
+    if (x >= P.nx) return;
+    const long long n = (long long)y * P.nx + x;
+    const float dth = (P.isothermal || theta == nullptr) ? 0.0f : (float)(theta[n] - P.theta0);
+    const float drho = (float)(rho[n] - 1.0);
+    const float rh = 1.0f + drho;
+    float drx[5], dry[5];
+    sym5_dev(P, (float)ux[n], dth, drx);
+    if (DIM == 2) sym5_dev(P, uy ? (float)uy[n] : 0.0f, dth, dry);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const float X = fmaf(drho, P.w1f[i], rh * drx[i]);
+        if (DIM == 1) {
+            Storage<S>::store(f + elem_index(P, i, x, y), X);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 5; ++j)
+                Storage<S>::store(f + elem_index(P, i * 5 + j, x, y),
+                                  fmaf(X, P.w1f[j] + dry[j], P.w1f[i] * dry[j]));
+        }
+    }
+}
+
+// Moments of a 16/32-bit (deviation) state: the row and column sums of the
+// stored deviations g in float-float arithmetic (an FP32 pair hi + lo carried
+// through error-free sums and products, ~2^-48 relative), then
+// rho = 1 + sum g, j = sum v g, E = d theta0 + sum |v|^2 g (the rest identities of
+// the 1D rule) and theta = (E / rho - |u|^2) / d in FP64.
+struct FF {
+    float hi, lo;
+};
+__device__ __forceinline__ FF ff_add(FF a, float b) {
+    const float s = a.hi + b;
+    const float t = s - a.hi;
+    const float e = (a.hi - (s - t)) + (b - t);
+    return {s, a.lo + e};
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+    const float s = a.hi + b.hi;
+    const float t = s - a.hi;
+    const float e = (a.hi - (s - t)) + (b.hi - t);
+    return {s, (a.lo + b.lo) + e};
+}
+__device__ __forceinline__ FF ff_scale(FF a, float v) {
+    const float p = a.hi * v;
+    const float e = fmaf(a.hi, v, -p);
+    return {p, fmaf(a.lo, v, e)};
+}
+__device__ __forceinline__ double ff_f64(FF a) { return (double)a.hi + (double)a.lo; }
+
+template <typename S, int Q1, int DIM>
+__global__ void k_moments_dev(const __grid_constant__ LatticeParams P, const S* __restrict__ f, double* rho,
+                              double* ux, double* uy, double* theta, int y0) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = y0 + blockIdx.y;
+    if (x >= P.nx) return;
+    FF Sx[Q1], Ty[Q1];
+#pragma unroll
+    for (int i = 0; i < Q1; ++i) Sx[i] = Ty[i] = FF{0.0f, 0.0f};
+#pragma unroll
+    for (int i = 0; i < Q1; ++i)
+#pragma unroll
+        for (int j = 0; j < (DIM == 2 ? Q1 : 1); ++j) {
+            const int p = DIM == 2 ? i * Q1 + j : i;
+            const float g = Storage<S>::load(f + elem_index(P, p, x, y));
+            Sx[i] = ff_add(Sx[i], g);
+            if (DIM == 2) Ty[j] = ff_add(Ty[j], g);
+        }
+    FF dm{0.0f, 0.0f}, jx = dm, jy = dm, de = dm;
+#pragma unroll
+    for (int i = 0; i < Q1; ++i) {
+        const float vi = (float)P.v[i];
+        dm = ff_add(dm, Sx[i]);
+        jx = ff_add(jx, ff_scale(Sx[i], vi));
+        de = ff_add(de, ff_scale(ff_scale(Sx[i], vi), vi));
+        if (DIM == 2) {
+            jy = ff_add(jy, ff_scale(Ty[i], vi));
+            de = ff_add(de, ff_scale(ff_scale(Ty[i], vi), vi));
+        }
+    }
+    const double r = 1.0 + ff_f64(dm);
+    const double ir = 1.0 / r;
+    const double a = ff_f64(jx) * ir, b = DIM == 2 ? ff_f64(jy) * ir : 0.0;
+    const long long n = (long long)y * P.nx + x;
+    if (rho) rho[n] = r;
+    if (ux) ux[n] = a;
+    if (uy) uy[n] = b;
+    if (theta) theta[n] = (((double)DIM * P.theta0 + ff_f64(de)) * ir - (a * a + b * b)) / (double)DIM;
+}
+
 template <typename S>
 __global__ void k_moments(const __grid_constant__ LatticeParams P, const S* __restrict__ f,
-                          double* rho, double* ux, double* uy, double* theta) {
+                          double* rho, double* ux, double* uy, double* theta, int y0) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
+    const int y = y0 + blockIdx.y;
     if (x >= P.nx) return;
     double fn[kMaxQ];
     for (int p = 0; p < P.q; ++p) fn[p] = Storage<S>::to_f64(f[elem_index(P, p, x, y)], P.W0[p]);
@@ -360,13 +482,35 @@ __global__ void k_set_pop(const __grid_constant__ LatticeParams P, const double*
         default: return cudaErrorInvalidValue;                           \
     }
 
+// The deviation-storage precisions only.
+#define PLBM_DISPATCH_DEV(prec, CALL)                                    \
+    switch (prec) {                                                      \
+        case kF32: { using S = float; CALL; break; }                     \
+        case kF16Dev: { using S = __half; CALL; break; }                 \
+        case kBF16Dev: { using S = __nv_bfloat16; CALL; break; }         \
+        default: return cudaErrorInvalidValue;                           \
+    }
+
 cudaError_t launch_init(int prec, const LatticeParams& P, const double* rho, const double* ux,
-                        const double* uy, const double* theta, void* f, cudaStream_t stream) {
-    dim3 grid((P.nx + 127) / 128, P.ny);
+                        const double* uy, const double* theta, void* f, cudaStream_t stream, int y0, int y1) {
+    if (y1 < 0) y1 = P.ny;
+    if (y1 <= y0) return cudaSuccess;
+    dim3 grid((P.nx + 127) / 128, y1 - y0);
+#define PLBM_INIT_DEV(DIMv)                                                                            \
+    if (P.dim == DIMv) {                                                                               \
+        PLBM_DISPATCH_DEV(prec, (k_init_sym5_dev<S, DIMv><<<grid, 128, 0, stream>>>(P, rho, ux, uy, theta, \
+                                                                                 static_cast<S*>(f), y0))); \
+        return cudaGetLastError();                                                                     \
+    }
+    if (prec != kF64 && P.sym5) {
+        PLBM_INIT_DEV(2)
+        PLBM_INIT_DEV(1)
+    }
+#undef PLBM_INIT_DEV
 #define PLBM_INIT_Q(Q1v, DIMv)                                                                          \
     if (P.q1 == Q1v && P.dim == DIMv) {                                                                 \
         PLBM_DISPATCH(prec, (k_init_q<S, Q1v, DIMv><<<grid, 128, 0, stream>>>(P, rho, ux, uy, theta,     \
-                                                                              static_cast<S*>(f))));     \
+                                                                              static_cast<S*>(f), y0)));  \
         return cudaGetLastError();                                                                      \
     }
     PLBM_INIT_Q(3, 2)
@@ -375,17 +519,23 @@ cudaError_t launch_init(int prec, const LatticeParams& P, const double* rho, con
     PLBM_INIT_Q(5, 1)
 #undef PLBM_INIT_Q
     PLBM_DISPATCH(prec, (k_init<S><<<grid, 128, 0, stream>>>(P, rho, ux, uy, theta,
-                                                             static_cast<S*>(f))));
+                                                             static_cast<S*>(f), y0)));
     return cudaGetLastError();
 }
 
 cudaError_t launch_moments(int prec, const LatticeParams& P, const void* f, double* rho,
-                           double* ux, double* uy, double* theta, cudaStream_t stream) {
-    dim3 grid((P.nx + 127) / 128, P.ny);
+                           double* ux, double* uy, double* theta, cudaStream_t stream, int y0, int y1) {
+    if (y1 < 0) y1 = P.ny;
+    if (y1 <= y0) return cudaSuccess;
+    dim3 grid((P.nx + 127) / 128, y1 - y0);
 #define PLBM_MOM_Q(Q1v, DIMv)                                                                           \
     if (P.q1 == Q1v && P.dim == DIMv) {                                                                 \
-        PLBM_DISPATCH(prec, (k_moments_q<S, Q1v, DIMv><<<grid, 128, 0, stream>>>(                       \
-                                P, static_cast<const S*>(f), rho, ux, uy, theta)));                     \
+        if (prec == kF64)                                                                               \
+            k_moments_q<double, Q1v, DIMv><<<grid, 128, 0, stream>>>(                                   \
+                P, static_cast<const double*>(f), rho, ux, uy, theta, y0);                                  \
+        else                                                                                            \
+            PLBM_DISPATCH_DEV(prec, (k_moments_dev<S, Q1v, DIMv><<<grid, 128, 0, stream>>>(             \
+                                    P, static_cast<const S*>(f), rho, ux, uy, theta, y0)));                 \
         return cudaGetLastError();                                                                      \
     }
     PLBM_MOM_Q(3, 2)
@@ -394,7 +544,7 @@ cudaError_t launch_moments(int prec, const LatticeParams& P, const void* f, doub
     PLBM_MOM_Q(5, 1)
 #undef PLBM_MOM_Q
     PLBM_DISPATCH(prec, (k_moments<S><<<grid, 128, 0, stream>>>(P, static_cast<const S*>(f), rho,
-                                                                ux, uy, theta)));
+                                                                ux, uy, theta, y0)));
     return cudaGetLastError();
 }
 

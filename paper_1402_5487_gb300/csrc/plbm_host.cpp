@@ -42,8 +42,17 @@ struct Handle {
     plbm_status sticky = PLBM_OK;
     bool initialised = false;
     bool in_batch = false;     // owned by a plbm_batch: not destroyable on its own
+    // Host-pointer init/moments: a staging buffer kept after first use, and a copy
+    // stream that overlaps the transfer of one band of rows with the kernel on another.
+    void* stage = nullptr;
+    size_t stage_bytes = 0;
+    cudaStream_t xfer = nullptr;
+    cudaEvent_t xev[8] = {};
     char err[512] = "";
 };
+
+constexpr int kXferChunks = 8;       // row bands of a pipelined host transfer
+constexpr size_t kXferMinNodes = 1u << 18;   // smaller lattices move in one band
 
 void set_err(Handle* h, const char* fmt, ...) {
     char buf[512];
@@ -234,6 +243,13 @@ plbm_status usable(Handle* h, bool need_init = true) {
 void free_handle(Handle* h) {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
+    if (h->xfer) {
+        cudaStreamSynchronize(h->xfer);
+        for (cudaEvent_t e : h->xev)
+            if (e) cudaEventDestroy(e);
+        cudaStreamDestroy(h->xfer);
+    }
+    if (h->stage) cudaFree(h->stage);
     if (h->owns_ws && h->ws) cudaFree(h->ws);
     if (h->host_buf) cudaFreeHost(h->host_buf);
     delete h;
@@ -244,6 +260,45 @@ plbm_status read_status(Handle* h, unsigned* bits) {
     CK(cudaStreamSynchronize(h->stream));
     std::memcpy(bits, h->host_buf + 8, sizeof(unsigned));
     return PLBM_OK;
+}
+
+// Staging buffer of at least `bytes` and the copy stream with its events (made
+// on first use; the previous host-pointer call has synchronised, so the buffer
+// is idle).
+#define XCK(call)                                                                      \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            set_err(h, "%s failed: %s", #call, cudaGetErrorString(e_));                \
+            h->sticky = PLBM_E_CUDA;                                                   \
+            return PLBM_E_CUDA;                                                        \
+        }                                                                              \
+    } while (0)
+
+plbm_status ensure_xfer(Handle* h, size_t bytes) {
+    if (!h->xfer) {
+        XCK(cudaStreamCreateWithFlags(&h->xfer, cudaStreamNonBlocking));
+        for (cudaEvent_t& e : h->xev) XCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    if (h->stage_bytes < bytes) {
+        if (h->stage) XCK(cudaFree(h->stage));
+        h->stage = nullptr;
+        h->stage_bytes = 0;
+        if (cudaMalloc(&h->stage, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            h->stage = nullptr;
+            set_err(h, "staging buffer of %zu bytes: out of device memory", bytes);
+            return PLBM_E_NOMEM;
+        }
+        h->stage_bytes = bytes;
+    }
+    return PLBM_OK;
+}
+
+// Row bands [y0, y1) of a pipelined transfer of an ny-row lattice.
+int xfer_bands(const Handle* h) {
+    const size_t n = (size_t)h->P.nx * h->P.ny;
+    return (n >= kXferMinNodes && h->P.ny >= kXferChunks) ? kXferChunks : 1;
 }
 
 // Temporary device buffer for host<->device staging, stream-ordered.
@@ -516,31 +571,35 @@ plbm_status plbm_init(plbm_handle hh, const double* rho, const double* ux, const
         return PLBM_E_ARG;
     }
     const size_t n = (size_t)h->P.nx * h->P.ny;
-    const double *d_rho = rho, *d_ux = ux, *d_uy = uy, *d_th = theta;
-    Staging stg;
-    stg.s = h->stream;
-    if (!on_device) {
-        CK(cudaMallocAsync(&stg.p, 4 * n * sizeof(double), h->stream));
-        double* base = static_cast<double*>(stg.p);
-        CK(cudaMemcpyAsync(base, rho, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-        CK(cudaMemcpyAsync(base + n, ux, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-        d_rho = base;
-        d_ux = base + n;
-        d_uy = nullptr;
-        d_th = nullptr;
-        if (uy && h->P.dim == 2) {
-            CK(cudaMemcpyAsync(base + 2 * n, uy, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-            d_uy = base + 2 * n;
-        }
-        if (theta) {
-            CK(cudaMemcpyAsync(base + 3 * n, theta, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-            d_th = base + 3 * n;
-        }
-    }
     h->cur = 0;
-    CK(plbm::launch_init(h->prec, h->P, d_rho, d_ux, d_uy, d_th, h->f[0], h->stream));
-    CK(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
-    if (!on_device) CK(cudaStreamSynchronize(h->stream));
+    if (on_device) {
+        CK(plbm::launch_init(h->prec, h->P, rho, ux, uy, theta, h->f[0], h->stream));
+        CK(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
+    } else {
+        // Band k of the four fields is copied on the copy stream while the kernel
+        // initialises band k - 1 on the handle's stream.
+        st = ensure_xfer(h, 4 * n * sizeof(double));
+        if (st != PLBM_OK) return st;
+        double* base = static_cast<double*>(h->stage);
+        const double* src[4] = {rho, ux, (uy && h->P.dim == 2) ? uy : nullptr, theta};
+        const double* dev[4];
+        for (int k = 0; k < 4; ++k) dev[k] = src[k] ? base + k * n : nullptr;
+        const int bands = xfer_bands(h);
+        const int ny = h->P.ny, nx = h->P.nx;
+        for (int b = 0; b < bands; ++b) {
+            const int y0 = (int)((long long)ny * b / bands), y1 = (int)((long long)ny * (b + 1) / bands);
+            const size_t off = (size_t)y0 * nx, cnt = (size_t)(y1 - y0) * nx;
+            for (int k = 0; k < 4; ++k)
+                if (src[k])
+                    CK(cudaMemcpyAsync(base + k * n + off, src[k] + off, cnt * sizeof(double),
+                                       cudaMemcpyHostToDevice, h->xfer));
+            CK(cudaEventRecord(h->xev[b], h->xfer));
+            CK(cudaStreamWaitEvent(h->stream, h->xev[b], 0));
+            CK(plbm::launch_init(h->prec, h->P, dev[0], dev[1], dev[2], dev[3], h->f[0], h->stream, y0, y1));
+        }
+        CK(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+    }
     h->steps = 0;
     h->initialised = true;
     return PLBM_OK;
@@ -595,16 +654,28 @@ plbm_status plbm_moments(plbm_handle hh, double* rho, double* ux, double* uy, do
         CK(plbm::launch_moments(h->prec, h->P, h->f[h->cur], rho, ux, uy, theta, h->stream));
         return PLBM_OK;
     }
-    Staging stg;
-    stg.s = h->stream;
-    CK(cudaMallocAsync(&stg.p, 4 * n * sizeof(double), h->stream));
-    double* b = static_cast<double*>(stg.p);
-    CK(plbm::launch_moments(h->prec, h->P, h->f[h->cur], rho ? b : nullptr, ux ? b + n : nullptr,
-                            uy ? b + 2 * n : nullptr, theta ? b + 3 * n : nullptr, h->stream));
+    // The kernel fills band k on the handle's stream while band k - 1 is copied
+    // to the host on the copy stream.
+    st = ensure_xfer(h, 4 * n * sizeof(double));
+    if (st != PLBM_OK) return st;
+    double* base = static_cast<double*>(h->stage);
     double* outs[4] = {rho, ux, uy, theta};
-    for (int k = 0; k < 4; ++k)
-        if (outs[k]) CK(cudaMemcpyAsync(outs[k], b + k * n, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
+    double* dev[4];
+    for (int k = 0; k < 4; ++k) dev[k] = outs[k] ? base + k * n : nullptr;
+    const int bands = xfer_bands(h);
+    const int ny = h->P.ny, nx = h->P.nx;
+    for (int b = 0; b < bands; ++b) {
+        const int y0 = (int)((long long)ny * b / bands), y1 = (int)((long long)ny * (b + 1) / bands);
+        const size_t off = (size_t)y0 * nx, cnt = (size_t)(y1 - y0) * nx;
+        CK(plbm::launch_moments(h->prec, h->P, h->f[h->cur], dev[0], dev[1], dev[2], dev[3], h->stream, y0, y1));
+        CK(cudaEventRecord(h->xev[b], h->stream));
+        CK(cudaStreamWaitEvent(h->xfer, h->xev[b], 0));
+        for (int k = 0; k < 4; ++k)
+            if (outs[k])
+                CK(cudaMemcpyAsync(outs[k] + off, base + k * n + off, cnt * sizeof(double),
+                                   cudaMemcpyDeviceToHost, h->xfer));
+    }
+    CK(cudaStreamSynchronize(h->xfer));
     return PLBM_OK;
 }
 

@@ -171,10 +171,13 @@ void set_thread_error(const char* msg);
 // on `stream` and return the launch error.
 cudaError_t launch_step(int prec, const LatticeParams& P, const void* src, void* dst,
                         bool reduce, cudaStream_t stream);
+// Rows [y0, y1) (y1 < 0: to the last row); field pointers index the whole lattice.
 cudaError_t launch_init(int prec, const LatticeParams& P, const double* rho, const double* ux,
-                        const double* uy, const double* theta, void* f, cudaStream_t stream);
+                        const double* uy, const double* theta, void* f, cudaStream_t stream, int y0 = 0,
+                        int y1 = -1);
 cudaError_t launch_moments(int prec, const LatticeParams& P, const void* f, double* rho,
-                           double* ux, double* uy, double* theta, cudaStream_t stream);
+                           double* ux, double* uy, double* theta, cudaStream_t stream, int y0 = 0,
+                           int y1 = -1);
 // Three-dimensional lattices (plbm_step3.cu): storage [q][nz][ny][pitch].
 long long reduce3_blocks(const LatticeParams& P);
 cudaError_t launch_step3(int prec, const LatticeParams& P, const void* src, void* dst, cudaStream_t s);
