@@ -44,18 +44,31 @@ KERNEL_NAME = {"f32": "k_stream_collide_pair<float>", "f16dev": "k_stream_collid
                "bf16dev": "k_stream_collide_pair<__nv_bfloat16>", "f64": "k_stream_collide<double,5,2>"}
 
 
+def kernel_fingerprint(sources):
+    """SHA-256 over the source text a kernel is compiled from.  An entry is a path,
+    or [path, first line, last line] for the part of a shared header the kernel
+    uses (the text from the first occurrence of one to the next of the other)."""
+    import hashlib
+    h = hashlib.sha256()
+    for src in sources:
+        path, part = (src, None) if isinstance(src, str) else (src[0], src[1:])
+        with open(os.path.join(ROOT, path), "rb") as fh:
+            text = fh.read()
+        if part:
+            a = text.index(part[0].encode())
+            b = text.index(part[1].encode(), a) + len(part[1])
+            text = text[a:b]
+        h.update(text)
+    return h.hexdigest()
+
+
 def read_traffic(prec):
     """DRAM bytes per launch from the committed ncu capture, or None when absent or
-    when the kernel sources changed since the counters were taken."""
-    import hashlib
+    when the kernel's sources changed since the counters were taken."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
             d = json.load(fh)[KERNEL_NAME[prec]]
-        h = hashlib.sha256()
-        for f in d["kernel_sources"]:
-            with open(os.path.join(ROOT, f), "rb") as fh:
-                h.update(fh.read())
-        if h.hexdigest() != d["kernel_sources_sha256"]:
+        if kernel_fingerprint(d["kernel_sources"]) != d["kernel_sources_sha256"]:
             return None
         return float(d["bytes_per_launch"])
     except Exception:
