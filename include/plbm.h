@@ -283,12 +283,26 @@ plbm_status plbm_batch_check(plbm_batch b, int *first_bad);
  * (0 = as many as fit). */
 plbm_status plbm_batch_set_config(plbm_batch b, int block_x, int ctas_per_sm);
 
+/* Order in which the persistent CTAs take the tiles (all instances' tiles form
+ * one list, instance by instance, pair row by pair row).  CONTIGUOUS: CTA c takes
+ * the range [c T / G, (c + 1) T / G) of the T tiles (G CTAs) and reloads an
+ * instance's parameters only at the few instance boundaries it meets.
+ * INTERLEAVED (default): CTA c takes tiles c, c + G, c + 2G, ..., so the tiles in
+ * flight at any moment are neighbours in memory, as in a plain grid; the
+ * instance of each tile comes from a per-tile table.  Errors: PLBM_E_ARG. */
+#define PLBM_BATCH_ORDER_CONTIGUOUS 0
+#define PLBM_BATCH_ORDER_INTERLEAVED 1
+plbm_status plbm_batch_set_order(plbm_batch b, int order);
+/* Current order, or -1 for a NULL batch. */
+int plbm_batch_get_order(plbm_batch b);
+
 /* Current launch shape and the occupancy limit for it. */
 plbm_status plbm_batch_info(plbm_batch b, int *ninst, int *total_tiles, int *block_x, int *ctas,
                             int *max_ctas_per_sm);
 
-/* Autotuner: times steps_per_trial persistent steps for every block_x and every
- * ctas_per_sm up to the occupancy limit and keeps the fastest.  It advances the
+/* Autotuner: times steps_per_trial persistent steps for both orders, every
+ * block_x and every ctas_per_sm up to the occupancy limit and keeps the
+ * fastest (plbm_batch_get_order reads the order it chose).  It advances the
  * instances (initialise them again afterwards if the state matters). */
 plbm_status plbm_batch_tune(plbm_batch b, int steps_per_trial, int *best_block_x, int *best_ctas_per_sm,
                             double *best_ms_per_step);

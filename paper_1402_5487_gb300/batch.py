@@ -30,6 +30,7 @@ PER_INSTANCE = 2
 PER_INSTANCE_GRAPH = 3
 MODES = {"persistent": PERSISTENT, "persistent_graph": PERSISTENT_GRAPH,
          "per_instance": PER_INSTANCE, "per_instance_graph": PER_INSTANCE_GRAPH}
+ORDERS = {"contiguous": 0, "interleaved": 1}   # PLBM_BATCH_ORDER_*
 
 
 def admissible(v, omega, theta0, u_max, nk=48):
@@ -112,6 +113,14 @@ class Batch:
     def set_config(self, block_x, ctas_per_sm):
         self._ok(plbm.lib().plbm_batch_set_config(self.b, int(block_x), int(ctas_per_sm)))
 
+    def set_order(self, order):
+        """"contiguous" or "interleaved" tile order of the persistent kernel."""
+        self._ok(plbm.lib().plbm_batch_set_order(self.b, ORDERS[order] if isinstance(order, str) else int(order)))
+
+    @property
+    def order(self):
+        return {v: k for k, v in ORDERS.items()}[plbm.lib().plbm_batch_get_order(self.b)]
+
     def info(self):
         vals = [ctypes.c_int() for _ in range(5)]
         self._ok(plbm.lib().plbm_batch_info(self.b, *[ctypes.byref(v) for v in vals]))
@@ -132,11 +141,12 @@ class Batch:
         if key in cache:
             c = cache[key]
             self.set_config(c["block_x"], c["ctas_per_sm"])
+            self.set_order(c.get("order", "contiguous"))
             return dict(c, cached=True)
         bx, cps, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
         self._ok(plbm.lib().plbm_batch_tune(self.b, int(steps_per_trial), ctypes.byref(bx), ctypes.byref(cps),
                                             ctypes.byref(ms)))
-        c = {"block_x": bx.value, "ctas_per_sm": cps.value, "ms_per_step": ms.value}
+        c = {"block_x": bx.value, "ctas_per_sm": cps.value, "order": self.order, "ms_per_step": ms.value}
         if cache_path:
             cache[key] = c
             d = os.path.dirname(os.path.abspath(cache_path))

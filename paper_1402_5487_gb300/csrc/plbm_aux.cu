@@ -13,19 +13,19 @@ cudaError_t launch_step_f32(const LatticeParams&, const void*, void*, bool, cuda
 cudaError_t launch_step_f16(const LatticeParams&, const void*, void*, bool, cudaStream_t);
 cudaError_t launch_step_bf16(const LatticeParams&, const void*, void*, bool, cudaStream_t);
 
-cudaError_t launch_batch_f32(const PairParams*, int, int, int, int, int, cudaStream_t);
-cudaError_t launch_batch_f16(const PairParams*, int, int, int, int, int, cudaStream_t);
-cudaError_t launch_batch_bf16(const PairParams*, int, int, int, int, int, cudaStream_t);
+cudaError_t launch_batch_f32(const PairParams*, int, int, int, int, int, const unsigned short*, cudaStream_t);
+cudaError_t launch_batch_f16(const PairParams*, int, int, int, int, int, const unsigned short*, cudaStream_t);
+cudaError_t launch_batch_bf16(const PairParams*, int, int, int, int, int, const unsigned short*, cudaStream_t);
 cudaError_t batch_occupancy_f32(int, int*);
 cudaError_t batch_occupancy_f16(int, int*);
 cudaError_t batch_occupancy_bf16(int, int*);
 
 cudaError_t launch_batch(int prec, const PairParams* inst, int ninst, int total_tiles, int block_x,
-                         int ctas, int parity, cudaStream_t stream) {
+                         int ctas, int parity, const unsigned short* tile_inst, cudaStream_t stream) {
     switch (prec) {
-        case kF32: return launch_batch_f32(inst, ninst, total_tiles, block_x, ctas, parity, stream);
-        case kF16Dev: return launch_batch_f16(inst, ninst, total_tiles, block_x, ctas, parity, stream);
-        case kBF16Dev: return launch_batch_bf16(inst, ninst, total_tiles, block_x, ctas, parity, stream);
+        case kF32: return launch_batch_f32(inst, ninst, total_tiles, block_x, ctas, parity, tile_inst, stream);
+        case kF16Dev: return launch_batch_f16(inst, ninst, total_tiles, block_x, ctas, parity, tile_inst, stream);
+        case kBF16Dev: return launch_batch_bf16(inst, ninst, total_tiles, block_x, ctas, parity, tile_inst, stream);
     }
     return cudaErrorInvalidValue;
 }

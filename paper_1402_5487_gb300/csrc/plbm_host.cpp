@@ -891,6 +891,9 @@ struct Batch {
     char* ws = nullptr;
     plbm::PairParams* d_table = nullptr;
     std::vector<plbm::PairParams> table;
+    unsigned short* d_tile_inst = nullptr;   // instance of every global tile (interleaved order)
+    size_t max_tiles = 0;                    // tiles at the smallest block_x
+    int order = PLBM_BATCH_ORDER_INTERLEAVED;
     int block_x = 128, ctas_per_sm = 0, sms = 0, total_tiles = 0;
     cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [kind][start parity]
     long long steps = 0;
@@ -942,8 +945,16 @@ plbm_status batch_table(Batch* b) {
         tile += Q.tiles_x * Q.half_ny;
     }
     b->total_tiles = tile;
+    std::vector<unsigned short> ti((size_t)tile);
+    for (size_t i = 0; i < b->inst.size(); ++i) {
+        const plbm::PairParams& Q = b->table[i];
+        std::fill(ti.begin() + Q.tile_begin, ti.begin() + Q.tile_begin + Q.tiles_x * Q.half_ny,
+                  (unsigned short)i);
+    }
     BCK(cudaMemcpyAsync(b->d_table, b->table.data(), sizeof(plbm::PairParams) * b->table.size(),
                         cudaMemcpyHostToDevice, b->stream));
+    BCK(cudaMemcpyAsync(b->d_tile_inst, ti.data(), sizeof(unsigned short) * ti.size(), cudaMemcpyHostToDevice,
+                        b->stream));
     BCK(cudaStreamSynchronize(b->stream));
     drop_graphs(b);
     return PLBM_OK;
@@ -966,8 +977,9 @@ void free_batch(Batch* b) {
 // One step of every instance with the chosen launch scheme (no graph).
 plbm_status batch_launch(Batch* b, int scheme, int parity, int ctas) {
     if (scheme == 0) {
-        BCK(plbm::launch_batch(b->prec, b->d_table, (int)b->inst.size(), b->total_tiles, b->block_x,
-                               ctas, parity, b->stream));
+        BCK(plbm::launch_batch(b->prec, b->d_table, (int)b->inst.size(), b->total_tiles, b->block_x, ctas,
+                               parity, b->order == PLBM_BATCH_ORDER_INTERLEAVED ? b->d_tile_inst : nullptr,
+                               b->stream));
     } else {
         for (Handle* h : b->inst)
             BCK(plbm::launch_step(b->prec, h->P, h->f[parity], h->f[parity ^ 1], false, b->stream));
@@ -1009,6 +1021,15 @@ plbm_status plbm_batch_create(const plbm_desc* descs, int n, void* stream, plbm_
     }
     const size_t table_off = total;
     total += align_up(sizeof(plbm::PairParams) * n, 256);
+    for (int i = 0; i < n; ++i)
+        b->max_tiles += (size_t)((descs[i].nx + 63) / 64) * (size_t)(descs[i].ny / 2);
+    const size_t tile_inst_off = total;
+    total += align_up(sizeof(unsigned short) * std::max<size_t>(b->max_tiles, 1), 256);
+    if (n > 65535) {
+        batch_err(b, "at most 65535 instances");
+        delete b;
+        return PLBM_E_ARG;
+    }
     if (cudaSetDevice(b->device) != cudaSuccess) {
         batch_err(b, "cudaSetDevice(%d) failed", b->device);
         delete b;
@@ -1034,6 +1055,7 @@ plbm_status plbm_batch_create(const plbm_desc* descs, int n, void* stream, plbm_
     }
     b->ws = static_cast<char*>(p);
     b->d_table = reinterpret_cast<plbm::PairParams*>(b->ws + table_off);
+    b->d_tile_inst = reinterpret_cast<unsigned short*>(b->ws + tile_inst_off);
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
     b->inst.assign(n, nullptr);
     b->table.resize(n);
@@ -1171,6 +1193,22 @@ plbm_status plbm_batch_set_config(plbm_batch bb, int block_x, int ctas_per_sm) {
     return batch_table(b);
 }
 
+plbm_status plbm_batch_set_order(plbm_batch bb, int order) {
+    Batch* b = reinterpret_cast<Batch*>(bb);
+    if (!b || (order != PLBM_BATCH_ORDER_CONTIGUOUS && order != PLBM_BATCH_ORDER_INTERLEAVED)) {
+        batch_err(b, "order must be PLBM_BATCH_ORDER_CONTIGUOUS or PLBM_BATCH_ORDER_INTERLEAVED");
+        return PLBM_E_ARG;
+    }
+    b->order = order;
+    drop_graphs(b);
+    return PLBM_OK;
+}
+
+int plbm_batch_get_order(plbm_batch bb) {
+    Batch* b = reinterpret_cast<Batch*>(bb);
+    return b ? b->order : -1;
+}
+
 plbm_status plbm_batch_info(plbm_batch bb, int* ninst, int* total_tiles, int* block_x, int* ctas,
                             int* max_ctas_per_sm) {
     Batch* b = reinterpret_cast<Batch*>(bb);
@@ -1198,13 +1236,15 @@ plbm_status plbm_batch_tune(plbm_batch bb, int steps_per_trial, int* best_block_
     BCK(cudaEventCreate(&e0));
     BCK(cudaEventCreate(&e1));
     double best = 1e300;
-    int bx_best = 128, cps_best = 0;
+    int bx_best = 128, cps_best = 0, order_best = PLBM_BATCH_ORDER_INTERLEAVED;
     const int bxs[3] = {64, 128, 256};
+    for (int order : {PLBM_BATCH_ORDER_CONTIGUOUS, PLBM_BATCH_ORDER_INTERLEAVED})
     for (int bx : bxs) {
         int occ = 0;
         if (plbm::batch_occupancy(b->prec, bx, &occ) != cudaSuccess || occ < 1) continue;
         for (int cps = 1; cps <= occ; ++cps) {
             plbm_status st = plbm_batch_set_config(bb, bx, cps);
+            if (st == PLBM_OK) st = plbm_batch_set_order(bb, order);
             if (st != PLBM_OK) return st;
             st = plbm_batch_step(bb, 2, PLBM_BATCH_PERSISTENT);
             if (st != PLBM_OK) return st;
@@ -1220,12 +1260,14 @@ plbm_status plbm_batch_tune(plbm_batch bb, int steps_per_trial, int* best_block_
                 best = per;
                 bx_best = bx;
                 cps_best = cps;
+                order_best = order;
             }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     plbm_status st = plbm_batch_set_config(bb, bx_best, cps_best);
+    if (st == PLBM_OK) st = plbm_batch_set_order(bb, order_best);
     if (st != PLBM_OK) return st;
     if (best_block_x) *best_block_x = bx_best;
     if (best_ctas_per_sm) *best_ctas_per_sm = cps_best;

@@ -203,8 +203,11 @@ cudaError_t launch_set_populations(int prec, const LatticeParams& P, const doubl
 
 // Batched persistent step over the instances of `inst` (device array, tile_begin
 // ascending); block_x in {64, 128, 256}; ctas persistent CTAs.
+// Persistent batched step.  tile_inst == nullptr: CTA c walks the contiguous tile
+// range [c * per_cta, (c + 1) * per_cta); otherwise the tiles c, c + ctas, ...
+// with tile_inst[t] the instance of global tile t.
 cudaError_t launch_batch(int prec, const PairParams* inst, int ninst, int total_tiles, int block_x,
-                         int ctas, int parity, cudaStream_t stream);
+                         int ctas, int parity, const unsigned short* tile_inst, cudaStream_t stream);
 cudaError_t batch_occupancy(int prec, int block_x, int* blocks_per_sm);
 
 // Number of blocks of a step launch (row-paired kernels cover two rows per block row).

@@ -271,10 +271,40 @@ cudaError_t launch_step_pair_t(const LatticeParams& L, const void* src, void* ds
 // ---------------------------------------------------------------------------
 template <typename S, int BX>
 __global__ void __launch_bounds__(BX)
-k_batch_pair(const PairParams* __restrict__ inst, int ninst, int total_tiles, int per_cta, int parity) {
+k_batch_pair(const PairParams* __restrict__ inst, int ninst, int total_tiles, int per_cta, int parity,
+             const unsigned short* __restrict__ tile_inst) {
     using V = typename PairStore<S>::V;
     __shared__ PairParams sp;
     __shared__ int s_inst;
+    constexpr int kWords = (int)(sizeof(PairParams) / sizeof(int));
+    NodeDiag d;
+    if (tile_inst) {
+        // Interleaved order: CTA c takes tiles c, c + G, c + 2G, ... (G CTAs), so the
+        // tiles in flight at any moment are neighbours in memory, as in a plain grid.
+        int cur = -1;
+        int t = blockIdx.x;
+        int i_next = t < total_tiles ? tile_inst[t] : 0;
+        for (; t < total_tiles; t += gridDim.x) {
+            const int i = i_next;
+            if (t + (int)gridDim.x < total_tiles) i_next = tile_inst[t + gridDim.x];
+            if (i != cur) {  // block-uniform
+                __syncthreads();
+                for (int k = threadIdx.x; k < kWords; k += BX)
+                    reinterpret_cast<int*>(&sp)[k] = reinterpret_cast<const int*>(&inst[i])[k];
+                __syncthreads();
+                cur = i;
+            }
+            const int local = t - sp.tile_begin;
+            const int r = local / sp.tiles_x;
+            const int x = (local - r * sp.tiles_x) * BX + threadIdx.x;
+            if (x < sp.nx) {
+                const V* src = static_cast<const V*>(sp.f[parity]);
+                V* dst = static_cast<V*>(sp.f[parity ^ 1]);
+                pair_node<S, false>(sp, src, dst, x, r, d);
+            }
+        }
+        return;
+    }
     const int t0 = blockIdx.x * per_cta;
     const int t1 = min(t0 + per_cta, total_tiles);
     if (t0 >= t1) return;
@@ -290,12 +320,10 @@ k_batch_pair(const PairParams* __restrict__ inst, int ninst, int total_tiles, in
     __syncthreads();
     int i = s_inst;
     int next_begin = (i + 1 < ninst) ? inst[i + 1].tile_begin : total_tiles;
-    constexpr int kWords = (int)(sizeof(PairParams) / sizeof(int));
     static_assert(sizeof(PairParams) % sizeof(int) == 0, "PairParams copy granularity");
     for (int k = threadIdx.x; k < kWords; k += BX)
         reinterpret_cast<int*>(&sp)[k] = reinterpret_cast<const int*>(&inst[i])[k];
     __syncthreads();
-    NodeDiag d;
     for (int t = t0; t < t1; ++t) {
         if (t >= next_begin) {  // block-uniform: move to the instance holding tile t
             while (t >= next_begin) {
@@ -320,12 +348,12 @@ k_batch_pair(const PairParams* __restrict__ inst, int ninst, int total_tiles, in
 
 template <typename S>
 cudaError_t launch_batch_pair_t(const PairParams* inst, int ninst, int total_tiles, int block_x, int ctas,
-                                int parity, cudaStream_t stream) {
+                                int parity, const unsigned short* tile_inst, cudaStream_t stream) {
     const int per_cta = (total_tiles + ctas - 1) / ctas;
     switch (block_x) {
-        case 64: k_batch_pair<S, 64><<<ctas, 64, 0, stream>>>(inst, ninst, total_tiles, per_cta, parity); break;
-        case 128: k_batch_pair<S, 128><<<ctas, 128, 0, stream>>>(inst, ninst, total_tiles, per_cta, parity); break;
-        case 256: k_batch_pair<S, 256><<<ctas, 256, 0, stream>>>(inst, ninst, total_tiles, per_cta, parity); break;
+        case 64: k_batch_pair<S, 64><<<ctas, 64, 0, stream>>>(inst, ninst, total_tiles, per_cta, parity, tile_inst); break;
+        case 128: k_batch_pair<S, 128><<<ctas, 128, 0, stream>>>(inst, ninst, total_tiles, per_cta, parity, tile_inst); break;
+        case 256: k_batch_pair<S, 256><<<ctas, 256, 0, stream>>>(inst, ninst, total_tiles, per_cta, parity, tile_inst); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -11,8 +11,8 @@ cudaError_t launch_step_f16(const LatticeParams& P, const void* src, void* dst, 
     return launch_step_t<__half>(P, src, dst, reduce, stream);
 }
 cudaError_t launch_batch_f16(const PairParams* inst, int ninst, int total_tiles, int block_x, int ctas,
-                             int parity, cudaStream_t stream) {
-    return launch_batch_pair_t<__half>(inst, ninst, total_tiles, block_x, ctas, parity, stream);
+                             int parity, const unsigned short* tile_inst, cudaStream_t stream) {
+    return launch_batch_pair_t<__half>(inst, ninst, total_tiles, block_x, ctas, parity, tile_inst, stream);
 }
 cudaError_t batch_occupancy_f16(int block_x, int* blocks_per_sm) {
     return batch_occupancy_t<__half>(block_x, blocks_per_sm);

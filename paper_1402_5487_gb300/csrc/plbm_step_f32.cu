@@ -11,8 +11,8 @@ cudaError_t launch_step_f32(const LatticeParams& P, const void* src, void* dst, 
     return launch_step_t<float>(P, src, dst, reduce, stream);
 }
 cudaError_t launch_batch_f32(const PairParams* inst, int ninst, int total_tiles, int block_x, int ctas,
-                             int parity, cudaStream_t stream) {
-    return launch_batch_pair_t<float>(inst, ninst, total_tiles, block_x, ctas, parity, stream);
+                             int parity, const unsigned short* tile_inst, cudaStream_t stream) {
+    return launch_batch_pair_t<float>(inst, ninst, total_tiles, block_x, ctas, parity, tile_inst, stream);
 }
 cudaError_t batch_occupancy_f32(int block_x, int* blocks_per_sm) {
     return batch_occupancy_t<float>(block_x, blocks_per_sm);

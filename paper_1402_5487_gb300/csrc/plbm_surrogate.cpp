@@ -540,7 +540,7 @@ plbm_status plbm_sur_advance(plbm_surrogate h, plbm_handle* hs, int n, int K, do
         if (plbm::batch_occupancy(bprec, kBX, &occ) != cudaSuccess || occ < 1) occ = 1;
         for (int k = 0; k < K; ++k)
             SCK(plbm::launch_batch(bprec, s->fb_table, (int)table.size(), tiles, kBX, s->sms * occ, k & 1,
-                                   s->stream));
+                                   nullptr, s->stream));
         for (int b : batched) {
             if (K & 1) *views[b].cur ^= 1;
             *views[b].steps += K;

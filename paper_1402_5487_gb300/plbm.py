@@ -95,6 +95,8 @@ SIGNATURES = {
     "plbm_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_long, ctypes.c_int]),
     "plbm_batch_check": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "plbm_batch_set_config": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "plbm_batch_set_order": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "plbm_batch_get_order": (ctypes.c_int, [ctypes.c_void_p]),
     "plbm_batch_info": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int)] * 5),
     "plbm_batch_tune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_int), _D]),

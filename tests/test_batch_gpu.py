@@ -23,10 +23,12 @@ def small_instances():
     return inst
 
 
-def _run(instances, mode, steps, prec="f32", config=None):
+def _run(instances, mode, steps, prec="f32", config=None, order=None):
     b = B.Batch(instances, prec=prec)
     if config:
         b.set_config(*config)
+    if order:
+        b.set_order(order)
     b.init()
     b.step(steps, mode)
     pops = [s.get_populations() for s in b.solvers]
@@ -43,9 +45,10 @@ def test_launch_schemes_bit_identical(small_instances):
         for a, b in zip(got, ref):
             assert np.array_equal(a, b), mode
     for cfg in ((64, 1), (256, 2), (128, 0)):
-        got, _ = _run(small_instances, "persistent_graph", 7, config=cfg)
-        for a, b in zip(got, ref):
-            assert np.array_equal(a, b), cfg
+        for order in ("contiguous", "interleaved"):
+            got, _ = _run(small_instances, "persistent_graph", 7, config=cfg, order=order)
+            for a, b in zip(got, ref):
+                assert np.array_equal(a, b), (cfg, order)
 
 
 def test_batch_equals_single_handles(small_instances):
