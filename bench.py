@@ -199,17 +199,23 @@ def run_variant3(torch, n, prec, steps, warmup):
             "status": "ok" if st == 0 else "diverged"}
 
 
-def run_batched(torch, steps=100, warmup=4, n=256):
-    """Batched sweep of n admissible instances (FP32): persistent graph vs per-instance launches."""
+def run_batched(torch, steps=100, warmup=4, n=256, config=None):
+    """Batched sweep of n admissible instances (FP32): persistent graph vs per-instance launches.
+    config = (block_x, ctas_per_sm, order) fixes the persistent launch instead of autotuning."""
     from paper_1402_5487_gb300 import batch as B
     t0 = time.perf_counter()
     inst, stats = B.draw_instances(n)
     t_draw = time.perf_counter() - t0
     b = B.Batch(inst, prec="f32")
     b.init()
-    cache = os.path.join(ROOT, "paper_1402_5487_gb300", "_build", "autotune.json")
-    tuned = b.autotune(steps_per_trial=6, cache_path=cache)
-    b.init()
+    if config:
+        b.set_config(int(config[0]), int(config[1]))
+        b.set_order(config[2])
+        tuned = {"block_x": int(config[0]), "ctas_per_sm": int(config[1]), "order": config[2], "fixed": True}
+    else:
+        cache = os.path.join(ROOT, "paper_1402_5487_gb300", "_build", "autotune.json")
+        tuned = b.autotune(steps_per_trial=6, cache_path=cache)
+        b.init()
     nodes = b.nodes
     out = {"instances": n, "nodes": nodes, "draw_seconds": t_draw, "acceptance": stats["acceptance"],
            "autotune": tuned, "launch": b.info()}
@@ -446,7 +452,8 @@ def run_case(torch, args):
     lattices (forward passes and Adam steps on seeded random tensors), the
     batched 256-instance sweep, or the D3Q125 shear layer on a size^3 grid."""
     if args.case == "batched":
-        return {"case": "batched", **run_batched(torch, steps=args.steps, warmup=args.warmup,
+        cfg = args.batch_config.split(",") if args.batch_config else None
+        return {"case": "batched", **run_batched(torch, steps=args.steps, warmup=args.warmup, config=cfg,
                                                  n=args.batch_instances)}
     if args.case == "longrun":
         return {"case": "longrun", "runs": run_longrun(torch, args.snapshots)}
@@ -547,6 +554,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-instances", type=int, default=256)
+    ap.add_argument("--batch-config", default=None,
+                    help="block_x,ctas_per_sm,order (contiguous|interleaved): fixed persistent launch "
+                         "instead of the autotuner (--case batched)")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--surrogate-train", type=int, default=2000, help="training trajectories")
     ap.add_argument("--surrogate-steps", type=int, default=6000, help="Adam steps")
