@@ -8,11 +8,13 @@
 // k_conv_ring<N, MODE> (64 input channels: the 64 -> 64 layers and the 64 -> 4
 // output layer with N = 16, four columns used) is warp-specialised and
 // pipelined:
-//   * warps 0..2 stream input row segments (pixels x0 - 1 .. x0 + 128,
-//     wrapped) into a ring of shared-memory slots with cp.async, each warp one
-//     row in flight.  A CTA owns a run of consecutive output rows of one column
-//     of tiles, so each input row is loaded once and serves the three taps ky
-//     of three output rows;
+//   * warps 0..2 stage input row segments (pixels x0 - 1 .. x0 + 128, wrapped)
+//     into a ring of shared-memory slots: lane 0 issues eight TMA tile copies
+//     (cp.async.bulk.tensor, one per 16-byte channel chunk) of the 128 pixels
+//     x0 .. x0 + 127, which complete on the slot's mbarrier by byte count, and
+//     16 lanes copy the two wrapped halo pixels.  A CTA owns a run of
+//     consecutive output rows of one column of tiles, so each input row is
+//     loaded once and serves the three taps ky of three output rows;
 //   * one thread each of warps 3 and 4 issues the 36 MMAs of alternate tiles
 //     into eight TMEM accumulators (a single issuing thread that waits on
 //     barriers between tiles leaves the tensor pipe idle; two keep it fed) and
@@ -33,8 +35,10 @@
 // Every wait is bounded by the global timer: on a timeout a kernel records it
 // in *err, stops issuing work, waits (bounded) for the MMAs it issued, frees
 // its tensor memory and returns.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <cstdint>
 
@@ -149,6 +153,21 @@ __device__ __forceinline__ bool bar_wait_drain(uint32_t bar, uint32_t parity) {
     }
 }
 
+__device__ __forceinline__ void bar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}\n" ::"r"(bar),
+                 "r"(bytes)
+                 : "memory");
+}
+// TMA tile copy of a 5D box to shared memory, completing `bar` by byte count.
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            int c4, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+        "%6}], [%7];\n" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+        : "memory");
+}
+
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
                  : "memory");
@@ -246,14 +265,18 @@ constexpr int kLoaders = 3;            // warps 0..2 load input rows
 constexpr int kIssuers = 2;            // warps 3, 4 issue the MMAs of alternate tiles
 constexpr int kRingThreads = 32 * (kLoaders + kIssuers + 4);  // warps 5..8 run the epilogue
 constexpr int kSegPix = kTile + 2;     // staged pixels per input row: x0 - 1 .. x0 + 128
-// One 16-byte channel chunk of every staged pixel, padded so that planes start
-// 64 bytes apart modulo 128: the loaders' 16-pixel x 2-chunk warp stores are
-// then free of bank conflicts.
-constexpr int kPlane = kSegPix * 16 + 32;  // 2112 bytes
-constexpr int kSeg = 8 * kPlane;       // 16896 bytes per staged row
+// One 16-byte channel chunk of every staged pixel (pixel p at 16 p).  A plane
+// starts 112 bytes into a 128-byte line, so pixel 1 (x0), the destination of
+// the TMA copy, is 128-byte aligned; planes are 17 lines apart.
+constexpr int kPlane = 17 * 128;       // 2176 bytes >= 130 pixels x 16 bytes
+constexpr int kPlaneOff = 112;
+constexpr int kSeg = 8 * kPlane;       // 17408 bytes per staged row
+static_assert(kSegPix * 16 <= kPlane && (kPlaneOff + 16) % 128 == 0 && kSeg % 128 == 0, "row slot layout");
 constexpr int kRing = 8;               // row slots
 static_assert(kRing >= 3 + kLoaders, "three rows feed the MMAs while every loader has one in flight");
-constexpr int kRingBytes = kRing * kSeg;
+constexpr uint32_t kRowTxBytes = 8 * kTile * 16;  // the eight TMA boxes of a row
+constexpr int kHaloLanes = 16;         // two wrapped pixels x 8 chunks
+constexpr int kRingBytes = kRing * kSeg + kPlaneOff;
 constexpr int kRingWOff = ((kRingBytes + 1023) / 1024) * 1024;  // weights after the ring, 1024-aligned
 constexpr int kRingBarBytes = 512 + 256;  // barriers, TMEM slot, abort flag, then 64 fp32 biases
 template <int N>
@@ -282,11 +305,13 @@ __device__ __forceinline__ Strip strip_at(int t, int t1, int H, int tiles_x) {
     return s;
 }
 
+// tmX views X as the 5D tensor [B][H][W][8 chunks][8 channels] (innermost last)
+// with a box of 128 pixels x 1 chunk.
 template <int N, int MODE>
 __global__ void __launch_bounds__(kRingThreads, 1)
-k_conv_ring(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ Wk,
-            const float* __restrict__ bias, const __nv_bfloat16* __restrict__ mask, void* __restrict__ Yv, int relu,
-            unsigned* __restrict__ err) {
+k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const __nv_bfloat16* __restrict__ X,
+            const __nv_bfloat16* __restrict__ Wk, const float* __restrict__ bias,
+            const __nv_bfloat16* __restrict__ mask, void* __restrict__ Yv, int relu, unsigned* __restrict__ err) {
     static_assert((N == 64 && MODE < 2) || (N == 16 && MODE == 2), "ring conv shapes");
     extern __shared__ unsigned char dsm_raw[];
     const uint32_t raw = s2u(dsm_raw);
@@ -309,7 +334,7 @@ k_conv_ring(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __nv
     const int t_end = min(ntiles, t_begin + per);
 
     if (tid == 0) {
-        for (int i = 0; i < kRing; ++i) bar_init(bar(kBarFull + i), 32);
+        for (int i = 0; i < kRing; ++i) bar_init(bar(kBarFull + i), 1 + kHaloLanes);
         for (int i = 0; i < kIssuers * kRing; ++i) bar_init(bar(kBarEmpty + i), 1);
         for (int i = 0; i < kAcc; ++i) {
             bar_init(bar(kBarTFull + i), 1);
@@ -334,8 +359,11 @@ k_conv_ring(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __nv
 
     if (warp < kLoaders) {
         // ---- loaders: rows y0 - 1 .. y0 + n of every strip; loader warp w takes
-        // the rows e = w mod kLoaders, one in flight, and publishes each (full
-        // barrier) as soon as its copies have landed ----
+        // the rows e = w mod kLoaders.  Lane 0 arms the slot's full barrier with
+        // the TMA byte count and issues the eight chunk copies; lanes 0..15 copy
+        // the halo pixels x0 - 1 and x0 + 128 (wrapped) and arrive after a proxy
+        // fence.  Nothing waits for the TMA data here: the issuers do. ----
+        if (lane == 0) asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tmX)) : "memory");
         uint32_t e = 0;
         bool ok = true;
         for (int t = t_begin; t < t_end && ok;) {
@@ -350,22 +378,28 @@ k_conv_ring(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __nv
                     break;
                 }
                 const int yy = wrapi(s.y0 - 1 + j, H);
-                const __nv_bfloat16* row = X + ((size_t)s.b * H + yy) * (size_t)W * kC;
-                const uint32_t seg = sRing + (uint32_t)slot * kSeg;
-                // lane pairs move one 32-byte sector (two chunks) of one pixel;
-                // a warp covers 16 consecutive pixels
-                for (int i = lane; i < kSegPix * 8; i += 32) {
-                    const int u = i >> 1, p = u % kSegPix, c = 2 * (u / kSegPix) + (i & 1);
-                    const int xx = wrapi(s.x0 - 1 + p, W);
-                    cp_async16(seg + c * kPlane + p * 16, row + (size_t)xx * kC + c * 8);
+                const uint32_t seg = sRing + (uint32_t)slot * kSeg + kPlaneOff;
+                const uint32_t full = bar(kBarFull + slot);
+                if (lane == 0) {
+                    bar_arrive_expect_tx(full, kRowTxBytes);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) tma_load_5d(seg + c * kPlane + 16, &tmX, 0, c, s.x0, yy, s.b, full);
                 }
-                asm volatile("cp.async.wait_all;\n" ::: "memory");
-                fence_async_smem();
-                bar_arrive(bar(kBarFull + slot));
+                if (lane < kHaloLanes) {
+                    const int right = lane >> 3, c = lane & 7;
+                    const int xx = wrapi(right ? s.x0 + kTile : s.x0 - 1, W);
+                    const uint4 v = __ldg(reinterpret_cast<const uint4*>(
+                        X + (((size_t)s.b * H + yy) * (size_t)W + xx) * kC + c * 8));
+                    const uint32_t dst = seg + c * kPlane + (right ? 16 * (kSegPix - 1) : 0);
+                    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n" ::"r"(dst), "r"(v.x), "r"(v.y),
+                                 "r"(v.z), "r"(v.w)
+                                 : "memory");
+                    fence_async_smem();
+                    bar_arrive(full);
+                }
             }
             t += s.n;
         }
-        asm volatile("cp.async.wait_all;\n" ::: "memory");
     } else if (warp < kLoaders + kIssuers) {
         if (lane == 0) {
             // ---- MMA issuers: issuer q computes the tiles with local index = q
@@ -374,7 +408,7 @@ k_conv_ring(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __nv
             // uses, so a release arrives once all of its earlier MMAs, including
             // every use of that row, have completed ----
             const int q = warp - kLoaders;
-            const uint64_t a0 = desc_plain(sRing, kPlane);
+            const uint64_t a0 = desc_plain(sRing + kPlaneOff, kPlane);
             const uint64_t b0 = desc_sw128(sW);
             const uint32_t empty0 = kBarEmpty + q * kRing;
             // entries below `ready` have been seen full; tiles below `freed` (of
@@ -508,7 +542,15 @@ k_conv_ring(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __nv
         }
     }
     __syncthreads();
-    if (tid == 0 && *abortp) atomicOr(err, 1u);
+    if (tid == 0 && *abortp) {
+        atomicOr(err, 1u);
+        // TMA copies the loaders issued may not have been waited for: give them
+        // time to land (they are plain copies) before the shared memory is released
+        const uint64_t t0 = gtime();
+        while (gtime() - t0 < 20000000ull) {
+        }
+    }
+    __syncthreads();
     if (warp == kLoaders) {
         tc_after_sync();
         tmem_free(tmem, kRingTmemCols);
@@ -676,10 +718,35 @@ static int tc_sms() {
     return n;
 }
 
+// Tensor map of a bf16 NHWC activation with 64 channels as [B][H][W][8][8]
+// (box: 8 channels x 1 chunk x 128 pixels), for the ring loaders' TMA copies.
+static cudaError_t encode_act_map(CUtensorMap* map, const void* X, int B, int H, int W) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q{};
+        void* fn = nullptr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    if (reinterpret_cast<uintptr_t>(X) % 16) return cudaErrorMisalignedAddress;
+    const cuuint64_t dims[5] = {8, 8, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+    const cuuint64_t strides[4] = {16, 128, (cuuint64_t)W * 128, (cuuint64_t)H * W * 128};
+    const cuuint32_t box[5] = {8, 1, (cuuint32_t)tc::kTile, 1, 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(X), dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <int N, int MODE>
 static cudaError_t launch_ring(int B, int H, int W, const void* X, const void* Wk, const float* bias,
                                const void* mask, void* Y, int relu, unsigned* err, cudaStream_t s) {
     if (W % tc::kTile || H < 1 || B < 1) return cudaErrorInvalidValue;
+    CUtensorMap map;
+    cudaError_t em = encode_act_map(&map, X, B, H, W);
+    if (em != cudaSuccess) return em;
     constexpr int smem = tc::ring_smem<N>();
     static bool attr = false;
     if (!attr) {
@@ -690,7 +757,7 @@ static cudaError_t launch_ring(int B, int H, int W, const void* X, const void* W
     const int ntiles = B * H * (W / tc::kTile);
     const int grid = ntiles < tc_sms() ? ntiles : tc_sms();
     tc::k_conv_ring<N, MODE><<<grid, tc::kRingThreads, smem, s>>>(
-        B, H, W, static_cast<const __nv_bfloat16*>(X), static_cast<const __nv_bfloat16*>(Wk), bias,
+        B, H, W, map, static_cast<const __nv_bfloat16*>(X), static_cast<const __nv_bfloat16*>(Wk), bias,
         static_cast<const __nv_bfloat16*>(mask), Y, relu, err);
     return cudaGetLastError();
 }
