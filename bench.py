@@ -277,7 +277,7 @@ def run_surrogate(torch, n_train=2000, n_test=100, train_steps=2000, batch=16, K
     tstack = SG.generate(test_seeds, L=L, K=K, snaps=snaps)
     mse_net, mse_p = net.evaluate(tstack, SG.pairs_of(n_test, snaps))
     out["test_mse_normalised"] = {"network": mse_net, "persistence": mse_p}
-    # rollouts: the LBM trajectory (FP32, parity-checked against the FP64 oracle) is the judge
+    # rollouts: the LBM trajectory (FP32, parity-checked against the FP64 oracle) is the reference
     nroll = min(n_test, 64)
 
     def rollout(tol, checkpoints=(1, 4, 16)):

@@ -312,7 +312,7 @@ const char *plbm_batch_last_error(plbm_batch b);
 
 /* ------------------------------------------------------------------------
  * Learned surrogate (not in the paper; a throughput service around its solver,
- * which generates the training data and stays the fallback and the judge).
+ * which generates the training data and stays the fallback and the reference).
  * A 6-layer 3x3 CNN with circular padding, channels 4 -> 64 -> 64 -> 64 -> 64
  * -> 64 -> 4, ReLU after the first five layers, BF16 weights and activations
  * with FP32 accumulation, maps the normalised fields (rho, u_x, u_y, theta)
