@@ -183,7 +183,11 @@ plbm_status plbm_init(plbm_handle h, const double *rho, const double *ux, const 
 /* Advance n >= 0 steps of Eq. (eq:srt) (pull-stream + BGK collision of the
  * equilibrium of Eq. eq:rdr).  Asynchronous unless check_every > 0, in which
  * case the device status is read (with a stream synchronisation) every
- * check_every steps and at the end; a set status returns PLBM_E_DIVERGED. */
+ * check_every steps and at the end; a set status returns PLBM_E_DIVERGED.
+ * Lattices of at most 2^18 nodes, whose steps are too short to hide the
+ * launches, advance by replays of a CUDA graph of 32 steps (captured at first
+ * use on a private stream, launched on the handle's stream; not when
+ * check_every > 0 or while the handle's stream is being captured). */
 plbm_status plbm_step(plbm_handle h, long n);
 
 /* Read the device status word (synchronises the stream).  Returns

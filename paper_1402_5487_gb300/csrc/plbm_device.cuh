@@ -402,14 +402,15 @@ struct DeviationCore {
 
 // ---------------------------------------------------------------------------
 // The fused stream-and-collide kernel.
-// grid = (ceil(nx / kBlockX), ny), block = kBlockX threads along x.
+// grid = (ceil(nx / blockDim.x), ny), blockDim.x threads along x (kBlockX when
+// REDUCE, whose per-block records assume it).
 // ---------------------------------------------------------------------------
 template <typename S, int Q1, int DIM, bool REDUCE>
 __global__ void __launch_bounds__(kBlockX)
 k_stream_collide(const __grid_constant__ LatticeParams P, const S* __restrict__ src,
                  S* __restrict__ dst) {
     constexpr int Q = (DIM == 1) ? Q1 : Q1 * Q1;
-    const int x = blockIdx.x * kBlockX + threadIdx.x;
+    const int x = blockIdx.x * (REDUCE ? kBlockX : (int)blockDim.x) + threadIdx.x;
     const int y = blockIdx.y;
     const bool active = x < P.nx;
 
@@ -485,12 +486,26 @@ k_stream_collide(const __grid_constant__ LatticeParams P, const S* __restrict__ 
     }
 }
 
+inline int device_sm_count() {
+    static int n = 0;
+    if (!n) {
+        int d = 0;
+        cudaGetDevice(&d);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || n < 1) n = 1;
+    }
+    return n;
+}
+
 template <typename S>
 cudaError_t launch_step_t(const LatticeParams& P, const void* src, void* dst, bool reduce,
                           cudaStream_t stream) {
     if (P.paired) return cudaErrorInvalidValue;  // row-paired layouts use k_stream_collide_pair
-    dim3 grid((P.nx + kBlockX - 1) / kBlockX, P.ny);
-    dim3 block(kBlockX);
+    // Small lattices (fewer than two blocks per SM): 32-thread blocks spread the
+    // nodes over four times as many SMs (GB300's FP64 rate per SM is low).
+    int bx = kBlockX;
+    if (!reduce && (long long)((P.nx + kBlockX - 1) / kBlockX) * P.ny < 2LL * device_sm_count()) bx = 32;
+    dim3 grid((P.nx + bx - 1) / bx, P.ny);
+    dim3 block(bx);
     const S* s = static_cast<const S*>(src);
     S* t = static_cast<S*>(dst);
 #define PLBM_LAUNCH(Q1v, DIMv)                                                              \

@@ -48,8 +48,14 @@ struct Handle {
     size_t stage_bytes = 0;
     cudaStream_t xfer = nullptr;
     cudaEvent_t xev[8] = {};
+    // Small lattices: kGraphSteps steps captured once per starting array and replayed.
+    cudaGraphExec_t sgraph[2] = {nullptr, nullptr};
+    cudaStream_t cap = nullptr;                // private stream the graphs are captured on
     char err[512] = "";
 };
+
+constexpr int kGraphSteps = 32;                 // even: a replay leaves the current array unchanged
+constexpr long long kGraphMaxNodes = 1 << 18;   // above this the GPU, not the launches, sets the pace
 
 constexpr int kXferChunks = 8;       // row bands of a pipelined host transfer
 constexpr size_t kXferMinNodes = 1u << 18;   // smaller lattices move in one band
@@ -243,6 +249,9 @@ plbm_status usable(Handle* h, bool need_init = true) {
 void free_handle(Handle* h) {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
+    for (cudaGraphExec_t g : h->sgraph)
+        if (g) cudaGraphExecDestroy(g);
+    if (h->cap) cudaStreamDestroy(h->cap);
     if (h->xfer) {
         cudaStreamSynchronize(h->xfer);
         for (cudaEvent_t e : h->xev)
@@ -626,7 +635,35 @@ plbm_status plbm_step(plbm_handle hh, long n) {
     if (st != PLBM_OK) return st;
     if (n < 0) { set_err(h, "n must be >= 0"); return PLBM_E_ARG; }
     const int ce = h->desc.check_every;
-    for (long s = 0; s < n; ++s) {
+    long s = 0;
+    const long long nodes = (long long)h->P.nx * h->P.ny * h->P.nz;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (ce == 0 && nodes <= kGraphMaxNodes && n >= 2 * kGraphSteps &&
+        cudaStreamIsCapturing(h->stream, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone) {
+        // launch-bound lattices: replay a run of kGraphSteps steps, captured on a
+        // private stream (any stream, the legacy default one included, can launch it)
+        for (; s + kGraphSteps <= n; s += kGraphSteps) {
+            cudaGraphExec_t& g = h->sgraph[h->cur];
+            if (!g) {
+                if (!h->cap) CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+                cudaGraph_t graph = nullptr;
+                CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+                cudaError_t el = cudaSuccess;
+                for (int k = 0, c = h->cur; k < kGraphSteps && el == cudaSuccess; ++k, c ^= 1)
+                    el = h->P.dim == 3 ? plbm::launch_step3(h->prec, h->P, h->f[c], h->f[c ^ 1], h->cap)
+                                       : plbm::launch_step(h->prec, h->P, h->f[c], h->f[c ^ 1], false, h->cap);
+                const cudaError_t ec = cudaStreamEndCapture(h->cap, &graph);
+                CK(el);
+                CK(ec);
+                const cudaError_t ei = cudaGraphInstantiate(&g, graph, 0);
+                cudaGraphDestroy(graph);
+                CK(ei);
+            }
+            CK(cudaGraphLaunch(g, h->stream));
+            h->steps += kGraphSteps;
+        }
+    }
+    for (; s < n; ++s) {
         if (h->P.dim == 3)
             CK(plbm::launch_step3(h->prec, h->P, h->f[h->cur], h->f[h->cur ^ 1], h->stream));
         else

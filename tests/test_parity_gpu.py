@@ -523,3 +523,26 @@ def test_taylor_green_converges_at_second_order_on_gpu(v, theta0, iso, omega, pr
     errs = taylor_green_errors(v, theta0, iso, omega, runner=runner)
     orders = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
     assert all(o > 1.8 for o in orders), (errs, orders)
+
+
+@pytest.mark.parametrize("prec,dim", [("f64", 1), ("f32", 2), ("f16dev", 2)])
+def test_graph_replayed_steps_equal_single_launches(prec, dim):
+    # Small lattices advance by replays of a captured 32-step graph; the result must
+    # equal the same steps launched one call at a time, bit for bit.
+    nx, ny = (1000, 1) if dim == 1 else (64, 48)
+    fields = I.kh_fields(nx, ny=ny) if dim == 2 else I.shock_tube_fields(nx)
+    out = []
+    for chunks in ([150], [1] * 150):
+        if dim == 1:
+            s = plbm.Solver(1, I.SET_013, 1.5, nx, 1, theta0=0.5, prec=prec, bc="fixed",
+                            left_state=(1.1, 0.0, 0.5), right_state=(1.0, 0.0, 0.5))
+            s.init(fields[0], fields[1], None, fields[3])
+        else:
+            s = plbm.Solver(2, I.SET_013, 1.3, nx, ny, theta0=1.0, prec=prec)
+            s.init(*fields)
+        for c in chunks:
+            s.step(c)
+        out.append(s.get_populations())
+        assert s.check() == 0
+        s.close()
+    assert np.array_equal(out[0], out[1])
