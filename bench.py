@@ -321,6 +321,11 @@ def run_surrogate(torch, n_train=2000, n_test=100, train_steps=2000, batch=16, K
     for tol in (3e-4, 1e-3):
         t_r, r_r, _, e_r = rollout(tol, checkpoints=(16,))
         sweep["%g" % tol] = (t_r, r_r, e_r["16"]["surrogate_vs_lbm"]["u"])
+    # the same gate after projecting each prediction onto the old global sums
+    net.set_conserve(True)
+    t_r, r_r, _, e_r = rollout(1e-4, checkpoints=(16,))
+    net.set_conserve(False)
+    sweep["1e-4, conservative projection"] = (t_r, r_r, e_r["16"]["surrogate_vs_lbm"]["u"])
     # gain test: the same lattices and horizon (16 x K steps) with plain batched LBM
     insts = [SG.trajectory_instance(sd, L)[0] for sd in test_seeds[:nroll]]
     bt = Batch(insts, prec="f32")

@@ -340,6 +340,12 @@ plbm_status plbm_sur_destroy(plbm_surrogate s);
  * convolutions and their backward-data passes: 1 (default) tcgen05.mma with
  * tensor-memory accumulators, 0 mma.sync (kept as a cross-check). */
 #define PLBM_SUR_OPT_TENSOR_PATH 1
+/* PLBM_SUR_OPT_CONSERVE: 1 shifts each lattice's predicted conserved densities
+ * (rho, rho u, E = rho (d theta + |u|^2)) uniformly so that their totals equal
+ * those of the old fields before the drift gate of plbm_sur_advance, which then
+ * only rejects non-finite or non-positive predictions (and FP32 rounding);
+ * 0 (default) gates the network's own prediction. */
+#define PLBM_SUR_OPT_CONSERVE 2
 plbm_status plbm_sur_set_option(plbm_surrogate s, int option, int value);
 
 /* PLBM_E_TIMEOUT if a bounded wait of a tensor-core kernel ran out (synchronous). */

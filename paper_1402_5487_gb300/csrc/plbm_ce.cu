@@ -162,6 +162,51 @@ __global__ void k_field_drift(const double* __restrict__ so, const double* __res
     }
 }
 
+// Conservative projection of predicted fields (option of the surrogate
+// advance): per lattice, the uniform shifts of the conserved densities
+// (rho, rho u_x, rho u_y, E = rho (2 theta + |u|^2)) that restore the old
+// fields' totals, delta_k = (old_k - new_k) / n, from the per-block partial
+// sums of k_field_sums_batch.  One warp per lattice.
+__global__ void k_conserve_coef(const double* __restrict__ so, const double* __restrict__ sn, int nblk, int nlat,
+                                long long n, float4* __restrict__ delta) {
+    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (b >= nlat) return;
+    double a[4] = {0, 0, 0, 0}, c[4] = {0, 0, 0, 0};
+    for (int k = lane; k < nblk; k += 32)
+        for (int j = 0; j < 4; ++j) {
+            a[j] += so[((long long)b * nblk + k) * 4 + j];
+            c[j] += sn[((long long)b * nblk + k) * 4 + j];
+        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            a[j] += __shfl_xor_sync(0xffffffffu, a[j], o);
+            c[j] += __shfl_xor_sync(0xffffffffu, c[j], o);
+        }
+    if (lane == 0)
+        delta[b] = make_float4((float)((a[0] - c[0]) / n), (float)((a[1] - c[1]) / n), (float)((a[2] - c[2]) / n),
+                               (float)((a[3] - c[3]) / n));
+}
+
+// F <- fields of (rho + d0, rho u + (d1, d2), E + d3); a non-positive density or
+// temperature becomes NaN, which the drift gate rejects.
+__global__ void k_conserve_apply(float4* __restrict__ F, long long n, const float4* __restrict__ delta) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blockIdx.y;
+    if (i >= n) return;
+    float4& a = F[(long long)b * n + i];
+    const float4 d = delta[b];
+    const float r = a.x + d.x;
+    const float jx = fmaf(a.x, a.y, d.y), jy = fmaf(a.x, a.z, d.z);
+    const float e = fmaf(a.x, 2.0f * a.w + a.y * a.y + a.z * a.z, d.w);
+    const float ux = jx / r, uy = jy / r;
+    const float th = 0.5f * (e / r - (ux * ux + uy * uy));
+    const bool ok = r > 0.0f && th > 0.0f;
+    a = ok ? make_float4(r, ux, uy, th) : make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
+}
+
 struct CEConsts {
     float Ginv[16];   // inverse of G_jk = sum_p w0_p m_j(p) m_k(p), m = (1, v_x, v_y, |v|^2)
     float coef;       // (1 - omega) / omega
@@ -313,6 +358,18 @@ cudaError_t ce_apply_delta(const float* F, const float* d, long long n, const fl
 }
 
 int ce_sum_blocks() { return 64; }
+
+cudaError_t ce_conserve(const float* Fold, float* Fnew, long long n, int nlat, double* partial_old,
+                        double* partial_new, float* delta, cudaStream_t s) {
+    const dim3 grid(ce_sum_blocks(), nlat);
+    k_field_sums_batch<<<grid, 256, 0, s>>>(reinterpret_cast<const float4*>(Fold), n, partial_old);
+    k_field_sums_batch<<<grid, 256, 0, s>>>(reinterpret_cast<const float4*>(Fnew), n, partial_new);
+    k_conserve_coef<<<(nlat + 3) / 4, 128, 0, s>>>(partial_old, partial_new, ce_sum_blocks(), nlat, n,
+                                                   reinterpret_cast<float4*>(delta));
+    k_conserve_apply<<<dim3((unsigned)((n + 255) / 256), nlat), 256, 0, s>>>(reinterpret_cast<float4*>(Fnew), n,
+                                                                          reinterpret_cast<const float4*>(delta));
+    return cudaGetLastError();
+}
 
 cudaError_t ce_field_drift(const float* Fold, const float* Fnew, long long n, int nlat, double* partial_old,
                            double* partial_new, double* drift, cudaStream_t s) {

@@ -149,6 +149,10 @@ cudaError_t ce_apply_delta(const float* F, const float* d, long long n, const fl
 int ce_sum_blocks();
 cudaError_t ce_field_sums(const float* F, long long n, double* partial, cudaStream_t s);
 cudaError_t ce_reconstruct(int prec, const LatticeParams& P, const float* F, void* f, cudaStream_t s);
+// Shift the predicted fields of nlat lattices so that their global mass,
+// momentum and energy equal the old fields' (delta: 4 floats per lattice).
+cudaError_t ce_conserve(const float* Fold, float* Fnew, long long n, int nlat, double* partial_old,
+                        double* partial_new, float* delta, cudaStream_t s);
 cudaError_t ce_field_drift(const float* Fold, const float* Fnew, long long n, int nlat, double* partial_old,
                            double* partial_new, double* drift, cudaStream_t s);
 

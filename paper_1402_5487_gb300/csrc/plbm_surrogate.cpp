@@ -44,6 +44,7 @@ struct Sur {
     void* wout = nullptr;           // last layer (64 -> 4) for tcgen05: bf16 [9][16][64]
     unsigned* derr = nullptr;       // device flag: a bounded wait in a tensor-core kernel ran out
     int use_tc = 1;                 // forward convolutions and 64 -> 64 backward data: 1 tcgen05, 0 mma.sync / CUDA cores
+    int conserve = 0;               // 1: project predicted fields onto the old global sums before the drift gate
     void* act[kLayers] = {nullptr}; // act[0..4] bf16 [B][H][W][64]; act[5] fp32 [B][H][W][4]
     void* dz[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // dL/d(pre-activation) of layers 1..5
     float* dout = nullptr;
@@ -248,7 +249,7 @@ plbm_status plbm_sur_create(int max_batch, int H, int W, unsigned long long seed
         {(void**)&s->Fold, pix * 4 * 4}, {(void**)&s->Fnew, pix * 4 * 4}, {&s->xin, pix * 4 * 2},
         {(void**)&s->planes, (size_t)H * W * 4 * 8}, {(void**)&s->sums, (size_t)max_batch * 2 * 64 * 4 * 8},
         {&s->wtc, 8 * 9 * 64 * 64 * 2}, {(void**)&s->derr, 256}, {&s->win, 6 * 64 * 8 * 2},
-        {&s->wout, 9 * 16 * 64 * 2}, {(void**)&s->drift, (size_t)max_batch * 8},
+        {&s->wout, 9 * 16 * 64 * 2}, {(void**)&s->drift, (size_t)max_batch * 24 + 16},
         {(void**)&s->fb_table, (size_t)max_batch * sizeof(plbm::PairParams)},
     };
     for (auto& a : allocs) {
@@ -338,6 +339,10 @@ plbm_status plbm_sur_set_option(plbm_surrogate h, int option, int value) {
     if (!s) return PLBM_E_ARG;
     if (option == PLBM_SUR_OPT_TENSOR_PATH && (value == 0 || value == 1)) {
         s->use_tc = value;
+        return PLBM_OK;
+    }
+    if (option == PLBM_SUR_OPT_CONSERVE && (value == 0 || value == 1)) {
+        s->conserve = value;
         return PLBM_OK;
     }
     serr(s, "unknown option %d or value %d", option, value);
@@ -485,6 +490,9 @@ plbm_status plbm_sur_advance(plbm_surrogate h, plbm_handle* hs, int n, int K, do
     SCK(plbm::ce_apply_delta(s->Fold, static_cast<const float*>(s->act[5]), npix * n, s->norm + 8, s->norm + 12,
                              s->Fnew, s->stream));
     const size_t half = (size_t)s->Bm * plbm::ce_sum_blocks() * 4;
+    if (s->conserve)
+        SCK(plbm::ce_conserve(s->Fold, s->Fnew, npix, n, s->sums, s->sums + half,
+                              reinterpret_cast<float*>(s->drift + ((s->Bm + 1) & ~1)), s->stream));
     SCK(plbm::ce_field_drift(s->Fold, s->Fnew, npix, n, s->sums, s->sums + half, s->drift, s->stream));
     SCK(cudaMemcpyAsync(s->host_sums, s->drift, (size_t)n * 8, cudaMemcpyDeviceToHost, s->stream));
     SCK(cudaStreamSynchronize(s->stream));

@@ -137,6 +137,11 @@ class Surrogate:
         """tcgen05.mma (True, default) or mma.sync (False) for the 64 -> 64 convolutions."""
         self._ok(plbm.lib().plbm_sur_set_option(self.h, 1, 1 if tcgen05 else 0))
 
+    def set_conserve(self, on: bool):
+        """Project predicted fields onto the old global mass, momentum and energy
+        before the drift gate of advance (PLBM_SUR_OPT_CONSERVE)."""
+        self._ok(plbm.lib().plbm_sur_set_option(self.h, 2, 1 if on else 0))
+
     def check(self):
         return int(plbm.lib().plbm_sur_check(self.h))
 

@@ -193,6 +193,39 @@ def test_reported_drift_matches_fields_before_and_after(trained):
     sol.close()
 
 
+def test_conservative_projection_keeps_the_global_sums(trained):
+    # With the projection option the predicted fields are shifted onto the old
+    # global mass, momentum and energy: an advance then passes even a tight gate
+    # and the stored populations keep the sums to FP32 rounding.
+    net = trained[0]
+    L = 128
+    sol = plbm.Solver(2, SG.V5, SG.OMEGA, L, L, theta0=SG.THETA0, prec="f32")
+    sol.init(*SG.trajectory_fields(2002, L))
+    sol.step(64)
+
+    def sums(m):
+        rho, ux, uy, th = m
+        return np.array([rho.sum(), (rho * ux).sum(), (rho * uy).sum(),
+                         (rho * (2 * th + ux * ux + uy * uy)).sum()])
+
+    m0 = sol.moments()
+    a = sums(m0)
+    net.set_conserve(True)
+    try:
+        flags = net.advance([sol], K=32, tol=1e-5)
+        reported = net.last_drift()[0]
+    finally:
+        net.set_conserve(False)
+    assert flags == [0]
+    m1 = sol.moments()
+    b = sums(m1)
+    drift = max(abs(b[0] - a[0]) / abs(a[0]), abs(b[3] - a[3]) / abs(a[3]),
+                np.hypot(b[1] - a[1], b[2] - a[2]) / (0.1 * abs(a[0])))
+    assert drift <= 2e-6 and reported <= 2e-6, (drift, reported)
+    assert np.max(np.abs(m1[1] - m0[1])) > 1e-3     # the network did move the flow
+    sol.close()
+
+
 @pytest.mark.parametrize("K", [32, 5])
 def test_batched_fallback_equals_plain_stepping(trained, K):
     # Several fallback lattices in the row-paired layout step together in one
