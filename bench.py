@@ -20,6 +20,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -73,6 +74,17 @@ def read_traffic(prec):
         return float(d["bytes_per_launch"])
     except Exception:
         return None
+
+
+def json_safe(obj):
+    """The object with every non-finite float replaced by None (strict JSON)."""
+    if isinstance(obj, float):
+        return obj if math.isfinite(obj) else None
+    if isinstance(obj, dict):
+        return {k: json_safe(v) for k, v in obj.items()}
+    if isinstance(obj, (list, tuple)):
+        return [json_safe(v) for v in obj]
+    return obj
 
 
 def read_peaks():
@@ -306,8 +318,11 @@ def run_surrogate(torch, n_train=2000, n_test=100, train_steps=2000, batch=16, K
                     ini = [ini[:, c].reshape(L, L) for c in range(4)]
                     e_net.append(_field_err(s.moments(), ref))
                     e_pers.append(_field_err(ini, ref))
-                errs[str(k)] = {"surrogate_vs_lbm": {f: float(np.mean([e[f] for e in e_net])) for f in ("rho", "u", "theta")},
-                                "persistence_vs_lbm": {f: float(np.mean([e[f] for e in e_pers])) for f in ("rho", "u", "theta")}}
+                fin = [e for e in e_net if all(np.isfinite(e[f]) for f in ("rho", "u", "theta"))]
+                errs[str(k)] = {"surrogate_vs_lbm": {f: (float(np.mean([e[f] for e in fin])) if fin else None)
+                                                     for f in ("rho", "u", "theta")},
+                                "persistence_vs_lbm": {f: float(np.mean([e[f] for e in e_pers])) for f in ("rho", "u", "theta")},
+                                "non_finite_lattices": len(e_net) - len(fin)}
         for s in solvers:
             s.close()
         return t_roll, fell / calls, np.concatenate(drifts), errs
@@ -317,15 +332,16 @@ def run_surrogate(torch, n_train=2000, n_test=100, train_steps=2000, batch=16, K
     out["fallback_rate"] = rate
     out["drift"] = {"tol": 1e-4, "median": float(np.median(d)), "p10": float(np.percentile(d, 10)),
                     "p90": float(np.percentile(d, 90)), "fraction_within_tol": float(np.mean(d <= 1e-4))}
-    sweep = {"1e-4": (t_roll, rate, errs["16"]["surrogate_vs_lbm"]["u"])}
+    sweep = {"1e-4": (t_roll, rate, errs["16"]["surrogate_vs_lbm"]["u"], errs["16"]["non_finite_lattices"])}
     for tol in (3e-4, 1e-3):
         t_r, r_r, _, e_r = rollout(tol, checkpoints=(16,))
-        sweep["%g" % tol] = (t_r, r_r, e_r["16"]["surrogate_vs_lbm"]["u"])
+        sweep["%g" % tol] = (t_r, r_r, e_r["16"]["surrogate_vs_lbm"]["u"], e_r["16"]["non_finite_lattices"])
     # the same gate after projecting each prediction onto the old global sums
     net.set_conserve(True)
     t_r, r_r, _, e_r = rollout(1e-4, checkpoints=(16,))
     net.set_conserve(False)
-    sweep["1e-4, conservative projection"] = (t_r, r_r, e_r["16"]["surrogate_vs_lbm"]["u"])
+    sweep["1e-4, conservative projection"] = (t_r, r_r, e_r["16"]["surrogate_vs_lbm"]["u"],
+                                              e_r["16"]["non_finite_lattices"])
     # gain test: the same lattices and horizon (16 x K steps) with plain batched LBM
     insts = [SG.trajectory_instance(sd, L)[0] for sd in test_seeds[:nroll]]
     bt = Batch(insts, prec="f32")
@@ -343,7 +359,8 @@ def run_surrogate(torch, n_train=2000, n_test=100, train_steps=2000, batch=16, K
     bt.close()
     out["gain_test"] = {"lattices": nroll, "horizon_steps": 16 * K, "lbm_s": t_lbm_roll,
                         "by_tol": {k: {"surrogate_with_fallback_s": v[0], "speedup": t_lbm_roll / v[0],
-                                       "fallback_rate": v[1], "u_error_at_horizon_vs_lbm": v[2]}
+                                       "fallback_rate": v[1], "u_error_at_horizon_vs_lbm": v[2],
+                                       "non_finite_lattices_at_horizon": v[3]}
                                    for k, v in sweep.items()}}
     # FP64 oracle check on two held-out seeds after one advance
     orc = []
@@ -608,7 +625,7 @@ def main():
                                  "sample": "%dx%d D2Q25 KH, %d timed FP64 steps of the C oracle" % (
                                      L, L, args.steps)},
                 "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-        print(json.dumps(line))
+        print(json.dumps(json_safe(line)))
         return 0
 
     import torch
@@ -622,7 +639,7 @@ def main():
     build.build()
     if args.case != "main":
         if rank == 0:
-            print(json.dumps(run_case(torch, args)))
+            print(json.dumps(json_safe(run_case(torch, args))))
         return 0
 
     def barrier():
@@ -711,7 +728,7 @@ def main():
                              "kernel": KERNEL_NAME[args.prec]},
                 "e2e": e2e, "gpu_launches": args.steps, "clocks": clock_info,
                 "cpu_baseline": cpu, "variants": variants}
-        print(json.dumps(line))
+        print(json.dumps(json_safe(line)))
     if dist is not None:
         dist.destroy_process_group()
     return 0
