@@ -149,3 +149,23 @@ def test_d3q125_conserves_to_rounding():
     s.close()
     scale = np.array([c0[0], c0[0], c0[0], c0[0], c0[4]])
     assert np.max(np.abs(c1 - c0) / scale) < 2e-6
+
+
+@pytest.mark.parametrize("prec,nz", [("f16dev", 6), ("bf16dev", 8), ("f32", 6)])
+def test_d3q125_checkpoint_resume_is_bit_identical(prec, nz):
+    # get/set_populations on the 3D layouts (z-paired for 16-bit storage and even nz)
+    from paper_1402_5487_gb300 import plbm
+    nx, ny = 40, 6
+    f = fields3(nx, ny, nz, 12)
+    a = plbm.Solver(3, V5, 1.3, nx, ny, nz=nz, prec=prec)
+    a.init(f[0], f[1], f[2], f[4], uz=f[3])
+    a.step(7)
+    f7 = a.get_populations()
+    a.step(9)
+    ref = a.get_populations()
+    b = plbm.Solver(3, V5, 1.3, nx, ny, nz=nz, prec=prec)
+    b.set_populations(f7, step=7)
+    b.step(9)
+    assert np.array_equal(b.get_populations(), ref)
+    a.close()
+    b.close()

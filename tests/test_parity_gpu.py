@@ -546,3 +546,30 @@ def test_graph_replayed_steps_equal_single_launches(prec, dim):
         assert s.check() == 0
         s.close()
     assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16dev", "f64"])
+def test_banded_host_transfers_equal_device_pointers(prec):
+    # Lattices of 2^18 nodes or more move host fields in eight row bands on a copy
+    # stream overlapped with the kernels; the result must equal the device-pointer
+    # calls bit for bit (640 x 512 = 327,680 nodes in bands of 64 rows; 520 x 517
+    # in uneven bands).
+    import torch
+    for nx, ny in ((640, 512), (520, 517)):
+        fields = I.kh_fields(nx, ny=ny, seed=6)
+        st = torch.cuda.Stream()
+        a = plbm.Solver(2, V5, 1.3, nx, ny, theta0=1.0, prec=prec, stream=st)
+        b = plbm.Solver(2, V5, 1.3, nx, ny, theta0=1.0, prec=prec, stream=st)
+        a.init(*fields)                                          # host pointers, banded
+        b.init(*[torch.from_numpy(f).to("cuda") for f in fields])  # device pointers
+        st.synchronize()
+        assert np.array_equal(a.get_populations(), b.get_populations())
+        a.step(3)
+        b.step(3)
+        mh = a.moments()                                         # host pointers, banded
+        md = b.moments(on_device=True)
+        st.synchronize()
+        for x, y in zip(mh, md):
+            assert np.array_equal(x, y.cpu().numpy())
+        a.close()
+        b.close()
