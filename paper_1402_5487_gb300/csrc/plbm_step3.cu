@@ -429,6 +429,104 @@ __global__ void __launch_bounds__(kB3) k_stream_collide3_f64(const __grid_consta
     for (int p = 0; p < q1 * q1 * q1; ++p) dst[(long long)p * P.plane + here] = (1.0 - om) * fin[p] + om * fe[p];
 }
 
+// FP64, compile-time q1 (3 or 5), in two passes over the pulled values so that
+// no thread holds all q1^3 of them: the first forms the row sums
+// R_ab = sum_c f, S_a, T_b, U_c; the second loads them again (L1/L2 hits) and
+// writes f' = (1 - omega) f + (omega rho r^x_a r^y_b) r^z_c.  The same formulas
+// as k_stream_collide3_f64 (moments, C mu rule), with the sums factorised.
+__device__ __forceinline__ double ldg_again(const double* p) {
+    double v;
+    asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+
+template <int Q1>
+__device__ __forceinline__ void rule_q(const LatticeParams& P, double u, double th, double (&r)[Q1]) {
+    double mu[Q1];
+    mu[0] = 1.0;
+    mu[1] = u;
+#pragma unroll
+    for (int n = 1; n + 1 < Q1; ++n) mu[n + 1] = u * mu[n] + (double)n * th * mu[n - 1];
+#pragma unroll
+    for (int i = 0; i < Q1; ++i) {
+        double t = 0.0;
+#pragma unroll
+        for (int n = 0; n < Q1; ++n) t += P.C[i * Q1 + n] * mu[n];
+        r[i] = t;
+    }
+}
+
+template <int Q1>
+__global__ void __launch_bounds__(kB3) k_stream_collide3_f64q(const __grid_constant__ LatticeParams P,
+                                                              const double* __restrict__ src,
+                                                              double* __restrict__ dst) {
+    const int x = blockIdx.x * kB3 + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (x >= P.nx) return;
+    // element offsets within a plane fit 32 bits (a plane is at most the device memory / 2 q^3 sizeof)
+    int xs[Q1], yr[Q1], zr[Q1];
+#pragma unroll
+    for (int i = 0; i < Q1; ++i) {
+        xs[i] = wrap_add(x, P.vxm[i], P.nx);
+        yr[i] = wrap_add(y, P.vym[i], P.ny) * P.pitch;
+        zr[i] = wrap_add(z, P.vzm[i], P.nz) * P.ny * P.pitch;
+    }
+    double Sa[Q1], Tb[Q1], Uc[Q1];
+#pragma unroll
+    for (int i = 0; i < Q1; ++i) Sa[i] = Tb[i] = Uc[i] = 0.0;
+#pragma unroll
+    for (int a = 0; a < Q1; ++a)
+#pragma unroll
+        for (int b = 0; b < Q1; ++b) {
+            double R = 0.0;
+#pragma unroll
+            for (int c = 0; c < Q1; ++c) {
+                const int p = (a * Q1 + b) * Q1 + c;
+                const double v = __ldg(src + (long long)p * P.plane + (zr[c] + yr[b] + xs[a]));
+                R += v;
+                Uc[c] += v;
+            }
+            Sa[a] += R;
+            Tb[b] += R;
+        }
+    double m0 = 0.0, mx = 0.0, my = 0.0, mz = 0.0, en = 0.0;
+#pragma unroll
+    for (int i = 0; i < Q1; ++i) {
+        const double vi = (double)P.v[i];
+        m0 += Sa[i];
+        mx += vi * Sa[i];
+        my += vi * Tb[i];
+        mz += vi * Uc[i];
+        en += vi * vi * (Sa[i] + Tb[i] + Uc[i]);
+    }
+    const double ux = mx / m0, uy = my / m0, uz = mz / m0;
+    const double th = (en / m0 - (ux * ux + uy * uy + uz * uz)) / 3.0;
+    flag_status<double>(P, m0, th);
+    const double the = P.isothermal ? P.theta0 : th;
+    double ra[Q1], rb[Q1], rc[Q1];
+    rule_q<Q1>(P, ux, the, ra);
+    rule_q<Q1>(P, uy, the, rb);
+    rule_q<Q1>(P, uz, the, rc);
+    const double om = P.omega, keep = 1.0 - om;
+    const long long here = ((long long)z * P.ny + y) * P.pitch + x;
+    long long plane2 = P.plane;   // fresh index terms: the second pass recomputes its addresses
+    asm volatile("" : "+l"(plane2));
+#pragma unroll
+    for (int i = 0; i < Q1; ++i) asm volatile("" : "+r"(xs[i]), "+r"(yr[i]), "+r"(zr[i]));
+#pragma unroll
+    for (int a = 0; a < Q1; ++a)
+#pragma unroll
+        for (int b = 0; b < Q1; ++b) {
+            const double X = om * m0 * ra[a] * rb[b];
+#pragma unroll
+            for (int c = 0; c < Q1; ++c) {
+                const int p = (a * Q1 + b) * Q1 + c;
+                const double f = ldg_again(src + (long long)p * plane2 + (zr[c] + yr[b] + xs[a]));
+                dst[(long long)p * plane2 + here] = fma(keep, f, X * rc[c]);
+            }
+        }
+}
+
 template <typename S>
 __global__ void k_init3(const __grid_constant__ LatticeParams P, const double* __restrict__ rho,
                         const double* __restrict__ ux, const double* __restrict__ uy, const double* __restrict__ uz,
@@ -561,7 +659,14 @@ long long reduce3_blocks(const LatticeParams& P) {
 
 cudaError_t launch_step3(int prec, const LatticeParams& P, const void* src, void* dst, cudaStream_t s) {
     if (prec == kF64) {
-        k_stream_collide3_f64<<<grid3(P), kB3, 0, s>>>(P, static_cast<const double*>(src), static_cast<double*>(dst));
+        const double* a = static_cast<const double*>(src);
+        double* b = static_cast<double*>(dst);
+        if (P.q1 == 5)
+            k_stream_collide3_f64q<5><<<grid3(P), kB3, 0, s>>>(P, a, b);
+        else if (P.q1 == 3)
+            k_stream_collide3_f64q<3><<<grid3(P), kB3, 0, s>>>(P, a, b);
+        else
+            k_stream_collide3_f64<<<grid3(P), kB3, 0, s>>>(P, a, b);
         return cudaGetLastError();
     }
     if (!P.sym5 || P.q1 != kQ1 || P.isothermal) return cudaErrorInvalidValue;
