@@ -260,8 +260,9 @@ def _field_err(mg, mr):
     return {"rho": rho, "u": u, "theta": th}
 
 
-def run_surrogate(torch, n_train=2000, n_test=100, train_steps=2000, batch=16, K=32, L=256):
-    """Learned surrogate: data from the batched solver, training, held-out errors, speed."""
+def run_surrogate(torch, n_train=2000, n_test=100, train_steps=2000, batch=16, K=32, L=256, mean_penalty=0.0):
+    """Learned surrogate: data from the batched solver, training (loss: MSE plus
+    mean_penalty x the squared lattice-mean error), held-out errors, speed."""
     import oracle as O
     from paper_1402_5487_gb300 import plbm, surrogate as SG
     from paper_1402_5487_gb300.batch import Batch
@@ -273,6 +274,8 @@ def run_surrogate(torch, n_train=2000, n_test=100, train_steps=2000, batch=16, K
     norm = SG.fit_norm(stack, pairs)
     net = SG.Surrogate(64, L, L, seed=0)
     net.set_norm(*norm)
+    net.set_mean_penalty(mean_penalty)
+    out["mean_penalty"] = mean_penalty
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     losses = net.train(stack, pairs, train_steps, batch=batch, lr=1e-3, lr_end=1e-4, log_every=train_steps // 4)

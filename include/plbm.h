@@ -374,8 +374,14 @@ plbm_status plbm_sur_backward(plbm_surrogate s, int B, const void *x, const floa
  * Synchronous. */
 plbm_status plbm_sur_copy(plbm_surrogate s, int kind, int layer, int B, void *dst);
 
-/* One Adam step on the mean squared error against target.  loss (host, may be
- * NULL) receives the loss, which synchronises the stream. */
+/* Training loss = mean squared error + lambda x mean over samples and fields of
+ * the squared lattice-mean error (the mean over all pixels of prediction minus
+ * target).  The second term aims the network at the global sums the drift gate
+ * of plbm_sur_advance checks.  lambda >= 0 (default 0); PLBM_E_ARG otherwise. */
+plbm_status plbm_sur_set_mean_penalty(plbm_surrogate s, float lambda);
+
+/* One Adam step on the training loss (above) against target.  loss (host, may be
+ * NULL) receives its mean squared error part, which synchronises the stream. */
 plbm_status plbm_sur_train_step(plbm_surrogate s, int B, const void *x, const float *target, float lr,
                                 float *loss);
 

@@ -564,15 +564,42 @@ __global__ void k_flip_thin(const float* __restrict__ W, int CI, int CO, float* 
     Wb[i] = W[((8 - tap) * CI + ci) * CO + co];
 }
 
-// Mean squared error of pred against target (fp32, n values) and its gradient
-// 2 (pred - target) / n; per-block partial sums of squares.
+// Per-sample, per-channel mean error m[b][c] = mean over the npix pixels of
+// pred - target (NHWC [B][npix][4]); one block per sample.
+__global__ void k_mean_err(const float* __restrict__ pred, const float* __restrict__ target, long long npix,
+                           float* __restrict__ m) {
+    __shared__ float sh[4][256];
+    const long long base = (long long)blockIdx.x * npix * 4;
+    float a[4] = {0.f, 0.f, 0.f, 0.f};
+    for (long long i = threadIdx.x; i < npix; i += blockDim.x)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) a[c] += pred[base + i * 4 + c] - target[base + i * 4 + c];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) sh[c][threadIdx.x] = a[c];
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if (threadIdx.x < k)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) m[blockIdx.x * 4 + threadIdx.x] = sh[threadIdx.x][0] / (float)npix;
+}
+
+// Loss (1/n) sum (pred - target)^2 + lam mean_{b,c} m[b][c]^2 (fp32, n = B npix 4
+// values; m from k_mean_err, or NULL for lam = 0) and its gradient
+// 2 (pred - target) / n + 2 lam m[b][c] / n; per-block partial sums of squares
+// (the first term).  The second term drives the lattice-mean error of every
+// predicted field, which the surrogate's drift gate measures, towards zero.
 __global__ void k_mse(const float* __restrict__ pred, const float* __restrict__ target, long long n,
-                      float* __restrict__ grad, float* __restrict__ partial) {
+                      long long npix, const float* __restrict__ m, float lam, float* __restrict__ grad,
+                      float* __restrict__ partial) {
     __shared__ float sh[256];
     float s = 0.0f;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const float d = pred[i] - target[i];
-        grad[i] = 2.0f * d / (float)n;
+        const float dm = m ? lam * m[(i / (npix * 4)) * 4 + (i & 3)] : 0.0f;
+        grad[i] = 2.0f * (d + dm) / (float)n;
         s += d * d;
     }
     sh[threadIdx.x] = s;
@@ -748,9 +775,14 @@ cudaError_t cnn_flip_thin(const float* W, int ci, int co, float* Wb, cudaStream_
     return cudaGetLastError();
 }
 
-cudaError_t cnn_mse(const float* pred, const float* target, long long n, float* grad, float* partial, int parts,
-                    cudaStream_t s) {
-    cnn::k_mse<<<parts, 256, 0, s>>>(pred, target, n, grad, partial);
+cudaError_t cnn_mse(const float* pred, const float* target, long long n, long long npix, float lam, float* merr,
+                    float* grad, float* partial, int parts, cudaStream_t s) {
+    if (lam != 0.0f) {
+        cnn::k_mean_err<<<(int)(n / (npix * 4)), 256, 0, s>>>(pred, target, npix, merr);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    cnn::k_mse<<<parts, 256, 0, s>>>(pred, target, n, npix, lam != 0.0f ? merr : nullptr, lam, grad, partial);
     return cudaGetLastError();
 }
 

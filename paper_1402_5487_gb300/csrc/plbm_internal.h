@@ -131,8 +131,8 @@ cudaError_t cnn_conv_in_tc(int B, int H, int W, const void* X, const void* Win, 
                            unsigned* err, cudaStream_t s);
 cudaError_t cnn_weights_out16(const float* W, void* Wo, cudaStream_t s);
 cudaError_t cnn_weights_in(const float* W, void* Win, cudaStream_t s);
-cudaError_t cnn_mse(const float* pred, const float* target, long long n, float* grad, float* partial, int parts,
-                    cudaStream_t s);
+cudaError_t cnn_mse(const float* pred, const float* target, long long n, long long npix, float lam, float* merr,
+                    float* grad, float* partial, int parts, cudaStream_t s);
 cudaError_t cnn_adam(float* p, const float* g, float* m, float* v, long long n, float lr, float b1, float b2, float eps,
                      int t, cudaStream_t s);
 cudaError_t cnn_to_bf16(const float* a, long long n, void* b, cudaStream_t s);

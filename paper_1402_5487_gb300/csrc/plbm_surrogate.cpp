@@ -45,6 +45,7 @@ struct Sur {
     unsigned* derr = nullptr;       // device flag: a bounded wait in a tensor-core kernel ran out
     int use_tc = 1;                 // forward convolutions and 64 -> 64 backward data: 1 tcgen05, 0 mma.sync / CUDA cores
     int conserve = 0;               // 1: project predicted fields onto the old global sums before the drift gate
+    float mean_penalty = 0.0f;      // weight of the lattice-mean error term of the training loss
     void* act[kLayers] = {nullptr}; // act[0..4] bf16 [B][H][W][64]; act[5] fp32 [B][H][W][4]
     void* dz[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // dL/d(pre-activation) of layers 1..5
     float* dout = nullptr;
@@ -245,7 +246,7 @@ plbm_status plbm_sur_create(int max_batch, int H, int W, unsigned long long seed
         {&s->wbf, 4 * 9 * 64 * 64 * 2}, {&s->wflip, 4 * 9 * 64 * 64 * 2}, {(void**)&s->w6flip, 9 * 4 * 64 * 4},
         {&s->dz[0], pix * 64 * 2}, {&s->dz[1], pix * 64 * 2}, {&s->dz[2], pix * 64 * 2},
         {&s->dz[3], pix * 64 * 2}, {&s->dz[4], pix * 64 * 2}, {(void**)&s->dout, pix * 4 * 4},
-        {(void**)&s->part, part_n * 4}, {(void**)&s->part_b, partb_n * 4}, {(void**)&s->loss_part, 1024 * 4},
+        {(void**)&s->part, part_n * 4}, {(void**)&s->part_b, partb_n * 4}, {(void**)&s->loss_part, (size_t)(1024 + 4 * max_batch) * 4},
         {(void**)&s->Fold, pix * 4 * 4}, {(void**)&s->Fnew, pix * 4 * 4}, {&s->xin, pix * 4 * 2},
         {(void**)&s->planes, (size_t)H * W * 4 * 8}, {(void**)&s->sums, (size_t)max_batch * 2 * 64 * 4 * 8},
         {&s->wtc, 8 * 9 * 64 * 64 * 2}, {(void**)&s->derr, 256}, {&s->win, 6 * 64 * 8 * 2},
@@ -349,6 +350,16 @@ plbm_status plbm_sur_set_option(plbm_surrogate h, int option, int value) {
     return PLBM_E_ARG;
 }
 
+plbm_status plbm_sur_set_mean_penalty(plbm_surrogate h, float lambda) {
+    Sur* s = as_sur(h);
+    if (!s || !(lambda >= 0.0f) || !(lambda < 1e30f)) {
+        serr(s, "mean penalty must be finite and >= 0");
+        return PLBM_E_ARG;
+    }
+    s->mean_penalty = lambda;
+    return PLBM_OK;
+}
+
 plbm_status plbm_sur_check(plbm_surrogate h) {
     Sur* s = as_sur(h);
     if (!s) return PLBM_E_ARG;
@@ -427,7 +438,8 @@ plbm_status plbm_sur_train_step(plbm_surrogate h, int B, const void* x, const fl
     if (r != PLBM_OK) return r;
     const long long n = (long long)B * s->H * s->W * 4;
     const int parts = 256;
-    SCK(plbm::cnn_mse(static_cast<const float*>(s->act[5]), target, n, s->dout, s->loss_part, parts, s->stream));
+    SCK(plbm::cnn_mse(static_cast<const float*>(s->act[5]), target, n, (long long)s->H * s->W, s->mean_penalty,
+                      s->loss_part + 1024, s->dout, s->loss_part, parts, s->stream));
     r = backward(s, B, x, s->dout);
     if (r != PLBM_OK) return r;
     ++s->adam_t;

@@ -130,6 +130,7 @@ SIGNATURES = {
     "plbm_sur_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "plbm_sur_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "plbm_sur_set_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "plbm_sur_set_mean_penalty": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_float]),
     "plbm_sur_check": (ctypes.c_int, [ctypes.c_void_p]),
     "plbm_sur_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "plbm_sur_set_norm": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_float)] * 4),

@@ -142,6 +142,10 @@ class Surrogate:
         before the drift gate of advance (PLBM_SUR_OPT_CONSERVE)."""
         self._ok(plbm.lib().plbm_sur_set_option(self.h, 2, 1 if on else 0))
 
+    def set_mean_penalty(self, lam: float):
+        """Weight of the lattice-mean error term of the training loss."""
+        self._ok(plbm.lib().plbm_sur_set_mean_penalty(self.h, float(lam)))
+
     def check(self):
         return int(plbm.lib().plbm_sur_check(self.h))
 

@@ -252,3 +252,36 @@ def test_batched_fallback_equals_plain_stepping(trained, K):
         assert np.array_equal(x.get_populations(), y.get_populations())
     for s in a + b:
         s.close()
+
+
+def test_mean_penalty_enters_the_training_gradient():
+    # loss = MSE + lam mean_{b,c} m_bc^2, m_bc = lattice mean of (pred - target) of
+    # sample b, field c: the gradient a training step forms must equal the
+    # backward pass of dout = 2 (pred - target + lam m) / n.
+    import ctypes
+    import torch
+    net = SG.Surrogate(2, H=5, W=128, seed=11)
+    g = torch.Generator().manual_seed(5)
+    x = torch.randn((2, 5, 128, 4), generator=g).to(torch.bfloat16).cuda()
+    y = (0.3 * torch.randn((2, 5, 128, 4), generator=g) + torch.tensor([0.2, -0.1, 0.05, 0.3])).cuda()
+    p0, _ = net.params()
+    lam = 7.0
+    for lam_k in (0.0, lam):
+        net.set_params(p0)
+        net.set_mean_penalty(lam_k)
+        torch.cuda.synchronize()
+        assert plbm.lib().plbm_sur_train_step(net.h, 2, x.data_ptr(), y.data_ptr(), ctypes.c_float(1e-3),
+                                              None) == plbm.PLBM_OK
+        g_step = net.params()[1].astype(np.float64)
+        net.set_params(p0)
+        pred = net.forward(x, 2).clone()
+        d = pred - y
+        m = d.mean(dim=(1, 2), keepdim=True)
+        dout = (2.0 * (d + lam_k * m) / d.numel()).contiguous()
+        g_ref = net.backward(x, dout, 2).astype(np.float64)
+        assert rel(g_step, g_ref) <= 1e-4, lam_k
+        if lam_k == 0.0:
+            g_plain = g_step
+    assert rel(g_step, g_plain) > 1e-3      # the penalty does change the gradient
+    net.set_mean_penalty(0.0)
+    net.close()
