@@ -159,6 +159,18 @@ def dist_env():
     return ws, rank, local
 
 
+def replica_throughput(torch, t_local, node_updates, dist=None, device="cuda"):
+    """Whole-job time and throughput of N independent replicas (one per rank, the
+    same node_updates each): the job time is the maximum of the ranks' times and
+    the throughput N x node_updates / that time, in MLUPS."""
+    t_max, ws = float(t_local), 1
+    if dist is not None:
+        tt = torch.tensor([t_local], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max, ws = float(tt.item()), dist.get_world_size()
+    return t_max, ws * node_updates / t_max / 1e6
+
+
 def time_device(solver, steps: int, warmup: int, torch, barrier):
     """CUDA-event time of `steps` plbm_step launches on the solver's stream."""
     solver.step(warmup)
@@ -553,13 +565,10 @@ def end_to_end(torch, plbm, fields, L, args, local, barrier, dist, ws):
     t_e2e = time.perf_counter() - t0
     barrier()
     solver2.close()
-    if dist is not None:
-        tt = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
+    t_e2e, e2e_value = replica_throughput(torch, t_e2e, L * L * e2e_steps, dist)
     h2d = 4 * L * L * 8
     d2h = 4 * L * L * 8
-    e2e = {"value": ws * L * L * e2e_steps / t_e2e / 1e6, "unit": "MLUPS",
+    e2e = {"value": e2e_value, "unit": "MLUPS",
            "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps,
            "job": "plbm_init from pinned host fields + %d steps + plbm_moments to pinned host" % e2e_steps}
 
@@ -671,12 +680,7 @@ def main():
     t = e0.elapsed_time(e1) * 1e-3
     healthy = solver.check() == 0
     solver.close()
-    t_max = t
-    if dist is not None:
-        tt = torch.tensor([t], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = ws * L * L * args.steps / t_max / 1e6
+    t_max, value = replica_throughput(torch, t, L * L * args.steps, dist)
     per_launch = t / args.steps
     alg_bytes = 2 * q * ELEM[args.prec] * L * L
     peak, peak_kind = read_peaks()
