@@ -5,8 +5,10 @@
 // [q][nz][ny][pitch] (row index z * ny + y of elem_index).  The rest equilibrium
 // is the product w0_p = w_a w_b w_c of the 1D rest weights.
 //
-// k_stream_collide3<S> (FP32 arithmetic; FP32, FP16 or BF16 storage of the
-// deviation g = f - w0; symmetric five-velocity sets (0, +-a, +-b), D3Q125):
+// k_stream_collide3<S> (FP32 arithmetic; FP16 or BF16 storage of the deviation
+// g = f - w0 on the plain layout; symmetric five-velocity sets (0, +-a, +-b),
+// D3Q125; k_stream_collide3_split below is the FP32 kernel, the same update
+// with a node's populations spread over five warps):
 //   * pull of the 125 populations (Eq. eq:srt read as pull + collide), one node
 //     per thread, coalesced along x;
 //   * moments from the row sums S_a = sum_{b,c} g, T_b, U_c of the deviations,
@@ -166,6 +168,116 @@ __global__ void __launch_bounds__(kB3, 2) k_stream_collide3(const __grid_constan
                 const float d = fmaf(X[a], Pbc, (om * P.w1f[a]) * Qbc);
                 Storage<S>::store(dst + (long long)p * P.plane + here, fmaf(keep, g[p], d));
             }
+        }
+}
+
+// The same update with the 125 populations of a node split over five warps:
+// warp a of a CTA takes the 25 populations (a, b, c) of the 32 nodes
+// x0 .. x0 + 31 (lane = node), so a thread holds 25 values instead of 125 and
+// far more warps fit per SM.  Each warp forms its partial sums (S_a, and T_b,
+// U_c over its own a) into shared memory; warp 0 completes the moments of the
+// 32 nodes and hands rho - 1, u and theta - theta0 back through shared memory.
+constexpr int kSplitNodes = 32;
+constexpr int kSplitThreads = kSplitNodes * kQ1;   // 160
+
+template <typename S>
+__global__ void __launch_bounds__(kSplitThreads) k_stream_collide3_split(const __grid_constant__ LatticeParams P,
+                                                                         const S* __restrict__ src,
+                                                                         S* __restrict__ dst) {
+    __shared__ float sS[kQ1][kSplitNodes];
+    __shared__ float sT[kQ1][kQ1][kSplitNodes];   // [warp a][b][node]
+    __shared__ float sU[kQ1][kQ1][kSplitNodes];   // [warp a][c][node]
+    __shared__ float sM[5][kSplitNodes];          // drho, ux, uy, uz, dth
+    const int a = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int x = blockIdx.x * kSplitNodes + lane;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const bool active = x < P.nx;
+    int xa = 0, yr[kQ1], zr[kQ1];
+    float g[kQ1 * kQ1];
+    if (active) {
+        xa = wrap_add(x, P.vxm[a], P.nx);
+#pragma unroll
+        for (int i = 0; i < kQ1; ++i) {
+            yr[i] = wrap_add(y, P.vym[i], P.ny) * P.pitch;
+            zr[i] = wrap_add(z, P.vzm[i], P.nz) * P.ny * P.pitch;
+        }
+        const long long pa = (long long)a * kQ1 * kQ1 * P.plane;
+#pragma unroll
+        for (int b = 0; b < kQ1; ++b)
+#pragma unroll
+            for (int c = 0; c < kQ1; ++c)
+                g[b * kQ1 + c] = Storage<S>::load(src + pa + (long long)(b * kQ1 + c) * P.plane + (zr[c] + yr[b] + xa));
+        float Sa = 0.0f, Uc[kQ1];
+#pragma unroll
+        for (int c = 0; c < kQ1; ++c) Uc[c] = 0.0f;
+#pragma unroll
+        for (int b = 0; b < kQ1; ++b) {
+            float T = 0.0f;
+#pragma unroll
+            for (int c = 0; c < kQ1; ++c) {
+                T += g[b * kQ1 + c];
+                Uc[c] += g[b * kQ1 + c];
+            }
+            sT[a][b][lane] = T;
+            Sa += T;
+        }
+        sS[a][lane] = Sa;
+#pragma unroll
+        for (int c = 0; c < kQ1; ++c) sU[a][c][lane] = Uc[c];
+    }
+    __syncthreads();
+    if (a == 0 && active) {
+        float drho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f, de = 0.0f;
+#pragma unroll
+        for (int i = 0; i < kQ1; ++i) {
+            const float vi = (float)P.v[i];
+            float Ti = 0.0f, Ui = 0.0f;
+#pragma unroll
+            for (int w = 0; w < kQ1; ++w) {
+                Ti += sT[w][i][lane];
+                Ui += sU[w][i][lane];
+            }
+            const float Si = sS[i][lane];
+            drho += Si;
+            jx += vi * Si;
+            jy += vi * Ti;
+            jz += vi * Ui;
+            de += vi * vi * (Si + Ti + Ui);
+        }
+        const float rho = 1.0f + drho;
+        const float ir = 1.0f / rho;
+        const float ux = jx * ir, uy = jy * ir, uz = jz * ir;
+        const float dth = ((de - 3.0f * P.theta0f * drho) * ir - (ux * ux + uy * uy + uz * uz)) * (1.0f / 3.0f);
+        flag_status<float>(P, rho, P.theta0f + dth);
+        sM[0][lane] = drho;
+        sM[1][lane] = ux;
+        sM[2][lane] = uy;
+        sM[3][lane] = uz;
+        sM[4][lane] = dth;
+    }
+    __syncthreads();
+    if (!active) return;
+    const float drho = sM[0][lane], dth = sM[4][lane];
+    const float rho = 1.0f + drho;
+    float drx[kQ1], dry[kQ1], drz[kQ1];
+    axis_dev(P, sM[1][lane], dth, drx);
+    axis_dev(P, sM[2][lane], dth, dry);
+    axis_dev(P, sM[3][lane], dth, drz);
+    const float om = P.omegaf;
+    const float X = om * fmaf(drho, P.w1f[a], rho * drx[a]);
+    const float Wa = om * P.w1f[a];
+    const float keep = 1.0f - om;
+    const long long here = ((long long)z * P.ny + y) * P.pitch + x;
+    const long long pa = (long long)a * kQ1 * kQ1 * P.plane;
+#pragma unroll
+    for (int b = 0; b < kQ1; ++b)
+#pragma unroll
+        for (int c = 0; c < kQ1; ++c) {
+            const float rzc = P.w1f[c] + drz[c];
+            const float Pbc = (P.w1f[b] + dry[b]) * rzc;
+            const float Qbc = dry[b] * rzc + P.w1f[b] * drz[c];
+            const float d = fmaf(X, Pbc, Wa * Qbc);
+            Storage<S>::store(dst + pa + (long long)(b * kQ1 + c) * P.plane + here, fmaf(keep, g[b * kQ1 + c], d));
         }
 }
 
@@ -684,7 +796,8 @@ cudaError_t launch_step3(int prec, const LatticeParams& P, const void* src, void
     }
     switch (prec) {
         case kF32:
-            k_stream_collide3<float><<<grid3(P), kB3, 0, s>>>(P, static_cast<const float*>(src), static_cast<float*>(dst));
+            k_stream_collide3_split<float><<<dim3((P.nx + kSplitNodes - 1) / kSplitNodes, P.ny, P.nz), kSplitThreads, 0,
+                                              s>>>(P, static_cast<const float*>(src), static_cast<float*>(dst));
             break;
         case kF16Dev:
             k_stream_collide3<__half><<<grid3(P), kB3, 0, s>>>(P, static_cast<const __half*>(src), static_cast<__half*>(dst));
