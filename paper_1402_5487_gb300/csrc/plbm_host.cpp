@@ -653,10 +653,11 @@ plbm_status plbm_step(plbm_handle hh, long n) {
                     el = h->P.dim == 3 ? plbm::launch_step3(h->prec, h->P, h->f[c], h->f[c ^ 1], h->cap)
                                        : plbm::launch_step(h->prec, h->P, h->f[c], h->f[c ^ 1], false, h->cap);
                 const cudaError_t ec = cudaStreamEndCapture(h->cap, &graph);
+                const cudaError_t ei = (el == cudaSuccess && ec == cudaSuccess)
+                                           ? cudaGraphInstantiate(&g, graph, 0) : cudaSuccess;
+                if (graph) cudaGraphDestroy(graph);
                 CK(el);
                 CK(ec);
-                const cudaError_t ei = cudaGraphInstantiate(&g, graph, 0);
-                cudaGraphDestroy(graph);
                 CK(ei);
             }
             CK(cudaGraphLaunch(g, h->stream));
