@@ -1180,10 +1180,11 @@ plbm_status plbm_batch_step(plbm_batch bb, long n, int mode) {
                 plbm_status st = batch_launch(b, scheme, parity, ctas);
                 if (st == PLBM_OK) st = batch_launch(b, scheme, parity ^ 1, ctas);
                 cudaError_t ec = cudaStreamEndCapture(b->stream, &graph);
+                cudaError_t ei = (st == PLBM_OK && ec == cudaSuccess) ? cudaGraphInstantiate(&g, graph, 0)
+                                                                       : cudaSuccess;
+                if (graph) cudaGraphDestroy(graph);
                 if (st != PLBM_OK) return st;
                 BCK(ec);
-                cudaError_t ei = cudaGraphInstantiate(&g, graph, 0);
-                cudaGraphDestroy(graph);
                 BCK(ei);
             }
             BCK(cudaGraphLaunch(g, b->stream));
