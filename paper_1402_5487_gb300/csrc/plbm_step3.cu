@@ -176,7 +176,9 @@ __global__ void __launch_bounds__(kB3, 2) k_stream_collide3(const __grid_constan
 // x0 .. x0 + 31 (lane = node), so a thread holds 25 values instead of 125 and
 // far more warps fit per SM.  Each warp forms its partial sums (S_a, and T_b,
 // U_c over its own a) into shared memory; warp 0 completes the moments of the
-// 32 nodes and hands rho - 1, u and theta - theta0 back through shared memory.
+// 32 nodes and the x rule; warp a then forms row b = a of the factor table
+// P_bc = r^y_b r^z_c, Q_bc = dr^y_b r^z_c + w_b dr^z_c, which every warp reads
+// (three barriers per CTA).
 constexpr int kSplitNodes = 32;
 constexpr int kSplitThreads = kSplitNodes * kQ1;   // 160
 
@@ -188,6 +190,9 @@ __global__ void __launch_bounds__(kSplitThreads) k_stream_collide3_split(const _
     __shared__ float sT[kQ1][kQ1][kSplitNodes];   // [warp a][b][node]
     __shared__ float sU[kQ1][kQ1][kSplitNodes];   // [warp a][c][node]
     __shared__ float sM[5][kSplitNodes];          // drho, ux, uy, uz, dth
+    __shared__ float sDx[kQ1][kSplitNodes];       // dr^x_a
+    __shared__ float sP[kQ1][kQ1][kSplitNodes];   // P_bc = r^y_b r^z_c
+    __shared__ float sQ[kQ1][kQ1][kSplitNodes];   // Q_bc = dr^y_b r^z_c + w_b dr^z_c
     const int a = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int x = blockIdx.x * kSplitNodes + lane;
     const int y = blockIdx.y, z = blockIdx.z;
@@ -250,21 +255,35 @@ __global__ void __launch_bounds__(kSplitThreads) k_stream_collide3_split(const _
         const float dth = ((de - 3.0f * P.theta0f * drho) * ir - (ux * ux + uy * uy + uz * uz)) * (1.0f / 3.0f);
         flag_status<float>(P, rho, P.theta0f + dth);
         sM[0][lane] = drho;
-        sM[1][lane] = ux;
-        sM[2][lane] = uy;
-        sM[3][lane] = uz;
+        sM[1][lane] = uy;
+        sM[2][lane] = uz;
         sM[4][lane] = dth;
+        float drx[kQ1];
+        axis_dev(P, ux, dth, drx);
+#pragma unroll
+        for (int i = 0; i < kQ1; ++i) sDx[i][lane] = drx[i];
+    }
+    __syncthreads();
+    // warp a forms row b = a of the factor table for its 32 nodes
+    if (active) {
+        const float dth = sM[4][lane];
+        float dry[kQ1], drz[kQ1];
+        axis_dev(P, sM[1][lane], dth, dry);
+        axis_dev(P, sM[2][lane], dth, drz);
+        const int b = a;
+#pragma unroll
+        for (int c = 0; c < kQ1; ++c) {
+            const float rzc = P.w1f[c] + drz[c];
+            sP[b][c][lane] = (P.w1f[b] + dry[b]) * rzc;
+            sQ[b][c][lane] = dry[b] * rzc + P.w1f[b] * drz[c];
+        }
     }
     __syncthreads();
     if (!active) return;
-    const float drho = sM[0][lane], dth = sM[4][lane];
+    const float drho = sM[0][lane];
     const float rho = 1.0f + drho;
-    float drx[kQ1], dry[kQ1], drz[kQ1];
-    axis_dev(P, sM[1][lane], dth, drx);
-    axis_dev(P, sM[2][lane], dth, dry);
-    axis_dev(P, sM[3][lane], dth, drz);
     const float om = P.omegaf;
-    const float X = om * fmaf(drho, P.w1f[a], rho * drx[a]);
+    const float X = om * fmaf(drho, P.w1f[a], rho * sDx[a][lane]);
     const float Wa = om * P.w1f[a];
     const float keep = 1.0f - om;
     const long long here = ((long long)z * P.ny + y) * P.pitch + x;
@@ -273,10 +292,7 @@ __global__ void __launch_bounds__(kSplitThreads) k_stream_collide3_split(const _
     for (int b = 0; b < kQ1; ++b)
 #pragma unroll
         for (int c = 0; c < kQ1; ++c) {
-            const float rzc = P.w1f[c] + drz[c];
-            const float Pbc = (P.w1f[b] + dry[b]) * rzc;
-            const float Qbc = dry[b] * rzc + P.w1f[b] * drz[c];
-            const float d = fmaf(X, Pbc, Wa * Qbc);
+            const float d = fmaf(X, sP[b][c][lane], Wa * sQ[b][c][lane]);
             Storage<S>::store(dst + pa + (long long)(b * kQ1 + c) * P.plane + here, fmaf(keep, g[b * kQ1 + c], d));
         }
 }
