@@ -148,3 +148,33 @@ def test_matched_relaxation_constant():
     assert abs(nu3 - nu4) < 1e-15
     # footnote: 362 LBGK iterations are 362 * 2/sqrt(3) ~ 418 zeta=4 iterations
     assert abs(vals["shock6_iterations_lbgk"] * 2 / math.sqrt(3) - vals["shock6_iterations_param"]) < 0.01
+
+
+def test_sound_wave_simulation_decay_and_speed():
+    # A right-moving adiabatic sound wave (rho' = eps, u' = c eps, theta' = (gamma - 1)
+    # eps theta0, gamma = (d+2)/d = 2) followed through its Riemann variable
+    # R = p'/c + u' (p = rho theta), which the entropy mode (p' = u' = 0) and the
+    # left-moving wave (p'/c = -u') do not carry: its amplitude decays at nu k^2 (the
+    # sound attenuation of this model equals nu) and its phase moves at c = sqrt(2 theta).
+    L, theta0, omega, eps = 256, 1.0, 1.3, 1e-4
+    c = math.sqrt(2.0 * theta0)
+    nu = (1 / omega - 0.5) * theta0
+    k = 2 * np.pi / L
+    lat = O.Lattice(2, V5, omega, L, 4, theta0=theta0)
+    x = np.arange(L)[None, :] * np.ones((4, 1))
+    s = np.cos(k * x)
+    f = lat.init(1 + eps * s, eps * c * s, 0 * x, theta0 * (1 + eps * s))
+    steps = 1850
+    modes = []
+    for _ in range(3):
+        f = lat.run(f, steps)
+        rho, ux, _, th = (m[0] for m in lat.moments(f))
+        R = (rho * th - theta0) / c + ux
+        modes.append(np.sum(R * np.exp(-1j * k * np.arange(L))))
+    rate = -math.log(abs(modes[2]) / abs(modes[0])) / (k * k * 2 * steps)
+    assert abs(rate / nu - 1) < 5e-3, rate / nu
+    # phase advance: R ~ cos(k (x - c t)); the mode's phase falls by k c t (mod 2 pi)
+    dphi = np.angle(modes[1] / modes[0])
+    expect = -(k * c * steps) % (2 * np.pi)
+    expect = expect - 2 * np.pi if expect > np.pi else expect
+    assert abs(dphi - expect) < 5e-3 * k * c * steps, (dphi, expect)
