@@ -205,7 +205,7 @@ def test_conservation_periodic_f64():
     s = plbm.Solver(2, V5, 1.3, L, L, theta0=1.0, prec="f64")
     s.init(*fields)
     c0 = s.conserved()
-    s.step(1000)
+    s.step(10000)
     c1 = s.conserved()
     assert np.max(np.abs(c1 - c0)) <= 1e-12 * np.max(np.abs(c0))
     lat = O.Lattice(2, V5, 1.3, L, L, theta0=1.0)
