@@ -539,8 +539,44 @@ def cpu_oracle_sample(L, seconds=12.0, max_steps=50):
         f = lat.step(f)
         n += 1
     dt = time.perf_counter() - t0
-    return {"value": L * L * n / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-            "sample": "%dx%d D2Q25 KH, %d FP64 steps of the C oracle (OpenMP over rows)" % (L, L, n)}
+    out = {"value": L * L * n / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+           "sample": "%dx%d D2Q25 KH, %d FP64 steps of the C oracle (OpenMP over rows)" % (L, L, n)}
+    out["per_config"] = oracle_configs(O, cores)
+    return out
+
+
+def oracle_configs(O, cores, seconds=2.0):
+    """The oracle on one host thread and on all of them, for the 1000-node D1Q5 shock
+    tube, the 512 x 512 and the 2048 x 2048 D2Q25 shear layers (short samples)."""
+    left, right = (1.1, 0.0, 0.5), (1.0, 0.0, 0.5)
+    cases = {
+        "shock1000_d1q5": (lambda: O.Lattice(1, V5, 1.5, 1000, 1, bc="fixed", theta0=0.5, left_state=left,
+                                             right_state=right), lambda: I.shock_tube_fields(1000, left, right),
+                           1000),
+        "kh512_d2q25": (lambda: O.Lattice(2, V5, OMEGA, 512, 512, theta0=THETA0), lambda: I.kh_fields(512),
+                        512 * 512),
+        "kh2048_d2q25": (lambda: O.Lattice(2, V5, OMEGA, 2048, 2048, theta0=THETA0), lambda: I.kh_fields(2048),
+                         2048 * 2048),
+    }
+    res = {}
+    try:
+        for name, (mk, fields, nodes) in cases.items():
+            lat = mk()
+            rho, ux, uy, th = fields()
+            f = lat.init(rho, ux, uy if lat.dim == 2 else None, th)
+            row = {}
+            for threads in (1, cores):
+                O.set_threads(threads)
+                f = lat.step(f)
+                n, t0 = 0, time.perf_counter()
+                while n < 1000 and (n < 1 or time.perf_counter() - t0 < seconds):
+                    f = lat.step(f)
+                    n += 1
+                row["threads_%d" % threads] = nodes * n / (time.perf_counter() - t0) / 1e6
+            res[name] = row
+    finally:
+        O.set_threads(cores)
+    return res
 
 
 def end_to_end(torch, plbm, fields, L, args, local, barrier, dist, ws):
