@@ -223,7 +223,7 @@ def run_variant3(torch, n, prec, steps, warmup):
             "status": "ok" if st == 0 else "diverged"}
 
 
-def run_batched(torch, steps=100, warmup=4, n=256, config=None):
+def run_batched(torch, steps=400, warmup=4, n=256, config=None):
     """Batched sweep of n admissible instances (FP32): persistent graph vs per-instance launches.
     config = (block_x, ctas_per_sm, order) fixes the persistent launch instead of autotuning."""
     from paper_1402_5487_gb300 import batch as B
