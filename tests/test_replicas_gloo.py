@@ -43,7 +43,7 @@ def _rank(rank, world, port, times, updates, out):
 def test_two_gloo_ranks_report_max_time_and_summed_throughput():
     world, updates = 2, 4096 * 4096 * 400
     times = [0.050, 0.047]
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_rank, args=(world, _free_port(), times, updates, out), nprocs=world, join=True)
         res = dict(out)
