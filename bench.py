@@ -657,11 +657,9 @@ def main():
         import oracle as O
         lat = O.Lattice(2, V5, OMEGA, L, L, theta0=THETA0)
         f = lat.init(*I.kh_fields(L))
-        for _ in range(args.warmup):
-            f = lat.step(f)
+        f = lat.run(f, args.warmup)
         t0 = time.perf_counter()
-        for _ in range(args.steps):
-            f = lat.step(f)
+        f = lat.run(f, args.steps)
         dt = time.perf_counter() - t0
         val = L * L * args.steps / dt / 1e6
         cores = O.max_threads()
