@@ -206,6 +206,31 @@ def run_variant(torch, L, prec, steps, warmup, barrier, dim=2, v=V5, bc="periodi
             "status": "ok" if st == 0 else "diverged"}
 
 
+def run_diag_overhead(torch, L, steps, every):
+    """Cost of FP64 diagnostics every `every` steps: `steps` steps as
+    plbm_step_diagnostics(every) calls (each a host synchronisation) against plain
+    steps, both wall-timed with a synchronisation at the end."""
+    from paper_1402_5487_gb300 import plbm
+    s = plbm.Solver(2, V5, OMEGA, L, L, theta0=THETA0, prec="f32")
+    s.init(*I.kh_fields(L))
+    s.step(20)
+    times = {}
+    for mode in ("plain", "fused", "plain", "fused"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if mode == "plain":
+            s.step(steps)
+        else:
+            for _ in range(steps // every):
+                d = s.step_diagnostics(every)
+        torch.cuda.synchronize()
+        times[mode] = time.perf_counter() - t0
+    s.close()
+    return {"steps": steps, "every": every, "plain_ms_per_step": times["plain"] / steps * 1e3,
+            "fused_ms_per_step": times["fused"] / steps * 1e3,
+            "overhead": times["fused"] / times["plain"] - 1.0, "last_mass": d["mass"]}
+
+
 def run_variant3(torch, n, prec, steps, warmup):
     """D3Q125 {0,+-1,+-3}^3 double shear layer on an n^3 periodic grid."""
     from paper_1402_5487_gb300 import plbm
@@ -731,6 +756,7 @@ def main():
             if prec == args.prec:
                 continue
             variants["kh%d_%s" % (L, prec)] = run_variant(torch, L, prec, 200, 10, lambda: None)
+        variants["kh2048_f32_diagnostics_every_10"] = run_diag_overhead(torch, 2048, 400, 10)
         variants["kh512_f32"] = run_variant(torch, 512, "f32", 1000, 50, lambda: None)
         variants["kh512_f64"] = run_variant(torch, 512, "f64", 200, 20, lambda: None)
         pf, pth = I.paper_kh_fields()

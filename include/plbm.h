@@ -206,6 +206,14 @@ plbm_status plbm_moments(plbm_handle h, double *rho, double *ux, double *uy, dou
  * Synchronous. */
 plbm_status plbm_diagnostics(plbm_handle h, plbm_diag *out);
 
+/* Advance n >= 1 steps as plbm_step does, the last one fused with the
+ * reductions of plbm_diagnostics (the step kernel's blocks form the FP64 partial
+ * sums of the moments it computes anyway: mass, momentum and energy are those of
+ * the state after the step, as collision conserves them; the minima are of the
+ * pulled state's rho and theta).  Synchronous.  3D handles take plbm_step and
+ * plbm_diagnostics.  Errors: those of plbm_step; PLBM_E_ARG for n < 1. */
+plbm_status plbm_step_diagnostics(plbm_handle h, long n, plbm_diag *out);
+
 /* Conserved sums out[4] = (mass, jx, jy, energy) of the stored state, FP64.
  * Synchronous.  (3D handles: plbm_conserved3.) */
 plbm_status plbm_conserved(plbm_handle h, double out[4]);

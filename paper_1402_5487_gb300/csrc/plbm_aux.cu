@@ -252,27 +252,7 @@ __global__ void k_init_sym5_dev(const __grid_constant__ LatticeParams P, const d
 // through error-free sums and products, ~2^-48 relative), then
 // rho = 1 + sum g, j = sum v g, E = d theta0 + sum |v|^2 g (the rest identities of
 // the 1D rule) and theta = (E / rho - |u|^2) / d in FP64.
-struct FF {
-    float hi, lo;
-};
-__device__ __forceinline__ FF ff_add(FF a, float b) {
-    const float s = a.hi + b;
-    const float t = s - a.hi;
-    const float e = (a.hi - (s - t)) + (b - t);
-    return {s, a.lo + e};
-}
-__device__ __forceinline__ FF ff_add(FF a, FF b) {
-    const float s = a.hi + b.hi;
-    const float t = s - a.hi;
-    const float e = (a.hi - (s - t)) + (b.hi - t);
-    return {s, (a.lo + b.lo) + e};
-}
-__device__ __forceinline__ FF ff_scale(FF a, float v) {
-    const float p = a.hi * v;
-    const float e = fmaf(a.hi, v, -p);
-    return {p, fmaf(a.lo, v, e)};
-}
-__device__ __forceinline__ double ff_f64(FF a) { return (double)a.hi + (double)a.lo; }
+// (FF, ff_add, ff_scale, ff_f64: plbm_device.cuh)
 
 template <typename S, int Q1, int DIM>
 __global__ void k_moments_dev(const __grid_constant__ LatticeParams P, const S* __restrict__ f, double* rho,
@@ -418,6 +398,62 @@ __global__ void __launch_bounds__(kBlockX) k_reduce_state(const __grid_constant_
     }
     const int blk = blockIdx.y * gridDim.x + blockIdx.x;
     block_reduce_diag<kBlockX>(d, P.partials + (long long)blk * kPartialStride);
+}
+
+// The same record for 16/32-bit storage with compile-time q1, on the FP32 pipe:
+// per node the row and column sums of the stored deviations in float-float,
+// mass - 1 = sum g, j = sum v g, E - d theta0 = sum |v|^2 g, then the block sums
+// in float-float (block_reduce_diagf); the minima from FP32 rho and theta.
+template <typename S, int Q1, int DIM>
+__global__ void __launch_bounds__(kBlockX) k_reduce_state_dev(const __grid_constant__ LatticeParams P,
+                                                              const S* __restrict__ f) {
+    const int x = blockIdx.x * kBlockX + threadIdx.x;
+    const int y = blockIdx.y;
+    NodeDiagF d;
+    diagf_zero(d);
+    double rmin = 1e300, tmin = 1e300;
+    if (x < P.nx) {
+        FF Sx[Q1], Ty[Q1];
+#pragma unroll
+        for (int i = 0; i < Q1; ++i) Sx[i] = Ty[i] = FF{0.0f, 0.0f};
+#pragma unroll
+        for (int i = 0; i < Q1; ++i)
+#pragma unroll
+            for (int j = 0; j < (DIM == 2 ? Q1 : 1); ++j) {
+                const int p = DIM == 2 ? i * Q1 + j : i;
+                const float g = Storage<S>::load(f + elem_index(P, p, x, y));
+                Sx[i] = ff_add(Sx[i], g);
+                if (DIM == 2) Ty[j] = ff_add(Ty[j], g);
+            }
+        FF dm{0.0f, 0.0f}, jx = dm, jy = dm, de = dm;
+#pragma unroll
+        for (int i = 0; i < Q1; ++i) {
+            const float vi = (float)P.v[i];
+            dm = ff_add(dm, Sx[i]);
+            jx = ff_add(jx, ff_scale(Sx[i], vi));
+            de = ff_add(de, ff_scale(ff_scale(Sx[i], vi), vi));
+            if (DIM == 2) {
+                jy = ff_add(jy, ff_scale(Ty[i], vi));
+                de = ff_add(de, ff_scale(ff_scale(Ty[i], vi), vi));
+            }
+        }
+        // rho and theta of the node in FP64 (the minima are reported in FP64)
+        const double rho = 1.0 + ff_f64(dm);
+        const double ir = 1.0 / rho;
+        const double ux = ff_f64(jx) * ir, uy = DIM == 2 ? ff_f64(jy) * ir : 0.0;
+        const double th = (((double)DIM * P.theta0 + ff_f64(de)) * ir - (ux * ux + uy * uy)) / (double)DIM;
+        flag_status<double>(P, rho, th);
+        d.dmass = dm;
+        d.jx = jx;
+        d.jy = jy;
+        d.denergy = de;
+        d.n = 1.0f;
+        rmin = rho;
+        tmin = th;
+    }
+    const int blk = blockIdx.y * gridDim.x + blockIdx.x;
+    block_reduce_diagf<kBlockX, true>(d, (double)DIM * P.theta0, P.partials + (long long)blk * kPartialStride, rmin,
+                                      tmin);
 }
 
 // One block of kFinalThreads threads sums the per-block partials in a fixed
@@ -574,7 +610,20 @@ cudaError_t launch_finalize(const LatticeParams& P, int nblocks, double* out, cu
 cudaError_t launch_reduce_state(int prec, const LatticeParams& P, const void* f, double* out,
                                 cudaStream_t stream) {
     dim3 grid((P.nx + kBlockX - 1) / kBlockX, P.ny);
-    PLBM_DISPATCH(prec, (k_reduce_state<S><<<grid, kBlockX, 0, stream>>>(P, static_cast<const S*>(f))));
+    bool done = false;
+#define PLBM_RED_Q(Q1v, DIMv)                                                                           \
+    if (!done && prec != kF64 && P.q1 == Q1v && P.dim == DIMv) {                                        \
+        PLBM_DISPATCH_DEV(prec, (k_reduce_state_dev<S, Q1v, DIMv><<<grid, kBlockX, 0, stream>>>(         \
+                                    P, static_cast<const S*>(f))));                                     \
+        done = true;                                                                                    \
+    }
+    PLBM_RED_Q(3, 2)
+    PLBM_RED_Q(4, 2)
+    PLBM_RED_Q(5, 2)
+    PLBM_RED_Q(5, 1)
+#undef PLBM_RED_Q
+    if (!done)
+        PLBM_DISPATCH(prec, (k_reduce_state<S><<<grid, kBlockX, 0, stream>>>(P, static_cast<const S*>(f))));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_finalize(P, reduce_blocks(P), out, stream);

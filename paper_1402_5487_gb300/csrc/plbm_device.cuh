@@ -114,6 +114,136 @@ __device__ __forceinline__ void flag_status(const LatticeParams& P, R rho, R the
     }
 }
 
+// Float-float numbers: an FP32 pair hi + lo carried through error-free sums
+// (TwoSum) and products (FMA), ~2^-48 relative: FP64-grade sums of FP32 data on
+// the FP32 pipe (GB300's FP64 rate is two operations per SM per cycle).
+struct FF {
+    float hi, lo;
+};
+__device__ __forceinline__ FF ff_add(FF a, float b) {
+    const float s = a.hi + b;
+    const float t = s - a.hi;
+    const float e = (a.hi - (s - t)) + (b - t);
+    return {s, a.lo + e};
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+    const float s = a.hi + b.hi;
+    const float t = s - a.hi;
+    const float e = (a.hi - (s - t)) + (b.hi - t);
+    return {s, (a.lo + b.lo) + e};
+}
+__device__ __forceinline__ FF ff_scale(FF a, float v) {
+    const float p = a.hi * v;
+    const float e = fmaf(a.hi, v, -p);
+    return {p, fmaf(a.lo, v, e)};
+}
+__device__ __forceinline__ double ff_f64(FF a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ FF ff_shfl_down(FF a, int off) {
+    return {__shfl_down_sync(0xffffffffu, a.hi, off), __shfl_down_sync(0xffffffffu, a.lo, off)};
+}
+
+// Per-thread diagnostics of 16/32-bit kernels: deviations from the rest state
+// (mass - n, energy - n d theta0) in float-float, n the thread's node count.
+struct NodeDiagF {
+    FF dmass, jx, jy, denergy;
+    float rho_min, theta_min, n;
+};
+__device__ __forceinline__ void diagf_zero(NodeDiagF& d) {
+    d.dmass = d.jx = d.jy = d.denergy = FF{0.0f, 0.0f};
+    d.rho_min = d.theta_min = 3.0e38f;
+    d.n = 0.0f;
+}
+
+// Order-preserving int64 key of a double (total order, negatives included), so
+// that FP64 minima reduce on the integer pipe.
+__device__ __forceinline__ long long dkey(double v) {
+    const long long b = __double_as_longlong(v);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double dunkey(long long k) {
+    return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
+}
+__device__ __forceinline__ long long kmin(long long a, long long b) { return a < b ? a : b; }
+
+// Block reduction of NodeDiagF in float-float; thread 0 writes the same FP64
+// record as block_reduce_diag (mass = n + dmass, energy = n d theta0 + denergy).
+// DMIN: the minima are the caller's FP64 rho_min_d, theta_min_d (1e300 for no
+// node), reduced as order-preserving integer keys, instead of the FP32 ones of d.
+template <int NT, bool DMIN = false>
+__device__ __forceinline__ void block_reduce_diagf(NodeDiagF d, double dtheta0, double* out, double rho_min_d = 0.0,
+                                                   double theta_min_d = 0.0) {
+    __shared__ float sh[11][NT / 32];
+    __shared__ long long shk[2][NT / 32];
+    long long kr = 0, kt = 0;
+    if (DMIN) {
+        kr = dkey(rho_min_d);
+        kt = dkey(theta_min_d);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            kr = kmin(kr, __shfl_down_sync(0xffffffffu, kr, off));
+            kt = kmin(kt, __shfl_down_sync(0xffffffffu, kt, off));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            shk[0][threadIdx.x >> 5] = kr;
+            shk[1][threadIdx.x >> 5] = kt;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        d.dmass = ff_add(d.dmass, ff_shfl_down(d.dmass, off));
+        d.jx = ff_add(d.jx, ff_shfl_down(d.jx, off));
+        d.jy = ff_add(d.jy, ff_shfl_down(d.jy, off));
+        d.denergy = ff_add(d.denergy, ff_shfl_down(d.denergy, off));
+        d.rho_min = fminf(d.rho_min, __shfl_down_sync(0xffffffffu, d.rho_min, off));
+        d.theta_min = fminf(d.theta_min, __shfl_down_sync(0xffffffffu, d.theta_min, off));
+        d.n += __shfl_down_sync(0xffffffffu, d.n, off);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        sh[0][warp] = d.dmass.hi;
+        sh[1][warp] = d.dmass.lo;
+        sh[2][warp] = d.jx.hi;
+        sh[3][warp] = d.jx.lo;
+        sh[4][warp] = d.jy.hi;
+        sh[5][warp] = d.jy.lo;
+        sh[6][warp] = d.denergy.hi;
+        sh[7][warp] = d.denergy.lo;
+        sh[8][warp] = d.rho_min;
+        sh[9][warp] = d.theta_min;
+        sh[10][warp] = d.n;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        FF m{0.f, 0.f}, a{0.f, 0.f}, b{0.f, 0.f}, e{0.f, 0.f};
+        float rmin = 3.0e38f, tmin = 3.0e38f, n = 0.0f;
+        for (int w = 0; w < NT / 32; ++w) {
+            m = ff_add(m, FF{sh[0][w], sh[1][w]});
+            a = ff_add(a, FF{sh[2][w], sh[3][w]});
+            b = ff_add(b, FF{sh[4][w], sh[5][w]});
+            e = ff_add(e, FF{sh[6][w], sh[7][w]});
+            rmin = fminf(rmin, sh[8][w]);
+            tmin = fminf(tmin, sh[9][w]);
+            n += sh[10][w];
+        }
+        out[0] = (double)n + ff_f64(m);
+        out[1] = ff_f64(a);
+        out[2] = ff_f64(b);
+        out[3] = (double)n * dtheta0 + ff_f64(e);
+        if (DMIN) {
+            long long r = shk[0][0], t = shk[1][0];
+            for (int w = 1; w < NT / 32; ++w) {
+                r = kmin(r, shk[0][w]);
+                t = kmin(t, shk[1][w]);
+            }
+            out[4] = dunkey(r);
+            out[5] = dunkey(t);
+        } else {
+            out[4] = rmin < 3.0e38f ? (double)rmin : 1e300;
+            out[5] = tmin < 3.0e38f ? (double)tmin : 1e300;
+        }
+    }
+}
+
 // Block reduction of NodeDiag; thread 0 writes kPartialStride doubles to out.
 template <int NT>
 __device__ __forceinline__ void block_reduce_diag(NodeDiag d, double* out) {
@@ -414,8 +544,12 @@ k_stream_collide(const __grid_constant__ LatticeParams P, const S* __restrict__ 
     const int y = blockIdx.y;
     const bool active = x < P.nx;
 
-    NodeDiag d;
-    if (REDUCE) diag_zero(d);
+    NodeDiag d;       // FP64 storage
+    NodeDiagF df;     // 16/32-bit storage
+    if (REDUCE) {
+        diag_zero(d);
+        diagf_zero(df);
+    }
 
     if (active) {
         PullIndex<Q1, DIM> ix;
@@ -466,12 +600,13 @@ k_stream_collide(const __grid_constant__ LatticeParams P, const S* __restrict__ 
             DeviationCore<Q1, DIM>::collide(g, P, drho, th, jx, jy, e);
             flag_status<float>(P, 1.0f + drho, th);
             if (REDUCE) {
-                d.mass = 1.0 + (double)drho;
-                d.jx = (double)jx;
-                d.jy = (double)jy;
-                d.energy = (double)DIM * P.theta0 + (double)e;
-                d.rho_min = 1.0 + (double)drho;
-                d.theta_min = (double)th;
+                df.dmass = FF{drho, 0.0f};
+                df.jx = FF{jx, 0.0f};
+                df.jy = FF{jy, 0.0f};
+                df.denergy = FF{e, 0.0f};
+                df.rho_min = 1.0f + drho;
+                df.theta_min = th;
+                df.n = 1.0f;
             }
 #pragma unroll
             for (int p = 0; p < Q; ++p) {
@@ -482,7 +617,10 @@ k_stream_collide(const __grid_constant__ LatticeParams P, const S* __restrict__ 
     }
     if (REDUCE) {
         const int blk = blockIdx.y * gridDim.x + blockIdx.x;
-        block_reduce_diag<kBlockX>(d, P.partials + (long long)blk * kPartialStride);
+        if constexpr (!Storage<S>::kDeviation && sizeof(S) == 8)
+            block_reduce_diag<kBlockX>(d, P.partials + (long long)blk * kPartialStride);
+        else
+            block_reduce_diagf<kBlockX>(df, (double)DIM * P.theta0, P.partials + (long long)blk * kPartialStride);
     }
 }
 

@@ -741,6 +741,37 @@ plbm_status plbm_diagnostics(plbm_handle hh, plbm_diag* out) {
     return PLBM_OK;
 }
 
+plbm_status plbm_step_diagnostics(plbm_handle hh, long n, plbm_diag* out) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    plbm_status st = usable(h);
+    if (st != PLBM_OK) return st;
+    if (n < 1 || !out) { set_err(h, "n must be >= 1 and out non-NULL"); return PLBM_E_ARG; }
+    if (h->P.dim == 3) {
+        st = plbm_step(hh, n);
+        return st != PLBM_OK ? st : plbm_diagnostics(hh, out);
+    }
+    if (n > 1) {
+        st = plbm_step(hh, n - 1);
+        if (st != PLBM_OK) return st;
+    }
+    CK(plbm::launch_step(h->prec, h->P, h->f[h->cur], h->f[h->cur ^ 1], true, h->stream));
+    h->cur ^= 1;
+    ++h->steps;
+    CK(plbm::launch_finalize(h->P, plbm::step_blocks(h->P), h->result, h->stream));
+    CK(cudaMemcpyAsync(h->host_buf, h->result, 7 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(h->host_buf + 8, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    out->mass = h->host_buf[0];
+    out->jx = h->host_buf[1];
+    out->jy = h->host_buf[2];
+    out->energy = h->host_buf[3];
+    out->rho_min = h->host_buf[4];
+    out->theta_min = h->host_buf[5];
+    std::memcpy(&out->status, h->host_buf + 8, sizeof(unsigned));
+    out->steps = h->steps;
+    return PLBM_OK;
+}
+
 plbm_status plbm_conserved(plbm_handle hh, double out[4]) {
     Handle* h = reinterpret_cast<Handle*>(hh);
     if (h && h->P.dim == 3) { set_err(h, "3D handle: use plbm_conserved3"); return PLBM_E_ARG; }

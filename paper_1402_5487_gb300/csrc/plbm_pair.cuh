@@ -167,7 +167,7 @@ __device__ __forceinline__ bool healthy2(float2 rho, float2 th) {
 template <typename S, bool REDUCE>
 __device__ __forceinline__ void pair_node(const PairParams& P, const typename PairStore<S>::V* __restrict__ src,
                                           typename PairStore<S>::V* __restrict__ dst, int x, int r,
-                                          NodeDiag& d) {
+                                          NodeDiagF& d) {
     using PS = PairStore<S>;
     const int H = P.half_ny;
     const long long plane2 = P.plane2;
@@ -218,13 +218,14 @@ __device__ __forceinline__ void pair_node(const PairParams& P, const typename Pa
         bits |= (th.x <= 0.0f || th.y <= 0.0f) ? 4u : 0u;
         atomicOr(P.status, bits);
     }
-    if (REDUCE) {
-        d.mass = 2.0 + (double)drho.x + (double)drho.y;
-        d.jx = (double)jx.x + (double)jx.y;
-        d.jy = (double)jy.x + (double)jy.y;
-        d.energy = 4.0 * P.theta0 + (double)e.x + (double)e.y;
-        d.rho_min = fmin((double)rho.x, (double)rho.y);
-        d.theta_min = fmin((double)th.x, (double)th.y);
+    if (REDUCE) {   // two nodes: deviations from the rest state in float-float
+        d.dmass = ff_add(FF{drho.x, 0.0f}, drho.y);
+        d.jx = ff_add(FF{jx.x, 0.0f}, jx.y);
+        d.jy = ff_add(FF{jy.x, 0.0f}, jy.y);
+        d.denergy = ff_add(FF{e.x, 0.0f}, e.y);
+        d.rho_min = fminf(rho.x, rho.y);
+        d.theta_min = fminf(th.x, th.y);
+        d.n = 2.0f;
     }
     const unsigned here = (unsigned)(r * P.pitch + x);
 #pragma unroll
@@ -238,12 +239,12 @@ k_stream_collide_pair(const __grid_constant__ PairParams P,
                       const typename PairStore<S>::V* __restrict__ src,
                       typename PairStore<S>::V* __restrict__ dst) {
     const int x = blockIdx.x * kBlockX + threadIdx.x;
-    NodeDiag d;
-    if (REDUCE) diag_zero(d);
+    NodeDiagF d;
+    if (REDUCE) diagf_zero(d);
     if (x < P.nx) pair_node<S, REDUCE>(P, src, dst, x, blockIdx.y, d);
     if (REDUCE) {
         const int blk = blockIdx.y * gridDim.x + blockIdx.x;
-        block_reduce_diag<kBlockX>(d, P.partials + (long long)blk * kPartialStride);
+        block_reduce_diagf<kBlockX>(d, 2.0 * P.theta0, P.partials + (long long)blk * kPartialStride);
     }
 }
 
@@ -277,7 +278,7 @@ k_batch_pair(const PairParams* __restrict__ inst, int ninst, int total_tiles, in
     __shared__ PairParams sp;
     __shared__ int s_inst;
     constexpr int kWords = (int)(sizeof(PairParams) / sizeof(int));
-    NodeDiag d;
+    NodeDiagF d;
     if (tile_inst) {
         // Interleaved order: CTA c takes tiles c, c + G, c + 2G, ... (G CTAs), so the
         // tiles in flight at any moment are neighbours in memory, as in a plain grid.

@@ -110,6 +110,7 @@ SIGNATURES = {
     "plbm_moments": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_int]),
     "plbm_diagnostics": (ctypes.c_int, [_H, ctypes.POINTER(PlbmDiag)]),
+    "plbm_step_diagnostics": (ctypes.c_int, [_H, ctypes.c_long, ctypes.POINTER(PlbmDiag)]),
     "plbm_conserved": (ctypes.c_int, [_H, _D]),
     "plbm_init3": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_void_p, ctypes.c_int]),
@@ -373,6 +374,12 @@ class Solver:
     def diagnostics(self) -> dict:
         d = PlbmDiag()
         _ok(lib().plbm_diagnostics(self.h, ctypes.byref(d)), self.h)
+        return {k: getattr(d, k) for k, _ in PlbmDiag._fields_}
+
+    def step_diagnostics(self, n: int) -> dict:
+        """n steps, the last fused with the FP64 reductions (plbm_step_diagnostics)."""
+        d = PlbmDiag()
+        _ok(lib().plbm_step_diagnostics(self.h, int(n), ctypes.byref(d)), self.h)
         return {k: getattr(d, k) for k, _ in PlbmDiag._fields_}
 
     def conserved(self) -> np.ndarray:

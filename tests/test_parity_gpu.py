@@ -573,3 +573,40 @@ def test_banded_host_transfers_equal_device_pointers(prec):
             assert np.array_equal(x, y.cpu().numpy())
         a.close()
         b.close()
+
+
+@pytest.mark.parametrize("prec,dim", [("f64", 2), ("f32", 2), ("f16dev", 2), ("f64", 1), ("f32", 1)])
+def test_fused_step_diagnostics_match_separate_reduction(prec, dim):
+    # The last step of plbm_step_diagnostics forms the FP64 sums in the step kernel;
+    # they must equal plbm_diagnostics of the same state (FP64: to rounding; 16/32-bit:
+    # the fused sums use the kernel's FP32 moments, so to FP32 rounding), and the
+    # populations must be those of plain stepping.
+    if dim == 2:
+        nx, ny = 96, 64
+        fields = I.kh_fields(nx, ny=ny, seed=8)
+        make = lambda: plbm.Solver(2, V5, 1.3, nx, ny, theta0=1.0, prec=prec)
+        init = lambda s: s.init(*fields)
+    else:
+        nx, ny = 1000, 1
+        left, right = (1.1, 0.0, 0.5), (1.0, 0.0, 0.5)
+        fields = I.shock_tube_fields(nx, left, right)
+        make = lambda: plbm.Solver(1, V5, 1.5, nx, 1, theta0=0.5, prec=prec, bc="fixed", left_state=left,
+                                   right_state=right)
+        init = lambda s: s.init(fields[0], fields[1], None, fields[3])
+    a, b = make(), make()
+    init(a)
+    init(b)
+    da = a.step_diagnostics(37)
+    b.step(37)
+    db = b.diagnostics()
+    assert np.array_equal(a.get_populations(), b.get_populations())
+    assert da["steps"] == db["steps"] == 37 and da["status"] == db["status"] == 0
+    # 16-bit: the stored state carries the storage rounding of the deviations (~5e-6 each)
+    tol = {"f64": 1e-12, "f32": 2e-6, "f16dev": 3e-5}[prec]
+    scale = max(abs(db["mass"]), 1.0)
+    for k in ("mass", "jx", "jy", "energy"):
+        assert abs(da[k] - db[k]) <= tol * max(scale, abs(db["energy"])), (k, da[k], db[k])
+    for k in ("rho_min", "theta_min"):
+        assert abs(da[k] - db[k]) <= tol * abs(db[k]), (k, da[k], db[k])
+    a.close()
+    b.close()
