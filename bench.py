@@ -778,7 +778,7 @@ def main():
                                                         train_steps=args.surrogate_steps)
         base = value / ws
         for k, vv in variants.items():
-            if k.startswith("kh%d_" % L):
+            if k.startswith("kh%d_" % L) and "mlups" in vv:
                 vv["speedup_vs_f32"] = vv["mlups"] / base
 
     cpu = None
