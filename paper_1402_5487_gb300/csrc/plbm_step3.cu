@@ -726,6 +726,101 @@ __global__ void __launch_bounds__(kB3) k_reduce3(const __grid_constant__ Lattice
     }
 }
 
+// The same record for 16/32-bit storage with q1 = 5 on the FP32 pipe: row sums
+// of the stored deviations in float-float (R_ab = sum_c g, S_a, T_b, U_c),
+// mass - 1, j, E - 3 theta0 per node, block sums in float-float, and the FP64
+// minima of rho and theta reduced as order-preserving integer keys.
+template <typename S>
+__global__ void __launch_bounds__(kB3) k_reduce3_dev(const __grid_constant__ LatticeParams P, const S* __restrict__ f) {
+    __shared__ float sh[11][kB3 / 32];
+    __shared__ long long shk[2][kB3 / 32];
+    const int x = blockIdx.x * kB3 + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    FF dm{0.f, 0.f}, jx = dm, jy = dm, jz = dm, de = dm;
+    float n = 0.0f;
+    long long kr = dkey(1e300), kt = dkey(1e300);
+    if (x < P.nx) {
+        const long long here = node3(P, x, y, z);
+        FF Sa[kQ1], Tb[kQ1], Uc[kQ1];
+#pragma unroll
+        for (int i = 0; i < kQ1; ++i) Sa[i] = Tb[i] = Uc[i] = FF{0.f, 0.f};
+#pragma unroll
+        for (int a = 0; a < kQ1; ++a)
+#pragma unroll
+            for (int b = 0; b < kQ1; ++b) {
+                FF R{0.f, 0.f};
+#pragma unroll
+                for (int c = 0; c < kQ1; ++c) {
+                    const float g = Storage<S>::load(f + (long long)((a * kQ1 + b) * kQ1 + c) * P.plane + here);
+                    R = ff_add(R, g);
+                    Uc[c] = ff_add(Uc[c], g);
+                }
+                Sa[a] = ff_add(Sa[a], R);
+                Tb[b] = ff_add(Tb[b], R);
+            }
+#pragma unroll
+        for (int i = 0; i < kQ1; ++i) {
+            const float vi = (float)P.v[i];
+            dm = ff_add(dm, Sa[i]);
+            jx = ff_add(jx, ff_scale(Sa[i], vi));
+            jy = ff_add(jy, ff_scale(Tb[i], vi));
+            jz = ff_add(jz, ff_scale(Uc[i], vi));
+            de = ff_add(de, ff_scale(ff_scale(ff_add(ff_add(Sa[i], Tb[i]), Uc[i]), vi), vi));
+        }
+        const double rho = 1.0 + ff_f64(dm);
+        const double ir = 1.0 / rho;
+        const double ux = ff_f64(jx) * ir, uy = ff_f64(jy) * ir, uz = ff_f64(jz) * ir;
+        const double th = ((3.0 * P.theta0 + ff_f64(de)) * ir - (ux * ux + uy * uy + uz * uz)) / 3.0;
+        flag_status<double>(P, rho, th);
+        n = 1.0f;
+        kr = dkey(rho);
+        kt = dkey(th);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        dm = ff_add(dm, ff_shfl_down(dm, off));
+        jx = ff_add(jx, ff_shfl_down(jx, off));
+        jy = ff_add(jy, ff_shfl_down(jy, off));
+        jz = ff_add(jz, ff_shfl_down(jz, off));
+        de = ff_add(de, ff_shfl_down(de, off));
+        n += __shfl_down_sync(0xffffffffu, n, off);
+        kr = kmin(kr, __shfl_down_sync(0xffffffffu, kr, off));
+        kt = kmin(kt, __shfl_down_sync(0xffffffffu, kt, off));
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        const FF v[5] = {dm, jx, jy, jz, de};
+        for (int k = 0; k < 5; ++k) {
+            sh[2 * k][warp] = v[k].hi;
+            sh[2 * k + 1][warp] = v[k].lo;
+        }
+        sh[10][warp] = n;
+        shk[0][warp] = kr;
+        shk[1][warp] = kt;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        FF t[5] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        float nn = 0.0f;
+        long long r = shk[0][0], q = shk[1][0];
+        for (int w = 0; w < kB3 / 32; ++w) {
+            for (int k = 0; k < 5; ++k) t[k] = ff_add(t[k], FF{sh[2 * k][w], sh[2 * k + 1][w]});
+            nn += sh[10][w];
+            r = kmin(r, shk[0][w]);
+            q = kmin(q, shk[1][w]);
+        }
+        const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        double* out = P.partials + blk * kPartialStride;
+        out[0] = (double)nn + ff_f64(t[0]);
+        out[1] = ff_f64(t[1]);
+        out[2] = ff_f64(t[2]);
+        out[3] = (double)nn * 3.0 * P.theta0 + ff_f64(t[4]);
+        out[4] = dunkey(r);
+        out[5] = dunkey(q);
+        out[6] = ff_f64(t[3]);
+    }
+}
+
 __global__ void k_finalize3(const double* __restrict__ partials, long long nblocks, double* __restrict__ out) {
     __shared__ double sh[7][256];
     double r[7] = {0, 0, 0, 0, 1e300, 1e300, 0};
@@ -841,7 +936,18 @@ cudaError_t launch_moments3(int prec, const LatticeParams& P, const void* f, dou
 }
 
 cudaError_t launch_reduce3(int prec, const LatticeParams& P, const void* f, double* out, cudaStream_t s) {
-    PLBM_DISPATCH3(prec, (k_reduce3<S><<<grid3(P), kB3, 0, s>>>(P, static_cast<const S*>(f))));
+    if (prec != kF64 && P.q1 == kQ1) {
+        switch (prec) {
+            case kF32: k_reduce3_dev<float><<<grid3(P), kB3, 0, s>>>(P, static_cast<const float*>(f)); break;
+            case kF16Dev: k_reduce3_dev<__half><<<grid3(P), kB3, 0, s>>>(P, static_cast<const __half*>(f)); break;
+            case kBF16Dev:
+                k_reduce3_dev<__nv_bfloat16><<<grid3(P), kB3, 0, s>>>(P, static_cast<const __nv_bfloat16*>(f));
+                break;
+            default: return cudaErrorInvalidValue;
+        }
+    } else {
+        PLBM_DISPATCH3(prec, (k_reduce3<S><<<grid3(P), kB3, 0, s>>>(P, static_cast<const S*>(f))));
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_finalize3<<<1, 256, 0, s>>>(P.partials, reduce3_blocks(P), out);

@@ -169,3 +169,31 @@ def test_d3q125_checkpoint_resume_is_bit_identical(prec, nz):
     assert np.array_equal(b.get_populations(), ref)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("prec,nz", [("f32", 5), ("f16dev", 6), ("bf16dev", 5)])
+def test_d3q125_diagnostics_equal_fp64_sums_of_the_stored_state(prec, nz):
+    # The 16/32-bit 3D reduction sums in float-float on the FP32 pipe; its record must
+    # equal FP64 sums (numpy) of the stored populations, and its minima the FP64
+    # minima of the nodes' rho and theta.
+    from paper_1402_5487_gb300 import plbm
+    nx, ny = 40, 6
+    f = fields3(nx, ny, nz, 13)
+    s = plbm.Solver(3, V5, 1.3, nx, ny, nz=nz, prec=prec)
+    s.init(f[0], f[1], f[2], f[4], uz=f[3])
+    s.step(9)
+    pops = s.get_populations()
+    lat = O.Lattice3(V5, 1.3, nx, ny, nz)
+    vel = lat.velocities().astype(np.float64)
+    flat = pops.reshape(pops.shape[0], -1)
+    mass = flat.sum(axis=0)
+    j = vel.T @ flat
+    e = (vel ** 2).sum(axis=1) @ flat
+    ref = np.array([mass.sum(), j[0].sum(), j[1].sum(), j[2].sum(), e.sum()])   # conserved3 order
+    got = s.conserved()
+    assert np.max(np.abs(got - ref)) <= 1e-12 * abs(ref[0]), (got, ref)
+    u = j / mass
+    th = (e / mass - (u ** 2).sum(axis=0)) / 3.0
+    d = s.diagnostics()
+    assert abs(d["rho_min"] - mass.min()) <= 1e-13 and abs(d["theta_min"] - th.min()) <= 1e-12
+    s.close()
