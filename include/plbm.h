@@ -339,7 +339,8 @@ typedef struct plbm_surrogate_s *plbm_surrogate;
 int plbm_sur_num_params(void);
 
 /* Network for batches of up to max_batch lattices of H x W nodes, He-initialised
- * from `seed` (last layer scaled by 0.1).  stream: cudaStream_t (NULL: own). */
+ * from `seed` (last layer scaled by 0.1).  stream: cudaStream_t (NULL: own).
+ * PLBM_E_ARG unless 1 <= max_batch <= 65535, H >= 3 and W is a multiple of 128. */
 plbm_status plbm_sur_create(int max_batch, int H, int W, unsigned long long seed, void *stream,
                             plbm_surrogate *out);
 plbm_status plbm_sur_destroy(plbm_surrogate s);

@@ -62,8 +62,10 @@ struct Sur {
     double* host_sums = nullptr;
     double* drift = nullptr;        // device: drift of every lattice of the last advance
     plbm::PairParams* fb_table = nullptr;  // device: batched fallback of row-paired lattices
+    unsigned short* fb_tile_inst = nullptr;  // device: lattice of every fallback tile (interleaved order)
     int sms = 0;
     std::vector<double> last_drift;
+    std::vector<unsigned short> fb_tiles;  // host copy of fb_tile_inst (kept for the async copy)
     cudaEvent_t ev = nullptr;
     char err[512] = "";
 };
@@ -106,7 +108,7 @@ void free_sur(Sur* s) {
     if (s->stream) cudaStreamSynchronize(s->stream);
     void* bufs[] = {s->p, s->g, s->m, s->v, s->pr, s->wbf, s->wflip, s->w6flip, s->dz[0], s->dz[1], s->dz[2],
                     s->dz[3], s->dz[4], s->dout, s->part, s->part_b, s->loss_part, s->Fold, s->Fnew, s->xin,
-                    s->planes, s->sums, s->wtc, s->derr, s->win, s->wout, s->drift, s->fb_table};
+                    s->planes, s->sums, s->wtc, s->derr, s->win, s->wout, s->drift, s->fb_table, s->fb_tile_inst};
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (void* a : s->act)
@@ -203,8 +205,8 @@ int plbm_sur_num_params(void) {
 }
 
 plbm_status plbm_sur_create(int max_batch, int H, int W, unsigned long long seed, void* stream, plbm_surrogate* out) {
-    if (!out || max_batch < 1 || H < 3 || W < 128 || W % 128) {
-        serr(nullptr, "plbm_sur_create: need max_batch >= 1, H >= 3 and W a multiple of 128");
+    if (!out || max_batch < 1 || max_batch > 65535 || H < 3 || W < 128 || W % 128) {
+        serr(nullptr, "plbm_sur_create: need 1 <= max_batch <= 65535, H >= 3 and W a multiple of 128");
         return PLBM_E_ARG;
     }
     *out = nullptr;
@@ -252,6 +254,7 @@ plbm_status plbm_sur_create(int max_batch, int H, int W, unsigned long long seed
         {&s->wtc, 8 * 9 * 64 * 64 * 2}, {(void**)&s->derr, 256}, {&s->win, 6 * 64 * 8 * 2},
         {&s->wout, 9 * 16 * 64 * 2}, {(void**)&s->drift, (size_t)max_batch * 24 + 16},
         {(void**)&s->fb_table, (size_t)max_batch * sizeof(plbm::PairParams)},
+        {(void**)&s->fb_tile_inst, (size_t)max_batch * ((W + 127) / 128) * ((H + 1) / 2) * sizeof(unsigned short) + 256},
     };
     for (auto& a : allocs) {
         if (cudaMalloc(a.p, a.n) != cudaSuccess) {
@@ -554,13 +557,22 @@ plbm_status plbm_sur_advance(plbm_surrogate h, plbm_handle* hs, int n, int K, do
             tiles += Q.tiles_x * Q.half_ny;
             table[k] = Q;
         }
+        // interleaved tile order (the batched runner's default): lattice of every tile
+        s->fb_tiles.assign((size_t)tiles, 0);
+        for (size_t k = 0; k < table.size(); ++k)
+            std::fill(s->fb_tiles.begin() + table[k].tile_begin,
+                      s->fb_tiles.begin() + table[k].tile_begin + table[k].tiles_x * table[k].half_ny,
+                      (unsigned short)k);
         SCK(cudaMemcpyAsync(s->fb_table, table.data(), sizeof(plbm::PairParams) * table.size(),
+                            cudaMemcpyHostToDevice, s->stream));
+        SCK(cudaMemcpyAsync(s->fb_tile_inst, s->fb_tiles.data(), sizeof(unsigned short) * s->fb_tiles.size(),
                             cudaMemcpyHostToDevice, s->stream));
         int occ = 1;
         if (plbm::batch_occupancy(bprec, kBX, &occ) != cudaSuccess || occ < 1) occ = 1;
+        const int ctas = s->sms * (occ < 3 ? occ : 3);   // the sweep's tuned shape: 128 threads, 3 CTAs per SM
         for (int k = 0; k < K; ++k)
-            SCK(plbm::launch_batch(bprec, s->fb_table, (int)table.size(), tiles, kBX, s->sms * occ, k & 1,
-                                   nullptr, s->stream));
+            SCK(plbm::launch_batch(bprec, s->fb_table, (int)table.size(), tiles, kBX, ctas, k & 1,
+                                   s->fb_tile_inst, s->stream));
         for (int b : batched) {
             if (K & 1) *views[b].cur ^= 1;
             *views[b].steps += K;

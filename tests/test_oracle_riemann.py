@@ -134,6 +134,47 @@ def test_isothermal_zeta4_shock_tube_printed_front():
     assert abs(front - vals["shock6_front_x"]) < 2.5
 
 
+def zeta4_vs_lbgk_small_ratio(tube=None, ratio=1.1):
+    """Sec. 3.2 and the captions of Figs. 3-4: isothermal three-velocity shock tubes at
+    rho_L/rho_R = 1.1 and theta = theta0, LBGK (zeta = 3, theta0 = 1/3, omega = 1, 362
+    iterations) against the parametric zeta = 4 model (theta0 = 1/4, 418 iterations), once with
+    the viscosity nu = (1/omega - 1/2) sqrt(theta0) dx / sqrt(zeta) matched (omega = 4 sqrt(3) - 6)
+    and once with nu_hat = nu (zeta - 1) / 2 matched instead.  Returns the largest density and
+    velocity (normalised by sqrt(theta0)) differences of both zeta = 4 runs against LBGK.
+    `tube(v, omega, theta0, left, right, steps)` returns the moments (rho, ux, uy, theta)."""
+    tube = tube or (lambda *a: _tube(*a, isothermal=True)[1])
+
+    def run(zeta, omega, steps):
+        th = 1.0 / zeta
+        rho, ux, _, _ = tube((0, 1, -1), omega, th, (ratio, 0.0, th), (1.0, 0.0, th), steps)
+        return np.asarray(rho).ravel(), np.asarray(ux).ravel() / math.sqrt(th)
+
+    nu_lbgk = (1.0 / 1.0 - 0.5) / math.sqrt(3)
+    omega_nu = 1.0 / (0.5 + nu_lbgk * math.sqrt(4))
+    omega_nu_hat = 1.0 / (0.5 + nu_lbgk * math.sqrt(4) * 2 / (4 - 1))
+    r3, u3 = run(3, 1.0, 362)
+    out = {}
+    for name, om in (("nu", omega_nu), ("nu_hat", omega_nu_hat)):
+        r4, u4 = run(4, om, 418)
+        out[name] = (float(np.max(np.abs(r4 - r3))), float(np.max(np.abs(u4 - u3))))
+    return out, omega_nu, omega_nu_hat
+
+
+def test_zeta4_differs_from_lbgk_by_about_three_tenths_of_a_percent():
+    vals = read_printed_values()
+    out, omega_nu, omega_nu_hat = zeta4_vs_lbgk_small_ratio()
+    assert abs(omega_nu - vals["omega_zeta4_matched"]) < 1e-14
+    # (zeta - 1)/2 (1/omega - 1/2)/sqrt(4) = (1 - 1/2)/sqrt(3)
+    assert abs(1.5 * (1 / omega_nu_hat - 0.5) / 2 - 0.5 / math.sqrt(3)) < 1e-15
+    printed = vals["shock11_max_diff_zeta4_lbgk"]
+    drho, du = out["nu"]
+    # "about 0.3 %" for both density and velocity (measured 0.29 % and 0.28 %)
+    assert abs(drho - printed) < 0.0005 and abs(du - printed) < 0.0005, out
+    # Fig. 4: matching nu_hat instead of nu reduces the difference markedly (measured 26x)
+    drho_h, du_h = out["nu_hat"]
+    assert drho_h < drho / 10 and du_h < du / 10, out
+
+
 @pytest.mark.parametrize("ratio,t_cmp,bounds", [(1.1, 361, (0.002, 0.02, 0.002)),
                                                 (2.0, 327, (0.01, 0.03, 0.01))])
 def test_d1q5_thermal_shock_tube_vs_exact(ratio, t_cmp, bounds):

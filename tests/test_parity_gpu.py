@@ -610,3 +610,51 @@ def test_fused_step_diagnostics_match_separate_reduction(prec, dim):
         assert abs(da[k] - db[k]) <= tol * abs(db[k]), (k, da[k], db[k])
     a.close()
     b.close()
+
+
+# --------------------------------------------------------------------------
+# The isothermal three-velocity shock tubes of Sec. 3.2 on the GPU path: the
+# 6:1 tube's printed front and post-shock velocity, and the 1.1:1 comparison of
+# the zeta = 4 model with LBGK under nu and nu_hat viscosity matching.
+# --------------------------------------------------------------------------
+def _gpu_tube(prec):
+    def tube(v, omega, theta0, left, right, steps):
+        fields = I.shock_tube_fields(1000, left, right)
+        (m, _, s) = gpu_run(1, v, omega, 1000, 1, fields, steps, prec=prec, theta0=theta0, bc="fixed",
+                            left=left, right=right, isothermal=True)
+        s.close()
+        return m
+    return tube
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 2e-6)])
+def test_zeta4_vs_lbgk_small_ratio_on_gpu(prec, tol):
+    from test_oracle_riemann import zeta4_vs_lbgk_small_ratio
+    ref, _, _ = zeta4_vs_lbgk_small_ratio()
+    got, _, _ = zeta4_vs_lbgk_small_ratio(tube=_gpu_tube(prec))
+    for k in ref:
+        for a, b in zip(got[k], ref[k]):
+            assert abs(a - b) <= tol, (k, got, ref)
+    assert got["nu_hat"][0] < got["nu"][0] / 10
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_zeta4_shock_tube_printed_front_on_gpu(prec):
+    from conftest import read_printed_values
+    vals = read_printed_values()
+    theta0 = 0.25
+    omega = 4 * math.sqrt(3) - 6
+    steps = int(vals["shock6_iterations_param"])
+    left, right = (6.0, 0.0, theta0), (1.0, 0.0, theta0)
+    mg = _gpu_tube(prec)((0, 1, -1), omega, theta0, left, right, steps)
+    _, _, mo = oracle_run(1, (0, 1, -1), omega, 1000, 1, I.shock_tube_fields(1000, left, right), steps,
+                          theta0=theta0, bc="fixed", left=left, right=right, isothermal=True)
+    errs = field_errors(mg, mo)
+    assert max(errs.values()) <= (TOL64 if prec == "f64" else TOL32), errs
+    rho, ux = mg[0][0], mg[1][0] / math.sqrt(theta0)
+    assert abs(np.mean(ux[650:750]) - vals["shock6_u_post"]) < 0.005
+    plateau = np.mean(rho[650:750])
+    half = 0.5 * (plateau + 1.0)
+    i = int(np.nonzero(rho > half)[0].max())
+    front = (i + 1) + (rho[i] - half) / (rho[i] - rho[i + 1])
+    assert abs(front - vals["shock6_front_x"]) < 2.5
