@@ -47,6 +47,9 @@ __device__ __forceinline__ unsigned smem_u32(const void* p) {
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem)), "l"(gmem));
 }
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(smem)), "l"(gmem));
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
@@ -477,10 +480,46 @@ k_thin_out_fwd(ConvShape S, const __nv_bfloat16* __restrict__ X, const float* __
 // Weight gradient of a thin layer, X with CX channels (bf16), dY with CG channels
 // (TG), one of CX, CG equal to 64 and the other to 4.  Thread (tap, a), a < 64,
 // accumulates the 4 entries of dW[tap][.][.] along the narrow axis over the CTA's
-// 128-pixel tiles staged in shared memory; threads with tap 0 also sum dY for the
-// bias.  partial[cta][tap][ci][co], partial_b[cta][co].
+// 128-pixel tiles; threads with tap 0 also sum dY for the bias.  Each tile's
+// three input rows and its dY row are staged with cp.async into one of two
+// shared-memory stages while the previous tile is summed, so the copies of a
+// tile are all in flight at once and overlap the arithmetic.
+// partial[cta][tap][ci][co], partial_b[cta][co].
 template <int CX, int CG, typename TG>
-constexpr int thin_wgrad_smem() { return 3 * kRowPix * CX * 2 + kTile * CG * (int)sizeof(TG); }
+constexpr int thin_wgrad_stage() { return 3 * kRowPix * CX * 2 + kTile * CG * (int)sizeof(TG); }
+template <int CX, int CG, typename TG>
+constexpr int thin_wgrad_smem() { return 2 * thin_wgrad_stage<CX, CG, TG>(); }
+
+template <int CX, int CG, typename TG>
+__device__ __forceinline__ void thin_wgrad_stage_in(ConvShape S, const __nv_bfloat16* __restrict__ X,
+                                                    const TG* __restrict__ dY, int t, unsigned char* st) {
+    const int tiles_x = S.W / kTile;
+    const int b = t / (S.H * tiles_x);
+    const int rem = t - b * S.H * tiles_x;
+    const int y = rem / tiles_x;
+    const int x0 = (rem - y * tiles_x) * kTile;
+    auto sX = reinterpret_cast<__nv_bfloat16 (*)[kRowPix][CX]>(st);
+    auto sG = reinterpret_cast<TG (*)[CG]>(st + 3 * kRowPix * CX * 2);
+    if (CX == 64) {   // 16-byte pieces: 8 channels of one pixel
+        for (int i = threadIdx.x; i < 3 * kRowPix * 8; i += blockDim.x) {
+            const int q = i & 7, pr = i >> 3, r = pr / kRowPix, p = pr - r * kRowPix;
+            cp_async16(&sX[r][p][8 * q],
+                       X + (((size_t)b * S.H + wrap(y + r - 1, S.H)) * S.W + wrap(x0 + p - 1, S.W)) * CX + 8 * q);
+        }
+    } else {          // 8-byte pieces: the 4 channels of one pixel
+        for (int i = threadIdx.x; i < 3 * kRowPix; i += blockDim.x) {
+            const int r = i / kRowPix, p = i - r * kRowPix;
+            cp_async8(&sX[r][p][0],
+                      X + (((size_t)b * S.H + wrap(y + r - 1, S.H)) * S.W + wrap(x0 + p - 1, S.W)) * CX);
+        }
+    }
+    constexpr int GV = 16 / (int)sizeof(TG);  // dY values per 16-byte piece
+    for (int i = threadIdx.x; i < kTile * (CG / GV); i += blockDim.x) {
+        const int q = i % (CG / GV), p = i / (CG / GV);
+        cp_async16(&sG[p][GV * q], dY + (((size_t)b * S.H + y) * S.W + x0 + p) * CG + GV * q);
+    }
+    cp_async_commit();
+}
 
 template <int CX, int CG, typename TG>
 __global__ void __launch_bounds__(576)
@@ -488,34 +527,25 @@ k_thin_wgrad(ConvShape S, const __nv_bfloat16* __restrict__ X, const TG* __restr
              float* __restrict__ partial_b) {
     static_assert((CX == 64 && CG == 4) || (CX == 4 && CG == 64), "thin layer shapes");
     extern __shared__ __align__(16) unsigned char dsm[];
-    auto sX = reinterpret_cast<__nv_bfloat16 (*)[kRowPix][CX]>(dsm);
-    auto sG = reinterpret_cast<TG (*)[CG]>(dsm + 3 * kRowPix * CX * 2);
+    constexpr int kStage = thin_wgrad_stage<CX, CG, TG>();
     const int tap = threadIdx.x / 64, a = threadIdx.x % 64;
     const int ky = tap / 3, kx = tap % 3;
-    const int tiles_x = S.W / kTile;
-    const int ntiles = S.B * S.H * tiles_x;
+    const int ntiles = S.B * S.H * (S.W / kTile);
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     float bacc = 0.0f;
+    int stage = 0;
+    if ((int)blockIdx.x < ntiles) thin_wgrad_stage_in<CX, CG, TG>(S, X, dY, blockIdx.x, dsm);
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int b = t / (S.H * tiles_x);
-        const int rem = t - b * S.H * tiles_x;
-        const int y = rem / tiles_x;
-        const int x0 = (rem - y * tiles_x) * kTile;
-        __syncthreads();
-        // staging in 8-byte pieces (4 bf16 of X, or 4 values of dY)
-        for (int i = threadIdx.x; i < 3 * kRowPix * (CX / 4); i += blockDim.x) {
-            const int q = i % (CX / 4), pr = i / (CX / 4), r = pr / kRowPix, p = pr - r * kRowPix;
-            const __nv_bfloat16* src =
-                X + (((size_t)b * S.H + wrap(y + r - 1, S.H)) * S.W + wrap(x0 + p - 1, S.W)) * CX + 4 * q;
-            *reinterpret_cast<uint2*>(&sX[r][p][4 * q]) = *reinterpret_cast<const uint2*>(src);
-        }
-        constexpr int GV = 8 / (int)sizeof(TG);  // dY values per 8-byte piece
-        for (int i = threadIdx.x; i < kTile * (CG / GV); i += blockDim.x) {
-            const int q = i % (CG / GV), p = i / (CG / GV);
-            *reinterpret_cast<uint2*>(&sG[p][GV * q]) =
-                *reinterpret_cast<const uint2*>(dY + (((size_t)b * S.H + y) * S.W + x0 + p) * CG + GV * q);
+        // the other stage was last read in the previous iteration, behind its closing barrier
+        if (t + (int)gridDim.x < ntiles) {
+            thin_wgrad_stage_in<CX, CG, TG>(S, X, dY, t + gridDim.x, dsm + (stage ^ 1) * kStage);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
         __syncthreads();
+        auto sX = reinterpret_cast<const __nv_bfloat16 (*)[kRowPix][CX]>(dsm + stage * kStage);
+        auto sG = reinterpret_cast<const TG (*)[CG]>(dsm + stage * kStage + 3 * kRowPix * CX * 2);
 #pragma unroll 4
         for (int p = 0; p < kTile; ++p) {
             if (CX == 64) {  // a = ci, narrow axis = co (dY fp32, 4 values)
@@ -525,7 +555,7 @@ k_thin_wgrad(ConvShape S, const __nv_bfloat16* __restrict__ X, const TG* __restr
                 for (int o = 0; o < 4; ++o) g[o] = to_f<TG>(sG[p][o]);
 #pragma unroll
                 for (int o = 0; o < 4; ++o) acc[o] = fmaf(xv, g[o], acc[o]);
-                if (tap == 0 && a < 4) bacc += g[a & 3];
+                if (tap == 0 && a < 4) bacc += to_f<TG>(sG[p][a]);
             } else {  // a = co, narrow axis = ci
                 const float g = to_f<TG>(sG[p][a]);
                 const uint2 raw = *reinterpret_cast<const uint2*>(&sX[ky][p + kx][0]);
@@ -535,6 +565,8 @@ k_thin_wgrad(ConvShape S, const __nv_bfloat16* __restrict__ X, const TG* __restr
                 if (tap == 0) bacc += g;
             }
         }
+        __syncthreads();
+        stage ^= 1;
     }
     float* out = partial + (size_t)blockIdx.x * 9 * CX * CG + (size_t)tap * CX * CG;
     if (CX == 64) {
@@ -742,6 +774,13 @@ cudaError_t cnn_conv_thin_wgrad(int ci, int co, int tx, int tg, int B, int H, in
     const __nv_bfloat16* Xb = static_cast<const __nv_bfloat16*>(X);
     if (ci == 4 && co == 64 && tg == 0) {
         constexpr int sm = cnn::thin_wgrad_smem<4, 64, __nv_bfloat16>();
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(cnn::k_thin_wgrad<4, 64, __nv_bfloat16>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
         cnn::k_thin_wgrad<4, 64, __nv_bfloat16><<<parts, 576, sm, s>>>(S, Xb, static_cast<const __nv_bfloat16*>(dY),
                                                                       partial, partial_b);
     } else if (ci == 64 && co == 4 && tg == 1) {
