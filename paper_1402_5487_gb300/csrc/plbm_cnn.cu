@@ -382,20 +382,19 @@ k_thin_in_fwd(ConvShape S, const TI* __restrict__ X, const float* __restrict__ W
         for (int i = 0; i < 4; ++i) in[tap * 4 + i] = to_f<TI>(xp[i]);
     }
     __syncthreads();
-    float acc[64];
+    float2 acc[32];   // output channels (2j, 2j + 1): packed FP32x2 FMAs, the same roundings as scalar ones
 #pragma unroll
-    for (int o = 0; o < 64; ++o) acc[o] = (mode == 0) ? bias[o] : 0.0f;
+    for (int j = 0; j < 32; ++j)
+        acc[j] = (mode == 0) ? make_float2(bias[2 * j], bias[2 * j + 1]) : make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int k = 0; k < 36; ++k) {
-        const float xv = in[k];
+        const float2 xv = make_float2(in[k], in[k]);
         const float4* w = reinterpret_cast<const float4*>(sW + k * 64);
 #pragma unroll
         for (int o4 = 0; o4 < 16; ++o4) {
             const float4 ww = w[o4];
-            acc[4 * o4 + 0] = fmaf(xv, ww.x, acc[4 * o4 + 0]);
-            acc[4 * o4 + 1] = fmaf(xv, ww.y, acc[4 * o4 + 1]);
-            acc[4 * o4 + 2] = fmaf(xv, ww.z, acc[4 * o4 + 2]);
-            acc[4 * o4 + 3] = fmaf(xv, ww.w, acc[4 * o4 + 3]);
+            acc[2 * o4] = __ffma2_rn(xv, make_float2(ww.x, ww.y), acc[2 * o4]);
+            acc[2 * o4 + 1] = __ffma2_rn(xv, make_float2(ww.z, ww.w), acc[2 * o4 + 1]);
         }
     }
     const size_t pix = ((size_t)b * S.H + y) * S.W + x;
@@ -403,7 +402,10 @@ k_thin_in_fwd(ConvShape S, const TI* __restrict__ X, const float* __restrict__ W
     for (int c = 0; c < 8; ++c) {
         float v[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) v[k] = acc[8 * c + k];
+        for (int k = 0; k < 4; ++k) {
+            v[2 * k] = acc[4 * c + k].x;
+            v[2 * k + 1] = acc[4 * c + k].y;
+        }
         if (mode == 0) {
             if (relu)
 #pragma unroll
@@ -531,7 +533,7 @@ k_thin_wgrad(ConvShape S, const __nv_bfloat16* __restrict__ X, const TG* __restr
     const int tap = threadIdx.x / 64, a = threadIdx.x % 64;
     const int ky = tap / 3, kx = tap % 3;
     const int ntiles = S.B * S.H * (S.W / kTile);
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    float2 acc01 = make_float2(0.f, 0.f), acc23 = acc01;   // packed FP32x2 FMAs
     float bacc = 0.0f;
     int stage = 0;
     if ((int)blockIdx.x < ntiles) thin_wgrad_stage_in<CX, CG, TG>(S, X, dY, blockIdx.x, dsm);
@@ -549,26 +551,28 @@ k_thin_wgrad(ConvShape S, const __nv_bfloat16* __restrict__ X, const TG* __restr
 #pragma unroll 4
         for (int p = 0; p < kTile; ++p) {
             if (CX == 64) {  // a = ci, narrow axis = co (dY fp32, 4 values)
-                const float xv = __bfloat162float(sX[ky][p + kx][a]);
-                float g[4];
-#pragma unroll
-                for (int o = 0; o < 4; ++o) g[o] = to_f<TG>(sG[p][o]);
-#pragma unroll
-                for (int o = 0; o < 4; ++o) acc[o] = fmaf(xv, g[o], acc[o]);
+                const float x1 = __bfloat162float(sX[ky][p + kx][a]);
+                const float2 xv = make_float2(x1, x1);
+                const float2 g01 = make_float2(to_f<TG>(sG[p][0]), to_f<TG>(sG[p][1]));
+                const float2 g23 = make_float2(to_f<TG>(sG[p][2]), to_f<TG>(sG[p][3]));
+                acc01 = __ffma2_rn(xv, g01, acc01);
+                acc23 = __ffma2_rn(xv, g23, acc23);
                 if (tap == 0 && a < 4) bacc += to_f<TG>(sG[p][a]);
             } else {  // a = co, narrow axis = ci
-                const float g = to_f<TG>(sG[p][a]);
+                const float g1 = to_f<TG>(sG[p][a]);
+                const float2 g = make_float2(g1, g1);
                 const uint2 raw = *reinterpret_cast<const uint2*>(&sX[ky][p + kx][0]);
-                const __nv_bfloat16* xv = reinterpret_cast<const __nv_bfloat16*>(&raw);
-#pragma unroll
-                for (int i = 0; i < 4; ++i) acc[i] = fmaf(__bfloat162float(xv[i]), g, acc[i]);
-                if (tap == 0) bacc += g;
+                const __nv_bfloat162* xv = reinterpret_cast<const __nv_bfloat162*>(&raw);
+                acc01 = __ffma2_rn(__bfloat1622float2(xv[0]), g, acc01);
+                acc23 = __ffma2_rn(__bfloat1622float2(xv[1]), g, acc23);
+                if (tap == 0) bacc += g1;
             }
         }
         __syncthreads();
         stage ^= 1;
     }
     float* out = partial + (size_t)blockIdx.x * 9 * CX * CG + (size_t)tap * CX * CG;
+    const float acc[4] = {acc01.x, acc01.y, acc23.x, acc23.y};
     if (CX == 64) {
 #pragma unroll
         for (int o = 0; o < 4; ++o) out[a * CG + o] = acc[o];
