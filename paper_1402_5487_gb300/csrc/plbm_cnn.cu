@@ -711,6 +711,11 @@ int cnn_wgrad64_parts(int B, int H, int W) {
     return ntiles < sm_count() ? ntiles : sm_count();
 }
 
+cudaError_t cnn_sum_partials(const float* partial, int nparts, int n, float* out, cudaStream_t s) {
+    cnn::k_sum_partials<<<(n + 255) / 256, 256, 0, s>>>(partial, nparts, n, out);
+    return cudaGetLastError();
+}
+
 cudaError_t cnn_conv64_wgrad(int B, int H, int W, const void* X, const void* dY, float* partial, float* partial_b,
                              float* dW, float* db, cudaStream_t s) {
     if (W % cnn::kTile) return cudaErrorInvalidValue;

@@ -32,6 +32,9 @@
 // x 4 channels) are gathered into one K = 48 row (zero padded) and three MMAs
 // make the tile.
 //
+// k_wgrad_tc is the weight gradient of the 64 -> 64 layers: the reduction over
+// pixels is the K dimension, both operands MN-major.
+//
 // Every wait is bounded by the global timer: on a timeout a kernel records it
 // in *err, stops issuing work, waits (bounded) for the MMAs it issued, frees
 // its tensor memory and returns.
@@ -675,6 +678,201 @@ k_conv_in_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __n
 }
 
 // ---------------------------------------------------------------------------
+// 64 -> 64 weight gradient: dW[tap][ci][co] = sum over pixels of
+// X[pixel shifted by the tap][ci] dY[pixel][co], bias gradient db[co] = sum dY.
+// Per tile (128 pixels of one row) the three input rows (pixels x0 - 1 ..
+// x0 + 128) and the dY row are staged with cp.async in the chunk-planar
+// no-swizzle layout (chunk c of pixel s at plane c, byte 16 s), which is the
+// MN-major canonical layout for both operands: A = X^T (M = channels, K =
+// pixels) and B = dY (K = pixels, N = channels), 8-pixel K blocks 128 bytes
+// apart (leading byte offset) and 8-channel blocks one plane apart (stride byte
+// offset).  Planes of consecutive rows follow each other, so two rows stack into
+// one M = 128 operand: rows (y - 1, y) give taps ky = 0, 1 and rows (y, y + 1)
+// give ky = 1 (again, discarded) and 2.  Per K step of 16 pixels and tap column
+// kx: two MMAs of 128 x 64 x 16 into six TMEM accumulators (384 columns) that
+// sum over all of the CTA's tiles; three stages rotate so that the next two
+// tiles' copies run under the current tile's MMAs.  The CTA writes its partial
+// sums partial[cta][tap][ci][co], partial_b[cta][co] at the end.
+// ---------------------------------------------------------------------------
+constexpr int kWgThreads = 256;
+constexpr int kWgRowPix = kTile + 2;
+constexpr int kWgPlaneX = kWgRowPix * 16;       // 2080
+constexpr int kWgX = 24 * kWgPlaneX;            // 3 rows x 8 chunk planes
+constexpr int kWgPlaneG = kTile * 16;           // 2048
+constexpr int kWgStage = kWgX + 8 * kWgPlaneG;  // 66304
+constexpr int kWgStages = 3;                    // tiles in flight: two being copied while one multiplies
+constexpr int kWgSmem = 128 + kWgStages * kWgStage + 64 + 256 * 4;
+constexpr uint32_t kWgTmemCols = 512;
+// kind::f16, D fp32, A and B bf16, both MN-major (bits 15, 16), N = 64, M = 128.
+constexpr uint32_t kIdescWg = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((64u >> 3) << 17) |
+                              ((128u >> 4) << 24);
+
+__device__ __forceinline__ uint64_t desc_mn(uint32_t addr, uint32_t mn_stride) {
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(mn_stride >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+__device__ __forceinline__ void mma_wg(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.u32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(kIdescWg), "r"(accumulate)
+        : "memory");
+}
+
+__global__ void __launch_bounds__(kWgThreads, 1)
+k_wgrad_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ dY,
+           float* __restrict__ partial, float* __restrict__ partial_b, unsigned* __restrict__ err) {
+    extern __shared__ unsigned char dsm_raw[];
+    const uint32_t raw = s2u(dsm_raw);
+    const uint32_t pad = (128 - (raw & 127)) & 127;
+    unsigned char* base = dsm_raw + pad;
+    const uint32_t sbase = raw + pad;
+    unsigned char* bars_p = base + kWgStages * kWgStage;
+    const uint32_t bar0 = s2u(bars_p), bar_drain = bar0 + 8 * kWgStages;   // bar0 + 8 s: MMAs of stage s done
+    volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(bars_p + 32);
+    volatile int* abortp = reinterpret_cast<volatile int*>(bars_p + 36);
+    float* red = reinterpret_cast<float*>(bars_p + 64);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tiles_x = W / kTile;
+    const int ntiles = B * H * tiles_x;
+    if (tid == 0) {
+        for (int k = 0; k < kWgStages; ++k) bar_init(bar0 + 8 * k, 1);
+        bar_init(bar_drain, 1);
+        *abortp = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(s2u(bars_p + 32), kWgTmemCols);
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    auto stage_in = [&](int t, int k) {
+        const int b = t / (H * tiles_x);
+        const int rem = t - b * H * tiles_x;
+        const int y = rem / tiles_x;
+        const int x0 = (rem - y * tiles_x) * kTile;
+        const uint32_t st = sbase + k * kWgStage;
+        for (int i = tid; i < 3 * kWgRowPix * 8; i += kWgThreads) {
+            const int c = i & 7, pr = i >> 3, r = pr / kWgRowPix, sp = pr - r * kWgRowPix;
+            const int yy = wrapi(y + r - 1, H), xx = wrapi(x0 + sp - 1, W);
+            cp_async16(st + (r * 8 + c) * kWgPlaneX + 16 * sp, X + (((size_t)b * H + yy) * W + xx) * kC + 8 * c);
+        }
+        for (int i = tid; i < kTile * 8; i += kWgThreads) {
+            const int c = i & 7, p = i >> 3;
+            cp_async16(st + kWgX + c * kWgPlaneG + 16 * p, dY + (((size_t)b * H + y) * W + x0 + p) * kC + 8 * c);
+        }
+    };
+
+    uint32_t phase = 0u;   // bit k: parity of the next completion of stage k's MMA barrier
+    int it = 0;
+    float bsum[8];         // warp w: channels 8 w .. 8 w + 7, pixels lane + 32 j of every tile
+#pragma unroll
+    for (int i = 0; i < 8; ++i) bsum[i] = 0.0f;
+    for (int j = 0; j < kWgStages - 1; ++j) {
+        if ((int)blockIdx.x + j * (int)gridDim.x < ntiles) stage_in(blockIdx.x + j * gridDim.x, j);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        const int k = it % kWgStages;
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(kWgStages - 2) : "memory");
+        fence_async_smem();
+        __syncthreads();
+        if (*abortp) break;
+        const uint32_t sX = sbase + k * kWgStage, sG = sX + kWgX;
+        if (tid == 0) {   // queued behind the previous tile's MMAs: the tensor pipe does not wait for the copies
+            tc_after_sync();
+#pragma unroll 1
+            for (int ks = 0; ks < kTile / 16; ++ks) {
+                const uint64_t bd = desc_mn(sG + 16 * 16 * ks, kWgPlaneG);
+#pragma unroll
+                for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+                    for (int pr = 0; pr < 2; ++pr)
+                        mma_wg(tmem + (uint32_t)((kx * 2 + pr) * 64),
+                               desc_mn(sX + pr * 8 * kWgPlaneX + 16 * (16 * ks + kx), kWgPlaneX), bd,
+                               (it > 0 || ks > 0) ? 1u : 0u);
+            }
+            tc_commit(bar0 + 8 * k);
+        }
+        // the stage of tile it - 1 takes tile it + kWgStages - 1 once that tile's MMAs are done
+        const int kf = (it + kWgStages - 1) % kWgStages;
+        if (it >= 1) {
+            if (!bar_wait(bar0 + 8 * kf, (phase >> kf) & 1u, abortp)) *abortp = 1;
+            phase ^= 1u << kf;
+        }
+        const int tf = t + (kWgStages - 1) * (int)gridDim.x;
+        if (!*abortp && tf < ntiles) stage_in(tf, kf);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        {   // bias: warp w sums plane w (channels 8 w ..), 16 contiguous bytes per pixel
+            const unsigned char* g = base + k * kWgStage + kWgX + warp * kWgPlaneG;
+#pragma unroll
+            for (int j = 0; j < kTile / 32; ++j) {
+                const uint4 r = *reinterpret_cast<const uint4*>(g + 16 * (lane + 32 * j));
+                const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&r);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float2 f = __bfloat1622float2(h[i]);
+                    bsum[2 * i] += f.x;
+                    bsum[2 * i + 1] += f.y;
+                }
+            }
+        }
+        __syncthreads();   // every thread is done with this stage before it is refilled
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    if (it > 0 && !*abortp) {
+        const int kl = (it - 1) % kWgStages;
+        if (!bar_wait(bar0 + 8 * kl, (phase >> kl) & 1u, abortp)) *abortp = 1;
+    }
+    __syncthreads();
+    tc_after_sync();
+    if (!*abortp && it > 0) {
+        // warps 0-3 read accumulators 0-2, warps 4-7 accumulators 3-5, each its own 32 TMEM lanes
+        const int L = 32 * (warp & 3) + lane;
+        const int ci = L & 63;
+        for (int j = 0; j < 3; ++j) {
+            const int acc = 3 * (warp >> 2) + j;
+            const int kx = acc >> 1, pr = acc & 1;
+            uint32_t v[64];
+            const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(acc * 64);
+            PLBM_TMEM_LD32(v, 0, taddr);
+            PLBM_TMEM_LD32(v, 32, taddr + 32);
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            if (pr == 1 && L < 64) continue;   // rows (y, y + 1), upper half: tap ky = 1 again
+            const int ky = pr == 0 ? (L < 64 ? 0 : 1) : 2;
+            float4* out = reinterpret_cast<float4*>(partial + (((size_t)blockIdx.x * 9 + ky * 3 + kx) * kC + ci) * kC);
+#pragma unroll
+            for (int c4 = 0; c4 < 16; ++c4)
+                out[c4] = make_float4(__uint_as_float(v[4 * c4]), __uint_as_float(v[4 * c4 + 1]),
+                                      __uint_as_float(v[4 * c4 + 2]), __uint_as_float(v[4 * c4 + 3]));
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        float v = bsum[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[8 * warp + i] = v;
+    }
+    tc_before_sync();
+    __syncthreads();
+    if (tid < kC) partial_b[(size_t)blockIdx.x * kC + tid] = red[tid];
+    if (tid == 0 && it > 0) {   // drain every issued MMA before the accumulators are released
+        tc_commit(bar_drain);
+        if (!bar_wait_drain(bar_drain, 0)) *abortp = 1;
+    }
+    __syncthreads();
+    if (tid == 0 && *abortp) atomicOr(err, 1u);
+    if (warp == 0) {
+        tc_after_sync();
+        tmem_free(tmem, kWgTmemCols);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Weight layouts for the kernels above, from W[tap][ci][co].
 // ---------------------------------------------------------------------------
 // 64 -> 64: forward Wf[tap][co][ci] = W[tap][ci][co]; backward data Wb[tap][ci][co] = W[8 - tap][ci][co].
@@ -788,6 +986,26 @@ cudaError_t cnn_conv_in_tc(int B, int H, int W, const void* X, const void* Win, 
                                                                static_cast<const __nv_bfloat16*>(Win), bias,
                                                                static_cast<__nv_bfloat16*>(Y), relu, err);
     return cudaGetLastError();
+}
+
+cudaError_t cnn_conv64_wgrad_tc(int B, int H, int W, const void* X, const void* dY, float* partial, float* partial_b,
+                                float* dW, float* db, unsigned* err, cudaStream_t s) {
+    if (W % tc::kTile || H < 1 || B < 1) return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(tc::k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kWgSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int grid = cnn_wgrad64_parts(B, H, W);   // one CTA per SM at most (the partial buffers' size)
+    tc::k_wgrad_tc<<<grid, tc::kWgThreads, tc::kWgSmem, s>>>(B, H, W, static_cast<const __nv_bfloat16*>(X),
+                                                             static_cast<const __nv_bfloat16*>(dY), partial,
+                                                             partial_b, err);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = cnn_sum_partials(partial, grid, 9 * tc::kC * tc::kC, dW, s);
+    if (e != cudaSuccess) return e;
+    return cnn_sum_partials(partial_b, grid, tc::kC, db, s);
 }
 
 cudaError_t cnn_weights_kmajor(const void* W, void* Wf, void* Wb, cudaStream_t s) {

@@ -177,8 +177,12 @@ plbm_status backward(Sur* s, int B, const void* x, const float* dout) {
     SCK(plbm::cnn_conv_thin_fwd(4, 64, 1, 0, B, H, W, dout, s->w6flip, nullptr, s->act[4], s->dz[4], 1, 0,
                                 s->stream));
     for (int l = 4; l >= 1; --l) {
-        SCK(plbm::cnn_conv64_wgrad(B, H, W, s->act[l - 1], s->dz[l], s->part, s->part_b, s->g + s->woff[l],
-                                   s->g + s->boff[l], s->stream));
+        if (s->use_tc)
+            SCK(plbm::cnn_conv64_wgrad_tc(B, H, W, s->act[l - 1], s->dz[l], s->part, s->part_b, s->g + s->woff[l],
+                                          s->g + s->boff[l], s->derr, s->stream));
+        else
+            SCK(plbm::cnn_conv64_wgrad(B, H, W, s->act[l - 1], s->dz[l], s->part, s->part_b, s->g + s->woff[l],
+                                       s->g + s->boff[l], s->stream));
         if (s->use_tc) {
             SCK(plbm::cnn_conv64_tc(B, H, W, s->dz[l], wtc_bwd(s, l), nullptr, s->act[l - 1], s->dz[l - 1], 1, 0,
                                     s->derr, s->stream));

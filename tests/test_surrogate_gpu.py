@@ -285,3 +285,25 @@ def test_mean_penalty_enters_the_training_gradient():
     assert rel(g_step, g_plain) > 1e-3      # the penalty does change the gradient
     net.set_mean_penalty(0.0)
     net.close()
+
+
+def test_weight_gradients_over_many_tiles_per_cta_match_oracle():
+    # 2 x 160 x 256 pixels = 640 tiles of 128: every CTA of the weight-gradient
+    # kernels sums several tiles (the accumulators carry across tiles).
+    import torch
+    net = SG.Surrogate(2, H=160, W=256, seed=11)
+    g = torch.Generator().manual_seed(5)
+    x = torch.randn((2, 160, 256, 4), generator=g).to(torch.bfloat16).cuda()
+    dout = (0.01 * torch.randn((2, 160, 256, 4), generator=g)).cuda()
+    for tc in (True, False):
+        net.set_tensor_path(tc)
+        net.forward(x, 2)
+        A = [net.tensor(0, l, 2).float().cpu().numpy().astype(np.float64) for l in range(1, 5)]
+        grads = split(net.backward(x, dout, 2))
+        dZ = [net.tensor(1, l, 2).float().cpu().numpy().astype(np.float64) for l in range(1, 6)]
+        assert net.check() == plbm.PLBM_OK
+        for l in range(1, 5):   # the 64 -> 64 layers: input A_l, upstream dZ_{l+1}
+            dW, db = N.conv3x3_grad_weight(A[l - 1], dZ[l])
+            assert rel(grads[l][0], dW) < 1e-3, (tc, l)
+            assert rel(grads[l][1], db) < 1e-3, (tc, l)
+    net.close()
