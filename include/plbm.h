@@ -345,9 +345,10 @@ plbm_status plbm_sur_create(int max_batch, int H, int W, unsigned long long seed
                             plbm_surrogate *out);
 plbm_status plbm_sur_destroy(plbm_surrogate s);
 
-/* Options: PLBM_SUR_OPT_TENSOR_PATH selects the kernel of the 64 -> 64
- * convolutions and their backward-data passes: 1 (default) tcgen05.mma with
- * tensor-memory accumulators, 0 mma.sync (kept as a cross-check). */
+/* Options: PLBM_SUR_OPT_TENSOR_PATH selects the kernels of the 64 -> 64
+ * convolutions, their backward-data passes and their weight gradients: 1
+ * (default) tcgen05.mma with tensor-memory accumulators, 0 mma.sync (kept as a
+ * cross-check). */
 #define PLBM_SUR_OPT_TENSOR_PATH 1
 /* PLBM_SUR_OPT_CONSERVE: 1 shifts each lattice's predicted conserved densities
  * (rho, rho u, E = rho (d theta + |u|^2)) uniformly so that their totals equal

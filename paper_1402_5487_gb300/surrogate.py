@@ -134,7 +134,8 @@ class Surrogate:
             pass
 
     def set_tensor_path(self, tcgen05: bool):
-        """tcgen05.mma (True, default) or mma.sync (False) for the 64 -> 64 convolutions."""
+        """tcgen05.mma (True, default) or mma.sync (False) for the 64 -> 64 convolutions,
+        their backward-data passes and their weight gradients."""
         self._ok(plbm.lib().plbm_sur_set_option(self.h, 1, 1 if tcgen05 else 0))
 
     def set_conserve(self, on: bool):
