@@ -32,8 +32,9 @@
 // x 4 channels) are gathered into one K = 48 row (zero padded) and three MMAs
 // make the tile.
 //
-// k_wgrad_tc is the weight gradient of the 64 -> 64 layers: the reduction over
-// pixels is the K dimension, both operands MN-major.
+// k_wgrad_tc and k_wgrad_in_tc are the weight gradients of the 64 -> 64 layers
+// and of the 4 -> 64 input layer: the reduction over pixels is the K dimension,
+// both operands MN-major.
 //
 // Every wait is bounded by the global timer: on a timeout a kernel records it
 // in *err, stops issuing work, waits (bounded) for the MMAs it issued, frees
@@ -873,6 +874,167 @@ k_wgrad_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __nv_
 }
 
 // ---------------------------------------------------------------------------
+// 4 -> 64 input-layer weight gradient: dW[tap][ci][co] = sum over pixels of
+// X[pixel shifted by the tap][ci] dY[pixel][co].  M = (tap, ci) = 36 rows, padded
+// to 128: per tile the 9 taps x 4 channels of each pixel are gathered (8-byte
+// cp.async per tap) into chunk planes 0..4 (row m = 4 tap + ci in plane m / 8),
+// planes 5..15 stay zero; dY as in k_wgrad_tc.  One MMA of 128 x 64 x 16 per 16
+// pixels into one accumulator summed over the CTA's tiles; three stages.
+// Partials per CTA: partial[cta][tap][ci][co], partial_b[cta][co].
+// ---------------------------------------------------------------------------
+constexpr int kWiA = 16 * kWgPlaneG;              // 32 KB: 16 planes of 128 pixels x 16 bytes
+constexpr int kWiStage = kWiA + 8 * kWgPlaneG;    // + dY
+constexpr int kWiSmem = 128 + kWgStages * kWiStage + 64 + 256 * 4;
+constexpr uint32_t kWiTmemCols = 64;
+
+__global__ void __launch_bounds__(kWgThreads, 1)
+k_wgrad_in_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ dY,
+              float* __restrict__ partial, float* __restrict__ partial_b, unsigned* __restrict__ err) {
+    extern __shared__ unsigned char dsm_raw[];
+    const uint32_t raw = s2u(dsm_raw);
+    const uint32_t pad = (128 - (raw & 127)) & 127;
+    unsigned char* base = dsm_raw + pad;
+    const uint32_t sbase = raw + pad;
+    unsigned char* bars_p = base + kWgStages * kWiStage;
+    const uint32_t bar0 = s2u(bars_p), bar_drain = bar0 + 8 * kWgStages;
+    volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(bars_p + 32);
+    volatile int* abortp = reinterpret_cast<volatile int*>(bars_p + 36);
+    float* red = reinterpret_cast<float*>(bars_p + 64);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tiles_x = W / kTile;
+    const int ntiles = B * H * tiles_x;
+    // zero the A planes of every stage once: the gathers write planes 0..4 only
+    // (plane 4: the first 8 bytes of each pixel, tap 8)
+    for (int i = tid; i < kWgStages * kWiA / 16; i += kWgThreads) {
+        const int k = i / (kWiA / 16), j = i - k * (kWiA / 16);
+        *reinterpret_cast<uint4*>(base + k * kWiStage + 16 * j) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (tid == 0) {
+        for (int k = 0; k < kWgStages; ++k) bar_init(bar0 + 8 * k, 1);
+        bar_init(bar_drain, 1);
+        *abortp = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(s2u(bars_p + 32), kWiTmemCols);
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    auto stage_in = [&](int t, int k) {
+        const int b = t / (H * tiles_x);
+        const int rem = t - b * H * tiles_x;
+        const int y = rem / tiles_x;
+        const int x0 = (rem - y * tiles_x) * kTile;
+        const uint32_t st = sbase + k * kWiStage;
+        for (int i = tid; i < kTile * 9; i += kWgThreads) {   // (pixel, tap): 4 channels = 8 bytes
+            const int p = i / 9, tap = i - 9 * p;
+            const int yy = wrapi(y + tap / 3 - 1, H), xx = wrapi(x0 + p + tap % 3 - 1, W);
+            const uint32_t dst = st + (tap >> 1) * kWgPlaneG + 16 * p + 8 * (tap & 1);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst),
+                         "l"(X + (((size_t)b * H + yy) * W + xx) * 4)
+                         : "memory");
+        }
+        for (int i = tid; i < kTile * 8; i += kWgThreads) {
+            const int c = i & 7, p = i >> 3;
+            cp_async16(st + kWiA + c * kWgPlaneG + 16 * p, dY + (((size_t)b * H + y) * W + x0 + p) * kC + 8 * c);
+        }
+    };
+
+    uint32_t phase = 0u;
+    int it = 0;
+    float bsum[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) bsum[i] = 0.0f;
+    for (int j = 0; j < kWgStages - 1; ++j) {
+        if ((int)blockIdx.x + j * (int)gridDim.x < ntiles) stage_in(blockIdx.x + j * gridDim.x, j);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        const int k = it % kWgStages;
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(kWgStages - 2) : "memory");
+        fence_async_smem();
+        __syncthreads();
+        if (*abortp) break;
+        const uint32_t sA = sbase + k * kWiStage, sG = sA + kWiA;
+        if (tid == 0) {
+            tc_after_sync();
+#pragma unroll 1
+            for (int ks = 0; ks < kTile / 16; ++ks)
+                mma_wg(tmem, desc_mn(sA + 16 * 16 * ks, kWgPlaneG), desc_mn(sG + 16 * 16 * ks, kWgPlaneG),
+                       (it > 0 || ks > 0) ? 1u : 0u);
+            tc_commit(bar0 + 8 * k);
+        }
+        const int kf = (it + kWgStages - 1) % kWgStages;
+        if (it >= 1) {
+            if (!bar_wait(bar0 + 8 * kf, (phase >> kf) & 1u, abortp)) *abortp = 1;
+            phase ^= 1u << kf;
+        }
+        const int tf = t + (kWgStages - 1) * (int)gridDim.x;
+        if (!*abortp && tf < ntiles) stage_in(tf, kf);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        {
+            const unsigned char* g = base + k * kWiStage + kWiA + warp * kWgPlaneG;
+#pragma unroll
+            for (int j = 0; j < kTile / 32; ++j) {
+                const uint4 r = *reinterpret_cast<const uint4*>(g + 16 * (lane + 32 * j));
+                const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&r);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float2 f = __bfloat1622float2(h[i]);
+                    bsum[2 * i] += f.x;
+                    bsum[2 * i + 1] += f.y;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    if (it > 0 && !*abortp) {
+        const int kl = (it - 1) % kWgStages;
+        if (!bar_wait(bar0 + 8 * kl, (phase >> kl) & 1u, abortp)) *abortp = 1;
+    }
+    __syncthreads();
+    tc_after_sync();
+    if (!*abortp && it > 0 && warp < 2) {   // TMEM lanes 0..63 hold rows m = 4 tap + ci < 36
+        const int m = 32 * warp + lane;
+        uint32_t v[64];
+        const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
+        PLBM_TMEM_LD32(v, 0, taddr);
+        PLBM_TMEM_LD32(v, 32, taddr + 32);
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        if (m < 36) {
+            float4* out = reinterpret_cast<float4*>(partial + ((size_t)blockIdx.x * 36 + m) * kC);
+#pragma unroll
+            for (int c4 = 0; c4 < 16; ++c4)
+                out[c4] = make_float4(__uint_as_float(v[4 * c4]), __uint_as_float(v[4 * c4 + 1]),
+                                      __uint_as_float(v[4 * c4 + 2]), __uint_as_float(v[4 * c4 + 3]));
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        float v = bsum[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[8 * warp + i] = v;
+    }
+    tc_before_sync();
+    __syncthreads();
+    if (tid < kC) partial_b[(size_t)blockIdx.x * kC + tid] = red[tid];
+    if (tid == 0 && it > 0) {
+        tc_commit(bar_drain);
+        if (!bar_wait_drain(bar_drain, 0)) *abortp = 1;
+    }
+    __syncthreads();
+    if (tid == 0 && *abortp) atomicOr(err, 1u);
+    if (warp == 0) {
+        tc_after_sync();
+        tmem_free(tmem, kWiTmemCols);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Weight layouts for the kernels above, from W[tap][ci][co].
 // ---------------------------------------------------------------------------
 // 64 -> 64: forward Wf[tap][co][ci] = W[tap][ci][co]; backward data Wb[tap][ci][co] = W[8 - tap][ci][co].
@@ -1004,6 +1166,27 @@ cudaError_t cnn_conv64_wgrad_tc(int B, int H, int W, const void* X, const void* 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = cnn_sum_partials(partial, grid, 9 * tc::kC * tc::kC, dW, s);
+    if (e != cudaSuccess) return e;
+    return cnn_sum_partials(partial_b, grid, tc::kC, db, s);
+}
+
+cudaError_t cnn_conv_in_wgrad_tc(int B, int H, int W, const void* X, const void* dY, float* partial, float* partial_b,
+                                 float* dW, float* db, unsigned* err, cudaStream_t s) {
+    if (W % tc::kTile || H < 1 || B < 1) return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e =
+            cudaFuncSetAttribute(tc::k_wgrad_in_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kWiSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int grid = cnn_wgrad64_parts(B, H, W);   // at most one CTA per SM: within the partial buffers
+    tc::k_wgrad_in_tc<<<grid, tc::kWgThreads, tc::kWiSmem, s>>>(B, H, W, static_cast<const __nv_bfloat16*>(X),
+                                                                static_cast<const __nv_bfloat16*>(dY), partial,
+                                                                partial_b, err);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = cnn_sum_partials(partial, grid, 9 * 4 * tc::kC, dW, s);
     if (e != cudaSuccess) return e;
     return cnn_sum_partials(partial_b, grid, tc::kC, db, s);
 }

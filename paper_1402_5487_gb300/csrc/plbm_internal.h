@@ -118,6 +118,8 @@ cudaError_t cnn_conv64_wgrad(int B, int H, int W, const void* X, const void* dY,
 cudaError_t cnn_conv64_wgrad_tc(int B, int H, int W, const void* X, const void* dY, float* partial, float* partial_b,
                                 float* dW, float* db, unsigned* err, cudaStream_t s);
 cudaError_t cnn_sum_partials(const float* partial, int nparts, int n, float* out, cudaStream_t s);
+cudaError_t cnn_conv_in_wgrad_tc(int B, int H, int W, const void* X, const void* dY, float* partial, float* partial_b,
+                                 float* dW, float* db, unsigned* err, cudaStream_t s);
 cudaError_t cnn_conv_thin_fwd(int ci, int co, int ti, int to, int B, int H, int W, const void* X, const float* Wf,
                               const float* bias, const void* mask, void* Y, int mode, int relu, cudaStream_t s);
 int cnn_thin_parts(int B, int H, int W, int* pix_per_block);

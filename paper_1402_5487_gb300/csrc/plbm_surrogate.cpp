@@ -191,8 +191,12 @@ plbm_status backward(Sur* s, int B, const void* x, const float* dout) {
             SCK(plbm::cnn_conv64_fwd(B, H, W, s->dz[l], wf, nullptr, s->act[l - 1], s->dz[l - 1], 1, 0, s->stream));
         }
     }
-    SCK(plbm::cnn_conv_thin_wgrad(4, 64, 0, 0, B, H, W, x, s->dz[0], s->part, s->part_b, s->g + s->woff[0],
-                                  s->g + s->boff[0], s->stream));
+    if (s->use_tc)
+        SCK(plbm::cnn_conv_in_wgrad_tc(B, H, W, x, s->dz[0], s->part, s->part_b, s->g + s->woff[0],
+                                       s->g + s->boff[0], s->derr, s->stream));
+    else
+        SCK(plbm::cnn_conv_thin_wgrad(4, 64, 0, 0, B, H, W, x, s->dz[0], s->part, s->part_b, s->g + s->woff[0],
+                                      s->g + s->boff[0], s->stream));
     return PLBM_OK;
 }
 

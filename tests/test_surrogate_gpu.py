@@ -289,7 +289,8 @@ def test_mean_penalty_enters_the_training_gradient():
 
 def test_weight_gradients_over_many_tiles_per_cta_match_oracle():
     # 2 x 160 x 256 pixels = 640 tiles of 128: every CTA of the weight-gradient
-    # kernels sums several tiles (the accumulators carry across tiles).
+    # kernels sums several tiles (the accumulators carry across tiles); the
+    # 64 -> 64 layers and the 4 -> 64 input layer on both tensor paths.
     import torch
     net = SG.Surrogate(2, H=160, W=256, seed=11)
     g = torch.Generator().manual_seed(5)
@@ -306,4 +307,8 @@ def test_weight_gradients_over_many_tiles_per_cta_match_oracle():
             dW, db = N.conv3x3_grad_weight(A[l - 1], dZ[l])
             assert rel(grads[l][0], dW) < 1e-3, (tc, l)
             assert rel(grads[l][1], db) < 1e-3, (tc, l)
+        # the 4 -> 64 input layer: input x, upstream dZ_1
+        dW, db = N.conv3x3_grad_weight(x.float().cpu().numpy().astype(np.float64), dZ[0])
+        assert rel(grads[0][0], dW) < 1e-3, (tc, 0)
+        assert rel(grads[0][1], db) < 1e-3, (tc, 0)
     net.close()
