@@ -137,6 +137,16 @@ def test_d1q5_zero_velocity_theta_window(v):
     assert abs(lo - a * a / 3) < 1e-9 and abs(hi - b * b / 3) < 1e-9
 
 
+def test_iteration_counts_cover_the_same_time():
+    # Sec. 3.2: with the lattice spacing fixed, a step of the three-velocity model
+    # {0, +-sqrt(zeta theta0)} lasts dt ~ 1 / sqrt(zeta) in units of sqrt(theta0), so
+    # 362 LBGK steps (zeta = 3) cover the time of 362 x 2 / sqrt(3) zeta = 4 steps,
+    # 418 up to the printed mismatch.
+    vals = read_printed_values()
+    n3, n4 = vals["shock6_iterations_lbgk"], vals["shock6_iterations_param"]
+    assert abs(n3 * math.sqrt(4) / math.sqrt(3) - n4 - vals["time_mismatch_iterations"]) < 5e-5
+
+
 def test_matched_relaxation_constant():
     # Sec. 3.2: nu = (1/omega - 1/2) sqrt(theta0) dx / sqrt(zeta); LBGK (zeta 3, omega 1)
     # and zeta = 4 share viscosity at omega = 4 sqrt(3) - 6.
