@@ -130,6 +130,21 @@ def test_d1q3_positivity_range(zeta, printed):
     assert abs(lo / math.sqrt(theta0) + vals[printed]) < 1e-9
 
 
+def test_d1q3_moving_population_touches_zero_at_the_printed_point():
+    # Fig. 1: with the lattice velocity 2 sqrt(theta0) (zeta = 4), r of the velocity
+    # against the flow reaches zero at u = sqrt(theta0) and is positive on either
+    # side; a slightly larger lattice velocity makes it negative there.
+    vals = read_printed_values()
+    u1, v2 = vals["fig1_P1_u"], vals["fig1_P1_v2"]
+    th = 1.0 / v2 ** 2   # lattice velocities {0, +-1} = {0, +-v2 sqrt(th)}
+    r = lambda ub, t=th: O.r1d((0, 1, -1), ub * math.sqrt(t), t)
+    assert abs(r(u1)[2]) < 1e-15 and r(u1)[0] > 0.4 and r(u1)[1] > 0.4
+    for ub in (0.9, 0.99, 1.01, 1.1):
+        assert r(ub)[2] > 0
+    th_wider = 1.0 / (1.01 * v2) ** 2
+    assert r(u1, th_wider)[2] < 0
+
+
 @pytest.mark.parametrize("v", [(0, 1, -1, 3, -3), (0, 1, -1, 2, -2), (0, 2, -2, 3, -3)])
 def test_d1q5_zero_velocity_theta_window(v):
     a, b = abs(v[1]), abs(v[3])
