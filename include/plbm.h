@@ -444,13 +444,20 @@ const char *plbm_sur_last_error(plbm_surrogate s);
  *        plbm_get_populations), velocities v (q1 integers, host memory).
  *   out: device pointer to 6 doubles: mass, jx, jy, energy (sum |v|^2 f),
  *        rho_min, theta_min, with the moment definitions of this header.
- * Runs on `stream` (cudaStream_t, NULL = default) of the current device and
- * returns without synchronising.  The first call on a device looks up the
- * scratch array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture starts.  All calls share the one array: calls that
- * overlap on the GPU race and may return wrong sums, so serialise them.
- * Errors: PLBM_E_ARG for bad arguments or nx * ny > PLBM_NOALLOC_MAX_NODES,
- * PLBM_E_CUDA for a failed lookup or launch (text in plbm_last_error(NULL)). */
+ * Runs on `stream` (cudaStream_t, NULL = default) in the CUDA context current
+ * on the calling thread and returns without synchronising.  Any context is
+ * supported: the runtime's primary context of a device, or a context the
+ * caller created and made current with the driver API.  The static array has
+ * its own address in each context; the first call in a context looks that
+ * address up (cudaGetSymbolAddress) and caches it under the context's unique
+ * ID (cuCtxGetId), for up to 64 contexts at a time; make that first call before
+ * any stream capture starts.  All calls share the one array of their context:
+ * calls that overlap on the GPU race and may return wrong sums, so serialise
+ * them.
+ * Errors: PLBM_E_ARG for bad arguments or nx * ny > PLBM_NOALLOC_MAX_NODES;
+ * PLBM_E_CUDA for a failed lookup, a failed launch (the message names the
+ * kernel) or a CUDA error that earlier work left pending (reported, not
+ * cleared); text in plbm_last_error(NULL). */
 plbm_status plbm_diagnostics_noalloc(int dim, int q1, const int *v, int nx, int ny, const double *f,
                                      double *out, void *stream);
 

@@ -2,7 +2,11 @@
 
 TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 CPU-baseline / reference leg of ``bench.py`` may import this package.  It shares
-no code with the CUDA path (``paper_1402_5487_gb300``) and never imports it.
+no code with the CUDA path (``paper_1402_5487_gb300``): no module here imports the
+library or its binding.  The one import from that package is
+``paper_1402_5487_gb300.inputs`` in ``oracle.kh_longrun``: the seeded input-field
+generators that both sides take their inputs from, which hold none of the
+method's arithmetic.
 
 The arithmetic lives in ``plbm_oracle.c`` (plain C, FP64, ``-ffp-contract=off``),
 loaded here through ctypes.  Companion tools written in NumPy:

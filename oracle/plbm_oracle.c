@@ -6,7 +6,7 @@
  * test suite, the smoke check and the CPU-baseline leg of the benchmark may
  * load it.  It shares no code, header or constant table with the CUDA path.
  *
- * Build: gcc -O2 -ffp-contract=off -fopenmp -shared -fPIC (see build_oracle.py).
+ * Build: gcc -O2 -ffp-contract=off -fopenmp -shared -fPIC (oracle/__init__.py, build()).
  * -ffp-contract=off keeps every product and sum rounded separately, so the
  * result only depends on the order of operations written below.
  *

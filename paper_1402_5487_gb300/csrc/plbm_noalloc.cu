@@ -9,9 +9,15 @@
 // file-scope device array below, which every GPU that loads the library holds
 // until the process exits.
 //
-// Set-up: the first call on a device looks up the device address of that array
-// with cudaGetSymbolAddress while the device is current and caches it.  Make the
-// first call on each device before any stream capture begins.
+// Set-up: a __device__ array exists once per CUDA context, at a different
+// address in each.  The first call made while a given context is current
+// looks up the array's address in that context with cudaGetSymbolAddress and
+// caches it under the context's unique ID (cuCtxGetId: IDs are never reused,
+// so a context destroyed by cudaDeviceReset or cuCtxDestroy and a new one at
+// the same handle value never share an entry).  Any context works: the
+// device's primary context of the runtime API, or one the caller created and
+// made current with the driver API.  Make the first call in each context
+// before any stream capture begins.
 //
 // Every call shares the one array.  Each block writes its own record before
 // the final pass reads it, so nothing has to start at zero and stale contents
@@ -23,6 +29,8 @@
 #include <cstdio>
 #include <mutex>
 
+#include <cuda.h>  // CUcontext and the driver's function types; nothing is linked from libcuda
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include "plbm_internal.h"
@@ -32,7 +40,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kMaxBlocks = PLBM_NOALLOC_MAX_NODES / kThreads;
 constexpr int kRecord = 8;     // doubles per block record (6 used)
-constexpr int kMaxDevices = 64;
+constexpr int kMaxContexts = 64;  // cached addresses; the oldest entry is replaced first
 constexpr int kFinalThreads = 512;
 
 static __device__ __align__(256) double g_noalloc_scratch[kMaxBlocks * kRecord];
@@ -106,12 +114,88 @@ __global__ void __launch_bounds__(kFinalThreads) k_noalloc_final(const double* _
 }
 
 std::mutex g_mutex;
-double* g_scratch_ptr[kMaxDevices] = {nullptr};
+
+struct ContextSlot {
+    unsigned long long id;  // cuCtxGetId of the context; 0 = empty slot
+    double* scratch;        // g_noalloc_scratch's device address in that context
+};
+ContextSlot g_slots[kMaxContexts] = {};
+int g_next_slot = 0;
+PFN_cuCtxGetCurrent_v4000 g_ctx_get_current = nullptr;
+PFN_cuCtxGetId_v12000 g_ctx_get_id = nullptr;
 
 void fail(const char* fmt, const char* a = "", long long n = 0) {
     char buf[256];
     std::snprintf(buf, sizeof buf, fmt, a, n);
     plbm::set_thread_error(buf);
+}
+
+// Driver entry points through the runtime (no link-time dependence on libcuda).
+bool load_driver_entry_points() {
+    if (g_ctx_get_current && g_ctx_get_id) return true;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 4000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+        return false;
+    g_ctx_get_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(fn);
+    fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+        return false;
+    g_ctx_get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(fn);
+    return true;
+}
+
+// Device address of g_noalloc_scratch in the context current on this thread.
+// Host code sees g_noalloc_scratch only as a stand-in symbol, so the kernels
+// must be given this address.  Called with g_mutex held.
+plbm_status scratch_of_current_context(double** out) {
+    if (!load_driver_entry_points()) {
+        fail("plbm_diagnostics_noalloc: driver entry points cuCtxGetCurrent/cuCtxGetId unavailable%s");
+        return PLBM_E_CUDA;
+    }
+    void* looked_up = nullptr;
+    CUcontext ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS) {
+        fail("plbm_diagnostics_noalloc: cuCtxGetCurrent failed%s");
+        return PLBM_E_CUDA;
+    }
+    if (!ctx) {
+        // No context is current on this thread yet: the runtime makes the current
+        // device's primary context current on its first call, this lookup.
+        const cudaError_t e = cudaGetSymbolAddress(&looked_up, g_noalloc_scratch);
+        if (e != cudaSuccess || !looked_up) {
+            fail("plbm_diagnostics_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+            return PLBM_E_CUDA;
+        }
+        if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx) {
+            fail("plbm_diagnostics_noalloc: no CUDA context is current%s");
+            return PLBM_E_CUDA;
+        }
+    }
+    unsigned long long id = 0;
+    if (g_ctx_get_id(ctx, &id) != CUDA_SUCCESS || id == 0) {
+        fail("plbm_diagnostics_noalloc: cuCtxGetId failed%s");
+        return PLBM_E_CUDA;
+    }
+    for (const ContextSlot& slot : g_slots) {
+        if (slot.id == id) {
+            *out = slot.scratch;
+            return PLBM_OK;
+        }
+    }
+    if (!looked_up) {
+        const cudaError_t e = cudaGetSymbolAddress(&looked_up, g_noalloc_scratch);
+        if (e != cudaSuccess || !looked_up) {
+            fail("plbm_diagnostics_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+            return PLBM_E_CUDA;
+        }
+    }
+    g_slots[g_next_slot] = ContextSlot{id, static_cast<double*>(looked_up)};
+    g_next_slot = (g_next_slot + 1) % kMaxContexts;
+    *out = static_cast<double*>(looked_up);
+    return PLBM_OK;
 }
 
 }  // namespace
@@ -129,27 +213,19 @@ extern "C" plbm_status plbm_diagnostics_noalloc(int dim, int q1, const int* v, i
              "(the size of the static scratch array)", "", nodes);
         return PLBM_E_ARG;
     }
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-        fail("plbm_diagnostics_noalloc: no usable current CUDA device: %s", cudaGetErrorString(e));
+    // An error left pending by earlier, unrelated work is reported as such (and
+    // left in place) rather than blamed on this call's launches.
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) {
+        fail("plbm_diagnostics_noalloc: a CUDA error from earlier work is pending (not cleared): %s",
+             cudaGetErrorString(e));
         return PLBM_E_CUDA;
     }
     double* scratch = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_mutex);
-        if (!g_scratch_ptr[dev]) {
-            // Host code sees g_noalloc_scratch only as a stand-in symbol: the kernel
-            // must get the device address, looked up once per device.
-            void* p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-            if (e != cudaSuccess || !p) {
-                fail("plbm_diagnostics_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-                return PLBM_E_CUDA;
-            }
-            g_scratch_ptr[dev] = static_cast<double*>(p);
-        }
-        scratch = g_scratch_ptr[dev];
+        const plbm_status st = scratch_of_current_context(&scratch);
+        if (st != PLBM_OK) return st;
     }
     NodeSet L{};
     L.dim = dim;
@@ -161,10 +237,15 @@ extern "C" plbm_status plbm_diagnostics_noalloc(int dim, int q1, const int* v, i
     const int nblocks = (int)((nodes + kThreads - 1) / kThreads);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     k_noalloc_partials<<<nblocks, kThreads, 0, s>>>(L, f, scratch);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        fail("plbm_diagnostics_noalloc: launch of k_noalloc_partials failed: %s", cudaGetErrorString(e));
+        return PLBM_E_CUDA;
+    }
     k_noalloc_final<<<1, kFinalThreads, 0, s>>>(scratch, nblocks, out);
     e = cudaGetLastError();
     if (e != cudaSuccess) {
-        fail("plbm_diagnostics_noalloc: launch failed: %s", cudaGetErrorString(e));
+        fail("plbm_diagnostics_noalloc: launch of k_noalloc_final failed: %s", cudaGetErrorString(e));
         return PLBM_E_CUDA;
     }
     return PLBM_OK;

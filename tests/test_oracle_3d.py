@@ -118,6 +118,21 @@ def test_adiabatic_sound_wave_travels_at_sqrt_gamma_theta():
     assert abs(speed / c - 1) < 0.01
 
 
+def test_conserved_sums_equal_sums_of_the_node_moments():
+    """orc3_conserved against the fields of orc3_moments on a random state
+    (sum |v|^2 f = rho (|u|^2 + 3 theta), reading R3 with d = 3)."""
+    lat = O.Lattice3(V5, 1.3, 5, 4, 3, theta0=1.0)
+    rng = np.random.default_rng(33)
+    q = len(V5) ** 3
+    f = rng.uniform(0.2, 1.8, (q, 3, 4, 5)) * (1.0 + 0.5 * rng.uniform(0, 1, (q, 1, 1, 1)))
+    rho, ux, uy, uz, th = lat.moments(f)
+    ref = np.array([rho.sum(), (rho * ux).sum(), (rho * uy).sum(), (rho * uz).sum(),
+                    (rho * (ux * ux + uy * uy + uz * uz + 3 * th)).sum()])
+    assert min(abs(ref[1] - ref[2]), abs(ref[2] - ref[3]), abs(ref[1] - ref[3])) > 1e-2 * ref[0]
+    got = lat.conserved(f)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * ref[0], (got, ref)
+
+
 # --------------------------------------------------------------------------
 # Mutants of the 3D code: each must fail at least one pin above.
 # --------------------------------------------------------------------------
@@ -130,6 +145,10 @@ MUTANTS_3D = [
     ("energy drops c_z^2", "en = en + (cx * cx + cy * cy + cz * cz) * fv;", "en = en + (cx * cx + cy * cy) * fv;"),
     ("population index transposed", "fi[p] = fsrc[p * vol + ((long)pz * ny + py) * nx + px];",
      "fi[p] = fsrc[((c * q1 + b) * q1 + a) * vol + ((long)pz * ny + py) * nx + px];"),
+    ("conserved y and z momentum swapped", "neu_add(&s[2], &c[2], cy * fv);\n                    neu_add(&s[3], &c[3], cz * fv);",
+     "neu_add(&s[2], &c[2], cz * fv);\n                    neu_add(&s[3], &c[3], cy * fv);"),
+    ("conserved energy drops c_z^2", "neu_add(&s[4], &c[4], (cx * cx + cy * cy + cz * cz) * fv);",
+     "neu_add(&s[4], &c[4], (cx * cx + cy * cy) * fv);"),
 ]
 
 
@@ -140,7 +159,8 @@ def _battery3():
                      ("reduction x", lambda: test_isothermal_3d_uniform_along_one_axis_is_the_2d_model("x")),
                      ("conservation", test_collision_conserves_and_equilibrium_is_fixed_point),
                      ("streaming", test_pure_streaming_moves_each_population_by_its_velocity),
-                     ("sound", test_adiabatic_sound_wave_travels_at_sqrt_gamma_theta)):
+                     ("sound", test_adiabatic_sound_wave_travels_at_sqrt_gamma_theta),
+                     ("conserved sums", test_conserved_sums_equal_sums_of_the_node_moments)):
         try:
             fn()
         except Exception:

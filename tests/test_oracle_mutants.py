@@ -48,6 +48,11 @@ MUTANTS = [
     ("vandermonde power off by one", "for (int e = 0; e < n; ++e) p = p * v[k];",
      "for (int e = 0; e <= n; ++e) p = p * v[k];"),
     ("elimination skips a row", "if (r == col) continue;", "if (r <= col) continue;"),
+    ("conserved momentum components swapped",
+     "neu_add(&s[1], &c[1], vx * fv);\n            neu_add(&s[2], &c[2], vy * fv);",
+     "neu_add(&s[1], &c[1], vy * fv);\n            neu_add(&s[2], &c[2], vx * fv);"),
+    ("conserved energy drops vy^2", "neu_add(&s[3], &c[3], (vx * vx + vy * vy) * fv);",
+     "neu_add(&s[3], &c[3], (vx * vx) * fv);"),
 ]
 
 
@@ -109,6 +114,11 @@ def _battery():
     nu = (1 / 1.3 - 0.5)
     ok = amps[0] > 0 and amps[1] > 0 and abs(-math.log(amps[1] / amps[0]) / (k * k * 40) / nu - 1) < 0.02
     check("shear decay", ok)
+    # global sums against the fields of the node moments (reading R3)
+    fr = rng.uniform(0.2, 1.8, lat.shape) * (1.0 + 0.5 * rng.uniform(0, 1, (lat.q, 1, 1)))
+    rho, ux, uy, th = lat.moments(fr)
+    ref = np.array([rho.sum(), (rho * ux).sum(), (rho * uy).sum(), (rho * (ux * ux + uy * uy + 2 * th)).sum()])
+    check("conserved sums", np.max(np.abs(lat.conserved(fr) - ref)) <= 1e-12 * ref[0])
     return fails
 
 

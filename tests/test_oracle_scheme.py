@@ -133,3 +133,38 @@ def test_init_reproduces_fields():
     r, a, b, t = lat.moments(f)
     for x, y in ((r, rho), (a, ux), (b, uy), (t, th)):
         assert np.max(np.abs(x - y)) < 1e-14
+
+
+@pytest.mark.parametrize("dim,nx,ny", [(2, 11, 7), (1, 23, 1)])
+def test_conserved_sums_equal_sums_of_the_node_moments(dim, nx, ny):
+    """orc_conserved against the fields of orc_moments (reading R3:
+    rho = sum f, rho u = sum v f, d rho theta = sum |v - u|^2 f, so that
+    sum |v|^2 f = rho (|u|^2 + d theta)) on a random, far-from-equilibrium
+    state whose momentum components differ: a swapped or rescaled component or
+    a dropped energy term cannot match."""
+    lat = O.Lattice(dim, V5, 1.3, nx, ny, theta0=1.0)
+    rng = np.random.default_rng(31)
+    f = rng.uniform(0.2, 1.8, lat.shape) * (1.0 + 0.5 * rng.uniform(0, 1, (lat.q, 1, 1)))
+    rho, ux, uy, th = lat.moments(f)
+    ref = np.array([rho.sum(), (rho * ux).sum(), (rho * uy).sum(),
+                    (rho * (ux * ux + uy * uy + dim * th)).sum()])
+    got = lat.conserved(f)
+    assert abs(ref[1]) > 1e-2 * ref[0]
+    if dim == 2:
+        assert abs(ref[1] - ref[2]) > 1e-2 * ref[0]
+    assert np.max(np.abs(got - ref)) <= 1e-12 * ref[0], (got, ref)
+
+
+def test_conserved_sums_of_an_equilibrium_are_the_field_integrals():
+    """For f = f^eq(rho, u, theta) the moment identity of Eq. (eq:rdr) (mu_0..mu_2
+    reproduced) makes the sums exactly sum rho, sum rho u and
+    sum rho (|u|^2 + 2 theta) of the fields that built it."""
+    lat = O.Lattice(2, V5, 1.3, 13, 9, theta0=1.0)
+    rng = np.random.default_rng(32)
+    rho = 1 + 0.1 * rng.uniform(-1, 1, (9, 13))
+    ux = 0.08 * rng.uniform(-0.2, 1, (9, 13))
+    uy = 0.08 * rng.uniform(-1, 0.3, (9, 13))
+    th = 1 + 0.1 * rng.uniform(-1, 1, (9, 13))
+    got = lat.conserved(lat.init(rho, ux, uy, th))
+    ref = np.array([rho.sum(), (rho * ux).sum(), (rho * uy).sum(), (rho * (ux * ux + uy * uy + 2 * th)).sum()])
+    assert np.max(np.abs(got - ref)) <= 1e-12 * ref[0], (got, ref)
