@@ -53,7 +53,7 @@ namespace tc {
 
 constexpr int kC = 64;
 constexpr int kTile = 128;
-constexpr unsigned long long kTimeoutNs = 2000000000ull;  // 2 s per wait
+constexpr unsigned long long kTimeoutNs = 2000000000ull;  // 2 s: default wait budget and the drain bound
 
 __device__ __forceinline__ uint32_t s2u(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -82,26 +82,43 @@ __device__ __forceinline__ void bar_arrive(uint32_t bar) {
 // One potentially blocking test of the phase: the thread may be suspended (up
 // to the hint, 10 ms) until the phase completes, so waiting warps do not take
 // issue slots from the warps that work.
-__device__ __forceinline__ bool bar_try(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ bool bar_try(uint32_t bar, uint32_t parity, uint32_t hint_ns = 10000000u) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(done)
-        : "r"(bar), "r"(parity), "r"(10000000u)
+        : "r"(bar), "r"(parity), "r"(hint_ns)
         : "memory");
     return done != 0;
 }
-// Wait for the phase of parity `parity` of `bar`; false on a timeout (which sets
-// *abort) or when another role has already set *abort.
-__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+// Budgets below this are checked on every poll with non-blocking tests (a
+// suspended try_wait may outlast a short hint); the default budget takes the
+// suspending path.
+constexpr unsigned long long kShortBudgetNs = 10000000ull;
+__device__ __forceinline__ bool bar_test(uint32_t bar, uint32_t parity);
+// Wait for the phase of parity `parity` of `bar`; false once budget_ns have
+// passed (which sets *abort) or when another role has already set *abort.
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, volatile int* abort,
+                                         unsigned long long budget_ns) {
+    if (budget_ns < kShortBudgetNs) {
+        const uint64_t t0 = gtime();
+        for (;;) {
+            if (bar_test(bar, parity)) return true;
+            if (*abort) return false;
+            if (gtime() - t0 > budget_ns) {
+                *abort = 1;
+                return false;
+            }
+        }
+    }
     if (bar_try(bar, parity)) return true;
     const uint64_t t0 = gtime();
     for (;;) {
         if (bar_try(bar, parity)) return true;
         if (*abort) return false;
-        if (gtime() - t0 > kTimeoutNs) {
+        if (gtime() - t0 > budget_ns) {
             *abort = 1;
             return false;
         }
@@ -122,14 +139,16 @@ __device__ __forceinline__ bool bar_test(uint32_t bar, uint32_t parity) {
         : "memory");
     return done != 0;
 }
-__device__ __forceinline__ bool bar_spin(uint32_t bar, uint32_t parity, volatile int* abort) {
+__device__ __forceinline__ bool bar_spin(uint32_t bar, uint32_t parity, volatile int* abort,
+                                         unsigned long long budget_ns) {
     if (bar_test(bar, parity)) return true;
     const uint64_t t0 = gtime();
+    const uint32_t every = budget_ns < kShortBudgetNs ? 0u : 255u;   // short budgets: check every poll
     for (uint32_t i = 1;; ++i) {
         if (bar_test(bar, parity)) return true;
-        if ((i & 255) == 0) {
+        if ((i & every) == 0) {
             if (*abort) return false;
-            if (gtime() - t0 > kTimeoutNs) {
+            if (gtime() - t0 > budget_ns) {
                 *abort = 1;
                 return false;
             }
@@ -148,7 +167,8 @@ __device__ __forceinline__ int test_many(const uint32_t (&bars)[4], const uint32
     while (c < n && d[c]) ++c;
     return c;
 }
-// The same without looking at *abort (used to drain issued MMAs before freeing TMEM).
+// The same without looking at *abort, bounded by the fixed kTimeoutNs whatever
+// the wait budget (used to drain issued MMAs before freeing TMEM).
 __device__ __forceinline__ bool bar_wait_drain(uint32_t bar, uint32_t parity) {
     const uint64_t t0 = gtime();
     for (;;) {
@@ -315,7 +335,7 @@ template <int N, int MODE>
 __global__ void __launch_bounds__(kRingThreads, 1)
 k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const __nv_bfloat16* __restrict__ X,
             const __nv_bfloat16* __restrict__ Wk, const float* __restrict__ bias,
-            const __nv_bfloat16* __restrict__ mask, void* __restrict__ Yv, int relu, unsigned* __restrict__ err) {
+            const __nv_bfloat16* __restrict__ mask, void* __restrict__ Yv, int relu, const TcErr err) {
     static_assert((N == 64 && MODE < 2) || (N == 16 && MODE == 2), "ring conv shapes");
     extern __shared__ unsigned char dsm_raw[];
     const uint32_t raw = s2u(dsm_raw);
@@ -376,8 +396,8 @@ k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const 
                 if ((int)(e % kLoaders) != warp) continue;
                 const int slot = (int)(e % kRing);
                 const uint32_t par = ((e / kRing) & 1) ^ 1;
-                if (!bar_wait(bar(kBarEmpty + slot), par, abortp) ||
-                    !bar_wait(bar(kBarEmpty + kRing + slot), par, abortp)) {
+                if (!bar_wait(bar(kBarEmpty + slot), par, abortp, err.wait_ns) ||
+                    !bar_wait(bar(kBarEmpty + kRing + slot), par, abortp, err.wait_ns)) {
                     ok = false;
                     break;
                 }
@@ -440,7 +460,7 @@ k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const 
                             }
                             const int c = test_many(b, par, n);
                             if (c) ready += c;
-                            else ok = bar_spin(b[0], par[0], abortp) && (++ready, true);
+                            else ok = bar_spin(b[0], par[0], abortp, err.wait_ns) && (++ready, true);
                         }
                         if (tcount >= (uint32_t)kAcc) {
                             // this issuer's tiles are tcount = q, q + 2, ...; tile u frees
@@ -459,7 +479,7 @@ k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const 
                                 }
                                 const int c = test_many(b, par, n);
                                 if (c) freed += 2 * c;
-                                else ok = bar_spin(b[0], par[0], abortp) && (freed += 2, true);
+                                else ok = bar_spin(b[0], par[0], abortp, err.wait_ns) && (freed += 2, true);
                             }
                         }
                         if (!ok) break;
@@ -508,7 +528,7 @@ k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const 
             const Strip s = strip_at(t, t_end, H, tiles_x);
             for (int i = 0; i < s.n; ++i) {
                 const uint32_t acc = tcount % kAcc;
-                if (!bar_wait(bar(kBarTFull + acc), (tcount / kAcc) & 1, abortp)) {
+                if (!bar_wait(bar(kBarTFull + acc), (tcount / kAcc) & 1, abortp, err.wait_ns)) {
                     ok = false;
                     break;
                 }
@@ -547,7 +567,7 @@ k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const 
     }
     __syncthreads();
     if (tid == 0 && *abortp) {
-        atomicOr(err, 1u);
+        atomicOr(err.flag, 1u);
         // TMA copies the loaders issued may not have been waited for: give them
         // time to land (they are plain copies) before the shared memory is released
         const uint64_t t0 = gtime();
@@ -579,7 +599,7 @@ constexpr uint32_t kInTmemCols = 64;
 
 __global__ void __launch_bounds__(kInThreads)
 k_conv_in_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ Win,
-             const float* __restrict__ bias, __nv_bfloat16* __restrict__ Y, int relu, unsigned* __restrict__ err) {
+             const float* __restrict__ bias, __nv_bfloat16* __restrict__ Y, int relu, const TcErr err) {
     extern __shared__ unsigned char dsm_raw[];
     const uint32_t raw = s2u(dsm_raw);
     const uint32_t pad = (128 - (raw & 127)) & 127;
@@ -651,7 +671,7 @@ k_conv_in_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __n
             issued = true;
         }
         if (t + (int)gridDim.x < ntiles) gather(t + gridDim.x, g);
-        if (!bar_wait(bar_mma, phase, abortp)) *abortp = 1;
+        if (!bar_wait(bar_mma, phase, abortp, err.wait_ns)) *abortp = 1;
         phase ^= 1;
         __syncthreads();
         if (*abortp) break;
@@ -670,7 +690,7 @@ k_conv_in_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __n
         if (!bar_wait_drain(bar_drain, 0)) *abortp = 1;
     }
     __syncthreads();
-    if (tid == 0 && *abortp) atomicOr(err, 1u);
+    if (tid == 0 && *abortp) atomicOr(err.flag, 1u);
     if (warp == 0) {
         tc_after_sync();
         tmem_free(tmem, kInTmemCols);
@@ -723,7 +743,7 @@ __device__ __forceinline__ void mma_wg(uint32_t tmem_d, uint64_t a, uint64_t b, 
 
 __global__ void __launch_bounds__(kWgThreads, 1)
 k_wgrad_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ dY,
-           float* __restrict__ partial, float* __restrict__ partial_b, unsigned* __restrict__ err) {
+           float* __restrict__ partial, float* __restrict__ partial_b, const TcErr err) {
     extern __shared__ unsigned char dsm_raw[];
     const uint32_t raw = s2u(dsm_raw);
     const uint32_t pad = (128 - (raw & 127)) & 127;
@@ -801,7 +821,7 @@ k_wgrad_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __nv_
         // the stage of tile it - 1 takes tile it + kWgStages - 1 once that tile's MMAs are done
         const int kf = (it + kWgStages - 1) % kWgStages;
         if (it >= 1) {
-            if (!bar_wait(bar0 + 8 * kf, (phase >> kf) & 1u, abortp)) *abortp = 1;
+            if (!bar_wait(bar0 + 8 * kf, (phase >> kf) & 1u, abortp, err.wait_ns)) *abortp = 1;
             phase ^= 1u << kf;
         }
         const int tf = t + (kWgStages - 1) * (int)gridDim.x;
@@ -826,7 +846,7 @@ k_wgrad_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __nv_
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     if (it > 0 && !*abortp) {
         const int kl = (it - 1) % kWgStages;
-        if (!bar_wait(bar0 + 8 * kl, (phase >> kl) & 1u, abortp)) *abortp = 1;
+        if (!bar_wait(bar0 + 8 * kl, (phase >> kl) & 1u, abortp, err.wait_ns)) *abortp = 1;
     }
     __syncthreads();
     tc_after_sync();
@@ -866,7 +886,7 @@ k_wgrad_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __nv_
         if (!bar_wait_drain(bar_drain, 0)) *abortp = 1;
     }
     __syncthreads();
-    if (tid == 0 && *abortp) atomicOr(err, 1u);
+    if (tid == 0 && *abortp) atomicOr(err.flag, 1u);
     if (warp == 0) {
         tc_after_sync();
         tmem_free(tmem, kWgTmemCols);
@@ -889,7 +909,7 @@ constexpr uint32_t kWiTmemCols = 64;
 
 __global__ void __launch_bounds__(kWgThreads, 1)
 k_wgrad_in_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ dY,
-              float* __restrict__ partial, float* __restrict__ partial_b, unsigned* __restrict__ err) {
+              float* __restrict__ partial, float* __restrict__ partial_b, const TcErr err) {
     extern __shared__ unsigned char dsm_raw[];
     const uint32_t raw = s2u(dsm_raw);
     const uint32_t pad = (128 - (raw & 127)) & 127;
@@ -968,7 +988,7 @@ k_wgrad_in_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __
         }
         const int kf = (it + kWgStages - 1) % kWgStages;
         if (it >= 1) {
-            if (!bar_wait(bar0 + 8 * kf, (phase >> kf) & 1u, abortp)) *abortp = 1;
+            if (!bar_wait(bar0 + 8 * kf, (phase >> kf) & 1u, abortp, err.wait_ns)) *abortp = 1;
             phase ^= 1u << kf;
         }
         const int tf = t + (kWgStages - 1) * (int)gridDim.x;
@@ -993,7 +1013,7 @@ k_wgrad_in_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     if (it > 0 && !*abortp) {
         const int kl = (it - 1) % kWgStages;
-        if (!bar_wait(bar0 + 8 * kl, (phase >> kl) & 1u, abortp)) *abortp = 1;
+        if (!bar_wait(bar0 + 8 * kl, (phase >> kl) & 1u, abortp, err.wait_ns)) *abortp = 1;
     }
     __syncthreads();
     tc_after_sync();
@@ -1027,7 +1047,7 @@ k_wgrad_in_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __
         if (!bar_wait_drain(bar_drain, 0)) *abortp = 1;
     }
     __syncthreads();
-    if (tid == 0 && *abortp) atomicOr(err, 1u);
+    if (tid == 0 && *abortp) atomicOr(err.flag, 1u);
     if (warp == 0) {
         tc_after_sync();
         tmem_free(tmem, kWiTmemCols);
@@ -1102,7 +1122,7 @@ static cudaError_t encode_act_map(CUtensorMap* map, const void* X, int B, int H,
 
 template <int N, int MODE>
 static cudaError_t launch_ring(int B, int H, int W, const void* X, const void* Wk, const float* bias,
-                               const void* mask, void* Y, int relu, unsigned* err, cudaStream_t s) {
+                               const void* mask, void* Y, int relu, TcErr err, cudaStream_t s) {
     if (W % tc::kTile || H < 1 || B < 1) return cudaErrorInvalidValue;
     CUtensorMap map;
     cudaError_t em = encode_act_map(&map, X, B, H, W);
@@ -1123,18 +1143,18 @@ static cudaError_t launch_ring(int B, int H, int W, const void* X, const void* W
 }
 
 cudaError_t cnn_conv64_tc(int B, int H, int W, const void* X, const void* Wk, const float* bias, const void* mask,
-                          void* Y, int mode, int relu, unsigned* err, cudaStream_t s) {
+                          void* Y, int mode, int relu, TcErr err, cudaStream_t s) {
     if (mode == 0) return launch_ring<64, 0>(B, H, W, X, Wk, bias, mask, Y, relu, err, s);
     return launch_ring<64, 1>(B, H, W, X, Wk, bias, mask, Y, relu, err, s);
 }
 
 cudaError_t cnn_conv_out_tc(int B, int H, int W, const void* X, const void* Wo, const float* bias, float* Y,
-                            unsigned* err, cudaStream_t s) {
+                            TcErr err, cudaStream_t s) {
     return launch_ring<16, 2>(B, H, W, X, Wo, bias, nullptr, Y, 0, err, s);
 }
 
 cudaError_t cnn_conv_in_tc(int B, int H, int W, const void* X, const void* Win, const float* bias, void* Y, int relu,
-                           unsigned* err, cudaStream_t s) {
+                           TcErr err, cudaStream_t s) {
     if (W % tc::kTile || H < 1 || B < 1) return cudaErrorInvalidValue;
     static bool attr = false;
     if (!attr) {
@@ -1151,7 +1171,7 @@ cudaError_t cnn_conv_in_tc(int B, int H, int W, const void* X, const void* Win, 
 }
 
 cudaError_t cnn_conv64_wgrad_tc(int B, int H, int W, const void* X, const void* dY, float* partial, float* partial_b,
-                                float* dW, float* db, unsigned* err, cudaStream_t s) {
+                                float* dW, float* db, TcErr err, cudaStream_t s) {
     if (W % tc::kTile || H < 1 || B < 1) return cudaErrorInvalidValue;
     static bool attr = false;
     if (!attr) {
@@ -1171,7 +1191,7 @@ cudaError_t cnn_conv64_wgrad_tc(int B, int H, int W, const void* X, const void* 
 }
 
 cudaError_t cnn_conv_in_wgrad_tc(int B, int H, int W, const void* X, const void* dY, float* partial, float* partial_b,
-                                 float* dW, float* db, unsigned* err, cudaStream_t s) {
+                                 float* dW, float* db, TcErr err, cudaStream_t s) {
     if (W % tc::kTile || H < 1 || B < 1) return cudaErrorInvalidValue;
     static bool attr = false;
     if (!attr) {

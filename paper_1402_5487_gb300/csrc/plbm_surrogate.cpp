@@ -43,6 +43,7 @@ struct Sur {
     void* win = nullptr;            // first layer (4 -> 64) for tcgen05: bf16 [6][64][8]
     void* wout = nullptr;           // last layer (64 -> 4) for tcgen05: bf16 [9][16][64]
     unsigned* derr = nullptr;       // device flag: a bounded wait in a tensor-core kernel ran out
+    unsigned long long wait_ns = 2000000000ull;  // budget of each of those waits
     int use_tc = 1;                 // forward convolutions and 64 -> 64 backward data: 1 tcgen05, 0 mma.sync / CUDA cores
     int conserve = 0;               // 1: project predicted fields onto the old global sums before the drift gate
     float mean_penalty = 0.0f;      // weight of the lattice-mean error term of the training loss
@@ -142,7 +143,7 @@ plbm_status refresh_weights(Sur* s) {
 plbm_status forward(Sur* s, int B, const void* x) {
     const int H = s->H, W = s->W;
     if (s->use_tc) {
-        SCK(plbm::cnn_conv_in_tc(B, H, W, x, s->win, s->p + s->boff[0], s->act[0], 1, s->derr, s->stream));
+        SCK(plbm::cnn_conv_in_tc(B, H, W, x, s->win, s->p + s->boff[0], s->act[0], 1, plbm::TcErr{s->derr, s->wait_ns}, s->stream));
     } else {
         SCK(plbm::cnn_conv_thin_fwd(4, 64, 0, 0, B, H, W, x, s->pr + s->woff[0], s->p + s->boff[0], nullptr,
                                     s->act[0], 0, 1, s->stream));
@@ -150,7 +151,7 @@ plbm_status forward(Sur* s, int B, const void* x) {
     for (int l = 1; l <= 4; ++l) {
         if (s->use_tc) {
             SCK(plbm::cnn_conv64_tc(B, H, W, s->act[l - 1], wtc_fwd(s, l), s->p + s->boff[l], nullptr, s->act[l], 0, 1,
-                                    s->derr, s->stream));
+                                    plbm::TcErr{s->derr, s->wait_ns}, s->stream));
         } else {
             const char* wb = static_cast<const char*>(s->wbf) + (size_t)(l - 1) * 9 * 64 * 64 * 2;
             SCK(plbm::cnn_conv64_fwd(B, H, W, s->act[l - 1], wb, s->p + s->boff[l], nullptr, s->act[l], 0, 1,
@@ -159,7 +160,7 @@ plbm_status forward(Sur* s, int B, const void* x) {
     }
     if (s->use_tc) {
         SCK(plbm::cnn_conv_out_tc(B, H, W, s->act[4], s->wout, s->p + s->boff[5], static_cast<float*>(s->act[5]),
-                                  s->derr, s->stream));
+                                  plbm::TcErr{s->derr, s->wait_ns}, s->stream));
     } else {
         SCK(plbm::cnn_conv_thin_fwd(64, 4, 0, 1, B, H, W, s->act[4], s->pr + s->woff[5], s->p + s->boff[5], nullptr,
                                     s->act[5], 0, 0, s->stream));
@@ -179,13 +180,13 @@ plbm_status backward(Sur* s, int B, const void* x, const float* dout) {
     for (int l = 4; l >= 1; --l) {
         if (s->use_tc)
             SCK(plbm::cnn_conv64_wgrad_tc(B, H, W, s->act[l - 1], s->dz[l], s->part, s->part_b, s->g + s->woff[l],
-                                          s->g + s->boff[l], s->derr, s->stream));
+                                          s->g + s->boff[l], plbm::TcErr{s->derr, s->wait_ns}, s->stream));
         else
             SCK(plbm::cnn_conv64_wgrad(B, H, W, s->act[l - 1], s->dz[l], s->part, s->part_b, s->g + s->woff[l],
                                        s->g + s->boff[l], s->stream));
         if (s->use_tc) {
             SCK(plbm::cnn_conv64_tc(B, H, W, s->dz[l], wtc_bwd(s, l), nullptr, s->act[l - 1], s->dz[l - 1], 1, 0,
-                                    s->derr, s->stream));
+                                    plbm::TcErr{s->derr, s->wait_ns}, s->stream));
         } else {
             const char* wf = static_cast<const char*>(s->wflip) + (size_t)(l - 1) * 9 * 64 * 64 * 2;
             SCK(plbm::cnn_conv64_fwd(B, H, W, s->dz[l], wf, nullptr, s->act[l - 1], s->dz[l - 1], 1, 0, s->stream));
@@ -193,7 +194,7 @@ plbm_status backward(Sur* s, int B, const void* x, const float* dout) {
     }
     if (s->use_tc)
         SCK(plbm::cnn_conv_in_wgrad_tc(B, H, W, x, s->dz[0], s->part, s->part_b, s->g + s->woff[0],
-                                       s->g + s->boff[0], s->derr, s->stream));
+                                       s->g + s->boff[0], plbm::TcErr{s->derr, s->wait_ns}, s->stream));
     else
         SCK(plbm::cnn_conv_thin_wgrad(4, 64, 0, 0, B, H, W, x, s->dz[0], s->part, s->part_b, s->g + s->woff[0],
                                       s->g + s->boff[0], s->stream));
@@ -357,6 +358,10 @@ plbm_status plbm_sur_set_option(plbm_surrogate h, int option, int value) {
         s->conserve = value;
         return PLBM_OK;
     }
+    if (option == PLBM_SUR_OPT_WAIT_NS && value >= 1) {
+        s->wait_ns = (unsigned long long)value;
+        return PLBM_OK;
+    }
     serr(s, "unknown option %d or value %d", option, value);
     return PLBM_E_ARG;
 }
@@ -378,7 +383,9 @@ plbm_status plbm_sur_check(plbm_surrogate h) {
     SCK(cudaMemcpyAsync(&e, s->derr, sizeof e, cudaMemcpyDeviceToHost, s->stream));
     SCK(cudaStreamSynchronize(s->stream));
     if (e) {
-        serr(s, "a tensor-core kernel gave up waiting for its MMAs");
+        SCK(cudaMemsetAsync(s->derr, 0, sizeof e, s->stream));  // reported once
+        SCK(cudaStreamSynchronize(s->stream));
+        serr(s, "a bounded wait of a tensor-core kernel ran out: the pass was abandoned, its results are invalid");
         return PLBM_E_TIMEOUT;
     }
     return PLBM_OK;

@@ -143,6 +143,10 @@ class Surrogate:
         before the drift gate of advance (PLBM_SUR_OPT_CONSERVE)."""
         self._ok(plbm.lib().plbm_sur_set_option(self.h, 2, 1 if on else 0))
 
+    def set_wait_ns(self, ns: int):
+        """Budget of each bounded wait of the tcgen05 kernels (PLBM_SUR_OPT_WAIT_NS)."""
+        self._ok(plbm.lib().plbm_sur_set_option(self.h, 3, int(ns)))
+
     def set_mean_penalty(self, lam: float):
         """Weight of the lattice-mean error term of the training loss."""
         self._ok(plbm.lib().plbm_sur_set_mean_penalty(self.h, float(lam)))

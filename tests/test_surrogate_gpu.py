@@ -312,3 +312,31 @@ def test_weight_gradients_over_many_tiles_per_cta_match_oracle():
         assert rel(grads[0][0], dW) < 1e-3, (tc, 0)
         assert rel(grads[0][1], db) < 1e-3, (tc, 0)
     net.close()
+
+
+def test_a_wait_that_runs_out_is_reported_and_the_next_pass_is_correct():
+    # With a wait budget of a few nanoseconds every tcgen05 kernel of the pass
+    # gives up at its first wait: it stops issuing, drains the MMAs it issued,
+    # frees its tensor memory and sets the flag, which plbm_sur_check reports as
+    # PLBM_E_TIMEOUT once.  With the default budget the same network then gives
+    # the results of an undisturbed pass (nothing was left behind).
+    import torch
+    net = SG.Surrogate(1, H=3, W=128, seed=5)
+    g = torch.Generator().manual_seed(9)
+    x = torch.randn((1, 3, 128, 4), generator=g).to(torch.bfloat16).cuda()
+    dout = (0.01 * torch.randn((1, 3, 128, 4), generator=g)).cuda()
+    ref_out = net.forward(x, 1).clone()
+    ref_grads = net.backward(x, dout, 1).astype(np.float64)
+    assert net.check() == plbm.PLBM_OK
+    net.set_wait_ns(4)
+    net.forward(x, 1)
+    net.backward(x, dout, 1)
+    assert net.check() == plbm.PLBM_E_TIMEOUT
+    assert net.check() == plbm.PLBM_OK      # reported once
+    net.set_wait_ns(2_000_000_000)
+    out = net.forward(x, 1).clone()
+    grads = net.backward(x, dout, 1).astype(np.float64)
+    assert net.check() == plbm.PLBM_OK
+    assert torch.equal(out, ref_out)
+    assert rel(grads, ref_grads) <= 1e-6
+    net.close()
