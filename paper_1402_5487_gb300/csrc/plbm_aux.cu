@@ -4,6 +4,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include "plbm.h"
 #include "plbm_device.cuh"
 
 namespace plbm {
@@ -19,6 +20,40 @@ cudaError_t launch_batch_bf16(const PairParams*, int, int, int, int, int, const 
 cudaError_t batch_occupancy_f32(int, int*);
 cudaError_t batch_occupancy_f16(int, int*);
 cudaError_t batch_occupancy_bf16(int, int*);
+
+cudaError_t launch_batch_node_f64(int, const LatticeParams*, const NodeSpan*, int, int, int, const unsigned short*,
+                                  cudaStream_t);
+cudaError_t launch_batch_node_f32(int, const LatticeParams*, const NodeSpan*, int, int, int, const unsigned short*,
+                                  cudaStream_t);
+cudaError_t launch_batch_node_f16(int, const LatticeParams*, const NodeSpan*, int, int, int, const unsigned short*,
+                                  cudaStream_t);
+cudaError_t launch_batch_node_bf16(int, const LatticeParams*, const NodeSpan*, int, int, int, const unsigned short*,
+                                   cudaStream_t);
+cudaError_t batch_node_occupancy_f64(int, int*);
+cudaError_t batch_node_occupancy_f32(int, int*);
+cudaError_t batch_node_occupancy_f16(int, int*);
+cudaError_t batch_node_occupancy_bf16(int, int*);
+
+cudaError_t launch_batch_node(int prec, int q1, const LatticeParams* inst, const NodeSpan* span, int total_tiles,
+                              int ctas, int parity, const unsigned short* tile_inst, cudaStream_t stream) {
+    switch (prec) {
+        case kF64: return launch_batch_node_f64(q1, inst, span, total_tiles, ctas, parity, tile_inst, stream);
+        case kF32: return launch_batch_node_f32(q1, inst, span, total_tiles, ctas, parity, tile_inst, stream);
+        case kF16Dev: return launch_batch_node_f16(q1, inst, span, total_tiles, ctas, parity, tile_inst, stream);
+        case kBF16Dev: return launch_batch_node_bf16(q1, inst, span, total_tiles, ctas, parity, tile_inst, stream);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t batch_node_occupancy(int prec, int q1, int* blocks_per_sm) {
+    switch (prec) {
+        case kF64: return batch_node_occupancy_f64(q1, blocks_per_sm);
+        case kF32: return batch_node_occupancy_f32(q1, blocks_per_sm);
+        case kF16Dev: return batch_node_occupancy_f16(q1, blocks_per_sm);
+        case kBF16Dev: return batch_node_occupancy_bf16(q1, blocks_per_sm);
+    }
+    return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_batch(int prec, const PairParams* inst, int ninst, int total_tiles, int block_x,
                          int ctas, int parity, const unsigned short* tile_inst, cudaStream_t stream) {
@@ -526,6 +561,31 @@ __global__ void k_set_pop(const __grid_constant__ LatticeParams P, const double*
         case kBF16Dev: { using S = __nv_bfloat16; CALL; break; }         \
         default: return cudaErrorInvalidValue;                           \
     }
+
+// Initial fields are checked on the device before the state is built from them:
+// a non-finite value sets PLBM_STATUS_NONFINITE, rho <= 0 PLBM_STATUS_RHO_NONPOS,
+// theta <= 0 PLBM_STATUS_THETA_NONPOS.  One atomic per warp that found any.
+__global__ void k_check_fields(FieldSet F, long long n, unsigned* __restrict__ status) {
+    unsigned bits = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        for (int k = 0; k < F.count; ++k) {
+            const double v = F.field[k][i];
+            if (!isfinite(v)) bits |= PLBM_STATUS_NONFINITE;
+            else if (k == F.rho && !(v > 0.0)) bits |= PLBM_STATUS_RHO_NONPOS;
+            else if (k == F.theta && !(v > 0.0)) bits |= PLBM_STATUS_THETA_NONPOS;
+        }
+    }
+    bits = __reduce_or_sync(0xffffffffu, bits);
+    if ((threadIdx.x & 31) == 0 && bits) atomicOr(status, bits);
+}
+
+cudaError_t launch_check_fields(const FieldSet& F, long long n, unsigned* status, cudaStream_t stream) {
+    if (n <= 0 || F.count <= 0) return cudaSuccess;
+    const long long blocks = (n + 255) / 256;
+    k_check_fields<<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, stream>>>(F, n, status);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_init(int prec, const LatticeParams& P, const double* rho, const double* ux,
                         const double* uy, const double* theta, void* f, cudaStream_t stream, int y0, int y1) {
