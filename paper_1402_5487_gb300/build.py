@@ -29,6 +29,7 @@ SOURCES = [
     "plbm_step3.cu",
     "plbm_step_bf16.cu",
     "plbm_noalloc.cu",
+    "plbm_slabs.cu",
     "plbm_cnn.cu",
     "plbm_cnn_tc.cu",
     "plbm_ce.cu",
