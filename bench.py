@@ -7,7 +7,8 @@ population arrays (2 x 839 MB) are far larger than the 129 MB L2, so every
 timed step streams its inputs from HBM.
 
 Prints ONE JSON line (rank 0).  ``value`` is whole-job MLUPS (node updates per
-microsecond summed over ranks) measured with CUDA events on the solver's stream;
+microsecond summed over ranks) measured with CUDA events on the solver's stream,
+the median of five timed runs of --steps steps each (all five are reported);
 ``e2e`` is the same metric through the public API with host (pinned) buffers:
 plbm_init from host fields, K steps, plbm_moments back to host.
 
@@ -37,6 +38,7 @@ from paper_1402_5487_gb300 import inputs as I  # noqa: E402
 
 V5 = I.SET_013
 OMEGA = 1.3
+REPEATS = 5            # timed runs of --steps steps in the bench line; the median is reported
 THETA0 = 1.0
 ELEM = {"f64": 8, "f32": 4, "f16dev": 2, "bf16dev": 2}
 
@@ -204,6 +206,29 @@ def run_variant(torch, L, prec, steps, warmup, barrier, dim=2, v=V5, bc="periodi
     return {"mlups": nx * ny * steps / t / 1e6, "ms_per_step": t / steps * 1e3,
             "gbs_algorithmic": 2 * q * ELEM[prec] * nx * ny * steps / t / 1e9,
             "status": "ok" if st == 0 else "diverged"}
+
+
+def run_slabs(torch, L, nslabs, steps, warmup, prec="f32"):
+    """KH L x L decomposed into nslabs y-slabs on this GPU (halo exchange + slab steps),
+    against the undivided lattice: the cost of the exchange."""
+    from paper_1402_5487_gb300 import plbm
+    st = torch.cuda.Stream()
+    sl = plbm.Slabs(V5, OMEGA, L, L, nslabs, theta0=THETA0, prec=prec, stream=st)
+    sl.init(*I.kh_fields(L))
+    sl.step(warmup)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    sl.step(steps)
+    e1.record(st)
+    e1.synchronize()
+    t = e0.elapsed_time(e1) * 1e-3
+    rows = [sl.slab(k)[2] for k in range(nslabs)]
+    sl.close()
+    return {"mlups": L * L * steps / t / 1e6, "ms_per_step": t / steps * 1e3, "slab_rows": rows,
+            "gbs_algorithmic": 2 * 25 * ELEM[prec] * L * L * steps / t / 1e9,
+            "launches_per_step": 1 + nslabs}
 
 
 def run_diag_overhead(torch, L, steps, every):
@@ -722,21 +747,29 @@ def main():
     solver.init(*fields)
     solver.step(args.warmup)
     st = solver.stream
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
     torch.cuda.synchronize()
     barrier()
     clocks.start()
     time.sleep(0.3)
-    e0.record(st)
-    solver.step(args.steps)
-    e1.record(st)
-    e1.synchronize()
-    torch.cuda.synchronize()
+    # REPEATS timed runs of exactly --steps steps each, every one bracketed by
+    # CUDA events on the solver's stream with a synchronisation and a barrier on
+    # both sides; the run of median duration is the reported one.
+    runs = []
+    for _ in range(REPEATS):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        barrier()
+        e0.record(st)
+        solver.step(args.steps)
+        e1.record(st)
+        e1.synchronize()
+        torch.cuda.synchronize()
+        barrier()
+        runs.append(e0.elapsed_time(e1) * 1e-3)
     clock_info = clocks.stop()
-    barrier()
-    t = e0.elapsed_time(e1) * 1e-3
+    t = statistics.median(runs)
     healthy = solver.check() == 0
     solver.close()
     t_max, value = replica_throughput(torch, t, L * L * args.steps, dist)
@@ -757,6 +790,9 @@ def main():
                 continue
             variants["kh%d_%s" % (L, prec)] = run_variant(torch, L, prec, 200, 10, lambda: None)
         variants["kh2048_f32_diagnostics_every_10"] = run_diag_overhead(torch, 2048, 400, 10)
+        # odd side: the plain layout, one node per thread (no row pairs)
+        variants["kh%d_f32_plain_layout" % (L - 1)] = run_variant(torch, L - 1, "f32", 200, 10, lambda: None)
+        variants["kh%d_f32_4slabs" % L] = run_slabs(torch, L, 4, 200, 10)
         variants["kh512_f32"] = run_variant(torch, 512, "f32", 1000, 50, lambda: None)
         variants["kh512_f64"] = run_variant(torch, 512, "f64", 200, 20, lambda: None)
         pf, pth = I.paper_kh_fields()
@@ -795,6 +831,9 @@ def main():
                              "peak_source": peak_kind + " (copy bandwidth, MEASURED_PEAKS.json hbm_gbs)",
                              "algorithmic_bytes_per_launch": alg_bytes,
                              "kernel": KERNEL_NAME[args.prec]},
+                "repeats": {"n": REPEATS, "reported": "median",
+                            "ms_per_step_each": [r / args.steps * 1e3 for r in runs],
+                            "spread": (max(runs) - min(runs)) / t},
                 "e2e": e2e, "gpu_launches": args.steps, "clocks": clock_info,
                 "cpu_baseline": cpu, "variants": variants}
         print(json.dumps(json_safe(line)))

@@ -71,6 +71,8 @@ typedef enum { PLBM_PERIODIC = 0, PLBM_FIXED_ENDS = 1 } plbm_bc;
 /* Descriptor flags. */
 #define PLBM_FLAG_ISOTHERMAL 0x1u      /* theta in f^eq held at theta0 (Eq. eq:1d3v models) */
 #define PLBM_FLAG_SKIP_ADMISSIBILITY 0x2u /* do not run the positivity gate at create */
+#define PLBM_FLAG_PLAIN_LAYOUT 0x4u    /* 2D: keep the plain layout [q][ny][pitch] (one node per
+                                          thread) where the row-paired one would be taken */
 
 typedef struct {
     int dim;                   /* 1, 2 or 3 */
@@ -176,7 +178,11 @@ plbm_status plbm_destroy(plbm_handle h);
  * (asynchronous); otherwise host memory, copied before return (through a
  * staging buffer of 4 nx ny doubles that the handle keeps after first use, in
  * row bands whose copies overlap the kernel).  Resets the step counter and
- * the status word. */
+ * the status word, then checks the fields on the device: a non-finite value,
+ * rho <= 0 or theta <= 0 sets the matching PLBM_STATUS_* bit.  With host
+ * pointers plbm_init then returns PLBM_E_ARG and leaves the handle
+ * uninitialised; with device pointers (asynchronous) the next plbm_check, or
+ * plbm_step with check_every > 0, returns PLBM_E_DIVERGED. */
 plbm_status plbm_init(plbm_handle h, const double *rho, const double *ux, const double *uy,
                       const double *theta, int on_device);
 
@@ -223,7 +229,7 @@ plbm_status plbm_conserved(plbm_handle h, double out[4]);
  * [nz][ny][nx]; populations [q][nz][ny][nx] with q = q1^3 and p = (a q1 + b) q1 + c
  * for the velocity (v[a], v[b], v[c]).  plbm_init, plbm_moments and
  * plbm_conserved return PLBM_E_ARG for 3D handles; these take their place.
- * on_device as in plbm_init / plbm_moments. */
+ * on_device as in plbm_init / plbm_moments, with the same check of the fields. */
 plbm_status plbm_init3(plbm_handle h, const double *rho, const double *ux, const double *uy, const double *uz,
                        const double *theta, int on_device);
 plbm_status plbm_moments3(plbm_handle h, double *rho, double *ux, double *uy, double *uz, double *theta,
@@ -238,6 +244,23 @@ plbm_status plbm_get_populations(plbm_handle h, double *f, int on_device);
 /* Replace the stored state with FP64 populations [q][ny][nx], rounded to the
  * handle's precision.  Resets the step counter to `step`. */
 plbm_status plbm_set_populations(plbm_handle h, const double *f, int on_device, int64_t step);
+
+/* Checkpoint and resume.  A checkpoint is a header (format version, ABI
+ * version, dim, q1, velocities, omega, theta0, sizes, storage precision and
+ * layout, a digest of the fixed-end states, step counter) followed by the
+ * stored population array byte for byte, in the handle's own precision and
+ * layout, so that resuming continues bit for bit as if uninterrupted.  A
+ * 64-bit FNV-1a checksum covers header and payload.
+ * plbm_checkpoint_bytes: size of a checkpoint of h (0 for NULL).
+ * plbm_checkpoint_save: writes it to host memory buf (bytes >= that size);
+ *   synchronous.  Errors: PLBM_E_ARG, PLBM_E_STATE (not initialised).
+ * plbm_checkpoint_load: replaces h's state and step counter from buf after
+ *   verifying the checksum and that the header describes h's lattice; the
+ *   status word is reset.  Synchronous.  PLBM_E_CHECKSUM for a corrupted or
+ *   truncated checkpoint or one of another lattice (nothing is changed). */
+size_t plbm_checkpoint_bytes(plbm_handle h);
+plbm_status plbm_checkpoint_save(plbm_handle h, void *buf, size_t bytes);
+plbm_status plbm_checkpoint_load(plbm_handle h, const void *buf, size_t bytes);
 
 /* Descriptor facts of a live handle. */
 plbm_status plbm_get_info(plbm_handle h, int *q, int *pitch, size_t *population_bytes);
@@ -268,13 +291,24 @@ typedef struct plbm_batch_s *plbm_batch;
 #define PLBM_BATCH_PER_INSTANCE 2
 #define PLBM_BATCH_PER_INSTANCE_GRAPH 3
 
-/* Create n instances from n descriptors (same precision and device; each 2D,
- * periodic, thermal, v = (0, a, -a, b, -b) with 0 < a != b, even ny, FP32/FP16/BF16
- * storage; each passes plbm_create's checks).  One device allocation holds all
- * instances; descs[i].workspace and .stream are ignored.  stream: cudaStream_t
- * for every launch (NULL: the batch creates its own non-blocking stream, as graph
- * capture cannot use the legacy default stream).  Synchronous. */
+/* Create n instances from n descriptors (one device; each a 2D lattice that
+ * passes plbm_create's checks, with 3 to 5 velocities per axis unless it takes
+ * the row-paired layout).  Instances may differ in size, velocity set, omega,
+ * theta0, storage precision, boundary and model (thermal or isothermal).  The
+ * batch advances them in groups, one persistent launch per group and step:
+ * instances in the row-paired layout (periodic thermal v = (0, a, -a, b, -b),
+ * even ny, FP32/FP16/BF16 storage) by the two-nodes-per-thread kernel, one group
+ * per precision; all others (odd ny, FP64 storage, isothermal models, other
+ * velocity sets) by a one-node-per-thread kernel, one group per (precision, q1).
+ * One device allocation holds all instances' populations; descs[i].workspace
+ * and .stream are ignored.  stream: cudaStream_t for every launch (NULL: the
+ * batch creates its own non-blocking stream, as graph capture cannot use the
+ * legacy default stream).  Synchronous. */
 plbm_status plbm_batch_create(const plbm_desc *descs, int n, void *stream, plbm_batch *out);
+
+/* How the batch splits: instances in the row-paired groups, instances in the
+ * plain-layout groups, and persistent launches per step (one per group). */
+plbm_status plbm_batch_groups(plbm_batch b, int *paired_instances, int *plain_instances, int *launches_per_step);
 
 /* Release the batch, its instances and its memory.  Accepts NULL. */
 plbm_status plbm_batch_destroy(plbm_batch b);
@@ -290,9 +324,10 @@ plbm_status plbm_batch_step(plbm_batch b, long n, int mode);
  * first bad instance in *first_bad (else -1). */
 plbm_status plbm_batch_check(plbm_batch b, int *first_bad);
 
-/* Launch shape of the persistent kernel: block_x in {64, 128, 256} threads (one
- * tile = block_x node pairs of one pair row), ctas_per_sm persistent CTAs per SM
- * (0 = as many as fit). */
+/* Launch shape of the row-paired persistent kernel: block_x in {64, 128, 256}
+ * threads (one tile = block_x node pairs of one pair row), ctas_per_sm
+ * persistent CTAs per SM (0 = as many as fit).  The plain-layout groups always
+ * take 128-node tiles and as many CTAs as fit. */
 plbm_status plbm_batch_set_config(plbm_batch b, int block_x, int ctas_per_sm);
 
 /* Order in which the persistent CTAs take the tiles (all instances' tiles form
@@ -356,9 +391,19 @@ plbm_status plbm_sur_destroy(plbm_surrogate s);
  * only rejects non-finite or non-positive predictions (and FP32 rounding);
  * 0 (default) gates the network's own prediction. */
 #define PLBM_SUR_OPT_CONSERVE 2
+/* PLBM_SUR_OPT_WAIT_NS: budget in nanoseconds (>= 1; default 2 x 10^9) of each
+ * bounded wait of the tcgen05 kernels (a warp waiting for staged inputs, for
+ * an accumulator or for a free buffer).  A wait that runs out makes the kernel
+ * stop issuing work, wait for the MMAs and copies it issued (a fixed bound of
+ * 2 s, whatever this budget), free its tensor memory and return, and sets the
+ * flag plbm_sur_check reads; the results of that pass are then invalid.  A
+ * budget of a few nanoseconds makes the waits of the next pass run out, which
+ * exercises this path without a fault. */
+#define PLBM_SUR_OPT_WAIT_NS 3
 plbm_status plbm_sur_set_option(plbm_surrogate s, int option, int value);
 
-/* PLBM_E_TIMEOUT if a bounded wait of a tensor-core kernel ran out (synchronous). */
+/* PLBM_E_TIMEOUT if a bounded wait of a tensor-core kernel ran out since the
+ * last call; the flag is cleared once reported (synchronous). */
 plbm_status plbm_sur_check(plbm_surrogate s);
 
 /* Replace (host FP32, resets Adam) or read the parameters and the last gradients. */
@@ -427,6 +472,63 @@ plbm_status plbm_sur_last_drift(plbm_surrogate s, double *out, int n);
 
 /* Text of the last error of s (or of the calling thread when NULL). */
 const char *plbm_sur_last_error(plbm_surrogate s);
+
+/* ------------------------------------------------------------------------
+ * Domain decomposition along y.  A step of Eq. (eq:srt) (pull, then the local
+ * BGK collision) reads a node's populations from at most w = max|v| rows away
+ * (integer velocities, Sec. 2.4), so a slab of consecutive rows advances on its
+ * own once the w rows on each side of it hold its neighbours' current state:
+ * the rows below it are read only by populations with v_y > 0, the rows above
+ * only by those with v_y < 0.
+ * ------------------------------------------------------------------------ */
+
+/* Rows of slab k when ny rows are split into nslabs slabs as evenly as
+ * possible (the first ny mod nslabs slabs take one row more): rows y0 ..
+ * y0 + rows - 1.  Host computation.  PLBM_E_ARG unless 1 <= nslabs <= ny and
+ * 0 <= k < nslabs. */
+plbm_status plbm_slab_rows(int ny, int nslabs, int k, int *y0, int *rows);
+
+/* Halo width w = max |v_i| of a velocity set (-1 for bad arguments). */
+int plbm_halo_width(int q1, const int *v);
+
+/* Populations (index p = ix q1 + iy, ascending) that a slab's halo must hold:
+ * side -1, the w rows below the slab (populations with v_y > 0); side +1, the
+ * w rows above it (v_y < 0).  pops may be NULL to query *count (at most
+ * q1 * q1).  Host computation. */
+plbm_status plbm_halo_plan(int q1, const int *v, int side, int *pops, int *count);
+
+/* A periodic 2D lattice (desc: dim 2, PLBM_PERIODIC) split into nslabs slabs of
+ * rows (plbm_slab_rows) on desc->device.  Slab k is an ordinary handle of
+ * rows_k + 2w rows: its own rows at w .. w + rows_k - 1 between a lower and an
+ * upper halo of w rows.  A decomposed step copies the halo populations of
+ * plbm_halo_plan from the neighbouring slabs' own rows (periodic in y, one
+ * launch for all slabs), then steps every slab; the halo rows' own results are
+ * discarded.  Every own row is computed from the same values by the same code
+ * as in the undivided lattice, so the result equals it bit for bit: where the
+ * undivided lattice takes the row-paired layout (even ny, see plbm_desc.prec)
+ * the slabs take an even number of rows each (ny / 2 row pairs split by
+ * plbm_slab_rows) and the row-paired layout too; otherwise every slab keeps the
+ * plain layout (PLBM_FLAG_PLAIN_LAYOUT).  Each slab needs at least w rows.
+ * Every launch goes to desc->stream (it must not be the legacy default stream,
+ * as step pairs are captured in a CUDA graph; NULL: s creates its own).   Errors: PLBM_E_ARG, PLBM_E_NOMEM, PLBM_E_CUDA, and
+ * those of plbm_create. */
+typedef struct plbm_slabs_s *plbm_slabs;
+plbm_status plbm_slabs_create(const plbm_desc *desc, int nslabs, plbm_slabs *out);
+plbm_status plbm_slabs_destroy(plbm_slabs s);
+/* Handle, first row and row count of slab k (the handle is owned by s). */
+plbm_status plbm_slabs_slab(plbm_slabs s, int k, plbm_handle *h, int *y0, int *rows);
+/* Equilibrium initial state from host FP64 fields [ny][nx] of the whole
+ * lattice (the halo rows take the neighbours' rows).  Synchronous. */
+plbm_status plbm_slabs_init(plbm_slabs s, const double *rho, const double *ux, const double *uy,
+                            const double *theta);
+/* n decomposed steps (pairs of them replay a CUDA graph).  Asynchronous. */
+plbm_status plbm_slabs_step(plbm_slabs s, long n);
+/* Fields [ny][nx] or populations [q][ny][nx] of the whole lattice, FP64 host
+ * memory, gathered from the slabs' own rows.  Synchronous. */
+plbm_status plbm_slabs_moments(plbm_slabs s, double *rho, double *ux, double *uy, double *theta);
+plbm_status plbm_slabs_get_populations(plbm_slabs s, double *f);
+/* Text of the last error of s (or of the calling thread's last slab call when NULL). */
+const char *plbm_slabs_last_error(plbm_slabs s);
 
 /* Largest lattice (nx * ny nodes) plbm_diagnostics_noalloc accepts: its
  * static scratch array holds one 64-byte record per 256 nodes (1 MiB). */

@@ -65,17 +65,20 @@ class Batch:
     """n lattices advanced together (see include/plbm.h, plbm_batch_*)."""
 
     def __init__(self, instances, prec="f32", device=0, stream=None):
+        """prec: storage precision of every instance whose own ``prec`` is None."""
         import torch
         self.torch = torch
         self.instances = list(instances)
         self.prec = prec
+        self.precs = [inst.prec or prec for inst in self.instances]
         self.stream = stream if stream is not None else torch.cuda.Stream(device=device)
         n = len(self.instances)
         descs = (plbm.PlbmDesc * n)()
         self._keep = []
         for i, inst in enumerate(self.instances):
-            d, keep = plbm.make_desc(2, inst.v, inst.omega, inst.L, inst.L, theta0=inst.theta0, prec=prec,
-                                     device=device, u_max=0.1 if inst.kind == "kh" else 1e-3)
+            d, keep = plbm.make_desc(2, inst.v, inst.omega, inst.L, inst.L, theta0=inst.theta0, prec=self.precs[i],
+                                     isothermal=inst.isothermal, device=device,
+                                     u_max=0.1 if inst.kind == "kh" else 1e-3)
             descs[i] = d
             self._keep.append(keep)
         b = ctypes.c_void_p()
@@ -87,7 +90,7 @@ class Batch:
         for i, inst in enumerate(self.instances):
             h = plbm._H()
             self._ok(plbm.lib().plbm_batch_instance(self.b, i, ctypes.byref(h)))
-            self.solvers.append(plbm.Solver._wrap(h, 2, inst.v, inst.L, inst.L, prec, self.stream, torch))
+            self.solvers.append(plbm.Solver._wrap(h, 2, inst.v, inst.L, inst.L, self.precs[i], self.stream, torch))
 
     def _ok(self, st):
         if st != plbm.PLBM_OK:
@@ -100,7 +103,14 @@ class Batch:
     def init(self):
         """Initial fields of every instance (host FP64, inputs.instance_fields)."""
         for inst, s in zip(self.instances, self.solvers):
-            s.init(*I.instance_fields(inst))
+            rho, ux, uy, th = I.instance_fields(inst)
+            s.init(rho, ux, uy, None if inst.isothermal else th)
+
+    def groups(self):
+        """(row-paired instances, plain-layout instances, persistent launches per step)."""
+        vals = [ctypes.c_int() for _ in range(3)]
+        self._ok(plbm.lib().plbm_batch_groups(self.b, *[ctypes.byref(v) for v in vals]))
+        return tuple(v.value for v in vals)
 
     def step(self, n=1, mode="persistent_graph"):
         self._ok(plbm.lib().plbm_batch_step(self.b, int(n), MODES[mode] if isinstance(mode, str) else int(mode)))
@@ -129,7 +139,9 @@ class Batch:
 
     def cache_key(self):
         n = self.nodes
-        return "%s/d2q25/%d-instances/%d-Mnodes" % (self.prec, len(self.instances), int(round(n / 1e6)))
+        paired, plain, _ = self.groups()
+        return "%s/d2q25/%d-instances/%d-paired/%d-Mnodes" % ("+".join(sorted(set(self.precs))), len(self.instances),
+                                                             paired, int(round(n / 1e6)))
 
     def autotune(self, steps_per_trial=6, cache_path=None):
         """Pick the persistent-kernel shape (cached in JSON by precision, count and size)."""

@@ -531,6 +531,80 @@ struct DeviationCore {
 };
 
 // ---------------------------------------------------------------------------
+// One node of the fused stream-and-collide step: pull, collide, store; the
+// node's contribution to the diagnostics when REDUCE (d for FP64 storage, df
+// for 16/32-bit storage).  Shared by the single-lattice kernel and the batched
+// persistent kernel, so both give bit-identical states.
+// ---------------------------------------------------------------------------
+template <typename S, int Q1, int DIM, bool REDUCE>
+__device__ __forceinline__ void node_update(const LatticeParams& P, const S* __restrict__ src,
+                                            S* __restrict__ dst, int x, int y, NodeDiag& d, NodeDiagF& df) {
+    constexpr int Q = (DIM == 1) ? Q1 : Q1 * Q1;
+    PullIndex<Q1, DIM> ix;
+    ix.build(P, x, y);
+    const long long here = (long long)y * P.pitch + x;
+    if constexpr (!Storage<S>::kDeviation && sizeof(S) == 8) {
+        // FP64: direct core
+        double f[Q];
+#pragma unroll
+        for (int i = 0; i < Q1; ++i) {
+#pragma unroll
+            for (int j = 0; j < (DIM == 2 ? Q1 : 1); ++j) {
+                const int p = (DIM == 2) ? i * Q1 + j : i;
+                f[p] = ix.okx[i] ? Storage<S>::load(src + p * P.plane + ix.row[j] + ix.col[i])
+                                 : (ix.leftx[i] ? P.ghostL[p] : P.ghostR[p]);
+            }
+        }
+        double rho, th, jx, jy, e;
+        DirectCore<Q1, DIM>::collide(f, P, rho, th, jx, jy, e);
+        flag_status<double>(P, rho, th);
+        if (REDUCE) {
+            d.mass = rho;
+            d.jx = jx;
+            d.jy = jy;
+            d.energy = e;
+            d.rho_min = rho;
+            d.theta_min = th;
+        }
+#pragma unroll
+        for (int p = 0; p < Q; ++p) Storage<S>::store(dst + p * P.plane + here, f[p]);
+    } else {
+        // FP32 arithmetic on deviations g = f - w0
+        float g[Q];
+#pragma unroll
+        for (int i = 0; i < Q1; ++i) {
+#pragma unroll
+            for (int j = 0; j < (DIM == 2 ? Q1 : 1); ++j) {
+                const int p = (DIM == 2) ? i * Q1 + j : i;
+                if (ix.okx[i]) {
+                    float s = Storage<S>::load(src + p * P.plane + ix.row[j] + ix.col[i]);
+                    g[p] = Storage<S>::kDeviation ? s : s - P.W0f[p];
+                } else {
+                    g[p] = ix.leftx[i] ? P.ghostLg[p] : P.ghostRg[p];
+                }
+            }
+        }
+        float drho, th, jx, jy, e;
+        DeviationCore<Q1, DIM>::collide(g, P, drho, th, jx, jy, e);
+        flag_status<float>(P, 1.0f + drho, th);
+        if (REDUCE) {
+            df.dmass = FF{drho, 0.0f};
+            df.jx = FF{jx, 0.0f};
+            df.jy = FF{jy, 0.0f};
+            df.denergy = FF{e, 0.0f};
+            df.rho_min = 1.0f + drho;
+            df.theta_min = th;
+            df.n = 1.0f;
+        }
+#pragma unroll
+        for (int p = 0; p < Q; ++p) {
+            const float out = Storage<S>::kDeviation ? g[p] : g[p] + P.W0f[p];
+            Storage<S>::store(dst + p * P.plane + here, out);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // The fused stream-and-collide kernel.
 // grid = (ceil(nx / blockDim.x), ny), blockDim.x threads along x (kBlockX when
 // REDUCE, whose per-block records assume it).
@@ -539,10 +613,8 @@ template <typename S, int Q1, int DIM, bool REDUCE>
 __global__ void __launch_bounds__(kBlockX)
 k_stream_collide(const __grid_constant__ LatticeParams P, const S* __restrict__ src,
                  S* __restrict__ dst) {
-    constexpr int Q = (DIM == 1) ? Q1 : Q1 * Q1;
     const int x = blockIdx.x * (REDUCE ? kBlockX : (int)blockDim.x) + threadIdx.x;
     const int y = blockIdx.y;
-    const bool active = x < P.nx;
 
     NodeDiag d;       // FP64 storage
     NodeDiagF df;     // 16/32-bit storage
@@ -550,77 +622,42 @@ k_stream_collide(const __grid_constant__ LatticeParams P, const S* __restrict__ 
         diag_zero(d);
         diagf_zero(df);
     }
-
-    if (active) {
-        PullIndex<Q1, DIM> ix;
-        ix.build(P, x, y);
-        const long long here = (long long)y * P.pitch + x;
-        if constexpr (!Storage<S>::kDeviation && sizeof(S) == 8) {
-            // FP64: direct core
-            double f[Q];
-#pragma unroll
-            for (int i = 0; i < Q1; ++i) {
-#pragma unroll
-                for (int j = 0; j < (DIM == 2 ? Q1 : 1); ++j) {
-                    const int p = (DIM == 2) ? i * Q1 + j : i;
-                    f[p] = ix.okx[i] ? Storage<S>::load(src + p * P.plane + ix.row[j] + ix.col[i])
-                                     : (ix.leftx[i] ? P.ghostL[p] : P.ghostR[p]);
-                }
-            }
-            double rho, th, jx, jy, e;
-            DirectCore<Q1, DIM>::collide(f, P, rho, th, jx, jy, e);
-            flag_status<double>(P, rho, th);
-            if (REDUCE) {
-                d.mass = rho;
-                d.jx = jx;
-                d.jy = jy;
-                d.energy = e;
-                d.rho_min = rho;
-                d.theta_min = th;
-            }
-#pragma unroll
-            for (int p = 0; p < Q; ++p) Storage<S>::store(dst + p * P.plane + here, f[p]);
-        } else {
-            // FP32 arithmetic on deviations g = f - w0
-            float g[Q];
-#pragma unroll
-            for (int i = 0; i < Q1; ++i) {
-#pragma unroll
-                for (int j = 0; j < (DIM == 2 ? Q1 : 1); ++j) {
-                    const int p = (DIM == 2) ? i * Q1 + j : i;
-                    if (ix.okx[i]) {
-                        float s = Storage<S>::load(src + p * P.plane + ix.row[j] + ix.col[i]);
-                        g[p] = Storage<S>::kDeviation ? s : s - P.W0f[p];
-                    } else {
-                        g[p] = ix.leftx[i] ? P.ghostLg[p] : P.ghostRg[p];
-                    }
-                }
-            }
-            float drho, th, jx, jy, e;
-            DeviationCore<Q1, DIM>::collide(g, P, drho, th, jx, jy, e);
-            flag_status<float>(P, 1.0f + drho, th);
-            if (REDUCE) {
-                df.dmass = FF{drho, 0.0f};
-                df.jx = FF{jx, 0.0f};
-                df.jy = FF{jy, 0.0f};
-                df.denergy = FF{e, 0.0f};
-                df.rho_min = 1.0f + drho;
-                df.theta_min = th;
-                df.n = 1.0f;
-            }
-#pragma unroll
-            for (int p = 0; p < Q; ++p) {
-                const float out = Storage<S>::kDeviation ? g[p] : g[p] + P.W0f[p];
-                Storage<S>::store(dst + p * P.plane + here, out);
-            }
-        }
-    }
+    if (x < P.nx) node_update<S, Q1, DIM, REDUCE>(P, src, dst, x, y, d, df);
     if (REDUCE) {
         const int blk = blockIdx.y * gridDim.x + blockIdx.x;
         if constexpr (!Storage<S>::kDeviation && sizeof(S) == 8)
             block_reduce_diag<kBlockX>(d, P.partials + (long long)blk * kPartialStride);
         else
             block_reduce_diagf<kBlockX>(df, (double)DIM * P.theta0, P.partials + (long long)blk * kPartialStride);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Batched persistent step over 2D lattices in the plain layout (one node per
+// thread): odd row counts, FP64 storage, isothermal models and velocity sets
+// other than (0, +-a, +-b), which the row-paired batched kernel does not take.
+// A tile is kBlockX nodes of one row of one lattice; all such lattices' tiles
+// form one list that CTA c walks as c, c + G, c + 2G, ... (G CTAs), reading
+// each tile's lattice from tile_inst and that lattice's parameters from the
+// device table (cached by L1).  Per node it runs node_update, as the
+// single-lattice kernel does.
+// ---------------------------------------------------------------------------
+template <typename S, int Q1>
+__global__ void __launch_bounds__(kBlockX)
+k_batch_node(const LatticeParams* __restrict__ inst, const NodeSpan* __restrict__ span, int total_tiles,
+             int parity, const unsigned short* __restrict__ tile_inst) {
+    NodeDiag d;
+    NodeDiagF df;
+    for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+        const int i = tile_inst[t];
+        const NodeSpan sp = span[i];
+        const LatticeParams& P = inst[i];
+        const int local = t - sp.tile_begin;
+        const int y = local / sp.tiles_x;
+        const int x = (local - y * sp.tiles_x) * kBlockX + threadIdx.x;
+        if (x < sp.nx)
+            node_update<S, Q1, 2, false>(P, static_cast<const S*>(sp.f[parity]), static_cast<S*>(sp.f[parity ^ 1]),
+                                         x, y, d, df);
     }
 }
 
@@ -667,6 +704,29 @@ cudaError_t launch_step_t(const LatticeParams& P, const void* src, void* dst, bo
     PLBM_LAUNCH(7, 2)
     PLBM_LAUNCH(8, 2)
 #undef PLBM_LAUNCH
+    return cudaErrorInvalidValue;
+}
+
+// Batched plain-layout step of every lattice of one (precision, q1) group.
+template <typename S>
+cudaError_t launch_batch_node_t(int q1, const LatticeParams* inst, const NodeSpan* span, int total_tiles,
+                                int ctas, int parity, const unsigned short* tile_inst, cudaStream_t stream) {
+    switch (q1) {
+        case 3: k_batch_node<S, 3><<<ctas, kBlockX, 0, stream>>>(inst, span, total_tiles, parity, tile_inst); break;
+        case 4: k_batch_node<S, 4><<<ctas, kBlockX, 0, stream>>>(inst, span, total_tiles, parity, tile_inst); break;
+        case 5: k_batch_node<S, 5><<<ctas, kBlockX, 0, stream>>>(inst, span, total_tiles, parity, tile_inst); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t batch_node_occupancy_t(int q1, int* blocks_per_sm) {
+    switch (q1) {
+        case 3: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batch_node<S, 3>, kBlockX, 0);
+        case 4: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batch_node<S, 4>, kBlockX, 0);
+        case 5: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batch_node<S, 5>, kBlockX, 0);
+    }
     return cudaErrorInvalidValue;
 }
 

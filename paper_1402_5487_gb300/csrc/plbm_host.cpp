@@ -322,6 +322,14 @@ struct Staging {
 namespace plbm {
 void set_thread_error(const char* msg) { std::snprintf(g_thread_error, sizeof g_thread_error, "%s", msg); }
 
+bool desc_row_paired(const plbm_desc* d) {
+    if (!d || !d->v || d->dim != 2 || d->q1 != 5) return false;
+    const int* v = d->v;
+    const bool sym5 = v[0] == 0 && v[1] > 0 && v[2] == -v[1] && v[3] > 0 && v[4] == -v[3] && v[1] != v[3];
+    return sym5 && d->ny % 2 == 0 && d->prec != PLBM_F64 && !(d->flags & PLBM_FLAG_ISOTHERMAL) &&
+           d->bc == PLBM_PERIODIC && !(d->flags & PLBM_FLAG_PLAIN_LAYOUT);
+}
+
 bool handle_view(void* hh, HandleView* out) {
     Handle* h = static_cast<Handle*>(hh);
     if (!h || !out || !h->initialised || h->sticky != PLBM_OK) return false;
@@ -453,7 +461,7 @@ plbm_status plbm_create(const plbm_desc* desc, plbm_handle* out) {
     // Row-paired layout and the two-nodes-per-thread kernel: 2D periodic symmetric
     // five-velocity thermal lattices with an even number of rows, 16/32-bit storage.
     P.paired = (dim == 2 && desc->ny % 2 == 0 && desc->prec != PLBM_F64 && P.sym5 && !P.isothermal &&
-                desc->bc == PLBM_PERIODIC) ? 1 : 0;
+                desc->bc == PLBM_PERIODIC && !(desc->flags & PLBM_FLAG_PLAIN_LAYOUT)) ? 1 : 0;
     P.half_ny = P.paired ? desc->ny / 2 : 0;
     // z-paired layout and the two-nodes-per-thread 3D kernel: 16-bit storage, even nz,
     // every |v| <= nz / 2 (one wrap of the pair row per pull).
@@ -569,6 +577,33 @@ plbm_status plbm_destroy(plbm_handle hh) {
     return PLBM_OK;
 }
 
+static plbm::FieldSet field_set(const double* const* d, int nd) {
+    plbm::FieldSet F{};
+    F.rho = -1;
+    F.theta = -1;
+    for (int k = 0; k < nd; ++k) {
+        if (!d[k]) continue;
+        if (k == 0) F.rho = F.count;
+        if (k == nd - 1) F.theta = F.count;
+        F.field[F.count++] = d[k];
+    }
+    return F;
+}
+
+// After a synchronous (host-pointer) init: PLBM_E_ARG if the field check set a
+// status bit; the handle is then left uninitialised.
+static plbm_status init_fields_verdict(Handle* h) {
+    unsigned bits = 0;
+    plbm_status st = read_status(h, &bits);
+    if (st != PLBM_OK) return st;
+    if (bits) {
+        h->initialised = false;
+        set_err(h, "initial fields rejected (status 0x%x): non-finite values, rho <= 0 or theta <= 0", bits);
+        return PLBM_E_ARG;
+    }
+    return PLBM_OK;
+}
+
 plbm_status plbm_init(plbm_handle hh, const double* rho, const double* ux, const double* uy,
                       const double* theta, int on_device) {
     Handle* h = reinterpret_cast<Handle*>(hh);
@@ -584,6 +619,8 @@ plbm_status plbm_init(plbm_handle hh, const double* rho, const double* ux, const
     if (on_device) {
         CK(plbm::launch_init(h->prec, h->P, rho, ux, uy, theta, h->f[0], h->stream));
         CK(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
+        const double* d[4] = {rho, ux, h->P.dim == 2 ? uy : nullptr, theta};
+        CK(plbm::launch_check_fields(field_set(d, 4), (long long)n, h->status, h->stream));
     } else {
         // Band k of the four fields is copied on the copy stream while the kernel
         // initialises band k - 1 on the handle's stream.
@@ -607,11 +644,11 @@ plbm_status plbm_init(plbm_handle hh, const double* rho, const double* ux, const
             CK(plbm::launch_init(h->prec, h->P, dev[0], dev[1], dev[2], dev[3], h->f[0], h->stream, y0, y1));
         }
         CK(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
-        CK(cudaStreamSynchronize(h->stream));
+        CK(plbm::launch_check_fields(field_set(dev, 4), (long long)n, h->status, h->stream));
     }
     h->steps = 0;
     h->initialised = true;
-    return PLBM_OK;
+    return on_device ? PLBM_OK : init_fields_verdict(h);
 }
 
 plbm_status plbm_check(plbm_handle hh) {
@@ -811,10 +848,10 @@ plbm_status plbm_init3(plbm_handle hh, const double* rho, const double* ux, cons
     h->cur = 0;
     CK(plbm::launch_init3(h->prec, h->P, d[0], d[1], d[2], d[3], d[4], h->f[0], h->stream));
     CK(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
-    if (!on_device) CK(cudaStreamSynchronize(h->stream));
+    CK(plbm::launch_check_fields(field_set(d, 5), (long long)n, h->status, h->stream));
     h->steps = 0;
     h->initialised = true;
-    return PLBM_OK;
+    return on_device ? PLBM_OK : init_fields_verdict(h);
 }
 
 plbm_status plbm_moments3(plbm_handle hh, double* rho, double* ux, double* uy, double* uz, double* theta,
@@ -908,6 +945,139 @@ plbm_status plbm_set_populations(plbm_handle hh, const double* f, int on_device,
     return PLBM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Checkpoints: a fixed header that describes the lattice, then the stored
+// population array byte for byte (its precision and layout), protected by a
+// 64-bit FNV-1a checksum over the header (checksum field zero) and the payload.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr char kCkptMagic[8] = {'P', 'L', 'B', 'M', 'C', 'K', 'P', 'T'};
+constexpr uint32_t kCkptFormat = 1;
+
+struct CkptHeader {
+    char magic[8];
+    uint32_t format, header_bytes;
+    int32_t abi, dim, q1, nx, ny, nz, prec, bc, isothermal, pitch, paired, zpaired;
+    int32_t v[plbm::kMaxQ1];
+    double omega, theta0;
+    uint64_t ends_digest;   // FNV-1a of the fixed-end ghost populations (0 when periodic)
+    int64_t step;
+    uint64_t payload_bytes;
+    uint64_t checksum;
+};
+
+// FNV-1a, 64-bit: for every byte, h = (h xor byte) * 1099511628211.
+uint64_t fnv1a(uint64_t h, const void* data, size_t n) {
+    const unsigned char* p = static_cast<const unsigned char*>(data);
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+constexpr uint64_t kFnvOffset = 14695981039346656037ull;
+
+CkptHeader ckpt_header_of(const Handle* h) {
+    CkptHeader c;
+    std::memset(&c, 0, sizeof c);
+    std::memcpy(c.magic, kCkptMagic, sizeof c.magic);
+    c.format = kCkptFormat;
+    c.header_bytes = sizeof(CkptHeader);
+    c.abi = PLBM_ABI_VERSION;
+    c.dim = h->P.dim;
+    c.q1 = h->P.q1;
+    c.nx = h->P.nx;
+    c.ny = h->P.ny;
+    c.nz = h->P.nz;
+    c.prec = h->prec;
+    c.bc = h->P.fixed_ends;
+    c.isothermal = h->P.isothermal;
+    c.pitch = h->P.pitch;
+    c.paired = h->P.paired;
+    c.zpaired = h->P.zpaired;
+    for (int i = 0; i < h->P.q1; ++i) c.v[i] = h->P.v[i];
+    c.omega = h->P.omega;
+    c.theta0 = h->P.theta0;
+    if (h->P.fixed_ends) {
+        c.ends_digest = fnv1a(kFnvOffset, h->P.ghostL, sizeof(double) * h->P.q);
+        c.ends_digest = fnv1a(c.ends_digest, h->P.ghostR, sizeof(double) * h->P.q);
+    }
+    c.step = h->steps;
+    c.payload_bytes = h->pop_bytes;
+    return c;
+}
+
+}  // namespace
+
+size_t plbm_checkpoint_bytes(plbm_handle hh) {
+    const Handle* h = reinterpret_cast<const Handle*>(hh);
+    return h ? sizeof(CkptHeader) + h->pop_bytes : 0;
+}
+
+plbm_status plbm_checkpoint_save(plbm_handle hh, void* buf, size_t bytes) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !buf) { set_err(h, "bad arguments"); return PLBM_E_ARG; }
+    if (!h->initialised) { set_err(h, "populations not initialised"); return PLBM_E_STATE; }
+    if (h->sticky == PLBM_E_CUDA) { set_err(h, "handle in CUDA error state"); return PLBM_E_CUDA; }
+    if (bytes < sizeof(CkptHeader) + h->pop_bytes) {
+        set_err(h, "checkpoint buffer of %zu bytes, %zu needed", bytes, sizeof(CkptHeader) + h->pop_bytes);
+        return PLBM_E_ARG;
+    }
+    CK(cudaSetDevice(h->desc.device));
+    unsigned char* out = static_cast<unsigned char*>(buf);
+    CK(cudaMemcpyAsync(out + sizeof(CkptHeader), h->f[h->cur], h->pop_bytes, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    CkptHeader c = ckpt_header_of(h);
+    uint64_t sum = fnv1a(kFnvOffset, &c, sizeof c);
+    c.checksum = fnv1a(sum, out + sizeof(CkptHeader), h->pop_bytes);
+    std::memcpy(out, &c, sizeof c);
+    return PLBM_OK;
+}
+
+plbm_status plbm_checkpoint_load(plbm_handle hh, const void* buf, size_t bytes) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    plbm_status st = usable(h, false);
+    if (st != PLBM_OK) return st;
+    if (!buf || bytes < sizeof(CkptHeader)) { set_err(h, "checkpoint too short"); return PLBM_E_CHECKSUM; }
+    CkptHeader c;
+    std::memcpy(&c, buf, sizeof c);
+    if (std::memcmp(c.magic, kCkptMagic, sizeof c.magic) != 0 || c.format != kCkptFormat ||
+        c.header_bytes != sizeof(CkptHeader)) {
+        set_err(h, "not a checkpoint of this format");
+        return PLBM_E_CHECKSUM;
+    }
+    if (c.payload_bytes != h->pop_bytes || bytes < sizeof(CkptHeader) + c.payload_bytes) {
+        set_err(h, "checkpoint payload of %llu bytes, handle holds %zu", (unsigned long long)c.payload_bytes,
+                h->pop_bytes);
+        return PLBM_E_CHECKSUM;
+    }
+    const unsigned char* in = static_cast<const unsigned char*>(buf);
+    const uint64_t stored = c.checksum;
+    c.checksum = 0;
+    const uint64_t sum = fnv1a(fnv1a(kFnvOffset, &c, sizeof c), in + sizeof(CkptHeader), c.payload_bytes);
+    if (sum != stored) {
+        set_err(h, "checkpoint checksum mismatch (stored %016llx, computed %016llx)", (unsigned long long)stored,
+                (unsigned long long)sum);
+        return PLBM_E_CHECKSUM;
+    }
+    CkptHeader mine = ckpt_header_of(h);
+    mine.step = c.step;
+    mine.checksum = 0;
+    if (std::memcmp(&mine, &c, sizeof c) != 0) {
+        set_err(h, "checkpoint describes another lattice (velocities, omega, theta0, sizes, precision, layout or "
+                   "boundary states differ)");
+        return PLBM_E_CHECKSUM;
+    }
+    h->cur = 0;
+    CK(cudaMemcpyAsync(h->f[0], in + sizeof(CkptHeader), h->pop_bytes, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->steps = c.step;
+    h->initialised = true;
+    return PLBM_OK;
+}
+
 plbm_status plbm_get_info(plbm_handle hh, int* q, int* pitch, size_t* population_bytes) {
     Handle* h = reinterpret_cast<Handle*>(hh);
     if (!h) { set_err(nullptr, "handle is NULL"); return PLBM_E_ARG; }
@@ -951,19 +1121,42 @@ const char* plbm_status_string(plbm_status s) {
 // ---------------------------------------------------------------------------
 namespace {
 
+// The instances fall into groups that one persistent launch per step advances:
+// row-paired lattices (2D periodic thermal (0, +-a, +-b), even row count,
+// 16/32-bit storage) by k_batch_pair, one group per storage precision; every
+// other 2D lattice (odd row counts, FP64, isothermal, other velocity sets with
+// q1 <= 5) by k_batch_node, one group per (precision, q1).
+struct PairGroup {
+    int prec = 0;
+    std::vector<int> members;                // indices into Batch::inst
+    std::vector<plbm::PairParams> table;
+    plbm::PairParams* d_table = nullptr;
+    unsigned short* d_tile_inst = nullptr;   // instance (index into table) of every tile
+    size_t max_tiles = 0;                    // tiles at the smallest block_x
+    int total_tiles = 0;
+};
+
+struct NodeGroup {
+    int prec = 0, q1 = 0;
+    std::vector<int> members;
+    plbm::LatticeParams* d_params = nullptr;
+    plbm::NodeSpan* d_span = nullptr;
+    unsigned short* d_tile_inst = nullptr;
+    int total_tiles = 0;
+    int ctas = 0;
+};
+
 struct Batch {
     std::vector<Handle*> inst;
-    int prec = 0;
     int device = 0;
     cudaStream_t stream = nullptr;
     bool owns_stream = false;
-    char* ws = nullptr;
-    plbm::PairParams* d_table = nullptr;
-    std::vector<plbm::PairParams> table;
-    unsigned short* d_tile_inst = nullptr;   // instance of every global tile (interleaved order)
-    size_t max_tiles = 0;                    // tiles at the smallest block_x
+    char* ws = nullptr;        // instance workspaces
+    char* tables = nullptr;    // group tables
+    std::vector<PairGroup> pairs;
+    std::vector<NodeGroup> nodes;
     int order = PLBM_BATCH_ORDER_INTERLEAVED;
-    int block_x = 128, ctas_per_sm = 0, sms = 0, total_tiles = 0;
+    int block_x = 128, ctas_per_sm = 0, sms = 0;
     cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [kind][start parity]
     long long steps = 0;
     char err[512] = "";
@@ -997,34 +1190,55 @@ void drop_graphs(Batch* b) {
             }
 }
 
+// Occupancy of the row-paired kernel at block_x: the smallest over the paired
+// groups' precisions (1 when there are none).
+int pair_occupancy(Batch* b, int block_x) {
+    int occ = 1 << 20;
+    for (const PairGroup& g : b->pairs) {
+        int o = 0;
+        if (plbm::batch_occupancy(g.prec, block_x, &o) != cudaSuccess || o < 1) o = 1;
+        occ = std::min(occ, o);
+    }
+    return b->pairs.empty() ? 1 : occ;
+}
+
 int batch_ctas(Batch* b, int* occ_out = nullptr) {
-    int occ = 0;
-    if (plbm::batch_occupancy(b->prec, b->block_x, &occ) != cudaSuccess || occ < 1) occ = 1;
+    const int occ = pair_occupancy(b, b->block_x);
     if (occ_out) *occ_out = occ;
     const int per_sm = b->ctas_per_sm > 0 ? std::min(b->ctas_per_sm, occ) : occ;
     return b->sms * per_sm;
 }
 
+int batch_total_tiles(const Batch* b) {
+    int t = 0;
+    for (const PairGroup& g : b->pairs) t += g.total_tiles;
+    for (const NodeGroup& g : b->nodes) t += g.total_tiles;
+    return t;
+}
+
+// Tile lists of the row-paired groups for the current block_x.
 plbm_status batch_table(Batch* b) {
-    int tile = 0;
-    for (size_t i = 0; i < b->inst.size(); ++i) {
-        plbm::PairParams& Q = b->table[i];
-        Q.tiles_x = (Q.nx + b->block_x - 1) / b->block_x;
-        Q.tile_begin = tile;
-        tile += Q.tiles_x * Q.half_ny;
+    for (PairGroup& g : b->pairs) {
+        int tile = 0;
+        for (plbm::PairParams& Q : g.table) {
+            Q.tiles_x = (Q.nx + b->block_x - 1) / b->block_x;
+            Q.tile_begin = tile;
+            tile += Q.tiles_x * Q.half_ny;
+        }
+        g.total_tiles = tile;
+        std::vector<unsigned short> ti((size_t)tile);
+        for (size_t i = 0; i < g.table.size(); ++i) {
+            const plbm::PairParams& Q = g.table[i];
+            std::fill(ti.begin() + Q.tile_begin, ti.begin() + Q.tile_begin + Q.tiles_x * Q.half_ny,
+                      (unsigned short)i);
+        }
+        BCK(cudaMemcpyAsync(g.d_table, g.table.data(), sizeof(plbm::PairParams) * g.table.size(),
+                            cudaMemcpyHostToDevice, b->stream));
+        if (tile > 0)
+            BCK(cudaMemcpyAsync(g.d_tile_inst, ti.data(), sizeof(unsigned short) * ti.size(),
+                                cudaMemcpyHostToDevice, b->stream));
+        BCK(cudaStreamSynchronize(b->stream));
     }
-    b->total_tiles = tile;
-    std::vector<unsigned short> ti((size_t)tile);
-    for (size_t i = 0; i < b->inst.size(); ++i) {
-        const plbm::PairParams& Q = b->table[i];
-        std::fill(ti.begin() + Q.tile_begin, ti.begin() + Q.tile_begin + Q.tiles_x * Q.half_ny,
-                  (unsigned short)i);
-    }
-    BCK(cudaMemcpyAsync(b->d_table, b->table.data(), sizeof(plbm::PairParams) * b->table.size(),
-                        cudaMemcpyHostToDevice, b->stream));
-    BCK(cudaMemcpyAsync(b->d_tile_inst, ti.data(), sizeof(unsigned short) * ti.size(), cudaMemcpyHostToDevice,
-                        b->stream));
-    BCK(cudaStreamSynchronize(b->stream));
     drop_graphs(b);
     return PLBM_OK;
 }
@@ -1039,6 +1253,7 @@ void free_batch(Batch* b) {
         free_handle(h);
     }
     if (b->ws) cudaFree(b->ws);
+    if (b->tables) cudaFree(b->tables);
     if (b->owns_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
 }
@@ -1046,14 +1261,128 @@ void free_batch(Batch* b) {
 // One step of every instance with the chosen launch scheme (no graph).
 plbm_status batch_launch(Batch* b, int scheme, int parity, int ctas) {
     if (scheme == 0) {
-        BCK(plbm::launch_batch(b->prec, b->d_table, (int)b->inst.size(), b->total_tiles, b->block_x, ctas,
-                               parity, b->order == PLBM_BATCH_ORDER_INTERLEAVED ? b->d_tile_inst : nullptr,
-                               b->stream));
+        for (const PairGroup& g : b->pairs)
+            BCK(plbm::launch_batch(g.prec, g.d_table, (int)g.table.size(), g.total_tiles, b->block_x, ctas, parity,
+                                   b->order == PLBM_BATCH_ORDER_INTERLEAVED ? g.d_tile_inst : nullptr, b->stream));
+        for (const NodeGroup& g : b->nodes)
+            BCK(plbm::launch_batch_node(g.prec, g.q1, g.d_params, g.d_span, g.total_tiles, g.ctas, parity,
+                                        g.d_tile_inst, b->stream));
     } else {
         for (Handle* h : b->inst)
-            BCK(plbm::launch_step(b->prec, h->P, h->f[parity], h->f[parity ^ 1], false, b->stream));
+            BCK(plbm::launch_step(h->prec, h->P, h->f[parity], h->f[parity ^ 1], false, b->stream));
     }
     return PLBM_OK;
+}
+
+// Groups the created instances and builds the groups' device tables.
+plbm_status batch_groups(Batch* b) {
+    for (size_t i = 0; i < b->inst.size(); ++i) {
+        const Handle* h = b->inst[i];
+        if (h->P.paired) {
+            PairGroup* g = nullptr;
+            for (PairGroup& c : b->pairs)
+                if (c.prec == h->prec) g = &c;
+            if (!g) {
+                b->pairs.emplace_back();
+                g = &b->pairs.back();
+                g->prec = h->prec;
+            }
+            g->members.push_back((int)i);
+            g->max_tiles += (size_t)((h->P.nx + 63) / 64) * (size_t)h->P.half_ny;
+        } else {
+            if (h->P.dim != 2 || h->P.q1 < 3 || h->P.q1 > 5) {
+                batch_err(b, "instance %zu: the batched runner takes 2D lattices with 3 to 5 velocities per axis", i);
+                return PLBM_E_ARG;
+            }
+            NodeGroup* g = nullptr;
+            for (NodeGroup& c : b->nodes)
+                if (c.prec == h->prec && c.q1 == h->P.q1) g = &c;
+            if (!g) {
+                b->nodes.emplace_back();
+                g = &b->nodes.back();
+                g->prec = h->prec;
+                g->q1 = h->P.q1;
+            }
+            g->members.push_back((int)i);
+        }
+    }
+    for (const PairGroup& g : b->pairs)
+        if (g.members.size() > 65535) { batch_err(b, "at most 65535 row-paired instances per precision"); return PLBM_E_ARG; }
+    for (const NodeGroup& g : b->nodes)
+        if (g.members.size() > 65535) { batch_err(b, "at most 65535 instances per group"); return PLBM_E_ARG; }
+    // one allocation for every group's tables
+    size_t total = 0;
+    std::vector<size_t> off;
+    for (const PairGroup& g : b->pairs) {
+        off.push_back(total);
+        total += align_up(sizeof(plbm::PairParams) * g.members.size(), 256);
+        off.push_back(total);
+        total += align_up(sizeof(unsigned short) * std::max<size_t>(g.max_tiles, 1), 256);
+    }
+    std::vector<std::vector<unsigned short>> node_tiles(b->nodes.size());
+    std::vector<std::vector<plbm::NodeSpan>> spans(b->nodes.size());
+    for (size_t k = 0; k < b->nodes.size(); ++k) {
+        NodeGroup& g = b->nodes[k];
+        int tile = 0;
+        for (size_t m = 0; m < g.members.size(); ++m) {
+            const Handle* h = b->inst[g.members[m]];
+            plbm::NodeSpan sp{};
+            sp.f[0] = h->f[0];
+            sp.f[1] = h->f[1];
+            sp.nx = h->P.nx;
+            sp.tiles_x = (h->P.nx + plbm::kBlockX - 1) / plbm::kBlockX;
+            sp.tile_begin = tile;
+            tile += sp.tiles_x * h->P.ny;
+            spans[k].push_back(sp);
+            node_tiles[k].insert(node_tiles[k].end(), (size_t)sp.tiles_x * h->P.ny, (unsigned short)m);
+        }
+        g.total_tiles = tile;
+        int occ = 0;
+        if (plbm::batch_node_occupancy(g.prec, g.q1, &occ) != cudaSuccess || occ < 1) occ = 1;
+        g.ctas = std::max(1, std::min(tile, b->sms * occ));
+        off.push_back(total);
+        total += align_up(sizeof(plbm::LatticeParams) * g.members.size(), 256);
+        off.push_back(total);
+        total += align_up(sizeof(plbm::NodeSpan) * g.members.size(), 256);
+        off.push_back(total);
+        total += align_up(sizeof(unsigned short) * std::max<size_t>(node_tiles[k].size(), 1), 256);
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(total, 256));
+    if (e != cudaSuccess) {
+        batch_err(b, "cudaMalloc(%zu) failed: %s", total, cudaGetErrorString(e));
+        return PLBM_E_NOMEM;
+    }
+    b->tables = static_cast<char*>(p);
+    size_t o = 0;
+    for (PairGroup& g : b->pairs) {
+        g.d_table = reinterpret_cast<plbm::PairParams*>(b->tables + off[o++]);
+        g.d_tile_inst = reinterpret_cast<unsigned short*>(b->tables + off[o++]);
+        for (int i : g.members) {
+            const Handle* h = b->inst[i];
+            plbm::PairParams Q = plbm::pair_params(h->P);
+            Q.f[0] = h->f[0];
+            Q.f[1] = h->f[1];
+            g.table.push_back(Q);
+        }
+    }
+    for (size_t k = 0; k < b->nodes.size(); ++k) {
+        NodeGroup& g = b->nodes[k];
+        g.d_params = reinterpret_cast<plbm::LatticeParams*>(b->tables + off[o++]);
+        g.d_span = reinterpret_cast<plbm::NodeSpan*>(b->tables + off[o++]);
+        g.d_tile_inst = reinterpret_cast<unsigned short*>(b->tables + off[o++]);
+        std::vector<plbm::LatticeParams> params;
+        for (int i : g.members) params.push_back(b->inst[i]->P);
+        BCK(cudaMemcpyAsync(g.d_params, params.data(), sizeof(plbm::LatticeParams) * params.size(),
+                            cudaMemcpyHostToDevice, b->stream));
+        BCK(cudaMemcpyAsync(g.d_span, spans[k].data(), sizeof(plbm::NodeSpan) * spans[k].size(),
+                            cudaMemcpyHostToDevice, b->stream));
+        if (!node_tiles[k].empty())
+            BCK(cudaMemcpyAsync(g.d_tile_inst, node_tiles[k].data(), sizeof(unsigned short) * node_tiles[k].size(),
+                                cudaMemcpyHostToDevice, b->stream));
+    }
+    BCK(cudaStreamSynchronize(b->stream));
+    return batch_table(b);
 }
 
 }  // namespace
@@ -1068,14 +1397,18 @@ plbm_status plbm_batch_create(const plbm_desc* descs, int n, void* stream, plbm_
     *out = nullptr;
     Batch* b = new (std::nothrow) Batch();
     if (!b) return PLBM_E_NOMEM;
-    b->prec = (int)descs[0].prec;
     b->device = descs[0].device;
     std::vector<size_t> off(n);
     size_t total = 0;
     for (int i = 0; i < n; ++i) {
         const plbm_desc& d = descs[i];
-        if ((int)d.prec != b->prec || d.device != b->device) {
-            batch_err(b, "instance %d: all instances need the same precision and device", i);
+        if (d.device != b->device) {
+            batch_err(b, "instance %d: all instances need the same device", i);
+            delete b;
+            return PLBM_E_ARG;
+        }
+        if (d.dim != 2) {
+            batch_err(b, "instance %d: the batched runner takes 2D lattices", i);
             delete b;
             return PLBM_E_ARG;
         }
@@ -1087,17 +1420,6 @@ plbm_status plbm_batch_create(const plbm_desc* descs, int n, void* stream, plbm_
         }
         off[i] = total;
         total += align_up(need, 256);
-    }
-    const size_t table_off = total;
-    total += align_up(sizeof(plbm::PairParams) * n, 256);
-    for (int i = 0; i < n; ++i)
-        b->max_tiles += (size_t)((descs[i].nx + 63) / 64) * (size_t)(descs[i].ny / 2);
-    const size_t tile_inst_off = total;
-    total += align_up(sizeof(unsigned short) * std::max<size_t>(b->max_tiles, 1), 256);
-    if (n > 65535) {
-        batch_err(b, "at most 65535 instances");
-        delete b;
-        return PLBM_E_ARG;
     }
     if (cudaSetDevice(b->device) != cudaSuccess) {
         batch_err(b, "cudaSetDevice(%d) failed", b->device);
@@ -1123,11 +1445,8 @@ plbm_status plbm_batch_create(const plbm_desc* descs, int n, void* stream, plbm_
         return PLBM_E_NOMEM;
     }
     b->ws = static_cast<char*>(p);
-    b->d_table = reinterpret_cast<plbm::PairParams*>(b->ws + table_off);
-    b->d_tile_inst = reinterpret_cast<unsigned short*>(b->ws + tile_inst_off);
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
     b->inst.assign(n, nullptr);
-    b->table.resize(n);
     for (int i = 0; i < n; ++i) {
         plbm_desc d = descs[i];
         d.workspace = b->ws + off[i];
@@ -1143,18 +1462,8 @@ plbm_status plbm_batch_create(const plbm_desc* descs, int n, void* stream, plbm_
         Handle* h = reinterpret_cast<Handle*>(hh);
         h->in_batch = true;
         b->inst[i] = h;
-        if (!h->P.paired) {
-            batch_err(b, "instance %d: the batched runner needs 2D periodic thermal lattices with "
-                         "v = (0, a, -a, b, -b), an even row count and FP32/FP16/BF16 storage", i);
-            free_batch(b);
-            return PLBM_E_ARG;
-        }
-        plbm::PairParams Q = plbm::pair_params(h->P);
-        Q.f[0] = h->f[0];
-        Q.f[1] = h->f[1];
-        b->table[i] = Q;
     }
-    plbm_status st = batch_table(b);
+    plbm_status st = batch_groups(b);
     if (st != PLBM_OK) {
         free_batch(b);
         return st;
@@ -1286,10 +1595,22 @@ plbm_status plbm_batch_info(plbm_batch bb, int* ninst, int* total_tiles, int* bl
     int occ = 0;
     const int c = batch_ctas(b, &occ);
     if (ninst) *ninst = (int)b->inst.size();
-    if (total_tiles) *total_tiles = b->total_tiles;
+    if (total_tiles) *total_tiles = batch_total_tiles(b);
     if (block_x) *block_x = b->block_x;
     if (ctas) *ctas = c;
     if (max_ctas_per_sm) *max_ctas_per_sm = occ;
+    return PLBM_OK;
+}
+
+plbm_status plbm_batch_groups(plbm_batch bb, int* paired_instances, int* plain_instances, int* launches_per_step) {
+    Batch* b = reinterpret_cast<Batch*>(bb);
+    if (!b) return PLBM_E_ARG;
+    int np = 0, nn = 0;
+    for (const PairGroup& g : b->pairs) np += (int)g.members.size();
+    for (const NodeGroup& g : b->nodes) nn += (int)g.members.size();
+    if (paired_instances) *paired_instances = np;
+    if (plain_instances) *plain_instances = nn;
+    if (launches_per_step) *launches_per_step = (int)(b->pairs.size() + b->nodes.size());
     return PLBM_OK;
 }
 
@@ -1308,29 +1629,35 @@ plbm_status plbm_batch_tune(plbm_batch bb, int steps_per_trial, int* best_block_
     double best = 1e300;
     int bx_best = 128, cps_best = 0, order_best = PLBM_BATCH_ORDER_INTERLEAVED;
     const int bxs[3] = {64, 128, 256};
-    for (int order : {PLBM_BATCH_ORDER_CONTIGUOUS, PLBM_BATCH_ORDER_INTERLEAVED})
-    for (int bx : bxs) {
-        int occ = 0;
-        if (plbm::batch_occupancy(b->prec, bx, &occ) != cudaSuccess || occ < 1) continue;
-        for (int cps = 1; cps <= occ; ++cps) {
-            plbm_status st = plbm_batch_set_config(bb, bx, cps);
-            if (st == PLBM_OK) st = plbm_batch_set_order(bb, order);
-            if (st != PLBM_OK) return st;
-            st = plbm_batch_step(bb, 2, PLBM_BATCH_PERSISTENT);
-            if (st != PLBM_OK) return st;
-            BCK(cudaEventRecord(e0, b->stream));
-            st = plbm_batch_step(bb, steps_per_trial, PLBM_BATCH_PERSISTENT);
-            if (st != PLBM_OK) return st;
-            BCK(cudaEventRecord(e1, b->stream));
-            BCK(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            BCK(cudaEventElapsedTime(&ms, e0, e1));
-            const double per = ms / steps_per_trial;
-            if (per < best) {
-                best = per;
-                bx_best = bx;
-                cps_best = cps;
-                order_best = order;
+    // Without row-paired instances the shape has nothing to choose: one trial.
+    const bool any_pairs = !b->pairs.empty();
+    for (int order : {PLBM_BATCH_ORDER_CONTIGUOUS, PLBM_BATCH_ORDER_INTERLEAVED}) {
+        if (!any_pairs && order != PLBM_BATCH_ORDER_INTERLEAVED) continue;
+        for (int bx : bxs) {
+            if (!any_pairs && bx != 128) continue;
+            const int occ = any_pairs ? pair_occupancy(b, bx) : 1;
+            for (int cps = any_pairs ? 1 : 0; cps <= occ; ++cps) {
+                if (any_pairs && cps == 0) continue;
+                plbm_status st = plbm_batch_set_config(bb, bx, cps);
+                if (st == PLBM_OK) st = plbm_batch_set_order(bb, order);
+                if (st != PLBM_OK) return st;
+                st = plbm_batch_step(bb, 2, PLBM_BATCH_PERSISTENT);
+                if (st != PLBM_OK) return st;
+                BCK(cudaEventRecord(e0, b->stream));
+                st = plbm_batch_step(bb, steps_per_trial, PLBM_BATCH_PERSISTENT);
+                if (st != PLBM_OK) return st;
+                BCK(cudaEventRecord(e1, b->stream));
+                BCK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                BCK(cudaEventElapsedTime(&ms, e0, e1));
+                const double per = ms / steps_per_trial;
+                if (per < best) {
+                    best = per;
+                    bx_best = bx;
+                    cps_best = cps;
+                    order_best = order;
+                }
+                if (!any_pairs) break;
             }
         }
     }

@@ -7,6 +7,8 @@
 
 #include <cuda_runtime.h>
 
+#include "plbm.h"
+
 namespace plbm {
 
 constexpr int kMaxQ1 = 8;
@@ -56,6 +58,13 @@ struct LatticeParams {
     float ghostLg[kMaxQ], ghostRg[kMaxQ];   // the same as deviations from w0 (FP32)
     unsigned* status;            // device status word (PLBM_STATUS_* bits)
     double* partials;            // reduction scratch, kPartialStride doubles per block
+};
+
+// Where a lattice of a batch in the plain layout sits: its two population
+// arrays and its first tile in the batch's tile list (tiles_x tiles per row).
+struct NodeSpan {
+    void* f[2];
+    int nx, tiles_x, tile_begin, pad_;
 };
 
 // Compact parameters of the row-paired kernel (one lattice).  The batched
@@ -109,6 +118,15 @@ inline PairParams pair_params(const LatticeParams& P) {
 double spectral_radius(int dim, int q1, const int* v, const double* C, double omega, double theta0,
                        bool isothermal, double ux, int nk, double stop_above);
 
+// Error flag of the tensor-core kernels and the budget of each of their bounded
+// waits: a wait that runs longer sets *flag, and the kernel stops issuing work,
+// drains the MMAs it issued (a fixed 2 s bound, whatever the budget), frees its
+// tensor memory and returns.
+struct TcErr {
+    unsigned* flag;
+    unsigned long long wait_ns;
+};
+
 // Surrogate kernels (plbm_cnn.cu, plbm_ce.cu).
 cudaError_t cnn_conv64_fwd(int B, int H, int W, const void* X, const void* Wt, const float* bias, const void* mask,
                            void* Y, int mode, int relu, cudaStream_t s);
@@ -116,10 +134,10 @@ int cnn_wgrad64_parts(int B, int H, int W);
 cudaError_t cnn_conv64_wgrad(int B, int H, int W, const void* X, const void* dY, float* partial, float* partial_b,
                              float* dW, float* db, cudaStream_t s);
 cudaError_t cnn_conv64_wgrad_tc(int B, int H, int W, const void* X, const void* dY, float* partial, float* partial_b,
-                                float* dW, float* db, unsigned* err, cudaStream_t s);
+                                float* dW, float* db, TcErr err, cudaStream_t s);
 cudaError_t cnn_sum_partials(const float* partial, int nparts, int n, float* out, cudaStream_t s);
 cudaError_t cnn_conv_in_wgrad_tc(int B, int H, int W, const void* X, const void* dY, float* partial, float* partial_b,
-                                 float* dW, float* db, unsigned* err, cudaStream_t s);
+                                 float* dW, float* db, TcErr err, cudaStream_t s);
 cudaError_t cnn_conv_thin_fwd(int ci, int co, int ti, int to, int B, int H, int W, const void* X, const float* Wf,
                               const float* bias, const void* mask, void* Y, int mode, int relu, cudaStream_t s);
 int cnn_thin_parts(int B, int H, int W, int* pix_per_block);
@@ -128,12 +146,12 @@ cudaError_t cnn_conv_thin_wgrad(int ci, int co, int tx, int tg, int B, int H, in
 cudaError_t cnn_flip64(const void* W, void* Wb, cudaStream_t s);
 cudaError_t cnn_flip_thin(const float* W, int ci, int co, float* Wb, cudaStream_t s);
 cudaError_t cnn_conv64_tc(int B, int H, int W, const void* X, const void* Wk, const float* bias, const void* mask,
-                          void* Y, int mode, int relu, unsigned* err, cudaStream_t s);
+                          void* Y, int mode, int relu, TcErr err, cudaStream_t s);
 cudaError_t cnn_weights_kmajor(const void* W, void* Wf, void* Wb, cudaStream_t s);
 cudaError_t cnn_conv_out_tc(int B, int H, int W, const void* X, const void* Wo, const float* bias, float* Y,
-                            unsigned* err, cudaStream_t s);
+                            TcErr err, cudaStream_t s);
 cudaError_t cnn_conv_in_tc(int B, int H, int W, const void* X, const void* Win, const float* bias, void* Y, int relu,
-                           unsigned* err, cudaStream_t s);
+                           TcErr err, cudaStream_t s);
 cudaError_t cnn_weights_out16(const float* W, void* Wo, cudaStream_t s);
 cudaError_t cnn_weights_in(const float* W, void* Win, cudaStream_t s);
 cudaError_t cnn_mse(const float* pred, const float* target, long long n, long long npix, float lam, float* merr,
@@ -172,6 +190,8 @@ struct HandleView {
     long long* steps;
 };
 bool handle_view(void* h, HandleView* out);
+// Whether plbm_create gives this descriptor the row-paired layout.
+bool desc_row_paired(const plbm_desc* d);
 
 // Records the error text returned by plbm_last_error(NULL) for this thread.
 void set_thread_error(const char* msg);
@@ -181,12 +201,25 @@ void set_thread_error(const char* msg);
 cudaError_t launch_step(int prec, const LatticeParams& P, const void* src, void* dst,
                         bool reduce, cudaStream_t stream);
 // Rows [y0, y1) (y1 < 0: to the last row); field pointers index the whole lattice.
+// Batched step of 2D lattices in the plain layout, all of precision prec and
+// q1 velocities per axis (q1 = 3, 4 or 5): tiles of kBlockX nodes of one row.
+cudaError_t launch_batch_node(int prec, int q1, const LatticeParams* inst, const NodeSpan* span, int total_tiles,
+                              int ctas, int parity, const unsigned short* tile_inst, cudaStream_t stream);
+cudaError_t batch_node_occupancy(int prec, int q1, int* blocks_per_sm);
 cudaError_t launch_init(int prec, const LatticeParams& P, const double* rho, const double* ux,
                         const double* uy, const double* theta, void* f, cudaStream_t stream, int y0 = 0,
                         int y1 = -1);
 cudaError_t launch_moments(int prec, const LatticeParams& P, const void* f, double* rho,
                            double* ux, double* uy, double* theta, cudaStream_t stream, int y0 = 0,
                            int y1 = -1);
+// Up to five FP64 field arrays of n values; rho and theta index the fields that
+// must be positive (-1: none).  Null pointers are not allowed in field[0..count).
+struct FieldSet {
+    const double* field[5];
+    int count, rho, theta;
+};
+// Sets PLBM_STATUS_* bits in *status for non-finite values, rho <= 0, theta <= 0.
+cudaError_t launch_check_fields(const FieldSet& F, long long n, unsigned* status, cudaStream_t stream);
 // Three-dimensional lattices (plbm_step3.cu): storage [q][nz][ny][pitch].
 long long reduce3_blocks(const LatticeParams& P);
 cudaError_t launch_step3(int prec, const LatticeParams& P, const void* src, void* dst, cudaStream_t s);

@@ -17,4 +17,11 @@ cudaError_t launch_batch_f32(const PairParams* inst, int ninst, int total_tiles,
 cudaError_t batch_occupancy_f32(int block_x, int* blocks_per_sm) {
     return batch_occupancy_t<float>(block_x, blocks_per_sm);
 }
+cudaError_t launch_batch_node_f32(int q1, const LatticeParams* inst, const NodeSpan* span, int total_tiles, int ctas,
+                                 int parity, const unsigned short* tile_inst, cudaStream_t stream) {
+    return launch_batch_node_t<float>(q1, inst, span, total_tiles, ctas, parity, tile_inst, stream);
+}
+cudaError_t batch_node_occupancy_f32(int q1, int* blocks_per_sm) {
+    return batch_node_occupancy_t<float>(q1, blocks_per_sm);
+}
 }  // namespace plbm

@@ -139,6 +139,8 @@ class Instance:
     kind: str            # "kh" or "shear"
     seed: int
     fields: tuple = field(default=(), repr=False)
+    prec: str | None = None      # storage precision; None: the batch's
+    isothermal: bool = False     # theta in f^eq held at theta0 (Eq. eq:1d3v models)
 
 
 def batch_candidates(n: int = 256, seed: int = 1000, size_lo: int = 64, size_hi: int = 1024,
@@ -146,9 +148,9 @@ def batch_candidates(n: int = 256, seed: int = 1000, size_lo: int = 64, size_hi:
                      max_draws: int = 64):
     """Seeded parameter draws for the batched sweep.
 
-    Instance k uses ``default_rng(seed + k)``: side L uniform over the even integers
-    of [size_lo, size_hi] (the row-paired kernels need an even row count),
-    then up to ``max_draws`` candidate (set, omega, theta) triples; the caller
+    Instance k uses ``default_rng(seed + k)``: side L uniform over the integers of
+    [size_lo, size_hi] (odd and even alike), then up to ``max_draws`` candidate
+    (set, omega, theta) triples; the caller
     keeps the first one that its admissibility gate accepts.  Even k are
     Kelvin-Helmholtz layers, odd k shear waves.
     Returns a list of (index, L, kind, [(v, omega, theta), ...]).
@@ -156,7 +158,7 @@ def batch_candidates(n: int = 256, seed: int = 1000, size_lo: int = 64, size_hi:
     out = []
     for k in range(n):
         rng = np.random.default_rng(seed + k)
-        L = 2 * int(rng.integers(size_lo // 2, size_hi // 2 + 1))
+        L = int(rng.integers(size_lo, size_hi + 1))
         cands = []
         for _ in range(max_draws):
             v = sets[int(rng.integers(0, len(sets)))]

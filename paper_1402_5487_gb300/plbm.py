@@ -101,6 +101,7 @@ SIGNATURES = {
     "plbm_batch_tune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_int), _D]),
     "plbm_batch_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "plbm_batch_groups": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int)] * 3),
     "plbm_create": (ctypes.c_int, [ctypes.POINTER(PlbmDesc), ctypes.POINTER(_H)]),
     "plbm_destroy": (ctypes.c_int, [_H]),
     "plbm_init": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -122,6 +123,23 @@ SIGNATURES = {
     "plbm_get_info": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_size_t)]),
     "plbm_device_populations": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_void_p)]),
+    "plbm_slab_rows": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int)]),
+    "plbm_halo_width": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "plbm_halo_plan": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "plbm_slabs_create": (ctypes.c_int, [ctypes.POINTER(PlbmDesc), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    "plbm_slabs_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "plbm_slabs_slab": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(_H),
+                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "plbm_slabs_init": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 4),
+    "plbm_slabs_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_long]),
+    "plbm_slabs_moments": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 4),
+    "plbm_slabs_get_populations": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "plbm_slabs_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "plbm_checkpoint_bytes": (ctypes.c_size_t, [_H]),
+    "plbm_checkpoint_save": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_size_t]),
+    "plbm_checkpoint_load": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_size_t]),
     "plbm_diagnostics_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                                  ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                                  ctypes.c_void_p, ctypes.c_void_p]),
@@ -408,6 +426,18 @@ class Solver:
         assert tuple(f.shape) == self._pop_shape()
         _ok(lib().plbm_set_populations(self.h, _ptr(f), on, int(step)), self.h)
 
+    def checkpoint(self) -> np.ndarray:
+        """Header + stored populations + checksum (plbm_checkpoint_save), as bytes."""
+        n = int(lib().plbm_checkpoint_bytes(self.h))
+        buf = np.empty(n, dtype=np.uint8)
+        _ok(lib().plbm_checkpoint_save(self.h, buf.ctypes.data, n), self.h)
+        return buf
+
+    def restore(self, buf) -> int:
+        """plbm_checkpoint_load; returns the status (PLBM_E_CHECKSUM is not raised)."""
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        return int(lib().plbm_checkpoint_load(self.h, buf.ctypes.data, buf.size))
+
     def info(self):
         q, pitch, nb = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
         _ok(lib().plbm_get_info(self.h, ctypes.byref(q), ctypes.byref(pitch), ctypes.byref(nb)), self.h)
@@ -430,3 +460,83 @@ class Solver:
         p = ctypes.c_void_p()
         _ok(lib().plbm_device_populations(self.h, ctypes.byref(p)), self.h)
         return int(p.value)
+
+
+# ---------------------------------------------------------------------------
+# Domain decomposition along y (plbm_slab_rows, plbm_halo_plan, plbm_slabs_*).
+# ---------------------------------------------------------------------------
+def slab_rows(ny: int, nslabs: int, k: int):
+    """(y0, rows) of slab k (host computation of the library)."""
+    y0, rows = ctypes.c_int(), ctypes.c_int()
+    _ok(lib().plbm_slab_rows(int(ny), int(nslabs), int(k), ctypes.byref(y0), ctypes.byref(rows)))
+    return y0.value, rows.value
+
+
+def halo_width(v) -> int:
+    va = (ctypes.c_int * len(v))(*[int(a) for a in v])
+    return int(lib().plbm_halo_width(len(v), va))
+
+
+def halo_plan(v, side: int):
+    """Populations a slab's halo needs: side -1 the rows below (v_y > 0), +1 above (v_y < 0)."""
+    q1 = len(v)
+    va = (ctypes.c_int * q1)(*[int(a) for a in v])
+    pops = (ctypes.c_int * (q1 * q1))()
+    n = ctypes.c_int()
+    _ok(lib().plbm_halo_plan(q1, va, int(side), pops, ctypes.byref(n)))
+    return [pops[i] for i in range(n.value)]
+
+
+class Slabs:
+    """A periodic 2D lattice split along y into slabs that exchange halo rows (one device)."""
+
+    def __init__(self, v, omega, nx, ny, nslabs, theta0=1.0, prec="f32", device=0, u_max=0.0, stream=None):
+        """stream: a torch.cuda.Stream (not the default stream) for every launch; None: the library's own."""
+        self.v, self.nx, self.ny, self.n = tuple(int(a) for a in v), int(nx), int(ny), int(nslabs)
+        self.q = len(v) ** 2
+        self.stream = stream
+        desc, self._keep = make_desc(2, v, omega, nx, ny, theta0=theta0, prec=prec, device=device, u_max=u_max,
+                                     stream=None if stream is None else stream.cuda_stream)
+        s = ctypes.c_void_p()
+        st = lib().plbm_slabs_create(ctypes.byref(desc), self.n, ctypes.byref(s))
+        if st != PLBM_OK:
+            raise PlbmError(st, lib().plbm_slabs_last_error(None).decode())
+        self.s = s
+
+    def _ok(self, st):
+        if st != PLBM_OK:
+            raise PlbmError(st, lib().plbm_slabs_last_error(self.s).decode())
+
+    def init(self, rho, ux, uy, theta):
+        arrs = [np.ascontiguousarray(np.broadcast_to(a, (self.ny, self.nx)), dtype=np.float64)
+                for a in (rho, ux, uy, theta)]
+        self._ok(lib().plbm_slabs_init(self.s, *[a.ctypes.data for a in arrs]))
+
+    def step(self, n=1):
+        self._ok(lib().plbm_slabs_step(self.s, int(n)))
+
+    def moments(self):
+        out = [np.empty((self.ny, self.nx)) for _ in range(4)]
+        self._ok(lib().plbm_slabs_moments(self.s, *[a.ctypes.data for a in out]))
+        return tuple(out)
+
+    def get_populations(self):
+        f = np.empty((self.q, self.ny, self.nx))
+        self._ok(lib().plbm_slabs_get_populations(self.s, f.ctypes.data))
+        return f
+
+    def slab(self, k):
+        h, y0, rows = _H(), ctypes.c_int(), ctypes.c_int()
+        self._ok(lib().plbm_slabs_slab(self.s, int(k), ctypes.byref(h), ctypes.byref(y0), ctypes.byref(rows)))
+        return h, y0.value, rows.value
+
+    def close(self):
+        if getattr(self, "s", None):
+            lib().plbm_slabs_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,5 +1,8 @@
 """Batched runner on the GPU: the four launch schemes agree bit for bit, agree
-with single-lattice handles, and match the FP64 oracle per instance."""
+with single-lattice handles, and match the FP64 oracle per instance.  The
+instances of the sweep have odd and even sides (reading R10: any integer side),
+so a batch holds row-paired lattices and plain-layout ones; a mixed batch adds
+FP64, FP16, isothermal D2Q9 and D2Q16 lattices."""
 import numpy as np
 import pytest
 
@@ -20,7 +23,21 @@ def _lib():
 @pytest.fixture(scope="module")
 def small_instances():
     inst, _ = B.draw_instances(10, seed=4242, size_lo=16, size_hi=150)
+    assert any(i.L % 2 for i in inst) and any(i.L % 2 == 0 for i in inst)
     return inst
+
+
+def _mixed():
+    """Lattices of every group kind: row-paired FP32 and FP16, plain-layout FP32 (odd
+    side), FP64, FP16 (odd side), isothermal D2Q9 and isothermal D2Q16."""
+    mk = lambda k, L, v, om, th, kind, prec=None, iso=False: I.Instance(
+        index=k, L=L, v=v, omega=om, theta0=th, kind=kind, seed=700 + k, prec=prec, isothermal=iso)
+    return [mk(0, 37, I.SET_013, 1.3, 1.0, "kh"), mk(1, 40, I.SET_012, 1.2, 0.7, "kh"),
+            mk(2, 33, I.SET_013, 1.1, 0.9, "shear", prec="f64"), mk(3, 36, I.SET_013, 1.25, 1.0, "kh", prec="f16dev"),
+            mk(4, 35, I.SET_012, 1.0, 0.8, "shear", prec="f16dev"),
+            mk(5, 30, (0, 1, -1), 1.2, 1.0 / 3.0, "shear", iso=True),
+            mk(6, 25, (1, -1, 3, -3), 1.1, 4.0 / 3.0, "shear", iso=True),
+            mk(7, 64, I.SET_013, 1.3, 1.0, "kh", prec="f64")]
 
 
 def _run(instances, mode, steps, prec="f32", config=None, order=None):
@@ -109,4 +126,43 @@ def test_instance_handles_are_owned_by_the_batch(small_instances):
     b = B.Batch(small_instances[:2])
     h = b.solvers[0].h
     assert plbm.lib().plbm_destroy(h) == plbm.PLBM_E_STATE
+    b.close()
+
+
+def test_mixed_batch_groups_schemes_and_single_handles():
+    inst = _mixed()
+    b = B.Batch(inst, prec="f32")
+    paired, plain, launches = b.groups()
+    assert (paired, plain) == (2, 6) and launches == 7   # pairs f32, f16; plain f32 q5, f64 q5, f16 q5, f32 q3, f32 q4
+    b.close()
+    ref, st = _run(inst, "persistent", 9)
+    assert st[0] == plbm.PLBM_OK
+    for mode in ("persistent_graph", "per_instance", "per_instance_graph"):
+        got, _ = _run(inst, mode, 9)
+        for a, c in zip(got, ref):
+            assert np.array_equal(a, c), mode
+    for i, g in zip(inst, ref):
+        s = plbm.Solver(2, i.v, i.omega, i.L, i.L, theta0=i.theta0, prec=i.prec or "f32", isothermal=i.isothermal)
+        rho, ux, uy, th = I.instance_fields(i)
+        s.init(rho, ux, uy, None if i.isothermal else th)
+        s.step(9)
+        assert np.array_equal(s.get_populations(), g), i
+        s.close()
+
+
+def test_mixed_batch_instances_vs_oracle_100_steps():
+    inst = _mixed()
+    b = B.Batch(inst, prec="f32")
+    b.init()
+    b.step(100, "persistent_graph")
+    tol = {"f64": 1e-12, "f32": 1e-5, "f16dev": 5e-3}
+    for i, s in zip(inst, b.solvers):
+        _, _, mo = oracle_run(2, i.v, i.omega, i.L, i.L, I.instance_fields(i), 100, theta0=i.theta0,
+                              isothermal=i.isothermal)
+        mg = s.moments()
+        e = field_errors(mg, mo)
+        du = np.max(np.hypot(mg[1] - mo[1], mg[2] - mo[2])) / 0.1
+        t = tol[i.prec or "f32"]
+        assert e["rho"] <= t and e["theta"] <= t and du <= t, (i, e, du)
+    assert b.check()[0] == plbm.PLBM_OK
     b.close()

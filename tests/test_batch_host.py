@@ -48,7 +48,8 @@ def test_draws_are_admissible_and_deterministic():
     inst, stats = B.draw_instances(24, seed=77)
     inst2, _ = B.draw_instances(24, seed=77)
     assert [(a.L, a.v, a.omega, a.theta0) for a in inst] == [(a.L, a.v, a.omega, a.theta0) for a in inst2]
-    assert all(a.L % 2 == 0 and 64 <= a.L <= 1024 for a in inst)
+    assert all(64 <= a.L <= 1024 for a in inst)
+    assert any(a.L % 2 for a in inst) and any(a.L % 2 == 0 for a in inst)   # R10: every integer side
     assert all(a.v != I.SET_023 for a in inst)  # its u = 0 window is 4/3 < theta < 3
     for a in inst[:6]:
         lat = O.Lattice(2, a.v, a.omega, 4, 4, theta0=a.theta0)
