@@ -275,10 +275,9 @@ plbm_status plbm_device_populations(plbm_handle h, void **ptr);
  * parameter sweeps over its models.  Each instance is an ordinary handle
  * (plbm_batch_instance) for init, moments, diagnostics and checkpoints; the
  * batch advances all of them with one of four launch schemes:
- *   PLBM_BATCH_PERSISTENT           one persistent launch per step for all
- *                                   instances (CTAs walk contiguous ranges of a
- *                                   global tile list; per-instance parameters in
- *                                   a device table);
+ *   PLBM_BATCH_PERSISTENT           one persistent launch per step and group of
+ *                                   instances (CTAs walk a global tile list;
+ *                                   per-instance parameters in a device table);
  *   PLBM_BATCH_PERSISTENT_GRAPH     the same, two steps per CUDA graph replay;
  *   PLBM_BATCH_PER_INSTANCE         one launch per instance per step;
  *   PLBM_BATCH_PER_INSTANCE_GRAPH   the same, captured in a CUDA graph.
@@ -296,9 +295,10 @@ typedef struct plbm_batch_s *plbm_batch;
  * the row-paired layout).  Instances may differ in size, velocity set, omega,
  * theta0, storage precision, boundary and model (thermal or isothermal).  The
  * batch advances them in groups, one persistent launch per group and step:
- * instances in the row-paired layout (periodic thermal v = (0, a, -a, b, -b),
- * even ny, FP32/FP16/BF16 storage) by the two-nodes-per-thread kernel, one group
- * per precision; all others (odd ny, FP64 storage, isothermal models, other
+ * periodic thermal lattices with v = (0, a, -a, b, -b) and FP32/FP16/BF16
+ * storage by the kernel of the row-paired layout, one group per precision
+ * (even ny: a node pair per thread; odd ny: the plain layout, one node per
+ * thread, same arithmetic); all others (FP64 storage, isothermal models, other
  * velocity sets) by a one-node-per-thread kernel, one group per (precision, q1).
  * One device allocation holds all instances' populations; descs[i].workspace
  * and .stream are ignored.  stream: cudaStream_t for every launch (NULL: the
@@ -306,8 +306,9 @@ typedef struct plbm_batch_s *plbm_batch;
  * legacy default stream).  Synchronous. */
 plbm_status plbm_batch_create(const plbm_desc *descs, int n, void *stream, plbm_batch *out);
 
-/* How the batch splits: instances in the row-paired groups, instances in the
- * plain-layout groups, and persistent launches per step (one per group). */
+/* How the batch splits: instances in the five-velocity thermal 16/32-bit groups
+ * (row-paired or plain layout), instances in the other groups, and persistent
+ * launches per step (one per group). */
 plbm_status plbm_batch_groups(plbm_batch b, int *paired_instances, int *plain_instances, int *launches_per_step);
 
 /* Release the batch, its instances and its memory.  Accepts NULL. */

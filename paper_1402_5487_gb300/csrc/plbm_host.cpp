@@ -1223,13 +1223,13 @@ plbm_status batch_table(Batch* b) {
         for (plbm::PairParams& Q : g.table) {
             Q.tiles_x = (Q.nx + b->block_x - 1) / b->block_x;
             Q.tile_begin = tile;
-            tile += Q.tiles_x * Q.half_ny;
+            tile += Q.tiles_x * plbm::tile_rows(Q);
         }
         g.total_tiles = tile;
         std::vector<unsigned short> ti((size_t)tile);
         for (size_t i = 0; i < g.table.size(); ++i) {
             const plbm::PairParams& Q = g.table[i];
-            std::fill(ti.begin() + Q.tile_begin, ti.begin() + Q.tile_begin + Q.tiles_x * Q.half_ny,
+            std::fill(ti.begin() + Q.tile_begin, ti.begin() + Q.tile_begin + Q.tiles_x * plbm::tile_rows(Q),
                       (unsigned short)i);
         }
         BCK(cudaMemcpyAsync(g.d_table, g.table.data(), sizeof(plbm::PairParams) * g.table.size(),
@@ -1278,7 +1278,11 @@ plbm_status batch_launch(Batch* b, int scheme, int parity, int ctas) {
 plbm_status batch_groups(Batch* b) {
     for (size_t i = 0; i < b->inst.size(); ++i) {
         const Handle* h = b->inst[i];
-        if (h->P.paired) {
+        // the two-nodes-per-thread kernel's groups also take the plain-layout lattices of
+        // the same arithmetic (symmetric five-velocity thermal sets, 16/32-bit storage)
+        const bool sym5_group = h->P.paired || (h->P.dim == 2 && h->P.sym5 && !h->P.isothermal &&
+                                                !h->P.fixed_ends && h->prec != plbm::kF64);
+        if (sym5_group) {
             PairGroup* g = nullptr;
             for (PairGroup& c : b->pairs)
                 if (c.prec == h->prec) g = &c;
@@ -1288,7 +1292,7 @@ plbm_status batch_groups(Batch* b) {
                 g->prec = h->prec;
             }
             g->members.push_back((int)i);
-            g->max_tiles += (size_t)((h->P.nx + 63) / 64) * (size_t)h->P.half_ny;
+            g->max_tiles += (size_t)((h->P.nx + 63) / 64) * (size_t)(h->P.paired ? h->P.half_ny : h->P.ny);
         } else {
             if (h->P.dim != 2 || h->P.q1 < 3 || h->P.q1 > 5) {
                 batch_err(b, "instance %zu: the batched runner takes 2D lattices with 3 to 5 velocities per axis", i);

@@ -80,8 +80,12 @@ struct PairParams {
     unsigned* status;
     double* partials;
     void* f[2];                   // population arrays (batched runner; unused by single launches)
-    int tile_begin, tiles_x;      // batched runner: first global tile, tiles per pair row
+    int tile_begin, tiles_x;      // batched runner: first global tile, tiles per pair row (per row, plain)
+    int paired;                   // 1: row-paired layout, plane2 in pairs; 0: plain, plane2 in elements
 };
+
+// Rows of tiles of a lattice in the batched runner: pair rows or rows.
+inline int tile_rows(const PairParams& Q) { return Q.paired ? Q.half_ny : Q.ny; }
 
 inline PairParams pair_params(const LatticeParams& P) {
     PairParams Q{};
@@ -89,7 +93,8 @@ inline PairParams pair_params(const LatticeParams& P) {
     Q.ny = P.ny;
     Q.half_ny = P.half_ny;
     Q.pitch = P.pitch;
-    Q.plane2 = (long long)P.half_ny * P.pitch;
+    Q.paired = P.paired;
+    Q.plane2 = P.paired ? (long long)P.half_ny * P.pitch : P.plane;
     for (int i = 0; i < 5; ++i) {
         Q.vxm[i] = P.vxm[i];
         Q.vym[i] = P.vym[i];

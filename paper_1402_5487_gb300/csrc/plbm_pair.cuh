@@ -36,6 +36,23 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, f2(-b.x, -b.y)); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// The same operations on one node (plain layout): each is the single-lane form of
+// the packed one above, correctly rounded and never contracted, so a node gets
+// bit for bit the same result whichever layout and kernel update it.
+__device__ __forceinline__ float add2(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub2(float a, float b) { return __fadd_rn(a, -b); }
+__device__ __forceinline__ float mul2(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fma2(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <class V>
+__device__ __forceinline__ V splat(float a);
+template <>
+__device__ __forceinline__ float2 splat<float2>(float a) { return f2s(a); }
+template <>
+__device__ __forceinline__ float splat<float>(float a) { return a; }
+__device__ __forceinline__ float2 neg2(float2 a) { return f2(-a.x, -a.y); }
+__device__ __forceinline__ float neg2(float a) { return -a; }
+__device__ __forceinline__ float2 rcp2(float2 a) { return f2(__frcp_rn(a.x), __frcp_rn(a.y)); }
+__device__ __forceinline__ float rcp2(float a) { return __frcp_rn(a); }
 
 // Storage of one node pair.
 template <typename S>
@@ -88,32 +105,32 @@ struct PairStore<__nv_bfloat16> {
 
 // dmu_1..dmu_4 = mu_n(u, theta) - mu_n(0, theta0) from mu_{n+1} = u mu_n + n theta mu_{n-1}
 // with mu(0, theta0) = (1, 0, theta0, 0, 3 theta0^2), then dr by the constraint form.
-__device__ __forceinline__ void sym5_axis(const PairParams& P, float2 u, float2 th, float2 dth,
-                                          float2 (&dr)[5]) {
-    const float2 th0 = f2s(P.theta0f);
-    const float2 d1 = u;
-    const float2 d2 = fma2(u, u, dth);
-    const float2 d3 = mul2(u, add2(add2(th0, d2), add2(th, th)));
-    const float2 d4 = fma2(u, d3, mul2(f2s(3.0f), fma2(th, d2, mul2(dth, th0))));
-    const float2 Ob = mul2(fma2(f2s(-P.sa2), d1, d3), f2s(P.kOb));
-    const float2 Oa = mul2(fma2(f2s(-2.0f * P.sb), Ob, d1), f2s(P.kOa));
-    const float2 Eb = mul2(fma2(f2s(-P.sa2), d2, d4), f2s(P.kEb));
-    const float2 Ea = mul2(fma2(f2s(-2.0f * P.sb2), Eb, d2), f2s(P.kEa));
-    dr[0] = mul2(f2s(-2.0f), add2(Ea, Eb));
+// V = float2: the two nodes of a pair; V = float: one node.
+template <class V>
+__device__ __forceinline__ void sym5_axis(const PairParams& P, V u, V th, V dth, V (&dr)[5]) {
+    const V th0 = splat<V>(P.theta0f);
+    const V d1 = u;
+    const V d2 = fma2(u, u, dth);
+    const V d3 = mul2(u, add2(add2(th0, d2), add2(th, th)));
+    const V d4 = fma2(u, d3, mul2(splat<V>(3.0f), fma2(th, d2, mul2(dth, th0))));
+    const V Ob = mul2(fma2(splat<V>(-P.sa2), d1, d3), splat<V>(P.kOb));
+    const V Oa = mul2(fma2(splat<V>(-2.0f * P.sb), Ob, d1), splat<V>(P.kOa));
+    const V Eb = mul2(fma2(splat<V>(-P.sa2), d2, d4), splat<V>(P.kEb));
+    const V Ea = mul2(fma2(splat<V>(-2.0f * P.sb2), Eb, d2), splat<V>(P.kEa));
+    dr[0] = mul2(splat<V>(-2.0f), add2(Ea, Eb));
     dr[1] = add2(Ea, Oa);
     dr[2] = sub2(Ea, Oa);
     dr[3] = add2(Eb, Ob);
     dr[4] = sub2(Eb, Ob);
 }
 
-// sum(p), col(p): pulled deviation p of both nodes, read for the moment sums and
-// for the collision; out: post-collision deviations.  Returns rho and theta of
-// both nodes (for the status check and reductions).
-template <class GetSum, class GetCol>
-__device__ __forceinline__ void sym5_collide(const PairParams& P, GetSum sum, GetCol col, float2 (&out)[25],
-                                             float2& rho_o, float2& th_o, float2& drho_o, float2& jx_o,
-                                             float2& jy_o, float2& e_o) {
-    float2 S[5], T[5];
+// sum(p), col(p): pulled deviation p of the node(s), read for the moment sums
+// and for the collision; out: post-collision deviations.  Returns rho and theta
+// (for the status check and reductions).
+template <class V, class GetSum, class GetCol>
+__device__ __forceinline__ void sym5_collide(const PairParams& P, GetSum sum, GetCol col, V (&out)[25], V& rho_o,
+                                             V& th_o, V& drho_o, V& jx_o, V& jy_o, V& e_o) {
+    V S[5], T[5];
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
         S[i] = add2(add2(sum(5 * i), sum(5 * i + 1)), add2(add2(sum(5 * i + 2), sum(5 * i + 3)), sum(5 * i + 4)));
@@ -122,20 +139,19 @@ __device__ __forceinline__ void sym5_collide(const PairParams& P, GetSum sum, Ge
     for (int j = 0; j < 5; ++j) {
         T[j] = add2(add2(sum(j), sum(5 + j)), add2(add2(sum(10 + j), sum(15 + j)), sum(20 + j)));
     }
-    const float2 a = f2s(P.sa), b = f2s(P.sb), a2 = f2s(P.sa2), b2 = f2s(P.sb2);
-    const float2 drho = add2(add2(S[0], S[1]), add2(add2(S[2], S[3]), S[4]));
-    const float2 jx = fma2(a, sub2(S[1], S[2]), mul2(b, sub2(S[3], S[4])));
-    const float2 ex = fma2(a2, add2(S[1], S[2]), mul2(b2, add2(S[3], S[4])));
-    const float2 jy = fma2(a, sub2(T[1], T[2]), mul2(b, sub2(T[3], T[4])));
-    const float2 ey = fma2(a2, add2(T[1], T[2]), mul2(b2, add2(T[3], T[4])));
-    const float2 rho = add2(f2s(1.0f), drho);
-    const float2 inv = f2(__frcp_rn(rho.x), __frcp_rn(rho.y));
-    const float2 ux = mul2(jx, inv), uy = mul2(jy, inv);
-    const float2 uu = fma2(ux, ux, mul2(uy, uy));
+    const V a = splat<V>(P.sa), b = splat<V>(P.sb), a2 = splat<V>(P.sa2), b2 = splat<V>(P.sb2);
+    const V drho = add2(add2(S[0], S[1]), add2(add2(S[2], S[3]), S[4]));
+    const V jx = fma2(a, sub2(S[1], S[2]), mul2(b, sub2(S[3], S[4])));
+    const V ex = fma2(a2, add2(S[1], S[2]), mul2(b2, add2(S[3], S[4])));
+    const V jy = fma2(a, sub2(T[1], T[2]), mul2(b, sub2(T[3], T[4])));
+    const V ey = fma2(a2, add2(T[1], T[2]), mul2(b2, add2(T[3], T[4])));
+    const V rho = add2(splat<V>(1.0f), drho);
+    const V inv = rcp2(rho);
+    const V ux = mul2(jx, inv), uy = mul2(jy, inv);
+    const V uu = fma2(ux, ux, mul2(uy, uy));
     // 2 rho theta = 2 theta0 + sum |v|^2 g - rho |u|^2  =>  theta - theta0:
-    const float2 dth = mul2(f2s(0.5f), fma2(fma2(f2s(-2.0f * P.theta0f), drho, add2(ex, ey)), inv,
-                                            f2(-uu.x, -uu.y)));
-    const float2 th = add2(f2s(P.theta0f), dth);
+    const V dth = mul2(splat<V>(0.5f), fma2(fma2(splat<V>(-2.0f * P.theta0f), drho, add2(ex, ey)), inv, neg2(uu)));
+    const V th = add2(splat<V>(P.theta0f), dth);
     rho_o = rho;
     th_o = th;
     drho_o = drho;
@@ -143,7 +159,7 @@ __device__ __forceinline__ void sym5_collide(const PairParams& P, GetSum sum, Ge
     jy_o = jy;
     e_o = add2(ex, ey);
 
-    float2 dx[5], dy[5];
+    V dx[5], dy[5];
     sym5_axis(P, ux, th, dth, dx);
     sym5_axis(P, uy, th, dth, dy);
 
@@ -151,20 +167,20 @@ __device__ __forceinline__ void sym5_collide(const PairParams& P, GetSum sum, Ge
     // f^eq - w0 = drho w_i w_j + rho (dx_i r^y_j + w_i dy_j),  r^y_j = w_j + dy_j:
     //   g'_ij = (1 - omega) g_ij + A_i r^y_j + w_i Y_j,
     //   A_i = omega rho dx_i,  Y_j = omega (rho dy_j + drho w_j).
-    const float2 om = f2s(P.omegaf);
-    const float2 orho = mul2(om, rho);
-    const float2 odrho = mul2(om, drho);
-    const float2 keep = f2s(1.0f - P.omegaf);
-    float2 ry[5], Y[5];
+    const V om = splat<V>(P.omegaf);
+    const V orho = mul2(om, rho);
+    const V odrho = mul2(om, drho);
+    const V keep = splat<V>(1.0f - P.omegaf);
+    V ry[5], Y[5];
 #pragma unroll
     for (int j = 0; j < 5; ++j) {
-        ry[j] = add2(f2s(P.w1f[j]), dy[j]);
-        Y[j] = fma2(orho, dy[j], mul2(odrho, f2s(P.w1f[j])));
+        ry[j] = add2(splat<V>(P.w1f[j]), dy[j]);
+        Y[j] = fma2(orho, dy[j], mul2(odrho, splat<V>(P.w1f[j])));
     }
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
-        const float2 A = mul2(orho, dx[i]);
-        const float2 w = f2s(P.w1f[i]);
+        const V A = mul2(orho, dx[i]);
+        const V w = splat<V>(P.w1f[i]);
 #pragma unroll
         for (int j = 0; j < 5; ++j) {
             const int p = 5 * i + j;
@@ -235,11 +251,12 @@ __device__ __forceinline__ void pair_node(const PairParams& P, const typename Pa
     if constexpr (PS::kReconvert) {
         typename PS::V v[25];
         pull25<PS>(src, plane2, row, col, swp, any_swap, v, [](typename PS::V a) { return a; });
-        sym5_collide(P, [&](int p) { return PS::cvt(v[p]); }, [&](int p) { return PS::cvt_again(v[p]); }, o,
-                     rho, th, drho, jx, jy, e);
+        sym5_collide<float2>(P, [&](int p) { return PS::cvt(v[p]); }, [&](int p) { return PS::cvt_again(v[p]); },
+                             o, rho, th, drho, jx, jy, e);
     } else {
         pull25<PS>(src, plane2, row, col, swp, any_swap, o, [](typename PS::V a) { return PS::cvt(a); });
-        sym5_collide(P, [&](int p) { return o[p]; }, [&](int p) { return o[p]; }, o, rho, th, drho, jx, jy, e);
+        sym5_collide<float2>(P, [&](int p) { return o[p]; }, [&](int p) { return o[p]; }, o, rho, th, drho, jx, jy,
+                             e);
     }
     if (!healthy2(rho, th)) {
         unsigned bits = 0u;
@@ -262,6 +279,84 @@ __device__ __forceinline__ void pair_node(const PairParams& P, const typename Pa
     const unsigned here = (unsigned)(r * P.pitch + x);
 #pragma unroll
     for (int p = 0; p < 25; ++p) PS::store(dst + p * plane2 + here, o[p]);
+}
+
+// One node (x, y) of a lattice in the plain layout (storage [25][ny][pitch], plane
+// elements per population), with the single-node forms of the pair arithmetic:
+// the same result as the row-paired kernels give the node.
+template <typename S>
+struct Scalar16;
+template <>
+struct Scalar16<float> {
+    static __device__ __forceinline__ float load(const float* p) { return __ldg(p); }
+    static __device__ __forceinline__ void store(float* p, float v) { *p = v; }
+};
+template <>
+struct Scalar16<__half> {
+    static __device__ __forceinline__ float load(const __half* p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ void store(__half* p, float v) { *p = __float2half_rn(v); }
+};
+template <>
+struct Scalar16<__nv_bfloat16> {
+    static __device__ __forceinline__ float load(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ void store(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+template <typename S, bool REDUCE>
+__device__ __forceinline__ void sym5_node(const PairParams& P, const S* __restrict__ src, S* __restrict__ dst,
+                                          int x, int y, NodeDiagF& d) {
+    unsigned col[5], row[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const int s = x + P.vxm[i];
+        col[i] = (unsigned)((s >= P.nx) ? s - P.nx : s);
+        int t = y + P.vym[i];
+        t = (t >= P.ny) ? t - P.ny : t;
+        row[i] = (unsigned)t * (unsigned)P.pitch;
+    }
+    const long long plane = P.plane2;   // elements per population plane (plain layout)
+    float g[25];
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            const int p = 5 * i + j;
+            g[p] = Scalar16<S>::load(src + p * plane + (row[j] + col[i]));
+        }
+    float rho, th, drho, jx, jy, e;
+    sym5_collide<float>(P, [&](int p) { return g[p]; }, [&](int p) { return g[p]; }, g, rho, th, drho, jx, jy, e);
+    if (!((rho > 0.0f) & (th > 0.0f) & (rho < 3.0e38f) & (th < 3.0e38f))) {
+        unsigned bits = (!(rho == rho) || !(th == th) || !(rho < 3.0e38f) || !(th < 3.0e38f)) ? 1u : 0u;
+        bits |= rho <= 0.0f ? 2u : 0u;
+        bits |= th <= 0.0f ? 4u : 0u;
+        atomicOr(P.status, bits);
+    }
+    if (REDUCE) {
+        d.dmass = FF{drho, 0.0f};
+        d.jx = FF{jx, 0.0f};
+        d.jy = FF{jy, 0.0f};
+        d.denergy = FF{e, 0.0f};
+        d.rho_min = rho;
+        d.theta_min = th;
+        d.n = 1.0f;
+    }
+    const unsigned here = (unsigned)y * (unsigned)P.pitch + (unsigned)x;
+#pragma unroll
+    for (int p = 0; p < 25; ++p) Scalar16<S>::store(dst + p * plane + here, g[p]);
+}
+
+// grid = (ceil(nx / blockDim.x), ny), one node per thread (blockDim.x = kBlockX when REDUCE).
+template <typename S, bool REDUCE>
+__global__ void __launch_bounds__(kBlockX)
+k_stream_collide_sym5(const __grid_constant__ PairParams P, const S* __restrict__ src, S* __restrict__ dst) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    NodeDiagF d;
+    if (REDUCE) diagf_zero(d);
+    if (x < P.nx) sym5_node<S, REDUCE>(P, src, dst, x, blockIdx.y, d);
+    if (REDUCE) {
+        const int blk = blockIdx.y * gridDim.x + blockIdx.x;
+        block_reduce_diagf<kBlockX>(d, 2.0 * P.theta0, P.partials + (long long)blk * kPartialStride);
+    }
 }
 
 // Resident CTAs per SM the register allocation aims at: seven 128-thread CTAs
@@ -289,6 +384,24 @@ k_stream_collide_pair(const __grid_constant__ PairParams P,
     }
 }
 
+// Plain-layout symmetric five-velocity lattices (odd ny, or PLBM_FLAG_PLAIN_LAYOUT):
+// one node per thread; small lattices take 32-thread blocks (more SMs busy).
+template <typename S>
+cudaError_t launch_step_sym5_t(const LatticeParams& L, const void* src, void* dst, bool reduce,
+                               cudaStream_t stream) {
+    const PairParams P = pair_params(L);
+    int bx = kBlockX;
+    if (!reduce && (long long)((P.nx + kBlockX - 1) / kBlockX) * P.ny < 2LL * device_sm_count()) bx = 32;
+    dim3 grid((P.nx + bx - 1) / bx, P.ny);
+    const S* s = static_cast<const S*>(src);
+    S* t = static_cast<S*>(dst);
+    if (reduce)
+        k_stream_collide_sym5<S, true><<<grid, kBlockX, 0, stream>>>(P, s, t);
+    else
+        k_stream_collide_sym5<S, false><<<grid, bx, 0, stream>>>(P, s, t);
+    return cudaGetLastError();
+}
+
 template <typename S>
 cudaError_t launch_step_pair_t(const LatticeParams& L, const void* src, void* dst, bool reduce,
                                cudaStream_t stream) {
@@ -306,11 +419,22 @@ cudaError_t launch_step_pair_t(const LatticeParams& L, const void* src, void* ds
 
 // ---------------------------------------------------------------------------
 // Batched persistent step: every instance of a batch advances one step in one
-// launch.  The instances' tiles (BX threads x one pair row) form one global
-// list; CTA c walks the contiguous range [c * per_cta, (c + 1) * per_cta), so it
+// launch.  The instances' tiles (BX threads x one pair row, or x one row for a
+// lattice in the plain layout) form one global list; CTA c walks the contiguous range [c * per_cta, (c + 1) * per_cta), so it
 // meets few instance boundaries and keeps the current instance's PairParams in
 // shared memory.  `parity` selects which of each instance's two arrays is read.
 // ---------------------------------------------------------------------------
+// One thread's node(s) of a tile of the batched sweep: a node pair of pair row r
+// (row-paired lattices) or node (x, r) (plain layout, odd ny).
+template <typename S>
+__device__ __forceinline__ void batch_tile_node(const PairParams& sp, int parity, int x, int r, NodeDiagF& d) {
+    using V = typename PairStore<S>::V;
+    if (sp.paired)
+        pair_node<S, false>(sp, static_cast<const V*>(sp.f[parity]), static_cast<V*>(sp.f[parity ^ 1]), x, r, d);
+    else
+        sym5_node<S, false>(sp, static_cast<const S*>(sp.f[parity]), static_cast<S*>(sp.f[parity ^ 1]), x, r, d);
+}
+
 template <typename S, int BX>
 __global__ void __launch_bounds__(BX)
 k_batch_pair(const PairParams* __restrict__ inst, int ninst, int total_tiles, int per_cta, int parity,
@@ -339,11 +463,7 @@ k_batch_pair(const PairParams* __restrict__ inst, int ninst, int total_tiles, in
             const int local = t - sp.tile_begin;
             const int r = local / sp.tiles_x;
             const int x = (local - r * sp.tiles_x) * BX + threadIdx.x;
-            if (x < sp.nx) {
-                const V* src = static_cast<const V*>(sp.f[parity]);
-                V* dst = static_cast<V*>(sp.f[parity ^ 1]);
-                pair_node<S, false>(sp, src, dst, x, r, d);
-            }
+            if (x < sp.nx) batch_tile_node<S>(sp, parity, x, r, d);
         }
         return;
     }
@@ -380,11 +500,7 @@ k_batch_pair(const PairParams* __restrict__ inst, int ninst, int total_tiles, in
         const int local = t - sp.tile_begin;
         const int r = local / sp.tiles_x;
         const int x = (local - r * sp.tiles_x) * BX + threadIdx.x;
-        if (x < sp.nx) {
-            const V* src = static_cast<const V*>(sp.f[parity]);
-            V* dst = static_cast<V*>(sp.f[parity ^ 1]);
-            pair_node<S, false>(sp, src, dst, x, r, d);
-        }
+        if (x < sp.nx) batch_tile_node<S>(sp, parity, x, r, d);
     }
 }
 

@@ -8,6 +8,7 @@ namespace plbm {
 cudaError_t launch_step_f32(const LatticeParams& P, const void* src, void* dst, bool reduce,
                              cudaStream_t stream) {
     if (P.paired) return launch_step_pair_t<float>(P, src, dst, reduce, stream);
+    if (P.dim == 2 && P.sym5 && !P.isothermal && !P.fixed_ends) return launch_step_sym5_t<float>(P, src, dst, reduce, stream);
     return launch_step_t<float>(P, src, dst, reduce, stream);
 }
 cudaError_t launch_batch_f32(const PairParams* inst, int ninst, int total_tiles, int block_x, int ctas,

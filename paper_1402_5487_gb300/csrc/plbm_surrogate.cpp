@@ -569,14 +569,14 @@ plbm_status plbm_sur_advance(plbm_surrogate h, plbm_handle* hs, int n, int K, do
             Q.f[1] = v.f_next;
             Q.tiles_x = (Q.nx + kBX - 1) / kBX;
             Q.tile_begin = tiles;
-            tiles += Q.tiles_x * Q.half_ny;
+            tiles += Q.tiles_x * plbm::tile_rows(Q);
             table[k] = Q;
         }
         // interleaved tile order (the batched runner's default): lattice of every tile
         s->fb_tiles.assign((size_t)tiles, 0);
         for (size_t k = 0; k < table.size(); ++k)
             std::fill(s->fb_tiles.begin() + table[k].tile_begin,
-                      s->fb_tiles.begin() + table[k].tile_begin + table[k].tiles_x * table[k].half_ny,
+                      s->fb_tiles.begin() + table[k].tile_begin + table[k].tiles_x * plbm::tile_rows(table[k]),
                       (unsigned short)k);
         SCK(cudaMemcpyAsync(s->fb_table, table.data(), sizeof(plbm::PairParams) * table.size(),
                             cudaMemcpyHostToDevice, s->stream));

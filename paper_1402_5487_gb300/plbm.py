@@ -30,6 +30,7 @@ PREC = {"f64": 0, "f32": 1, "f16dev": 2, "bf16dev": 3}
 BC = {"periodic": 0, "fixed": 1}
 FLAG_ISOTHERMAL = 0x1
 FLAG_SKIP_ADMISSIBILITY = 0x2
+FLAG_PLAIN_LAYOUT = 0x4
 
 
 class PlbmError(RuntimeError):
@@ -213,7 +214,7 @@ def coefficients(v) -> np.ndarray:
 
 def make_desc(dim, v, omega, nx, ny=1, theta0=1.0, prec="f32", bc="periodic", left_state=None,
               right_state=None, isothermal=False, check_every=0, u_max=0.0, stream=None,
-              device=0, skip_admissibility=False, nz=1):
+              device=0, skip_admissibility=False, nz=1, plain_layout=False):
     """Build a PlbmDesc; the returned tuple keeps the ctypes buffers alive."""
     q1 = len(v)
     va = (ctypes.c_int * q1)(*[int(a) for a in v])
@@ -231,7 +232,8 @@ def make_desc(dim, v, omega, nx, ny=1, theta0=1.0, prec="f32", bc="periodic", le
         d.right_state = ctypes.cast(rs, _D)
         keep += [ls, rs]
     d.stream = stream
-    d.flags = (FLAG_ISOTHERMAL if isothermal else 0) | (FLAG_SKIP_ADMISSIBILITY if skip_admissibility else 0)
+    d.flags = ((FLAG_ISOTHERMAL if isothermal else 0) | (FLAG_SKIP_ADMISSIBILITY if skip_admissibility else 0) |
+               (FLAG_PLAIN_LAYOUT if plain_layout else 0))
     d.check_every = int(check_every)
     d.u_max = float(u_max)
     d.device = int(device)
@@ -279,7 +281,8 @@ class Solver:
 
     def __init__(self, dim, v, omega, nx, ny=1, theta0=1.0, prec="f32", bc="periodic",
                  left_state=None, right_state=None, isothermal=False, check_every=0, u_max=0.0,
-                 device=0, stream=None, skip_admissibility=False, torch_workspace=True, nz=1):
+                 device=0, stream=None, skip_admissibility=False, torch_workspace=True, nz=1,
+                 plain_layout=False):
         import torch  # device memory and streams only
 
         self.torch = torch
@@ -292,7 +295,8 @@ class Solver:
         self.prec = prec
         desc, self._keep = make_desc(dim, v, omega, nx, self.ny, theta0, prec, bc, left_state,
                                      right_state, isothermal, check_every, u_max,
-                                     self.stream.cuda_stream, device, skip_admissibility, self.nz)
+                                     self.stream.cuda_stream, device, skip_admissibility, self.nz,
+                                     plain_layout)
         self._ws = None
         if torch_workspace:
             nbytes = workspace_bytes(desc)

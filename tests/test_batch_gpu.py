@@ -133,7 +133,9 @@ def test_mixed_batch_groups_schemes_and_single_handles():
     inst = _mixed()
     b = B.Batch(inst, prec="f32")
     paired, plain, launches = b.groups()
-    assert (paired, plain) == (2, 6) and launches == 7   # pairs f32, f16; plain f32 q5, f64 q5, f16 q5, f32 q3, f32 q4
+    # five-velocity thermal 16/32-bit groups (f32: 37 odd, 40 even; f16: 36 even, 35 odd) and
+    # one-node-per-thread groups (f64 q5 x2, isothermal f32 q3, isothermal f32 q4)
+    assert (paired, plain) == (4, 4) and launches == 5
     b.close()
     ref, st = _run(inst, "persistent", 9)
     assert st[0] == plbm.PLBM_OK

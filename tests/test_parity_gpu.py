@@ -700,3 +700,23 @@ def test_rest_state_is_a_fixed_point(prec, dim):
     else:
         assert np.array_equal(f, f0)
     s.close()
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16dev", "bf16dev"])
+def test_plain_and_row_paired_layouts_give_the_same_state(prec):
+    # The plain-layout kernel (one node per thread: odd ny, PLBM_FLAG_PLAIN_LAYOUT)
+    # runs the single-lane forms of the row-paired kernel's packed operations,
+    # each correctly rounded, so both layouts give every node the same bits.
+    nx, ny = 70, 48
+    fields = I.kh_fields(nx, ny=ny)
+    out = []
+    for plain in (False, True):
+        s = plbm.Solver(2, V5, 1.3, nx, ny, theta0=1.0, prec=prec, plain_layout=plain)
+        s.init(*fields)
+        s.step(25)
+        d = s.step_diagnostics(1)
+        out.append((s.get_populations(), d))
+        s.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    for k in ("mass", "jx", "jy", "energy", "rho_min", "theta_min"):
+        assert abs(out[0][1][k] - out[1][1][k]) <= 1e-12 * max(1.0, abs(out[0][1][k])), k
