@@ -39,6 +39,7 @@ from paper_1402_5487_gb300 import inputs as I  # noqa: E402
 V5 = I.SET_013
 OMEGA = 1.3
 REPEATS = 5            # timed runs of --steps steps in the bench line; the median is reported
+SURROGATE_NOISE = 0.2  # input perturbation of the surrogate's training (normalised units)
 THETA0 = 1.0
 ELEM = {"f64": 8, "f32": 4, "f16dev": 2, "bf16dev": 2}
 
@@ -322,9 +323,11 @@ def _field_err(mg, mr):
     return {"rho": rho, "u": u, "theta": th}
 
 
-def run_surrogate(torch, n_train=2000, n_test=100, train_steps=2000, batch=16, K=32, L=256, mean_penalty=0.0):
+def run_surrogate(torch, n_train=2000, n_test=100, train_steps=2000, batch=16, K=32, L=256, mean_penalty=0.0,
+                  noise=SURROGATE_NOISE):
     """Learned surrogate: data from the batched solver, training (loss: MSE plus
-    mean_penalty x the squared lattice-mean error), held-out errors, speed."""
+    mean_penalty x the squared lattice-mean error; inputs perturbed by `noise` x
+    N(0, 1) in normalised units), held-out errors, speed."""
     import oracle as O
     from paper_1402_5487_gb300 import plbm, surrogate as SG
     from paper_1402_5487_gb300.batch import Batch
@@ -340,7 +343,9 @@ def run_surrogate(torch, n_train=2000, n_test=100, train_steps=2000, batch=16, K
     out["mean_penalty"] = mean_penalty
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    losses = net.train(stack, pairs, train_steps, batch=batch, lr=1e-3, lr_end=1e-4, log_every=train_steps // 4)
+    losses = net.train(stack, pairs, train_steps, batch=batch, lr=1e-3, lr_end=1e-4, log_every=train_steps // 4,
+                       noise=noise)
+    out["input_noise"] = noise
     t_train = time.perf_counter() - t0
     flops_sample = 3 * 2.0 * L * L * (9 * 4 * 64 + 4 * 9 * 64 * 64 + 9 * 64 * 4)
     out["training"] = {"steps": train_steps, "batch": batch, "seconds": t_train,
@@ -397,16 +402,19 @@ def run_surrogate(torch, n_train=2000, n_test=100, train_steps=2000, batch=16, K
     out["fallback_rate"] = rate
     out["drift"] = {"tol": 1e-4, "median": float(np.median(d)), "p10": float(np.percentile(d, 10)),
                     "p90": float(np.percentile(d, 90)), "fraction_within_tol": float(np.mean(d <= 1e-4))}
-    sweep = {"1e-4": (t_roll, rate, errs["16"]["surrogate_vs_lbm"]["u"], errs["16"]["non_finite_lattices"])}
-    for tol in (3e-4, 1e-3):
-        t_r, r_r, _, e_r = rollout(tol, checkpoints=(16,))
-        sweep["%g" % tol] = (t_r, r_r, e_r["16"]["surrogate_vs_lbm"]["u"], e_r["16"]["non_finite_lattices"])
+    sweep = {"1e-4": (t_roll, rate, errs["16"]["surrogate_vs_lbm"]["u"], errs["16"]["non_finite_lattices"],
+                      errs["4"]["surrogate_vs_lbm"]["u"])}
+    for tol in (3e-4, 1e-3, float("inf")):
+        t_r, r_r, _, e_r = rollout(tol, checkpoints=(4, 16))
+        sweep["%g" % tol if tol < 1 else "no gate"] = (t_r, r_r, e_r["16"]["surrogate_vs_lbm"]["u"],
+                                                       e_r["16"]["non_finite_lattices"],
+                                                       e_r["4"]["surrogate_vs_lbm"]["u"])
     # the same gate after projecting each prediction onto the old global sums
     net.set_conserve(True)
-    t_r, r_r, _, e_r = rollout(1e-4, checkpoints=(16,))
+    t_r, r_r, _, e_r = rollout(1e-4, checkpoints=(4, 16))
     net.set_conserve(False)
     sweep["1e-4, conservative projection"] = (t_r, r_r, e_r["16"]["surrogate_vs_lbm"]["u"],
-                                              e_r["16"]["non_finite_lattices"])
+                                              e_r["16"]["non_finite_lattices"], e_r["4"]["surrogate_vs_lbm"]["u"])
     # gain test: the same lattices and horizon (16 x K steps) with plain batched LBM
     insts = [SG.trajectory_instance(sd, L)[0] for sd in test_seeds[:nroll]]
     bt = Batch(insts, prec="f32")
@@ -425,7 +433,8 @@ def run_surrogate(torch, n_train=2000, n_test=100, train_steps=2000, batch=16, K
     out["gain_test"] = {"lattices": nroll, "horizon_steps": 16 * K, "lbm_s": t_lbm_roll,
                         "by_tol": {k: {"surrogate_with_fallback_s": v[0], "speedup": t_lbm_roll / v[0],
                                        "fallback_rate": v[1], "u_error_at_horizon_vs_lbm": v[2],
-                                       "non_finite_lattices_at_horizon": v[3]}
+                                       "non_finite_lattices_at_horizon": v[3],
+                                       "u_error_after_4_advances_vs_lbm": v[4]}
                                    for k, v in sweep.items()}}
     # FP64 oracle check on two held-out seeds after one advance
     orc = []
@@ -544,6 +553,10 @@ def run_case(torch, args):
                                                  n=args.batch_instances)}
     if args.case == "longrun":
         return {"case": "longrun", "runs": run_longrun(torch, args.snapshots)}
+    if args.case == "surrogate_gain":
+        return {"case": "surrogate_gain", **run_surrogate(torch, n_train=args.surrogate_train,
+                                                          train_steps=args.surrogate_steps,
+                                                          noise=args.surrogate_noise)}
     if args.case == "d3q125":
         return {"case": "d3q125", "prec": args.prec,
                 **run_variant3(torch, args.size, args.prec, args.steps, args.warmup)}
@@ -680,7 +693,10 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--surrogate-train", type=int, default=2000, help="training trajectories")
     ap.add_argument("--surrogate-steps", type=int, default=6000, help="Adam steps")
-    ap.add_argument("--case", default="main", choices=["main", "surrogate", "batched", "d3q125", "longrun"],
+    ap.add_argument("--surrogate-noise", type=float, default=SURROGATE_NOISE,
+                    help="input noise of the surrogate's training (normalised units)")
+    ap.add_argument("--case", default="main", choices=["main", "surrogate", "surrogate_gain", "batched", "d3q125",
+                                                       "longrun"],
                     help="main: the bench line; any other: one secondary workload alone (a JSON "
                          "line of its own); longrun: errors against FP64 oracle snapshots")
     ap.add_argument("--batch", type=int, default=16, help="lattices per surrogate call (--case surrogate)")
@@ -811,7 +827,7 @@ def main():
             variants["batched_%d_f32" % args.batch_instances] = run_batched(torch, n=args.batch_instances)
         if not args.no_surrogate:
             variants["surrogate_kh256"] = run_surrogate(torch, n_train=args.surrogate_train,
-                                                        train_steps=args.surrogate_steps)
+                                                        train_steps=args.surrogate_steps, noise=args.surrogate_noise)
         base = value / ws
         for k, vv in variants.items():
             if k.startswith("kh%d_" % L) and "mlups" in vv:

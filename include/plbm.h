@@ -451,6 +451,18 @@ plbm_status plbm_sur_pack_fields(const double *rho, const double *ux, const doub
 plbm_status plbm_sur_assemble(plbm_surrogate s, const float *snaps, long long npix, const int *pairs, int B,
                               void *x, float *y);
 
+/* The same with sigma x a standard normal number added to every normalised input
+ * element before its bf16 rounding (training on inputs perturbed like the
+ * network's own predictions keeps repeated advances stable).  The numbers come
+ * from a counter-based generator: element e = 4 (b npix + pixel) + field draws
+ * SplitMix64(seed xor SplitMix64(e)) (SplitMix64: z += 0x9e3779b97f4a7c15,
+ * z = (z ^ z >> 30) 0xbf58476d1ce4e5b9, z = (z ^ z >> 27) 0x94d049bb133111eb,
+ * z ^ z >> 31), whose bits 40..63 and 16..39 give u1 = (k + 1) / 2^24 and
+ * u2 = k / 2^24, and Box-Muller sqrt(-2 ln u1) cos(2 pi u2).  sigma = 0: no
+ * noise.  PLBM_E_ARG for a negative or non-finite sigma. */
+plbm_status plbm_sur_assemble_noise(plbm_surrogate s, const float *snaps, long long npix, const int *pairs, int B,
+                                    void *x, float *y, float sigma, unsigned long long seed);
+
 /* Advance n lattices (handles of H x W periodic 2D lattices, 16/32/64-bit
  * storage) by K steps with the network: fields from the populations, predicted
  * change, and the FP64 global drift of mass, energy (relative) and momentum

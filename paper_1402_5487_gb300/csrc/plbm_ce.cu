@@ -36,22 +36,48 @@ __global__ void k_pack_fields(const double* __restrict__ rho, const double* __re
     if (i < n) out[i] = make_float4((float)rho[i], (float)ux[i], (float)uy[i], (float)th[i]);
 }
 
-// Training pair b: x[b] = (F[s0] - mean_in) / std_in (bf16), y[b] = (F[s1] - F[s0] - mean_d) / std_d (fp32),
-// F a stack of snapshots of `npix` nodes x 4 fields, pairs[b] = (s0, s1).
+// SplitMix64 (Steele, Lea and Flood, 2014): the output function applied to z.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
+    z += 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+// Standard normal number of counter `ctr` under `seed`: the two halves of one
+// 48-bit draw as uniforms u1 in (0, 1], u2 in [0, 1), then Box and Muller (1958):
+// sqrt(-2 ln u1) cos(2 pi u2).
+__device__ __forceinline__ float gauss_of(unsigned long long seed, unsigned long long ctr) {
+    const unsigned long long h = splitmix64(seed ^ splitmix64(ctr));
+    const float u1 = ((float)(h >> 40) + 1.0f) * (1.0f / 16777216.0f);
+    const float u2 = (float)((h >> 16) & 0xffffffull) * (1.0f / 16777216.0f);
+    return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+}
+
+// Training pair b: x[b] = (F[s0] - mean_in) / std_in + sigma n (bf16), y[b] = (F[s1] - F[s0] - mean_d) / std_d
+// (fp32), F a stack of snapshots of `npix` nodes x 4 fields, pairs[b] = (s0, s1); n a standard normal number
+// per input element (counter 4 i + field under `seed`), none when sigma = 0.
 __global__ void k_assemble(const float4* __restrict__ snaps, long long npix, const int* __restrict__ pairs,
                            int B, float4 mean_in, float4 istd_in, float4 mean_d, float4 istd_d,
-                           __nv_bfloat16* __restrict__ x, float4* __restrict__ y) {
+                           __nv_bfloat16* __restrict__ x, float4* __restrict__ y, float sigma,
+                           unsigned long long seed) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= npix * B) return;
     const int b = (int)(i / npix);
     const long long k = i - (long long)b * npix;
     const float4 a = snaps[(long long)pairs[2 * b] * npix + k];
     const float4 c = snaps[(long long)pairs[2 * b + 1] * npix + k];
+    float4 n = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (sigma > 0.0f) {
+        const unsigned long long c0 = 4ull * (unsigned long long)i;
+        n = make_float4(sigma * gauss_of(seed, c0), sigma * gauss_of(seed, c0 + 1), sigma * gauss_of(seed, c0 + 2),
+                        sigma * gauss_of(seed, c0 + 3));
+    }
     __nv_bfloat16* xo = x + i * 4;
-    xo[0] = __float2bfloat16_rn((a.x - mean_in.x) * istd_in.x);
-    xo[1] = __float2bfloat16_rn((a.y - mean_in.y) * istd_in.y);
-    xo[2] = __float2bfloat16_rn((a.z - mean_in.z) * istd_in.z);
-    xo[3] = __float2bfloat16_rn((a.w - mean_in.w) * istd_in.w);
+    xo[0] = __float2bfloat16_rn((a.x - mean_in.x) * istd_in.x + n.x);
+    xo[1] = __float2bfloat16_rn((a.y - mean_in.y) * istd_in.y + n.y);
+    xo[2] = __float2bfloat16_rn((a.z - mean_in.z) * istd_in.z + n.z);
+    xo[3] = __float2bfloat16_rn((a.w - mean_in.w) * istd_in.w + n.w);
     y[i] = make_float4((c.x - a.x - mean_d.x) * istd_d.x, (c.y - a.y - mean_d.y) * istd_d.y,
                        (c.z - a.z - mean_d.z) * istd_d.z, (c.w - a.w - mean_d.w) * istd_d.w);
 }
@@ -326,7 +352,7 @@ cudaError_t ce_pack_fields(const double* rho, const double* ux, const double* uy
 
 cudaError_t ce_assemble(const float* snaps, long long npix, const int* pairs, int B, const float* mean_in,
                         const float* std_in, const float* mean_d, const float* std_d, void* x, float* y,
-                        cudaStream_t s) {
+                        float sigma, unsigned long long seed, cudaStream_t s) {
     const float4 mi = make_float4(mean_in[0], mean_in[1], mean_in[2], mean_in[3]);
     const float4 si = make_float4(1.f / std_in[0], 1.f / std_in[1], 1.f / std_in[2], 1.f / std_in[3]);
     const float4 md = make_float4(mean_d[0], mean_d[1], mean_d[2], mean_d[3]);
@@ -334,7 +360,7 @@ cudaError_t ce_assemble(const float* snaps, long long npix, const int* pairs, in
     const long long n = npix * B;
     k_assemble<<<(int)((n + 255) / 256), 256, 0, s>>>(reinterpret_cast<const float4*>(snaps), npix, pairs, B, mi, si,
                                                        md, sd, static_cast<__nv_bfloat16*>(x),
-                                                       reinterpret_cast<float4*>(y));
+                                                       reinterpret_cast<float4*>(y), sigma, seed);
     return cudaGetLastError();
 }
 

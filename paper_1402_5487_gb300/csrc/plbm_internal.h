@@ -169,7 +169,7 @@ cudaError_t ce_pack_fields(const double* rho, const double* ux, const double* uy
                            float* out, cudaStream_t s);
 cudaError_t ce_assemble(const float* snaps, long long npix, const int* pairs, int B, const float* mean_in,
                         const float* std_in, const float* mean_d, const float* std_d, void* x, float* y,
-                        cudaStream_t s);
+                        float sigma, unsigned long long seed, cudaStream_t s);
 cudaError_t ce_normalise(const float* F, long long n, const float* mean_in, const float* std_in, void* x,
                          cudaStream_t s);
 cudaError_t ce_apply_delta(const float* F, const float* d, long long n, const float* mean_d, const float* std_d,

@@ -257,9 +257,10 @@ plbm_status plbm_slabs_create(const plbm_desc* desc, int nslabs, plbm_slabs* out
     }
     plbm_halo_plan(s->q1, s->v, -1, s->pops.lo, &s->pops.nlo);
     plbm_halo_plan(s->q1, s->v, 1, s->pops.hi, &s->pops.nhi);
-    // The slabs take the layout of the undivided lattice, so that they run the
-    // same per-node code: even row counts and row pairs when it is row-paired
-    // (rows + 2w then stays even), the plain layout otherwise.
+    // Both layouts give a node the same bits (the plain-layout kernel runs the
+    // single-lane forms of the row-paired arithmetic); slabs of a row-paired lattice
+    // take even row counts all the same, so that they keep the faster two-nodes-per-
+    // thread kernel (rows + 2w stays even).
     const bool paired = plbm::desc_row_paired(desc);
     s->y0.resize(nslabs);
     s->rows.resize(nslabs);

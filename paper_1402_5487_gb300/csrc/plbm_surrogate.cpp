@@ -483,9 +483,19 @@ plbm_status plbm_sur_pack_fields(const double* rho, const double* ux, const doub
 
 plbm_status plbm_sur_assemble(plbm_surrogate h, const float* snaps, long long npix, const int* pairs, int B, void* x,
                               float* y) {
+    return plbm_sur_assemble_noise(h, snaps, npix, pairs, B, x, y, 0.0f, 0ull);
+}
+
+plbm_status plbm_sur_assemble_noise(plbm_surrogate h, const float* snaps, long long npix, const int* pairs, int B,
+                                    void* x, float* y, float sigma, unsigned long long seed) {
     Sur* s = as_sur(h);
     if (!s || !snaps || !pairs || !x || !y || B < 1) return PLBM_E_ARG;
-    SCK(plbm::ce_assemble(snaps, npix, pairs, B, s->norm, s->norm + 4, s->norm + 8, s->norm + 12, x, y, s->stream));
+    if (!(sigma >= 0.0f) || !(sigma < 1e30f)) {
+        serr(s, "input noise sigma must be finite and >= 0");
+        return PLBM_E_ARG;
+    }
+    SCK(plbm::ce_assemble(snaps, npix, pairs, B, s->norm, s->norm + 4, s->norm + 8, s->norm + 12, x, y, sigma, seed,
+                          s->stream));
     return PLBM_OK;
 }
 

@@ -163,6 +163,9 @@ SIGNATURES = {
                                                                      ctypes.c_void_p]),
     "plbm_sur_assemble": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p,
                                          ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "plbm_sur_assemble_noise": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p,
+                                               ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float,
+                                               ctypes.c_ulonglong]),
     "plbm_sur_advance": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
                                         ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_int)]),
     "plbm_sur_last_drift": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),

@@ -189,8 +189,10 @@ class Surrogate:
         self._ok(plbm.lib().plbm_sur_copy(self.h, int(kind), int(layer), int(B), out.data_ptr()))
         return out
 
-    def train(self, stack, pairs, steps, batch=16, lr=1e-3, lr_end=None, seed=0, log_every=0):
-        """Adam steps on random minibatches of `pairs`; returns the list of (step, loss)."""
+    def train(self, stack, pairs, steps, batch=16, lr=1e-3, lr_end=None, seed=0, log_every=0, noise=0.0):
+        """Adam steps on random minibatches of `pairs`; returns the list of (step, loss).
+        noise: standard deviation of the normal perturbation added to the normalised
+        inputs of every minibatch (plbm_sur_assemble_noise; 0 = none)."""
         torch = self.torch
         rng = np.random.default_rng(seed)
         npix = self.H * self.W
@@ -207,8 +209,9 @@ class Surrogate:
             pos += batch
             pairs_dev.copy_(torch.from_numpy(sel), non_blocking=False)
             torch.cuda.current_stream().synchronize()
-            self._ok(plbm.lib().plbm_sur_assemble(self.h, stack.data_ptr(), npix, pairs_dev.data_ptr(), batch,
-                                                  self.x.data_ptr(), self.y.data_ptr()))
+            self._ok(plbm.lib().plbm_sur_assemble_noise(self.h, stack.data_ptr(), npix, pairs_dev.data_ptr(), batch,
+                                                        self.x.data_ptr(), self.y.data_ptr(), float(noise),
+                                                        (int(seed) << 32) + it))
             frac = it / max(1, steps - 1)
             lr_t = lr * (lr_end / lr) ** frac
             want = log_every and (it % log_every == 0 or it == steps - 1)

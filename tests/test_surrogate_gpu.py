@@ -340,3 +340,47 @@ def test_a_wait_that_runs_out_is_reported_and_the_next_pass_is_correct():
     assert torch.equal(out, ref_out)
     assert rel(grads, ref_grads) <= 1e-6
     net.close()
+
+
+def _splitmix64(z):
+    """SplitMix64 output function (Steele, Lea and Flood 2014) on uint64 arrays (wrapping)."""
+    z = z + np.uint64(0x9E3779B97F4A7C15)
+    z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+    z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
+
+
+def test_input_noise_is_the_stated_counter_based_normal_draw():
+    # plbm_sur_assemble_noise adds sigma x N(0, 1) to every normalised input element,
+    # the normal number of element e drawn as SplitMix64(seed ^ SplitMix64(e)) and
+    # Box-Muller; restated here in FP64 NumPy from the published definitions.
+    import torch
+    H, W, sigma, seed = 3, 128, 0.05, 1234
+    net = SG.Surrogate(2, H=H, W=W, seed=1)
+    net.set_norm(np.zeros(4), np.ones(4), np.zeros(4), np.ones(4))
+    npix = H * W
+    g = torch.Generator().manual_seed(8)
+    stack = torch.rand((2, npix, 4), generator=g).cuda()
+    pairs = torch.tensor([[0, 1], [1, 0]], dtype=torch.int32).cuda()
+    x0 = torch.empty((2, H, W, 4), dtype=torch.bfloat16, device="cuda")
+    x1, y = torch.empty_like(x0), torch.empty((2, H, W, 4), dtype=torch.float32, device="cuda")
+    L = plbm.lib()
+    assert L.plbm_sur_assemble(net.h, stack.data_ptr(), npix, pairs.data_ptr(), 2, x0.data_ptr(), y.data_ptr()) == 0
+    assert L.plbm_sur_assemble_noise(net.h, stack.data_ptr(), npix, pairs.data_ptr(), 2, x1.data_ptr(), y.data_ptr(),
+                                     sigma, seed) == 0
+    net.stream.synchronize()
+    e = np.arange(2 * npix * 4, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        h = _splitmix64(np.uint64(seed) ^ _splitmix64(e))
+    u1 = ((h >> np.uint64(40)).astype(np.float64) + 1.0) / 2.0 ** 24
+    u2 = ((h >> np.uint64(16)) & np.uint64(0xFFFFFF)).astype(np.float64) / 2.0 ** 24
+    gauss = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+    clean = stack[pairs[:, 0].long()].cpu().numpy().astype(np.float64).reshape(-1)
+    ref = bf16(clean + sigma * gauss)
+    got = x1.float().cpu().numpy().astype(np.float64).reshape(-1)
+    assert np.all(np.abs(got - ref) <= 2.0 ** -8 * np.abs(ref) + 1e-6)
+    d = got - x0.float().cpu().numpy().astype(np.float64).reshape(-1)
+    assert abs(d.mean()) < 0.1 * sigma and abs(d.std() / sigma - 1.0) < 0.1
+    assert L.plbm_sur_assemble_noise(net.h, stack.data_ptr(), npix, pairs.data_ptr(), 2, x1.data_ptr(), y.data_ptr(),
+                                     -1.0, seed) == plbm.PLBM_E_ARG
+    net.close()
