@@ -133,6 +133,23 @@ __device__ void node_moments_f64(const LatticeParams& P, const double* f, double
     jy_o = jy;
 }
 
+// Check of one node's initial fields, made by the initialisation kernels that read
+// them anyway: a non-finite value sets PLBM_STATUS_NONFINITE, otherwise rho <= 0
+// PLBM_STATUS_RHO_NONPOS and theta <= 0 PLBM_STATUS_THETA_NONPOS.
+__device__ __forceinline__ void check_init_node(const LatticeParams& P, const double* rho, const double* ux,
+                                                const double* uy, const double* theta, long long n) {
+    const double r = rho[n], a = ux[n];
+    const double b = (P.dim == 2 && uy) ? uy[n] : 0.0;
+    const bool has_t = !(P.isothermal || theta == nullptr);
+    const double t = has_t ? theta[n] : 1.0;
+    if (isfinite(r) && isfinite(a) && isfinite(b) && isfinite(t) && r > 0.0 && t > 0.0) return;
+    unsigned bits = 0u;
+    if (!isfinite(r) || !isfinite(a) || !isfinite(b) || !isfinite(t)) bits |= PLBM_STATUS_NONFINITE;
+    if (isfinite(r) && !(r > 0.0)) bits |= PLBM_STATUS_RHO_NONPOS;
+    if (isfinite(t) && !(t > 0.0)) bits |= PLBM_STATUS_THETA_NONPOS;
+    atomicOr(P.status, bits);
+}
+
 template <typename S>
 __global__ void k_init(const __grid_constant__ LatticeParams P, const double* __restrict__ rho,
                        const double* __restrict__ ux, const double* __restrict__ uy,
@@ -141,6 +158,7 @@ __global__ void k_init(const __grid_constant__ LatticeParams P, const double* __
     const int y = y0 + blockIdx.y;
     if (x >= P.nx) return;
     const long long n = (long long)y * P.nx + x;
+    check_init_node(P, rho, ux, uy, theta, n);
     const double th = (P.isothermal || theta == nullptr) ? P.theta0 : theta[n];
     double feq[kMaxQ];
     node_feq_f64(P, rho[n], ux[n], (P.dim == 2 && uy) ? uy[n] : 0.0, th, feq);
@@ -158,6 +176,7 @@ __global__ void k_init_q(const __grid_constant__ LatticeParams P, const double* 
     const int y = y0 + blockIdx.y;
     if (x >= P.nx) return;
     const long long n = (long long)y * P.nx + x;
+    check_init_node(P, rho, ux, uy, theta, n);
     const double th = (P.isothermal || theta == nullptr) ? P.theta0 : theta[n];
     double r[DIM][Q1];
 #pragma unroll
@@ -262,6 +281,7 @@ __global__ void k_init_sym5_dev(const __grid_constant__ LatticeParams P, const d
     const int y = y0 + blockIdx.y;
     if (x >= P.nx) return;
     const long long n = (long long)y * P.nx + x;
+    check_init_node(P, rho, ux, uy, theta, n);
     const float dth = (P.isothermal || theta == nullptr) ? 0.0f : (float)(theta[n] - P.theta0);
     const float drho = (float)(rho[n] - 1.0);
     const float rh = 1.0f + drho;

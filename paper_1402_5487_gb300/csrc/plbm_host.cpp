@@ -616,11 +616,11 @@ plbm_status plbm_init(plbm_handle hh, const double* rho, const double* ux, const
     }
     const size_t n = (size_t)h->P.nx * h->P.ny;
     h->cur = 0;
+    // the status word is cleared first: the initialisation kernels set its bits for
+    // non-finite fields, rho <= 0 or theta <= 0 as they read them
+    CK(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
     if (on_device) {
         CK(plbm::launch_init(h->prec, h->P, rho, ux, uy, theta, h->f[0], h->stream));
-        CK(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
-        const double* d[4] = {rho, ux, h->P.dim == 2 ? uy : nullptr, theta};
-        CK(plbm::launch_check_fields(field_set(d, 4), (long long)n, h->status, h->stream));
     } else {
         // Band k of the four fields is copied on the copy stream while the kernel
         // initialises band k - 1 on the handle's stream.
@@ -643,8 +643,6 @@ plbm_status plbm_init(plbm_handle hh, const double* rho, const double* ux, const
             CK(cudaStreamWaitEvent(h->stream, h->xev[b], 0));
             CK(plbm::launch_init(h->prec, h->P, dev[0], dev[1], dev[2], dev[3], h->f[0], h->stream, y0, y1));
         }
-        CK(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
-        CK(plbm::launch_check_fields(field_set(dev, 4), (long long)n, h->status, h->stream));
     }
     h->steps = 0;
     h->initialised = true;
