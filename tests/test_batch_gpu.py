@@ -168,3 +168,31 @@ def test_mixed_batch_instances_vs_oracle_100_steps():
         assert e["rho"] <= t and e["theta"] <= t and du <= t, (i, e, du)
     assert b.check()[0] == plbm.PLBM_OK
     b.close()
+
+
+def test_full_sweep_sampled_nodes():
+    # The bench's sweep (256 instances drawn by the R8 gates, sides over every
+    # integer of [64, 1024], 1.0e8 nodes) in its timed launch scheme: after k steps a
+    # node depends only on nodes within 3k, so the oracle advances a (6k+1)^2
+    # periodic window of the instance's own fields around sampled nodes.
+    from parity_util import patch_fields
+    inst, _ = B.draw_instances(256)
+    b = B.Batch(inst, prec="f32")
+    b.init()
+    k, half = 4, 12
+    b.step(k, "persistent_graph")
+    assert b.check()[0] == plbm.PLBM_OK
+    odd = [i for i, x in enumerate(inst) if x.L % 2][:4]
+    even = [i for i, x in enumerate(inst) if x.L % 2 == 0][:4]
+    rng = np.random.default_rng(21)
+    for idx in odd + even:
+        x = inst[idx]
+        fields = I.instance_fields(x)
+        mg = b.solvers[idx].moments()
+        for _ in range(3):
+            cx, cy = (int(a) for a in rng.integers(0, x.L, 2))
+            pf = patch_fields(fields, cx, cy, half, x.L, x.L)
+            _, _, mo = oracle_run(2, x.v, x.omega, 2 * half + 1, 2 * half + 1, pf, k, theta0=x.theta0)
+            for f_g, f_o, scale in zip(mg, mo, (1.0, 0.1, 0.1, x.theta0)):
+                assert abs(f_g[cy, cx] - f_o[half, half]) <= 1e-6 * scale, (idx, x.L, cx, cy)
+    b.close()

@@ -197,3 +197,30 @@ def test_d3q125_diagnostics_equal_fp64_sums_of_the_stored_state(prec, nz):
     d = s.diagnostics()
     assert abs(d["rho_min"] - mass.min()) <= 1e-13 and abs(d["theta_min"] - th.min()) <= 1e-12
     s.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("f32", 2e-6), ("f16dev", 2e-3), ("bf16dev", 2e-2)])
+def test_d3q125_bench_size_sampled_nodes(prec, tol):
+    # The bench's 3D workload (256^3 double shear layer; FP32 on the split kernel,
+    # 16-bit storage on the z-paired one): after k steps a node depends only on
+    # nodes within 3k, so the oracle advances a (6k+1)^3 periodic window around
+    # each sampled node and its centre must match the GPU.
+    from paper_1402_5487_gb300 import inputs as I, plbm
+    n, k, half = 256, 2, 6
+    f = I.kh3_fields(n, n, n)
+    s = plbm.Solver(3, V5, 1.3, n, n, nz=n, theta0=1.0, prec=prec)
+    s.init(f[0], f[1], f[2], f[4], uz=f[3])
+    s.step(k)
+    mg = s.moments()                       # rho, ux, uy, uz, theta, each [nz][ny][nx]
+    s.close()
+    rng = np.random.default_rng(31)
+    pts = [(0, 0, 0), (n - 1, n - 1, n - 1), (5, 250, 128)] + [tuple(int(a) for a in rng.integers(0, n, 3))
+                                                                for _ in range(5)]
+    w = 2 * half + 1
+    for cx, cy, cz in pts:
+        zs, ys, xs = (np.arange(c - half, c + half + 1) % n for c in (cz, cy, cx))
+        patch = [np.ascontiguousarray(a[np.ix_(zs, ys, xs)]) for a in f]
+        lat = O.Lattice3(V5, 1.3, w, w, w, theta0=1.0)
+        mo = lat.moments(lat.run(lat.init(*patch), k))
+        for g, o, scale in zip(mg, mo, (1.0, 0.1, 0.1, 0.1, 1.0)):
+            assert abs(g[cz, cy, cx] - o[half, half, half]) <= tol * scale, (prec, cx, cy, cz)

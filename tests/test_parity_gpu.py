@@ -171,13 +171,16 @@ def test_parity_kh_512_config_1000_steps():
     assert max(e32.values()) <= TOL32 and rel(f32, fo) <= TOL32, e32
 
 
-def test_fullsize_2048_sampled_nodes():
-    # Bench workload (2048^2 KH, FP32): after k steps a node depends only on nodes within
-    # 3k in each direction, so the oracle advances a (6k+1)^2 periodic window around each
+@pytest.mark.parametrize("L,prec,tol", [(2048, "f32", 1e-6), (2047, "f32", 1e-6), (2048, "f16dev", 2e-3),
+                                         (2048, "bf16dev", 2e-2)])
+def test_fullsize_2048_sampled_nodes(L, prec, tol):
+    # Bench workloads (2048^2 KH in FP32 and 16-bit storage on row pairs; 2047^2, the
+    # plain layout of odd sides): after k steps a node depends only on nodes within 3k
+    # in each direction, so the oracle advances a (6k+1)^2 periodic window around each
     # sampled node and its centre must match the GPU.
-    L, k, half = 2048, 4, 12
+    k, half = 4, 12
     fields = I.kh_fields(L)
-    s = plbm.Solver(2, V5, 1.3, L, L, theta0=1.0, prec="f32")
+    s = plbm.Solver(2, V5, 1.3, L, L, theta0=1.0, prec=prec)
     s.init(*fields)
     s.step(k)
     mg = s.moments()
@@ -191,11 +194,11 @@ def test_fullsize_2048_sampled_nodes():
         for gi, oi in zip(mg, mo):
             errs.append(abs(gi[cy, cx] - oi[half, half]) / max(1e-30, np.max(np.abs(fields[0]))))
     rho_g, ux_g, uy_g, _ = mg
-    assert max(errs[0::4]) < 1e-6      # rho
-    assert max(errs[3::4]) < 1e-6      # theta
-    assert max(max(errs[1::4]), max(errs[2::4])) < 1e-6  # velocity components (scale ~0.1)
+    assert max(errs[0::4]) < tol      # rho
+    assert max(errs[3::4]) < tol      # theta
+    assert max(max(errs[1::4]), max(errs[2::4])) < tol  # velocity components (scale ~0.1)
     d = s.diagnostics()
-    assert abs(d["mass"] - L * L) / (L * L) < 1e-6
+    assert abs(d["mass"] - L * L) / (L * L) < max(tol, 1e-6)
     s.close()
 
 

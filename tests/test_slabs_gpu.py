@@ -53,3 +53,20 @@ def test_slab_errors():
         plbm.Slabs(V5, 1.3, 32, 10, 4)          # 4 slabs of 10 rows: fewer than 3 rows each
     with pytest.raises(plbm.PlbmError):
         plbm.Slabs(V5, 1.3, 32, 32, 0)
+
+
+def test_bench_decomposition_2048_equals_the_undivided_lattice():
+    # The bench variant: 2048^2 FP32 in four slabs of 512 rows.
+    L = 2048
+    fields = I.kh_fields(L)
+    one = plbm.Solver(2, V5, 1.3, L, L, theta0=1.0, prec="f32")
+    one.init(*fields)
+    one.step(7)
+    ref = one.get_populations()
+    one.close()
+    sl = plbm.Slabs(V5, 1.3, L, L, 4, theta0=1.0, prec="f32")
+    assert [sl.slab(k)[2] for k in range(4)] == [512] * 4
+    sl.init(*fields)
+    sl.step(7)
+    assert np.array_equal(sl.get_populations(), ref)
+    sl.close()
