@@ -381,13 +381,22 @@ __device__ __forceinline__ float dev_f32<double>(const double* f, long long i, d
     return (float)(__ldg(f + i) - w0);
 }
 
+// refs (batched launch, grid.z = lattice): lattice blockIdx.z reads refs[z].f and
+// writes its fields at refs[z].index * nx * ny of the stacks F and x.
 template <typename S, int Q1>
 __global__ void k_moments_pack(const __grid_constant__ LatticeParams P, const S* __restrict__ f,
                                float4* __restrict__ F, __nv_bfloat16* __restrict__ x, float4 mean_in,
-                               float4 istd_in) {
+                               float4 istd_in, const LatticeRef* __restrict__ refs) {
     const int xx = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (xx >= P.nx) return;
+    if (refs) {
+        const LatticeRef r = refs[blockIdx.z];
+        f = static_cast<const S*>(r.f);
+        const long long off = r.index * P.nx * P.ny;
+        F += off;
+        x += off * 4;
+    }
     constexpr int kQ1 = Q1 ? Q1 : kMaxQ1;
     const int q1 = Q1 ? Q1 : P.q1;
     float sx[kQ1], ty[kQ1];
@@ -670,14 +679,33 @@ cudaError_t launch_moments_pack(int prec, const LatticeParams& P, const void* f,
     const float4 mi = make_float4(mean_in[0], mean_in[1], mean_in[2], mean_in[3]);
     const float4 si = make_float4(1.f / std_in[0], 1.f / std_in[1], 1.f / std_in[2], 1.f / std_in[3]);
     dim3 grid((P.nx + 127) / 128, P.ny);
+    const LatticeRef* none = nullptr;
     if (P.q1 == 5) {
         PLBM_DISPATCH(prec, (k_moments_pack<S, 5><<<grid, 128, 0, stream>>>(
                                 P, static_cast<const S*>(f), reinterpret_cast<float4*>(F),
-                                static_cast<__nv_bfloat16*>(x), mi, si)));
+                                static_cast<__nv_bfloat16*>(x), mi, si, none)));
     } else {
         PLBM_DISPATCH(prec, (k_moments_pack<S, 0><<<grid, 128, 0, stream>>>(
                                 P, static_cast<const S*>(f), reinterpret_cast<float4*>(F),
-                                static_cast<__nv_bfloat16*>(x), mi, si)));
+                                static_cast<__nv_bfloat16*>(x), mi, si, none)));
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments_pack_batch(int prec, const LatticeParams& P, const LatticeRef* refs, int n, float* F,
+                                      void* x, const float* mean_in, const float* std_in, cudaStream_t stream) {
+    if (P.dim != 2 || n < 1 || n > 65535) return cudaErrorInvalidValue;
+    const float4 mi = make_float4(mean_in[0], mean_in[1], mean_in[2], mean_in[3]);
+    const float4 si = make_float4(1.f / std_in[0], 1.f / std_in[1], 1.f / std_in[2], 1.f / std_in[3]);
+    dim3 grid((P.nx + 127) / 128, P.ny, n);
+    if (P.q1 == 5) {
+        PLBM_DISPATCH(prec, (k_moments_pack<S, 5><<<grid, 128, 0, stream>>>(
+                                P, nullptr, reinterpret_cast<float4*>(F), static_cast<__nv_bfloat16*>(x), mi, si,
+                                refs)));
+    } else {
+        PLBM_DISPATCH(prec, (k_moments_pack<S, 0><<<grid, 128, 0, stream>>>(
+                                P, nullptr, reinterpret_cast<float4*>(F), static_cast<__nv_bfloat16*>(x), mi, si,
+                                refs)));
     }
     return cudaGetLastError();
 }

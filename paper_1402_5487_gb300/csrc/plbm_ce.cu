@@ -240,13 +240,20 @@ struct CEConsts {
 
 // Q1: the 1D velocity count when known at compile time (arrays then stay in
 // registers), 0 for any q1 <= kMaxQ1.
+// refs (batched launch, grid.z = lattice): lattice blockIdx.z writes refs[z].f from
+// the fields at refs[z].index * nx * ny of F.
 template <typename S, int Q1>
 __global__ void k_ce_reconstruct(const __grid_constant__ LatticeParams P, const __grid_constant__ CEConsts K,
-                                 const float4* __restrict__ F, S* __restrict__ f) {
+                                 const float4* __restrict__ F, S* __restrict__ f, const LatticeRef* __restrict__ refs) {
     constexpr int kQ1 = Q1 ? Q1 : kMaxQ1;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= P.nx) return;
+    if (refs) {
+        const LatticeRef r = refs[blockIdx.z];
+        f = static_cast<S*>(r.f);
+        F += r.index * P.nx * P.ny;
+    }
     const int nx = P.nx, ny = P.ny;
     const int xp = x + 1 == nx ? 0 : x + 1, xm = x == 0 ? nx - 1 : x - 1;
     const int yp = y + 1 == ny ? 0 : y + 1, ym = y == 0 ? ny - 1 : y - 1;
@@ -411,7 +418,21 @@ cudaError_t ce_field_sums(const float* F, long long n, double* partial, cudaStre
     return cudaGetLastError();
 }
 
+static cudaError_t ce_reconstruct_batch_impl(int prec, const LatticeParams& P, const float* F, void* f,
+                                             const LatticeRef* refs, int n, cudaStream_t s);
+
 cudaError_t ce_reconstruct(int prec, const LatticeParams& P, const float* F, void* f, cudaStream_t s) {
+    return ce_reconstruct_batch_impl(prec, P, F, f, nullptr, 1, s);
+}
+
+cudaError_t ce_reconstruct_batch(int prec, const LatticeParams& P, const float* F, const LatticeRef* refs, int n,
+                                 cudaStream_t s) {
+    if (n < 1 || n > 65535) return cudaErrorInvalidValue;
+    return ce_reconstruct_batch_impl(prec, P, F, nullptr, refs, n, s);
+}
+
+static cudaError_t ce_reconstruct_batch_impl(int prec, const LatticeParams& P, const float* F, void* f,
+                                             const LatticeRef* refs, int n, cudaStream_t s) {
     if (P.dim != 2) return cudaErrorInvalidValue;
     // G_jk = sum_p w0_p m_j m_k, m = (1, vx, vy, |v|^2), inverted in FP64 on the host.
     double G[4][4] = {{0}};
@@ -448,26 +469,28 @@ cudaError_t ce_reconstruct(int prec, const LatticeParams& P, const float* F, voi
     for (int a = 0; a < 4; ++a)
         for (int b = 0; b < 4; ++b) K.Ginv[4 * a + b] = (float)A[a][4 + b];
     K.coef = (float)((1.0 - P.omega) / P.omega);
-    dim3 grid((P.nx + 127) / 128, P.ny);
+    dim3 grid((P.nx + 127) / 128, P.ny, n);
     const float4* Fv = reinterpret_cast<const float4*>(F);
     switch (prec) {
         case kF32:
-            if (P.q1 == 5) k_ce_reconstruct<float, 5><<<grid, 128, 0, s>>>(P, K, Fv, static_cast<float*>(f));
-            else k_ce_reconstruct<float, 0><<<grid, 128, 0, s>>>(P, K, Fv, static_cast<float*>(f));
+            if (P.q1 == 5) k_ce_reconstruct<float, 5><<<grid, 128, 0, s>>>(P, K, Fv, static_cast<float*>(f), refs);
+            else k_ce_reconstruct<float, 0><<<grid, 128, 0, s>>>(P, K, Fv, static_cast<float*>(f), refs);
             break;
         case kF16Dev:
-            if (P.q1 == 5) k_ce_reconstruct<__half, 5><<<grid, 128, 0, s>>>(P, K, Fv, static_cast<__half*>(f));
-            else k_ce_reconstruct<__half, 0><<<grid, 128, 0, s>>>(P, K, Fv, static_cast<__half*>(f));
+            if (P.q1 == 5) k_ce_reconstruct<__half, 5><<<grid, 128, 0, s>>>(P, K, Fv, static_cast<__half*>(f), refs);
+            else k_ce_reconstruct<__half, 0><<<grid, 128, 0, s>>>(P, K, Fv, static_cast<__half*>(f), refs);
             break;
         case kBF16Dev:
             if (P.q1 == 5)
-                k_ce_reconstruct<__nv_bfloat16, 5><<<grid, 128, 0, s>>>(P, K, Fv, static_cast<__nv_bfloat16*>(f));
+                k_ce_reconstruct<__nv_bfloat16, 5><<<grid, 128, 0, s>>>(P, K, Fv, static_cast<__nv_bfloat16*>(f),
+                                                                        refs);
             else
-                k_ce_reconstruct<__nv_bfloat16, 0><<<grid, 128, 0, s>>>(P, K, Fv, static_cast<__nv_bfloat16*>(f));
+                k_ce_reconstruct<__nv_bfloat16, 0><<<grid, 128, 0, s>>>(P, K, Fv, static_cast<__nv_bfloat16*>(f),
+                                                                        refs);
             break;
         case kF64:
-            if (P.q1 == 5) k_ce_reconstruct<double, 5><<<grid, 128, 0, s>>>(P, K, Fv, static_cast<double*>(f));
-            else k_ce_reconstruct<double, 0><<<grid, 128, 0, s>>>(P, K, Fv, static_cast<double*>(f));
+            if (P.q1 == 5) k_ce_reconstruct<double, 5><<<grid, 128, 0, s>>>(P, K, Fv, static_cast<double*>(f), refs);
+            else k_ce_reconstruct<double, 0><<<grid, 128, 0, s>>>(P, K, Fv, static_cast<double*>(f), refs);
             break;
         default:
             return cudaErrorInvalidValue;

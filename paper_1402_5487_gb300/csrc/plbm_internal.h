@@ -177,6 +177,16 @@ cudaError_t ce_apply_delta(const float* F, const float* d, long long n, const fl
 int ce_sum_blocks();
 cudaError_t ce_field_sums(const float* F, long long n, double* partial, cudaStream_t s);
 cudaError_t ce_reconstruct(int prec, const LatticeParams& P, const float* F, void* f, cudaStream_t s);
+// A lattice of a batched launch over lattices of one model (the same
+// LatticeParams but for the arrays): its population array and its index in the
+// field stacks (fields of lattice `index` start at index * nx * ny).
+struct LatticeRef {
+    void* f;
+    long long index;
+};
+// ce_reconstruct for n lattices in one launch (grid.z = lattice): refs in device memory.
+cudaError_t ce_reconstruct_batch(int prec, const LatticeParams& P, const float* F, const LatticeRef* refs, int n,
+                                 cudaStream_t s);
 // Shift the predicted fields of nlat lattices so that their global mass,
 // momentum and energy equal the old fields' (delta: 4 floats per lattice).
 cudaError_t ce_conserve(const float* Fold, float* Fnew, long long n, int nlat, double* partial_old,
@@ -237,6 +247,10 @@ cudaError_t launch_get_pop3(int prec, const LatticeParams& P, const void* f, dou
 cudaError_t launch_set_pop3(int prec, const LatticeParams& P, const double* in, void* f, cudaStream_t s);
 cudaError_t launch_moments_pack(int prec, const LatticeParams& P, const void* f, float* F, void* x,
                                 const float* mean_in, const float* std_in, cudaStream_t stream);
+// launch_moments_pack for n lattices of one model in one launch; F and x are the
+// stacks, lattice r writes at r.index * nx * ny.
+cudaError_t launch_moments_pack_batch(int prec, const LatticeParams& P, const LatticeRef* refs, int n, float* F,
+                                      void* x, const float* mean_in, const float* std_in, cudaStream_t stream);
 // Per-block partial sums of the stored state, then one deterministic final pass
 // writing out[0..5] = mass, jx, jy, energy, rho_min, theta_min.
 cudaError_t launch_reduce_state(int prec, const LatticeParams& P, const void* f, double* out,

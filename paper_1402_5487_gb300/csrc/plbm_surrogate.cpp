@@ -64,6 +64,8 @@ struct Sur {
     double* drift = nullptr;        // device: drift of every lattice of the last advance
     plbm::PairParams* fb_table = nullptr;  // device: batched fallback of row-paired lattices
     unsigned short* fb_tile_inst = nullptr;  // device: lattice of every fallback tile (interleaved order)
+    plbm::LatticeRef* dref = nullptr;   // device: lattices of the batched moments and reconstruction launches
+    plbm::LatticeRef* href = nullptr;   // pinned host copy (2 x max_batch: moments, then reconstruction)
     int sms = 0;
     std::vector<double> last_drift;
     std::vector<unsigned short> fb_tiles;  // host copy of fb_tile_inst (kept for the async copy)
@@ -109,16 +111,27 @@ void free_sur(Sur* s) {
     if (s->stream) cudaStreamSynchronize(s->stream);
     void* bufs[] = {s->p, s->g, s->m, s->v, s->pr, s->wbf, s->wflip, s->w6flip, s->dz[0], s->dz[1], s->dz[2],
                     s->dz[3], s->dz[4], s->dout, s->part, s->part_b, s->loss_part, s->Fold, s->Fnew, s->xin,
-                    s->planes, s->sums, s->wtc, s->derr, s->win, s->wout, s->drift, s->fb_table, s->fb_tile_inst};
+                    s->planes, s->sums, s->wtc, s->derr, s->win, s->wout, s->drift, s->fb_table, s->fb_tile_inst,
+                    s->dref};
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (void* a : s->act)
         if (a) cudaFree(a);
     if (s->host_loss) cudaFreeHost(s->host_loss);
     if (s->host_sums) cudaFreeHost(s->host_sums);
+    if (s->href) cudaFreeHost(s->href);
     if (s->ev) cudaEventDestroy(s->ev);
     if (s->owns_stream) cudaStreamDestroy(s->stream);
     delete s;
+}
+
+// Whether two lattices share every parameter the per-lattice kernels of an
+// advance read (all but their arrays, status word and reduction scratch).
+bool same_model(const plbm::LatticeParams& a, const plbm::LatticeParams& b) {
+    plbm::LatticeParams x = a, y = b;
+    x.status = y.status = nullptr;
+    x.partials = y.partials = nullptr;
+    return std::memcmp(&x, &y, sizeof x) == 0;
 }
 
 void* wtc_fwd(Sur* s, int l) { return static_cast<char*>(s->wtc) + (size_t)(2 * (l - 1)) * 9 * 64 * 64 * 2; }
@@ -264,6 +277,7 @@ plbm_status plbm_sur_create(int max_batch, int H, int W, unsigned long long seed
         {&s->wout, 9 * 16 * 64 * 2}, {(void**)&s->drift, (size_t)max_batch * 24 + 16},
         {(void**)&s->fb_table, (size_t)max_batch * sizeof(plbm::PairParams)},
         {(void**)&s->fb_tile_inst, (size_t)max_batch * ((W + 127) / 128) * ((H + 1) / 2) * sizeof(unsigned short) + 256},
+        {(void**)&s->dref, (size_t)2 * max_batch * sizeof(plbm::LatticeRef)},
     };
     for (auto& a : allocs) {
         if (cudaMalloc(a.p, a.n) != cudaSuccess) {
@@ -281,7 +295,8 @@ plbm_status plbm_sur_create(int max_batch, int H, int W, unsigned long long seed
     }
     if (cudaMalloc(&s->act[5], pix * 4 * 4) != cudaSuccess ||
         cudaMallocHost((void**)&s->host_loss, 1024 * 4) != cudaSuccess ||
-        cudaMallocHost((void**)&s->host_sums, (size_t)max_batch * 2 * 64 * 4 * 8) != cudaSuccess) {
+        cudaMallocHost((void**)&s->host_sums, (size_t)max_batch * 2 * 64 * 4 * 8) != cudaSuccess ||
+        cudaMallocHost((void**)&s->href, (size_t)2 * max_batch * sizeof(plbm::LatticeRef)) != cudaSuccess) {
         serr(s, "allocation failed");
         free_sur(s);
         return PLBM_E_NOMEM;
@@ -515,14 +530,26 @@ plbm_status plbm_sur_advance(plbm_surrogate h, plbm_handle* hs, int n, int K, do
             return PLBM_E_ARG;
         }
     }
+    // Lattices of one model (the same parameters but for their arrays) take the
+    // per-lattice kernels below in one launch each (grid.z = lattice).
+    bool one_model = n > 1;
+    for (int b = 1; b < n && one_model; ++b) one_model = views[b].prec == views[0].prec && same_model(*views[b].P, *views[0].P);
     // 1. fields and network input of every lattice, on the surrogate's stream
     //    once the lattice's own stream has reached this point
     for (int b = 0; b < n; ++b) {
         SCK(cudaEventRecord(s->ev, views[b].stream));
         SCK(cudaStreamWaitEvent(s->stream, s->ev, 0));
-        SCK(plbm::launch_moments_pack(views[b].prec, *views[b].P, views[b].f_cur, s->Fold + (size_t)b * npix * 4,
-                                      static_cast<char*>(s->xin) + (size_t)b * npix * 4 * 2, s->norm, s->norm + 4,
-                                      s->stream));
+        if (!one_model)
+            SCK(plbm::launch_moments_pack(views[b].prec, *views[b].P, views[b].f_cur, s->Fold + (size_t)b * npix * 4,
+                                          static_cast<char*>(s->xin) + (size_t)b * npix * 4 * 2, s->norm,
+                                          s->norm + 4, s->stream));
+    }
+    if (one_model) {
+        for (int b = 0; b < n; ++b) s->href[b] = plbm::LatticeRef{views[b].f_cur, b};
+        SCK(cudaMemcpyAsync(s->dref, s->href, (size_t)n * sizeof(plbm::LatticeRef), cudaMemcpyHostToDevice,
+                            s->stream));
+        SCK(plbm::launch_moments_pack_batch(views[0].prec, *views[0].P, s->dref, n, s->Fold, s->xin, s->norm,
+                                            s->norm + 4, s->stream));
     }
     // 2. network, predicted fields, drift of the conserved sums
     plbm_status r = forward(s, n, s->xin);
@@ -540,14 +567,23 @@ plbm_status plbm_sur_advance(plbm_surrogate h, plbm_handle* hs, int n, int K, do
     // 3. accepted lattices: Chapman-Enskog populations on the surrogate's stream,
     //    which the lattice's stream then waits for; the others run K LBM steps
     bool any = false;
+    int nacc = 0;
     for (int b = 0; b < n; ++b) {
         const bool fall = !(s->last_drift[b] <= tol);
         if (fell_back) fell_back[b] = fall ? 1 : 0;
         if (fall) continue;
-        SCK(plbm::ce_reconstruct(views[b].prec, *views[b].P, s->Fnew + (size_t)b * npix * 4, views[b].f_cur,
-                                 s->stream));
+        if (one_model)
+            s->href[s->Bm + nacc++] = plbm::LatticeRef{views[b].f_cur, b};
+        else
+            SCK(plbm::ce_reconstruct(views[b].prec, *views[b].P, s->Fnew + (size_t)b * npix * 4, views[b].f_cur,
+                                     s->stream));
         *views[b].steps += K;
         any = true;
+    }
+    if (nacc > 0) {
+        SCK(cudaMemcpyAsync(s->dref + s->Bm, s->href + s->Bm, (size_t)nacc * sizeof(plbm::LatticeRef),
+                            cudaMemcpyHostToDevice, s->stream));
+        SCK(plbm::ce_reconstruct_batch(views[0].prec, *views[0].P, s->Fnew, s->dref + s->Bm, nacc, s->stream));
     }
     // Fallback lattices in the row-paired layout (one precision) take K steps
     // together, one persistent launch per step over all of them (the batched
