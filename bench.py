@@ -44,7 +44,7 @@ THETA0 = 1.0
 ELEM = {"f64": 8, "f32": 4, "f16dev": 2, "bf16dev": 2}
 
 
-KERNEL_NAME = {"f32": "k_stream_collide_pair<float>", "f16dev": "k_stream_collide_pair<__half>",
+KERNEL_NAME = {"f32": "k_stream_collide_pair<float>", "f16dev": "k_stream_collide_pair2<__half>",
                "bf16dev": "k_stream_collide_pair<__nv_bfloat16>", "f64": "k_stream_collide<double,5,2>"}
 
 
