@@ -549,8 +549,8 @@ const char *plbm_slabs_last_error(plbm_slabs s);
 
 /* Diagnostics for callers that cannot allocate device memory.  The paper has
  * no counterpart; this is a service of the library.  Some callers cannot call
- * cudaMalloc: code recording a CUDA graph, plug-ins whose host application owns
- * every allocation, or embedded set-ups that forbid allocation after start-up.
+ * cudaMalloc: plug-ins whose host application owns every allocation, or
+ * embedded set-ups that forbid allocation after start-up.
  * This call needs no handle, allocates nothing (no cudaMalloc or cudaFree, no
  * allocating library routine) and keeps its only scratch in a static device
  * array of PLBM_NOALLOC_MAX_NODES / 256 records (1 MiB) that every GPU loading
@@ -565,8 +565,8 @@ const char *plbm_slabs_last_error(plbm_slabs s);
  * caller created and made current with the driver API.  The static array has
  * its own address in each context; the first call in a context looks that
  * address up (cudaGetSymbolAddress) and caches it under the context's unique
- * ID (cuCtxGetId), for up to 64 contexts at a time; make that first call before
- * any stream capture starts.  All calls share the one array of their context:
+ * ID (cuCtxGetId), for up to 64 contexts at a time.  All calls share the one
+ * array of their context:
  * calls that overlap on the GPU race and may return wrong sums, so serialise
  * them.
  * Errors: PLBM_E_ARG for bad arguments or nx * ny > PLBM_NOALLOC_MAX_NODES;

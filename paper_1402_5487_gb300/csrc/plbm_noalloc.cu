@@ -1,10 +1,9 @@
 // plbm_diagnostics_noalloc: global sums and extrema of caller-held FP64
 // populations for callers that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc at all: code running inside a CUDA
-// graph that is being captured, plug-ins whose host application owns every
-// allocation (custom allocators, fixed memory budgets), or embedded setups that
-// forbid allocation after start-up.  This entry point needs no handle and no
+// Some callers cannot call cudaMalloc at all: plug-ins whose host application
+// owns every allocation (custom allocators, fixed memory budgets), or embedded
+// setups that forbid allocation after start-up.  This entry point needs no handle and no
 // workspace.  Its only scratch (one partial-sum record per block) lives in the
 // file-scope device array below, which every GPU that loads the library holds
 // until the process exits.
@@ -16,8 +15,7 @@
 // so a context destroyed by cudaDeviceReset or cuCtxDestroy and a new one at
 // the same handle value never share an entry).  Any context works: the
 // device's primary context of the runtime API, or one the caller created and
-// made current with the driver API.  Make the first call in each context
-// before any stream capture begins.
+// made current with the driver API.
 //
 // Every call shares the one array.  Each block writes its own record before
 // the final pass reads it, so nothing has to start at zero and stale contents

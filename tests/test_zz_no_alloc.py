@@ -1,7 +1,7 @@
 """plbm_diagnostics_noalloc against plbm_diagnostics (GPU).
 
-Some callers cannot allocate device memory (graph capture, host-owned memory,
-no-allocation embedded set-ups).  plbm_diagnostics_noalloc serves them with a
+Some callers cannot allocate device memory (host-owned memory, no-allocation
+embedded set-ups).  plbm_diagnostics_noalloc serves them with a
 static scratch array instead of a workspace.  This test calls it through the C
 ABI on caller-held device populations and checks its six outputs against the
 handle-based plbm_diagnostics on the same state, twice in a row with different
