@@ -705,14 +705,17 @@ def test_rest_state_is_a_fixed_point(prec, dim):
     s.close()
 
 
-@pytest.mark.parametrize("prec,ny", [("f32", 48), ("f16dev", 48), ("bf16dev", 48), ("f16dev", 12),
-                                     ("bf16dev", 16), ("f16dev", 20)])
-def test_plain_and_row_paired_layouts_give_the_same_state(prec, ny):
+@pytest.mark.parametrize("prec,ny,nx", [("f32", 48, 70), ("f16dev", 48, 70), ("bf16dev", 48, 70), ("f16dev", 12, 70),
+                                        ("bf16dev", 16, 70), ("f16dev", 20, 70), ("f16dev", 14, 50),
+                                        ("f16dev", 22, 200), ("f16dev", 2, 1)])
+def test_plain_and_row_paired_layouts_give_the_same_state(prec, ny, nx):
     # The plain-layout kernel (one node per thread: odd ny, PLBM_FLAG_PLAIN_LAYOUT)
     # runs the single-lane forms of the row-paired kernel's packed operations,
     # each correctly rounded, so both layouts give every node the same bits.
     # ny = 12, 16, 20: most pair rows pull across the pair boundary (swapped lanes).
-    nx = 70
+    # FP16 steps take two node pairs per thread (tiles of 64 pairs): nx = 50, ny = 14
+    # gives an odd tile count (the last thread block has one tile), nx = 200 a ragged
+    # last tile, and 1 x 2 a single node pair.
     fields = I.kh_fields(nx, ny=ny)
     out = []
     for plain in (False, True):
