@@ -384,3 +384,32 @@ def test_input_noise_is_the_stated_counter_based_normal_draw():
     assert L.plbm_sur_assemble_noise(net.h, stack.data_ptr(), npix, pairs.data_ptr(), 2, x1.data_ptr(), y.data_ptr(),
                                      -1.0, seed) == plbm.PLBM_E_ARG
     net.close()
+
+
+def test_one_launch_per_model_equals_one_launch_per_lattice(trained):
+    # Lattices that share a model take the moments/input and the reconstruction
+    # kernels of an advance in one launch each; a set that mixes models (another
+    # omega, another storage precision) takes them per lattice.  The per-node code
+    # is the same and the network treats every lattice on its own, so each
+    # lattice must end with the same bits either way.
+    net = trained[0]
+    L = 128
+
+    def mk(seed, omega=SG.OMEGA, prec="f32"):
+        s = plbm.Solver(2, SG.V5, omega, L, L, theta0=SG.THETA0, prec=prec)
+        s.init(*SG.trajectory_fields(seed, L))
+        s.step(64)
+        return s
+
+    same = [mk(4000), mk(4001)]                                       # one model: batched launches
+    mixed = [mk(4000), mk(4001), mk(4002, omega=1.6), mk(4003, prec="f16dev")]
+    alone = [mk(4002, omega=1.6), mk(4003, prec="f16dev")]
+    assert net.advance(same, K=32, tol=1.0) == [0, 0]
+    assert net.advance(mixed, K=32, tol=1.0) == [0, 0, 0, 0]
+    for s in alone:
+        assert net.advance([s], K=32, tol=1.0) == [0]
+    for x, y in zip(same + alone, mixed):
+        assert np.array_equal(x.get_populations(), y.get_populations())
+        assert x.diagnostics()["steps"] == y.diagnostics()["steps"] == 96
+    for s in same + mixed + alone:
+        s.close()
