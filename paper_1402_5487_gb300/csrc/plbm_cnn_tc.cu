@@ -192,6 +192,28 @@ __device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
+// TMA tile store of a 2D box from shared memory (bulk async group of this thread).
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int c0, int c1, uint32_t src) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];\n" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(c0), "r"(c1), "r"(src)
+                 : "memory");
+}
+// Named barrier `id` over `n` threads that also returns the OR of their predicates.
+__device__ __forceinline__ bool bar_or(int id, int n, bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "barrier.red.or.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(id), "r"(n)
+        : "memory");
+    return r != 0;
+}
+__device__ __forceinline__ void bar_named(int id, int n) { asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(n) : "memory"); }
+
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
                  : "memory");
@@ -278,6 +300,39 @@ __device__ __forceinline__ void store64(const uint32_t (&v)[64], int mode, int r
     }
 }
 
+// The same 64 outputs of pixel px into a shared tile of 128 pixels x 128 bytes in
+// the 128-byte swizzle of a TMA box (16-byte chunk q of pixel p at
+// p * 128 + (q ^ (p mod 8)) * 16): the 32 lanes of a warp store 512 bytes per
+// instruction without bank conflicts.
+__device__ __forceinline__ void stage64(const uint32_t (&v)[64], int mode, int relu, const float* __restrict__ bias,
+                                        const __nv_bfloat16* __restrict__ mask, uint32_t stage, int px) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        float f[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) f[k] = __uint_as_float(v[8 * q + k]);
+        if (mode == 0) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                f[k] += bias[8 * q + k];
+                if (relu) f[k] = fmaxf(f[k], 0.0f);
+            }
+        } else {
+            const uint4 mk = *reinterpret_cast<const uint4*>(mask + 8 * q);
+            const __nv_bfloat16* m = reinterpret_cast<const __nv_bfloat16*>(&mk);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) f[k] = __bfloat162float(m[k]) > 0.0f ? f[k] : 0.0f;
+        }
+        uint4 o;
+        __nv_bfloat162* ob = reinterpret_cast<__nv_bfloat162*>(&o);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) ob[k] = __floats2bfloat162_rn(f[2 * k], f[2 * k + 1]);
+        const uint32_t a = stage + (uint32_t)px * 128u + (uint32_t)((q ^ (px & 7)) * 16);
+        asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n" ::"r"(a), "r"(o.x), "r"(o.y), "r"(o.z), "r"(o.w)
+                     : "memory");
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Ring-staged convolution with 64 input channels.
 // MODE 0: Y bf16 [.][64] = relu?(conv + bias)    (N = 64)
@@ -301,10 +356,14 @@ static_assert(kRing >= 3 + kLoaders, "three rows feed the MMAs while every loade
 constexpr uint32_t kRowTxBytes = 8 * kTile * 16;  // the eight TMA boxes of a row
 constexpr int kHaloLanes = 16;         // two wrapped pixels x 8 chunks
 constexpr int kRingBytes = kRing * kSeg + kPlaneOff;
-constexpr int kRingWOff = ((kRingBytes + 1023) / 1024) * 1024;  // weights after the ring, 1024-aligned
+constexpr int kRingSOff = ((kRingBytes + 1023) / 1024) * 1024;  // output staging tile after the ring
+constexpr int kStageBytes = kTile * kC * 2;                      // 128 pixels x 64 bf16 (N = 64 modes)
+template <int N>
+__host__ __device__ constexpr int ring_woff() { return kRingSOff + (N == 64 ? kStageBytes : 0); }  // weights, 1024-aligned
 constexpr int kRingBarBytes = 512 + 256;  // barriers, TMEM slot, abort flag, then 64 fp32 biases
 template <int N>
-constexpr int ring_smem() { return 1024 + kRingWOff + 9 * N * 128 + kRingBarBytes; }
+constexpr int ring_smem() { return 1024 + ring_woff<N>() + 9 * N * 128 + kRingBarBytes; }
+static_assert(ring_smem<64>() <= 232448, "ring kernel shared memory within the 227 KB a CTA may use");
 constexpr int kAcc = 8;                  // TMEM accumulators (all 512 columns); issuer q uses acc = q mod 2
 constexpr uint32_t kRingTmemCols = 64 * kAcc;
 
@@ -333,8 +392,8 @@ __device__ __forceinline__ Strip strip_at(int t, int t1, int H, int tiles_x) {
 // with a box of 128 pixels x 1 chunk.
 template <int N, int MODE>
 __global__ void __launch_bounds__(kRingThreads, 1)
-k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const __nv_bfloat16* __restrict__ X,
-            const __nv_bfloat16* __restrict__ Wk, const float* __restrict__ bias,
+k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
+            const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ Wk, const float* __restrict__ bias,
             const __nv_bfloat16* __restrict__ mask, void* __restrict__ Yv, int relu, const TcErr err) {
     static_assert((N == 64 && MODE < 2) || (N == 16 && MODE == 2), "ring conv shapes");
     extern __shared__ unsigned char dsm_raw[];
@@ -342,8 +401,9 @@ k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const 
     const uint32_t pad = (1024 - (raw & 1023)) & 1023;
     unsigned char* base = dsm_raw + pad;
     const uint32_t sRing = raw + pad;
-    const uint32_t sW = sRing + kRingWOff;
-    unsigned char* bars_p = base + kRingWOff + 9 * N * 128;
+    const uint32_t sStage = sRing + kRingSOff;
+    const uint32_t sW = sRing + ring_woff<N>();
+    unsigned char* bars_p = base + ring_woff<N>() + 9 * N * 128;
     const uint32_t bars = s2u(bars_p);
     volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(bars_p + kBarCount * 8);
     volatile int* abortp = reinterpret_cast<volatile int*>(bars_p + kBarCount * 8 + 8);
@@ -519,16 +579,24 @@ k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const 
         }
         __syncwarp();
     } else {
-        // ---- epilogue: warps 5..8, TMEM lanes 32 (warp % 4) .. + 31 ----
+        // ---- epilogue: warps 5..8, TMEM lanes 32 (warp % 4) .. + 31.  For N = 64 the
+        // tile's 128 x 64 bf16 outputs go through a shared staging tile in the 128-byte
+        // swizzle and leave as one TMA store: written straight from the threads
+        // (128 bytes per pixel, pixels 128 bytes apart) they took 32 L1 wavefronts per
+        // warp store, which the MMAs' shared-memory operand reads then waited behind.
+        // The four warps decide together whether to go on (a barrier that ORs their
+        // wait results), so an abort never leaves one of them at the next barrier. ----
         const int quad = warp & 3;
         const int px = 32 * quad + lane;
+        const bool leader = warp == kLoaders + kIssuers && lane == 0;
         uint32_t tcount = 0;
         bool ok = true;
         for (int t = t_begin; t < t_end && ok;) {
             const Strip s = strip_at(t, t_end, H, tiles_x);
             for (int i = 0; i < s.n; ++i) {
                 const uint32_t acc = tcount % kAcc;
-                if (!bar_wait(bar(kBarTFull + acc), (tcount / kAcc) & 1, abortp, err.wait_ns)) {
+                const bool got = bar_wait(bar(kBarTFull + acc), (tcount / kAcc) & 1, abortp, err.wait_ns);
+                if (bar_or(1, 128, !got || *abortp)) {
                     ok = false;
                     break;
                 }
@@ -549,7 +617,7 @@ k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const 
                     o.y = __uint_as_float(v[1]) + sbias[1];
                     o.z = __uint_as_float(v[2]) + sbias[2];
                     o.w = __uint_as_float(v[3]) + sbias[3];
-                    reinterpret_cast<float4*>(Yv)[pix] = o;
+                    reinterpret_cast<float4*>(Yv)[pix] = o;   // 16 bytes per pixel: coalesced
                 } else {
                     uint32_t v[64];
                     PLBM_TMEM_LD32(v, 0, taddr);
@@ -557,13 +625,23 @@ k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const 
                     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
                     tc_before_sync();
                     bar_arrive(bar(kBarTEmpty + acc));
-                    store64(v, MODE, relu, sbias, MODE == 1 ? mask + pix * kC : nullptr,
-                            static_cast<__nv_bfloat16*>(Yv) + pix * kC);
+                    // the previous tile's store has finished reading the staging tile
+                    if (leader) asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+                    bar_named(1, 128);
+                    stage64(v, MODE, relu, sbias, MODE == 1 ? mask + pix * kC : nullptr, sStage, px);
+                    fence_async_smem();
+                    bar_named(1, 128);
+                    if (leader) {
+                        tma_store_2d(&tmY, 0, (int)(pix - px), sStage);
+                        asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+                    }
                 }
                 ++tcount;
             }
             t += s.n;
         }
+        // every store has left the staging tile and reached global memory
+        if (leader) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
     }
     __syncthreads();
     if (tid == 0 && *abortp) {
@@ -1120,13 +1198,41 @@ static cudaError_t encode_act_map(CUtensorMap* map, const void* X, int B, int H,
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// Tensor map of a bf16 NHWC output with 64 channels as [pixels][64] (box: 64
+// channels x 128 pixels, 128-byte swizzle), for the ring epilogue's TMA stores.
+static cudaError_t encode_out_map(CUtensorMap* map, void* Y, long long npix) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q{};
+        void* fn = nullptr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    if (reinterpret_cast<uintptr_t>(Y) % 16) return cudaErrorMisalignedAddress;
+    const cuuint64_t dims[2] = {64, (cuuint64_t)npix};
+    const cuuint64_t strides[1] = {128};
+    const cuuint32_t box[2] = {64, (cuuint32_t)tc::kTile};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Y, dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <int N, int MODE>
 static cudaError_t launch_ring(int B, int H, int W, const void* X, const void* Wk, const float* bias,
                                const void* mask, void* Y, int relu, TcErr err, cudaStream_t s) {
     if (W % tc::kTile || H < 1 || B < 1) return cudaErrorInvalidValue;
-    CUtensorMap map;
+    CUtensorMap map, mapY;
     cudaError_t em = encode_act_map(&map, X, B, H, W);
     if (em != cudaSuccess) return em;
+    if (N == 64) {
+        em = encode_out_map(&mapY, Y, (long long)B * H * W);
+        if (em != cudaSuccess) return em;
+    } else {
+        mapY = map;   // not used by the 64 -> 4 layer (fp32 stores from the threads)
+    }
     constexpr int smem = tc::ring_smem<N>();
     static bool attr = false;
     if (!attr) {
@@ -1137,7 +1243,7 @@ static cudaError_t launch_ring(int B, int H, int W, const void* X, const void* W
     const int ntiles = B * H * (W / tc::kTile);
     const int grid = ntiles < tc_sms() ? ntiles : tc_sms();
     tc::k_conv_ring<N, MODE><<<grid, tc::kRingThreads, smem, s>>>(
-        B, H, W, map, static_cast<const __nv_bfloat16*>(X), static_cast<const __nv_bfloat16*>(Wk), bias,
+        B, H, W, map, mapY, static_cast<const __nv_bfloat16*>(X), static_cast<const __nv_bfloat16*>(Wk), bias,
         static_cast<const __nv_bfloat16*>(mask), Y, relu, err);
     return cudaGetLastError();
 }
