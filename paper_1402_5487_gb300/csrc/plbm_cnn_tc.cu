@@ -303,7 +303,8 @@ __device__ __forceinline__ void store64(const uint32_t (&v)[64], int mode, int r
 // The same 64 outputs of pixel px into a shared tile of 128 pixels x 128 bytes in
 // the 128-byte swizzle of a TMA box (16-byte chunk q of pixel p at
 // p * 128 + (q ^ (p mod 8)) * 16): the 32 lanes of a warp store 512 bytes per
-// instruction without bank conflicts.
+// instruction without bank conflicts.  Mode 1 with no mask pointer reads the
+// pixel's mask from the tile itself (staged there beforehand) and overwrites it.
 __device__ __forceinline__ void stage64(const uint32_t (&v)[64], int mode, int relu, const float* __restrict__ bias,
                                         const __nv_bfloat16* __restrict__ mask, uint32_t stage, int px) {
 #pragma unroll
@@ -317,8 +318,18 @@ __device__ __forceinline__ void stage64(const uint32_t (&v)[64], int mode, int r
                 f[k] += bias[8 * q + k];
                 if (relu) f[k] = fmaxf(f[k], 0.0f);
             }
-        } else {
-            const uint4 mk = *reinterpret_cast<const uint4*>(mask + 8 * q);
+        }
+        const uint32_t a = stage + (uint32_t)px * 128u + (uint32_t)((q ^ (px & 7)) * 16);
+        if (mode == 1) {
+            uint4 mk;
+            if (mask) {
+                mk = *reinterpret_cast<const uint4*>(mask + 8 * q);
+            } else {
+                asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];\n"
+                             : "=r"(mk.x), "=r"(mk.y), "=r"(mk.z), "=r"(mk.w)
+                             : "r"(a)
+                             : "memory");
+            }
             const __nv_bfloat16* m = reinterpret_cast<const __nv_bfloat16*>(&mk);
 #pragma unroll
             for (int k = 0; k < 8; ++k) f[k] = __bfloat162float(m[k]) > 0.0f ? f[k] : 0.0f;
@@ -327,7 +338,6 @@ __device__ __forceinline__ void stage64(const uint32_t (&v)[64], int mode, int r
         __nv_bfloat162* ob = reinterpret_cast<__nv_bfloat162*>(&o);
 #pragma unroll
         for (int k = 0; k < 4; ++k) ob[k] = __floats2bfloat162_rn(f[2 * k], f[2 * k + 1]);
-        const uint32_t a = stage + (uint32_t)px * 128u + (uint32_t)((q ^ (px & 7)) * 16);
         asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n" ::"r"(a), "r"(o.x), "r"(o.y), "r"(o.z), "r"(o.w)
                      : "memory");
     }
@@ -628,7 +638,24 @@ k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const 
                     // the previous tile's store has finished reading the staging tile
                     if (leader) asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
                     bar_named(1, 128);
-                    stage64(v, MODE, relu, sbias, MODE == 1 ? mask + pix * kC : nullptr, sStage, px);
+                    if (MODE == 1) {
+                        // the warp's 32 mask pixels (4 KB, contiguous) with coalesced loads:
+                        // lane l takes chunk l mod 8 of pixel 4 k + l / 8, into the pixel's
+                        // swizzled place in the staging tile, where stage64 reads it back
+                        const __nv_bfloat16* mw = mask + (pix - lane) * kC;
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            const int p = 4 * k + (lane >> 3), c = lane & 7;
+                            const uint4 mv = *reinterpret_cast<const uint4*>(mw + p * kC + c * 8);
+                            const int pt = 32 * quad + p;
+                            const uint32_t a = sStage + (uint32_t)pt * 128u + (uint32_t)((c ^ (pt & 7)) * 16);
+                            asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n" ::"r"(a), "r"(mv.x), "r"(mv.y),
+                                         "r"(mv.z), "r"(mv.w)
+                                         : "memory");
+                        }
+                        __syncwarp();
+                    }
+                    stage64(v, MODE, relu, sbias, nullptr, sStage, px);
                     fence_async_smem();
                     bar_named(1, 128);
                     if (leader) {
@@ -664,27 +691,30 @@ k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const 
 // A row of a pixel: K = tap * 4 + ci for the 36 products, zero to K = 48, in the
 // no-swizzle chunk-planar layout (6 planes of 128 pixels x 16 bytes).
 // Win: bf16 [6 chunks][64 n][8], the same layout for B (plane = 64 x 16 bytes).
-// One tile at a time per CTA; several CTAs per SM overlap.
+// One tile at a time per CTA; several CTAs per SM overlap.  Once a tile's MMAs
+// are done, its A region holds the tile's outputs in the 128-byte swizzle of a
+// TMA box, and one TMA store writes them (coalesced, off the threads).
 // ---------------------------------------------------------------------------
 constexpr int kInThreads = 128;
 constexpr int kInPlanes = 6;
 constexpr int kInA = kInPlanes * kTile * 16;  // 12288
+constexpr int kInAS = kTile * kC * 2;         // 16384: A, then the output staging tile
 constexpr int kInB = kInPlanes * kC * 16;     // 6144
 constexpr int kInBar = 64 + 256;  // barriers, TMEM slot, abort flag, 64 fp32 biases
-constexpr int kInSmem = 26 * 1024;  // A, B, barriers and padding that caps residency at 8 CTAs per SM
-static_assert(128 + kInA + kInB + kInBar <= kInSmem, "input-layer shared memory");
+constexpr int kInSmem = 26 * 1024;  // A/staging, B, barriers and padding that caps residency at 8 CTAs per SM
+static_assert(kInA <= kInAS && 1024 + kInAS + kInB + kInBar <= kInSmem, "input-layer shared memory");
 constexpr uint32_t kInTmemCols = 64;
 
 __global__ void __launch_bounds__(kInThreads)
 k_conv_in_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ Win,
-             const float* __restrict__ bias, __nv_bfloat16* __restrict__ Y, int relu, const TcErr err) {
+             const float* __restrict__ bias, const __grid_constant__ CUtensorMap tmY, int relu, const TcErr err) {
     extern __shared__ unsigned char dsm_raw[];
     const uint32_t raw = s2u(dsm_raw);
-    const uint32_t pad = (128 - (raw & 127)) & 127;
+    const uint32_t pad = (1024 - (raw & 1023)) & 1023;   // the staging tile's swizzle wants 1024-byte alignment
     unsigned char* base = dsm_raw + pad;
     const uint32_t sA = raw + pad;
-    const uint32_t sB = sA + kInA;
-    unsigned char* bars_p = base + kInA + kInB;
+    const uint32_t sB = sA + kInAS;
+    unsigned char* bars_p = base + kInAS + kInB;
     const uint32_t bar_mma = s2u(bars_p), bar_drain = bar_mma + 8;
     volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(bars_p + 16);
     volatile int* abortp = reinterpret_cast<volatile int*>(bars_p + 24);
@@ -702,7 +732,7 @@ k_conv_in_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __n
     }
     if (warp == 0) tmem_alloc(s2u(bars_p + 16), kInTmemCols);
     for (int i = tid; i < kInB / 16; i += kInThreads)
-        *reinterpret_cast<uint4*>(base + kInA + 16 * i) = reinterpret_cast<const uint4*>(Win)[i];
+        *reinterpret_cast<uint4*>(base + kInAS + 16 * i) = reinterpret_cast<const uint4*>(Win)[i];
     fence_async_smem();
     tc_before_sync();
     __syncthreads();
@@ -723,7 +753,6 @@ k_conv_in_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __n
             g[tap] = *reinterpret_cast<const uint2*>(X + (((size_t)b * H + yy) * W + xx) * 4);
         }
     };
-    *reinterpret_cast<uint4*>(base + 5 * kTile * 16 + tid * 16) = make_uint4(0u, 0u, 0u, 0u);
     uint2 g[9];
     if ((int)blockIdx.x < ntiles) gather(blockIdx.x, g);
     uint32_t phase = 0;
@@ -732,7 +761,11 @@ k_conv_in_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __n
         const int b = t / (H * tiles_x);
         const int rem = t - b * H * tiles_x;
         const int y = rem / tiles_x;
-        const int x = (rem - y * tiles_x) * kTile + tid;
+        const int x0 = (rem - y * tiles_x) * kTile;
+        // the previous tile's store has finished reading the region A is written to
+        if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+        __syncthreads();
+        *reinterpret_cast<uint4*>(base + 5 * kTile * 16 + tid * 16) = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
         for (int c = 0; c < 4; ++c)
             *reinterpret_cast<uint4*>(base + c * kTile * 16 + tid * 16) =
@@ -760,9 +793,15 @@ k_conv_in_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __n
         PLBM_TMEM_LD32(v, 32, taddr + 32);
         asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
         tc_before_sync();
-        store64(v, 0, relu, sbias, nullptr, Y + (((size_t)b * H + y) * W + x) * kC);
+        stage64(v, 0, relu, sbias, nullptr, sA, tid);
+        fence_async_smem();
         __syncthreads();
+        if (tid == 0) {
+            tma_store_2d(&tmY, 0, (int)(((size_t)b * H + y) * W + x0), sA);
+            asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+        }
     }
+    if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
     if (tid == 0 && issued) {  // drain before the accumulator is released
         tc_commit(bar_drain);
         if (!bar_wait_drain(bar_drain, 0)) *abortp = 1;
@@ -1268,11 +1307,14 @@ cudaError_t cnn_conv_in_tc(int B, int H, int W, const void* X, const void* Win, 
         if (e != cudaSuccess) return e;
         attr = true;
     }
+    CUtensorMap mapY;
+    cudaError_t em = encode_out_map(&mapY, Y, (long long)B * H * W);
+    if (em != cudaSuccess) return em;
     const int ntiles = B * H * (W / tc::kTile);
     const int grid = ntiles < 8 * tc_sms() ? ntiles : 8 * tc_sms();
     tc::k_conv_in_tc<<<grid, tc::kInThreads, tc::kInSmem, s>>>(B, H, W, static_cast<const __nv_bfloat16*>(X),
-                                                               static_cast<const __nv_bfloat16*>(Win), bias,
-                                                               static_cast<__nv_bfloat16*>(Y), relu, err);
+                                                               static_cast<const __nv_bfloat16*>(Win), bias, mapY,
+                                                               relu, err);
     return cudaGetLastError();
 }
 
