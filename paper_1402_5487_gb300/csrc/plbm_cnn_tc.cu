@@ -8,20 +8,30 @@
 // k_conv_ring<N, MODE> (64 input channels: the 64 -> 64 layers and the 64 -> 4
 // output layer with N = 16, four columns used) is warp-specialised and
 // pipelined:
-//   * warps 0..2 stage input row segments (pixels x0 - 1 .. x0 + 128, wrapped)
-//     into a ring of shared-memory slots: lane 0 issues eight TMA tile copies
-//     (cp.async.bulk.tensor, one per 16-byte channel chunk) of the 128 pixels
-//     x0 .. x0 + 127, which complete on the slot's mbarrier by byte count, and
-//     16 lanes copy the two wrapped halo pixels.  A CTA owns a run of
-//     consecutive output rows of one column of tiles, so each input row is
-//     loaded once and serves the three taps ky of three output rows;
-//   * one thread each of warps 3 and 4 issues the 36 MMAs of alternate tiles
-//     into eight TMEM accumulators (a single issuing thread that waits on
-//     barriers between tiles leaves the tensor pipe idle; two keep it fed) and
-//     commits them to mbarriers that hand the accumulator to the epilogue and
-//     the rows no later tile needs back to the loaders;
-//   * warps 5..8 read the accumulator (warp w owns TMEM lanes 32 (w % 4)..),
-//     hand it back, and run the epilogue while later tiles' MMAs run.
+//   * the CTA's tile range is cut into two streams, each with its own warps,
+//     row slots, accumulators and staging tile (below, per stream);
+//   * two loader warps stage input row segments (pixels x0 - 1 .. x0 + 128,
+//     wrapped) into the stream's ring of shared-memory slots: lane 0 issues
+//     eight TMA tile copies (cp.async.bulk.tensor, one per 16-byte channel
+//     chunk) of the 128 pixels x0 .. x0 + 127 and 16 lanes one 16-byte bulk
+//     copy each of the two wrapped halo pixels, all completing on the slot's
+//     mbarrier by byte count.
+//     A CTA owns a run of consecutive output rows of one column of tiles, so
+//     each input row is loaded once;
+//   * one issuing thread walks the input rows in order.  Input row y_in feeds
+//     the output rows y_in + 1, y_in, y_in - 1 through the taps ky = 0, 1, 2;
+//     with the weights of the three taps (ky, kx) stacked along N and the
+//     accumulators of consecutive output rows in descending TMEM columns, the
+//     three products of one (kx, K-step) are one MMA of N = 3 x 64, 12 MMAs per
+//     input row, and A, the shifted input row, is read from shared memory once
+//     per input row instead of three times per output row.  Commits hand each
+//     finished accumulator to the epilogue and each consumed row slot back to
+//     the loaders;
+//   * four epilogue warps read the accumulator (warp w owns TMEM lanes
+//     32 (w % 4) ..), hand it back and, for N = 64, write the tile's outputs into a shared
+//     staging tile in the 128-byte swizzle that one TMA store sends out.  The
+//     threads' own stores (128 bytes per pixel, pixels 128 bytes apart: 32 L1
+//     wavefronts per warp instruction) held up the MMAs' operand reads.
 // The row slots use the no-swizzle K-major layout with one plane per 16-byte
 // channel chunk (pixel p, chunk c at c * plane + 16 p): 8-row core matrices are
 // contiguous 128-byte blocks, so the tap shift kx is a 16 * kx byte offset of
@@ -192,6 +202,14 @@ __device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
+// Plain bulk copy global -> shared (16-byte aligned, size a multiple of 16),
+// completing `bar` by byte count.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
 // TMA tile store of a 2D box from shared memory (bulk async group of this thread).
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int c0, int c1, uint32_t src) {
     asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];\n" ::"l"(
@@ -247,6 +265,19 @@ struct Idesc {
     static constexpr uint32_t value = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
                                       ((uint32_t)(kTile >> 4) << 24);
 };
+
+// The same for N known at run time (a multiple of 16, 16..256).
+__device__ __forceinline__ uint32_t idesc_n(uint32_t n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((uint32_t)(kTile >> 4) << 24);
+}
+__device__ __forceinline__ void mma_n(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.u32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
 
 template <int N>
 __device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
@@ -350,9 +381,17 @@ __device__ __forceinline__ void stage64(const uint32_t (&v)[64], int mode, int r
 // MODE 2: Y fp32 [.][4]  = conv + bias           (N = 16, output columns 0..3)
 // Wk: bf16 [9 taps][N][64], K-major.
 // ---------------------------------------------------------------------------
-constexpr int kLoaders = 3;            // warps 0..2 load input rows
-constexpr int kIssuers = 2;            // warps 3, 4 issue the MMAs of alternate tiles
-constexpr int kRingThreads = 32 * (kLoaders + kIssuers + 4);  // warps 5..8 run the epilogue
+// Streams: the CTA works on the two halves of its tile range at once, each with
+// its own issuer, row slots, accumulators (256 TMEM columns) and epilogue warps,
+// so that one issuer's barrier tests and set-up between rows overlap the other
+// stream's MMAs.  At B = 16 a 64 -> 64 layer takes 71.8 us with two streams and
+// 106.7 us with one (8 row slots, 8 accumulators).
+constexpr int kStreams = 2;
+constexpr int kLoadersPer = 2;         // loader warps per stream
+constexpr int kLoaders = kStreams * kLoadersPer;
+constexpr int kIssuers = kStreams;     // warp kLoaders + q issues the MMAs of stream q
+constexpr int kEpiWarps = 4;           // epilogue warps per stream
+constexpr int kRingThreads = 32 * (kLoaders + kIssuers + kStreams * kEpiWarps);
 constexpr int kSegPix = kTile + 2;     // staged pixels per input row: x0 - 1 .. x0 + 128
 // One 16-byte channel chunk of every staged pixel (pixel p at 16 p).  A plane
 // starts 112 bytes into a 128-byte line, so pixel 1 (x0), the destination of
@@ -361,26 +400,36 @@ constexpr int kPlane = 17 * 128;       // 2176 bytes >= 130 pixels x 16 bytes
 constexpr int kPlaneOff = 112;
 constexpr int kSeg = 8 * kPlane;       // 17408 bytes per staged row
 static_assert(kSegPix * 16 <= kPlane && (kPlaneOff + 16) % 128 == 0 && kSeg % 128 == 0, "row slot layout");
-constexpr int kRing = 8;               // row slots
-static_assert(kRing >= 3 + kLoaders, "three rows feed the MMAs while every loader has one in flight");
-constexpr uint32_t kRowTxBytes = 8 * kTile * 16;  // the eight TMA boxes of a row
+constexpr int kRingS = 3;              // row slots per stream (slots kRingS q ..)
+constexpr int kRing = kStreams * kRingS;
+// A loader waits for the release of the row kRingS before its own; the row it
+// loaded before that one is at most kRingS rows back, so that release's
+// previous phase has completed and a parity test cannot be fooled.
+static_assert(kLoadersPer <= kRingS, "loader lag within the row ring");
 constexpr int kHaloLanes = 16;         // two wrapped pixels x 8 chunks
+// the eight TMA boxes of a row and the 16 bulk copies of its halo chunks
+constexpr uint32_t kRowTxBytes = 8 * kTile * 16 + kHaloLanes * 16;
 constexpr int kRingBytes = kRing * kSeg + kPlaneOff;
-constexpr int kRingSOff = ((kRingBytes + 1023) / 1024) * 1024;  // output staging tile after the ring
+constexpr int kRingSOff = ((kRingBytes + 1023) / 1024) * 1024;  // output staging tiles after the ring
 constexpr int kStageBytes = kTile * kC * 2;                      // 128 pixels x 64 bf16 (N = 64 modes)
 template <int N>
-__host__ __device__ constexpr int ring_woff() { return kRingSOff + (N == 64 ? kStageBytes : 0); }  // weights, 1024-aligned
+__host__ __device__ constexpr int ring_woff() { return kRingSOff + (N == 64 ? kStreams * kStageBytes : 0); }
 constexpr int kRingBarBytes = 512 + 256;  // barriers, TMEM slot, abort flag, then 64 fp32 biases
 template <int N>
 constexpr int ring_smem() { return 1024 + ring_woff<N>() + 9 * N * 128 + kRingBarBytes; }
 static_assert(ring_smem<64>() <= 232448, "ring kernel shared memory within the 227 KB a CTA may use");
-constexpr int kAcc = 8;                  // TMEM accumulators (all 512 columns); issuer q uses acc = q mod 2
-constexpr uint32_t kRingTmemCols = 64 * kAcc;
+constexpr uint32_t kRingTmemCols = 512;
+constexpr uint32_t kStreamCols = kRingTmemCols / kStreams;   // stream q: columns kStreamCols q ..
+constexpr int kAccS = (int)kStreamCols / 64;                 // accumulators per stream, N columns each
+// Accumulator of the stream's tile u: descending, so that the tiles of output
+// rows y + 1, y, y - 1 (consecutive u) sit in ascending TMEM columns.
+__device__ __forceinline__ uint32_t acc_slot(uint32_t u) { return (uint32_t)(kAccS - (int)(u % kAccS)) % kAccS; }
 
-// barrier slots (8 bytes each) after the weights; row slot s has one release
-// barrier per issuer (kBarEmpty + q * kRing + s)
-constexpr int kBarFull = 0, kBarEmpty = kRing, kBarTFull = (1 + kIssuers) * kRing, kBarTEmpty = kBarTFull + kAcc,
-              kBarDrain = kBarTEmpty + kAcc, kBarCount = kBarDrain + kIssuers;
+// barrier slots (8 bytes each) after the weights: per row slot a full and an
+// empty barrier, per stream and accumulator a full and an empty barrier, per
+// issuer a drain barrier
+constexpr int kBarFull = 0, kBarEmpty = kRing, kBarTFull = 2 * kRing, kBarTEmpty = kBarTFull + kStreams * kAccS,
+              kBarDrain = kBarTEmpty + kStreams * kAccS, kBarCount = kBarDrain + kIssuers;
 static_assert(kBarCount * 8 + 16 <= 512, "barrier area below the biases");
 
 // Tiles t = ((b * tiles_x + xt) * H + y); a CTA takes a contiguous range, which
@@ -406,12 +455,12 @@ k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const 
             const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ Wk, const float* __restrict__ bias,
             const __nv_bfloat16* __restrict__ mask, void* __restrict__ Yv, int relu, const TcErr err) {
     static_assert((N == 64 && MODE < 2) || (N == 16 && MODE == 2), "ring conv shapes");
+    static_assert(kAccS * N <= (int)kStreamCols, "a stream's accumulators fit its share of the TMEM columns");
     extern __shared__ unsigned char dsm_raw[];
     const uint32_t raw = s2u(dsm_raw);
     const uint32_t pad = (1024 - (raw & 1023)) & 1023;
     unsigned char* base = dsm_raw + pad;
     const uint32_t sRing = raw + pad;
-    const uint32_t sStage = sRing + kRingSOff;
     const uint32_t sW = sRing + ring_woff<N>();
     unsigned char* bars_p = base + ring_woff<N>() + 9 * N * 128;
     const uint32_t bars = s2u(bars_p);
@@ -426,13 +475,18 @@ k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const 
     const int per = (ntiles + gridDim.x - 1) / gridDim.x;
     const int t_begin = min(ntiles, (int)blockIdx.x * per);
     const int t_end = min(ntiles, t_begin + per);
+    // stream q: tiles [tq0(q), tq1(q)), the CTA's range cut into kStreams parts
+    auto tq0 = [&](int q) { return t_begin + (int)((long long)(t_end - t_begin) * q / kStreams); };
+    auto tq1 = [&](int q) { return t_begin + (int)((long long)(t_end - t_begin) * (q + 1) / kStreams); };
 
     if (tid == 0) {
-        for (int i = 0; i < kRing; ++i) bar_init(bar(kBarFull + i), 1 + kHaloLanes);
-        for (int i = 0; i < kIssuers * kRing; ++i) bar_init(bar(kBarEmpty + i), 1);
-        for (int i = 0; i < kAcc; ++i) {
+        for (int i = 0; i < kRing; ++i) {
+            bar_init(bar(kBarFull + i), 1);
+            bar_init(bar(kBarEmpty + i), 1);
+        }
+        for (int i = 0; i < kStreams * kAccS; ++i) {
             bar_init(bar(kBarTFull + i), 1);
-            bar_init(bar(kBarTEmpty + i), 128);
+            bar_init(bar(kBarTEmpty + i), 32 * kEpiWarps);
         }
         for (int i = 0; i < kIssuers; ++i) bar_init(bar(kBarDrain + i), 1);
         *abortp = 0;
@@ -441,7 +495,8 @@ k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const 
     if (warp == kLoaders) tmem_alloc(s2u(bars_p + kBarCount * 8), kRingTmemCols);
     for (int i = tid; i < 9 * N * 8; i += kRingThreads) {  // weights: 9 N rows of 8 chunks, swizzled
         const int c = i & 7, row = i >> 3;
-        cp_async16(sW + swz(row, c), Wk + (size_t)row * kC + c * 8);
+        const int tap = row / N, n = row - tap * N, ky = tap / 3, kx = tap - 3 * ky;
+        cp_async16(sW + swz((kx * 3 + ky) * N + n, c), Wk + (size_t)row * kC + c * 8);
     }
     if (MODE != 1 && tid < (MODE == 2 ? 4 : 64)) sbias[tid] = bias[tid];
     asm volatile("cp.async.wait_all;\n" ::: "memory");
@@ -452,22 +507,23 @@ k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const 
     const uint32_t tmem = *tmem_slot;
 
     if (warp < kLoaders) {
-        // ---- loaders: rows y0 - 1 .. y0 + n of every strip; loader warp w takes
-        // the rows e = w mod kLoaders.  Lane 0 arms the slot's full barrier with
-        // the TMA byte count and issues the eight chunk copies; lanes 0..15 copy
-        // the halo pixels x0 - 1 and x0 + 128 (wrapped) and arrive after a proxy
-        // fence.  Nothing waits for the TMA data here: the issuers do. ----
+        // ---- loaders: stream q = warp / 2 loads its rows k = warp mod 2, + 2, ...
+        // (rows y0 - 1 .. y0 + n of every strip, in order) into its row slots
+        // 4 q + k mod 4.  Lane 0 arms the slot's full barrier with the TMA byte
+        // count and issues the eight chunk copies; lanes 0..15 copy the halo
+        // pixels x0 - 1 and x0 + 128 (wrapped) and arrive after a proxy fence.
+        // Nothing waits for the TMA data here: the issuer does. ----
+        const int q = warp / kLoadersPer, r = warp % kLoadersPer;
         if (lane == 0) asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tmX)) : "memory");
-        uint32_t e = 0;
+        uint32_t k = 0;
         bool ok = true;
-        for (int t = t_begin; t < t_end && ok;) {
-            const Strip s = strip_at(t, t_end, H, tiles_x);
-            for (int j = 0; j < s.n + 2; ++j, ++e) {
-                if ((int)(e % kLoaders) != warp) continue;
-                const int slot = (int)(e % kRing);
-                const uint32_t par = ((e / kRing) & 1) ^ 1;
-                if (!bar_wait(bar(kBarEmpty + slot), par, abortp, err.wait_ns) ||
-                    !bar_wait(bar(kBarEmpty + kRing + slot), par, abortp, err.wait_ns)) {
+        for (int t = tq0(q); t < tq1(q) && ok;) {
+            const Strip s = strip_at(t, tq1(q), H, tiles_x);
+            for (int j = 0; j < s.n + 2; ++j, ++k) {
+                if ((int)(k % kLoadersPer) != r) continue;
+                const int slot = q * kRingS + (int)(k % kRingS);
+                const uint32_t par = ((k / kRingS) & 1) ^ 1;
+                if (!bar_wait(bar(kBarEmpty + slot), par, abortp, err.wait_ns)) {
                     ok = false;
                     break;
                 }
@@ -479,106 +535,94 @@ k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const 
 #pragma unroll
                     for (int c = 0; c < 8; ++c) tma_load_5d(seg + c * kPlane + 16, &tmX, 0, c, s.x0, yy, s.b, full);
                 }
+                __syncwarp();
                 if (lane < kHaloLanes) {
+                    // halo pixels by the async proxy too (a generic store would need a
+                    // proxy fence before the tensor cores read it)
                     const int right = lane >> 3, c = lane & 7;
                     const int xx = wrapi(right ? s.x0 + kTile : s.x0 - 1, W);
-                    const uint4 v = __ldg(reinterpret_cast<const uint4*>(
-                        X + (((size_t)s.b * H + yy) * (size_t)W + xx) * kC + c * 8));
                     const uint32_t dst = seg + c * kPlane + (right ? 16 * (kSegPix - 1) : 0);
-                    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n" ::"r"(dst), "r"(v.x), "r"(v.y),
-                                 "r"(v.z), "r"(v.w)
-                                 : "memory");
-                    fence_async_smem();
-                    bar_arrive(full);
+                    bulk_load(dst, X + (((size_t)s.b * H + yy) * (size_t)W + xx) * kC + c * 8, 16, full);
                 }
             }
             t += s.n;
         }
     } else if (warp < kLoaders + kIssuers) {
+        const int q = warp - kLoaders;
         if (lane == 0) {
-            // ---- MMA issuers: issuer q computes the tiles with local index = q
-            // mod 2.  Both walk every tile: after tile i of a strip each releases
-            // (on its own barrier of the row slot) the rows that no later tile
-            // uses, so a release arrives once all of its earlier MMAs, including
-            // every use of that row, have completed ----
-            const int q = warp - kLoaders;
+            // ---- MMA issuer of stream q.  Input row e of a strip of n output rows
+            // (pixel row y0 - 1 + e) feeds the strip's tiles i = e - ky through the
+            // taps ky in [ky_lo, ky_hi]: with the weights of the three taps (ky, kx)
+            // stacked along N (shared-memory rows (kx * 3 + ky) N + n) and the
+            // accumulators of consecutive tiles in descending TMEM columns, one
+            // MMA of up to 3 N columns per (kx, K-step) feeds all three, and A, the
+            // shifted input row, is read once per input row.  Tile i = e opens
+            // (zeroes its accumulator) with the first MMA of row e; tile i = e - 2
+            // is complete after row e. ----
             const uint64_t a0 = desc_plain(sRing + kPlaneOff, kPlane);
             const uint64_t b0 = desc_sw128(sW);
-            const uint32_t empty0 = kBarEmpty + q * kRing;
-            // entries below `ready` have been seen full; tiles below `freed` (of
-            // this issuer's accumulators) have been released by the epilogue
-            uint32_t e0 = 0, tcount = 0, ready = 0, freed = (uint32_t)q, nent = 0;
-            for (int t = t_begin; t < t_end;) {
-                const Strip s = strip_at(t, t_end, H, tiles_x);
-                nent += s.n + 2;
-                t += s.n;
-            }
-            const uint32_t ntile = (uint32_t)(t_end - t_begin);
+            const uint32_t cols = tmem + kStreamCols * (uint32_t)q;
+            uint32_t k = 0, T0 = 0, freed = 0;
             bool ok = true, issued = false;
-            for (int t = t_begin; t < t_end && ok;) {
-                const Strip s = strip_at(t, t_end, H, tiles_x);
-                for (int i = 0; i < s.n; ++i, ++tcount) {
-                    if ((int)(tcount & 1) == q) {
-                        const uint32_t need = e0 + i + 2;
-                        while (ok && ready <= need) {
-                            uint32_t b[4], par[4];
-                            const int n = (int)min(4u, nent - ready);
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) {
-                                b[k] = bar(kBarFull + (ready + k) % kRing);
-                                par[k] = ((ready + k) / kRing) & 1;
-                            }
-                            const int c = test_many(b, par, n);
-                            if (c) ready += c;
-                            else ok = bar_spin(b[0], par[0], abortp, err.wait_ns) && (++ready, true);
+            for (int t = tq0(q); t < tq1(q) && ok;) {
+                const Strip s = strip_at(t, tq1(q), H, tiles_x);
+                for (int e = 0; e < s.n + 2; ++e, ++k) {
+                    const uint32_t row_slot = q * kRingS + k % kRingS;
+                    ok = bar_spin(bar(kBarFull + row_slot), (k / kRingS) & 1, abortp, err.wait_ns);
+                    const int ky_lo = max(0, e - (s.n - 1)), ky_hi = min(2, e);
+                    if (ok && ky_lo == 0 && T0 + e >= (uint32_t)kAccS) {
+                        // tile T0 + e reuses the accumulator of tile T0 + e - kAccS; the
+                        // epilogue releases the tiles in order
+                        const uint32_t want = T0 + e - kAccS;
+                        if (freed <= want) {
+                            ok = bar_spin(bar(kBarTEmpty + q * kAccS + acc_slot(want)), (want / kAccS) & 1, abortp,
+                                          err.wait_ns);
+                            freed = want + 1;
                         }
-                        if (tcount >= (uint32_t)kAcc) {
-                            // this issuer's tiles are tcount = q, q + 2, ...; tile u frees
-                            // accumulator u mod kAcc for tile u + kAcc
-                            const uint32_t want = tcount - kAcc;
-                            while (ok && freed <= want) {
-                                uint32_t b[4], par[4];
-                                uint32_t u = freed;
-                                int n = 0;
+                    }
+                    if (!ok) break;
+                    tc_after_sync();
+                    // The MMAs of one (kx, K-step), as segments of taps ky: the opening
+                    // product of tile e alone, otherwise as many taps as fit before
+                    // the accumulators wrap around the stream's columns (at most
+                    // three segments); f = 0 for the first (kx, K-step), 1 for the rest.
+                    const uint32_t s_lo = acc_slot(T0 + e - ky_lo);
+                    uint32_t sd[2][3], sb[2][3], si[2][3], sa[2][3];
+                    bool sv[2][3];
 #pragma unroll
-                                for (int k = 0; k < 4; ++k) {
-                                    const uint32_t uk = u + 2 * k;
-                                    b[k] = bar(kBarTEmpty + uk % kAcc);
-                                    par[k] = (uk / kAcc) & 1;
-                                    if (uk + kAcc < ntile) ++n;
-                                }
-                                const int c = test_many(b, par, n);
-                                if (c) freed += 2 * c;
-                                else ok = bar_spin(b[0], par[0], abortp, err.wait_ns) && (freed += 2, true);
-                            }
+                    for (int f = 0; f < 2; ++f) {
+                        int kk = ky_lo;
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) {
+                            sv[f][j] = kk <= ky_hi;
+                            const bool open = f == 0 && kk == 0;
+                            const uint32_t sl = (s_lo + (uint32_t)(kk - ky_lo)) % kAccS;
+                            const int end = min(open ? 0 : ky_hi, kk + (int)(kAccS - 1 - sl));
+                            sd[f][j] = cols + sl * N;
+                            sb[f][j] = (uint32_t)(kk * N * 128) >> 4;
+                            si[f][j] = idesc_n((uint32_t)(end - kk + 1) * N);
+                            sa[f][j] = open ? 0u : 1u;
+                            kk = end + 1;
                         }
-                        if (!ok) break;
-                        const uint32_t slot[3] = {(e0 + i) % kRing, (e0 + i + 1) % kRing, (e0 + i + 2) % kRing};
-                        const uint32_t acc = tcount % kAcc;
-                        tc_after_sync();
-                        const uint32_t d = tmem + acc * 64;
-#pragma unroll
-                        for (int ky = 0; ky < 3; ++ky)
-#pragma unroll
-                            for (int kx = 0; kx < 3; ++kx)
-#pragma unroll
-                                for (int ks = 0; ks < 4; ++ks) {
-                                    const uint32_t aoff = slot[ky] * kSeg + kx * 16 + ks * 2 * kPlane;
-                                    const uint32_t boff = (ky * 3 + kx) * N * 128 + ks * 32;
-                                    mma<N>(d, a0 + (aoff >> 4), b0 + (boff >> 4), (ky | kx | ks) != 0);
-                                }
-                        tc_commit(bar(kBarTFull + acc));
-                        issued = true;
                     }
-                    // rows no later tile of the strip uses
-                    tc_commit(bar(empty0 + (e0 + i) % kRing));
-                    if (i == s.n - 1) {
-                        tc_commit(bar(empty0 + (e0 + s.n) % kRing));
-                        tc_commit(bar(empty0 + (e0 + s.n + 1) % kRing));
-                    }
+                    const uint64_t arow = a0 + ((row_slot * kSeg) >> 4);
+#pragma unroll
+                    for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+                        for (int ks = 0; ks < 4; ++ks) {
+                            const uint64_t a = arow + ((kx * 16 + ks * 2 * kPlane) >> 4);
+                            const uint64_t b = b0 + ((kx * 3 * N * 128 + ks * 32) >> 4);
+                            const int f = (kx == 0 && ks == 0) ? 0 : 1;
+#pragma unroll
+                            for (int j = 0; j < 3; ++j)
+                                if (sv[f][j]) mma_n(sd[f][j], a, b + sb[f][j], si[f][j], sa[f][j]);
+                        }
+                    if (e >= 2) tc_commit(bar(kBarTFull + q * kAccS + acc_slot(T0 + e - 2)));
+                    tc_commit(bar(kBarEmpty + row_slot));
+                    issued = true;
                 }
                 if (!ok) break;
-                e0 += s.n + 2;
+                T0 += s.n;
                 t += s.n;
             }
             // every MMA issued has completed before the accumulators are released
@@ -589,29 +633,29 @@ k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const 
         }
         __syncwarp();
     } else {
-        // ---- epilogue: warps 5..8, TMEM lanes 32 (warp % 4) .. + 31.  For N = 64 the
-        // tile's 128 x 64 bf16 outputs go through a shared staging tile in the 128-byte
-        // swizzle and leave as one TMA store: written straight from the threads
-        // (128 bytes per pixel, pixels 128 bytes apart) they took 32 L1 wavefronts per
-        // warp store, which the MMAs' shared-memory operand reads then waited behind.
-        // The four warps decide together whether to go on (a barrier that ORs their
-        // wait results), so an abort never leaves one of them at the next barrier. ----
+        // ---- epilogue of stream q: 4 warps, TMEM lanes 32 (warp % 4) .. + 31.  For
+        // N = 64 the tile's outputs go through the stream's staging tile (128-byte
+        // swizzle) and leave as one TMA store; the four warps decide together
+        // whether to go on (a barrier that ORs their wait results). ----
+        const int q = (warp - kLoaders - kIssuers) / kEpiWarps;
         const int quad = warp & 3;
         const int px = 32 * quad + lane;
-        const bool leader = warp == kLoaders + kIssuers && lane == 0;
-        uint32_t tcount = 0;
+        const bool leader = (warp - kLoaders - kIssuers) % kEpiWarps == 0 && lane == 0;
+        const int nb = 1 + q;   // named barrier of the group
+        const uint32_t sStage = sRing + kRingSOff + (uint32_t)q * kStageBytes;
+        uint32_t u = 0;
         bool ok = true;
-        for (int t = t_begin; t < t_end && ok;) {
-            const Strip s = strip_at(t, t_end, H, tiles_x);
-            for (int i = 0; i < s.n; ++i) {
-                const uint32_t acc = tcount % kAcc;
-                const bool got = bar_wait(bar(kBarTFull + acc), (tcount / kAcc) & 1, abortp, err.wait_ns);
-                if (bar_or(1, 128, !got || *abortp)) {
+        for (int t = tq0(q); t < tq1(q) && ok;) {
+            const Strip s = strip_at(t, tq1(q), H, tiles_x);
+            for (int i = 0; i < s.n; ++i, ++u) {
+                const uint32_t acc = acc_slot(u);
+                const bool got = bar_wait(bar(kBarTFull + q * kAccS + acc), (u / kAccS) & 1, abortp, err.wait_ns);
+                if (bar_or(nb, 32 * kEpiWarps, !got || *abortp)) {
                     ok = false;
                     break;
                 }
                 tc_after_sync();
-                const uint32_t taddr = tmem + ((uint32_t)(32 * quad) << 16) + acc * 64;
+                const uint32_t taddr = tmem + ((uint32_t)(32 * quad) << 16) + kStreamCols * q + acc * N;
                 const size_t pix = ((size_t)s.b * H + s.y0 + i) * W + s.x0 + px;
                 if (MODE == 2) {
                     uint32_t v[4];
@@ -621,7 +665,7 @@ k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const 
                                  : "memory");
                     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
                     tc_before_sync();
-                    bar_arrive(bar(kBarTEmpty + acc));
+                    bar_arrive(bar(kBarTEmpty + q * kAccS + acc));
                     float4 o;
                     o.x = __uint_as_float(v[0]) + sbias[0];
                     o.y = __uint_as_float(v[1]) + sbias[1];
@@ -634,10 +678,10 @@ k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const 
                     PLBM_TMEM_LD32(v, 32, taddr + 32);
                     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
                     tc_before_sync();
-                    bar_arrive(bar(kBarTEmpty + acc));
+                    bar_arrive(bar(kBarTEmpty + q * kAccS + acc));
                     // the previous tile's store has finished reading the staging tile
                     if (leader) asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
-                    bar_named(1, 128);
+                    bar_named(nb, 32 * kEpiWarps);
                     if (MODE == 1) {
                         // the warp's 32 mask pixels (4 KB, contiguous) with coalesced loads:
                         // lane l takes chunk l mod 8 of pixel 4 k + l / 8, into the pixel's
@@ -645,11 +689,11 @@ k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const 
                         const __nv_bfloat16* mw = mask + (pix - lane) * kC;
 #pragma unroll
                         for (int k = 0; k < 8; ++k) {
-                            const int p = 4 * k + (lane >> 3), c = lane & 7;
-                            const uint4 mv = *reinterpret_cast<const uint4*>(mw + p * kC + c * 8);
-                            const int pt = 32 * quad + p;
-                            const uint32_t a = sStage + (uint32_t)pt * 128u + (uint32_t)((c ^ (pt & 7)) * 16);
-                            asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n" ::"r"(a), "r"(mv.x), "r"(mv.y),
+                            const int pp = 4 * k + (lane >> 3), c = lane & 7;
+                            const uint4 mv = *reinterpret_cast<const uint4*>(mw + pp * kC + c * 8);
+                            const int pt = 32 * quad + pp;
+                            const uint32_t ad = sStage + (uint32_t)pt * 128u + (uint32_t)((c ^ (pt & 7)) * 16);
+                            asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n" ::"r"(ad), "r"(mv.x), "r"(mv.y),
                                          "r"(mv.z), "r"(mv.w)
                                          : "memory");
                         }
@@ -657,13 +701,12 @@ k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const 
                     }
                     stage64(v, MODE, relu, sbias, nullptr, sStage, px);
                     fence_async_smem();
-                    bar_named(1, 128);
+                    bar_named(nb, 32 * kEpiWarps);
                     if (leader) {
                         tma_store_2d(&tmY, 0, (int)(pix - px), sStage);
                         asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
                     }
                 }
-                ++tcount;
             }
             t += s.n;
         }
