@@ -877,12 +877,19 @@ k_conv_in_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __n
 // ---------------------------------------------------------------------------
 constexpr int kWgThreads = 256;
 constexpr int kWgRowPix = kTile + 2;
-constexpr int kWgPlaneX = kWgRowPix * 16;       // 2080
-constexpr int kWgX = 24 * kWgPlaneX;            // 3 rows x 8 chunk planes
+// X planes 17 lines apart, pixel 0 of a plane 112 bytes into a line, so that pixel
+// 1 (x0), the destination of the TMA box, is 128-byte aligned
+constexpr int kWgPlaneX = 17 * 128;             // 2176 >= 130 pixels x 16 bytes
+constexpr int kWgXOff = 112;
+constexpr int kWgX = 24 * kWgPlaneX + 128;      // 3 rows x 8 chunk planes (+ the pixel-0 offset)
 constexpr int kWgPlaneG = kTile * 16;           // 2048
-constexpr int kWgStage = kWgX + 8 * kWgPlaneG;  // 66304
+constexpr int kWgStage = kWgX + 8 * kWgPlaneG;  // 68736
+// Per stage: 24 TMA boxes of X rows and 8 of the dY row (the 48 halo chunks of
+// 16 bytes are copied by the threads).
+constexpr uint32_t kWgTxBytes = 24 * kTile * 16 + 8 * kTile * 16;
 constexpr int kWgStages = 3;                    // tiles in flight: two being copied while one multiplies
 constexpr int kWgSmem = 128 + kWgStages * kWgStage + 64 + 256 * 4;
+static_assert(kWgStage % 128 == 0 && kWgSmem <= 232448, "weight-gradient stages");
 constexpr uint32_t kWgTmemCols = 512;
 // kind::f16, D fp32, A and B bf16, both MN-major (bits 15, 16), N = 64, M = 128.
 constexpr uint32_t kIdescWg = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((64u >> 3) << 17) |
@@ -902,8 +909,9 @@ __device__ __forceinline__ void mma_wg(uint32_t tmem_d, uint64_t a, uint64_t b, 
 }
 
 __global__ void __launch_bounds__(kWgThreads, 1)
-k_wgrad_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ dY,
-           float* __restrict__ partial, float* __restrict__ partial_b, const TcErr err) {
+k_wgrad_tc(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmG,
+           const __nv_bfloat16* __restrict__ X, float* __restrict__ partial, float* __restrict__ partial_b,
+           const TcErr err) {
     extern __shared__ unsigned char dsm_raw[];
     const uint32_t raw = s2u(dsm_raw);
     const uint32_t pad = (128 - (raw & 127)) & 127;
@@ -911,39 +919,62 @@ k_wgrad_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __nv_
     const uint32_t sbase = raw + pad;
     unsigned char* bars_p = base + kWgStages * kWgStage;
     const uint32_t bar0 = s2u(bars_p), bar_drain = bar0 + 8 * kWgStages;   // bar0 + 8 s: MMAs of stage s done
-    volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(bars_p + 32);
-    volatile int* abortp = reinterpret_cast<volatile int*>(bars_p + 36);
+    const uint32_t barf0 = bar_drain + 8;   // barf0 + 8 s: stage s filled (bytes 32..55; TMEM slot at 56)
+    volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(bars_p + 56);
+    volatile int* abortp = reinterpret_cast<volatile int*>(bars_p + 60);
     float* red = reinterpret_cast<float*>(bars_p + 64);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tiles_x = W / kTile;
     const int ntiles = B * H * tiles_x;
     if (tid == 0) {
-        for (int k = 0; k < kWgStages; ++k) bar_init(bar0 + 8 * k, 1);
+        for (int k = 0; k < kWgStages; ++k) {
+            bar_init(bar0 + 8 * k, 1);
+            bar_init(barf0 + 8 * k, 1 + 24);
+        }
         bar_init(bar_drain, 1);
         *abortp = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    if (warp == 0) tmem_alloc(s2u(bars_p + 32), kWgTmemCols);
+    if (warp == 0) tmem_alloc(s2u(bars_p + 56), kWgTmemCols);
     tc_before_sync();
     __syncthreads();
     tc_after_sync();
     const uint32_t tmem = *tmem_slot;
 
+    // Stage fill by warp 1: lane 0 arms the stage's barrier with the byte count;
+    // lanes 0..23 issue the X row boxes (row r = lane / 8, chunk lane mod 8) and
+    // copy the two halo chunks of their plane (loads and shared stores, then a
+    // proxy fence and an arrival: tiny bulk copies cost more), lanes 24..31 issue
+    // the dY boxes.
     auto stage_in = [&](int t, int k) {
         const int b = t / (H * tiles_x);
         const int rem = t - b * H * tiles_x;
         const int y = rem / tiles_x;
         const int x0 = (rem - y * tiles_x) * kTile;
         const uint32_t st = sbase + k * kWgStage;
-        for (int i = tid; i < 3 * kWgRowPix * 8; i += kWgThreads) {
-            const int c = i & 7, pr = i >> 3, r = pr / kWgRowPix, sp = pr - r * kWgRowPix;
-            const int yy = wrapi(y + r - 1, H), xx = wrapi(x0 + sp - 1, W);
-            cp_async16(st + (r * 8 + c) * kWgPlaneX + 16 * sp, X + (((size_t)b * H + yy) * W + xx) * kC + 8 * c);
-        }
-        for (int i = tid; i < kTile * 8; i += kWgThreads) {
-            const int c = i & 7, p = i >> 3;
-            cp_async16(st + kWgX + c * kWgPlaneG + 16 * p, dY + (((size_t)b * H + y) * W + x0 + p) * kC + 8 * c);
+        const uint32_t full = barf0 + 8 * k;
+        if (lane == 0) bar_arrive_expect_tx(full, kWgTxBytes);
+        __syncwarp();
+        if (lane < 24) {
+            const int r = lane >> 3, c = lane & 7;
+            const int yy = wrapi(y + r - 1, H);
+            const uint32_t plane = st + kWgXOff + (uint32_t)(r * 8 + c) * kWgPlaneX;
+            tma_load_5d(plane + 16, &tmX, 0, c, x0, yy, b, full);
+            const size_t row = ((size_t)b * H + yy) * W;
+            const uint4 lft = __ldg(reinterpret_cast<const uint4*>(X + (row + wrapi(x0 - 1, W)) * kC + 8 * c));
+            const uint4 rgt = __ldg(reinterpret_cast<const uint4*>(X + (row + wrapi(x0 + kTile, W)) * kC + 8 * c));
+            asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n" ::"r"(plane), "r"(lft.x), "r"(lft.y), "r"(lft.z),
+                         "r"(lft.w)
+                         : "memory");
+            asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n" ::"r"(plane + 16 * (kWgRowPix - 1)), "r"(rgt.x),
+                         "r"(rgt.y), "r"(rgt.z), "r"(rgt.w)
+                         : "memory");
+            fence_async_smem();
+            bar_arrive(full);
+        } else {
+            const int c = lane - 24;
+            tma_load_5d(st + kWgX + c * kWgPlaneG, &tmG, 0, c, x0, y, b, full);
         }
     };
 
@@ -952,17 +983,18 @@ k_wgrad_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __nv_
     float bsum[8];         // warp w: channels 8 w .. 8 w + 7, pixels lane + 32 j of every tile
 #pragma unroll
     for (int i = 0; i < 8; ++i) bsum[i] = 0.0f;
-    for (int j = 0; j < kWgStages - 1; ++j) {
-        if ((int)blockIdx.x + j * (int)gridDim.x < ntiles) stage_in(blockIdx.x + j * gridDim.x, j);
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    if (warp == 1) {
+        if (lane == 0) asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tmX)) : "memory");
+        for (int j = 0; j < kWgStages - 1; ++j)
+            if ((int)blockIdx.x + j * (int)gridDim.x < ntiles) stage_in(blockIdx.x + j * gridDim.x, j);
     }
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
         const int k = it % kWgStages;
-        asm volatile("cp.async.wait_group %0;\n" ::"n"(kWgStages - 2) : "memory");
-        fence_async_smem();
+        // stage k holds tile t once its barrier completes (fill number it / kWgStages)
+        if (!bar_wait(barf0 + 8 * k, (uint32_t)(it / kWgStages) & 1u, abortp, err.wait_ns)) *abortp = 1;
         __syncthreads();
         if (*abortp) break;
-        const uint32_t sX = sbase + k * kWgStage, sG = sX + kWgX;
+        const uint32_t sX = sbase + k * kWgStage + kWgXOff, sG = sbase + k * kWgStage + kWgX;
         if (tid == 0) {   // queued behind the previous tile's MMAs: the tensor pipe does not wait for the copies
             tc_after_sync();
 #pragma unroll 1
@@ -985,10 +1017,9 @@ k_wgrad_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __nv_
             phase ^= 1u << kf;
         }
         const int tf = t + (kWgStages - 1) * (int)gridDim.x;
-        if (!*abortp && tf < ntiles) stage_in(tf, kf);
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        if (warp == 1 && !*abortp && tf < ntiles) stage_in(tf, kf);
         {   // bias: warp w sums plane w (channels 8 w ..), 16 contiguous bytes per pixel
-            const unsigned char* g = base + k * kWgStage + kWgX + warp * kWgPlaneG;
+            const unsigned char* g = base + k * kWgStage + kWgX + warp * kWgPlaneG;   // dY plane of channels 8 w ..
 #pragma unroll
             for (int j = 0; j < kTile / 32; ++j) {
                 const uint4 r = *reinterpret_cast<const uint4*>(g + 16 * (lane + 32 * j));
@@ -1003,7 +1034,6 @@ k_wgrad_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __nv_
         }
         __syncthreads();   // every thread is done with this stage before it is refilled
     }
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     if (it > 0 && !*abortp) {
         const int kl = (it - 1) % kWgStages;
         if (!bar_wait(bar0 + 8 * kl, (phase >> kl) & 1u, abortp, err.wait_ns)) *abortp = 1;
@@ -1370,10 +1400,13 @@ cudaError_t cnn_conv64_wgrad_tc(int B, int H, int W, const void* X, const void* 
         if (e != cudaSuccess) return e;
         attr = true;
     }
+    CUtensorMap mapX, mapG;
+    cudaError_t em = encode_act_map(&mapX, X, B, H, W);
+    if (em == cudaSuccess) em = encode_act_map(&mapG, dY, B, H, W);
+    if (em != cudaSuccess) return em;
     const int grid = cnn_wgrad64_parts(B, H, W);   // one CTA per SM at most (the partial buffers' size)
-    tc::k_wgrad_tc<<<grid, tc::kWgThreads, tc::kWgSmem, s>>>(B, H, W, static_cast<const __nv_bfloat16*>(X),
-                                                             static_cast<const __nv_bfloat16*>(dY), partial,
-                                                             partial_b, err);
+    tc::k_wgrad_tc<<<grid, tc::kWgThreads, tc::kWgSmem, s>>>(B, H, W, mapX, mapG, static_cast<const __nv_bfloat16*>(X),
+                                                             partial, partial_b, err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = cnn_sum_partials(partial, grid, 9 * tc::kC * tc::kC, dW, s);
