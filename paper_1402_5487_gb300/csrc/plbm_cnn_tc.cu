@@ -13,9 +13,9 @@
 //   * two loader warps stage input row segments (pixels x0 - 1 .. x0 + 128,
 //     wrapped) into the stream's ring of shared-memory slots: lane 0 issues
 //     eight TMA tile copies (cp.async.bulk.tensor, one per 16-byte channel
-//     chunk) of the 128 pixels x0 .. x0 + 127 and 16 lanes one 16-byte bulk
-//     copy each of the two wrapped halo pixels, all completing on the slot's
-//     mbarrier by byte count.
+//     chunk) of the 128 pixels x0 .. x0 + 127, completing on the slot's
+//     mbarrier by byte count, and 16 lanes copy the two wrapped halo pixels and
+//     arrive on it.
 //     A CTA owns a run of consecutive output rows of one column of tiles, so
 //     each input row is loaded once;
 //   * one issuing thread walks the input rows in order.  Input row y_in feeds
@@ -407,8 +407,7 @@ constexpr int kRing = kStreams * kRingS;
 // previous phase has completed and a parity test cannot be fooled.
 static_assert(kLoadersPer <= kRingS, "loader lag within the row ring");
 constexpr int kHaloLanes = 16;         // two wrapped pixels x 8 chunks
-// the eight TMA boxes of a row and the 16 bulk copies of its halo chunks
-constexpr uint32_t kRowTxBytes = 8 * kTile * 16 + kHaloLanes * 16;
+constexpr uint32_t kRowTxBytes = 8 * kTile * 16;  // the eight TMA boxes of a row
 constexpr int kRingBytes = kRing * kSeg + kPlaneOff;
 constexpr int kRingSOff = ((kRingBytes + 1023) / 1024) * 1024;  // output staging tiles after the ring
 constexpr int kStageBytes = kTile * kC * 2;                      // 128 pixels x 64 bf16 (N = 64 modes)
@@ -481,7 +480,7 @@ k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const 
 
     if (tid == 0) {
         for (int i = 0; i < kRing; ++i) {
-            bar_init(bar(kBarFull + i), 1);
+            bar_init(bar(kBarFull + i), 1 + kHaloLanes);
             bar_init(bar(kBarEmpty + i), 1);
         }
         for (int i = 0; i < kStreams * kAccS; ++i) {
@@ -535,14 +534,19 @@ k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const 
 #pragma unroll
                     for (int c = 0; c < 8; ++c) tma_load_5d(seg + c * kPlane + 16, &tmX, 0, c, s.x0, yy, s.b, full);
                 }
-                __syncwarp();
                 if (lane < kHaloLanes) {
-                    // halo pixels by the async proxy too (a generic store would need a
-                    // proxy fence before the tensor cores read it)
+                    // halo chunks by the threads (loads, shared stores, a proxy fence and
+                    // an arrival): 16-byte bulk copies cost more
                     const int right = lane >> 3, c = lane & 7;
                     const int xx = wrapi(right ? s.x0 + kTile : s.x0 - 1, W);
+                    const uint4 v = __ldg(reinterpret_cast<const uint4*>(
+                        X + (((size_t)s.b * H + yy) * (size_t)W + xx) * kC + c * 8));
                     const uint32_t dst = seg + c * kPlane + (right ? 16 * (kSegPix - 1) : 0);
-                    bulk_load(dst, X + (((size_t)s.b * H + yy) * (size_t)W + xx) * kC + c * 8, 16, full);
+                    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n" ::"r"(dst), "r"(v.x), "r"(v.y),
+                                 "r"(v.z), "r"(v.w)
+                                 : "memory");
+                    fence_async_smem();
+                    bar_arrive(full);
                 }
             }
             t += s.n;
