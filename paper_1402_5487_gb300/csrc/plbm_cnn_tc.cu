@@ -734,7 +734,10 @@ k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const 
 }
 
 // ---------------------------------------------------------------------------
-// 4 -> 64 input layer: Y bf16 [.][64] = relu?(conv(X) + bias), X bf16 [.][4].
+// 4 -> 64 input layer: Y bf16 [.][64] = relu?(conv(X) + bias), X bf16 [.][4]
+// (mode 0); the same kernel computes the output layer's backward data,
+// Y = conv(X) * (mask > 0) with X = bf16 upstream gradient [.][4] and the flipped
+// weights (mode 1).
 // A row of a pixel: K = tap * 4 + ci for the 36 products, zero to K = 48, in the
 // no-swizzle chunk-planar layout (6 planes of 128 pixels x 16 bytes).
 // Win: bf16 [6 chunks][64 n][8], the same layout for B (plane = 64 x 16 bytes).
@@ -754,7 +757,8 @@ constexpr uint32_t kInTmemCols = 64;
 
 __global__ void __launch_bounds__(kInThreads)
 k_conv_in_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ Win,
-             const float* __restrict__ bias, const __grid_constant__ CUtensorMap tmY, int relu, const TcErr err) {
+             const float* __restrict__ bias, const __nv_bfloat16* __restrict__ mask,
+             const __grid_constant__ CUtensorMap tmY, int mode, int relu, const TcErr err) {
     extern __shared__ unsigned char dsm_raw[];
     const uint32_t raw = s2u(dsm_raw);
     const uint32_t pad = (1024 - (raw & 1023)) & 1023;   // the staging tile's swizzle wants 1024-byte alignment
@@ -770,7 +774,7 @@ k_conv_in_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __n
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tiles_x = W / kTile;
     const int ntiles = B * H * tiles_x;
-    if (tid < 64) sbias[tid] = bias[tid];
+    if (tid < 64) sbias[tid] = mode == 0 ? bias[tid] : 0.0f;
     if (tid == 0) {
         bar_init(bar_mma, 1);
         bar_init(bar_drain, 1);
@@ -840,7 +844,23 @@ k_conv_in_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __n
         PLBM_TMEM_LD32(v, 32, taddr + 32);
         asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
         tc_before_sync();
-        stage64(v, 0, relu, sbias, nullptr, sA, tid);
+        if (mode == 1) {
+            // the warp's 32 mask pixels with coalesced loads into their swizzled places
+            // of the staging tile (lane l: chunk l mod 8 of pixel 4 k + l / 8)
+            const __nv_bfloat16* mw = mask + (((size_t)b * H + y) * W + x0 + 32 * warp) * kC;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int pp = 4 * k + (lane >> 3), c = lane & 7;
+                const uint4 mv = *reinterpret_cast<const uint4*>(mw + pp * kC + c * 8);
+                const int pt = 32 * warp + pp;
+                const uint32_t ad = sA + (uint32_t)pt * 128u + (uint32_t)((c ^ (pt & 7)) * 16);
+                asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n" ::"r"(ad), "r"(mv.x), "r"(mv.y), "r"(mv.z),
+                             "r"(mv.w)
+                             : "memory");
+            }
+            __syncwarp();
+        }
+        stage64(v, mode, relu, sbias, nullptr, sA, tid);
         fence_async_smem();
         __syncthreads();
         if (tid == 0) {
@@ -1375,8 +1395,9 @@ cudaError_t cnn_conv_out_tc(int B, int H, int W, const void* X, const void* Wo, 
     return launch_ring<16, 2>(B, H, W, X, Wo, bias, nullptr, Y, 0, err, s);
 }
 
-cudaError_t cnn_conv_in_tc(int B, int H, int W, const void* X, const void* Win, const float* bias, void* Y, int relu,
-                           TcErr err, cudaStream_t s) {
+cudaError_t cnn_conv_in_tc(int B, int H, int W, const void* X, const void* Win, const float* bias, const void* mask,
+                           void* Y, int mode, int relu, TcErr err, cudaStream_t s) {
+    if ((mode == 0 && !bias) || (mode == 1 && !mask) || mode < 0 || mode > 1) return cudaErrorInvalidValue;
     if (W % tc::kTile || H < 1 || B < 1) return cudaErrorInvalidValue;
     static bool attr = false;
     if (!attr) {
@@ -1390,7 +1411,8 @@ cudaError_t cnn_conv_in_tc(int B, int H, int W, const void* X, const void* Win, 
     const int ntiles = B * H * (W / tc::kTile);
     const int grid = ntiles < 8 * tc_sms() ? ntiles : 8 * tc_sms();
     tc::k_conv_in_tc<<<grid, tc::kInThreads, tc::kInSmem, s>>>(B, H, W, static_cast<const __nv_bfloat16*>(X),
-                                                               static_cast<const __nv_bfloat16*>(Win), bias, mapY,
+                                                               static_cast<const __nv_bfloat16*>(Win), bias,
+                                                               static_cast<const __nv_bfloat16*>(mask), mapY, mode,
                                                                relu, err);
     return cudaGetLastError();
 }

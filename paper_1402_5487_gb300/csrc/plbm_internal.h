@@ -155,8 +155,11 @@ cudaError_t cnn_conv64_tc(int B, int H, int W, const void* X, const void* Wk, co
 cudaError_t cnn_weights_kmajor(const void* W, void* Wf, void* Wb, cudaStream_t s);
 cudaError_t cnn_conv_out_tc(int B, int H, int W, const void* X, const void* Wo, const float* bias, float* Y,
                             TcErr err, cudaStream_t s);
-cudaError_t cnn_conv_in_tc(int B, int H, int W, const void* X, const void* Win, const float* bias, void* Y, int relu,
-                           TcErr err, cudaStream_t s);
+// mode 0: Y = relu?(conv(X) + bias) (the 4 -> 64 input layer); mode 1: Y = conv(X) *
+// (mask > 0) (the 64 -> 4 output layer's backward data, X = its bf16 upstream gradient,
+// Win from the flipped weights).
+cudaError_t cnn_conv_in_tc(int B, int H, int W, const void* X, const void* Win, const float* bias, const void* mask,
+                           void* Y, int mode, int relu, TcErr err, cudaStream_t s);
 cudaError_t cnn_weights_out16(const float* W, void* Wo, cudaStream_t s);
 cudaError_t cnn_weights_in(const float* W, void* Win, cudaStream_t s);
 cudaError_t cnn_mse(const float* pred, const float* target, long long n, long long npix, float lam, float* merr,

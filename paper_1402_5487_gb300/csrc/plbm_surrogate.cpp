@@ -41,6 +41,8 @@ struct Sur {
     float* w6flip = nullptr;        // backward-data weights of the last layer (4 -> 64)
     void* wtc = nullptr;            // K-major bf16 weights for tcgen05: 4 layers x (forward, backward data)
     void* win = nullptr;            // first layer (4 -> 64) for tcgen05: bf16 [6][64][8]
+    void* win6 = nullptr;           // the last layer's backward-data weights in the same layout
+    void* dout16 = nullptr;         // bf16 copy of the upstream gradient of the output [pix][4]
     void* wout = nullptr;           // last layer (64 -> 4) for tcgen05: bf16 [9][16][64]
     unsigned* derr = nullptr;       // device flag: a bounded wait in a tensor-core kernel ran out
     unsigned long long wait_ns = 2000000000ull;  // budget of each of those waits
@@ -111,7 +113,7 @@ void free_sur(Sur* s) {
     if (s->stream) cudaStreamSynchronize(s->stream);
     void* bufs[] = {s->p, s->g, s->m, s->v, s->pr, s->wbf, s->wflip, s->w6flip, s->dz[0], s->dz[1], s->dz[2],
                     s->dz[3], s->dz[4], s->dout, s->part, s->part_b, s->loss_part, s->Fold, s->Fnew, s->xin,
-                    s->planes, s->sums, s->wtc, s->derr, s->win, s->wout, s->drift, s->fb_table, s->fb_tile_inst,
+                    s->planes, s->sums, s->wtc, s->derr, s->win, s->win6, s->dout16, s->wout, s->drift, s->fb_table, s->fb_tile_inst,
                     s->dref};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -149,6 +151,7 @@ plbm_status refresh_weights(Sur* s) {
     }
     SCK(plbm::cnn_flip_thin(s->pr + s->woff[5], 64, 4, s->w6flip, s->stream));
     SCK(plbm::cnn_weights_in(s->pr + s->woff[0], s->win, s->stream));
+    SCK(plbm::cnn_weights_in(s->w6flip, s->win6, s->stream));
     SCK(plbm::cnn_weights_out16(s->pr + s->woff[5], s->wout, s->stream));
     return PLBM_OK;
 }
@@ -156,7 +159,8 @@ plbm_status refresh_weights(Sur* s) {
 plbm_status forward(Sur* s, int B, const void* x) {
     const int H = s->H, W = s->W;
     if (s->use_tc) {
-        SCK(plbm::cnn_conv_in_tc(B, H, W, x, s->win, s->p + s->boff[0], s->act[0], 1, plbm::TcErr{s->derr, s->wait_ns}, s->stream));
+        SCK(plbm::cnn_conv_in_tc(B, H, W, x, s->win, s->p + s->boff[0], nullptr, s->act[0], 0, 1,
+                                 plbm::TcErr{s->derr, s->wait_ns}, s->stream));
     } else {
         SCK(plbm::cnn_conv_thin_fwd(4, 64, 0, 0, B, H, W, x, s->pr + s->woff[0], s->p + s->boff[0], nullptr,
                                     s->act[0], 0, 1, s->stream));
@@ -188,8 +192,14 @@ plbm_status backward(Sur* s, int B, const void* x, const float* dout) {
     // last layer (64 -> 4): weights, then dZ_5 = (conv^T dout) * (A_5 > 0)
     SCK(plbm::cnn_conv_thin_wgrad(64, 4, 0, 1, B, H, W, s->act[4], dout, s->part, s->part_b, s->g + s->woff[5],
                                   s->g + s->boff[5], s->stream));
-    SCK(plbm::cnn_conv_thin_fwd(4, 64, 1, 0, B, H, W, dout, s->w6flip, nullptr, s->act[4], s->dz[4], 1, 0,
-                                s->stream));
+    if (s->use_tc) {   // tcgen05, on the bf16-rounded upstream gradient (the other layers' gradients are bf16 too)
+        SCK(plbm::cnn_to_bf16(dout, (long long)B * H * W * 4, s->dout16, s->stream));
+        SCK(plbm::cnn_conv_in_tc(B, H, W, s->dout16, s->win6, nullptr, s->act[4], s->dz[4], 1, 0,
+                                 plbm::TcErr{s->derr, s->wait_ns}, s->stream));
+    } else {
+        SCK(plbm::cnn_conv_thin_fwd(4, 64, 1, 0, B, H, W, dout, s->w6flip, nullptr, s->act[4], s->dz[4], 1, 0,
+                                    s->stream));
+    }
     for (int l = 4; l >= 1; --l) {
         if (s->use_tc)
             SCK(plbm::cnn_conv64_wgrad_tc(B, H, W, s->act[l - 1], s->dz[l], s->part, s->part_b, s->g + s->woff[l],
@@ -274,6 +284,7 @@ plbm_status plbm_sur_create(int max_batch, int H, int W, unsigned long long seed
         {(void**)&s->Fold, pix * 4 * 4}, {(void**)&s->Fnew, pix * 4 * 4}, {&s->xin, pix * 4 * 2},
         {(void**)&s->planes, (size_t)H * W * 4 * 8}, {(void**)&s->sums, (size_t)max_batch * 2 * 64 * 4 * 8},
         {&s->wtc, 8 * 9 * 64 * 64 * 2}, {(void**)&s->derr, 256}, {&s->win, 6 * 64 * 8 * 2},
+        {&s->win6, 6 * 64 * 8 * 2}, {&s->dout16, pix * 4 * 2},
         {&s->wout, 9 * 16 * 64 * 2}, {(void**)&s->drift, (size_t)max_batch * 24 + 16},
         {(void**)&s->fb_table, (size_t)max_batch * sizeof(plbm::PairParams)},
         {(void**)&s->fb_tile_inst, (size_t)max_batch * ((W + 127) / 128) * ((H + 1) / 2) * sizeof(unsigned short) + 256},

@@ -60,6 +60,7 @@ def net_and_pass(request):
     import torch
     net = SG.Surrogate(2, H=5, W=128, seed=7)
     net.set_tensor_path(request.param == "tcgen05")
+    net.tc_path = request.param == "tcgen05"
     g = torch.Generator().manual_seed(3)
     x = torch.randn((2, 5, 128, 4), generator=g).to(torch.bfloat16).cuda()
     dout = (0.01 * torch.randn((2, 5, 128, 4), generator=g)).cuda()
@@ -97,8 +98,10 @@ def test_weight_gradients_match_oracle(net_and_pass):
 
 
 def test_backward_data_convolutions_match_oracle(net_and_pass):
-    _, A, dZ, dout, params, _ = net_and_pass
-    ups = dZ + [dout]
+    net, A, dZ, dout, params, _ = net_and_pass
+    # the tcgen05 path takes the output layer's upstream gradient in bf16, as it
+    # does every other layer's; the mma.sync path keeps it in FP32
+    ups = dZ + [bf16(dout) if net.tc_path else dout]
     for l in range(5, 0, -1):  # dZ of layer l from the upstream gradient of layer l + 1
         W, _ = params[l]
         ref = N.conv3x3_grad_input(ups[l], bf16(W)) * (A[l] > 0)

@@ -11,7 +11,9 @@ tensor paths (tcgen05 and mma.sync), and compare with the FP64 oracle:
 
 1. Per operation, on the GPU's own bf16 inputs (only that operation's rounding
    differs): every forward convolution (4 -> 64, 4 x 64 -> 64, 64 -> 4), every
-   backward-data convolution with its ReLU mask, every weight and bias gradient.
+   backward-data convolution with its ReLU mask (the tcgen05 path rounds the
+   output layer's FP32 upstream gradient to bf16 first, as the network keeps
+   every other gradient), every weight and bias gradient.
 2. Along the oracle's own chain: a forward and backward pass computed entirely
    by the oracle from the same bf16 input, bf16 weights and upstream gradient,
    with every stored activation and gradient rounded to bf16 as the network
@@ -124,7 +126,8 @@ def gpu_pass(request):
     p, _ = net.params()
     assert net.check() == plbm.PLBM_OK
     net.close()
-    yield dict(A=A, out=out, dZ=dZ, dout=dout.cpu().numpy().astype(np.float64), params=split(p), grads=grads)
+    yield dict(A=A, out=out, dZ=dZ, dout=dout.cpu().numpy().astype(np.float64), params=split(p), grads=grads,
+               tc=path == "tcgen05")
 
 
 def test_each_forward_convolution_on_the_gpu_inputs(gpu_pass):
@@ -139,8 +142,11 @@ def test_each_forward_convolution_on_the_gpu_inputs(gpu_pass):
 
 
 def test_each_backward_data_convolution_on_the_gpu_inputs(gpu_pass):
+    # the tcgen05 path takes the output layer's upstream gradient in bf16 (as
+    # every other layer's), the mma.sync path in FP32
     A, dZ, params = gpu_pass["A"], gpu_pass["dZ"], gpu_pass["params"]
-    ups = dZ + [gpu_pass["dout"]]
+    dout = gpu_pass["dout"]
+    ups = dZ + [bf16(dout) if gpu_pass["tc"] else dout]
     for l in range(5, 0, -1):
         ref = N.conv3x3_grad_input(ups[l], bf16(params[l][0])) * (A[l] > 0)
         assert close_bf16(dZ[l - 1], ref), l
