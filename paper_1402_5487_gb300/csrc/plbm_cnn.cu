@@ -584,6 +584,102 @@ k_thin_wgrad(ConvShape S, const __nv_bfloat16* __restrict__ X, const TG* __restr
     }
 }
 
+// 64 -> 4 weight gradient (FP32 upstream gradient): 256 threads, thread (ci =
+// t mod 64, group g = t / 64) takes input channel ci over the pixels 32 g ..
+// 32 g + 31 of every tile and keeps all 36 sums dW[tap][ci][0..3] in registers:
+// per pixel three new inputs (one per row, a sliding window over kx) and one
+// broadcast float4 of dY feed 18 packed FMAs, against 4 multiply-adds per
+// thread and pixel when every (tap, ci) had a thread of its own.  The four
+// groups' sums are added in a fixed order at the end.  Stages and layout as
+// k_thin_wgrad<64, 4, float>.
+__global__ void __launch_bounds__(256)
+k_thin_wgrad_64x4(ConvShape S, const __nv_bfloat16* __restrict__ X, const float* __restrict__ dY,
+                  float* __restrict__ partial, float* __restrict__ partial_b) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    constexpr int kStage = thin_wgrad_stage<64, 4, float>();
+    const int ci = threadIdx.x & 63, g = threadIdx.x >> 6;
+    const int ntiles = S.B * S.H * (S.W / kTile);
+    float2 acc[9][2];   // [tap][co pair]
+#pragma unroll
+    for (int k = 0; k < 9; ++k) acc[k][0] = acc[k][1] = make_float2(0.f, 0.f);
+    float4 bacc = make_float4(0.f, 0.f, 0.f, 0.f);
+    int stage = 0;
+    if ((int)blockIdx.x < ntiles) thin_wgrad_stage_in<64, 4, float>(S, X, dY, blockIdx.x, dsm);
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        if (t + (int)gridDim.x < ntiles) {
+            thin_wgrad_stage_in<64, 4, float>(S, X, dY, t + gridDim.x, dsm + (stage ^ 1) * kStage);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        auto sX = reinterpret_cast<const __nv_bfloat16 (*)[kRowPix][64]>(dsm + stage * kStage);
+        auto sG = reinterpret_cast<const float4*>(dsm + stage * kStage + 3 * kRowPix * 64 * 2);
+        const int p0 = 32 * g;
+        float x[3][3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            x[r][0] = __bfloat162float(sX[r][p0][ci]);
+            x[r][1] = __bfloat162float(sX[r][p0 + 1][ci]);
+        }
+#pragma unroll
+        for (int p = p0; p < p0 + 32; ++p) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r) x[r][2] = __bfloat162float(sX[r][p + 2][ci]);
+            const float4 d = sG[p];
+            const float2 d01 = make_float2(d.x, d.y), d23 = make_float2(d.z, d.w);
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int kx = 0; kx < 3; ++kx) {
+                    const float2 xv = make_float2(x[r][kx], x[r][kx]);
+                    acc[r * 3 + kx][0] = __ffma2_rn(xv, d01, acc[r * 3 + kx][0]);
+                    acc[r * 3 + kx][1] = __ffma2_rn(xv, d23, acc[r * 3 + kx][1]);
+                }
+            if (ci == 0) {
+                bacc.x += d.x;
+                bacc.y += d.y;
+                bacc.z += d.z;
+                bacc.w += d.w;
+            }
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                x[r][0] = x[r][1];
+                x[r][1] = x[r][2];
+            }
+        }
+        __syncthreads();
+        stage ^= 1;
+    }
+    // the four groups' sums in a fixed order: red[g][ci][tap * 4 + co]
+    float* red = reinterpret_cast<float*>(dsm);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        float* r = red + ((size_t)g * 64 + ci) * 36 + 4 * k;
+        r[0] = acc[k][0].x;
+        r[1] = acc[k][0].y;
+        r[2] = acc[k][1].x;
+        r[3] = acc[k][1].y;
+    }
+    float* redb = red + 4 * 64 * 36;
+    if (ci == 0) {
+        redb[4 * g + 0] = bacc.x;
+        redb[4 * g + 1] = bacc.y;
+        redb[4 * g + 2] = bacc.z;
+        redb[4 * g + 3] = bacc.w;
+    }
+    __syncthreads();
+    float* out = partial + (size_t)blockIdx.x * 9 * 64 * 4;   // [tap][ci][co]
+    for (int i = threadIdx.x; i < 9 * 64 * 4; i += 256) {
+        const int co = i & 3, c = (i >> 2) & 63, tap = i >> 8;
+        const int j = c * 36 + 4 * tap + co;
+        out[i] = ((red[j] + red[64 * 36 + j]) + red[2 * 64 * 36 + j]) + red[3 * 64 * 36 + j];
+    }
+    if (threadIdx.x < 4)
+        partial_b[(size_t)blockIdx.x * 4 + threadIdx.x] =
+            ((redb[threadIdx.x] + redb[4 + threadIdx.x]) + redb[8 + threadIdx.x]) + redb[12 + threadIdx.x];
+}
+
 // Backward-data weights of a 64 -> 64 layer: Wb[tap'][co][ci] = W[8 - tap'][ci][co] (bf16).
 __global__ void k_flip64(const __nv_bfloat16* __restrict__ W, __nv_bfloat16* __restrict__ Wb) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -794,15 +890,14 @@ cudaError_t cnn_conv_thin_wgrad(int ci, int co, int tx, int tg, int B, int H, in
                                                                       partial, partial_b);
     } else if (ci == 64 && co == 4 && tg == 1) {
         constexpr int sm = cnn::thin_wgrad_smem<64, 4, float>();
+        static_assert(sm >= (4 * 64 * 36 + 16) * 4, "reduction area within the stages");
         static bool attr = false;
         if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute(cnn::k_thin_wgrad<64, 4, float>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            cudaError_t e = cudaFuncSetAttribute(cnn::k_thin_wgrad_64x4, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
             if (e != cudaSuccess) return e;
             attr = true;
         }
-        cnn::k_thin_wgrad<64, 4, float><<<parts, 576, sm, s>>>(S, Xb, static_cast<const float*>(dY), partial,
-                                                               partial_b);
+        cnn::k_thin_wgrad_64x4<<<parts, 256, sm, s>>>(S, Xb, static_cast<const float*>(dY), partial, partial_b);
     } else {
         return cudaErrorInvalidValue;
     }
