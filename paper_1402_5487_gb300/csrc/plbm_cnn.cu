@@ -330,13 +330,37 @@ k_conv64_wgrad(ConvShape S, const __nv_bfloat16* __restrict__ X, const __nv_bflo
     }
 }
 
-// out[j] = sum_c partial[c * n + j] in a fixed order.
-__global__ void k_sum_partials(const float* __restrict__ partial, int nparts, int n, float* __restrict__ out) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
+// out[j] = sum_c partial[c * n + j] in a fixed order: block = 32 consecutive j;
+// warp w sums the parts c of its contiguous eighth (in order, four loads in
+// flight), and lane j adds the eight warps' sums in warp order.
+__global__ void __launch_bounds__(256) k_sum_partials(const float* __restrict__ partial, int nparts, int n,
+                                                      float* __restrict__ out) {
+    __shared__ float sh[8][33];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = blockIdx.x * 32 + lane;
+    const int per = (nparts + 7) / 8;
+    const int c0 = w * per, c1 = min(nparts, c0 + per);
     float s = 0.0f;
-    for (int c = 0; c < nparts; ++c) s += partial[(size_t)c * n + j];
-    out[j] = s;
+    if (j < n) {
+        int c = c0;
+        for (; c + 4 <= c1; c += 4) {
+            const float a0 = partial[(size_t)c * n + j], a1 = partial[(size_t)(c + 1) * n + j];
+            const float a2 = partial[(size_t)(c + 2) * n + j], a3 = partial[(size_t)(c + 3) * n + j];
+            s += a0;
+            s += a1;
+            s += a2;
+            s += a3;
+        }
+        for (; c < c1; ++c) s += partial[(size_t)c * n + j];
+    }
+    sh[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && j < n) {
+        float t = sh[0][lane];
+#pragma unroll
+        for (int k = 1; k < 8; ++k) t += sh[k][lane];
+        out[j] = t;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -808,7 +832,7 @@ int cnn_wgrad64_parts(int B, int H, int W) {
 }
 
 cudaError_t cnn_sum_partials(const float* partial, int nparts, int n, float* out, cudaStream_t s) {
-    cnn::k_sum_partials<<<(n + 255) / 256, 256, 0, s>>>(partial, nparts, n, out);
+    cnn::k_sum_partials<<<(n + 31) / 32, 256, 0, s>>>(partial, nparts, n, out);
     return cudaGetLastError();
 }
 
@@ -827,8 +851,8 @@ cudaError_t cnn_conv64_wgrad(int B, int H, int W, const void* X, const void* dY,
         cnn::ConvShape{B, H, W}, static_cast<const __nv_bfloat16*>(X), static_cast<const __nv_bfloat16*>(dY), partial,
         partial_b);
     const int n = 9 * cnn::kC * cnn::kC;
-    cnn::k_sum_partials<<<(n + 255) / 256, 256, 0, s>>>(partial, grid, n, dW);
-    cnn::k_sum_partials<<<1, 64, 0, s>>>(partial_b, grid, cnn::kC, db);
+    cnn::k_sum_partials<<<(n + 31) / 32, 256, 0, s>>>(partial, grid, n, dW);
+    cnn::k_sum_partials<<<(cnn::kC + 31) / 32, 256, 0, s>>>(partial_b, grid, cnn::kC, db);
     return cudaGetLastError();
 }
 
@@ -902,8 +926,8 @@ cudaError_t cnn_conv_thin_wgrad(int ci, int co, int tx, int tg, int B, int H, in
         return cudaErrorInvalidValue;
     }
     const int n = 9 * ci * co;
-    cnn::k_sum_partials<<<(n + 255) / 256, 256, 0, s>>>(partial, parts, n, dW);
-    cnn::k_sum_partials<<<1, 64, 0, s>>>(partial_b, parts, co, db);
+    cnn::k_sum_partials<<<(n + 31) / 32, 256, 0, s>>>(partial, parts, n, dW);
+    cnn::k_sum_partials<<<(co + 31) / 32, 256, 0, s>>>(partial_b, parts, co, db);
     return cudaGetLastError();
 }
 
