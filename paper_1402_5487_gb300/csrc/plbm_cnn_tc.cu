@@ -591,36 +591,77 @@ k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const 
                     // the accumulators wrap around the stream's columns (at most
                     // three segments); f = 0 for the first (kx, K-step), 1 for the rest.
                     const uint32_t s_lo = acc_slot(T0 + e - ky_lo);
-                    uint32_t sd[2][3], sb[2][3], si[2][3], sa[2][3];
-                    bool sv[2][3];
-#pragma unroll
-                    for (int f = 0; f < 2; ++f) {
-                        int kk = ky_lo;
-#pragma unroll
-                        for (int j = 0; j < 3; ++j) {
-                            sv[f][j] = kk <= ky_hi;
-                            const bool open = f == 0 && kk == 0;
-                            const uint32_t sl = (s_lo + (uint32_t)(kk - ky_lo)) % kAccS;
-                            const int end = min(open ? 0 : ky_hi, kk + (int)(kAccS - 1 - sl));
-                            sd[f][j] = cols + sl * N;
-                            sb[f][j] = (uint32_t)(kk * N * 128) >> 4;
-                            si[f][j] = idesc_n((uint32_t)(end - kk + 1) * N);
-                            sa[f][j] = open ? 0u : 1u;
-                            kk = end + 1;
-                        }
-                    }
                     const uint64_t arow = a0 + ((row_slot * kSeg) >> 4);
+                    if (ky_lo == 0 && ky_hi == 2 && s_lo + 2 < (uint32_t)kAccS) {
+                        // an interior row whose three accumulators do not wrap (the common
+                        // case): the opening product, then one MMA of 3 N columns each
+                        const uint32_t d = cols + s_lo * N;
+                        const uint32_t i1 = idesc_n(N), i2 = idesc_n(2 * N), i3 = idesc_n(3 * N);
 #pragma unroll
-                    for (int kx = 0; kx < 3; ++kx)
+                        for (int kx = 0; kx < 3; ++kx)
 #pragma unroll
-                        for (int ks = 0; ks < 4; ++ks) {
-                            const uint64_t a = arow + ((kx * 16 + ks * 2 * kPlane) >> 4);
-                            const uint64_t b = b0 + ((kx * 3 * N * 128 + ks * 32) >> 4);
-                            const int f = (kx == 0 && ks == 0) ? 0 : 1;
+                            for (int ks = 0; ks < 4; ++ks) {
+                                const uint64_t a = arow + ((kx * 16 + ks * 2 * kPlane) >> 4);
+                                const uint64_t b = b0 + ((kx * 3 * N * 128 + ks * 32) >> 4);
+                                if (kx == 0 && ks == 0) {
+                                    mma_n(d, a, b, i1, 0u);
+                                    mma_n(d + N, a, b + ((N * 128) >> 4), i2, 1u);
+                                } else {
+                                    mma_n(d, a, b, i3, 1u);
+                                }
+                            }
+                    } else if (ky_lo == 0 && ky_hi == 2) {
+                        // an interior row whose accumulators wrap: the first w taps at
+                        // s_lo, the rest from column 0 (the opening product alone)
+                        const uint32_t w = (uint32_t)kAccS - s_lo;   // 1 or 2
+                        const uint32_t d = cols + s_lo * N;
+                        const uint32_t i1 = idesc_n(N), iw = idesc_n(w * N), ir = idesc_n((3 - w) * N);
+                        const uint32_t bw = (w * N * 128) >> 4;
 #pragma unroll
-                            for (int j = 0; j < 3; ++j)
-                                if (sv[f][j]) mma_n(sd[f][j], a, b + sb[f][j], si[f][j], sa[f][j]);
+                        for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+                            for (int ks = 0; ks < 4; ++ks) {
+                                const uint64_t a = arow + ((kx * 16 + ks * 2 * kPlane) >> 4);
+                                const uint64_t b = b0 + ((kx * 3 * N * 128 + ks * 32) >> 4);
+                                if (kx == 0 && ks == 0) {
+                                    mma_n(d, a, b, i1, 0u);
+                                    if (w == 2) mma_n(d + N, a, b + ((N * 128) >> 4), i1, 1u);
+                                } else {
+                                    mma_n(d, a, b, iw, 1u);
+                                }
+                                mma_n(cols, a, b + bw, ir, 1u);
+                            }
+                    } else {
+                        uint32_t sd[2][3], sb[2][3], si[2][3], sa[2][3];
+                        bool sv[2][3];
+#pragma unroll
+                        for (int f = 0; f < 2; ++f) {
+                            int kk = ky_lo;
+#pragma unroll
+                            for (int j = 0; j < 3; ++j) {
+                                sv[f][j] = kk <= ky_hi;
+                                const bool open = f == 0 && kk == 0;
+                                const uint32_t sl = (s_lo + (uint32_t)(kk - ky_lo)) % kAccS;
+                                const int end = min(open ? 0 : ky_hi, kk + (int)(kAccS - 1 - sl));
+                                sd[f][j] = cols + sl * N;
+                                sb[f][j] = (uint32_t)(kk * N * 128) >> 4;
+                                si[f][j] = idesc_n((uint32_t)(end - kk + 1) * N);
+                                sa[f][j] = open ? 0u : 1u;
+                                kk = end + 1;
+                            }
                         }
+#pragma unroll
+                        for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+                            for (int ks = 0; ks < 4; ++ks) {
+                                const uint64_t a = arow + ((kx * 16 + ks * 2 * kPlane) >> 4);
+                                const uint64_t b = b0 + ((kx * 3 * N * 128 + ks * 32) >> 4);
+                                const int f = (kx == 0 && ks == 0) ? 0 : 1;
+#pragma unroll
+                                for (int j = 0; j < 3; ++j)
+                                    if (sv[f][j]) mma_n(sd[f][j], a, b + sb[f][j], si[f][j], sa[f][j]);
+                            }
+                    }
                     if (e >= 2) tc_commit(bar(kBarTFull + q * kAccS + acc_slot(T0 + e - 2)));
                     tc_commit(bar(kBarEmpty + row_slot));
                     issued = true;
