@@ -428,7 +428,8 @@ __device__ __forceinline__ uint32_t acc_slot(uint32_t u) { return (uint32_t)(kAc
 // empty barrier, per stream and accumulator a full and an empty barrier, per
 // issuer a drain barrier
 constexpr int kBarFull = 0, kBarEmpty = kRing, kBarTFull = 2 * kRing, kBarTEmpty = kBarTFull + kStreams * kAccS,
-              kBarDrain = kBarTEmpty + kStreams * kAccS, kBarCount = kBarDrain + kIssuers;
+              kBarDrain = kBarTEmpty + kStreams * kAccS, kBarMask = kBarDrain + kIssuers,
+              kBarCount = kBarMask + kStreams;
 static_assert(kBarCount * 8 + 16 <= 512, "barrier area below the biases");
 
 // Tiles t = ((b * tiles_x + xt) * H + y); a CTA takes a contiguous range, which
@@ -451,7 +452,8 @@ __device__ __forceinline__ Strip strip_at(int t, int t1, int H, int tiles_x) {
 template <int N, int MODE>
 __global__ void __launch_bounds__(kRingThreads, 1)
 k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
-            const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ Wk, const float* __restrict__ bias,
+            const __grid_constant__ CUtensorMap tmM, const __nv_bfloat16* __restrict__ X,
+            const __nv_bfloat16* __restrict__ Wk, const float* __restrict__ bias,
             const __nv_bfloat16* __restrict__ mask, void* __restrict__ Yv, int relu, const TcErr err) {
     static_assert((N == 64 && MODE < 2) || (N == 16 && MODE == 2), "ring conv shapes");
     static_assert(kAccS * N <= (int)kStreamCols, "a stream's accumulators fit its share of the TMEM columns");
@@ -488,6 +490,7 @@ k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const 
             bar_init(bar(kBarTEmpty + i), 32 * kEpiWarps);
         }
         for (int i = 0; i < kIssuers; ++i) bar_init(bar(kBarDrain + i), 1);
+        for (int i = 0; i < kStreams; ++i) bar_init(bar(kBarMask + i), 1);
         *abortp = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
@@ -688,6 +691,23 @@ k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const 
         const bool leader = (warp - kLoaders - kIssuers) % kEpiWarps == 0 && lane == 0;
         const int nb = 1 + q;   // named barrier of the group
         const uint32_t sStage = sRing + kRingSOff + (uint32_t)q * kStageBytes;
+        // Backward data (MODE 1): the leader loads each tile's ReLU mask (16 KB, the
+        // output's layout) into the staging tile by TMA, as soon as the previous
+        // tile's store has read it out; the threads read their pixel's mask from
+        // there and overwrite it with the output.
+        const uint32_t mbar = bar(kBarMask + q);
+        auto load_mask = [&](int pix0) {
+            bar_arrive_expect_tx(mbar, (uint32_t)kStageBytes);
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+                "[%4];\n" ::"r"(sStage),
+                "l"(reinterpret_cast<uint64_t>(&tmM)), "r"(0), "r"(pix0), "r"(mbar)
+                : "memory");
+        };
+        if (MODE == 1 && leader && tq0(q) < tq1(q)) {
+            const Strip s0 = strip_at(tq0(q), tq1(q), H, tiles_x);
+            load_mask((int)(((size_t)s0.b * H + s0.y0) * W + s0.x0));
+        }
         uint32_t u = 0;
         bool ok = true;
         for (int t = tq0(q); t < tq1(q) && ok;) {
@@ -724,25 +744,13 @@ k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const 
                     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
                     tc_before_sync();
                     bar_arrive(bar(kBarTEmpty + q * kAccS + acc));
-                    // the previous tile's store has finished reading the staging tile
-                    if (leader) asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
-                    bar_named(nb, 32 * kEpiWarps);
                     if (MODE == 1) {
-                        // the warp's 32 mask pixels (4 KB, contiguous) with coalesced loads:
-                        // lane l takes chunk l mod 8 of pixel 4 k + l / 8, into the pixel's
-                        // swizzled place in the staging tile, where stage64 reads it back
-                        const __nv_bfloat16* mw = mask + (pix - lane) * kC;
-#pragma unroll
-                        for (int k = 0; k < 8; ++k) {
-                            const int pp = 4 * k + (lane >> 3), c = lane & 7;
-                            const uint4 mv = *reinterpret_cast<const uint4*>(mw + pp * kC + c * 8);
-                            const int pt = 32 * quad + pp;
-                            const uint32_t ad = sStage + (uint32_t)pt * 128u + (uint32_t)((c ^ (pt & 7)) * 16);
-                            asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n" ::"r"(ad), "r"(mv.x), "r"(mv.y),
-                                         "r"(mv.z), "r"(mv.w)
-                                         : "memory");
-                        }
-                        __syncwarp();
+                        // this tile's mask has landed in the staging tile
+                        if (!bar_wait(mbar, u & 1, abortp, err.wait_ns)) *abortp = 1;
+                    } else {
+                        // the previous tile's store has finished reading the staging tile
+                        if (leader) asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+                        bar_named(nb, 32 * kEpiWarps);
                     }
                     stage64(v, MODE, relu, sbias, nullptr, sStage, px);
                     fence_async_smem();
@@ -750,6 +758,20 @@ k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const 
                     if (leader) {
                         tma_store_2d(&tmY, 0, (int)(pix - px), sStage);
                         asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+                        if (MODE == 1) {
+                            // the next tile's mask, once this store has read the staging tile out
+                            int np = -1;
+                            if (i + 1 < s.n) {
+                                np = (int)(pix - px) + W;
+                            } else if (t + s.n < tq1(q)) {
+                                const Strip s1 = strip_at(t + s.n, tq1(q), H, tiles_x);
+                                np = (int)(((size_t)s1.b * H + s1.y0) * W + s1.x0);
+                            }
+                            if (np >= 0 && !*abortp) {
+                                asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+                                load_mask(np);
+                            }
+                        }
                     }
                 }
             }
@@ -1404,9 +1426,14 @@ static cudaError_t launch_ring(int B, int H, int W, const void* X, const void* W
     CUtensorMap map, mapY;
     cudaError_t em = encode_act_map(&map, X, B, H, W);
     if (em != cudaSuccess) return em;
+    CUtensorMap mapM = map;   // the backward pass's ReLU mask (MODE 1 only)
     if (N == 64) {
         em = encode_out_map(&mapY, Y, (long long)B * H * W);
         if (em != cudaSuccess) return em;
+        if (MODE == 1) {
+            em = encode_out_map(&mapM, const_cast<void*>(mask), (long long)B * H * W);
+            if (em != cudaSuccess) return em;
+        }
     } else {
         mapY = map;   // not used by the 64 -> 4 layer (fp32 stores from the threads)
     }
@@ -1420,7 +1447,7 @@ static cudaError_t launch_ring(int B, int H, int W, const void* X, const void* W
     const int ntiles = B * H * (W / tc::kTile);
     const int grid = ntiles < tc_sms() ? ntiles : tc_sms();
     tc::k_conv_ring<N, MODE><<<grid, tc::kRingThreads, smem, s>>>(
-        B, H, W, map, mapY, static_cast<const __nv_bfloat16*>(X), static_cast<const __nv_bfloat16*>(Wk), bias,
+        B, H, W, map, mapY, mapM, static_cast<const __nv_bfloat16*>(X), static_cast<const __nv_bfloat16*>(Wk), bias,
         static_cast<const __nv_bfloat16*>(mask), Y, relu, err);
     return cudaGetLastError();
 }
