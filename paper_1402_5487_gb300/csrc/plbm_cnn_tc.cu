@@ -995,7 +995,14 @@ __device__ __forceinline__ void mma_wg(uint32_t tmem_d, uint64_t a, uint64_t b, 
         : "memory");
 }
 
-__global__ void __launch_bounds__(kWgThreads, 1)
+// Warp roles: lane 0 of warp 0 issues the MMAs, warp 1 fills the stages, warps
+// 2 and 3 sum dY for the bias gradient.  They hand stages over through mbarriers
+// only (full[k]: stage k's copies have landed; mma[k]: its MMAs are done;
+// bias[k]: both bias warps have read it), so the MMA issue never waits at a
+// block barrier.  Stage k holds the CTA's tiles it = k, k + 3, ...
+constexpr int kWgsThreads = 128;
+
+__global__ void __launch_bounds__(kWgsThreads, 1)
 k_wgrad_tc(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmG,
            const __nv_bfloat16* __restrict__ X, float* __restrict__ partial, float* __restrict__ partial_b,
            const TcErr err) {
@@ -1009,15 +1016,19 @@ k_wgrad_tc(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const _
     const uint32_t barf0 = bar_drain + 8;   // barf0 + 8 s: stage s filled (bytes 32..55; TMEM slot at 56)
     volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(bars_p + 56);
     volatile int* abortp = reinterpret_cast<volatile int*>(bars_p + 60);
-    float* red = reinterpret_cast<float*>(bars_p + 64);
+    float* red = reinterpret_cast<float*>(bars_p + 64);   // 64 bias sums
+    const uint32_t barb0 = s2u(bars_p + 64 + 512);         // barb0 + 8 s: stage s read by the bias warps
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tiles_x = W / kTile;
     const int ntiles = B * H * tiles_x;
+    // the CTA's tiles are t = blockIdx.x + it * gridDim.x, it < ntl
+    const int ntl = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     if (tid == 0) {
         for (int k = 0; k < kWgStages; ++k) {
             bar_init(bar0 + 8 * k, 1);
             bar_init(barf0 + 8 * k, 1 + 24);
+            bar_init(barb0 + 8 * k, 64);
         }
         bar_init(bar_drain, 1);
         *abortp = 0;
@@ -1029,113 +1040,137 @@ k_wgrad_tc(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const _
     tc_after_sync();
     const uint32_t tmem = *tmem_slot;
 
-    // Stage fill by warp 1: lane 0 arms the stage's barrier with the byte count;
-    // lanes 0..23 issue the X row boxes (row r = lane / 8, chunk lane mod 8) and
-    // copy the two halo chunks of their plane (loads and shared stores, then a
-    // proxy fence and an arrival: tiny bulk copies cost more), lanes 24..31 issue
-    // the dY boxes.
-    auto stage_in = [&](int t, int k) {
-        const int b = t / (H * tiles_x);
-        const int rem = t - b * H * tiles_x;
-        const int y = rem / tiles_x;
-        const int x0 = (rem - y * tiles_x) * kTile;
-        const uint32_t st = sbase + k * kWgStage;
-        const uint32_t full = barf0 + 8 * k;
-        if (lane == 0) bar_arrive_expect_tx(full, kWgTxBytes);
-        __syncwarp();
-        if (lane < 24) {
-            const int r = lane >> 3, c = lane & 7;
-            const int yy = wrapi(y + r - 1, H);
-            const uint32_t plane = st + kWgXOff + (uint32_t)(r * 8 + c) * kWgPlaneX;
-            tma_load_5d(plane + 16, &tmX, 0, c, x0, yy, b, full);
-            const size_t row = ((size_t)b * H + yy) * W;
-            const uint4 lft = __ldg(reinterpret_cast<const uint4*>(X + (row + wrapi(x0 - 1, W)) * kC + 8 * c));
-            const uint4 rgt = __ldg(reinterpret_cast<const uint4*>(X + (row + wrapi(x0 + kTile, W)) * kC + 8 * c));
-            asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n" ::"r"(plane), "r"(lft.x), "r"(lft.y), "r"(lft.z),
-                         "r"(lft.w)
-                         : "memory");
-            asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n" ::"r"(plane + 16 * (kWgRowPix - 1)), "r"(rgt.x),
-                         "r"(rgt.y), "r"(rgt.z), "r"(rgt.w)
-                         : "memory");
-            fence_async_smem();
-            bar_arrive(full);
-        } else {
-            const int c = lane - 24;
-            tma_load_5d(st + kWgX + c * kWgPlaneG, &tmG, 0, c, x0, y, b, full);
-        }
-    };
+    float bsum[4][8];   // bias warp 2 + h: planes 4 h + pl (channels 8 (4 h + pl) + i), pixels lane + 32 j
+#pragma unroll
+    for (int pl = 0; pl < 4; ++pl)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) bsum[pl][i] = 0.0f;
 
-    uint32_t phase = 0u;   // bit k: parity of the next completion of stage k's MMA barrier
-    int it = 0;
-    float bsum[8];         // warp w: channels 8 w .. 8 w + 7, pixels lane + 32 j of every tile
-#pragma unroll
-    for (int i = 0; i < 8; ++i) bsum[i] = 0.0f;
     if (warp == 1) {
+        // Stage fill: lane 0 arms the stage's barrier with the byte count; lanes
+        // 0..23 issue the X row boxes (row r = lane / 8, chunk lane mod 8) and copy
+        // the two halo chunks of their plane (loads and shared stores, then a proxy
+        // fence and an arrival: tiny bulk copies cost more), lanes 24..31 issue the
+        // dY boxes.
         if (lane == 0) asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tmX)) : "memory");
-        for (int j = 0; j < kWgStages - 1; ++j)
-            if ((int)blockIdx.x + j * (int)gridDim.x < ntiles) stage_in(blockIdx.x + j * gridDim.x, j);
-    }
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
-        const int k = it % kWgStages;
-        // stage k holds tile t once its barrier completes (fill number it / kWgStages)
-        if (!bar_wait(barf0 + 8 * k, (uint32_t)(it / kWgStages) & 1u, abortp, err.wait_ns)) *abortp = 1;
-        __syncthreads();
-        if (*abortp) break;
-        const uint32_t sX = sbase + k * kWgStage + kWgXOff, sG = sbase + k * kWgStage + kWgX;
-        if (tid == 0) {   // queued behind the previous tile's MMAs: the tensor pipe does not wait for the copies
-            tc_after_sync();
-#pragma unroll 1
-            for (int ks = 0; ks < kTile / 16; ++ks) {
-                const uint64_t bd = desc_mn(sG + 16 * 16 * ks, kWgPlaneG);
-#pragma unroll
-                for (int kx = 0; kx < 3; ++kx)
-#pragma unroll
-                    for (int pr = 0; pr < 2; ++pr)
-                        mma_wg(tmem + (uint32_t)((kx * 2 + pr) * 64),
-                               desc_mn(sX + pr * 8 * kWgPlaneX + 16 * (16 * ks + kx), kWgPlaneX), bd,
-                               (it > 0 || ks > 0) ? 1u : 0u);
+        int filled = 0;
+        for (int it = 0; it < ntl; ++it) {
+            const int k = it % kWgStages;
+            if (it >= kWgStages) {   // the stage's previous tile: MMAs done and bias read
+                const uint32_t par = (uint32_t)(it / kWgStages - 1) & 1u;
+                if (!bar_wait(bar0 + 8 * k, par, abortp, err.wait_ns)) break;
+                if (!bar_wait(barb0 + 8 * k, par, abortp, err.wait_ns)) break;
             }
-            tc_commit(bar0 + 8 * k);
+            const int t = (int)blockIdx.x + it * (int)gridDim.x;
+            const int b = t / (H * tiles_x);
+            const int rem = t - b * H * tiles_x;
+            const int y = rem / tiles_x;
+            const int x0 = (rem - y * tiles_x) * kTile;
+            const uint32_t st = sbase + k * kWgStage;
+            const uint32_t full = barf0 + 8 * k;
+            if (lane == 0) bar_arrive_expect_tx(full, kWgTxBytes);
+            __syncwarp();
+            if (lane < 24) {
+                const int r = lane >> 3, c = lane & 7;
+                const int yy = wrapi(y + r - 1, H);
+                const uint32_t plane = st + kWgXOff + (uint32_t)(r * 8 + c) * kWgPlaneX;
+                tma_load_5d(plane + 16, &tmX, 0, c, x0, yy, b, full);
+                const size_t row = ((size_t)b * H + yy) * W;
+                const uint4 lft = __ldg(reinterpret_cast<const uint4*>(X + (row + wrapi(x0 - 1, W)) * kC + 8 * c));
+                const uint4 rgt =
+                    __ldg(reinterpret_cast<const uint4*>(X + (row + wrapi(x0 + kTile, W)) * kC + 8 * c));
+                asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n" ::"r"(plane), "r"(lft.x), "r"(lft.y),
+                             "r"(lft.z), "r"(lft.w)
+                             : "memory");
+                asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n" ::"r"(plane + 16 * (kWgRowPix - 1)),
+                             "r"(rgt.x), "r"(rgt.y), "r"(rgt.z), "r"(rgt.w)
+                             : "memory");
+                fence_async_smem();
+                bar_arrive(full);
+            } else {
+                const int c = lane - 24;
+                tma_load_5d(st + kWgX + c * kWgPlaneG, &tmG, 0, c, x0, y, b, full);
+            }
+            ++filled;
         }
-        // the stage of tile it - 1 takes tile it + kWgStages - 1 once that tile's MMAs are done
-        const int kf = (it + kWgStages - 1) % kWgStages;
-        if (it >= 1) {
-            if (!bar_wait(bar0 + 8 * kf, (phase >> kf) & 1u, abortp, err.wait_ns)) *abortp = 1;
-            phase ^= 1u << kf;
+        // copies still in flight after an abort land before the CTA exits (each
+        // stage's last fill completes its barrier; earlier fills were consumed)
+        if (lane == 0 && *abortp)
+            for (int k = 0; k < kWgStages && k < filled; ++k)
+                bar_wait_drain(barf0 + 8 * k, (uint32_t)((filled - 1 - k) / kWgStages) & 1u);
+    } else if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int it = 0; it < ntl; ++it) {
+                const int k = it % kWgStages;
+                if (!bar_spin(barf0 + 8 * k, (uint32_t)(it / kWgStages) & 1u, abortp, err.wait_ns)) break;
+                tc_after_sync();
+                const uint32_t sX = sbase + k * kWgStage + kWgXOff, sG = sbase + k * kWgStage + kWgX;
+#pragma unroll 1
+                for (int ks = 0; ks < kTile / 16; ++ks) {
+                    const uint64_t bd = desc_mn(sG + 16 * 16 * ks, kWgPlaneG);
+#pragma unroll
+                    for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+                        for (int pr = 0; pr < 2; ++pr)
+                            mma_wg(tmem + (uint32_t)((kx * 2 + pr) * 64),
+                                   desc_mn(sX + pr * 8 * kWgPlaneX + 16 * (16 * ks + kx), kWgPlaneX), bd,
+                                   (it > 0 || ks > 0) ? 1u : 0u);
+                }
+                tc_commit(bar0 + 8 * k);
+                ++issued;
+            }
+            if (issued > 0) {   // every issued MMA done before the accumulators are read or released
+                tc_commit(bar_drain);
+                if (!bar_wait_drain(bar_drain, 0)) *abortp = 1;
+            }
         }
-        const int tf = t + (kWgStages - 1) * (int)gridDim.x;
-        if (warp == 1 && !*abortp && tf < ntiles) stage_in(tf, kf);
-        {   // bias: warp w sums plane w (channels 8 w ..), 16 contiguous bytes per pixel
-            const unsigned char* g = base + k * kWgStage + kWgX + warp * kWgPlaneG;   // dY plane of channels 8 w ..
+        __syncwarp();
+    } else {
+        // bias: warp 2 + h sums the dY planes 4 h .. 4 h + 3, 16 contiguous bytes per pixel
+        const int h = warp - 2;
+        for (int it = 0; it < ntl; ++it) {
+            const int k = it % kWgStages;
+            if (!bar_wait(barf0 + 8 * k, (uint32_t)(it / kWgStages) & 1u, abortp, err.wait_ns)) break;
 #pragma unroll
-            for (int j = 0; j < kTile / 32; ++j) {
-                const uint4 r = *reinterpret_cast<const uint4*>(g + 16 * (lane + 32 * j));
-                const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&r);
+            for (int pl = 0; pl < 4; ++pl) {
+                const unsigned char* g = base + k * kWgStage + kWgX + (4 * h + pl) * kWgPlaneG;
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float2 f = __bfloat1622float2(h[i]);
-                    bsum[2 * i] += f.x;
-                    bsum[2 * i + 1] += f.y;
+                for (int j = 0; j < kTile / 32; ++j) {
+                    const uint4 r = *reinterpret_cast<const uint4*>(g + 16 * (lane + 32 * j));
+                    const __nv_bfloat162* hv = reinterpret_cast<const __nv_bfloat162*>(&r);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float2 f = __bfloat1622float2(hv[i]);
+                        bsum[pl][2 * i] += f.x;
+                        bsum[pl][2 * i + 1] += f.y;
+                    }
                 }
             }
+            bar_arrive(barb0 + 8 * k);
         }
-        __syncthreads();   // every thread is done with this stage before it is refilled
+#pragma unroll
+        for (int pl = 0; pl < 4; ++pl)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                float v = bsum[pl][i];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) red[8 * (4 * h + pl) + i] = v;
+            }
     }
-    if (it > 0 && !*abortp) {
-        const int kl = (it - 1) % kWgStages;
-        if (!bar_wait(bar0 + 8 * kl, (phase >> kl) & 1u, abortp, err.wait_ns)) *abortp = 1;
-    }
+    tc_before_sync();
     __syncthreads();
     tc_after_sync();
-    if (!*abortp && it > 0) {
-        // warps 0-3 read accumulators 0-2, warps 4-7 accumulators 3-5, each its own 32 TMEM lanes
-        const int L = 32 * (warp & 3) + lane;
+    if (!*abortp && ntl > 0) {
+        // warp w reads TMEM lanes 32 w .. 32 w + 31 of the six accumulators
+        const int L = 32 * warp + lane;
         const int ci = L & 63;
-        for (int j = 0; j < 3; ++j) {
-            const int acc = 3 * (warp >> 2) + j;
+#pragma unroll 1
+        for (int acc = 0; acc < 6; ++acc) {
             const int kx = acc >> 1, pr = acc & 1;
             uint32_t v[64];
-            const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(acc * 64);
+            const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(acc * 64);
             PLBM_TMEM_LD32(v, 0, taddr);
             PLBM_TMEM_LD32(v, 32, taddr + 32);
             asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
@@ -1148,20 +1183,8 @@ k_wgrad_tc(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const _
                                       __uint_as_float(v[4 * c4 + 2]), __uint_as_float(v[4 * c4 + 3]));
         }
     }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        float v = bsum[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) red[8 * warp + i] = v;
-    }
+    if (tid < kC) partial_b[(size_t)blockIdx.x * kC + tid] = ntl > 0 ? red[tid] : 0.0f;
     tc_before_sync();
-    __syncthreads();
-    if (tid < kC) partial_b[(size_t)blockIdx.x * kC + tid] = red[tid];
-    if (tid == 0 && it > 0) {   // drain every issued MMA before the accumulators are released
-        tc_commit(bar_drain);
-        if (!bar_wait_drain(bar_drain, 0)) *abortp = 1;
-    }
     __syncthreads();
     if (tid == 0 && *abortp) atomicOr(err.flag, 1u);
     if (warp == 0) {
@@ -1499,7 +1522,7 @@ cudaError_t cnn_conv64_wgrad_tc(int B, int H, int W, const void* X, const void* 
     if (em == cudaSuccess) em = encode_act_map(&mapG, dY, B, H, W);
     if (em != cudaSuccess) return em;
     const int grid = cnn_wgrad64_parts(B, H, W);   // one CTA per SM at most (the partial buffers' size)
-    tc::k_wgrad_tc<<<grid, tc::kWgThreads, tc::kWgSmem, s>>>(B, H, W, mapX, mapG, static_cast<const __nv_bfloat16*>(X),
+    tc::k_wgrad_tc<<<grid, tc::kWgsThreads, tc::kWgSmem, s>>>(B, H, W, mapX, mapG, static_cast<const __nv_bfloat16*>(X),
                                                              partial, partial_b, err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
