@@ -948,35 +948,44 @@ k_conv_in_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __n
 // ---------------------------------------------------------------------------
 // 64 -> 64 weight gradient: dW[tap][ci][co] = sum over pixels of
 // X[pixel shifted by the tap][ci] dY[pixel][co], bias gradient db[co] = sum dY.
-// Per tile (128 pixels of one row) the three input rows (pixels x0 - 1 ..
-// x0 + 128) and the dY row are staged with cp.async in the chunk-planar
-// no-swizzle layout (chunk c of pixel s at plane c, byte 16 s), which is the
-// MN-major canonical layout for both operands: A = X^T (M = channels, K =
-// pixels) and B = dY (K = pixels, N = channels), 8-pixel K blocks 128 bytes
-// apart (leading byte offset) and 8-channel blocks one plane apart (stride byte
-// offset).  Planes of consecutive rows follow each other, so two rows stack into
-// one M = 128 operand: rows (y - 1, y) give taps ky = 0, 1 and rows (y, y + 1)
-// give ky = 1 (again, discarded) and 2.  Per K step of 16 pixels and tap column
-// kx: two MMAs of 128 x 64 x 16 into six TMEM accumulators (384 columns) that
-// sum over all of the CTA's tiles; three stages rotate so that the next two
-// tiles' copies run under the current tile's MMAs.  The CTA writes its partial
-// sums partial[cta][tap][ci][co], partial_b[cta][co] at the end.
+// A tile is 128 pixels of one row; its three input rows (pixels x0 - 1 ..
+// x0 + 128) and its dY row are staged in the chunk-planar no-swizzle layout
+// (chunk c of pixel s at plane c, byte 16 s), which is the MN-major canonical
+// layout for both operands: A = X^T (M = channels, K = pixels) and B = dY (K =
+// pixels, N = channels), 8-pixel K blocks 128 bytes apart (leading byte offset)
+// and 8-channel blocks one plane apart (stride byte offset).  Planes of
+// consecutive rows follow each other, so two rows stack into one M = 128
+// operand: rows (y - 1, y) give taps ky = 0, 1 and rows (y, y + 1) give ky = 1
+// (again, discarded) and 2.  Per K step of 16 pixels and tap column kx: two MMAs
+// of 128 x 64 x 16 into six TMEM accumulators (384 columns) that sum over all of
+// the CTA's tiles.
+//
+// A CTA takes a contiguous range of tiles in column order, t = (b * W / 128 +
+// xt) * H + y, so that consecutive tiles are consecutive rows of one 128-pixel
+// wide column: an input row is staged once, into a ring of kWrR row slots, and
+// serves the three tiles that read it (a column's first tile stages three rows,
+// every other tile one).  Slot kWrR is a second copy of slot 0, so that the row
+// pair of every tile is two adjacent slots.  The dY rows rotate through
+// kWgStages slots.  The CTA writes its partial sums partial[cta][tap][ci][co],
+// partial_b[cta][co] at the end.
 // ---------------------------------------------------------------------------
-constexpr int kWgThreads = 256;
+constexpr int kWgThreads = 256;   // k_wgrad_in_tc
 constexpr int kWgRowPix = kTile + 2;
 // X planes 17 lines apart, pixel 0 of a plane 112 bytes into a line, so that pixel
 // 1 (x0), the destination of the TMA box, is 128-byte aligned
 constexpr int kWgPlaneX = 17 * 128;             // 2176 >= 130 pixels x 16 bytes
 constexpr int kWgXOff = 112;
-constexpr int kWgX = 24 * kWgPlaneX + 128;      // 3 rows x 8 chunk planes (+ the pixel-0 offset)
 constexpr int kWgPlaneG = kTile * 16;           // 2048
-constexpr int kWgStage = kWgX + 8 * kWgPlaneG;  // 68736
-// Per stage: 24 TMA boxes of X rows and 8 of the dY row (the 48 halo chunks of
-// 16 bytes are copied by the threads).
-constexpr uint32_t kWgTxBytes = 24 * kTile * 16 + 8 * kTile * 16;
-constexpr int kWgStages = 3;                    // tiles in flight: two being copied while one multiplies
-constexpr int kWgSmem = 128 + kWgStages * kWgStage + 64 + 256 * 4;
-static_assert(kWgStage % 128 == 0 && kWgSmem <= 232448, "weight-gradient stages");
+constexpr int kWgStages = 3;                    // dY slots: two being copied while one multiplies
+constexpr int kWrR = 8;                         // input row slots
+constexpr int kWrSlot = 8 * kWgPlaneX;          // 17408: one input row, 8 chunk planes
+constexpr int kWrG = (kWrR + 1) * kWrSlot + 128;                // dY ring (after slot kWrR and the offset)
+constexpr int kWrBars = kWrG + kWgStages * 8 * kWgPlaneG;       // barriers, TMEM slot, bias sums
+constexpr int kWrSmem = 128 + kWrBars + 512;
+// Per input row: 8 TMA boxes of 128 pixels (the 16 halo chunks of 16 bytes are
+// copied by the threads); per dY row 8 boxes.
+constexpr uint32_t kWrRowTx = 8 * kTile * 16;
+static_assert(kWrSlot % 128 == 0 && kWrG % 128 == 0 && kWrSmem <= 232448, "weight-gradient rings");
 constexpr uint32_t kWgTmemCols = 512;
 // kind::f16, D fp32, A and B bf16, both MN-major (bits 15, 16), N = 64, M = 128.
 constexpr uint32_t kIdescWg = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((64u >> 3) << 17) |
@@ -995,11 +1004,14 @@ __device__ __forceinline__ void mma_wg(uint32_t tmem_d, uint64_t a, uint64_t b, 
         : "memory");
 }
 
-// Warp roles: lane 0 of warp 0 issues the MMAs, warp 1 fills the stages, warps
-// 2 and 3 sum dY for the bias gradient.  They hand stages over through mbarriers
-// only (full[k]: stage k's copies have landed; mma[k]: its MMAs are done;
-// bias[k]: both bias warps have read it), so the MMA issue never waits at a
-// block barrier.  Stage k holds the CTA's tiles it = k, k + 3, ...
+// Warp roles: lane 0 of warp 0 issues the MMAs, warp 1 stages the rows, warps 2
+// and 3 sum dY for the bias gradient.  They hand slots over through mbarriers
+// only: xfull[s] (row slot s landed), gfull[k] (dY slot k landed), done[k] (the
+// MMAs of the tiles up to the one in dY slot k are done; tcgen05.commit tracks
+// every earlier MMA of the thread), bias[k] (both bias warps have read dY slot
+// k).  Row fills are numbered f = 0, 1, ... in the CTA; fill f goes to slot
+// f mod kWrR (and also to slot kWrR when that is 0), tile i's dY to slot
+// i mod kWgStages.
 constexpr int kWgsThreads = 128;
 
 __global__ void __launch_bounds__(kWgsThreads, 1)
@@ -1011,113 +1023,155 @@ k_wgrad_tc(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const _
     const uint32_t pad = (128 - (raw & 127)) & 127;
     unsigned char* base = dsm_raw + pad;
     const uint32_t sbase = raw + pad;
-    unsigned char* bars_p = base + kWgStages * kWgStage;
-    const uint32_t bar0 = s2u(bars_p), bar_drain = bar0 + 8 * kWgStages;   // bar0 + 8 s: MMAs of stage s done
-    const uint32_t barf0 = bar_drain + 8;   // barf0 + 8 s: stage s filled (bytes 32..55; TMEM slot at 56)
-    volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(bars_p + 56);
-    volatile int* abortp = reinterpret_cast<volatile int*>(bars_p + 60);
-    float* red = reinterpret_cast<float*>(bars_p + 64);   // 64 bias sums
-    const uint32_t barb0 = s2u(bars_p + 64 + 512);         // barb0 + 8 s: stage s read by the bias warps
+    unsigned char* bars_p = base + kWrBars;
+    const uint32_t bar_done0 = s2u(bars_p), bar_drain = bar_done0 + 24;
+    volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(bars_p + 32);
+    volatile int* abortp = reinterpret_cast<volatile int*>(bars_p + 36);
+    const uint32_t bar_xfull0 = bar_done0 + 40;                  // kWrR barriers
+    const uint32_t bar_gfull0 = bar_xfull0 + 8 * kWrR;           // kWgStages each
+    const uint32_t bar_bias0 = bar_gfull0 + 8 * kWgStages;
+    float* red = reinterpret_cast<float*>(bars_p + 160);          // 64 bias sums
+    static_assert(40 + 8 * kWrR + 16 * kWgStages <= 160, "weight-gradient barriers");
+    const uint32_t sX = sbase + kWgXOff, sG = sbase + kWrG;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tiles_x = W / kTile;
-    const int ntiles = B * H * tiles_x;
-    // the CTA's tiles are t = blockIdx.x + it * gridDim.x, it < ntl
-    const int ntl = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const long long ntiles = (long long)B * H * tiles_x;
+    const int t0 = (int)(ntiles * blockIdx.x / gridDim.x);
+    const int ntl = (int)(ntiles * (blockIdx.x + 1) / gridDim.x) - t0;   // >= 1: the grid is at most ntiles
     if (tid == 0) {
         for (int k = 0; k < kWgStages; ++k) {
-            bar_init(bar0 + 8 * k, 1);
-            bar_init(barf0 + 8 * k, 1 + 24);
-            bar_init(barb0 + 8 * k, 64);
+            bar_init(bar_done0 + 8 * k, 1);
+            bar_init(bar_gfull0 + 8 * k, 1);
+            bar_init(bar_bias0 + 8 * k, 64);
         }
+        for (int k = 0; k < kWrR; ++k) bar_init(bar_xfull0 + 8 * k, 1 + 8);
         bar_init(bar_drain, 1);
         *abortp = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    if (warp == 0) tmem_alloc(s2u(bars_p + 56), kWgTmemCols);
+    if (warp == 0) tmem_alloc(s2u(bars_p + 32), kWgTmemCols);
     tc_before_sync();
     __syncthreads();
     tc_after_sync();
     const uint32_t tmem = *tmem_slot;
 
-    float bsum[4][8];   // bias warp 2 + h: planes 4 h + pl (channels 8 (4 h + pl) + i), pixels lane + 32 j
-#pragma unroll
-    for (int pl = 0; pl < 4; ++pl)
-#pragma unroll
-        for (int i = 0; i < 8; ++i) bsum[pl][i] = 0.0f;
-
     if (warp == 1) {
-        // Stage fill: lane 0 arms the stage's barrier with the byte count; lanes
-        // 0..23 issue the X row boxes (row r = lane / 8, chunk lane mod 8) and copy
-        // the two halo chunks of their plane (loads and shared stores, then a proxy
-        // fence and an arrival: tiny bulk copies cost more), lanes 24..31 issue the
-        // dY boxes.
+        // ---- rows: lane 8 q + c stages chunk plane c of the tile's q-th new row
+        // (TMA box for pixels x0 .. x0 + 127, loads and shared stores for the two
+        // halo pixels, then a proxy fence and an arrival); lanes 24..31 stage the
+        // dY planes ----
         if (lane == 0) asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tmX)) : "memory");
-        int filled = 0;
-        for (int it = 0; it < ntl; ++it) {
-            const int k = it % kWgStages;
-            if (it >= kWgStages) {   // the stage's previous tile: MMAs done and bias read
-                const uint32_t par = (uint32_t)(it / kWgStages - 1) & 1u;
-                if (!bar_wait(bar0 + 8 * k, par, abortp, err.wait_ns)) break;
-                if (!bar_wait(barb0 + 8 * k, par, abortp, err.wait_ns)) break;
+        int lastuse[kWrR];   // the last tile that reads the row in each slot
+#pragma unroll
+        for (int k = 0; k < kWrR; ++k) lastuse[k] = -1;
+        int F = -1;          // the last fill so far
+        int i = 0;
+        for (; i < ntl; ++i) {
+            const int t = t0 + i;
+            const int col = t / H, y = t - col * H;
+            const int b = col / tiles_x, x0 = (col - b * tiles_x) * kTile;
+            const int nf = (i == 0 || y == 0) ? 3 : 1;   // a column's first tile stages rows y - 1, y, y + 1
+            const int f0 = F + 1;
+            // slots free: the tiles that read their rows, and the tile of dY slot i mod kWgStages, done
+            int w = i - kWgStages;
+#pragma unroll
+            for (int k = 0; k < kWrR; ++k) {
+                const bool refill = ((k - f0 % kWrR + kWrR) % kWrR) < nf && f0 + ((k - f0 % kWrR + kWrR) % kWrR) >= kWrR;
+                if (refill && lastuse[k] > w) w = lastuse[k];
             }
-            const int t = (int)blockIdx.x + it * (int)gridDim.x;
-            const int b = t / (H * tiles_x);
-            const int rem = t - b * H * tiles_x;
-            const int y = rem / tiles_x;
-            const int x0 = (rem - y * tiles_x) * kTile;
-            const uint32_t st = sbase + k * kWgStage;
-            const uint32_t full = barf0 + 8 * k;
-            if (lane == 0) bar_arrive_expect_tx(full, kWgTxBytes);
+            if (w >= 0 && !bar_wait(bar_done0 + 8 * (w % kWgStages), (uint32_t)(w / kWgStages) & 1u, abortp,
+                                    err.wait_ns))
+                break;
+            if (i >= kWgStages && !bar_wait(bar_bias0 + 8 * (i % kWgStages),
+                                            (uint32_t)(i / kWgStages - 1) & 1u, abortp, err.wait_ns))
+                break;
+            // arm the barriers (before any copy of this tile is issued)
+            if (lane < nf) {
+                const int sl = (f0 + lane) % kWrR;
+                bar_arrive_expect_tx(bar_xfull0 + 8 * sl, sl == 0 ? 2 * kWrRowTx : kWrRowTx);
+            }
+            if (lane == 24) bar_arrive_expect_tx(bar_gfull0 + 8 * (i % kWgStages), kWrRowTx);
             __syncwarp();
-            if (lane < 24) {
-                const int r = lane >> 3, c = lane & 7;
-                const int yy = wrapi(y + r - 1, H);
-                const uint32_t plane = st + kWgXOff + (uint32_t)(r * 8 + c) * kWgPlaneX;
-                tma_load_5d(plane + 16, &tmX, 0, c, x0, yy, b, full);
+            if (lane < 8 * nf) {
+                const int q = lane >> 3, c = lane & 7;
+                const int sl = (f0 + q) % kWrR;
+                const int yy = wrapi(nf == 3 ? y + q - 1 : y + 1, H);
+                const uint32_t full = bar_xfull0 + 8 * sl;
                 const size_t row = ((size_t)b * H + yy) * W;
                 const uint4 lft = __ldg(reinterpret_cast<const uint4*>(X + (row + wrapi(x0 - 1, W)) * kC + 8 * c));
                 const uint4 rgt =
                     __ldg(reinterpret_cast<const uint4*>(X + (row + wrapi(x0 + kTile, W)) * kC + 8 * c));
-                asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n" ::"r"(plane), "r"(lft.x), "r"(lft.y),
-                             "r"(lft.z), "r"(lft.w)
-                             : "memory");
-                asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n" ::"r"(plane + 16 * (kWgRowPix - 1)),
-                             "r"(rgt.x), "r"(rgt.y), "r"(rgt.z), "r"(rgt.w)
-                             : "memory");
+                for (int dup = 0; dup < (sl == 0 ? 2 : 1); ++dup) {
+                    const uint32_t plane = sX + (uint32_t)((dup ? kWrR : sl) * kWrSlot + c * kWgPlaneX);
+                    tma_load_5d(plane + 16, &tmX, 0, c, x0, yy, b, full);
+                    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n" ::"r"(plane), "r"(lft.x), "r"(lft.y),
+                                 "r"(lft.z), "r"(lft.w)
+                                 : "memory");
+                    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n" ::"r"(plane + 16 * (kWgRowPix - 1)),
+                                 "r"(rgt.x), "r"(rgt.y), "r"(rgt.z), "r"(rgt.w)
+                                 : "memory");
+                }
                 fence_async_smem();
                 bar_arrive(full);
-            } else {
+            } else if (lane >= 24) {
                 const int c = lane - 24;
-                tma_load_5d(st + kWgX + c * kWgPlaneG, &tmG, 0, c, x0, y, b, full);
+                tma_load_5d(sG + (uint32_t)((i % kWgStages) * 8 * kWgPlaneG + c * kWgPlaneG), &tmG, 0, c, x0, y, b,
+                            bar_gfull0 + 8 * (i % kWgStages));
             }
-            ++filled;
+            // the new rows' readers: row y - 1 + p (p = 0, 1, 2) serves tiles i .. i + p of this column and range
+            const int reach = min(H - 1 - y, ntl - 1 - i);
+#pragma unroll
+            for (int k = 0; k < kWrR; ++k) {
+                const int q = (k - f0 % kWrR + kWrR) % kWrR;
+                if (q < nf) lastuse[k] = i + min(nf == 3 ? q : 2, reach);
+            }
+            F += nf;
         }
-        // copies still in flight after an abort land before the CTA exits (each
-        // stage's last fill completes its barrier; earlier fills were consumed)
-        if (lane == 0 && *abortp)
-            for (int k = 0; k < kWgStages && k < filled; ++k)
-                bar_wait_drain(barf0 + 8 * k, (uint32_t)((filled - 1 - k) / kWgStages) & 1u);
+        // after an abort, the copies already issued land before the CTA exits:
+        // each slot's last fill completes its barrier (every fill arms all of its arrivals)
+        if (lane == 0 && *abortp) {
+            for (int k = 0; k < kWrR; ++k) {
+                const int f = F - ((F - k) % kWrR + kWrR) % kWrR;
+                if (f >= 0) bar_wait_drain(bar_xfull0 + 8 * k, (uint32_t)(f / kWrR) & 1u);
+            }
+            for (int k = 0; k < kWgStages; ++k) {
+                const int j = (i - 1) - (((i - 1) - k) % kWgStages + kWgStages) % kWgStages;
+                if (j >= 0) bar_wait_drain(bar_gfull0 + 8 * k, (uint32_t)(j / kWgStages) & 1u);
+            }
+        }
     } else if (warp == 0) {
         if (lane == 0) {
-            int issued = 0;
-            for (int it = 0; it < ntl; ++it) {
-                const int k = it % kWgStages;
-                if (!bar_spin(barf0 + 8 * k, (uint32_t)(it / kWgStages) & 1u, abortp, err.wait_ns)) break;
+            int F = -1, issued = 0;
+            for (int i = 0; i < ntl; ++i) {
+                const int t = t0 + i;
+                const int y = t - (t / H) * H;
+                const int nf = (i == 0 || y == 0) ? 3 : 1;
+                bool ok = true;
+                for (int q = 0; q < nf && ok; ++q) {
+                    const int f = F + 1 + q;
+                    ok = bar_spin(bar_xfull0 + 8 * (f % kWrR), (uint32_t)(f / kWrR) & 1u, abortp, err.wait_ns);
+                }
+                F += nf;
+                const int k = i % kWgStages;
+                if (!ok || !bar_spin(bar_gfull0 + 8 * k, (uint32_t)(i / kWgStages) & 1u, abortp, err.wait_ns)) break;
                 tc_after_sync();
-                const uint32_t sX = sbase + k * kWgStage + kWgXOff, sG = sbase + k * kWgStage + kWgX;
+                // row pairs (y - 1, y) and (y, y + 1): fills F - 2, F - 1 and F - 1, F in adjacent slots
+                const uint32_t a0 = sX + (uint32_t)(((F - 2) % kWrR) * kWrSlot);
+                const uint32_t a1 = sX + (uint32_t)(((F - 1) % kWrR) * kWrSlot);
+                const uint32_t g = sG + (uint32_t)(k * 8 * kWgPlaneG);
 #pragma unroll 1
                 for (int ks = 0; ks < kTile / 16; ++ks) {
-                    const uint64_t bd = desc_mn(sG + 16 * 16 * ks, kWgPlaneG);
+                    const uint64_t bd = desc_mn(g + 16 * 16 * ks, kWgPlaneG);
 #pragma unroll
                     for (int kx = 0; kx < 3; ++kx)
 #pragma unroll
                         for (int pr = 0; pr < 2; ++pr)
                             mma_wg(tmem + (uint32_t)((kx * 2 + pr) * 64),
-                                   desc_mn(sX + pr * 8 * kWgPlaneX + 16 * (16 * ks + kx), kWgPlaneX), bd,
-                                   (it > 0 || ks > 0) ? 1u : 0u);
+                                   desc_mn((pr ? a1 : a0) + 16 * (16 * ks + kx), kWgPlaneX), bd,
+                                   (i > 0 || ks > 0) ? 1u : 0u);
                 }
-                tc_commit(bar0 + 8 * k);
+                tc_commit(bar_done0 + 8 * k);
                 ++issued;
             }
             if (issued > 0) {   // every issued MMA done before the accumulators are read or released
@@ -1127,42 +1181,47 @@ k_wgrad_tc(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const _
         }
         __syncwarp();
     } else {
-        // bias: warp 2 + h sums the dY planes 4 h .. 4 h + 3, 16 contiguous bytes per pixel
+        // ---- bias: warp 2 + h sums the dY planes 4 h .. 4 h + 3, 16 contiguous bytes per pixel ----
         const int h = warp - 2;
-        for (int it = 0; it < ntl; ++it) {
-            const int k = it % kWgStages;
-            if (!bar_wait(barf0 + 8 * k, (uint32_t)(it / kWgStages) & 1u, abortp, err.wait_ns)) break;
+        float bsum[4][8];   // planes 4 h + pl (channels 8 (4 h + pl) + e), pixels lane + 32 j
+#pragma unroll
+        for (int pl = 0; pl < 4; ++pl)
+#pragma unroll
+            for (int e = 0; e < 8; ++e) bsum[pl][e] = 0.0f;
+        for (int i = 0; i < ntl; ++i) {
+            const int k = i % kWgStages;
+            if (!bar_wait(bar_gfull0 + 8 * k, (uint32_t)(i / kWgStages) & 1u, abortp, err.wait_ns)) break;
 #pragma unroll
             for (int pl = 0; pl < 4; ++pl) {
-                const unsigned char* g = base + k * kWgStage + kWgX + (4 * h + pl) * kWgPlaneG;
+                const unsigned char* g = base + kWrG + (k * 8 + 4 * h + pl) * kWgPlaneG;
 #pragma unroll
                 for (int j = 0; j < kTile / 32; ++j) {
                     const uint4 r = *reinterpret_cast<const uint4*>(g + 16 * (lane + 32 * j));
                     const __nv_bfloat162* hv = reinterpret_cast<const __nv_bfloat162*>(&r);
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const float2 f = __bfloat1622float2(hv[i]);
-                        bsum[pl][2 * i] += f.x;
-                        bsum[pl][2 * i + 1] += f.y;
+                    for (int e = 0; e < 4; ++e) {
+                        const float2 f = __bfloat1622float2(hv[e]);
+                        bsum[pl][2 * e] += f.x;
+                        bsum[pl][2 * e + 1] += f.y;
                     }
                 }
             }
-            bar_arrive(barb0 + 8 * k);
+            bar_arrive(bar_bias0 + 8 * k);
         }
 #pragma unroll
         for (int pl = 0; pl < 4; ++pl)
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                float v = bsum[pl][i];
+            for (int e = 0; e < 8; ++e) {
+                float v = bsum[pl][e];
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (lane == 0) red[8 * (4 * h + pl) + i] = v;
+                if (lane == 0) red[8 * (4 * h + pl) + e] = v;
             }
     }
     tc_before_sync();
     __syncthreads();
     tc_after_sync();
-    if (!*abortp && ntl > 0) {
+    if (!*abortp) {
         // warp w reads TMEM lanes 32 w .. 32 w + 31 of the six accumulators
         const int L = 32 * warp + lane;
         const int ci = L & 63;
@@ -1182,8 +1241,8 @@ k_wgrad_tc(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const _
                 out[c4] = make_float4(__uint_as_float(v[4 * c4]), __uint_as_float(v[4 * c4 + 1]),
                                       __uint_as_float(v[4 * c4 + 2]), __uint_as_float(v[4 * c4 + 3]));
         }
+        if (tid < kC) partial_b[(size_t)blockIdx.x * kC + tid] = red[tid];
     }
-    if (tid < kC) partial_b[(size_t)blockIdx.x * kC + tid] = ntl > 0 ? red[tid] : 0.0f;
     tc_before_sync();
     __syncthreads();
     if (tid == 0 && *abortp) atomicOr(err.flag, 1u);
@@ -1513,7 +1572,7 @@ cudaError_t cnn_conv64_wgrad_tc(int B, int H, int W, const void* X, const void* 
     if (W % tc::kTile || H < 1 || B < 1) return cudaErrorInvalidValue;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(tc::k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kWgSmem);
+        cudaError_t e = cudaFuncSetAttribute(tc::k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kWrSmem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -1522,7 +1581,7 @@ cudaError_t cnn_conv64_wgrad_tc(int B, int H, int W, const void* X, const void* 
     if (em == cudaSuccess) em = encode_act_map(&mapG, dY, B, H, W);
     if (em != cudaSuccess) return em;
     const int grid = cnn_wgrad64_parts(B, H, W);   // one CTA per SM at most (the partial buffers' size)
-    tc::k_wgrad_tc<<<grid, tc::kWgsThreads, tc::kWgSmem, s>>>(B, H, W, mapX, mapG, static_cast<const __nv_bfloat16*>(X),
+    tc::k_wgrad_tc<<<grid, tc::kWgsThreads, tc::kWrSmem, s>>>(B, H, W, mapX, mapG, static_cast<const __nv_bfloat16*>(X),
                                                              partial, partial_b, err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
