@@ -966,7 +966,7 @@ k_conv_in_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __n
 // serves the three tiles that read it (a column's first tile stages three rows,
 // every other tile one).  Slot kWrR is a second copy of slot 0, so that the row
 // pair of every tile is two adjacent slots.  The dY rows rotate through
-// kWgStages slots.  The CTA writes its partial sums partial[cta][tap][ci][co],
+// kWrD slots.  The CTA writes its partial sums partial[cta][tap][ci][co],
 // partial_b[cta][co] at the end.
 // ---------------------------------------------------------------------------
 constexpr int kWgThreads = 256;   // k_wgrad_in_tc
@@ -976,11 +976,12 @@ constexpr int kWgRowPix = kTile + 2;
 constexpr int kWgPlaneX = 17 * 128;             // 2176 >= 130 pixels x 16 bytes
 constexpr int kWgXOff = 112;
 constexpr int kWgPlaneG = kTile * 16;           // 2048
-constexpr int kWgStages = 3;                    // dY slots: two being copied while one multiplies
-constexpr int kWrR = 8;                         // input row slots
+constexpr int kWgStages = 3;                    // k_wgrad_in_tc: two tiles being copied while one multiplies
+constexpr int kWrR = 7;                         // input row slots
+constexpr int kWrD = 4;                         // dY row slots
 constexpr int kWrSlot = 8 * kWgPlaneX;          // 17408: one input row, 8 chunk planes
 constexpr int kWrG = (kWrR + 1) * kWrSlot + 128;                // dY ring (after slot kWrR and the offset)
-constexpr int kWrBars = kWrG + kWgStages * 8 * kWgPlaneG;       // barriers, TMEM slot, bias sums
+constexpr int kWrBars = kWrG + kWrD * 8 * kWgPlaneG;       // barriers, TMEM slot, bias sums
 constexpr int kWrSmem = 128 + kWrBars + 512;
 // Per input row: 8 TMA boxes of 128 pixels (the 16 halo chunks of 16 bytes are
 // copied by the threads); per dY row 8 boxes.
@@ -1011,7 +1012,7 @@ __device__ __forceinline__ void mma_wg(uint32_t tmem_d, uint64_t a, uint64_t b, 
 // every earlier MMA of the thread), bias[k] (both bias warps have read dY slot
 // k).  Row fills are numbered f = 0, 1, ... in the CTA; fill f goes to slot
 // f mod kWrR (and also to slot kWrR when that is 0), tile i's dY to slot
-// i mod kWgStages.
+// i mod kWrD.
 constexpr int kWgsThreads = 128;
 
 __global__ void __launch_bounds__(kWgsThreads, 1)
@@ -1024,14 +1025,16 @@ k_wgrad_tc(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const _
     unsigned char* base = dsm_raw + pad;
     const uint32_t sbase = raw + pad;
     unsigned char* bars_p = base + kWrBars;
-    const uint32_t bar_done0 = s2u(bars_p), bar_drain = bar_done0 + 24;
-    volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(bars_p + 32);
-    volatile int* abortp = reinterpret_cast<volatile int*>(bars_p + 36);
-    const uint32_t bar_xfull0 = bar_done0 + 40;                  // kWrR barriers
-    const uint32_t bar_gfull0 = bar_xfull0 + 8 * kWrR;           // kWgStages each
-    const uint32_t bar_bias0 = bar_gfull0 + 8 * kWgStages;
-    float* red = reinterpret_cast<float*>(bars_p + 160);          // 64 bias sums
-    static_assert(40 + 8 * kWrR + 16 * kWgStages <= 160, "weight-gradient barriers");
+    // done[kWrD], drain, TMEM slot, abort flag, xfull[kWrR], gfull[kWrD], bias[kWrD]; 64 bias sums at 256
+    const uint32_t bar_done0 = s2u(bars_p), bar_drain = bar_done0 + 8 * kWrD;
+    unsigned char* slot_p = bars_p + 8 * kWrD + 8;
+    volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(slot_p);
+    volatile int* abortp = reinterpret_cast<volatile int*>(slot_p + 4);
+    const uint32_t bar_xfull0 = bar_drain + 16;
+    const uint32_t bar_gfull0 = bar_xfull0 + 8 * kWrR;
+    const uint32_t bar_bias0 = bar_gfull0 + 8 * kWrD;
+    float* red = reinterpret_cast<float*>(bars_p + 256);
+    static_assert(8 * kWrD + 16 + 8 * kWrR + 16 * kWrD <= 256, "weight-gradient barriers");
     const uint32_t sX = sbase + kWgXOff, sG = sbase + kWrG;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1040,7 +1043,7 @@ k_wgrad_tc(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const _
     const int t0 = (int)(ntiles * blockIdx.x / gridDim.x);
     const int ntl = (int)(ntiles * (blockIdx.x + 1) / gridDim.x) - t0;   // >= 1: the grid is at most ntiles
     if (tid == 0) {
-        for (int k = 0; k < kWgStages; ++k) {
+        for (int k = 0; k < kWrD; ++k) {
             bar_init(bar_done0 + 8 * k, 1);
             bar_init(bar_gfull0 + 8 * k, 1);
             bar_init(bar_bias0 + 8 * k, 64);
@@ -1050,7 +1053,7 @@ k_wgrad_tc(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const _
         *abortp = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    if (warp == 0) tmem_alloc(s2u(bars_p + 32), kWgTmemCols);
+    if (warp == 0) tmem_alloc(s2u(slot_p), kWgTmemCols);
     tc_before_sync();
     __syncthreads();
     tc_after_sync();
@@ -1073,25 +1076,25 @@ k_wgrad_tc(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const _
             const int b = col / tiles_x, x0 = (col - b * tiles_x) * kTile;
             const int nf = (i == 0 || y == 0) ? 3 : 1;   // a column's first tile stages rows y - 1, y, y + 1
             const int f0 = F + 1;
-            // slots free: the tiles that read their rows, and the tile of dY slot i mod kWgStages, done
-            int w = i - kWgStages;
+            // slots free: the tiles that read their rows, and the tile of dY slot i mod kWrD, done
+            int w = i - kWrD;
 #pragma unroll
             for (int k = 0; k < kWrR; ++k) {
                 const bool refill = ((k - f0 % kWrR + kWrR) % kWrR) < nf && f0 + ((k - f0 % kWrR + kWrR) % kWrR) >= kWrR;
                 if (refill && lastuse[k] > w) w = lastuse[k];
             }
-            if (w >= 0 && !bar_wait(bar_done0 + 8 * (w % kWgStages), (uint32_t)(w / kWgStages) & 1u, abortp,
+            if (w >= 0 && !bar_wait(bar_done0 + 8 * (w % kWrD), (uint32_t)(w / kWrD) & 1u, abortp,
                                     err.wait_ns))
                 break;
-            if (i >= kWgStages && !bar_wait(bar_bias0 + 8 * (i % kWgStages),
-                                            (uint32_t)(i / kWgStages - 1) & 1u, abortp, err.wait_ns))
+            if (i >= kWrD && !bar_wait(bar_bias0 + 8 * (i % kWrD),
+                                            (uint32_t)(i / kWrD - 1) & 1u, abortp, err.wait_ns))
                 break;
             // arm the barriers (before any copy of this tile is issued)
             if (lane < nf) {
                 const int sl = (f0 + lane) % kWrR;
                 bar_arrive_expect_tx(bar_xfull0 + 8 * sl, sl == 0 ? 2 * kWrRowTx : kWrRowTx);
             }
-            if (lane == 24) bar_arrive_expect_tx(bar_gfull0 + 8 * (i % kWgStages), kWrRowTx);
+            if (lane == 24) bar_arrive_expect_tx(bar_gfull0 + 8 * (i % kWrD), kWrRowTx);
             __syncwarp();
             if (lane < 8 * nf) {
                 const int q = lane >> 3, c = lane & 7;
@@ -1116,8 +1119,8 @@ k_wgrad_tc(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const _
                 bar_arrive(full);
             } else if (lane >= 24) {
                 const int c = lane - 24;
-                tma_load_5d(sG + (uint32_t)((i % kWgStages) * 8 * kWgPlaneG + c * kWgPlaneG), &tmG, 0, c, x0, y, b,
-                            bar_gfull0 + 8 * (i % kWgStages));
+                tma_load_5d(sG + (uint32_t)((i % kWrD) * 8 * kWgPlaneG + c * kWgPlaneG), &tmG, 0, c, x0, y, b,
+                            bar_gfull0 + 8 * (i % kWrD));
             }
             // the new rows' readers: row y - 1 + p (p = 0, 1, 2) serves tiles i .. i + p of this column and range
             const int reach = min(H - 1 - y, ntl - 1 - i);
@@ -1135,9 +1138,9 @@ k_wgrad_tc(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const _
                 const int f = F - ((F - k) % kWrR + kWrR) % kWrR;
                 if (f >= 0) bar_wait_drain(bar_xfull0 + 8 * k, (uint32_t)(f / kWrR) & 1u);
             }
-            for (int k = 0; k < kWgStages; ++k) {
-                const int j = (i - 1) - (((i - 1) - k) % kWgStages + kWgStages) % kWgStages;
-                if (j >= 0) bar_wait_drain(bar_gfull0 + 8 * k, (uint32_t)(j / kWgStages) & 1u);
+            for (int k = 0; k < kWrD; ++k) {
+                const int j = (i - 1) - (((i - 1) - k) % kWrD + kWrD) % kWrD;
+                if (j >= 0) bar_wait_drain(bar_gfull0 + 8 * k, (uint32_t)(j / kWrD) & 1u);
             }
         }
     } else if (warp == 0) {
@@ -1153,8 +1156,8 @@ k_wgrad_tc(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const _
                     ok = bar_spin(bar_xfull0 + 8 * (f % kWrR), (uint32_t)(f / kWrR) & 1u, abortp, err.wait_ns);
                 }
                 F += nf;
-                const int k = i % kWgStages;
-                if (!ok || !bar_spin(bar_gfull0 + 8 * k, (uint32_t)(i / kWgStages) & 1u, abortp, err.wait_ns)) break;
+                const int k = i % kWrD;
+                if (!ok || !bar_spin(bar_gfull0 + 8 * k, (uint32_t)(i / kWrD) & 1u, abortp, err.wait_ns)) break;
                 tc_after_sync();
                 // row pairs (y - 1, y) and (y, y + 1): fills F - 2, F - 1 and F - 1, F in adjacent slots
                 const uint32_t a0 = sX + (uint32_t)(((F - 2) % kWrR) * kWrSlot);
@@ -1189,8 +1192,8 @@ k_wgrad_tc(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const _
 #pragma unroll
             for (int e = 0; e < 8; ++e) bsum[pl][e] = 0.0f;
         for (int i = 0; i < ntl; ++i) {
-            const int k = i % kWgStages;
-            if (!bar_wait(bar_gfull0 + 8 * k, (uint32_t)(i / kWgStages) & 1u, abortp, err.wait_ns)) break;
+            const int k = i % kWrD;
+            if (!bar_wait(bar_gfull0 + 8 * k, (uint32_t)(i / kWrD) & 1u, abortp, err.wait_ns)) break;
 #pragma unroll
             for (int pl = 0; pl < 4; ++pl) {
                 const unsigned char* g = base + kWrG + (k * 8 + 4 * h + pl) * kWgPlaneG;
@@ -1444,6 +1447,235 @@ __global__ void k_weights_in(const float* __restrict__ W, __nv_bfloat16* __restr
     Win[i] = __float2bfloat16_rn(k < 36 ? W[((k >> 2) * 4 + (k & 3)) * kC + n] : 0.0f);
 }
 
+
+// ---------------------------------------------------------------------------
+// 64 -> 4 output-layer weight gradient on tcgen05: dW[tap][ci][co] = sum over
+// pixels of X[y + ky - 1][x + kx - 1][ci] dY[y][x][co], db[co] = sum dY.  The
+// same sum taken over the input pixel (y', x') = (y + ky - 1, x + kx - 1) pairs
+// X[y'][x'] with dY[y' - ky + 1][x' - kx + 1], so a tile of two input rows
+// (y0, y0 + 1) x 128 pixels is one M = 128 operand (A = X^T: (row, ci) x pixels,
+// staged by TMA in the chunk-planar layout, with no halo), and the shifted
+// upstream gradients of dY rows y0 - 1 .. y0 + 2 form B: K = pixels, N = (j,
+// kx, co) = 4 rows x 3 shifts x 4 channels = 48 columns.  Row y' = y0 + r of X
+// meets dY row y = y0 - 1 + j in tap ky = y' - y + 1 = r - j + 2 when that lies
+// in 0..2 (3 of the 4 rows j for either r).  dY is FP32: B carries it as a bf16 pair
+// hi + lo (hi = bf16(dY), lo = bf16(dY - hi)) in columns 0..47 and 48..95, so
+// that the products keep FP32 accuracy (N = 96).  X rows past the lattice (odd
+// H) are zero (TMA out-of-range fill).
+// Warps: 0 issues the MMAs (lane 0), 1 issues the TMA copies of X, 2..5 build B
+// (one pixel a thread) and sum dY for db, then read the accumulators.
+// ---------------------------------------------------------------------------
+constexpr int kWoThreads = 192;
+constexpr int kWoStages = 3;
+constexpr int kWoX = 16 * kWgPlaneG;                 // 32 KB: 2 rows x 8 chunk planes of 128 pixels
+constexpr int kWoStage = kWoX + 12 * kWgPlaneG;      // + B: 12 planes of 8 columns
+constexpr int kWoBars = kWoStages * kWoStage;
+constexpr int kWoSmem = 128 + kWoBars + 128;
+constexpr uint32_t kWoTmemCols = 128;
+static_assert(kWoSmem <= 232448 && 9 * kC * 4 * 4 <= kWoBars, "output-layer weight-gradient stages");
+// kind::f16, D fp32, A and B bf16, both MN-major, N = 96, M = 128.
+constexpr uint32_t kIdescWo = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((96u >> 3) << 17) |
+                              ((128u >> 4) << 24);
+
+__global__ void __launch_bounds__(kWoThreads, 1)
+k_wgrad_out_tc(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const float* __restrict__ dY,
+               float* __restrict__ partial, float* __restrict__ partial_b, const TcErr err) {
+    extern __shared__ unsigned char dsm_raw[];
+    const uint32_t raw = s2u(dsm_raw);
+    const uint32_t pad = (128 - (raw & 127)) & 127;
+    unsigned char* base = dsm_raw + pad;
+    const uint32_t sbase = raw + pad;
+    unsigned char* bars_p = base + kWoBars;
+    // xfull[k] at 8 k, bfull[k] at 24 + 8 k, done[k] at 48 + 8 k, drain 72, TMEM slot 80, abort flag 84
+    const uint32_t bar_x0 = s2u(bars_p), bar_b0 = bar_x0 + 24, bar_d0 = bar_x0 + 48, bar_drain = bar_x0 + 72;
+    volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(bars_p + 80);
+    volatile int* abortp = reinterpret_cast<volatile int*>(bars_p + 84);
+    static_assert(kWoStages == 3, "barrier layout");
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tiles_x = W / kTile, hp = (H + 1) / 2;
+    const int ntiles = B * hp * tiles_x;
+    const int ntl = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    if (tid == 0) {
+        for (int k = 0; k < kWoStages; ++k) {
+            bar_init(bar_x0 + 8 * k, 1);
+            bar_init(bar_b0 + 8 * k, 128);
+            bar_init(bar_d0 + 8 * k, 1);
+        }
+        bar_init(bar_drain, 1);
+        *abortp = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(s2u(bars_p + 80), kWoTmemCols);
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    float bacc[4] = {0.f, 0.f, 0.f, 0.f};
+
+    if (warp == 1) {
+        if (lane == 0) asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tmX)) : "memory");
+        int it = 0;
+        for (; it < ntl; ++it) {
+            const int k = it % kWoStages;
+            if (it >= kWoStages &&
+                !bar_wait(bar_d0 + 8 * k, (uint32_t)(it / kWoStages - 1) & 1u, abortp, err.wait_ns))
+                break;
+            const int t = (int)blockIdx.x + it * (int)gridDim.x;
+            const int b = t / (hp * tiles_x);
+            const int rem = t - b * hp * tiles_x;
+            const int y0 = 2 * (rem / tiles_x);
+            const int x0 = (rem % tiles_x) * kTile;
+            if (lane == 0) bar_arrive_expect_tx(bar_x0 + 8 * k, (uint32_t)kWoX);
+            __syncwarp();
+            if (lane < 16)   // plane (r, c) of row y0 + r; row H (odd H) is out of range: zeros
+                tma_load_5d(sbase + (uint32_t)(k * kWoStage + lane * kWgPlaneG), &tmX, 0, lane & 7, x0,
+                            y0 + (lane >> 3), b, bar_x0 + 8 * k);
+        }
+        if (lane == 0 && *abortp)   // copies already issued land before the CTA exits
+            for (int k = 0; k < kWoStages; ++k) {
+                const int j = (it - 1) - (((it - 1) - k) % kWoStages + kWoStages) % kWoStages;
+                if (j >= 0) bar_wait_drain(bar_x0 + 8 * k, (uint32_t)(j / kWoStages) & 1u);
+            }
+    } else if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int it = 0; it < ntl; ++it) {
+                const int k = it % kWoStages;
+                const uint32_t par = (uint32_t)(it / kWoStages) & 1u;
+                if (!bar_spin(bar_x0 + 8 * k, par, abortp, err.wait_ns) ||
+                    !bar_spin(bar_b0 + 8 * k, par, abortp, err.wait_ns))
+                    break;
+                tc_after_sync();
+                const uint32_t sA = sbase + (uint32_t)(k * kWoStage), sB = sA + kWoX;
+#pragma unroll
+                for (int ks = 0; ks < kTile / 16; ++ks) {
+                    const uint64_t a = desc_mn(sA + 256 * ks, kWgPlaneG), bd = desc_mn(sB + 256 * ks, kWgPlaneG);
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\t"
+                        "setp.ne.u32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+                        "l"(a), "l"(bd), "r"(kIdescWo), "r"((it > 0 || ks > 0) ? 1u : 0u)
+                        : "memory");
+                }
+                tc_commit(bar_d0 + 8 * k);
+                ++issued;
+            }
+            if (issued > 0) {
+                tc_commit(bar_drain);
+                if (!bar_wait_drain(bar_drain, 0)) *abortp = 1;
+            }
+        }
+        __syncwarp();
+    } else {
+        // B builders: thread q = pixel q of the tile; column n = 48 h + 12 j + 4 kx + co
+        const int q = tid - 64;
+        for (int it = 0; it < ntl; ++it) {
+            const int k = it % kWoStages;
+            if (it >= kWoStages &&
+                !bar_wait(bar_d0 + 8 * k, (uint32_t)(it / kWoStages - 1) & 1u, abortp, err.wait_ns))
+                break;
+            const int t = (int)blockIdx.x + it * (int)gridDim.x;
+            const int b = t / (hp * tiles_x);
+            const int rem = t - b * hp * tiles_x;
+            const int y0 = 2 * (rem / tiles_x);
+            const int x0 = (rem % tiles_x) * kTile;
+            const uint32_t sB = sbase + (uint32_t)(k * kWoStage + kWoX) + 16 * q;
+            float4 d[4][3];   // every load in flight before the first shared store
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int yj = ((y0 - 1 + j) % H + H) % H;
+                const float4* row = reinterpret_cast<const float4*>(dY) + ((size_t)b * H + yj) * W;
+#pragma unroll
+                for (int kx = 0; kx < 3; ++kx) d[j][kx] = __ldg(row + wrapi(x0 + q - kx + 1, W));
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int kx = 0; kx < 3; ++kx) {
+                    const float4 e = d[j][kx];
+                    const __nv_bfloat162 h01 = __floats2bfloat162_rn(e.x, e.y), h23 = __floats2bfloat162_rn(e.z, e.w);
+                    const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+                    const __nv_bfloat162 l01 = __floats2bfloat162_rn(e.x - f01.x, e.y - f01.y);
+                    const __nv_bfloat162 l23 = __floats2bfloat162_rn(e.z - f23.x, e.w - f23.y);
+                    const int n = 12 * j + 4 * kx;   // hi at n, lo at 48 + n
+                    const uint32_t dh = sB + (uint32_t)((n >> 3) * kWgPlaneG + 2 * (n & 7));
+                    const uint32_t dl = sB + (uint32_t)(((48 + n) >> 3) * kWgPlaneG + 2 * ((48 + n) & 7));
+                    asm volatile("st.shared.v2.u32 [%0], {%1, %2};\n" ::"r"(dh),
+                                 "r"(*reinterpret_cast<const uint32_t*>(&h01)),
+                                 "r"(*reinterpret_cast<const uint32_t*>(&h23))
+                                 : "memory");
+                    asm volatile("st.shared.v2.u32 [%0], {%1, %2};\n" ::"r"(dl),
+                                 "r"(*reinterpret_cast<const uint32_t*>(&l01)),
+                                 "r"(*reinterpret_cast<const uint32_t*>(&l23))
+                                 : "memory");
+                    if (kx == 1 && (j == 1 || (j == 2 && y0 + 1 < H))) {   // the tile's own dY rows, once each
+                        bacc[0] += e.x;
+                        bacc[1] += e.y;
+                        bacc[2] += e.z;
+                        bacc[3] += e.w;
+                    }
+                }
+            fence_async_smem();
+            bar_arrive(bar_b0 + 8 * k);
+        }
+    }
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    // red[tap][ci][co] (the stages are free: every MMA is done), redb[q][co]
+    float* red = reinterpret_cast<float*>(base);
+    float* redb = red + 9 * kC * 4;
+    const bool ok = !*abortp && ntl > 0;
+    uint32_t v[96];
+    if (warp >= 2) {
+        const int L = 32 * (warp & 3) + lane;   // TMEM lane: row r = L / 64, channel ci = L mod 64
+        const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+        PLBM_TMEM_LD32(v, 0, taddr);
+        PLBM_TMEM_LD32(v, 32, taddr + 32);
+        PLBM_TMEM_LD32(v, 64, taddr + 64);
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        if (L < 64 && ok)   // row y0: tap ky = 2 - j
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int n = 0; n < 12; ++n)
+                    red[((2 - j) * 3 + n / 4) * kC * 4 + L * 4 + (n & 3)] =
+                        __uint_as_float(v[12 * j + n]) + __uint_as_float(v[48 + 12 * j + n]);
+        const int qq = tid - 64;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) redb[qq * 4 + c] = bacc[c];
+    }
+    __syncthreads();
+    if (warp >= 2 && ok) {
+        const int L = 32 * (warp & 3) + lane;
+        if (L >= 64) {   // row y0 + 1: tap ky = 3 - j, added to row y0's part
+            const int ci = L - 64;
+            float* out = partial + (size_t)blockIdx.x * 9 * kC * 4;
+#pragma unroll
+            for (int j = 1; j < 4; ++j)
+#pragma unroll
+                for (int n = 0; n < 12; ++n) {
+                    const int i = ((3 - j) * 3 + n / 4) * kC * 4 + ci * 4 + (n & 3);
+                    out[i] = red[i] + (__uint_as_float(v[12 * j + n]) + __uint_as_float(v[48 + 12 * j + n]));
+                }
+        }
+        if (tid - 64 < 4) {
+            const int c = tid - 64;
+            float sum = 0.0f;
+            for (int i = 0; i < 128; ++i) sum += redb[i * 4 + c];
+            partial_b[(size_t)blockIdx.x * 4 + c] = sum;
+        }
+    }
+    tc_before_sync();
+    __syncthreads();
+    if (tid == 0 && *abortp) atomicOr(err.flag, 1u);
+    if (warp == 0) {
+        tc_after_sync();
+        tmem_free(tmem, kWoTmemCols);
+    }
+}
+
 }  // namespace tc
 
 static int tc_sms() {
@@ -1625,6 +1857,31 @@ cudaError_t cnn_weights_out16(const float* W, void* Wo, cudaStream_t s) {
 cudaError_t cnn_weights_in(const float* W, void* Win, cudaStream_t s) {
     tc::k_weights_in<<<(tc::kInPlanes * 64 * 8 + 255) / 256, 256, 0, s>>>(W, static_cast<__nv_bfloat16*>(Win));
     return cudaGetLastError();
+}
+
+
+cudaError_t cnn_conv_out_wgrad_tc(int B, int H, int W, const void* X, const float* dY, float* partial,
+                                  float* partial_b, float* dW, float* db, TcErr err, cudaStream_t s) {
+    if (W % tc::kTile || H < 1 || B < 1) return cudaErrorInvalidValue;
+    if (reinterpret_cast<uintptr_t>(dY) % 16) return cudaErrorMisalignedAddress;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e =
+            cudaFuncSetAttribute(tc::k_wgrad_out_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kWoSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    CUtensorMap mapX;
+    cudaError_t em = encode_act_map(&mapX, X, B, H, W);
+    if (em != cudaSuccess) return em;
+    const int ntiles = B * ((H + 1) / 2) * (W / tc::kTile);
+    const int grid = ntiles < tc_sms() ? ntiles : tc_sms();   // within the partial buffers (one part per SM)
+    tc::k_wgrad_out_tc<<<grid, tc::kWoThreads, tc::kWoSmem, s>>>(B, H, W, mapX, dY, partial, partial_b, err);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = cnn_sum_partials(partial, grid, 9 * tc::kC * 4, dW, s);
+    if (e != cudaSuccess) return e;
+    return cnn_sum_partials(partial_b, grid, 4, db, s);
 }
 
 }  // namespace plbm

@@ -143,6 +143,10 @@ cudaError_t cnn_conv64_wgrad_tc(int B, int H, int W, const void* X, const void* 
 cudaError_t cnn_sum_partials(const float* partial, int nparts, int n, float* out, cudaStream_t s);
 cudaError_t cnn_conv_in_wgrad_tc(int B, int H, int W, const void* X, const void* dY, float* partial, float* partial_b,
                                  float* dW, float* db, TcErr err, cudaStream_t s);
+// Output-layer (64 -> 4) weight and bias gradients on tcgen05 from the bf16 activations X and the FP32
+// upstream gradient dY ([B][H][W][4], 16-byte aligned).
+cudaError_t cnn_conv_out_wgrad_tc(int B, int H, int W, const void* X, const float* dY, float* partial,
+                                  float* partial_b, float* dW, float* db, TcErr err, cudaStream_t s);
 cudaError_t cnn_conv_thin_fwd(int ci, int co, int ti, int to, int B, int H, int W, const void* X, const float* Wf,
                               const float* bias, const void* mask, void* Y, int mode, int relu, cudaStream_t s);
 int cnn_thin_parts(int B, int H, int W, int* pix_per_block);

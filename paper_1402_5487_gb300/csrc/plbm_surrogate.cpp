@@ -190,8 +190,12 @@ plbm_status forward(Sur* s, int B, const void* x) {
 plbm_status backward(Sur* s, int B, const void* x, const float* dout) {
     const int H = s->H, W = s->W;
     // last layer (64 -> 4): weights, then dZ_5 = (conv^T dout) * (A_5 > 0)
-    SCK(plbm::cnn_conv_thin_wgrad(64, 4, 0, 1, B, H, W, s->act[4], dout, s->part, s->part_b, s->g + s->woff[5],
-                                  s->g + s->boff[5], s->stream));
+    if (s->use_tc && reinterpret_cast<uintptr_t>(dout) % 16 == 0)
+        SCK(plbm::cnn_conv_out_wgrad_tc(B, H, W, s->act[4], dout, s->part, s->part_b, s->g + s->woff[5],
+                                        s->g + s->boff[5], plbm::TcErr{s->derr, s->wait_ns}, s->stream));
+    else
+        SCK(plbm::cnn_conv_thin_wgrad(64, 4, 0, 1, B, H, W, s->act[4], dout, s->part, s->part_b, s->g + s->woff[5],
+                                      s->g + s->boff[5], s->stream));
     if (s->use_tc) {   // tcgen05, on the bf16-rounded upstream gradient (the other layers' gradients are bf16 too)
         SCK(plbm::cnn_to_bf16(dout, (long long)B * H * W * 4, s->dout16, s->stream));
         SCK(plbm::cnn_conv_in_tc(B, H, W, s->dout16, s->win6, nullptr, s->act[4], s->dz[4], 1, 0,
@@ -481,7 +485,7 @@ plbm_status plbm_sur_train_step(plbm_surrogate h, int B, const void* x, const fl
     plbm_status r = forward(s, B, x);
     if (r != PLBM_OK) return r;
     const long long n = (long long)B * s->H * s->W * 4;
-    const int parts = 256;
+    const int parts = 1024;   // the loss partials (loss_part[0 .. 1023])
     SCK(plbm::cnn_mse(static_cast<const float*>(s->act[5]), target, n, (long long)s->H * s->W, s->mean_penalty,
                       s->loss_part + 1024, s->dout, s->loss_part, parts, s->stream));
     r = backward(s, B, x, s->dout);
