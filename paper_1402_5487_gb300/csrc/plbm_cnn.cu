@@ -332,12 +332,23 @@ k_conv64_wgrad(ConvShape S, const __nv_bfloat16* __restrict__ X, const __nv_bflo
 
 // out[j] = sum_c partial[c * n + j] in a fixed order: block = 32 consecutive j;
 // warp w sums the parts c of its contiguous eighth (in order, four loads in
-// flight), and lane j adds the eight warps' sums in warp order.
+// flight), and lane j adds the eight warps' sums in warp order.  The blocks past
+// the first (n + 31) / 32 do the same for a second array (partial2, n2, out2),
+// so that a weight gradient and its bias gradient take one launch.
 __global__ void __launch_bounds__(256) k_sum_partials(const float* __restrict__ partial, int nparts, int n,
-                                                      float* __restrict__ out) {
+                                                      float* __restrict__ out, const float* __restrict__ partial2,
+                                                      int n2, float* __restrict__ out2) {
     __shared__ float sh[8][33];
+    int blk = blockIdx.x;
+    const int nb1 = (n + 31) / 32;
+    if (blk >= nb1) {
+        partial = partial2;
+        n = n2;
+        out = out2;
+        blk -= nb1;
+    }
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int j = blockIdx.x * 32 + lane;
+    const int j = blk * 32 + lane;
     const int per = (nparts + 7) / 8;
     const int c0 = w * per, c1 = min(nparts, c0 + per);
     float s = 0.0f;
@@ -704,21 +715,7 @@ k_thin_wgrad_64x4(ConvShape S, const __nv_bfloat16* __restrict__ X, const float*
             ((redb[threadIdx.x] + redb[4 + threadIdx.x]) + redb[8 + threadIdx.x]) + redb[12 + threadIdx.x];
 }
 
-// Backward-data weights of a 64 -> 64 layer: Wb[tap'][co][ci] = W[8 - tap'][ci][co] (bf16).
-__global__ void k_flip64(const __nv_bfloat16* __restrict__ W, __nv_bfloat16* __restrict__ Wb) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= 9 * kC * kC) return;
-    const int ci = i % kC, co = (i / kC) % kC, tap = i / (kC * kC);
-    Wb[i] = W[((8 - tap) * kC + ci) * kC + co];
-}
 
-// Backward-data weights of a thin layer (fp32): Wb[tap'][co][ci] = W[8 - tap'][ci][co].
-__global__ void k_flip_thin(const float* __restrict__ W, int CI, int CO, float* __restrict__ Wb) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= 9 * CI * CO) return;
-    const int ci = i % CI, co = (i / CI) % CO, tap = i / (CI * CO);
-    Wb[i] = W[((8 - tap) * CI + ci) * CO + co];
-}
 
 // Per-sample, per-channel mean error m[b][c] = mean over the npix pixels of
 // pred - target (NHWC [B][npix][4]); one block per sample.
@@ -771,7 +768,7 @@ __global__ void k_mse(const float* __restrict__ pred, const float* __restrict__ 
 // and grad; per element the same arithmetic as k_mse.
 __global__ void k_mse4(const float4* __restrict__ pred, const float4* __restrict__ target, long long n,
                        long long npix, const float4* __restrict__ m, float lam, float4* __restrict__ grad,
-                       float* __restrict__ partial) {
+                       uint2* __restrict__ grad16, float* __restrict__ partial) {
     __shared__ float sh[256];
     float s = 0.0f;
     const long long n4 = n / 4;
@@ -784,8 +781,13 @@ __global__ void k_mse4(const float4* __restrict__ pred, const float4* __restrict
             const float4 mm = m[i / npix];
             dm = make_float4(lam * mm.x, lam * mm.y, lam * mm.z, lam * mm.w);
         }
-        grad[i] = make_float4(2.0f * (d.x + dm.x) / fn, 2.0f * (d.y + dm.y) / fn, 2.0f * (d.z + dm.z) / fn,
-                              2.0f * (d.w + dm.w) / fn);
+        const float4 g = make_float4(2.0f * (d.x + dm.x) / fn, 2.0f * (d.y + dm.y) / fn, 2.0f * (d.z + dm.z) / fn,
+                                     2.0f * (d.w + dm.w) / fn);
+        grad[i] = g;
+        if (grad16) {   // the same gradient in bf16 (round to nearest), for the tensor-core backward pass
+            const __nv_bfloat162 a = __floats2bfloat162_rn(g.x, g.y), b = __floats2bfloat162_rn(g.z, g.w);
+            grad16[i] = make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
+        }
         s += d.x * d.x;
         s += d.y * d.y;
         s += d.z * d.z;
@@ -819,10 +821,6 @@ __global__ void k_f32_to_bf16(const float* __restrict__ a, long long n, __nv_bfl
     if (i < n) b[i] = __float2bfloat16_rn(a[i]);
 }
 
-__global__ void k_bf16_round_f32(const float* __restrict__ a, long long n, float* __restrict__ b) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) b[i] = __bfloat162float(__float2bfloat16_rn(a[i]));
-}
 
 }  // namespace cnn
 
@@ -865,7 +863,13 @@ int cnn_wgrad64_parts(int B, int H, int W) {
 }
 
 cudaError_t cnn_sum_partials(const float* partial, int nparts, int n, float* out, cudaStream_t s) {
-    cnn::k_sum_partials<<<(n + 31) / 32, 256, 0, s>>>(partial, nparts, n, out);
+    cnn::k_sum_partials<<<(n + 31) / 32, 256, 0, s>>>(partial, nparts, n, out, nullptr, 0, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t cnn_sum_partials2(const float* partial, int n, float* out, const float* partial2, int n2, float* out2,
+                              int nparts, cudaStream_t s) {
+    cnn::k_sum_partials<<<(n + 31) / 32 + (n2 + 31) / 32, 256, 0, s>>>(partial, nparts, n, out, partial2, n2, out2);
     return cudaGetLastError();
 }
 
@@ -884,9 +888,7 @@ cudaError_t cnn_conv64_wgrad(int B, int H, int W, const void* X, const void* dY,
         cnn::ConvShape{B, H, W}, static_cast<const __nv_bfloat16*>(X), static_cast<const __nv_bfloat16*>(dY), partial,
         partial_b);
     const int n = 9 * cnn::kC * cnn::kC;
-    cnn::k_sum_partials<<<(n + 31) / 32, 256, 0, s>>>(partial, grid, n, dW);
-    cnn::k_sum_partials<<<(cnn::kC + 31) / 32, 256, 0, s>>>(partial_b, grid, cnn::kC, db);
-    return cudaGetLastError();
+    return cnn_sum_partials2(partial, n, dW, partial_b, cnn::kC, db, grid, s);
 }
 
 // Thin layer dispatch: (ci, co, ti, to) with ti/to 0 = bf16, 1 = fp32.
@@ -959,38 +961,31 @@ cudaError_t cnn_conv_thin_wgrad(int ci, int co, int tx, int tg, int B, int H, in
         return cudaErrorInvalidValue;
     }
     const int n = 9 * ci * co;
-    cnn::k_sum_partials<<<(n + 31) / 32, 256, 0, s>>>(partial, parts, n, dW);
-    cnn::k_sum_partials<<<(co + 31) / 32, 256, 0, s>>>(partial_b, parts, co, db);
-    return cudaGetLastError();
+    return cnn_sum_partials2(partial, n, dW, partial_b, co, db, parts, s);
 }
 
-cudaError_t cnn_flip64(const void* W, void* Wb, cudaStream_t s) {
-    cnn::k_flip64<<<(9 * 64 * 64 + 255) / 256, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(W),
-                                                            static_cast<__nv_bfloat16*>(Wb));
-    return cudaGetLastError();
-}
 
-cudaError_t cnn_flip_thin(const float* W, int ci, int co, float* Wb, cudaStream_t s) {
-    cnn::k_flip_thin<<<(9 * ci * co + 255) / 256, 256, 0, s>>>(W, ci, co, Wb);
-    return cudaGetLastError();
-}
 
 cudaError_t cnn_mse(const float* pred, const float* target, long long n, long long npix, float lam, float* merr,
-                    float* grad, float* partial, int parts, cudaStream_t s) {
+                    float* grad, void* grad16, float* partial, int parts, cudaStream_t s) {
     if (lam != 0.0f) {
         cnn::k_mean_err<<<(int)(n / (npix * 4)), 256, 0, s>>>(pred, target, npix, merr);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     const bool vec = n % 4 == 0 && (reinterpret_cast<uintptr_t>(pred) | reinterpret_cast<uintptr_t>(target) |
-                                    reinterpret_cast<uintptr_t>(grad) | reinterpret_cast<uintptr_t>(merr)) % 16 == 0;
-    if (vec)
+                                    reinterpret_cast<uintptr_t>(grad) | reinterpret_cast<uintptr_t>(merr)) % 16 == 0 &&
+                     reinterpret_cast<uintptr_t>(grad16) % 8 == 0;
+    if (vec) {
         cnn::k_mse4<<<parts, 256, 0, s>>>(reinterpret_cast<const float4*>(pred), reinterpret_cast<const float4*>(target),
                                           n, npix, lam != 0.0f ? reinterpret_cast<const float4*>(merr) : nullptr, lam,
-                                          reinterpret_cast<float4*>(grad), partial);
-    else
-        cnn::k_mse<<<parts, 256, 0, s>>>(pred, target, n, npix, lam != 0.0f ? merr : nullptr, lam, grad, partial);
-    return cudaGetLastError();
+                                          reinterpret_cast<float4*>(grad), static_cast<uint2*>(grad16), partial);
+        return cudaGetLastError();
+    }
+    cnn::k_mse<<<parts, 256, 0, s>>>(pred, target, n, npix, lam != 0.0f ? merr : nullptr, lam, grad, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !grad16) return e;
+    return cnn_to_bf16(grad, n, grad16, s);
 }
 
 cudaError_t cnn_adam(float* p, const float* g, float* m, float* v, long long n, float lr, float b1, float b2, float eps,
@@ -1005,9 +1000,5 @@ cudaError_t cnn_to_bf16(const float* a, long long n, void* b, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t cnn_bf16_round(const float* a, long long n, float* b, cudaStream_t s) {
-    cnn::k_bf16_round_f32<<<(int)((n + 255) / 256), 256, 0, s>>>(a, n, b);
-    return cudaGetLastError();
-}
 
 }  // namespace plbm

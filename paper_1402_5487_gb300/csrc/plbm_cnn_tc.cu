@@ -1416,36 +1416,8 @@ k_wgrad_in_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __
     }
 }
 
-// ---------------------------------------------------------------------------
-// Weight layouts for the kernels above, from W[tap][ci][co].
-// ---------------------------------------------------------------------------
-// 64 -> 64: forward Wf[tap][co][ci] = W[tap][ci][co]; backward data Wb[tap][ci][co] = W[8 - tap][ci][co].
-__global__ void k_weights_kmajor(const __nv_bfloat16* __restrict__ W, __nv_bfloat16* __restrict__ Wf,
-                                 __nv_bfloat16* __restrict__ Wb) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= 9 * kC * kC) return;
-    const int co = i % kC, ci = (i / kC) % kC, tap = i / (kC * kC);
-    const __nv_bfloat16 w = W[i];
-    Wf[(tap * kC + co) * kC + ci] = w;
-    Wb[((8 - tap) * kC + ci) * kC + co] = w;
-}
 
-// 64 -> 4 output layer (fp32 W[9][64][4]): Wo[tap][n][ci], n < 16, zero for n >= 4.
-__global__ void k_weights_out16(const float* __restrict__ W, __nv_bfloat16* __restrict__ Wo) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= 9 * 16 * kC) return;
-    const int ci = i % kC, n = (i / kC) % 16, tap = i / (16 * kC);
-    Wo[i] = __float2bfloat16_rn(n < 4 ? W[(tap * kC + ci) * 4 + n] : 0.0f);
-}
 
-// 4 -> 64 input layer (fp32 W[9][4][64]): Win[c][n][j] = W[tap][ci][n] for k = 8c + j = 4 tap + ci < 36.
-__global__ void k_weights_in(const float* __restrict__ W, __nv_bfloat16* __restrict__ Win) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= kInPlanes * kC * 8) return;
-    const int j = i % 8, n = (i / 8) % kC, c = i / (8 * kC);
-    const int k = 8 * c + j;
-    Win[i] = __float2bfloat16_rn(k < 36 ? W[((k >> 2) * 4 + (k & 3)) * kC + n] : 0.0f);
-}
 
 
 // ---------------------------------------------------------------------------
@@ -1676,6 +1648,74 @@ k_wgrad_out_tc(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, con
     }
 }
 
+
+// Every derived weight array of the surrogate from the FP32 master weights p in
+// one launch: pr = bf16-rounded p;
+// for the 64 -> 64 layers l = 1..4 the bf16 weights [tap][ci][co], their
+// backward-data form [8 - tap][co][ci] and the two K-major tensor-core layouts;
+// the output layer's backward-data weights w6flip[tap][co][ci] = pr[8 - tap][ci][co]
+// (FP32); and the tensor-core layouts of the input layer, of w6flip and of the
+// output layer.  One thread per output element.
+struct RefreshArgs {
+    const float* p;
+    long long np;
+    long long woff[6];
+    float* pr;
+    __nv_bfloat16* wbf;
+    __nv_bfloat16* wflip;
+    __nv_bfloat16* wtc;
+    float* w6flip;
+    __nv_bfloat16* win;
+    __nv_bfloat16* win6;
+    __nv_bfloat16* wout;
+};
+constexpr int kW64 = 9 * kC * kC;
+
+__global__ void k_refresh_weights(const RefreshArgs a) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const float* p = a.p;
+    if (i < a.np) {
+        a.pr[i] = __bfloat162float(__float2bfloat16_rn(p[i]));
+        return;
+    }
+    i -= a.np;
+    if (i < 4 * kW64) {   // source element (tap, ci, co) of layer l
+        const int l = (int)(i / kW64), e = (int)(i % kW64);
+        const int co = e % kC, ci = (e / kC) % kC, tap = e / (kC * kC);
+        const __nv_bfloat16 w = __float2bfloat16_rn(p[a.woff[l + 1] + e]);
+        a.wbf[(size_t)l * kW64 + e] = w;
+        a.wflip[(size_t)l * kW64 + ((8 - tap) * kC + co) * kC + ci] = w;
+        a.wtc[(size_t)(2 * l) * kW64 + (tap * kC + co) * kC + ci] = w;
+        a.wtc[(size_t)(2 * l + 1) * kW64 + ((8 - tap) * kC + ci) * kC + co] = w;
+        return;
+    }
+    i -= 4 * kW64;
+    const float* w5 = p + a.woff[5];
+    const float* w0 = p + a.woff[0];
+    auto r = [](float v) { return __bfloat162float(__float2bfloat16_rn(v)); };
+    if (i < 9 * 4 * kC) {   // w6flip[(tap * 4 + co) * 64 + ci]
+        const int ci = (int)i % kC, co = ((int)i / kC) % 4, tap = (int)i / (4 * kC);
+        a.w6flip[i] = r(w5[((8 - tap) * kC + ci) * 4 + co]);
+        return;
+    }
+    i -= 9 * 4 * kC;
+    if (i < 2 * kInPlanes * kC * 8) {   // win, then win6: [plane c][n][8], k = 8 c + j < 36
+        const bool six = i >= kInPlanes * kC * 8;
+        const int e = (int)(six ? i - kInPlanes * kC * 8 : i);
+        const int j = e % 8, n = (e / 8) % kC, c = e / (8 * kC);
+        const int k = 8 * c + j;
+        float v = 0.0f;
+        if (k < 36) v = six ? r(w5[((8 - (k >> 2)) * kC + n) * 4 + (k & 3)]) : r(w0[k * kC + n]);
+        (six ? a.win6 : a.win)[e] = __float2bfloat16_rn(v);
+        return;
+    }
+    i -= 2 * kInPlanes * kC * 8;
+    if (i < 9 * 16 * kC) {   // wout[tap][n][ci], n < 4
+        const int ci = (int)i % kC, n = ((int)i / kC) % 16, tap = (int)i / (16 * kC);
+        a.wout[i] = __float2bfloat16_rn(n < 4 ? w5[(tap * kC + ci) * 4 + n] : 0.0f);
+    }
+}
+
 }  // namespace tc
 
 static int tc_sms() {
@@ -1817,9 +1857,7 @@ cudaError_t cnn_conv64_wgrad_tc(int B, int H, int W, const void* X, const void* 
                                                              partial, partial_b, err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = cnn_sum_partials(partial, grid, 9 * tc::kC * tc::kC, dW, s);
-    if (e != cudaSuccess) return e;
-    return cnn_sum_partials(partial_b, grid, tc::kC, db, s);
+    return cnn_sum_partials2(partial, 9 * tc::kC * tc::kC, dW, partial_b, tc::kC, db, grid, s);
 }
 
 cudaError_t cnn_conv_in_wgrad_tc(int B, int H, int W, const void* X, const void* dY, float* partial, float* partial_b,
@@ -1838,26 +1876,11 @@ cudaError_t cnn_conv_in_wgrad_tc(int B, int H, int W, const void* X, const void*
                                                                 partial_b, err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = cnn_sum_partials(partial, grid, 9 * 4 * tc::kC, dW, s);
-    if (e != cudaSuccess) return e;
-    return cnn_sum_partials(partial_b, grid, tc::kC, db, s);
+    return cnn_sum_partials2(partial, 9 * 4 * tc::kC, dW, partial_b, tc::kC, db, grid, s);
 }
 
-cudaError_t cnn_weights_kmajor(const void* W, void* Wf, void* Wb, cudaStream_t s) {
-    tc::k_weights_kmajor<<<(9 * 64 * 64 + 255) / 256, 256, 0, s>>>(
-        static_cast<const __nv_bfloat16*>(W), static_cast<__nv_bfloat16*>(Wf), static_cast<__nv_bfloat16*>(Wb));
-    return cudaGetLastError();
-}
 
-cudaError_t cnn_weights_out16(const float* W, void* Wo, cudaStream_t s) {
-    tc::k_weights_out16<<<(9 * 16 * 64 + 255) / 256, 256, 0, s>>>(W, static_cast<__nv_bfloat16*>(Wo));
-    return cudaGetLastError();
-}
 
-cudaError_t cnn_weights_in(const float* W, void* Win, cudaStream_t s) {
-    tc::k_weights_in<<<(tc::kInPlanes * 64 * 8 + 255) / 256, 256, 0, s>>>(W, static_cast<__nv_bfloat16*>(Win));
-    return cudaGetLastError();
-}
 
 
 cudaError_t cnn_conv_out_wgrad_tc(int B, int H, int W, const void* X, const float* dY, float* partial,
@@ -1879,9 +1902,28 @@ cudaError_t cnn_conv_out_wgrad_tc(int B, int H, int W, const void* X, const floa
     tc::k_wgrad_out_tc<<<grid, tc::kWoThreads, tc::kWoSmem, s>>>(B, H, W, mapX, dY, partial, partial_b, err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = cnn_sum_partials(partial, grid, 9 * tc::kC * 4, dW, s);
-    if (e != cudaSuccess) return e;
-    return cnn_sum_partials(partial_b, grid, 4, db, s);
+    return cnn_sum_partials2(partial, 9 * tc::kC * 4, dW, partial_b, 4, db, grid, s);
+}
+
+
+cudaError_t cnn_refresh_weights(const float* p, long long np, const long long* woff, float* pr, void* wbf,
+                                void* wflip, void* wtc, float* w6flip, void* win, void* win6, void* wout,
+                                cudaStream_t s) {
+    tc::RefreshArgs a;
+    a.p = p;
+    a.np = np;
+    for (int l = 0; l < 6; ++l) a.woff[l] = woff[l];
+    a.pr = pr;
+    a.wbf = static_cast<__nv_bfloat16*>(wbf);
+    a.wflip = static_cast<__nv_bfloat16*>(wflip);
+    a.wtc = static_cast<__nv_bfloat16*>(wtc);
+    a.w6flip = w6flip;
+    a.win = static_cast<__nv_bfloat16*>(win);
+    a.win6 = static_cast<__nv_bfloat16*>(win6);
+    a.wout = static_cast<__nv_bfloat16*>(wout);
+    const long long n = np + 4LL * tc::kW64 + 9 * 4 * tc::kC + 2 * tc::kInPlanes * tc::kC * 8 + 9 * 16 * tc::kC;
+    tc::k_refresh_weights<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 }  // namespace plbm

@@ -141,8 +141,18 @@ cudaError_t cnn_conv64_wgrad(int B, int H, int W, const void* X, const void* dY,
 cudaError_t cnn_conv64_wgrad_tc(int B, int H, int W, const void* X, const void* dY, float* partial, float* partial_b,
                                 float* dW, float* db, TcErr err, cudaStream_t s);
 cudaError_t cnn_sum_partials(const float* partial, int nparts, int n, float* out, cudaStream_t s);
+// Two partial-sum reductions (a weight gradient and its bias gradient) in one launch.
+cudaError_t cnn_sum_partials2(const float* partial, int n, float* out, const float* partial2, int n2, float* out2,
+                              int nparts, cudaStream_t s);
 cudaError_t cnn_conv_in_wgrad_tc(int B, int H, int W, const void* X, const void* dY, float* partial, float* partial_b,
                                  float* dW, float* db, TcErr err, cudaStream_t s);
+// Every derived weight array of the surrogate from the FP32 master weights p (np
+// values, layer l's weights at woff[l], 6 layers) in one launch: pr (bf16-rounded
+// p), wbf / wflip (4 x 9*64*64 bf16), wtc (8 x 9*64*64 bf16), w6flip (FP32), and
+// the tensor-core layouts win, win6, wout.
+cudaError_t cnn_refresh_weights(const float* p, long long np, const long long* woff, float* pr, void* wbf,
+                                void* wflip, void* wtc, float* w6flip, void* win, void* win6, void* wout,
+                                cudaStream_t s);
 // Output-layer (64 -> 4) weight and bias gradients on tcgen05 from the bf16 activations X and the FP32
 // upstream gradient dY ([B][H][W][4], 16-byte aligned).
 cudaError_t cnn_conv_out_wgrad_tc(int B, int H, int W, const void* X, const float* dY, float* partial,
@@ -152,11 +162,8 @@ cudaError_t cnn_conv_thin_fwd(int ci, int co, int ti, int to, int B, int H, int 
 int cnn_thin_parts(int B, int H, int W, int* pix_per_block);
 cudaError_t cnn_conv_thin_wgrad(int ci, int co, int tx, int tg, int B, int H, int W, const void* X, const void* dY,
                                 float* partial, float* partial_b, float* dW, float* db, cudaStream_t s);
-cudaError_t cnn_flip64(const void* W, void* Wb, cudaStream_t s);
-cudaError_t cnn_flip_thin(const float* W, int ci, int co, float* Wb, cudaStream_t s);
 cudaError_t cnn_conv64_tc(int B, int H, int W, const void* X, const void* Wk, const float* bias, const void* mask,
                           void* Y, int mode, int relu, TcErr err, cudaStream_t s);
-cudaError_t cnn_weights_kmajor(const void* W, void* Wf, void* Wb, cudaStream_t s);
 cudaError_t cnn_conv_out_tc(int B, int H, int W, const void* X, const void* Wo, const float* bias, float* Y,
                             TcErr err, cudaStream_t s);
 // mode 0: Y = relu?(conv(X) + bias) (the 4 -> 64 input layer); mode 1: Y = conv(X) *
@@ -164,14 +171,12 @@ cudaError_t cnn_conv_out_tc(int B, int H, int W, const void* X, const void* Wo, 
 // Win from the flipped weights).
 cudaError_t cnn_conv_in_tc(int B, int H, int W, const void* X, const void* Win, const float* bias, const void* mask,
                            void* Y, int mode, int relu, TcErr err, cudaStream_t s);
-cudaError_t cnn_weights_out16(const float* W, void* Wo, cudaStream_t s);
-cudaError_t cnn_weights_in(const float* W, void* Win, cudaStream_t s);
+// grad16 (optional): the gradient also in bf16.
 cudaError_t cnn_mse(const float* pred, const float* target, long long n, long long npix, float lam, float* merr,
-                    float* grad, float* partial, int parts, cudaStream_t s);
+                    float* grad, void* grad16, float* partial, int parts, cudaStream_t s);
 cudaError_t cnn_adam(float* p, const float* g, float* m, float* v, long long n, float lr, float b1, float b2, float eps,
                      int t, cudaStream_t s);
 cudaError_t cnn_to_bf16(const float* a, long long n, void* b, cudaStream_t s);
-cudaError_t cnn_bf16_round(const float* a, long long n, float* b, cudaStream_t s);
 cudaError_t ce_pack_fields(const double* rho, const double* ux, const double* uy, const double* th, long long n,
                            float* out, cudaStream_t s);
 cudaError_t ce_assemble(const float* snaps, long long npix, const int* pairs, int B, const float* mean_in,

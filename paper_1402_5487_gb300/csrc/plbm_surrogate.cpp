@@ -141,18 +141,8 @@ void* wtc_bwd(Sur* s, int l) { return static_cast<char*>(s->wtc) + (size_t)(2 * 
 
 // Rounded copies, bf16 weights and backward-data weights from the FP32 master weights.
 plbm_status refresh_weights(Sur* s) {
-    SCK(plbm::cnn_bf16_round(s->p, s->nparams, s->pr, s->stream));
-    for (int l = 1; l <= 4; ++l) {
-        char* wb = static_cast<char*>(s->wbf) + (size_t)(l - 1) * 9 * 64 * 64 * 2;
-        char* wf = static_cast<char*>(s->wflip) + (size_t)(l - 1) * 9 * 64 * 64 * 2;
-        SCK(plbm::cnn_to_bf16(s->p + s->woff[l], 9LL * 64 * 64, wb, s->stream));
-        SCK(plbm::cnn_flip64(wb, wf, s->stream));
-        SCK(plbm::cnn_weights_kmajor(wb, wtc_fwd(s, l), wtc_bwd(s, l), s->stream));
-    }
-    SCK(plbm::cnn_flip_thin(s->pr + s->woff[5], 64, 4, s->w6flip, s->stream));
-    SCK(plbm::cnn_weights_in(s->pr + s->woff[0], s->win, s->stream));
-    SCK(plbm::cnn_weights_in(s->w6flip, s->win6, s->stream));
-    SCK(plbm::cnn_weights_out16(s->pr + s->woff[5], s->wout, s->stream));
+    SCK(plbm::cnn_refresh_weights(s->p, s->nparams, s->woff, s->pr, s->wbf, s->wflip, s->wtc, s->w6flip, s->win,
+                                  s->win6, s->wout, s->stream));
     return PLBM_OK;
 }
 
@@ -187,7 +177,8 @@ plbm_status forward(Sur* s, int B, const void* x) {
 
 // Gradients of every parameter into s->g for the upstream gradient dout of the
 // output.  dz[k] keeps dL/dZ of layer k + 1 (Z = convolution output before ReLU).
-plbm_status backward(Sur* s, int B, const void* x, const float* dout) {
+// dout16_ready: s->dout16 already holds dout in bf16 (written with the loss).
+plbm_status backward(Sur* s, int B, const void* x, const float* dout, bool dout16_ready = false) {
     const int H = s->H, W = s->W;
     // last layer (64 -> 4): weights, then dZ_5 = (conv^T dout) * (A_5 > 0)
     if (s->use_tc && reinterpret_cast<uintptr_t>(dout) % 16 == 0)
@@ -197,7 +188,7 @@ plbm_status backward(Sur* s, int B, const void* x, const float* dout) {
         SCK(plbm::cnn_conv_thin_wgrad(64, 4, 0, 1, B, H, W, s->act[4], dout, s->part, s->part_b, s->g + s->woff[5],
                                       s->g + s->boff[5], s->stream));
     if (s->use_tc) {   // tcgen05, on the bf16-rounded upstream gradient (the other layers' gradients are bf16 too)
-        SCK(plbm::cnn_to_bf16(dout, (long long)B * H * W * 4, s->dout16, s->stream));
+        if (!dout16_ready) SCK(plbm::cnn_to_bf16(dout, (long long)B * H * W * 4, s->dout16, s->stream));
         SCK(plbm::cnn_conv_in_tc(B, H, W, s->dout16, s->win6, nullptr, s->act[4], s->dz[4], 1, 0,
                                  plbm::TcErr{s->derr, s->wait_ns}, s->stream));
     } else {
@@ -487,8 +478,8 @@ plbm_status plbm_sur_train_step(plbm_surrogate h, int B, const void* x, const fl
     const long long n = (long long)B * s->H * s->W * 4;
     const int parts = 1024;   // the loss partials (loss_part[0 .. 1023])
     SCK(plbm::cnn_mse(static_cast<const float*>(s->act[5]), target, n, (long long)s->H * s->W, s->mean_penalty,
-                      s->loss_part + 1024, s->dout, s->loss_part, parts, s->stream));
-    r = backward(s, B, x, s->dout);
+                      s->loss_part + 1024, s->dout, s->use_tc ? s->dout16 : nullptr, s->loss_part, parts, s->stream));
+    r = backward(s, B, x, s->dout, s->use_tc);
     if (r != PLBM_OK) return r;
     ++s->adam_t;
     SCK(plbm::cnn_adam(s->p, s->g, s->m, s->v, s->nparams, lr, 0.9f, 0.999f, 1e-8f, s->adam_t, s->stream));
