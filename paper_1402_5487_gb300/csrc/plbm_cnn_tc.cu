@@ -969,14 +969,12 @@ k_conv_in_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __n
 // kWrD slots.  The CTA writes its partial sums partial[cta][tap][ci][co],
 // partial_b[cta][co] at the end.
 // ---------------------------------------------------------------------------
-constexpr int kWgThreads = 256;   // k_wgrad_in_tc
 constexpr int kWgRowPix = kTile + 2;
 // X planes 17 lines apart, pixel 0 of a plane 112 bytes into a line, so that pixel
 // 1 (x0), the destination of the TMA box, is 128-byte aligned
 constexpr int kWgPlaneX = 17 * 128;             // 2176 >= 130 pixels x 16 bytes
 constexpr int kWgXOff = 112;
 constexpr int kWgPlaneG = kTile * 16;           // 2048
-constexpr int kWgStages = 3;                    // k_wgrad_in_tc: two tiles being copied while one multiplies
 constexpr int kWrR = 7;                         // input row slots
 constexpr int kWrD = 4;                         // dY row slots
 constexpr int kWrSlot = 8 * kWgPlaneX;          // 17408: one input row, 8 chunk planes
@@ -1258,135 +1256,185 @@ k_wgrad_tc(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const _
 // ---------------------------------------------------------------------------
 // 4 -> 64 input-layer weight gradient: dW[tap][ci][co] = sum over pixels of
 // X[pixel shifted by the tap][ci] dY[pixel][co].  M = (tap, ci) = 36 rows, padded
-// to 128: per tile the 9 taps x 4 channels of each pixel are gathered (8-byte
-// cp.async per tap) into chunk planes 0..4 (row m = 4 tap + ci in plane m / 8),
-// planes 5..15 stay zero; dY as in k_wgrad_tc.  One MMA of 128 x 64 x 16 per 16
-// pixels into one accumulator summed over the CTA's tiles; three stages.
-// Partials per CTA: partial[cta][tap][ci][co], partial_b[cta][co].
+// to 128: per tile the 9 taps x 4 channels of each pixel are gathered into chunk
+// planes 0..4 (row m = 4 tap + ci in plane m / 8; planes 5..15 and the upper half
+// of plane 4 stay zero); dY (B: K = pixels, N = 64) arrives by TMA in the
+// chunk-planar layout.  One MMA of 128 x 64 x 16 per 16 pixels into one
+// accumulator summed over the CTA's tiles.  Warps: 0 issues the MMAs (lane 0),
+// 1 issues the dY copies, 2..5 gather A (one pixel a thread) and then sum the
+// stage's dY for db (warp w: planes 2 (w - 2), 2 (w - 2) + 1).  Barriers per
+// stage k: xfull (dY landed), afull (A gathered), done (MMAs done), bias (dY
+// summed).  Partials per CTA: partial[cta][tap][ci][co], partial_b[cta][co].
 // ---------------------------------------------------------------------------
+constexpr int kWiThreads = 192;
+constexpr int kWiStages = 4;
 constexpr int kWiA = 16 * kWgPlaneG;              // 32 KB: 16 planes of 128 pixels x 16 bytes
 constexpr int kWiStage = kWiA + 8 * kWgPlaneG;    // + dY
-constexpr int kWiSmem = 128 + kWgStages * kWiStage + 64 + 256 * 4;
+constexpr int kWiBars = kWiStages * kWiStage;
+constexpr int kWiSmem = 128 + kWiBars + 256 + 64 * 4;
 constexpr uint32_t kWiTmemCols = 64;
+static_assert(kWiSmem <= 232448, "input-layer weight-gradient stages");
 
-__global__ void __launch_bounds__(kWgThreads, 1)
-k_wgrad_in_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ dY,
+__global__ void __launch_bounds__(kWiThreads, 1)
+k_wgrad_in_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __grid_constant__ CUtensorMap tmG,
               float* __restrict__ partial, float* __restrict__ partial_b, const TcErr err) {
     extern __shared__ unsigned char dsm_raw[];
     const uint32_t raw = s2u(dsm_raw);
     const uint32_t pad = (128 - (raw & 127)) & 127;
     unsigned char* base = dsm_raw + pad;
     const uint32_t sbase = raw + pad;
-    unsigned char* bars_p = base + kWgStages * kWiStage;
-    const uint32_t bar0 = s2u(bars_p), bar_drain = bar0 + 8 * kWgStages;
-    volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(bars_p + 32);
-    volatile int* abortp = reinterpret_cast<volatile int*>(bars_p + 36);
-    float* red = reinterpret_cast<float*>(bars_p + 64);
+    unsigned char* bars_p = base + kWiBars;
+    // xfull[k] 8 k, afull[k] 32 + 8 k, done[k] 64 + 8 k, bias[k] 96 + 8 k, drain 128, TMEM slot 136, abort 140
+    const uint32_t bar_x0 = s2u(bars_p), bar_a0 = bar_x0 + 32, bar_d0 = bar_x0 + 64, bar_b0 = bar_x0 + 96;
+    const uint32_t bar_drain = bar_x0 + 128;
+    volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(bars_p + 136);
+    volatile int* abortp = reinterpret_cast<volatile int*>(bars_p + 140);
+    float* red = reinterpret_cast<float*>(bars_p + 256);   // 64 bias sums
+    static_assert(kWiStages == 4, "barrier layout");
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tiles_x = W / kTile;
     const int ntiles = B * H * tiles_x;
+    const int ntl = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     // zero the A planes of every stage once: the gathers write planes 0..4 only
     // (plane 4: the first 8 bytes of each pixel, tap 8)
-    for (int i = tid; i < kWgStages * kWiA / 16; i += kWgThreads) {
+    for (int i = tid; i < kWiStages * kWiA / 16; i += kWiThreads) {
         const int k = i / (kWiA / 16), j = i - k * (kWiA / 16);
         *reinterpret_cast<uint4*>(base + k * kWiStage + 16 * j) = make_uint4(0u, 0u, 0u, 0u);
     }
+    fence_async_smem();
     if (tid == 0) {
-        for (int k = 0; k < kWgStages; ++k) bar_init(bar0 + 8 * k, 1);
+        for (int k = 0; k < kWiStages; ++k) {
+            bar_init(bar_x0 + 8 * k, 1);
+            bar_init(bar_a0 + 8 * k, 128);
+            bar_init(bar_d0 + 8 * k, 1);
+            bar_init(bar_b0 + 8 * k, 128);
+        }
         bar_init(bar_drain, 1);
         *abortp = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    if (warp == 0) tmem_alloc(s2u(bars_p + 32), kWiTmemCols);
+    if (warp == 0) tmem_alloc(s2u(bars_p + 136), kWiTmemCols);
     tc_before_sync();
     __syncthreads();
     tc_after_sync();
     const uint32_t tmem = *tmem_slot;
+    float bsum[2][8];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int e = 0; e < 8; ++e) bsum[h][e] = 0.0f;
 
-    auto stage_in = [&](int t, int k) {
-        const int b = t / (H * tiles_x);
-        const int rem = t - b * H * tiles_x;
-        const int y = rem / tiles_x;
-        const int x0 = (rem - y * tiles_x) * kTile;
-        const uint32_t st = sbase + k * kWiStage;
-        for (int i = tid; i < kTile * 9; i += kWgThreads) {   // (pixel, tap): 4 channels = 8 bytes
-            const int p = i / 9, tap = i - 9 * p;
-            const int yy = wrapi(y + tap / 3 - 1, H), xx = wrapi(x0 + p + tap % 3 - 1, W);
-            const uint32_t dst = st + (tap >> 1) * kWgPlaneG + 16 * p + 8 * (tap & 1);
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst),
-                         "l"(X + (((size_t)b * H + yy) * W + xx) * 4)
-                         : "memory");
+    if (warp == 1) {
+        if (lane == 0) asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tmG)) : "memory");
+        int it = 0;
+        for (; it < ntl; ++it) {
+            const int k = it % kWiStages;
+            if (it >= kWiStages) {   // the stage's previous tile: MMAs done and dY summed
+                const uint32_t par = (uint32_t)(it / kWiStages - 1) & 1u;
+                if (!bar_wait(bar_d0 + 8 * k, par, abortp, err.wait_ns) ||
+                    !bar_wait(bar_b0 + 8 * k, par, abortp, err.wait_ns))
+                    break;
+            }
+            const int t = (int)blockIdx.x + it * (int)gridDim.x;
+            const int b = t / (H * tiles_x);
+            const int rem = t - b * H * tiles_x;
+            const int y = rem / tiles_x;
+            const int x0 = (rem - y * tiles_x) * kTile;
+            if (lane == 0) bar_arrive_expect_tx(bar_x0 + 8 * k, 8 * kWgPlaneG);
+            __syncwarp();
+            if (lane < 8)
+                tma_load_5d(sbase + (uint32_t)(k * kWiStage + kWiA + lane * kWgPlaneG), &tmG, 0, lane, x0, y, b,
+                            bar_x0 + 8 * k);
         }
-        for (int i = tid; i < kTile * 8; i += kWgThreads) {
-            const int c = i & 7, p = i >> 3;
-            cp_async16(st + kWiA + c * kWgPlaneG + 16 * p, dY + (((size_t)b * H + y) * W + x0 + p) * kC + 8 * c);
-        }
-    };
-
-    uint32_t phase = 0u;
-    int it = 0;
-    float bsum[8];
+        if (lane == 0 && *abortp)   // copies already issued land before the CTA exits
+            for (int k = 0; k < kWiStages; ++k) {
+                const int j = (it - 1) - (((it - 1) - k) % kWiStages + kWiStages) % kWiStages;
+                if (j >= 0) bar_wait_drain(bar_x0 + 8 * k, (uint32_t)(j / kWiStages) & 1u);
+            }
+    } else if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int it = 0; it < ntl; ++it) {
+                const int k = it % kWiStages;
+                const uint32_t par = (uint32_t)(it / kWiStages) & 1u;
+                if (!bar_spin(bar_a0 + 8 * k, par, abortp, err.wait_ns) ||
+                    !bar_spin(bar_x0 + 8 * k, par, abortp, err.wait_ns))
+                    break;
+                tc_after_sync();
+                const uint32_t sA = sbase + (uint32_t)(k * kWiStage), sG = sA + kWiA;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) bsum[i] = 0.0f;
-    for (int j = 0; j < kWgStages - 1; ++j) {
-        if ((int)blockIdx.x + j * (int)gridDim.x < ntiles) stage_in(blockIdx.x + j * gridDim.x, j);
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
-    }
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
-        const int k = it % kWgStages;
-        asm volatile("cp.async.wait_group %0;\n" ::"n"(kWgStages - 2) : "memory");
-        fence_async_smem();
-        __syncthreads();
-        if (*abortp) break;
-        const uint32_t sA = sbase + k * kWiStage, sG = sA + kWiA;
-        if (tid == 0) {
-            tc_after_sync();
-#pragma unroll 1
-            for (int ks = 0; ks < kTile / 16; ++ks)
-                mma_wg(tmem, desc_mn(sA + 16 * 16 * ks, kWgPlaneG), desc_mn(sG + 16 * 16 * ks, kWgPlaneG),
-                       (it > 0 || ks > 0) ? 1u : 0u);
-            tc_commit(bar0 + 8 * k);
-        }
-        const int kf = (it + kWgStages - 1) % kWgStages;
-        if (it >= 1) {
-            if (!bar_wait(bar0 + 8 * kf, (phase >> kf) & 1u, abortp, err.wait_ns)) *abortp = 1;
-            phase ^= 1u << kf;
-        }
-        const int tf = t + (kWgStages - 1) * (int)gridDim.x;
-        if (!*abortp && tf < ntiles) stage_in(tf, kf);
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
-        {
-            const unsigned char* g = base + k * kWiStage + kWiA + warp * kWgPlaneG;
-#pragma unroll
-            for (int j = 0; j < kTile / 32; ++j) {
-                const uint4 r = *reinterpret_cast<const uint4*>(g + 16 * (lane + 32 * j));
-                const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&r);
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float2 f = __bfloat1622float2(h[i]);
-                    bsum[2 * i] += f.x;
-                    bsum[2 * i + 1] += f.y;
-                }
+                for (int ks = 0; ks < kTile / 16; ++ks)
+                    mma_wg(tmem, desc_mn(sA + 16 * 16 * ks, kWgPlaneG), desc_mn(sG + 16 * 16 * ks, kWgPlaneG),
+                           (it > 0 || ks > 0) ? 1u : 0u);
+                tc_commit(bar_d0 + 8 * k);
+                ++issued;
+            }
+            if (issued > 0) {
+                tc_commit(bar_drain);
+                if (!bar_wait_drain(bar_drain, 0)) *abortp = 1;
             }
         }
-        __syncthreads();
+        __syncwarp();
+    } else {
+        const int q = tid - 64;       // gather: pixel q of the tile
+        const int pw = warp - 2;      // bias: dY planes 2 pw, 2 pw + 1
+        for (int it = 0; it < ntl; ++it) {
+            const int k = it % kWiStages;
+            if (it >= kWiStages &&
+                !bar_wait(bar_d0 + 8 * k, (uint32_t)(it / kWiStages - 1) & 1u, abortp, err.wait_ns))
+                break;
+            const int t = (int)blockIdx.x + it * (int)gridDim.x;
+            const int b = t / (H * tiles_x);
+            const int rem = t - b * H * tiles_x;
+            const int y = rem / tiles_x;
+            const int x0 = (rem - y * tiles_x) * kTile;
+            uint2 v[9];   // every load in flight before the first shared store
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap) {
+                const int yy = wrapi(y + tap / 3 - 1, H), xx = wrapi(x0 + q + tap % 3 - 1, W);
+                v[tap] = __ldg(reinterpret_cast<const uint2*>(X + (((size_t)b * H + yy) * W + xx) * 4));
+            }
+            const uint32_t st = sbase + (uint32_t)(k * kWiStage) + 16 * q;
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap)
+                asm volatile("st.shared.v2.u32 [%0], {%1, %2};\n" ::"r"(st + (tap >> 1) * kWgPlaneG + 8 * (tap & 1)),
+                             "r"(v[tap].x), "r"(v[tap].y)
+                             : "memory");
+            fence_async_smem();
+            bar_arrive(bar_a0 + 8 * k);
+            // bias: this stage's dY once it has landed
+            if (!bar_wait(bar_x0 + 8 * k, (uint32_t)(it / kWiStages) & 1u, abortp, err.wait_ns)) break;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const unsigned char* g = base + k * kWiStage + kWiA + (2 * pw + h) * kWgPlaneG;
+#pragma unroll
+                for (int j = 0; j < kTile / 32; ++j) {
+                    const uint4 r = *reinterpret_cast<const uint4*>(g + 16 * (lane + 32 * j));
+                    const __nv_bfloat162* hv = reinterpret_cast<const __nv_bfloat162*>(&r);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float2 f = __bfloat1622float2(hv[e]);
+                        bsum[h][2 * e] += f.x;
+                        bsum[h][2 * e + 1] += f.y;
+                    }
+                }
+            }
+            bar_arrive(bar_b0 + 8 * k);
+        }
     }
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    if (it > 0 && !*abortp) {
-        const int kl = (it - 1) % kWgStages;
-        if (!bar_wait(bar0 + 8 * kl, (phase >> kl) & 1u, abortp, err.wait_ns)) *abortp = 1;
-    }
+    tc_before_sync();
     __syncthreads();
     tc_after_sync();
-    if (!*abortp && it > 0 && warp < 2) {   // TMEM lanes 0..63 hold rows m = 4 tap + ci < 36
-        const int m = 32 * warp + lane;
+    const bool ok = !*abortp && ntl > 0;
+    if (warp >= 4) {   // TMEM lanes 0..63 (warps 4, 5) hold rows m = 4 tap + ci < 36
+        const int m = 32 * (warp - 4) + lane;
         uint32_t v[64];
-        const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
+        const uint32_t taddr = tmem + ((uint32_t)(32 * (warp - 4)) << 16);
         PLBM_TMEM_LD32(v, 0, taddr);
         PLBM_TMEM_LD32(v, 32, taddr + 32);
         asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-        if (m < 36) {
+        if (ok && m < 36) {
             float4* out = reinterpret_cast<float4*>(partial + ((size_t)blockIdx.x * 36 + m) * kC);
 #pragma unroll
             for (int c4 = 0; c4 < 16; ++c4)
@@ -1394,21 +1442,20 @@ k_wgrad_in_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __
                                       __uint_as_float(v[4 * c4 + 2]), __uint_as_float(v[4 * c4 + 3]));
         }
     }
+    if (warp >= 2) {   // per warp and lane: channels 8 (2 pw + h) + e
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        float v = bsum[i];
+        for (int h = 0; h < 2; ++h)
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) red[8 * warp + i] = v;
+            for (int e = 0; e < 8; ++e) {
+                float v = bsum[h][e];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) red[8 * (2 * (warp - 2) + h) + e] = v;
+            }
     }
     tc_before_sync();
     __syncthreads();
-    if (tid < kC) partial_b[(size_t)blockIdx.x * kC + tid] = red[tid];
-    if (tid == 0 && it > 0) {
-        tc_commit(bar_drain);
-        if (!bar_wait_drain(bar_drain, 0)) *abortp = 1;
-    }
-    __syncthreads();
+    if (ok && tid < kC) partial_b[(size_t)blockIdx.x * kC + tid] = red[tid];
     if (tid == 0 && *abortp) atomicOr(err.flag, 1u);
     if (warp == 0) {
         tc_after_sync();
@@ -1870,10 +1917,13 @@ cudaError_t cnn_conv_in_wgrad_tc(int B, int H, int W, const void* X, const void*
         if (e != cudaSuccess) return e;
         attr = true;
     }
+    if (reinterpret_cast<uintptr_t>(X) % 8) return cudaErrorMisalignedAddress;
+    CUtensorMap mapG;
+    cudaError_t em = encode_act_map(&mapG, dY, B, H, W);
+    if (em != cudaSuccess) return em;
     const int grid = cnn_wgrad64_parts(B, H, W);   // at most one CTA per SM: within the partial buffers
-    tc::k_wgrad_in_tc<<<grid, tc::kWgThreads, tc::kWiSmem, s>>>(B, H, W, static_cast<const __nv_bfloat16*>(X),
-                                                                static_cast<const __nv_bfloat16*>(dY), partial,
-                                                                partial_b, err);
+    tc::k_wgrad_in_tc<<<grid, tc::kWiThreads, tc::kWiSmem, s>>>(B, H, W, static_cast<const __nv_bfloat16*>(X), mapG,
+                                                                partial, partial_b, err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return cnn_sum_partials2(partial, 9 * 4 * tc::kC, dW, partial_b, tc::kC, db, grid, s);
