@@ -1157,20 +1157,22 @@ k_wgrad_tc(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const _
                 const int k = i % kWrD;
                 if (!ok || !bar_spin(bar_gfull0 + 8 * k, (uint32_t)(i / kWrD) & 1u, abortp, err.wait_ns)) break;
                 tc_after_sync();
-                // row pairs (y - 1, y) and (y, y + 1): fills F - 2, F - 1 and F - 1, F in adjacent slots
-                const uint32_t a0 = sX + (uint32_t)(((F - 2) % kWrR) * kWrSlot);
-                const uint32_t a1 = sX + (uint32_t)(((F - 1) % kWrR) * kWrSlot);
-                const uint32_t g = sG + (uint32_t)(k * 8 * kWgPlaneG);
-#pragma unroll 1
+                // row pairs (y - 1, y) and (y, y + 1): fills F - 2, F - 1 and F - 1, F in adjacent slots.
+                // The descriptors of one tile differ from these three by constants in the
+                // start-address field (byte offset / 16, no carry: shared addresses < 256 KB).
+                const uint64_t da0 = desc_mn(sX + (uint32_t)(((F - 2) % kWrR) * kWrSlot), kWgPlaneX);
+                const uint64_t da1 = desc_mn(sX + (uint32_t)(((F - 1) % kWrR) * kWrSlot), kWgPlaneX);
+                const uint64_t dg = desc_mn(sG + (uint32_t)(k * 8 * kWgPlaneG), kWgPlaneG);
+                const uint32_t acc0 = i > 0 ? 1u : 0u;
+#pragma unroll
                 for (int ks = 0; ks < kTile / 16; ++ks) {
-                    const uint64_t bd = desc_mn(g + 16 * 16 * ks, kWgPlaneG);
 #pragma unroll
                     for (int kx = 0; kx < 3; ++kx)
 #pragma unroll
                         for (int pr = 0; pr < 2; ++pr)
                             mma_wg(tmem + (uint32_t)((kx * 2 + pr) * 64),
-                                   desc_mn((pr ? a1 : a0) + 16 * (16 * ks + kx), kWgPlaneX), bd,
-                                   (i > 0 || ks > 0) ? 1u : 0u);
+                                   (pr ? da1 : da0) + (uint64_t)(16 * ks + kx), dg + (uint64_t)(16 * ks),
+                                   ks > 0 ? 1u : acc0);
                 }
                 tc_commit(bar_done0 + 8 * k);
                 ++issued;
