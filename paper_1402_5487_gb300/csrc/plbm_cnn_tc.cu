@@ -5,8 +5,10 @@
 // D[128 x N] = sum over 9 taps (ky, kx) and 4 K-steps of A[128 x 16] B[16 x N],
 // A = input pixels shifted by the tap, B = the tap's weights.
 //
-// k_conv_ring<N, MODE> (64 input channels: the 64 -> 64 layers and the 64 -> 4
-// output layer with N = 16, four columns used) is warp-specialised and
+// k_conv_ring<N, MODE, BITS> (64 input channels: the 64 -> 64 layers and the
+// 64 -> 4 output layer with N = 16, four columns used; BITS: a forward pass that
+// also records each pixel's ReLU bits, one uint64_t, for the backward pass, whose
+// MODE 1 reads them instead of the 128-byte activations) is warp-specialised and
 // pipelined:
 //   * the CTA's tile range is cut into two streams, each with its own warps,
 //     row slots, accumulators and staging tile (below, per stream);
@@ -42,9 +44,9 @@
 // x 4 channels) are gathered into one K = 48 row (zero padded) and three MMAs
 // make the tile.
 //
-// k_wgrad_tc and k_wgrad_in_tc are the weight gradients of the 64 -> 64 layers
-// and of the 4 -> 64 input layer: the reduction over pixels is the K dimension,
-// both operands MN-major.
+// k_wgrad_tc, k_wgrad_in_tc and k_wgrad_out_tc are the weight gradients of the
+// 64 -> 64 layers, the 4 -> 64 input layer and the 64 -> 4 output layer: the
+// reduction over pixels is the K dimension, both operands MN-major.
 //
 // Every wait is bounded by the global timer: on a timeout a kernel records it
 // in *err, stops issuing work, waits (bounded) for the MMAs it issued, frees
@@ -303,41 +305,16 @@ __device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uin
         : "r"(addr)                                                                                                 \
         : "memory")
 
-// 64 accumulator columns of this thread's TMEM lane -> bias/ReLU or mask -> 64 bf16 at dst.
-__device__ __forceinline__ void store64(const uint32_t (&v)[64], int mode, int relu, const float* __restrict__ bias,
-                                        const __nv_bfloat16* __restrict__ mask, __nv_bfloat16* __restrict__ dst) {
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {  // 8 channels per 16-byte store
-        float f[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) f[k] = __uint_as_float(v[8 * q + k]);
-        if (mode == 0) {
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                f[k] += bias[8 * q + k];
-                if (relu) f[k] = fmaxf(f[k], 0.0f);
-            }
-        } else {
-            const uint4 mk = *reinterpret_cast<const uint4*>(mask + 8 * q);
-            const __nv_bfloat16* m = reinterpret_cast<const __nv_bfloat16*>(&mk);
-#pragma unroll
-            for (int k = 0; k < 8; ++k) f[k] = __bfloat162float(m[k]) > 0.0f ? f[k] : 0.0f;
-        }
-        uint4 o;
-        __nv_bfloat162* ob = reinterpret_cast<__nv_bfloat162*>(&o);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) ob[k] = __floats2bfloat162_rn(f[2 * k], f[2 * k + 1]);
-        *reinterpret_cast<uint4*>(dst + 8 * q) = o;
-    }
-}
-
-// The same 64 outputs of pixel px into a shared tile of 128 pixels x 128 bytes in
-// the 128-byte swizzle of a TMA box (16-byte chunk q of pixel p at
-// p * 128 + (q ^ (p mod 8)) * 16): the 32 lanes of a warp store 512 bytes per
-// instruction without bank conflicts.  Mode 1 with no mask pointer reads the
-// pixel's mask from the tile itself (staged there beforehand) and overwrites it.
-__device__ __forceinline__ void stage64(const uint32_t (&v)[64], int mode, int relu, const float* __restrict__ bias,
-                                        const __nv_bfloat16* __restrict__ mask, uint32_t stage, int px) {
+// The 64 outputs of pixel px (its TMEM lane's 64 accumulator columns) into a
+// shared tile of 128 pixels x 128 bytes in the 128-byte swizzle of a TMA box
+// (16-byte chunk q of pixel p at p * 128 + (q ^ (p mod 8)) * 16): the 32 lanes
+// of a warp store 512 bytes per instruction without bank conflicts.  Mode 0:
+// relu?(acc + bias); with want_bits the return value holds the pixel's ReLU bits
+// (bit c: stored bf16 output c > 0, i.e. its bit pattern h has 1 <= h <= 0x7F80,
+// +inf included, NaN not).  Mode 1: acc where bit c of mbits is set, else 0.
+__device__ __forceinline__ uint64_t stage64(const uint32_t (&v)[64], int mode, int relu, const float* __restrict__ bias,
+                                            uint64_t mbits, bool want_bits, uint32_t stage, int px) {
+    uint32_t bits[2] = {0u, 0u};
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         float f[8];
@@ -349,35 +326,34 @@ __device__ __forceinline__ void stage64(const uint32_t (&v)[64], int mode, int r
                 f[k] += bias[8 * q + k];
                 if (relu) f[k] = fmaxf(f[k], 0.0f);
             }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) f[k] = (mbits >> (8 * q + k)) & 1u ? f[k] : 0.0f;
         }
         const uint32_t a = stage + (uint32_t)px * 128u + (uint32_t)((q ^ (px & 7)) * 16);
-        if (mode == 1) {
-            uint4 mk;
-            if (mask) {
-                mk = *reinterpret_cast<const uint4*>(mask + 8 * q);
-            } else {
-                asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];\n"
-                             : "=r"(mk.x), "=r"(mk.y), "=r"(mk.z), "=r"(mk.w)
-                             : "r"(a)
-                             : "memory");
-            }
-            const __nv_bfloat16* m = reinterpret_cast<const __nv_bfloat16*>(&mk);
+        uint32_t o[4];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) f[k] = __bfloat162float(m[k]) > 0.0f ? f[k] : 0.0f;
+        for (int k = 0; k < 4; ++k) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(f[2 * k], f[2 * k + 1]);
+            o[k] = *reinterpret_cast<const uint32_t*>(&h);
         }
-        uint4 o;
-        __nv_bfloat162* ob = reinterpret_cast<__nv_bfloat162*>(&o);
+        if (mode == 0 && want_bits) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) ob[k] = __floats2bfloat162_rn(f[2 * k], f[2 * k + 1]);
-        asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n" ::"r"(a), "r"(o.x), "r"(o.y), "r"(o.z), "r"(o.w)
+            for (int k = 0; k < 4; ++k) {
+                bits[q >> 2] |= (uint32_t)(((o[k] & 0xFFFFu) - 1u) < 0x7F80u) << (8 * (q & 3) + 2 * k);
+                bits[q >> 2] |= (uint32_t)(((o[k] >> 16) - 1u) < 0x7F80u) << (8 * (q & 3) + 2 * k + 1);
+            }
+        }
+        asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n" ::"r"(a), "r"(o[0]), "r"(o[1]), "r"(o[2]), "r"(o[3])
                      : "memory");
     }
+    return (uint64_t)bits[1] << 32 | bits[0];
 }
 
 // ---------------------------------------------------------------------------
 // Ring-staged convolution with 64 input channels.
 // MODE 0: Y bf16 [.][64] = relu?(conv + bias)    (N = 64)
-// MODE 1: Y bf16 [.][64] = conv * (mask > 0)     (N = 64, backward data)
+// MODE 1: Y bf16 [.][64] = conv * relu bit       (N = 64, backward data)
 // MODE 2: Y fp32 [.][4]  = conv + bias           (N = 16, output columns 0..3)
 // Wk: bf16 [9 taps][N][64], K-major.
 // ---------------------------------------------------------------------------
@@ -428,8 +404,7 @@ __device__ __forceinline__ uint32_t acc_slot(uint32_t u) { return (uint32_t)(kAc
 // empty barrier, per stream and accumulator a full and an empty barrier, per
 // issuer a drain barrier
 constexpr int kBarFull = 0, kBarEmpty = kRing, kBarTFull = 2 * kRing, kBarTEmpty = kBarTFull + kStreams * kAccS,
-              kBarDrain = kBarTEmpty + kStreams * kAccS, kBarMask = kBarDrain + kIssuers,
-              kBarCount = kBarMask + kStreams;
+              kBarDrain = kBarTEmpty + kStreams * kAccS, kBarCount = kBarDrain + kIssuers;
 static_assert(kBarCount * 8 + 16 <= 512, "barrier area below the biases");
 
 // Tiles t = ((b * tiles_x + xt) * H + y); a CTA takes a contiguous range, which
@@ -449,13 +424,13 @@ __device__ __forceinline__ Strip strip_at(int t, int t1, int H, int tiles_x) {
 
 // tmX views X as the 5D tensor [B][H][W][8 chunks][8 channels] (innermost last)
 // with a box of 128 pixels x 1 chunk.
-template <int N, int MODE>
+template <int N, int MODE, bool BITS>
 __global__ void __launch_bounds__(kRingThreads, 1)
 k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
-            const __grid_constant__ CUtensorMap tmM, const __nv_bfloat16* __restrict__ X,
-            const __nv_bfloat16* __restrict__ Wk, const float* __restrict__ bias,
-            const __nv_bfloat16* __restrict__ mask, void* __restrict__ Yv, int relu, const TcErr err) {
+            const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ Wk, const float* __restrict__ bias,
+            uint64_t* __restrict__ rbits, void* __restrict__ Yv, int relu, const TcErr err) {
     static_assert((N == 64 && MODE < 2) || (N == 16 && MODE == 2), "ring conv shapes");
+    static_assert(!BITS || MODE == 0, "ReLU bits come from the forward pass");
     static_assert(kAccS * N <= (int)kStreamCols, "a stream's accumulators fit its share of the TMEM columns");
     extern __shared__ unsigned char dsm_raw[];
     const uint32_t raw = s2u(dsm_raw);
@@ -490,7 +465,6 @@ k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const 
             bar_init(bar(kBarTEmpty + i), 32 * kEpiWarps);
         }
         for (int i = 0; i < kIssuers; ++i) bar_init(bar(kBarDrain + i), 1);
-        for (int i = 0; i < kStreams; ++i) bar_init(bar(kBarMask + i), 1);
         *abortp = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
@@ -691,29 +665,15 @@ k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const 
         const bool leader = (warp - kLoaders - kIssuers) % kEpiWarps == 0 && lane == 0;
         const int nb = 1 + q;   // named barrier of the group
         const uint32_t sStage = sRing + kRingSOff + (uint32_t)q * kStageBytes;
-        // Backward data (MODE 1): the leader loads each tile's ReLU mask (16 KB, the
-        // output's layout) into the staging tile by TMA, as soon as the previous
-        // tile's store has read it out; the threads read their pixel's mask from
-        // there and overwrite it with the output.
-        const uint32_t mbar = bar(kBarMask + q);
-        auto load_mask = [&](int pix0) {
-            bar_arrive_expect_tx(mbar, (uint32_t)kStageBytes);
-            asm volatile(
-                "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-                "[%4];\n" ::"r"(sStage),
-                "l"(reinterpret_cast<uint64_t>(&tmM)), "r"(0), "r"(pix0), "r"(mbar)
-                : "memory");
-        };
-        if (MODE == 1 && leader && tq0(q) < tq1(q)) {
-            const Strip s0 = strip_at(tq0(q), tq1(q), H, tiles_x);
-            load_mask((int)(((size_t)s0.b * H + s0.y0) * W + s0.x0));
-        }
         uint32_t u = 0;
         bool ok = true;
         for (int t = tq0(q); t < tq1(q) && ok;) {
             const Strip s = strip_at(t, tq1(q), H, tiles_x);
             for (int i = 0; i < s.n; ++i, ++u) {
                 const uint32_t acc = acc_slot(u);
+                const size_t pix = ((size_t)s.b * H + s.y0 + i) * W + s.x0 + px;
+                // backward data: the pixel's ReLU bits, loaded while the MMAs run
+                const uint64_t mb = MODE == 1 ? __ldg(rbits + pix) : 0ull;
                 const bool got = bar_wait(bar(kBarTFull + q * kAccS + acc), (u / kAccS) & 1, abortp, err.wait_ns);
                 if (bar_or(nb, 32 * kEpiWarps, !got || *abortp)) {
                     ok = false;
@@ -721,7 +681,6 @@ k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const 
                 }
                 tc_after_sync();
                 const uint32_t taddr = tmem + ((uint32_t)(32 * quad) << 16) + kStreamCols * q + acc * N;
-                const size_t pix = ((size_t)s.b * H + s.y0 + i) * W + s.x0 + px;
                 if (MODE == 2) {
                     uint32_t v[4];
                     asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n"
@@ -744,34 +703,16 @@ k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const 
                     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
                     tc_before_sync();
                     bar_arrive(bar(kBarTEmpty + q * kAccS + acc));
-                    if (MODE == 1) {
-                        // this tile's mask has landed in the staging tile
-                        if (!bar_wait(mbar, u & 1, abortp, err.wait_ns)) *abortp = 1;
-                    } else {
-                        // the previous tile's store has finished reading the staging tile
-                        if (leader) asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
-                        bar_named(nb, 32 * kEpiWarps);
-                    }
-                    stage64(v, MODE, relu, sbias, nullptr, sStage, px);
+                    // the previous tile's store has finished reading the staging tile
+                    if (leader) asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+                    bar_named(nb, 32 * kEpiWarps);
+                    const uint64_t bits = stage64(v, MODE, relu, sbias, mb, BITS, sStage, px);
+                    if (BITS) rbits[pix] = bits;   // forward: the ReLU bits for the backward pass
                     fence_async_smem();
                     bar_named(nb, 32 * kEpiWarps);
                     if (leader) {
                         tma_store_2d(&tmY, 0, (int)(pix - px), sStage);
                         asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
-                        if (MODE == 1) {
-                            // the next tile's mask, once this store has read the staging tile out
-                            int np = -1;
-                            if (i + 1 < s.n) {
-                                np = (int)(pix - px) + W;
-                            } else if (t + s.n < tq1(q)) {
-                                const Strip s1 = strip_at(t + s.n, tq1(q), H, tiles_x);
-                                np = (int)(((size_t)s1.b * H + s1.y0) * W + s1.x0);
-                            }
-                            if (np >= 0 && !*abortp) {
-                                asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
-                                load_mask(np);
-                            }
-                        }
                     }
                 }
             }
@@ -798,9 +739,10 @@ k_conv_ring(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const 
 
 // ---------------------------------------------------------------------------
 // 4 -> 64 input layer: Y bf16 [.][64] = relu?(conv(X) + bias), X bf16 [.][4]
-// (mode 0); the same kernel computes the output layer's backward data,
-// Y = conv(X) * (mask > 0) with X = bf16 upstream gradient [.][4] and the flipped
-// weights (mode 1).
+// (mode 0; rbits, when given, receives each pixel's ReLU bits); the same kernel
+// computes the output layer's backward data, Y = conv(X) * relu bit with X =
+// bf16 upstream gradient [.][4], the flipped weights and the bits rbits of the
+// forward pass (mode 1).
 // A row of a pixel: K = tap * 4 + ci for the 36 products, zero to K = 48, in the
 // no-swizzle chunk-planar layout (6 planes of 128 pixels x 16 bytes).
 // Win: bf16 [6 chunks][64 n][8], the same layout for B (plane = 64 x 16 bytes).
@@ -820,7 +762,7 @@ constexpr uint32_t kInTmemCols = 64;
 
 __global__ void __launch_bounds__(kInThreads)
 k_conv_in_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ Win,
-             const float* __restrict__ bias, const __nv_bfloat16* __restrict__ mask,
+             const float* __restrict__ bias, uint64_t* __restrict__ rbits,
              const __grid_constant__ CUtensorMap tmY, int mode, int relu, const TcErr err) {
     extern __shared__ unsigned char dsm_raw[];
     const uint32_t raw = s2u(dsm_raw);
@@ -876,6 +818,8 @@ k_conv_in_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __n
         const int rem = t - b * H * tiles_x;
         const int y = rem / tiles_x;
         const int x0 = (rem - y * tiles_x) * kTile;
+        const size_t pix = ((size_t)b * H + y) * W + x0 + tid;
+        const uint64_t mb = mode == 1 ? __ldg(rbits + pix) : 0ull;   // backward data: the pixel's ReLU bits
         // the previous tile's store has finished reading the region A is written to
         if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
         __syncthreads();
@@ -907,23 +851,8 @@ k_conv_in_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __n
         PLBM_TMEM_LD32(v, 32, taddr + 32);
         asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
         tc_before_sync();
-        if (mode == 1) {
-            // the warp's 32 mask pixels with coalesced loads into their swizzled places
-            // of the staging tile (lane l: chunk l mod 8 of pixel 4 k + l / 8)
-            const __nv_bfloat16* mw = mask + (((size_t)b * H + y) * W + x0 + 32 * warp) * kC;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int pp = 4 * k + (lane >> 3), c = lane & 7;
-                const uint4 mv = *reinterpret_cast<const uint4*>(mw + pp * kC + c * 8);
-                const int pt = 32 * warp + pp;
-                const uint32_t ad = sA + (uint32_t)pt * 128u + (uint32_t)((c ^ (pt & 7)) * 16);
-                asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n" ::"r"(ad), "r"(mv.x), "r"(mv.y), "r"(mv.z),
-                             "r"(mv.w)
-                             : "memory");
-            }
-            __syncwarp();
-        }
-        stage64(v, mode, relu, sbias, nullptr, sA, tid);
+        const uint64_t bits = stage64(v, mode, relu, sbias, mb, mode == 0 && rbits, sA, tid);
+        if (mode == 0 && rbits) rbits[pix] = bits;
         fence_async_smem();
         __syncthreads();
         if (tid == 0) {
@@ -1822,43 +1751,40 @@ static cudaError_t encode_out_map(CUtensorMap* map, void* Y, long long npix) {
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int N, int MODE>
+template <int N, int MODE, bool BITS = false>
 static cudaError_t launch_ring(int B, int H, int W, const void* X, const void* Wk, const float* bias,
-                               const void* mask, void* Y, int relu, TcErr err, cudaStream_t s) {
+                               uint64_t* rbits, void* Y, int relu, TcErr err, cudaStream_t s) {
     if (W % tc::kTile || H < 1 || B < 1) return cudaErrorInvalidValue;
+    if (MODE == 1 && !rbits) return cudaErrorInvalidValue;
     CUtensorMap map, mapY;
     cudaError_t em = encode_act_map(&map, X, B, H, W);
     if (em != cudaSuccess) return em;
-    CUtensorMap mapM = map;   // the backward pass's ReLU mask (MODE 1 only)
     if (N == 64) {
         em = encode_out_map(&mapY, Y, (long long)B * H * W);
         if (em != cudaSuccess) return em;
-        if (MODE == 1) {
-            em = encode_out_map(&mapM, const_cast<void*>(mask), (long long)B * H * W);
-            if (em != cudaSuccess) return em;
-        }
     } else {
         mapY = map;   // not used by the 64 -> 4 layer (fp32 stores from the threads)
     }
     constexpr int smem = tc::ring_smem<N>();
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(tc::k_conv_ring<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = cudaFuncSetAttribute(tc::k_conv_ring<N, MODE, BITS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     const int ntiles = B * H * (W / tc::kTile);
     const int grid = ntiles < tc_sms() ? ntiles : tc_sms();
-    tc::k_conv_ring<N, MODE><<<grid, tc::kRingThreads, smem, s>>>(
-        B, H, W, map, mapY, mapM, static_cast<const __nv_bfloat16*>(X), static_cast<const __nv_bfloat16*>(Wk), bias,
-        static_cast<const __nv_bfloat16*>(mask), Y, relu, err);
+    tc::k_conv_ring<N, MODE, BITS><<<grid, tc::kRingThreads, smem, s>>>(
+        B, H, W, map, mapY, static_cast<const __nv_bfloat16*>(X), static_cast<const __nv_bfloat16*>(Wk), bias, rbits,
+        Y, relu, err);
     return cudaGetLastError();
 }
 
-cudaError_t cnn_conv64_tc(int B, int H, int W, const void* X, const void* Wk, const float* bias, const void* mask,
+cudaError_t cnn_conv64_tc(int B, int H, int W, const void* X, const void* Wk, const float* bias, uint64_t* rbits,
                           void* Y, int mode, int relu, TcErr err, cudaStream_t s) {
-    if (mode == 0) return launch_ring<64, 0>(B, H, W, X, Wk, bias, mask, Y, relu, err, s);
-    return launch_ring<64, 1>(B, H, W, X, Wk, bias, mask, Y, relu, err, s);
+    if (mode == 0 && rbits) return launch_ring<64, 0, true>(B, H, W, X, Wk, bias, rbits, Y, relu, err, s);
+    if (mode == 0) return launch_ring<64, 0>(B, H, W, X, Wk, bias, nullptr, Y, relu, err, s);
+    return launch_ring<64, 1>(B, H, W, X, Wk, bias, rbits, Y, relu, err, s);
 }
 
 cudaError_t cnn_conv_out_tc(int B, int H, int W, const void* X, const void* Wo, const float* bias, float* Y,
@@ -1866,9 +1792,9 @@ cudaError_t cnn_conv_out_tc(int B, int H, int W, const void* X, const void* Wo, 
     return launch_ring<16, 2>(B, H, W, X, Wo, bias, nullptr, Y, 0, err, s);
 }
 
-cudaError_t cnn_conv_in_tc(int B, int H, int W, const void* X, const void* Win, const float* bias, const void* mask,
+cudaError_t cnn_conv_in_tc(int B, int H, int W, const void* X, const void* Win, const float* bias, uint64_t* rbits,
                            void* Y, int mode, int relu, TcErr err, cudaStream_t s) {
-    if ((mode == 0 && !bias) || (mode == 1 && !mask) || mode < 0 || mode > 1) return cudaErrorInvalidValue;
+    if ((mode == 0 && !bias) || (mode == 1 && !rbits) || mode < 0 || mode > 1) return cudaErrorInvalidValue;
     if (W % tc::kTile || H < 1 || B < 1) return cudaErrorInvalidValue;
     static bool attr = false;
     if (!attr) {
@@ -1882,9 +1808,8 @@ cudaError_t cnn_conv_in_tc(int B, int H, int W, const void* X, const void* Win, 
     const int ntiles = B * H * (W / tc::kTile);
     const int grid = ntiles < 8 * tc_sms() ? ntiles : 8 * tc_sms();
     tc::k_conv_in_tc<<<grid, tc::kInThreads, tc::kInSmem, s>>>(B, H, W, static_cast<const __nv_bfloat16*>(X),
-                                                               static_cast<const __nv_bfloat16*>(Win), bias,
-                                                               static_cast<const __nv_bfloat16*>(mask), mapY, mode,
-                                                               relu, err);
+                                                               static_cast<const __nv_bfloat16*>(Win), bias, rbits,
+                                                               mapY, mode, relu, err);
     return cudaGetLastError();
 }
 

@@ -162,14 +162,17 @@ cudaError_t cnn_conv_thin_fwd(int ci, int co, int ti, int to, int B, int H, int 
 int cnn_thin_parts(int B, int H, int W, int* pix_per_block);
 cudaError_t cnn_conv_thin_wgrad(int ci, int co, int tx, int tg, int B, int H, int W, const void* X, const void* dY,
                                 float* partial, float* partial_b, float* dW, float* db, cudaStream_t s);
-cudaError_t cnn_conv64_tc(int B, int H, int W, const void* X, const void* Wk, const float* bias, const void* mask,
+// ReLU bits rbits: one uint64_t per pixel, bit c set when the stored bf16 output
+// channel c of a forward ReLU layer is > 0.  mode 0 (forward) writes them when
+// rbits is not null; mode 1 (backward data, Y = conv(X) * bit) reads them.
+cudaError_t cnn_conv64_tc(int B, int H, int W, const void* X, const void* Wk, const float* bias, uint64_t* rbits,
                           void* Y, int mode, int relu, TcErr err, cudaStream_t s);
 cudaError_t cnn_conv_out_tc(int B, int H, int W, const void* X, const void* Wo, const float* bias, float* Y,
                             TcErr err, cudaStream_t s);
-// mode 0: Y = relu?(conv(X) + bias) (the 4 -> 64 input layer); mode 1: Y = conv(X) *
-// (mask > 0) (the 64 -> 4 output layer's backward data, X = its bf16 upstream gradient,
-// Win from the flipped weights).
-cudaError_t cnn_conv_in_tc(int B, int H, int W, const void* X, const void* Win, const float* bias, const void* mask,
+// mode 0: Y = relu?(conv(X) + bias) (the 4 -> 64 input layer; ReLU bits to rbits
+// when given); mode 1: Y = conv(X) * bit (the 64 -> 4 output layer's backward data,
+// X = its bf16 upstream gradient, Win from the flipped weights, rbits required).
+cudaError_t cnn_conv_in_tc(int B, int H, int W, const void* X, const void* Win, const float* bias, uint64_t* rbits,
                            void* Y, int mode, int relu, TcErr err, cudaStream_t s);
 // grad16 (optional): the gradient also in bf16.
 cudaError_t cnn_mse(const float* pred, const float* target, long long n, long long npix, float lam, float* merr,

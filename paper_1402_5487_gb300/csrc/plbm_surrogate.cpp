@@ -43,6 +43,7 @@ struct Sur {
     void* win = nullptr;            // first layer (4 -> 64) for tcgen05: bf16 [6][64][8]
     void* win6 = nullptr;           // the last layer's backward-data weights in the same layout
     void* dout16 = nullptr;         // bf16 copy of the upstream gradient of the output [pix][4]
+    uint64_t* rbits = nullptr;      // ReLU bits of the hidden layers 0..4 (tensor-core path), 5 x [pix]
     void* wout = nullptr;           // last layer (64 -> 4) for tcgen05: bf16 [9][16][64]
     unsigned* derr = nullptr;       // device flag: a bounded wait in a tensor-core kernel ran out
     unsigned long long wait_ns = 2000000000ull;  // budget of each of those waits
@@ -114,7 +115,7 @@ void free_sur(Sur* s) {
     void* bufs[] = {s->p, s->g, s->m, s->v, s->pr, s->wbf, s->wflip, s->w6flip, s->dz[0], s->dz[1], s->dz[2],
                     s->dz[3], s->dz[4], s->dout, s->part, s->part_b, s->loss_part, s->Fold, s->Fnew, s->xin,
                     s->planes, s->sums, s->wtc, s->derr, s->win, s->win6, s->dout16, s->wout, s->drift, s->fb_table, s->fb_tile_inst,
-                    s->dref};
+                    s->dref, s->rbits};
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (void* a : s->act)
@@ -138,6 +139,8 @@ bool same_model(const plbm::LatticeParams& a, const plbm::LatticeParams& b) {
 
 void* wtc_fwd(Sur* s, int l) { return static_cast<char*>(s->wtc) + (size_t)(2 * (l - 1)) * 9 * 64 * 64 * 2; }
 void* wtc_bwd(Sur* s, int l) { return static_cast<char*>(s->wtc) + (size_t)(2 * (l - 1) + 1) * 9 * 64 * 64 * 2; }
+// ReLU bits of hidden layer l (output of layer l, 0..4): one uint64_t per pixel
+uint64_t* rbits_of(Sur* s, int l) { return s->rbits + (size_t)l * s->Bm * s->H * s->W; }
 
 // Rounded copies, bf16 weights and backward-data weights from the FP32 master weights.
 plbm_status refresh_weights(Sur* s) {
@@ -146,10 +149,13 @@ plbm_status refresh_weights(Sur* s) {
     return PLBM_OK;
 }
 
-plbm_status forward(Sur* s, int B, const void* x) {
+// keep_bits: the tensor-core path also records the ReLU bits of every hidden
+// layer for a backward pass.
+plbm_status forward(Sur* s, int B, const void* x, bool keep_bits = false) {
     const int H = s->H, W = s->W;
     if (s->use_tc) {
-        SCK(plbm::cnn_conv_in_tc(B, H, W, x, s->win, s->p + s->boff[0], nullptr, s->act[0], 0, 1,
+        SCK(plbm::cnn_conv_in_tc(B, H, W, x, s->win, s->p + s->boff[0], keep_bits ? rbits_of(s, 0) : nullptr,
+                                 s->act[0], 0, 1,
                                  plbm::TcErr{s->derr, s->wait_ns}, s->stream));
     } else {
         SCK(plbm::cnn_conv_thin_fwd(4, 64, 0, 0, B, H, W, x, s->pr + s->woff[0], s->p + s->boff[0], nullptr,
@@ -157,7 +163,8 @@ plbm_status forward(Sur* s, int B, const void* x) {
     }
     for (int l = 1; l <= 4; ++l) {
         if (s->use_tc) {
-            SCK(plbm::cnn_conv64_tc(B, H, W, s->act[l - 1], wtc_fwd(s, l), s->p + s->boff[l], nullptr, s->act[l], 0, 1,
+            SCK(plbm::cnn_conv64_tc(B, H, W, s->act[l - 1], wtc_fwd(s, l), s->p + s->boff[l],
+                                    keep_bits ? rbits_of(s, l) : nullptr, s->act[l], 0, 1,
                                     plbm::TcErr{s->derr, s->wait_ns}, s->stream));
         } else {
             const char* wb = static_cast<const char*>(s->wbf) + (size_t)(l - 1) * 9 * 64 * 64 * 2;
@@ -189,7 +196,7 @@ plbm_status backward(Sur* s, int B, const void* x, const float* dout, bool dout1
                                       s->g + s->boff[5], s->stream));
     if (s->use_tc) {   // tcgen05, on the bf16-rounded upstream gradient (the other layers' gradients are bf16 too)
         if (!dout16_ready) SCK(plbm::cnn_to_bf16(dout, (long long)B * H * W * 4, s->dout16, s->stream));
-        SCK(plbm::cnn_conv_in_tc(B, H, W, s->dout16, s->win6, nullptr, s->act[4], s->dz[4], 1, 0,
+        SCK(plbm::cnn_conv_in_tc(B, H, W, s->dout16, s->win6, nullptr, rbits_of(s, 4), s->dz[4], 1, 0,
                                  plbm::TcErr{s->derr, s->wait_ns}, s->stream));
     } else {
         SCK(plbm::cnn_conv_thin_fwd(4, 64, 1, 0, B, H, W, dout, s->w6flip, nullptr, s->act[4], s->dz[4], 1, 0,
@@ -203,7 +210,7 @@ plbm_status backward(Sur* s, int B, const void* x, const float* dout, bool dout1
             SCK(plbm::cnn_conv64_wgrad(B, H, W, s->act[l - 1], s->dz[l], s->part, s->part_b, s->g + s->woff[l],
                                        s->g + s->boff[l], s->stream));
         if (s->use_tc) {
-            SCK(plbm::cnn_conv64_tc(B, H, W, s->dz[l], wtc_bwd(s, l), nullptr, s->act[l - 1], s->dz[l - 1], 1, 0,
+            SCK(plbm::cnn_conv64_tc(B, H, W, s->dz[l], wtc_bwd(s, l), nullptr, rbits_of(s, l - 1), s->dz[l - 1], 1, 0,
                                     plbm::TcErr{s->derr, s->wait_ns}, s->stream));
         } else {
             const char* wf = static_cast<const char*>(s->wflip) + (size_t)(l - 1) * 9 * 64 * 64 * 2;
@@ -284,6 +291,7 @@ plbm_status plbm_sur_create(int max_batch, int H, int W, unsigned long long seed
         {(void**)&s->fb_table, (size_t)max_batch * sizeof(plbm::PairParams)},
         {(void**)&s->fb_tile_inst, (size_t)max_batch * ((W + 127) / 128) * ((H + 1) / 2) * sizeof(unsigned short) + 256},
         {(void**)&s->dref, (size_t)2 * max_batch * sizeof(plbm::LatticeRef)},
+        {(void**)&s->rbits, 5 * pix * 8},
     };
     for (auto& a : allocs) {
         if (cudaMalloc(a.p, a.n) != cudaSuccess) {
@@ -441,7 +449,7 @@ plbm_status plbm_sur_forward(plbm_surrogate h, int B, const void* x, float* out)
 plbm_status plbm_sur_backward(plbm_surrogate h, int B, const void* x, const float* dout) {
     Sur* s = as_sur(h);
     if (!s || !x || !dout || B < 1 || B > s->Bm) return PLBM_E_ARG;
-    plbm_status r = forward(s, B, x);
+    plbm_status r = forward(s, B, x, true);
     if (r != PLBM_OK) return r;
     return backward(s, B, x, dout);
 }
@@ -473,7 +481,7 @@ plbm_status plbm_sur_copy(plbm_surrogate h, int kind, int layer, int B, void* ds
 plbm_status plbm_sur_train_step(plbm_surrogate h, int B, const void* x, const float* target, float lr, float* loss) {
     Sur* s = as_sur(h);
     if (!s || !x || !target || B < 1 || B > s->Bm || !(lr > 0.0f)) return PLBM_E_ARG;
-    plbm_status r = forward(s, B, x);
+    plbm_status r = forward(s, B, x, true);
     if (r != PLBM_OK) return r;
     const long long n = (long long)B * s->H * s->W * 4;
     const int parts = 1024;   // the loss partials (loss_part[0 .. 1023])
