@@ -760,10 +760,13 @@ constexpr int kInSmem = 26 * 1024;  // A/staging, B, barriers and padding that c
 static_assert(kInA <= kInAS && 1024 + kInAS + kInB + kInBar <= kInSmem, "input-layer shared memory");
 constexpr uint32_t kInTmemCols = 64;
 
+template <int MODE, bool BITS>
 __global__ void __launch_bounds__(kInThreads)
 k_conv_in_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ Win,
              const float* __restrict__ bias, uint64_t* __restrict__ rbits,
-             const __grid_constant__ CUtensorMap tmY, int mode, int relu, const TcErr err) {
+             const __grid_constant__ CUtensorMap tmY, int relu, const TcErr err) {
+    static_assert(MODE == 0 || (MODE == 1 && !BITS), "ReLU bits come from the forward pass");
+    constexpr int mode = MODE;
     extern __shared__ unsigned char dsm_raw[];
     const uint32_t raw = s2u(dsm_raw);
     const uint32_t pad = (1024 - (raw & 1023)) & 1023;   // the staging tile's swizzle wants 1024-byte alignment
@@ -851,8 +854,8 @@ k_conv_in_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __n
         PLBM_TMEM_LD32(v, 32, taddr + 32);
         asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
         tc_before_sync();
-        const uint64_t bits = stage64(v, mode, relu, sbias, mb, mode == 0 && rbits, sA, tid);
-        if (mode == 0 && rbits) rbits[pix] = bits;
+        const uint64_t bits = stage64(v, mode, relu, sbias, mb, BITS, sA, tid);
+        if (BITS) rbits[pix] = bits;
         fence_async_smem();
         __syncthreads();
         if (tid == 0) {
@@ -1792,13 +1795,13 @@ cudaError_t cnn_conv_out_tc(int B, int H, int W, const void* X, const void* Wo, 
     return launch_ring<16, 2>(B, H, W, X, Wo, bias, nullptr, Y, 0, err, s);
 }
 
-cudaError_t cnn_conv_in_tc(int B, int H, int W, const void* X, const void* Win, const float* bias, uint64_t* rbits,
-                           void* Y, int mode, int relu, TcErr err, cudaStream_t s) {
-    if ((mode == 0 && !bias) || (mode == 1 && !rbits) || mode < 0 || mode > 1) return cudaErrorInvalidValue;
-    if (W % tc::kTile || H < 1 || B < 1) return cudaErrorInvalidValue;
+template <int MODE, bool BITS>
+static cudaError_t launch_in(int B, int H, int W, const void* X, const void* Win, const float* bias, uint64_t* rbits,
+                             void* Y, int relu, TcErr err, cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(tc::k_conv_in_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kInSmem);
+        cudaError_t e = cudaFuncSetAttribute(tc::k_conv_in_tc<MODE, BITS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             tc::kInSmem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -1807,10 +1810,19 @@ cudaError_t cnn_conv_in_tc(int B, int H, int W, const void* X, const void* Win, 
     if (em != cudaSuccess) return em;
     const int ntiles = B * H * (W / tc::kTile);
     const int grid = ntiles < 8 * tc_sms() ? ntiles : 8 * tc_sms();
-    tc::k_conv_in_tc<<<grid, tc::kInThreads, tc::kInSmem, s>>>(B, H, W, static_cast<const __nv_bfloat16*>(X),
-                                                               static_cast<const __nv_bfloat16*>(Win), bias, rbits,
-                                                               mapY, mode, relu, err);
+    tc::k_conv_in_tc<MODE, BITS><<<grid, tc::kInThreads, tc::kInSmem, s>>>(
+        B, H, W, static_cast<const __nv_bfloat16*>(X), static_cast<const __nv_bfloat16*>(Win), bias, rbits, mapY, relu,
+        err);
     return cudaGetLastError();
+}
+
+cudaError_t cnn_conv_in_tc(int B, int H, int W, const void* X, const void* Win, const float* bias, uint64_t* rbits,
+                           void* Y, int mode, int relu, TcErr err, cudaStream_t s) {
+    if ((mode == 0 && !bias) || (mode == 1 && !rbits) || mode < 0 || mode > 1) return cudaErrorInvalidValue;
+    if (W % tc::kTile || H < 1 || B < 1) return cudaErrorInvalidValue;
+    if (mode == 1) return launch_in<1, false>(B, H, W, X, Win, bias, rbits, Y, relu, err, s);
+    if (rbits) return launch_in<0, true>(B, H, W, X, Win, bias, rbits, Y, relu, err, s);
+    return launch_in<0, false>(B, H, W, X, Win, bias, nullptr, Y, relu, err, s);
 }
 
 cudaError_t cnn_conv64_wgrad_tc(int B, int H, int W, const void* X, const void* dY, float* partial, float* partial_b,
