@@ -880,26 +880,27 @@ k_conv_in_tc(int B, int H, int W, const __nv_bfloat16* __restrict__ X, const __n
 // ---------------------------------------------------------------------------
 // 64 -> 64 weight gradient: dW[tap][ci][co] = sum over pixels of
 // X[pixel shifted by the tap][ci] dY[pixel][co], bias gradient db[co] = sum dY.
-// A tile is 128 pixels of one row; its three input rows (pixels x0 - 1 ..
-// x0 + 128) and its dY row are staged in the chunk-planar no-swizzle layout
-// (chunk c of pixel s at plane c, byte 16 s), which is the MN-major canonical
-// layout for both operands: A = X^T (M = channels, K = pixels) and B = dY (K =
-// pixels, N = channels), 8-pixel K blocks 128 bytes apart (leading byte offset)
-// and 8-channel blocks one plane apart (stride byte offset).  Planes of
-// consecutive rows follow each other, so two rows stack into one M = 128
-// operand: rows (y - 1, y) give taps ky = 0, 1 and rows (y, y + 1) give ky = 1
-// (again, discarded) and 2.  Per K step of 16 pixels and tap column kx: two MMAs
-// of 128 x 64 x 16 into six TMEM accumulators (384 columns) that sum over all of
-// the CTA's tiles.
+// Rows of 128 pixels (input rows with their two halo pixels x0 - 1, x0 + 128)
+// are staged in the chunk-planar no-swizzle layout (chunk c of pixel s at plane
+// c, byte 16 s), which is the MN-major canonical layout for both operands: A =
+// X^T (M = channels, K = pixels) and B = dY (K = pixels, N = channels), 8-pixel
+// K blocks 128 bytes apart (leading byte offset) and 8-channel blocks one plane
+// apart (stride byte offset).  Planes of consecutive rows follow each other, so
+// two rows stack into one operand of 128 channels.
 //
-// A CTA takes a contiguous range of tiles in column order, t = (b * W / 128 +
-// xt) * H + y, so that consecutive tiles are consecutive rows of one 128-pixel
-// wide column: an input row is staged once, into a ring of kWrR row slots, and
-// serves the three tiles that read it (a column's first tile stages three rows,
-// every other tile one).  Slot kWrR is a second copy of slot 0, so that the row
-// pair of every tile is two adjacent slots.  The dY rows rotate through
-// kWrD slots.  The CTA writes its partial sums partial[cta][tap][ci][co],
-// partial_b[cta][co] at the end.
+// Step r multiplies the input rows (r, r + 1) (M = 128) by the dY rows (r, r + 1)
+// (N = 128): per K step of 16 pixels and tap column kx one MMA of 128 x 128 x 16
+// into the kx-th 128-column TMEM accumulator.  Input row r + i meets dY row r + j
+// in tap ky = i - j + 1: quadrant (0, 0) is ky = 1, (0, 1) ky = 0, (1, 0) ky = 2,
+// and (1, 1) is ky = 1 again (not read out).  A CTA takes a contiguous range of
+// output rows in column order (t = (b * W / 128 + xt) * H + y); a run of n rows
+// y .. y + n - 1 of one column takes the n + 1 steps r = y - 1 .. y + n - 1 with
+// the dY rows y - 1 and y + n taken as zero, so that every output row meets its
+// three input rows once in quadrants (0, 0), (0, 1), (1, 0).  Each input row and
+// dY row is staged once, as fill f = 0, 1, ... of the CTA into row slot f mod
+// kWpR of two rings (input, dY); slot kWpR is a second copy of slot 0, so that
+// the rows of every step are two adjacent slots of each ring.  The CTA writes
+// its partial sums partial[cta][tap][ci][co], partial_b[cta][co] at the end.
 // ---------------------------------------------------------------------------
 constexpr int kWgRowPix = kTile + 2;
 // X planes 17 lines apart, pixel 0 of a plane 112 bytes into a line, so that pixel
@@ -907,19 +908,23 @@ constexpr int kWgRowPix = kTile + 2;
 constexpr int kWgPlaneX = 17 * 128;             // 2176 >= 130 pixels x 16 bytes
 constexpr int kWgXOff = 112;
 constexpr int kWgPlaneG = kTile * 16;           // 2048
-constexpr int kWrR = 7;                         // input row slots
-constexpr int kWrD = 4;                         // dY row slots
-constexpr int kWrSlot = 8 * kWgPlaneX;          // 17408: one input row, 8 chunk planes
-constexpr int kWrG = (kWrR + 1) * kWrSlot + 128;                // dY ring (after slot kWrR and the offset)
-constexpr int kWrBars = kWrG + kWrD * 8 * kWgPlaneG;       // barriers, TMEM slot, bias sums
-constexpr int kWrSmem = 128 + kWrBars + 512;
-// Per input row: 8 TMA boxes of 128 pixels (the 16 halo chunks of 16 bytes are
-// copied by the threads); per dY row 8 boxes.
-constexpr uint32_t kWrRowTx = 8 * kTile * 16;
-static_assert(kWrSlot % 128 == 0 && kWrG % 128 == 0 && kWrSmem <= 232448, "weight-gradient rings");
+constexpr int kWpR = 5;                         // row slots of each ring
+constexpr int kWpD = 8;                         // commit barriers of the steps
+constexpr int kWpXSlot = 8 * kWgPlaneX;         // 17408: one input row
+constexpr int kWpGSlot = 8 * kWgPlaneG;         // 16384: one dY row
+constexpr int kWpG = (kWpR + 1) * kWpXSlot + 128;               // dY ring (after slot kWpR and the offset)
+constexpr int kWpBars = kWpG + (kWpR + 1) * kWpGSlot;           // barriers, TMEM slot, bias sums
+constexpr int kWpSmem = 128 + kWpBars + 512;
+// Per fill: 8 TMA boxes of 128 input pixels (the 16 halo chunks of 16 bytes are
+// copied by the threads) and 8 boxes of the dY row (none for a zero dY row).
+constexpr uint32_t kWpRowTx = 8 * kTile * 16;
+static_assert(kWpXSlot % 128 == 0 && kWpG % 128 == 0 && kWpSmem <= 232448, "weight-gradient rings");
 constexpr uint32_t kWgTmemCols = 512;
 // kind::f16, D fp32, A and B bf16, both MN-major (bits 15, 16), N = 64, M = 128.
 constexpr uint32_t kIdescWg = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((64u >> 3) << 17) |
+                              ((128u >> 4) << 24);
+// The same with N = 128.
+constexpr uint32_t kIdescWp = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((128u >> 3) << 17) |
                               ((128u >> 4) << 24);
 
 __device__ __forceinline__ uint64_t desc_mn(uint32_t addr, uint32_t mn_stride) {
@@ -934,15 +939,35 @@ __device__ __forceinline__ void mma_wg(uint32_t tmem_d, uint64_t a, uint64_t b, 
         "l"(a), "l"(b), "r"(kIdescWg), "r"(accumulate)
         : "memory");
 }
+__device__ __forceinline__ void mma_wp(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.u32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(kIdescWp), "r"(accumulate)
+        : "memory");
+}
+
+// The CTA's output rows come as runs within one column: run of n rows from (b,
+// x0, y), n = min(H - y, rows left).
+struct WpRun {
+    int b, x0, y, n;
+};
+__device__ __forceinline__ WpRun wp_run(int t, int left, int H, int tiles_x) {
+    const int col = t / H;
+    WpRun r;
+    r.y = t - col * H;
+    r.b = col / tiles_x;
+    r.x0 = (col - r.b * tiles_x) * kTile;
+    r.n = min(H - r.y, left);
+    return r;
+}
 
 // Warp roles: lane 0 of warp 0 issues the MMAs, warp 1 stages the rows, warps 2
 // and 3 sum dY for the bias gradient.  They hand slots over through mbarriers
-// only: xfull[s] (row slot s landed), gfull[k] (dY slot k landed), done[k] (the
-// MMAs of the tiles up to the one in dY slot k are done; tcgen05.commit tracks
-// every earlier MMA of the thread), bias[k] (both bias warps have read dY slot
-// k).  Row fills are numbered f = 0, 1, ... in the CTA; fill f goes to slot
-// f mod kWrR (and also to slot kWrR when that is 0), tile i's dY to slot
-// i mod kWrD.
+// only: full[s] (fill in row slot s landed, input row and dY row), done[t mod
+// kWpD] (the MMAs of steps up to t are done: tcgen05.commit tracks every earlier
+// MMA of the thread), bias[s] (both bias warps have read the dY row of slot s).
 constexpr int kWgsThreads = 128;
 
 __global__ void __launch_bounds__(kWgsThreads, 1)
@@ -954,18 +979,17 @@ k_wgrad_tc(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const _
     const uint32_t pad = (128 - (raw & 127)) & 127;
     unsigned char* base = dsm_raw + pad;
     const uint32_t sbase = raw + pad;
-    unsigned char* bars_p = base + kWrBars;
-    // done[kWrD], drain, TMEM slot, abort flag, xfull[kWrR], gfull[kWrD], bias[kWrD]; 64 bias sums at 256
-    const uint32_t bar_done0 = s2u(bars_p), bar_drain = bar_done0 + 8 * kWrD;
-    unsigned char* slot_p = bars_p + 8 * kWrD + 8;
+    unsigned char* bars_p = base + kWpBars;
+    // done[kWpD], drain, TMEM slot, abort flag, full[kWpR], bias[kWpR]; 64 bias sums at 256
+    const uint32_t bar_done0 = s2u(bars_p), bar_drain = bar_done0 + 8 * kWpD;
+    unsigned char* slot_p = bars_p + 8 * kWpD + 8;
     volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(slot_p);
     volatile int* abortp = reinterpret_cast<volatile int*>(slot_p + 4);
-    const uint32_t bar_xfull0 = bar_drain + 16;
-    const uint32_t bar_gfull0 = bar_xfull0 + 8 * kWrR;
-    const uint32_t bar_bias0 = bar_gfull0 + 8 * kWrD;
+    const uint32_t bar_full0 = bar_drain + 16;
+    const uint32_t bar_bias0 = bar_full0 + 8 * kWpR;
     float* red = reinterpret_cast<float*>(bars_p + 256);
-    static_assert(8 * kWrD + 16 + 8 * kWrR + 16 * kWrD <= 256, "weight-gradient barriers");
-    const uint32_t sX = sbase + kWgXOff, sG = sbase + kWrG;
+    static_assert(8 * kWpD + 16 + 16 * kWpR <= 256, "weight-gradient barriers");
+    const uint32_t sX = sbase + kWgXOff, sG = sbase + kWpG;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tiles_x = W / kTile;
@@ -973,12 +997,11 @@ k_wgrad_tc(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const _
     const int t0 = (int)(ntiles * blockIdx.x / gridDim.x);
     const int ntl = (int)(ntiles * (blockIdx.x + 1) / gridDim.x) - t0;   // >= 1: the grid is at most ntiles
     if (tid == 0) {
-        for (int k = 0; k < kWrD; ++k) {
-            bar_init(bar_done0 + 8 * k, 1);
-            bar_init(bar_gfull0 + 8 * k, 1);
+        for (int k = 0; k < kWpD; ++k) bar_init(bar_done0 + 8 * k, 1);
+        for (int k = 0; k < kWpR; ++k) {
+            bar_init(bar_full0 + 8 * k, 1 + 8);
             bar_init(bar_bias0 + 8 * k, 64);
         }
-        for (int k = 0; k < kWrR; ++k) bar_init(bar_xfull0 + 8 * k, 1 + 8);
         bar_init(bar_drain, 1);
         *abortp = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -990,158 +1013,159 @@ k_wgrad_tc(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const _
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 1) {
-        // ---- rows: lane 8 q + c stages chunk plane c of the tile's q-th new row
+        // ---- staging: per fill, lane c < 8 stages chunk plane c of the input row
         // (TMA box for pixels x0 .. x0 + 127, loads and shared stores for the two
-        // halo pixels, then a proxy fence and an arrival); lanes 24..31 stage the
-        // dY planes ----
+        // halo pixels) and zeroes plane c of a zero dY row, then fences and
+        // arrives; lanes 24..31 issue the dY boxes ----
         if (lane == 0) asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tmX)) : "memory");
-        int lastuse[kWrR];   // the last tile that reads the row in each slot
+        int lastuse[kWpR];   // the last step that reads the fill in each slot
 #pragma unroll
-        for (int k = 0; k < kWrR; ++k) lastuse[k] = -1;
-        int F = -1;          // the last fill so far
-        int i = 0;
-        for (; i < ntl; ++i) {
-            const int t = t0 + i;
-            const int col = t / H, y = t - col * H;
-            const int b = col / tiles_x, x0 = (col - b * tiles_x) * kTile;
-            const int nf = (i == 0 || y == 0) ? 3 : 1;   // a column's first tile stages rows y - 1, y, y + 1
-            const int f0 = F + 1;
-            // slots free: the tiles that read their rows, and the tile of dY slot i mod kWrD, done
-            int w = i - kWrD;
+        for (int k = 0; k < kWpR; ++k) lastuse[k] = -1;
+        int f = 0, t = 0;    // fills and steps so far
+        bool stop = false;
+        for (int i = 0; i < ntl && !stop;) {
+            const WpRun run = wp_run(t0 + i, ntl - i, H, tiles_x);
+            for (int j = 0; j < run.n + 2; ++j, ++f) {
+                const int sl = f % kWpR;
+                if (f >= kWpR) {   // the slot's previous fill: its last step's MMAs done, its dY summed
+                    int u = -1;
 #pragma unroll
-            for (int k = 0; k < kWrR; ++k) {
-                const bool refill = ((k - f0 % kWrR + kWrR) % kWrR) < nf && f0 + ((k - f0 % kWrR + kWrR) % kWrR) >= kWrR;
-                if (refill && lastuse[k] > w) w = lastuse[k];
-            }
-            if (w >= 0 && !bar_wait(bar_done0 + 8 * (w % kWrD), (uint32_t)(w / kWrD) & 1u, abortp,
-                                    err.wait_ns))
-                break;
-            if (i >= kWrD && !bar_wait(bar_bias0 + 8 * (i % kWrD),
-                                            (uint32_t)(i / kWrD - 1) & 1u, abortp, err.wait_ns))
-                break;
-            // arm the barriers (before any copy of this tile is issued)
-            if (lane < nf) {
-                const int sl = (f0 + lane) % kWrR;
-                bar_arrive_expect_tx(bar_xfull0 + 8 * sl, sl == 0 ? 2 * kWrRowTx : kWrRowTx);
-            }
-            if (lane == 24) bar_arrive_expect_tx(bar_gfull0 + 8 * (i % kWrD), kWrRowTx);
-            __syncwarp();
-            if (lane < 8 * nf) {
-                const int q = lane >> 3, c = lane & 7;
-                const int sl = (f0 + q) % kWrR;
-                const int yy = wrapi(nf == 3 ? y + q - 1 : y + 1, H);
-                const uint32_t full = bar_xfull0 + 8 * sl;
-                const size_t row = ((size_t)b * H + yy) * W;
-                const uint4 lft = __ldg(reinterpret_cast<const uint4*>(X + (row + wrapi(x0 - 1, W)) * kC + 8 * c));
-                const uint4 rgt =
-                    __ldg(reinterpret_cast<const uint4*>(X + (row + wrapi(x0 + kTile, W)) * kC + 8 * c));
-                for (int dup = 0; dup < (sl == 0 ? 2 : 1); ++dup) {
-                    const uint32_t plane = sX + (uint32_t)((dup ? kWrR : sl) * kWrSlot + c * kWgPlaneX);
-                    tma_load_5d(plane + 16, &tmX, 0, c, x0, yy, b, full);
-                    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n" ::"r"(plane), "r"(lft.x), "r"(lft.y),
-                                 "r"(lft.z), "r"(lft.w)
-                                 : "memory");
-                    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n" ::"r"(plane + 16 * (kWgRowPix - 1)),
-                                 "r"(rgt.x), "r"(rgt.y), "r"(rgt.z), "r"(rgt.w)
-                                 : "memory");
+                    for (int k = 0; k < kWpR; ++k)
+                        if (k == sl) u = lastuse[k];
+                    if (!bar_wait(bar_done0 + 8 * (u % kWpD), (uint32_t)(u / kWpD) & 1u, abortp, err.wait_ns) ||
+                        !bar_wait(bar_bias0 + 8 * sl, (uint32_t)((f - kWpR) / kWpR) & 1u, abortp, err.wait_ns)) {
+                        stop = true;
+                        break;
+                    }
                 }
-                fence_async_smem();
-                bar_arrive(full);
-            } else if (lane >= 24) {
-                const int c = lane - 24;
-                tma_load_5d(sG + (uint32_t)((i % kWrD) * 8 * kWgPlaneG + c * kWgPlaneG), &tmG, 0, c, x0, y, b,
-                            bar_gfull0 + 8 * (i % kWrD));
-            }
-            // the new rows' readers: row y - 1 + p (p = 0, 1, 2) serves tiles i .. i + p of this column and range
-            const int reach = min(H - 1 - y, ntl - 1 - i);
+                const bool zero = j == 0 || j == run.n + 1;   // dY rows y - 1 and y + n
+                const int xr = wrapi(run.y - 1 + j, H), gr = run.y - 1 + j;
+                const int ncopy = sl == 0 ? 2 : 1;
+                const uint32_t full = bar_full0 + 8 * sl;
+                if (lane == 0) bar_arrive_expect_tx(full, (uint32_t)ncopy * (zero ? kWpRowTx : 2 * kWpRowTx));
+                __syncwarp();
+                if (lane < 8) {
+                    const int c = lane;
+                    const size_t row = ((size_t)run.b * H + xr) * W;
+                    const uint4 lft =
+                        __ldg(reinterpret_cast<const uint4*>(X + (row + wrapi(run.x0 - 1, W)) * kC + 8 * c));
+                    const uint4 rgt =
+                        __ldg(reinterpret_cast<const uint4*>(X + (row + wrapi(run.x0 + kTile, W)) * kC + 8 * c));
+                    for (int dup = 0; dup < ncopy; ++dup) {
+                        const int s = dup ? kWpR : sl;
+                        const uint32_t plane = sX + (uint32_t)(s * kWpXSlot + c * kWgPlaneX);
+                        tma_load_5d(plane + 16, &tmX, 0, c, run.x0, xr, run.b, full);
+                        asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n" ::"r"(plane), "r"(lft.x),
+                                     "r"(lft.y), "r"(lft.z), "r"(lft.w)
+                                     : "memory");
+                        asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n" ::"r"(plane + 16 * (kWgRowPix - 1)),
+                                     "r"(rgt.x), "r"(rgt.y), "r"(rgt.z), "r"(rgt.w)
+                                     : "memory");
+                        if (zero) {
+                            const uint32_t gp = sG + (uint32_t)(s * kWpGSlot + c * kWgPlaneG);
+                            for (int e = 0; e < kWgPlaneG / 16; ++e)
+                                asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};\n" ::"r"(gp + 16 * e), "r"(0u)
+                                             : "memory");
+                        }
+                    }
+                    fence_async_smem();
+                    bar_arrive(full);
+                } else if (lane >= 24 && !zero) {
+                    const int c = lane - 24;
+                    for (int dup = 0; dup < ncopy; ++dup)
+                        tma_load_5d(sG + (uint32_t)((dup ? kWpR : sl) * kWpGSlot + c * kWgPlaneG), &tmG, 0, c,
+                                    run.x0, gr, run.b, full);
+                }
+                // fill j of the run is read by its steps j - 1 and j (0 .. n)
 #pragma unroll
-            for (int k = 0; k < kWrR; ++k) {
-                const int q = (k - f0 % kWrR + kWrR) % kWrR;
-                if (q < nf) lastuse[k] = i + min(nf == 3 ? q : 2, reach);
+                for (int k = 0; k < kWpR; ++k)
+                    if (k == sl) lastuse[k] = t + min(j, run.n);
             }
-            F += nf;
+            t += run.n + 1;
+            i += run.n;
         }
         // after an abort, the copies already issued land before the CTA exits:
         // each slot's last fill completes its barrier (every fill arms all of its arrivals)
-        if (lane == 0 && *abortp) {
-            for (int k = 0; k < kWrR; ++k) {
-                const int f = F - ((F - k) % kWrR + kWrR) % kWrR;
-                if (f >= 0) bar_wait_drain(bar_xfull0 + 8 * k, (uint32_t)(f / kWrR) & 1u);
+        if (lane == 0 && *abortp)
+            for (int k = 0; k < kWpR; ++k) {
+                const int fl = (f - 1) - (((f - 1) - k) % kWpR + kWpR) % kWpR;
+                if (fl >= 0) bar_wait_drain(bar_full0 + 8 * k, (uint32_t)(fl / kWpR) & 1u);
             }
-            for (int k = 0; k < kWrD; ++k) {
-                const int j = (i - 1) - (((i - 1) - k) % kWrD + kWrD) % kWrD;
-                if (j >= 0) bar_wait_drain(bar_gfull0 + 8 * k, (uint32_t)(j / kWrD) & 1u);
-            }
-        }
     } else if (warp == 0) {
         if (lane == 0) {
-            int F = -1, issued = 0;
-            for (int i = 0; i < ntl; ++i) {
-                const int t = t0 + i;
-                const int y = t - (t / H) * H;
-                const int nf = (i == 0 || y == 0) ? 3 : 1;
-                bool ok = true;
-                for (int q = 0; q < nf && ok; ++q) {
-                    const int f = F + 1 + q;
-                    ok = bar_spin(bar_xfull0 + 8 * (f % kWrR), (uint32_t)(f / kWrR) & 1u, abortp, err.wait_ns);
-                }
-                F += nf;
-                const int k = i % kWrD;
-                if (!ok || !bar_spin(bar_gfull0 + 8 * k, (uint32_t)(i / kWrD) & 1u, abortp, err.wait_ns)) break;
-                tc_after_sync();
-                // row pairs (y - 1, y) and (y, y + 1): fills F - 2, F - 1 and F - 1, F in adjacent slots.
-                // The descriptors of one tile differ from these three by constants in the
-                // start-address field (byte offset / 16, no carry: shared addresses < 256 KB).
-                const uint64_t da0 = desc_mn(sX + (uint32_t)(((F - 2) % kWrR) * kWrSlot), kWgPlaneX);
-                const uint64_t da1 = desc_mn(sX + (uint32_t)(((F - 1) % kWrR) * kWrSlot), kWgPlaneX);
-                const uint64_t dg = desc_mn(sG + (uint32_t)(k * 8 * kWgPlaneG), kWgPlaneG);
-                const uint32_t acc0 = i > 0 ? 1u : 0u;
+            int fbase = 0, t = 0, waited = -1;
+            bool ok = true;
+            for (int i = 0; i < ntl && ok;) {
+                const WpRun run = wp_run(t0 + i, ntl - i, H, tiles_x);
+                for (int k = 0; k <= run.n && ok; ++k, ++t) {
+                    const int a = fbase + k;   // the step's fills a, a + 1
+                    for (int fw = waited + 1; fw <= a + 1 && ok; ++fw) {
+                        if (fw < a) continue;
+                        ok = bar_spin(bar_full0 + 8 * (fw % kWpR), (uint32_t)(fw / kWpR) & 1u, abortp, err.wait_ns);
+                    }
+                    if (!ok) break;
+                    waited = a + 1;
+                    tc_after_sync();
+                    // descriptors of the step: constant offsets (start-address field, byte
+                    // offset / 16, no carry: shared addresses < 256 KB) of two bases
+                    const uint64_t da = desc_mn(sX + (uint32_t)((a % kWpR) * kWpXSlot), kWgPlaneX);
+                    const uint64_t dg = desc_mn(sG + (uint32_t)((a % kWpR) * kWpGSlot), kWgPlaneG);
+                    const uint32_t acc0 = t > 0 ? 1u : 0u;
 #pragma unroll
-                for (int ks = 0; ks < kTile / 16; ++ks) {
+                    for (int ks = 0; ks < kTile / 16; ++ks)
 #pragma unroll
-                    for (int kx = 0; kx < 3; ++kx)
-#pragma unroll
-                        for (int pr = 0; pr < 2; ++pr)
-                            mma_wg(tmem + (uint32_t)((kx * 2 + pr) * 64),
-                                   (pr ? da1 : da0) + (uint64_t)(16 * ks + kx), dg + (uint64_t)(16 * ks),
+                        for (int kx = 0; kx < 3; ++kx)
+                            mma_wp(tmem + (uint32_t)(kx * 128), da + (uint64_t)(16 * ks + kx), dg + (uint64_t)(16 * ks),
                                    ks > 0 ? 1u : acc0);
+                    tc_commit(bar_done0 + 8 * (t % kWpD));
                 }
-                tc_commit(bar_done0 + 8 * k);
-                ++issued;
+                fbase += run.n + 2;
+                i += run.n;
             }
-            if (issued > 0) {   // every issued MMA done before the accumulators are read or released
+            if (t > 0) {   // every issued MMA done before the accumulators are read or released
                 tc_commit(bar_drain);
                 if (!bar_wait_drain(bar_drain, 0)) *abortp = 1;
             }
         }
         __syncwarp();
     } else {
-        // ---- bias: warp 2 + h sums the dY planes 4 h .. 4 h + 3, 16 contiguous bytes per pixel ----
+        // ---- bias: warp 2 + h sums the dY planes 4 h .. 4 h + 3 of every real dY row ----
         const int h = warp - 2;
         float bsum[4][8];   // planes 4 h + pl (channels 8 (4 h + pl) + e), pixels lane + 32 j
 #pragma unroll
         for (int pl = 0; pl < 4; ++pl)
 #pragma unroll
             for (int e = 0; e < 8; ++e) bsum[pl][e] = 0.0f;
-        for (int i = 0; i < ntl; ++i) {
-            const int k = i % kWrD;
-            if (!bar_wait(bar_gfull0 + 8 * k, (uint32_t)(i / kWrD) & 1u, abortp, err.wait_ns)) break;
+        int f = 0;
+        bool ok = true;
+        for (int i = 0; i < ntl && ok;) {
+            const WpRun run = wp_run(t0 + i, ntl - i, H, tiles_x);
+            for (int j = 0; j < run.n + 2; ++j, ++f) {
+                const int sl = f % kWpR;
+                if (!bar_wait(bar_full0 + 8 * sl, (uint32_t)(f / kWpR) & 1u, abortp, err.wait_ns)) {
+                    ok = false;
+                    break;
+                }
+                if (j >= 1 && j <= run.n) {
 #pragma unroll
-            for (int pl = 0; pl < 4; ++pl) {
-                const unsigned char* g = base + kWrG + (k * 8 + 4 * h + pl) * kWgPlaneG;
+                    for (int pl = 0; pl < 4; ++pl) {
+                        const unsigned char* g = base + kWpG + sl * kWpGSlot + (4 * h + pl) * kWgPlaneG;
 #pragma unroll
-                for (int j = 0; j < kTile / 32; ++j) {
-                    const uint4 r = *reinterpret_cast<const uint4*>(g + 16 * (lane + 32 * j));
-                    const __nv_bfloat162* hv = reinterpret_cast<const __nv_bfloat162*>(&r);
+                        for (int jj = 0; jj < kTile / 32; ++jj) {
+                            const uint4 r = *reinterpret_cast<const uint4*>(g + 16 * (lane + 32 * jj));
+                            const __nv_bfloat162* hv = reinterpret_cast<const __nv_bfloat162*>(&r);
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const float2 f = __bfloat1622float2(hv[e]);
-                        bsum[pl][2 * e] += f.x;
-                        bsum[pl][2 * e + 1] += f.y;
+                            for (int e = 0; e < 4; ++e) {
+                                const float2 v = __bfloat1622float2(hv[e]);
+                                bsum[pl][2 * e] += v.x;
+                                bsum[pl][2 * e + 1] += v.y;
+                            }
+                        }
                     }
                 }
+                bar_arrive(bar_bias0 + 8 * sl);
             }
-            bar_arrive(bar_bias0 + 8 * k);
+            i += run.n;
         }
 #pragma unroll
         for (int pl = 0; pl < 4; ++pl)
@@ -1157,25 +1181,28 @@ k_wgrad_tc(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const _
     __syncthreads();
     tc_after_sync();
     if (!*abortp) {
-        // warp w reads TMEM lanes 32 w .. 32 w + 31 of the six accumulators
+        // warp w reads TMEM lanes 32 w .. 32 w + 31: lanes < 64 are input row r (i = 0):
+        // columns 0..63 tap ky = 1, 64..127 ky = 0; lanes >= 64 (i = 1): columns 0..63 ky = 2
         const int L = 32 * warp + lane;
         const int ci = L & 63;
 #pragma unroll 1
-        for (int acc = 0; acc < 6; ++acc) {
-            const int kx = acc >> 1, pr = acc & 1;
-            uint32_t v[64];
-            const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(acc * 64);
-            PLBM_TMEM_LD32(v, 0, taddr);
-            PLBM_TMEM_LD32(v, 32, taddr + 32);
-            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-            if (pr == 1 && L < 64) continue;   // rows (y, y + 1), upper half: tap ky = 1 again
-            const int ky = pr == 0 ? (L < 64 ? 0 : 1) : 2;
-            float4* out = reinterpret_cast<float4*>(partial + (((size_t)blockIdx.x * 9 + ky * 3 + kx) * kC + ci) * kC);
+        for (int kx = 0; kx < 3; ++kx)
+#pragma unroll 1
+            for (int jc = 0; jc < 2; ++jc) {
+                if (warp >= 2 && jc == 1) continue;   // quadrant (1, 1): ky = 1 again
+                uint32_t v[64];
+                const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(kx * 128 + jc * 64);
+                PLBM_TMEM_LD32(v, 0, taddr);
+                PLBM_TMEM_LD32(v, 32, taddr + 32);
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                const int ky = L < 64 ? (jc == 0 ? 1 : 0) : 2;
+                float4* out =
+                    reinterpret_cast<float4*>(partial + (((size_t)blockIdx.x * 9 + ky * 3 + kx) * kC + ci) * kC);
 #pragma unroll
-            for (int c4 = 0; c4 < 16; ++c4)
-                out[c4] = make_float4(__uint_as_float(v[4 * c4]), __uint_as_float(v[4 * c4 + 1]),
-                                      __uint_as_float(v[4 * c4 + 2]), __uint_as_float(v[4 * c4 + 3]));
-        }
+                for (int c4 = 0; c4 < 16; ++c4)
+                    out[c4] = make_float4(__uint_as_float(v[4 * c4]), __uint_as_float(v[4 * c4 + 1]),
+                                          __uint_as_float(v[4 * c4 + 2]), __uint_as_float(v[4 * c4 + 3]));
+            }
         if (tid < kC) partial_b[(size_t)blockIdx.x * kC + tid] = red[tid];
     }
     tc_before_sync();
@@ -1830,7 +1857,7 @@ cudaError_t cnn_conv64_wgrad_tc(int B, int H, int W, const void* X, const void* 
     if (W % tc::kTile || H < 1 || B < 1) return cudaErrorInvalidValue;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(tc::k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kWrSmem);
+        cudaError_t e = cudaFuncSetAttribute(tc::k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kWpSmem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -1839,7 +1866,7 @@ cudaError_t cnn_conv64_wgrad_tc(int B, int H, int W, const void* X, const void* 
     if (em == cudaSuccess) em = encode_act_map(&mapG, dY, B, H, W);
     if (em != cudaSuccess) return em;
     const int grid = cnn_wgrad64_parts(B, H, W);   // one CTA per SM at most (the partial buffers' size)
-    tc::k_wgrad_tc<<<grid, tc::kWgsThreads, tc::kWrSmem, s>>>(B, H, W, mapX, mapG, static_cast<const __nv_bfloat16*>(X),
+    tc::k_wgrad_tc<<<grid, tc::kWgsThreads, tc::kWpSmem, s>>>(B, H, W, mapX, mapG, static_cast<const __nv_bfloat16*>(X),
                                                              partial, partial_b, err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
