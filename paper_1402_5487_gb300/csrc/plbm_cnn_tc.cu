@@ -1021,68 +1021,79 @@ k_wgrad_tc(int B, int H, int W, const __grid_constant__ CUtensorMap tmX, const _
         int lastuse[kWpR];   // the last step that reads the fill in each slot
 #pragma unroll
         for (int k = 0; k < kWpR; ++k) lastuse[k] = -1;
-        int f = 0, t = 0;    // fills and steps so far
-        bool stop = false;
-        for (int i = 0; i < ntl && !stop;) {
-            const WpRun run = wp_run(t0 + i, ntl - i, H, tiles_x);
-            for (int j = 0; j < run.n + 2; ++j, ++f) {
-                const int sl = f % kWpR;
-                if (f >= kWpR) {   // the slot's previous fill: its last step's MMAs done, its dY summed
-                    int u = -1;
-#pragma unroll
-                    for (int k = 0; k < kWpR; ++k)
-                        if (k == sl) u = lastuse[k];
-                    if (!bar_wait(bar_done0 + 8 * (u % kWpD), (uint32_t)(u / kWpD) & 1u, abortp, err.wait_ns) ||
-                        !bar_wait(bar_bias0 + 8 * sl, (uint32_t)((f - kWpR) / kWpR) & 1u, abortp, err.wait_ns)) {
-                        stop = true;
-                        break;
-                    }
-                }
-                const bool zero = j == 0 || j == run.n + 1;   // dY rows y - 1 and y + n
-                const int xr = wrapi(run.y - 1 + j, H), gr = run.y - 1 + j;
-                const int ncopy = sl == 0 ? 2 : 1;
-                const uint32_t full = bar_full0 + 8 * sl;
-                if (lane == 0) bar_arrive_expect_tx(full, (uint32_t)ncopy * (zero ? kWpRowTx : 2 * kWpRowTx));
-                __syncwarp();
-                if (lane < 8) {
-                    const int c = lane;
-                    const size_t row = ((size_t)run.b * H + xr) * W;
-                    const uint4 lft =
-                        __ldg(reinterpret_cast<const uint4*>(X + (row + wrapi(run.x0 - 1, W)) * kC + 8 * c));
-                    const uint4 rgt =
-                        __ldg(reinterpret_cast<const uint4*>(X + (row + wrapi(run.x0 + kTile, W)) * kC + 8 * c));
-                    for (int dup = 0; dup < ncopy; ++dup) {
-                        const int s = dup ? kWpR : sl;
-                        const uint32_t plane = sX + (uint32_t)(s * kWpXSlot + c * kWgPlaneX);
-                        tma_load_5d(plane + 16, &tmX, 0, c, run.x0, xr, run.b, full);
-                        asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n" ::"r"(plane), "r"(lft.x),
-                                     "r"(lft.y), "r"(lft.z), "r"(lft.w)
-                                     : "memory");
-                        asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n" ::"r"(plane + 16 * (kWgRowPix - 1)),
-                                     "r"(rgt.x), "r"(rgt.y), "r"(rgt.z), "r"(rgt.w)
-                                     : "memory");
-                        if (zero) {
-                            const uint32_t gp = sG + (uint32_t)(s * kWpGSlot + c * kWgPlaneG);
-                            for (int e = 0; e < kWgPlaneG / 16; ++e)
-                                asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};\n" ::"r"(gp + 16 * e), "r"(0u)
-                                             : "memory");
-                        }
-                    }
-                    fence_async_smem();
-                    bar_arrive(full);
-                } else if (lane >= 24 && !zero) {
-                    const int c = lane - 24;
-                    for (int dup = 0; dup < ncopy; ++dup)
-                        tma_load_5d(sG + (uint32_t)((dup ? kWpR : sl) * kWpGSlot + c * kWgPlaneG), &tmG, 0, c,
-                                    run.x0, gr, run.b, full);
-                }
-                // fill j of the run is read by its steps j - 1 and j (0 .. n)
+        // the fill in hand: fill j of the run that starts at output row t0 + i; the
+        // halo chunks of the next fill are loaded while this one is staged, so that
+        // their latency is not paid fill after fill
+        int i = 0, j = 0, f = 0, t = 0;   // t: the first step of the run
+        WpRun run = wp_run(t0, ntl, H, tiles_x);
+        uint4 lft = make_uint4(0u, 0u, 0u, 0u), rgt = lft;
+        auto halo = [&](const WpRun& r, int jj, int c) {
+            const size_t row = ((size_t)r.b * H + wrapi(r.y - 1 + jj, H)) * W;
+            lft = __ldg(reinterpret_cast<const uint4*>(X + (row + wrapi(r.x0 - 1, W)) * kC + 8 * c));
+            rgt = __ldg(reinterpret_cast<const uint4*>(X + (row + wrapi(r.x0 + kTile, W)) * kC + 8 * c));
+        };
+        if (lane < 8) halo(run, 0, lane);
+        for (;;) {
+            const int sl = f % kWpR;
+            if (f >= kWpR) {   // the slot's previous fill: its last step's MMAs done, its dY summed
+                int u = -1;
 #pragma unroll
                 for (int k = 0; k < kWpR; ++k)
-                    if (k == sl) lastuse[k] = t + min(j, run.n);
+                    if (k == sl) u = lastuse[k];
+                if (!bar_wait(bar_done0 + 8 * (u % kWpD), (uint32_t)(u / kWpD) & 1u, abortp, err.wait_ns) ||
+                    !bar_wait(bar_bias0 + 8 * sl, (uint32_t)((f - kWpR) / kWpR) & 1u, abortp, err.wait_ns))
+                    break;
             }
-            t += run.n + 1;
-            i += run.n;
+            const bool zero = j == 0 || j == run.n + 1;   // dY rows y - 1 and y + n
+            const int xr = wrapi(run.y - 1 + j, H), gr = run.y - 1 + j;
+            const int ncopy = sl == 0 ? 2 : 1;
+            const uint32_t full = bar_full0 + 8 * sl;
+            if (lane == 0) bar_arrive_expect_tx(full, (uint32_t)ncopy * (zero ? kWpRowTx : 2 * kWpRowTx));
+            __syncwarp();
+            if (lane < 8) {
+                const int c = lane;
+                for (int dup = 0; dup < ncopy; ++dup) {
+                    const int s = dup ? kWpR : sl;
+                    const uint32_t plane = sX + (uint32_t)(s * kWpXSlot + c * kWgPlaneX);
+                    tma_load_5d(plane + 16, &tmX, 0, c, run.x0, xr, run.b, full);
+                }
+                for (int dup = 0; dup < ncopy; ++dup) {
+                    const int s = dup ? kWpR : sl;
+                    const uint32_t plane = sX + (uint32_t)(s * kWpXSlot + c * kWgPlaneX);
+                    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n" ::"r"(plane), "r"(lft.x), "r"(lft.y),
+                                 "r"(lft.z), "r"(lft.w)
+                                 : "memory");
+                    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n" ::"r"(plane + 16 * (kWgRowPix - 1)),
+                                 "r"(rgt.x), "r"(rgt.y), "r"(rgt.z), "r"(rgt.w)
+                                 : "memory");
+                    if (zero) {
+                        const uint32_t gp = sG + (uint32_t)(s * kWpGSlot + c * kWgPlaneG);
+                        for (int e = 0; e < kWgPlaneG / 16; ++e)
+                            asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};\n" ::"r"(gp + 16 * e), "r"(0u)
+                                         : "memory");
+                    }
+                }
+                fence_async_smem();
+                bar_arrive(full);
+            } else if (lane >= 24 && !zero) {
+                const int c = lane - 24;
+                for (int dup = 0; dup < ncopy; ++dup)
+                    tma_load_5d(sG + (uint32_t)((dup ? kWpR : sl) * kWpGSlot + c * kWgPlaneG), &tmG, 0, c, run.x0, gr,
+                                run.b, full);
+            }
+            // fill j of the run is read by its steps j - 1 and j (0 .. n)
+#pragma unroll
+            for (int k = 0; k < kWpR; ++k)
+                if (k == sl) lastuse[k] = t + min(j, run.n);
+            ++f;
+            if (++j == run.n + 2) {   // the next run
+                t += run.n + 1;
+                i += run.n;
+                if (i >= ntl) break;
+                run = wp_run(t0 + i, ntl - i, H, tiles_x);
+                j = 0;
+            }
+            if (lane < 8) halo(run, j, lane);
         }
         // after an abort, the copies already issued land before the CTA exits:
         // each slot's last fill completes its barrier (every fill arms all of its arrivals)
