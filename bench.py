@@ -589,6 +589,44 @@ def run_case(torch, args):
     return out
 
 
+def variant_summary(variants, peak):
+    """The variants' headline figures in a few hundred characters, last on the line (a reader
+    that keeps only the end of a long line still sees them): MLUPS, fraction of the measured
+    copy bandwidth for the HBM-bound ones, the surrogate's speedups and errors."""
+    out = {}
+
+    def put(key, name, field="mlups", nd=0):
+        v = variants.get(name) or {}
+        if field in v and v[field] is not None:
+            out[key] = round(v[field], nd) if nd else int(round(v[field]))
+
+    put("f16dev_mlups", "kh2048_f16dev")
+    put("bf16dev_mlups", "kh2048_bf16dev")
+    put("f16dev_vs_f32", "kh2048_f16dev", "speedup_vs_f32", 2)
+    put("f64_mlups", "kh2048_f64")
+    put("odd2047_f32_mlups", "kh2047_f32_plain_layout")
+    put("slabs4_f32_mlups", "kh2048_f32_4slabs")
+    put("diag_every10_overhead", "kh2048_f32_diagnostics_every_10", "overhead", 3)
+    for prec in ("f32", "f16dev", "bf16dev"):
+        put("d3q125_256_%s_frac" % prec, "kh3d256_d3q125_%s" % prec, "frac_of_measured_hbm", 3)
+    b = next((v for k, v in variants.items() if k.startswith("batched_")), None) or {}
+    if "persistent_graph" in b:
+        out["batched_mlups"] = int(round(b["persistent_graph"]["mlups"]))
+        out["batched_frac"] = round(b["persistent_graph"]["gbs_algorithmic"] / peak, 3)
+        out["batched_vs_per_instance"] = round(b.get("speedup_persistent_graph_vs_per_instance", 0.0), 2)
+    s = variants.get("surrogate_kh256") or {}
+    if "gain_test" in s:
+        g = {}
+        for tol, r in s["gain_test"]["by_tol"].items():
+            g[tol] = [round(r["speedup"], 2), round(r["fallback_rate"], 2),
+                      round(r["u_error_after_4_advances_vs_lbm"], 3)]
+        out["surrogate_gain_speedup_fallback_uerr4"] = g
+        out["surrogate_advance_speedup_b64"] = round(s["speed_one_advance"]["64"]["speedup_vs_lbm"], 2)
+        out["surrogate_train_tflops"] = round(s["training"]["tflops"], 1)
+        out["surrogate_heldout_mse"] = round(s["test_mse_normalised"]["network"], 3)
+    return out
+
+
 def cpu_oracle_sample(L, seconds=12.0, max_steps=50):
     """Time the FP64 oracle as it stands on this host's cores on an L x L KH grid."""
     import oracle as O
@@ -851,7 +889,7 @@ def main():
                             "ms_per_step_each": [r / args.steps * 1e3 for r in runs],
                             "spread": (max(runs) - min(runs)) / t},
                 "e2e": e2e, "gpu_launches": args.steps, "clocks": clock_info,
-                "cpu_baseline": cpu, "variants": variants}
+                "cpu_baseline": cpu, "variants": variants, "variant_summary": variant_summary(variants, peak)}
         print(json.dumps(json_safe(line)))
     if dist is not None:
         dist.destroy_process_group()
