@@ -196,21 +196,25 @@ class Surrogate:
         torch = self.torch
         rng = np.random.default_rng(seed)
         npix = self.H * self.W
+        # every minibatch's pair indices on the device before the first step: the
+        # steps run on the surrogate's stream while the host goes ahead, so an
+        # index buffer rewritten per step would be read by a later step's copy
+        sels = np.empty((steps, batch, 2), dtype=np.int32)
         order = rng.permutation(len(pairs))
         pos = 0
-        pairs_dev = torch.empty((batch, 2), dtype=torch.int32, device="cuda")
-        losses = []
-        lr_end = lr if lr_end is None else lr_end
         for it in range(steps):
             if pos + batch > len(order):
                 order = rng.permutation(len(pairs))
                 pos = 0
-            sel = pairs[order[pos:pos + batch]]
+            sels[it] = pairs[order[pos:pos + batch]]
             pos += batch
-            pairs_dev.copy_(torch.from_numpy(sel), non_blocking=False)
-            torch.cuda.current_stream().synchronize()
-            self._ok(plbm.lib().plbm_sur_assemble_noise(self.h, stack.data_ptr(), npix, pairs_dev.data_ptr(), batch,
-                                                        self.x.data_ptr(), self.y.data_ptr(), float(noise),
+        pairs_all = torch.from_numpy(sels).to("cuda")
+        torch.cuda.current_stream().synchronize()
+        losses = []
+        lr_end = lr if lr_end is None else lr_end
+        for it in range(steps):
+            self._ok(plbm.lib().plbm_sur_assemble_noise(self.h, stack.data_ptr(), npix, pairs_all[it].data_ptr(),
+                                                        batch, self.x.data_ptr(), self.y.data_ptr(), float(noise),
                                                         (int(seed) << 32) + it))
             frac = it / max(1, steps - 1)
             lr_t = lr * (lr_end / lr) ** frac

@@ -416,3 +416,42 @@ def test_one_launch_per_model_equals_one_launch_per_lattice(trained):
         assert x.diagnostics()["steps"] == y.diagnostics()["steps"] == 96
     for s in same + mixed + alone:
         s.close()
+
+
+@pytest.mark.parametrize("tc", [True, False])
+def test_gradients_are_bitwise_reproducible(tc):
+    # Every reduction of the backward pass has a fixed order (per-CTA partial sums
+    # over fixed tile ranges, then an ordered sum over the CTAs), so the same pass
+    # on the same inputs gives the same bits; at the training shape (16 lattices
+    # of 256 x 256) the weight-gradient CTAs' row ranges cross columns and lattices.
+    import torch
+    B = 16
+    net = SG.Surrogate(B, H=256, W=256, seed=5)
+    net.set_tensor_path(tc)
+    g = torch.Generator().manual_seed(9)
+    x = torch.randn((B, 256, 256, 4), generator=g).to(torch.bfloat16).cuda()
+    dout = (0.01 * torch.randn((B, 256, 256, 4), generator=g)).cuda()
+    first = net.backward(x, dout, B).copy()
+    for _ in range(3):
+        again = net.backward(x, dout, B)
+        assert np.array_equal(again, first), np.flatnonzero(again != first)[:10]
+    assert net.check() == plbm.PLBM_OK
+    net.close()
+
+
+def test_training_is_bitwise_reproducible():
+    # The same data, seed and steps give the same weights: the minibatches are the
+    # seeded draw (their indices reach the device before the steps, which run
+    # ahead of the host), the noise is counter-based and every step deterministic.
+    L, snaps = 128, 3
+    stack = SG.generate(range(8), L=L, snaps=snaps, chunk=8)
+    pairs = SG.pairs_of(8, snaps)
+    norm = SG.fit_norm(stack, pairs)
+    ws = []
+    for _ in range(2):
+        net = SG.Surrogate(4, H=L, W=L, seed=2)
+        net.set_norm(*norm)
+        net.train(stack, pairs, 40, batch=4, lr=1e-3, seed=3, noise=0.2)
+        ws.append(net.params()[0].copy())
+        net.close()
+    assert np.array_equal(ws[0], ws[1])
